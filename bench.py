@@ -1,0 +1,389 @@
+"""Benchmark: queries/s of the norm-ranging LSH hot path at recall@10 >= 0.9.
+
+One step = one pass of the whole path over one batch of synthetic input:
+index build (norms, percentile partition, SIMPLE-LSH transform, sign-random-
+projection codes, bucket order) over the resident items, then the query batch
+(hash, Hamming histograms, bucket walk, candidate selection, exact re-rank,
+top-k).  Workload: the Netflix-sized preset (n = 17,770 items, d = 300 fp32,
+lognormal(0, 0.8) norms, m = 32, L = 32, 1,000 unit queries per GPU, top-10);
+the probe budget B and eps are calibrated (untimed) as the smallest B of the
+1%..20% sweep (and the smallest eps of 0.1/0.2/0.3) that reaches recall@10 >= 0.9
+against the exact top-10 (the same library at B = n, which the parity tests pin
+to exact MIPS).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU: each rank builds its own replica of
+the index and answers its own query batch (weak scaling, no data-path
+collective).  --impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1809_08782_gb300 import workloads as W  # noqa: E402
+
+METRIC = "queries/s at recall@10>=0.9, plain FP32 vs BF16-batched; HBM GB/s; p50/p99 ms"
+WORKLOAD = "netflix-n17770-d300"
+EPS_CHOICES = (0.1, 0.2, 0.3)
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP32 CUDA-core rate for the ALU roofline: 152 SMs x 128 FMA lanes x 2 flop x clock
+SMS, FP32_LANES = 152, 128
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="nrlsh_clocks_", suffix=".csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1809_08782_gb300.nrlsh as N
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1809_08782_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    N.load()
+
+    w = W.make_workload(WORKLOAD)
+    Qh = W.gen_queries(w.nq, w.d, w.query_seed + 7919 * rank)
+    X = torch.from_numpy(w.items).to(dev)
+    Q = torch.from_numpy(Qh).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # -------- calibration (untimed): exact top-10 and the (eps, B) operating point
+    idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=0.1)
+    truth, _ = N.nrlsh_query_ex(idx, Q, w.k, w.n)
+    truth = truth.cpu().numpy()
+    idx.free()
+
+    def recall(ids):
+        ids = ids.cpu().numpy()
+        return float(np.mean([len(set(ids[i]) & set(truth[i])) for i in range(len(ids))])) / w.k
+
+    chosen = None
+    best = (0.0, None, None)
+    for eps in EPS_CHOICES:
+        idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=float(np.float32(eps)))
+        for B_ in w.budget_sweep:
+            ids, _ = N.nrlsh_query_ex(idx, Q, w.k, B_)
+            r = recall(ids)
+            if r > best[0]:
+                best = (r, eps, B_)
+            if r >= 0.9:
+                if chosen is None or B_ < chosen[1]:
+                    chosen = (eps, B_, r)
+                break
+        idx.free()
+    if chosen is None:
+        chosen = (best[1], best[2], best[0])
+    eps, budget, rec = chosen
+    eps = float(np.float32(eps))
+
+    def step():
+        ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps)
+        ids, sc = N.nrlsh_query_ex(ix, Q, w.k, budget)
+        return ix, ids
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    for _ in range(args.warmup):
+        ix, _ = step()
+        ix.free()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = N.nrlsh_launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix, ids = step()
+        e1.record(stream)
+        ix.free()                       # synchronises; outside the timed region
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = N.nrlsh_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    ms_step = float(np.mean(times))
+    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = w.nq * world / (ms_max / 1e3)
+
+    # -------- per-kernel times: the same steps again with event brackets on
+    N.nrlsh_set_profiling(True)
+    N.nrlsh_profile_read()
+    for _ in range(args.steps):
+        flush.zero_()
+        ix, _ = step()
+        ix.free()
+    torch.cuda.synchronize()
+    prof = N.nrlsh_profile_read()
+    N.nrlsh_set_profiling(False)
+
+    # -------- end to end through the public API with host buffers
+    Xh = torch.from_numpy(w.items).pin_memory()
+    Qp = torch.from_numpy(Qh).pin_memory()
+    ids_h = torch.empty((w.nq, w.k), dtype=torch.int64).pin_memory()
+    sc_h = torch.empty((w.nq, w.k), dtype=torch.float32).pin_memory()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = N.nrlsh_build_ex(Xh, w.m, w.L, w.index_seed, eps=eps)
+        N.nrlsh_query_ex(ix, Qp, w.k, budget, ids=ids_h, scores=sc_h)
+        t1 = time.perf_counter()
+        ix.free()
+        if i >= args.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_ms = float(np.mean(e2e_t)) * 1e3
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = w.nq * world / (float(te.item()) / 1e3)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded Gaussian directions, lognormal norms)",
+            "form": "plain_fp32",
+            "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "m": w.m, "L": w.L,
+                       "queries_per_gpu": w.nq, "k": w.k, "probe_budget": budget,
+                       "eps": eps, "recall_at_10": rec,
+                       "step": "index build + query batch",
+                       "l2": "flushed (512 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(np.percentile(times, 50)),
+                           "p99": float(np.percentile(times, 99))},
+            "e2e": {"value": e2e_value, "unit": "queries/s",
+                    "h2d_bytes_per_step": int(w.items.nbytes + Qh.nbytes),
+                    "d2h_bytes_per_step": int(w.nq * w.k * (8 + 4))},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        line["roofline"] = roofline(prof, w, budget, args.steps)
+        line["kernels_ms_per_step"] = {k: v[0] / args.steps for k, v in
+                                       sorted(prof.items(), key=lambda kv: -kv[1][0])}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, Qh, eps, budget)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def algorithmic(name: str, w, budget: int):
+    """(kind, units per launch) for the kernels whose roofline is stated:
+    bytes for HBM-bound kernels, flops for ALU-bound ones (per launch of one step)."""
+    n, d, L, nq, k = w.n, w.d, w.L, w.nq, w.k
+    cb = 4 if L <= 32 else 8
+    if name.startswith("rerank_fp32"):
+        return "alu", 2.0 * nq * budget * d
+    if name.startswith("project_fp32"):
+        return "hbm", float(n * d * 4 + n * cb + n * 12)
+    if name.startswith("hist"):
+        return "hbm", float(n * cb * -(-nq // 128) + nq * w.m * (L + 1) * 4)
+    if name.startswith("select"):
+        return "hbm", float(nq * (n * cb + budget * 4))
+    if name.startswith("topk"):
+        return "hbm", float(nq * budget * 8)
+    if name.startswith("sqnorm"):
+        return "hbm", float(n * d * 4 + n * 8)
+    return None, None
+
+
+def roofline(prof: dict, w, budget: int, steps: int):
+    hbm, sm_mhz, src = peaks()
+    if not prof:
+        return None
+    name, (ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    kind, units = algorithmic(name, w, budget)
+    per_launch_ms = ms / max(launches, 1)
+    if kind is None:
+        return {"kernel": name, "bound": None, "note": "no algorithmic model for this kernel"}
+    launches_per_step = launches / steps
+    units_per_launch = units / launches_per_step
+    if kind == "hbm":
+        achieved = units_per_launch / (per_launch_ms * 1e-3) / 1e9
+        peak = hbm
+        unit = "GB/s"
+        peak_src = f"hbm_gbs of {src} peaks"
+    else:
+        achieved = units_per_launch / (per_launch_ms * 1e-3) / 1e12
+        peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        unit = "TFLOP/s"
+        peak_src = f"FP32 FMA rate at {sm_mhz:.0f} MHz (152 SMs x 128 lanes)"
+    return {"kernel": name, "bound": kind, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+            "launch_ms": per_launch_ms}
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+def cpu_baseline(w, Qh, eps, budget, target_s: float = 12.0):
+    """The oracle as it stands, single-threaded NumPy on the host: one full index
+    build plus as many queries as fit in about `target_s` seconds; scaled to a step
+    (build + the whole query batch)."""
+    from oracle import nrlsh as O
+    X64 = W.items_to_f64(w.items, w.dtype)
+    t0 = time.perf_counter()
+    ref = O.build(X64, w.m, w.L, w.index_seed, eps=eps)
+    t_build = time.perf_counter() - t0
+    done = 0
+    t1 = time.perf_counter()
+    while done < w.nq and time.perf_counter() - t1 < target_s:
+        O.query(ref, Qh[done:done + 10].astype(np.float64), w.k, budget)
+        done += min(10, w.nq - done)
+    t_q = (time.perf_counter() - t1) / done
+    step_s = t_build + t_q * w.nq
+    return {"value": w.nq / step_s, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"index build over all {w.n} items + {done} of {w.nq} queries, "
+                      f"scaled to build + {w.nq} queries"}
+
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from oracle import nrlsh as O
+    w = W.make_workload(WORKLOAD)
+    Qh = W.gen_queries(w.nq, w.d, w.query_seed)
+    X64 = W.items_to_f64(w.items, w.dtype)
+    eps, budget = float(np.float32(0.3)), w.budget_sweep[2]
+    sample_q = 40
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ref = O.build(X64, w.m, w.L, w.index_seed, eps=eps)
+        O.query(ref, Qh[:sample_q].astype(np.float64), w.k, budget)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    step_s = float(np.mean(times))
+    value = sample_q / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "m": w.m, "L": w.L,
+                       "queries_per_step": sample_q, "k": w.k, "probe_budget": budget,
+                       "eps": eps, "step": "index build + query sample"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"index build over all {w.n} items + {sample_q} queries per step"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(var, "1")
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

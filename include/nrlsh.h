@@ -1,0 +1,197 @@
+/*
+ * nrlsh.h - C ABI of the GB300 norm-ranging LSH library (libnrlsh.so).
+ *
+ * Norm-ranging LSH for maximum inner product search (Yan, Li, Dai, Chen, Cheng,
+ * NeurIPS 2018).  Given items x_1..x_n in R^d and a query q, MIPS returns the
+ * item(s) with the largest q^T x (Eq. 1).  The index partitions the items into m
+ * sub-datasets by 2-norm percentile, normalises each by its own largest norm U_j,
+ * applies the SIMPLE-LSH transform P(x) = [x/U_j; sqrt(1 - ||x/U_j||^2)]
+ * (Algorithm 1, Eq. 8) and stores L-bit sign-random-projection codes (Eq. 4).
+ * A query probes buckets (sub-dataset j, number of identical bits l) in
+ * descending order of s_hat = U_j cos[pi (1 - eps)(1 - l/L)] (Eq. 12 and the
+ * sorted (U_j, l) structure of Section 3.3) until the probe budget B is reached,
+ * re-ranks the probed items by exact inner product and returns the top k.
+ *
+ * Determinism.  Every floating-point value that decides an integer result is
+ * fixed by a rule, so results are a deterministic function of the inputs:
+ *   - squared norms s_x: FP64 sum of x_k^2 over k = 0..d-1 in order;
+ *   - ranking for the partition: (s_x, id) ascending; sub-dataset j holds ranks
+ *     [floor(j n / m), floor((j+1) n / m)); U_j^2 = max s_x in S_j;
+ *   - code bit b of x in S_j: [fl(sum_k a_{k,b} x_k + fl(a_{d,b} tau_x)) >= 0] in
+ *     FP64 with the sum taken in order k = 0..d-1, tau_x = fl(sqrt(fl(U_j^2 - s_x)))
+ *     (tau_x = 1 if U_j = 0); query bit b: [sum_k a_{k,b} q_k >= 0] likewise.
+ *     Fast tiers compute the projection in FP32 (or BF16 on tensor cores) with a
+ *     proven error bound and recompute the undecided (item, bit) pairs in FP64;
+ *   - A: (d+1) x L entries, Philox4x64-10 (Salmon et al., SC'11) with counter
+ *     (row, col, 0, 0) and key (seed, 0), Box-Muller, rounded to bfloat16;
+ *   - bucket order: s_hat = fl(U_j * c_l) with c_l = cos(pi (1-eps)(L-l)/L)
+ *     correctly rounded, descending; ties by larger l, then larger j;
+ *   - candidates: the first min(B, n) items in (bucket order, item id) order;
+ *   - scores: FP64 sum of q_k x_k in order k = 0..d-1; top-k by (score desc,
+ *     id asc); the reported score is that FP64 value rounded to fp32.
+ *
+ * Memory and streams.  Unless stated otherwise pointers may be device pointers
+ * (any CUDA allocation of the current device, e.g. from PyTorch) or host
+ * pointers; host buffers are staged through device memory and the call then
+ * synchronises its stream before returning.  With device pointers only, calls
+ * are asynchronous on `stream` (NULL = the legacy default stream).  The caller
+ * keeps ownership of every buffer it passes; the index owns a copy of the items
+ * and everything it derives from them.  Query calls allocate their scratch
+ * with the stream-ordered allocator and free it on the same stream.
+ *
+ * Errors.  Every entry point validates its arguments before launching any work
+ * and returns a status; a thread-local message is available from
+ * nrlsh_last_error().  A CUDA error (including a sticky error left by earlier
+ * work) is reported as NRLSH_ERR_CUDA.  No entry point aborts the process.
+ */
+#ifndef NRLSH_H
+#define NRLSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define NRLSH_API __attribute__((visibility("default")))
+#else
+#define NRLSH_API
+#endif
+
+typedef struct nrlsh_index nrlsh_index;
+
+typedef enum nrlsh_status {
+    NRLSH_OK = 0,
+    NRLSH_ERR_ARG = -1,          /* an argument is out of range or a pointer is NULL */
+    NRLSH_ERR_OOM = -2,          /* a device or host allocation failed */
+    NRLSH_ERR_CUDA = -3,         /* a CUDA call failed */
+    NRLSH_ERR_TIMEOUT = -4,      /* a bounded device wait ran out */
+    NRLSH_ERR_UNSUPPORTED = -5   /* valid request this build does not support */
+} nrlsh_status;
+
+typedef enum nrlsh_dtype {
+    NRLSH_F32 = 0,               /* items are float32, row-major n x d */
+    NRLSH_BF16 = 1               /* items are bfloat16, row-major n x d */
+} nrlsh_dtype;
+
+/* Query flags. */
+#define NRLSH_WHOLE_BUCKETS 0x1u /* probe the boundary bucket whole (|C| may exceed B) */
+
+/* Limits checked by the entry points. */
+#define NRLSH_MAX_L 64
+#define NRLSH_MAX_BUCKETS 16384  /* m * (L + 1) */
+#define NRLSH_MAX_K 1024
+
+typedef struct nrlsh_info {
+    int64_t n;
+    int32_t d;
+    int32_t m;
+    int32_t L;
+    int32_t dtype;               /* nrlsh_dtype */
+    float eps;
+    uint64_t seed;
+    int32_t code_bytes;          /* 4 for L <= 32, 8 otherwise */
+    int32_t row_stride;          /* elements per stored item row (d rounded up to 8) */
+    int64_t device_bytes;        /* device memory owned by the index */
+    int64_t ambiguous_bits;      /* (item, bit) pairs the fast tier left to FP64 */
+} nrlsh_info;
+
+/*
+ * Index building (Algorithm 1).
+ *   items   n x d row-major fp32 (nrlsh_build) or `dtype` (nrlsh_build_ex)
+ *   n >= 1, d >= 1, 1 <= m <= n, 1 <= L <= 64, m * (L + 1) <= NRLSH_MAX_BUCKETS,
+ *   0 < eps < 1 (nrlsh_build uses eps = 0.1), seed selects A.
+ * On success *out receives a new index, released with nrlsh_free().  The items
+ * are copied; the caller may free them once the call (and, for device items,
+ * the work it queued on `stream`) has finished.
+ */
+NRLSH_API nrlsh_status nrlsh_build(const float* items, int64_t n, int32_t d, int32_t m,
+                                   int32_t L, uint64_t seed, nrlsh_index** out);
+NRLSH_API nrlsh_status nrlsh_build_ex(const void* items, int64_t n, int32_t d, int32_t m,
+                                      int32_t L, uint64_t seed, nrlsh_dtype dtype, float eps,
+                                      void* stream, nrlsh_index** out);
+
+/*
+ * Query processing (Section 3.3 multi-probe, exact re-rank, top-k; Eq. 1).
+ *   queries       nq x d row-major fp32 (not normalised by the library)
+ *   nq >= 0, 1 <= k <= NRLSH_MAX_K, probe_budget >= 1 (values above n act as n)
+ *   ids           nq x k int64: original item ids, best first; -1 past the end
+ *                 when fewer than k items were probed
+ *   scores        nq x k fp32: the matching inner products; -inf past the end
+ * nrlsh_query runs on the legacy default stream with no flags.
+ */
+NRLSH_API nrlsh_status nrlsh_query(const nrlsh_index* index, const float* queries, int64_t nq,
+                                   int32_t k, int64_t probe_budget, int64_t* ids,
+                                   float* scores);
+NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* index, const float* queries,
+                                      int64_t nq, int32_t k, int64_t probe_budget,
+                                      uint32_t flags, int64_t* ids, float* scores,
+                                      void* stream);
+
+/*
+ * Introspection of the query path, for testing against a reference.  Device or
+ * host pointers as above.
+ * nrlsh_hash_queries: codes (nq uint64; bit b of the code is hash bit b).
+ * nrlsh_query_histograms: H (nq x m x (L+1) uint32), H[q][j][l] = number of
+ *   items of sub-dataset j sharing exactly l hash bits with query q.
+ * nrlsh_query_candidates: the probed items of each query (Section 3.3):
+ *   cand (nq x cap int32 original ids) and count (nq int64).  For each query the
+ *   ids of the buckets probed whole come first, in storage order (sub-dataset,
+ *   then id), followed by the items taken from the boundary bucket, by id.  Fails
+ *   with NRLSH_ERR_ARG if a query has more than `cap` candidates (count is still
+ *   written).  Without NRLSH_WHOLE_BUCKETS, count = min(B, n).
+ */
+NRLSH_API nrlsh_status nrlsh_hash_queries(const nrlsh_index* index, const float* queries,
+                                          int64_t nq, uint64_t* codes, void* stream);
+NRLSH_API nrlsh_status nrlsh_query_histograms(const nrlsh_index* index, const float* queries,
+                                              int64_t nq, uint32_t* H, void* stream);
+NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* index, const float* queries,
+                                              int64_t nq, int64_t probe_budget, uint32_t flags,
+                                              int64_t cap, int32_t* cand, int64_t* count,
+                                              void* stream);
+
+/*
+ * Index introspection.  These copy into caller-owned HOST buffers and
+ * synchronise the index's build stream.
+ * nrlsh_get_codes:       n uint64 codes in original id order.
+ * nrlsh_get_partition:   sub_of_id (n int32), U2 (m doubles, U_j^2), sqnorm (n doubles,
+ *                        s_x in id order); any of the three may be NULL.
+ * nrlsh_get_projections: A ((d+1) x L floats, row-major; every value is bf16).
+ * nrlsh_get_buckets:     the probing order: bucket_j, bucket_l (m(L+1) int32 each)
+ *                        and s_hat (m(L+1) doubles) in probing order; any may be NULL.
+ * nrlsh_get_info:        sizes and build statistics.
+ */
+NRLSH_API nrlsh_status nrlsh_get_codes(const nrlsh_index* index, uint64_t* codes);
+NRLSH_API nrlsh_status nrlsh_get_partition(const nrlsh_index* index, int32_t* sub_of_id,
+                                           double* U2, double* sqnorm);
+NRLSH_API nrlsh_status nrlsh_get_projections(const nrlsh_index* index, float* A);
+NRLSH_API nrlsh_status nrlsh_get_buckets(const nrlsh_index* index, int32_t* bucket_j,
+                                         int32_t* bucket_l, double* s_hat);
+NRLSH_API nrlsh_status nrlsh_get_info(const nrlsh_index* index, nrlsh_info* info);
+
+/* Releases the index and its device memory (after synchronising its stream). */
+NRLSH_API void nrlsh_free(nrlsh_index* index);
+
+/* Message for the last failed call on this thread ("" if none). */
+NRLSH_API const char* nrlsh_last_error(void);
+
+/*
+ * Instrumentation.  nrlsh_launch_count: kernels this library has launched in
+ * this process.  With profiling on, every kernel launch is bracketed by CUDA
+ * events on its stream; nrlsh_profile_read synchronises those events, adds up
+ * the time per kernel name and clears the record.  names receives a
+ * '\n'-separated list (up to names_cap bytes), ms and launches one entry per
+ * name (up to cap).  Returns the number of distinct names through *count.
+ */
+NRLSH_API uint64_t nrlsh_launch_count(void);
+NRLSH_API nrlsh_status nrlsh_set_profiling(int32_t enable);
+NRLSH_API nrlsh_status nrlsh_profile_read(char* names, int64_t names_cap, double* ms,
+                                          int64_t* launches, int32_t cap, int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRLSH_H */

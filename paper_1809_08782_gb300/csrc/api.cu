@@ -1,0 +1,728 @@
+// C ABI of libnrlsh.so: argument checks, device memory ownership, the order of
+// kernel launches for index building (Algorithm 1) and query processing
+// (Section 3.3), host<->device staging, introspection and instrumentation.
+#include "nrlsh_internal.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+struct nrlsh_index {
+    int64_t n = 0;
+    int32_t d = 0, m = 0, L = 0, Lp = 0, dp = 0, code_bytes = 0, ncls = 0;
+    nrlsh_dtype dtype = NRLSH_F32;
+    float eps = 0.1f;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int64_t device_bytes = 0;
+    std::vector<void*> owned;
+    // device arrays (storage order = sub-dataset major, id ascending inside)
+    void* Xp = nullptr;            // n x dp items, stored dtype, zero padded
+    uint32_t* perm = nullptr;      // position -> original id
+    uint32_t* sub_of_id = nullptr; // id -> sub-dataset
+    double* s_id = nullptr;        // id -> ||x||^2
+    double* s_pos = nullptr;       // position -> ||x||^2
+    double* tau64 = nullptr;       // position -> sqrt(U_j^2 - ||x||^2)
+    float* tau32 = nullptr;
+    float* xnorm = nullptr;        // position -> fp32 upper bound of ||x||
+    double* U2 = nullptr;          // m
+    float* A = nullptr;            // (d+1) x L
+    float* A_pad = nullptr;        // (d+1) x Lp
+    float* anorm = nullptr;        // Lp
+    void* codes = nullptr;         // n code words, position order
+    uint32_t* order = nullptr;     // ncls bucket ids j*(L+1)+l in probing order
+    double* shat_sorted = nullptr; // ncls
+    nrlsh::PosTile* tiles = nullptr;
+    int32_t ntiles = 0;
+    unsigned long long* ambiguous = nullptr;
+};
+
+namespace nrlsh {
+
+// ------------------------------------------------------------ error state
+
+namespace state {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+struct ProfRecord {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+std::vector<ProfRecord> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+thread_local cudaEvent_t t_pending = nullptr;
+
+cudaEvent_t take_event() {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace state
+
+using namespace state;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+nrlsh_status cuda_status(cudaError_t e, const char* what) {
+    set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return NRLSH_ERR_OOM;
+    return NRLSH_ERR_CUDA;
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(const char*, cudaStream_t s) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    t_pending = take_event();
+    cudaEventRecord(t_pending, s);
+}
+
+void prof_end(const char* name, cudaStream_t s) {
+    if (!t_pending) return;
+    cudaEvent_t b = take_event();
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.push_back({name, t_pending, b});
+    t_pending = nullptr;
+}
+
+}  // namespace nrlsh
+
+using namespace nrlsh;
+
+namespace {
+
+nrlsh_status arg_error(const std::string& msg) {
+    set_error(msg);
+    return NRLSH_ERR_ARG;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The stream-ordered pool keeps freed blocks for reuse instead of returning
+// them to the driver at every synchronisation.
+void keep_pool_memory(int device) {
+    static std::once_flag once;
+    std::call_once(once, [device] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    });
+}
+
+// Scratch allocations of one call, released on its stream at scope exit.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    nrlsh_status get(T** out, size_t count) {
+        void* p = nullptr;
+        const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync");
+        ptrs.push_back(p);
+        *out = (T*)p;
+        return NRLSH_OK;
+    }
+};
+
+template <typename T>
+nrlsh_status own(nrlsh_index* ix, T** out, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (index)");
+    ix->owned.push_back(p);
+    ix->device_bytes += (int64_t)bytes;
+    *out = (T*)p;
+    return NRLSH_OK;
+}
+
+void destroy(nrlsh_index* ix) {
+    if (!ix) return;
+    cudaStreamSynchronize(ix->stream);
+    for (void* p : ix->owned) cudaFree(p);
+    delete ix;
+}
+
+int bits_for(int64_t v) {  // smallest b with 2^b >= v
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+// Copy `bytes` from a host or device pointer into fresh device scratch when the
+// pointer is not device memory; otherwise return it unchanged.
+nrlsh_status stage_in(Scratch& sc, const void* src, size_t bytes, const void** dev) {
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return NRLSH_OK;
+    }
+    char* d = nullptr;
+    NRLSH_CKS(sc.get(&d, bytes));
+    NRLSH_CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, sc.s));
+    *dev = d;
+    return NRLSH_OK;
+}
+
+nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int32_t L,
+                        uint64_t seed, nrlsh_dtype dtype, float eps, void* stream,
+                        nrlsh_index** out) {
+    if (!out) return arg_error("out is NULL");
+    *out = nullptr;
+    if (!items) return arg_error("items is NULL");
+    if (n < 1 || n > (int64_t)INT32_MAX) return arg_error("need 1 <= n <= 2^31 - 1");
+    if (d < 1) return arg_error("need d >= 1");
+    if (m < 1 || m > n) return arg_error("need 1 <= m <= n");
+    if (L < 1 || L > NRLSH_MAX_L) return arg_error("need 1 <= L <= 64");
+    if ((int64_t)m * (L + 1) > NRLSH_MAX_BUCKETS) return arg_error("need m * (L + 1) <= 16384");
+    if (!(eps > 0.0f && eps < 1.0f)) return arg_error("need 0 < eps < 1");
+    if (dtype != NRLSH_F32 && dtype != NRLSH_BF16) return arg_error("unknown dtype");
+    const size_t esz = dtype == NRLSH_BF16 ? 2 : 4;
+    if ((int64_t)d * (int64_t)esz * n / n != (int64_t)d * (int64_t)esz) return arg_error("n*d overflows");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    nrlsh_index* ix = new nrlsh_index();
+    ix->n = n;
+    ix->d = d;
+    ix->m = m;
+    ix->L = L;
+    ix->Lp = L <= 8 ? 8 : L <= 16 ? 16 : L <= 32 ? 32 : 64;
+    ix->dp = (d + 7) / 8 * 8;
+    ix->code_bytes = L <= 32 ? 4 : 8;
+    ix->ncls = m * (L + 1);
+    ix->dtype = dtype;
+    ix->eps = eps;
+    ix->seed = seed;
+    ix->stream = st;
+    cudaGetDevice(&ix->device);
+    keep_pool_memory(ix->device);
+
+    auto fail = [&](nrlsh_status s) {
+        destroy(ix);
+        return s;
+    };
+#define B_CK(expr)                                            \
+    do {                                                      \
+        nrlsh_status s_ = (expr);                             \
+        if (s_ != NRLSH_OK) return fail(s_);                  \
+    } while (0)
+#define B_CU(expr)                                            \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return fail(cuda_status(e_, #expr)); \
+    } while (0)
+
+    // sticky errors from earlier work surface here rather than mid-build
+    B_CU(cudaGetLastError());
+    B_CK(own(ix, (char**)&ix->Xp, (size_t)n * ix->dp * esz));
+    B_CK(own(ix, &ix->perm, n));
+    B_CK(own(ix, &ix->sub_of_id, n));
+    B_CK(own(ix, &ix->s_id, n));
+    B_CK(own(ix, &ix->s_pos, n));
+    B_CK(own(ix, &ix->tau64, n));
+    B_CK(own(ix, &ix->tau32, n));
+    B_CK(own(ix, &ix->xnorm, n));
+    B_CK(own(ix, &ix->U2, m));
+    B_CK(own(ix, &ix->A, (size_t)(d + 1) * L));
+    B_CK(own(ix, &ix->A_pad, (size_t)(d + 1) * ix->Lp));
+    B_CK(own(ix, &ix->anorm, ix->Lp));
+    B_CK(own(ix, (char**)&ix->codes, (size_t)n * ix->code_bytes));
+    B_CK(own(ix, &ix->order, ix->ncls));
+    B_CK(own(ix, &ix->shat_sorted, ix->ncls));
+    B_CK(own(ix, &ix->ambiguous, 1));
+
+    // histogram tiles: runs of positions inside one sub-dataset
+    {
+        const int64_t tile = 16384 / ix->code_bytes;
+        std::vector<PosTile> tl;
+        for (int32_t j = 0; j < m; ++j) {
+            const int64_t a = seg_start(j, n, m), b = seg_start(j + 1, n, m);
+            for (int64_t s = a; s < b; s += tile) tl.push_back({s, (int32_t)std::min(tile, b - s), j});
+        }
+        ix->ntiles = (int32_t)tl.size();
+        B_CK(own(ix, &ix->tiles, tl.size()));
+        B_CU(cudaMemcpyAsync(ix->tiles, tl.data(), tl.size() * sizeof(PosTile),
+                             cudaMemcpyHostToDevice, st));
+        B_CU(cudaStreamSynchronize(st));  // tl is a host temporary
+    }
+
+    {
+        Scratch sc(st);
+        const void* X = nullptr;
+        B_CK(stage_in(sc, items, (size_t)n * d * esz, &X));
+        uint64_t *keys, *keys_alt;
+        uint32_t *vals, *vals_alt, *jkeys, *jkeys_alt;
+        double* bucket_keys;
+        char* sort_tmp;
+        B_CK(sc.get(&keys, n));
+        B_CK(sc.get(&keys_alt, n));
+        B_CK(sc.get(&vals, n));
+        B_CK(sc.get(&vals_alt, n));
+        B_CK(sc.get(&jkeys, n));
+        B_CK(sc.get(&jkeys_alt, n));
+        B_CK(sc.get(&bucket_keys, ix->ncls));
+        B_CK(sc.get(&sort_tmp, radix_sort_temp_bytes(n)));
+
+        B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned long long), st));
+        B_CU(cudaMemsetAsync(ix->U2, 0, sizeof(double) * m, st));
+        // A and the tiles of its columns (Eq. 4 projections)
+        B_CU(launch_gen_projections(ix->A, d, L, seed, st));
+        B_CU(launch_prepare_projections(ix->A, d, L, ix->Lp, ix->A_pad, ix->anorm, st));
+        // Algorithm 1: rank by norm, percentile partition, U_j
+        B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, st));
+        B_CU(launch_iota_keys(ix->s_id, keys, vals, n, st));
+        bool alt = false;
+        B_CU(radix_sort_u64(keys, vals, keys_alt, vals_alt, n, 64, sort_tmp, &alt, st));
+        B_CU(launch_segment_assign(alt ? keys_alt : keys, alt ? vals_alt : vals, n, m,
+                                   ix->sub_of_id, ix->U2, st));
+        // storage order: stable sort of ids by sub-dataset
+        B_CU(cudaMemcpyAsync(jkeys, ix->sub_of_id, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
+                             st));
+        B_CU(launch_iota(vals, n, st));
+        const int jbits = (bits_for(m) + 7) / 8 * 8;
+        B_CU(radix_sort_u32(jkeys, vals, jkeys_alt, vals_alt, n, jbits, sort_tmp, &alt, st));
+        B_CU(cudaMemcpyAsync(ix->perm, alt ? vals_alt : vals, sizeof(uint32_t) * n,
+                             cudaMemcpyDeviceToDevice, st));
+        // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
+        B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, m, ix->s_id, ix->U2, ix->Xp,
+                                 ix->s_pos, ix->tau64, ix->tau32, ix->xnorm, st));
+        // Eq. 4: sign random projection codes
+        B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
+                                 ix->tau64, ix->tau32, ix->xnorm, ix->codes, ix->code_bytes,
+                                 ix->ambiguous, st));
+        // Eq. 12 and the sorted (U_j, l) structure
+        B_CU(launch_bucket_order(ix->U2, m, L, eps, ix->shat_sorted, ix->order, bucket_keys, st));
+    }
+    if (!is_device_ptr(items)) B_CU(cudaStreamSynchronize(st));
+#undef B_CK
+#undef B_CU
+    *out = ix;
+    return NRLSH_OK;
+}
+
+// ------------------------------------------------------------------ queries
+
+struct QueryOut {
+    int64_t* ids = nullptr;      // nq x k_ld
+    float* scores = nullptr;
+    int32_t k_ld = 0;
+    // candidates mode
+    int32_t* cand = nullptr;     // nq x cand_cap
+    int64_t cand_cap = 0;
+    int64_t* count = nullptr;
+    // histogram mode
+    uint32_t* H = nullptr;
+    // hash mode
+    uint64_t* codes = nullptr;
+};
+
+enum class Stage { Hash, Hist, Cand, TopK };
+
+__global__ void widen_codes_kernel(const uint32_t* in, uint64_t* out, int64_t nq) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nq) out[i] = in[i];
+}
+
+// Runs the query path up to `stage` for queries [0, nq) (device pointers).
+nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int32_t k,
+                         int64_t budget, uint32_t flags, Stage stage, const QueryOut& o,
+                         cudaStream_t st) {
+    const int64_t n = ix->n;
+    const int64_t Bp = std::min(budget, n);
+    const bool whole = (flags & NRLSH_WHOLE_BUCKETS) != 0;
+    // per-query scratch beyond the candidate arrays
+    const int64_t fixed = (int64_t)ix->ncls * 4 + ix->m + 64 + 8 + 4;
+    int64_t cap = Bp;
+    const int64_t per_cand = 4 + 4 + 4 + 4 + 8;
+    const int64_t budget_bytes = (int64_t)1 << 30;
+    int64_t chunk = std::max<int64_t>(1, budget_bytes / (fixed + (stage >= Stage::Cand ? cap * per_cand : 0)));
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(nq, 1));
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t qc = std::min(chunk, nq - q0);
+        const float* Qc = Q + q0 * ix->d;
+        Scratch sc(st);
+        float* qnorm;
+        char* qcodes;
+        unsigned long long* qamb;
+        NRLSH_CKS(sc.get(&qnorm, qc));
+        NRLSH_CKS(sc.get(&qamb, 1));
+        NRLSH_CKS(sc.get(&qcodes, qc * ix->code_bytes));
+        NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
+        // P(q) = [q; 0] (Eq. 8), hashed by Eq. 4
+        NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
+                                     ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
+                                     qamb, st));
+        if (stage == Stage::Hash) {
+            if (ix->code_bytes == 8) {
+                NRLSH_CK(cudaMemcpyAsync(o.codes + q0, qcodes, 8 * qc, cudaMemcpyDeviceToDevice, st));
+            } else {
+                count_launch();
+                widen_codes_kernel<<<(unsigned)ceil_div(qc, 256), 256, 0, st>>>(
+                    (const uint32_t*)qcodes, o.codes + q0, qc);
+                NRLSH_CK(cudaGetLastError());
+            }
+            continue;
+        }
+        uint32_t* H;
+        if (stage == Stage::Hist) {
+            H = o.H + q0 * ix->ncls;
+        } else {
+            NRLSH_CKS(sc.get(&H, qc * ix->ncls));
+        }
+        NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
+        NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
+                             ix->ntiles, H, st));
+        if (stage == Stage::Hist) continue;
+        uint8_t* lam;
+        Boundary* bnd;
+        NRLSH_CKS(sc.get(&lam, qc * ix->m));
+        NRLSH_CKS(sc.get(&bnd, qc));
+        NRLSH_CK(launch_threshold(H, ix->order, ix->m, ix->L, qc, n, budget, nullptr, flags, lam,
+                                  bnd, st));
+        int64_t ccap = cap;
+        if (whole) {  // the boundary bucket may overshoot B: size the lists first
+            std::vector<Boundary> hb(qc);
+            NRLSH_CK(cudaMemcpyAsync(hb.data(), bnd, sizeof(Boundary) * qc, cudaMemcpyDeviceToHost, st));
+            NRLSH_CK(cudaStreamSynchronize(st));
+            ccap = 1;
+            for (auto& b : hb) ccap = std::max<int64_t>(ccap, (int64_t)b.full + b.r);
+        }
+        uint32_t* cand;
+        NRLSH_CKS(sc.get(&cand, qc * ccap));
+        NRLSH_CK(launch_select(ix->codes, qcodes, ix->code_bytes, n, ix->m, ix->L, qc, lam, bnd,
+                               cand, ccap, st));
+        if (stage == Stage::Cand) {
+            NRLSH_CK(launch_cand_to_ids(cand, ccap, bnd, ix->perm, qc, o.cand + q0 * o.cand_cap,
+                                        o.cand_cap, o.count + q0, st));
+            continue;
+        }
+        float *lo, *hi;
+        uint32_t* cont;
+        double* cont_s;
+        NRLSH_CKS(sc.get(&lo, qc * ccap));
+        NRLSH_CKS(sc.get(&hi, qc * ccap));
+        NRLSH_CKS(sc.get(&cont, qc * ccap));
+        NRLSH_CKS(sc.get(&cont_s, qc * ccap));
+        NRLSH_CK(launch_rerank_fp32(ix->Xp, ix->dtype, ix->dp, ix->d, Qc, qc, cand, ccap, bnd,
+                                    ix->xnorm, qnorm, lo, hi, st));
+        NRLSH_CK(launch_topk(lo, hi, cand, ccap, bnd, qc, k, nullptr, ix->Xp, ix->dtype, ix->dp,
+                             ix->d, Qc, ix->perm, cont, cont_s, o.ids + q0 * o.k_ld,
+                             o.scores + q0 * o.k_ld, o.k_ld, st));
+    }
+    return NRLSH_OK;
+}
+
+nrlsh_status check_query_args(const nrlsh_index* ix, const float* Q, int64_t nq) {
+    if (!ix) return arg_error("index is NULL");
+    if (nq < 0) return arg_error("need nq >= 0");
+    if (nq > 0 && !Q) return arg_error("queries is NULL");
+    return NRLSH_OK;
+}
+
+// Stage host output buffers: returns a device pointer to write into and
+// remembers the host destination for the copy back.
+struct OutStage {
+    void* host = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+};
+
+template <typename T>
+nrlsh_status stage_out(Scratch& sc, T* p, size_t count, OutStage& os, T** dev) {
+    if (is_device_ptr(p)) {
+        *dev = p;
+        return NRLSH_OK;
+    }
+    T* d = nullptr;
+    NRLSH_CKS(sc.get(&d, count));
+    os.host = p;
+    os.dev = d;
+    os.bytes = count * sizeof(T);
+    *dev = d;
+    return NRLSH_OK;
+}
+
+nrlsh_status finish_out(cudaStream_t st, std::initializer_list<OutStage*> outs, bool any_host) {
+    for (OutStage* o : outs)
+        if (o->host) NRLSH_CK(cudaMemcpyAsync(o->host, o->dev, o->bytes, cudaMemcpyDeviceToHost, st));
+    if (any_host) NRLSH_CK(cudaStreamSynchronize(st));
+    return NRLSH_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+NRLSH_API nrlsh_status nrlsh_build(const float* items, int64_t n, int32_t d, int32_t m, int32_t L,
+                                   uint64_t seed, nrlsh_index** out) {
+    return build_impl(items, n, d, m, L, seed, NRLSH_F32, 0.1f, nullptr, out);
+}
+
+NRLSH_API nrlsh_status nrlsh_build_ex(const void* items, int64_t n, int32_t d, int32_t m,
+                                      int32_t L, uint64_t seed, nrlsh_dtype dtype, float eps,
+                                      void* stream, nrlsh_index** out) {
+    return build_impl(items, n, d, m, L, seed, dtype, eps, stream, out);
+}
+
+NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* queries, int64_t nq,
+                                      int32_t k, int64_t probe_budget, uint32_t flags,
+                                      int64_t* ids, float* scores, void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (k < 1 || k > NRLSH_MAX_K) return arg_error("need 1 <= k <= 1024");
+    if (probe_budget < 1) return arg_error("need probe_budget >= 1");
+    if (flags & ~NRLSH_WHOLE_BUCKETS) return arg_error("unknown flags");
+    if (nq > 0 && (!ids || !scores)) return arg_error("ids/scores is NULL");
+    if (nq == 0) return NRLSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    Scratch sc(st);
+    const void* Qd;
+    NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    OutStage oi, os;
+    QueryOut o;
+    NRLSH_CKS(stage_out(sc, ids, (size_t)nq * k, oi, &o.ids));
+    NRLSH_CKS(stage_out(sc, scores, (size_t)nq * k, os, &o.scores));
+    o.k_ld = k;
+    NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, k, probe_budget, flags, Stage::TopK, o, st));
+    return finish_out(st, {&oi, &os}, oi.host || os.host || Qd != queries);
+}
+
+NRLSH_API nrlsh_status nrlsh_query(const nrlsh_index* ix, const float* queries, int64_t nq,
+                                   int32_t k, int64_t probe_budget, int64_t* ids, float* scores) {
+    return nrlsh_query_ex(ix, queries, nq, k, probe_budget, 0u, ids, scores, nullptr);
+}
+
+NRLSH_API nrlsh_status nrlsh_hash_queries(const nrlsh_index* ix, const float* queries, int64_t nq,
+                                          uint64_t* codes, void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (nq > 0 && !codes) return arg_error("codes is NULL");
+    if (nq == 0) return NRLSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    Scratch sc(st);
+    const void* Qd;
+    NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    OutStage oc;
+    QueryOut o;
+    NRLSH_CKS(stage_out(sc, codes, (size_t)nq, oc, &o.codes));
+    NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, 1, 0u, Stage::Hash, o, st));
+    return finish_out(st, {&oc}, oc.host || Qd != queries);
+}
+
+NRLSH_API nrlsh_status nrlsh_query_histograms(const nrlsh_index* ix, const float* queries,
+                                              int64_t nq, uint32_t* H, void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (nq > 0 && !H) return arg_error("H is NULL");
+    if (nq == 0) return NRLSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    Scratch sc(st);
+    const void* Qd;
+    NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    OutStage oh;
+    QueryOut o;
+    NRLSH_CKS(stage_out(sc, H, (size_t)nq * ix->ncls, oh, &o.H));
+    NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, 1, 0u, Stage::Hist, o, st));
+    return finish_out(st, {&oh}, oh.host || Qd != queries);
+}
+
+NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* ix, const float* queries,
+                                              int64_t nq, int64_t probe_budget, uint32_t flags,
+                                              int64_t cap, int32_t* cand, int64_t* count,
+                                              void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (probe_budget < 1) return arg_error("need probe_budget >= 1");
+    if (cap < 1) return arg_error("need cap >= 1");
+    if (flags & ~NRLSH_WHOLE_BUCKETS) return arg_error("unknown flags");
+    if (nq > 0 && (!cand || !count)) return arg_error("cand/count is NULL");
+    if (nq == 0) return NRLSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    Scratch sc(st);
+    const void* Qd;
+    NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    OutStage oc, on;
+    QueryOut o;
+    NRLSH_CKS(stage_out(sc, cand, (size_t)(nq * cap), oc, &o.cand));
+    NRLSH_CKS(stage_out(sc, count, (size_t)nq, on, &o.count));
+    o.cand_cap = cap;
+    NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, probe_budget, flags, Stage::Cand, o, st));
+    NRLSH_CKS(finish_out(st, {&oc, &on}, true));
+    // counts are needed on the host to report an overflow of `cap`
+    std::vector<int64_t> hc(nq);
+    const int64_t* cnt = on.host ? (const int64_t*)on.host : nullptr;
+    if (!cnt) {
+        NRLSH_CK(cudaMemcpy(hc.data(), count, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost));
+        cnt = hc.data();
+    }
+    for (int64_t i = 0; i < nq; ++i)
+        if (cnt[i] > cap) return arg_error("a query has more candidates than cap");
+    return NRLSH_OK;
+}
+
+NRLSH_API nrlsh_status nrlsh_get_codes(const nrlsh_index* ix, uint64_t* codes) {
+    if (!ix || !codes) return arg_error("NULL argument");
+    NRLSH_CK(cudaStreamSynchronize(ix->stream));
+    const int64_t n = ix->n;
+    std::vector<uint32_t> perm(n);
+    std::vector<unsigned char> raw((size_t)n * ix->code_bytes);
+    NRLSH_CK(cudaMemcpy(perm.data(), ix->perm, 4 * n, cudaMemcpyDeviceToHost));
+    NRLSH_CK(cudaMemcpy(raw.data(), ix->codes, raw.size(), cudaMemcpyDeviceToHost));
+    for (int64_t p = 0; p < n; ++p) {
+        uint64_t c = 0;
+        if (ix->code_bytes == 4) {
+            uint32_t v;
+            std::memcpy(&v, raw.data() + 4 * p, 4);
+            c = v;
+        } else {
+            std::memcpy(&c, raw.data() + 8 * p, 8);
+        }
+        codes[perm[p]] = c;
+    }
+    return NRLSH_OK;
+}
+
+NRLSH_API nrlsh_status nrlsh_get_partition(const nrlsh_index* ix, int32_t* sub_of_id, double* U2,
+                                           double* sqnorm) {
+    if (!ix) return arg_error("index is NULL");
+    NRLSH_CK(cudaStreamSynchronize(ix->stream));
+    if (sub_of_id)
+        NRLSH_CK(cudaMemcpy(sub_of_id, ix->sub_of_id, 4 * ix->n, cudaMemcpyDeviceToHost));
+    if (U2) NRLSH_CK(cudaMemcpy(U2, ix->U2, 8 * ix->m, cudaMemcpyDeviceToHost));
+    if (sqnorm) NRLSH_CK(cudaMemcpy(sqnorm, ix->s_id, 8 * ix->n, cudaMemcpyDeviceToHost));
+    return NRLSH_OK;
+}
+
+NRLSH_API nrlsh_status nrlsh_get_projections(const nrlsh_index* ix, float* A) {
+    if (!ix || !A) return arg_error("NULL argument");
+    NRLSH_CK(cudaStreamSynchronize(ix->stream));
+    NRLSH_CK(cudaMemcpy(A, ix->A, sizeof(float) * (ix->d + 1) * ix->L, cudaMemcpyDeviceToHost));
+    return NRLSH_OK;
+}
+
+NRLSH_API nrlsh_status nrlsh_get_buckets(const nrlsh_index* ix, int32_t* bucket_j,
+                                         int32_t* bucket_l, double* s_hat) {
+    if (!ix) return arg_error("index is NULL");
+    NRLSH_CK(cudaStreamSynchronize(ix->stream));
+    std::vector<uint32_t> ord(ix->ncls);
+    NRLSH_CK(cudaMemcpy(ord.data(), ix->order, 4 * ix->ncls, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < ix->ncls; ++i) {
+        if (bucket_j) bucket_j[i] = (int32_t)(ord[i] / (ix->L + 1));
+        if (bucket_l) bucket_l[i] = (int32_t)(ord[i] % (ix->L + 1));
+    }
+    if (s_hat)
+        NRLSH_CK(cudaMemcpy(s_hat, ix->shat_sorted, 8 * ix->ncls, cudaMemcpyDeviceToHost));
+    return NRLSH_OK;
+}
+
+NRLSH_API nrlsh_status nrlsh_get_info(const nrlsh_index* ix, nrlsh_info* info) {
+    if (!ix || !info) return arg_error("NULL argument");
+    NRLSH_CK(cudaStreamSynchronize(ix->stream));
+    unsigned long long amb = 0;
+    NRLSH_CK(cudaMemcpy(&amb, ix->ambiguous, sizeof(amb), cudaMemcpyDeviceToHost));
+    info->n = ix->n;
+    info->d = ix->d;
+    info->m = ix->m;
+    info->L = ix->L;
+    info->dtype = ix->dtype;
+    info->eps = ix->eps;
+    info->seed = ix->seed;
+    info->code_bytes = ix->code_bytes;
+    info->row_stride = ix->dp;
+    info->device_bytes = ix->device_bytes;
+    info->ambiguous_bits = (int64_t)amb;
+    return NRLSH_OK;
+}
+
+NRLSH_API void nrlsh_free(nrlsh_index* ix) { destroy(ix); }
+
+NRLSH_API const char* nrlsh_last_error(void) { return g_last_error.c_str(); }
+
+NRLSH_API uint64_t nrlsh_launch_count(void) { return g_launches.load(); }
+
+NRLSH_API nrlsh_status nrlsh_set_profiling(int32_t enable) {
+    g_prof_on.store(enable != 0);
+    return NRLSH_OK;
+}
+
+NRLSH_API nrlsh_status nrlsh_profile_read(char* names, int64_t names_cap, double* ms,
+                                          int64_t* launches, int32_t cap, int32_t* count) {
+    std::vector<ProfRecord> recs;
+    {
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        recs.swap(g_prof);
+    }
+    std::map<std::string, std::pair<double, int64_t>> agg;
+    std::vector<std::string> order;
+    for (auto& r : recs) {
+        NRLSH_CK(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        NRLSH_CK(cudaEventElapsedTime(&t, r.a, r.b));
+        auto it = agg.find(r.name);
+        if (it == agg.end()) {
+            order.push_back(r.name);
+            agg[r.name] = {t, 1};
+        } else {
+            it->second.first += t;
+            it->second.second += 1;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        for (auto& r : recs) {
+            g_event_pool.push_back(r.a);
+            g_event_pool.push_back(r.b);
+        }
+    }
+    std::string all;
+    int32_t i = 0;
+    for (auto& nm : order) {
+        if (i < cap) {
+            if (ms) ms[i] = agg[nm].first;
+            if (launches) launches[i] = agg[nm].second;
+        }
+        all += nm;
+        all += '\n';
+        ++i;
+    }
+    if (count) *count = (int32_t)order.size();
+    if (names && names_cap > 0) {
+        const size_t nb = std::min<size_t>(all.size(), (size_t)names_cap - 1);
+        std::memcpy(names, all.data(), nb);
+        names[nb] = 0;
+    }
+    return NRLSH_OK;
+}
+
+}  // extern "C"

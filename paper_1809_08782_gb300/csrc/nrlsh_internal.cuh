@@ -1,0 +1,152 @@
+// Internal declarations shared by the translation units of libnrlsh.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+
+#include "../../include/nrlsh.h"
+
+namespace nrlsh {
+
+// ------------------------------------------------------------------ status
+
+// Sets the thread-local message returned by nrlsh_last_error().
+void set_error(const std::string& msg);
+nrlsh_status cuda_status(cudaError_t e, const char* what);
+
+#define NRLSH_CK(expr)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (expr);                                              \
+        if (e_ != cudaSuccess) return ::nrlsh::cuda_status(e_, #expr);        \
+    } while (0)
+
+#define NRLSH_CKS(expr)                                                       \
+    do {                                                                      \
+        nrlsh_status s_ = (expr);                                             \
+        if (s_ != NRLSH_OK) return s_;                                        \
+    } while (0)
+
+// ------------------------------------------------------- launch accounting
+
+// Every kernel goes through launch(): it counts the launch and, when
+// profiling is on, brackets it with CUDA events on its stream.
+void prof_begin(const char* name, cudaStream_t s);
+void prof_end(const char* name, cudaStream_t s);
+void count_launch();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                          size_t smem, cudaStream_t s, Args&&... args) {
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+    count_launch();
+    prof_begin(name, s);
+    kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+    cudaError_t e = cudaGetLastError();
+    prof_end(name, s);
+    return e;
+}
+
+// ------------------------------------------------------------ small helpers
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Sub-dataset j holds ranks (and storage positions) [seg_start(j), seg_start(j+1)),
+// seg_start(j) = floor(j n / m)  (Algorithm 1, percentile ranges).
+__host__ __device__ inline int64_t seg_start(int64_t j, int64_t n, int64_t m) {
+    return (j * n) / m;
+}
+// The j with seg_start(j) <= r < seg_start(j+1): the largest j with j n < (r+1) m.
+__host__ __device__ inline int32_t seg_of(int64_t r, int64_t n, int64_t m) {
+    return (int32_t)(((r + 1) * m + n - 1) / n - 1);
+}
+
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+// Code words: L <= 32 bits in uint32, otherwise uint64.
+__device__ __forceinline__ int popc_word(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ int popc_word(uint64_t v) { return __popcll(v); }
+
+// Histogram tile: a run of storage positions inside one sub-dataset.
+struct PosTile {
+    int64_t start;
+    int32_t len;
+    int32_t seg;
+};
+
+// ----------------------------------------------------------- build launchers
+// All return cudaError_t of the last launch; pointers are device pointers.
+
+cudaError_t launch_gen_projections(float* A, int d, int L, uint64_t seed, cudaStream_t s);
+cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64_t ld, double* s,
+                          cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of the key.
+// Buffers alternate; returns through *result_in_alt whether the result is in the alt pair.
+size_t radix_sort_temp_bytes(int64_t n);
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                           int64_t n, int key_bits, void* temp, bool* result_in_alt,
+                           cudaStream_t s);
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                           int64_t n, int key_bits, void* temp, bool* result_in_alt,
+                           cudaStream_t s);
+cudaError_t launch_iota_keys(const double* s, uint64_t* keys, uint32_t* vals, int64_t n,
+                             cudaStream_t st);
+cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* sorted_ids,
+                                  int64_t n, int m, uint32_t* sub_of_id, double* U2,
+                                  cudaStream_t st);
+cudaError_t launch_iota(uint32_t* v, int64_t n, cudaStream_t st);
+cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
+                                const uint32_t* perm, int64_t n, int m, const double* s_id,
+                                const double* U2, void* Xp, double* s_pos, double* tau64,
+                                float* tau32, float* xnorm, cudaStream_t st);
+cudaError_t launch_prepare_projections(const float* A, int d, int L, int Lp, float* A_pad,
+                                       float* anorm, cudaStream_t st);
+// Sign random projection of rows of X (n x dp, stored dtype) with the FP32 fast
+// tier and the FP64 recompute; items (tau != null) or queries (tau == null).
+cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int dp,
+                                int L, int Lp, const float* A_pad, const float* anorm,
+                                const double* tau64, const float* tau32, const float* xnorm,
+                                void* codes, int code_bytes, unsigned long long* ambiguous,
+                                cudaStream_t st);
+cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, double* shat_sorted,
+                                uint32_t* order, double* scratch_keys, cudaStream_t st);
+
+// ----------------------------------------------------------- query launchers
+
+cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnorm,
+                                  cudaStream_t st);
+cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, int64_t nq, int m,
+                        int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st);
+struct Boundary {
+    int32_t j;       // boundary bucket (j*, l*)
+    int32_t l;
+    int32_t r;       // items taken from the boundary bucket
+    int32_t full;    // items in buckets probed whole
+};
+cudaError_t launch_threshold(const uint32_t* H, const uint32_t* order, int m, int L, int64_t nq,
+                             int64_t n, int64_t budget, const int64_t* budgets, uint32_t flags,
+                             uint8_t* lam, Boundary* bnd, cudaStream_t st);
+cudaError_t launch_select(const void* codes, const void* qcodes, int code_bytes, int64_t n, int m,
+                          int L, int64_t nq, const uint8_t* lam, const Boundary* bnd,
+                          uint32_t* cand, int64_t cap, cudaStream_t st);
+cudaError_t launch_rerank_fp32(const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
+                               int64_t nq, const uint32_t* cand, int64_t cap, const Boundary* bnd,
+                               const float* xnorm, const float* qnorm, float* lo, float* hi,
+                               cudaStream_t st);
+cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, int64_t cap,
+                        const Boundary* bnd, int64_t nq, int k, const int32_t* ks,
+                        const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
+                        const uint32_t* perm, uint32_t* cont, double* cont_s,
+                        int64_t* out_ids, float* out_scores, int out_ld, cudaStream_t st);
+cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
+                               const uint32_t* perm, int64_t nq, int32_t* out, int64_t out_cap,
+                               int64_t* count, cudaStream_t st);
+
+}  // namespace nrlsh

@@ -1,0 +1,293 @@
+"""Python binding of libnrlsh.so (ctypes).  Argument marshalling only: every
+step of index building and query processing runs in the library's CUDA
+kernels.  Functions carry the names of the C entry points in include/nrlsh.h.
+
+Tensors may live on the GPU (the usual case: calls are then asynchronous on
+PyTorch's current stream) or on the CPU (the library stages them through device
+memory and synchronises).  There is no CPU fallback: if the library has not been
+built, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnrlsh.so")
+
+NRLSH_F32 = 0
+NRLSH_BF16 = 1
+NRLSH_WHOLE_BUCKETS = 0x1
+
+_STATUS = {0: "NRLSH_OK", -1: "NRLSH_ERR_ARG", -2: "NRLSH_ERR_OOM", -3: "NRLSH_ERR_CUDA",
+           -4: "NRLSH_ERR_TIMEOUT", -5: "NRLSH_ERR_UNSUPPORTED"}
+
+# Names and ctypes signatures of every entry point declared in include/nrlsh.h.
+_P = ctypes.c_void_p
+_I32, _I64, _U32, _U64, _F32 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                ctypes.c_uint64, ctypes.c_float)
+SIGNATURES = {
+    "nrlsh_build": (_I32, [_P, _I64, _I32, _I32, _I32, _U64, _P]),
+    "nrlsh_build_ex": (_I32, [_P, _I64, _I32, _I32, _I32, _U64, _I32, _F32, _P, _P]),
+    "nrlsh_query": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P]),
+    "nrlsh_query_ex": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _P, _P, _P]),
+    "nrlsh_hash_queries": (_I32, [_P, _P, _I64, _P, _P]),
+    "nrlsh_query_histograms": (_I32, [_P, _P, _I64, _P, _P]),
+    "nrlsh_query_candidates": (_I32, [_P, _P, _I64, _I64, _U32, _I64, _P, _P, _P]),
+    "nrlsh_get_codes": (_I32, [_P, _P]),
+    "nrlsh_get_partition": (_I32, [_P, _P, _P, _P]),
+    "nrlsh_get_projections": (_I32, [_P, _P]),
+    "nrlsh_get_buckets": (_I32, [_P, _P, _P, _P]),
+    "nrlsh_get_info": (_I32, [_P, _P]),
+    "nrlsh_free": (None, [_P]),
+    "nrlsh_last_error": (ctypes.c_char_p, []),
+    "nrlsh_launch_count": (_U64, []),
+    "nrlsh_set_profiling": (_I32, [_I32]),
+    "nrlsh_profile_read": (_I32, [_P, _I64, _P, _P, _I32, _P]),
+}
+
+
+class NrlshInfo(ctypes.Structure):
+    _fields_ = [("n", _I64), ("d", _I32), ("m", _I32), ("L", _I32), ("dtype", _I32),
+                ("eps", _F32), ("seed", _U64), ("code_bytes", _I32), ("row_stride", _I32),
+                ("device_bytes", _I64), ("ambiguous_bits", _I64)]
+
+
+class NrlshError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libnrlsh.so (built in-tree by paper_1809_08782_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1809_08782_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise NrlshError(status, load().nrlsh_last_error().decode())
+
+
+def _stream(t: torch.Tensor, stream) -> Optional[int]:
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    if t.is_cuda:
+        return int(torch.cuda.current_stream(t.device).cuda_stream)
+    return None
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Index:
+    """Owner of an nrlsh_index handle; freed with nrlsh_free when collected."""
+
+    def __init__(self, handle: ctypes.c_void_p, n: int, d: int, m: int, L: int, device):
+        self.handle = handle
+        self.n, self.d, self.m, self.L = n, d, m, L
+        self.device = device
+
+    def free(self):
+        if self.handle:
+            load().nrlsh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # conveniences that mirror the C calls
+    def query(self, queries, k, probe_budget, flags=0, stream=None):
+        return nrlsh_query_ex(self, queries, k, probe_budget, flags, stream)
+
+    def info(self):
+        return nrlsh_get_info(self)
+
+
+def _items_dtype(items: torch.Tensor) -> int:
+    if items.dtype == torch.float32:
+        return NRLSH_F32
+    if items.dtype == torch.bfloat16:
+        return NRLSH_BF16
+    raise TypeError("items must be float32 or bfloat16")
+
+
+def nrlsh_build_ex(items: torch.Tensor, m: int, L: int, seed: int, eps: float = 0.1,
+                   stream=None) -> Index:
+    """Index building (Algorithm 1).  items: (n, d) float32 or bfloat16, row-major."""
+    lib = load()
+    if items.dim() != 2:
+        raise ValueError("items must be 2-D (n, d)")
+    items = items.contiguous()
+    n, d = items.shape
+    out = ctypes.c_void_p()
+    _check(lib.nrlsh_build_ex(_ptr(items), n, d, m, L, seed, _items_dtype(items), eps,
+                              _stream(items, stream), ctypes.byref(out)))
+    return Index(out, n, d, m, L, items.device)
+
+
+def nrlsh_build(items: torch.Tensor, m: int, L: int, seed: int) -> Index:
+    """Short form: fp32 items, eps = 0.1, legacy default stream."""
+    lib = load()
+    if items.dtype != torch.float32 or items.dim() != 2:
+        raise TypeError("nrlsh_build takes a 2-D float32 tensor")
+    items = items.contiguous()
+    n, d = items.shape
+    out = ctypes.c_void_p()
+    _check(lib.nrlsh_build(_ptr(items), n, d, m, L, seed, ctypes.byref(out)))
+    return Index(out, n, d, m, L, items.device)
+
+
+def _queries(index: Index, queries: torch.Tensor) -> torch.Tensor:
+    if queries.dtype != torch.float32 or queries.dim() != 2 or queries.shape[1] != index.d:
+        raise ValueError(f"queries must be float32 of shape (nq, {index.d})")
+    return queries.contiguous()
+
+
+def nrlsh_query_ex(index: Index, queries: torch.Tensor, k: int, probe_budget: int,
+                   flags: int = 0, stream=None, ids: Optional[torch.Tensor] = None,
+                   scores: Optional[torch.Tensor] = None):
+    """Multi-probe query + exact re-rank + top-k.  Returns (ids int64, scores fp32),
+    both (nq, k), on the queries' device unless output tensors are given."""
+    lib = load()
+    queries = _queries(index, queries)
+    nq = queries.shape[0]
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+    if scores is None:
+        scores = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    _check(lib.nrlsh_query_ex(index.handle, _ptr(queries), nq, k, probe_budget, flags,
+                              _ptr(ids), _ptr(scores), _stream(queries, stream)))
+    return ids, scores
+
+
+def nrlsh_query(index: Index, queries: torch.Tensor, k: int, probe_budget: int):
+    """Short form on the legacy default stream."""
+    lib = load()
+    queries = _queries(index, queries)
+    nq = queries.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+    scores = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    _check(lib.nrlsh_query(index.handle, _ptr(queries), nq, k, probe_budget, _ptr(ids),
+                           _ptr(scores)))
+    return ids, scores
+
+
+def nrlsh_hash_queries(index: Index, queries: torch.Tensor, stream=None) -> torch.Tensor:
+    lib = load()
+    queries = _queries(index, queries)
+    codes = torch.empty(queries.shape[0], dtype=torch.int64, device=queries.device)
+    _check(lib.nrlsh_hash_queries(index.handle, _ptr(queries), queries.shape[0], _ptr(codes),
+                                  _stream(queries, stream)))
+    return codes
+
+
+def nrlsh_query_histograms(index: Index, queries: torch.Tensor, stream=None) -> torch.Tensor:
+    lib = load()
+    queries = _queries(index, queries)
+    H = torch.empty((queries.shape[0], index.m, index.L + 1), dtype=torch.int32,
+                    device=queries.device)
+    _check(lib.nrlsh_query_histograms(index.handle, _ptr(queries), queries.shape[0], _ptr(H),
+                                      _stream(queries, stream)))
+    return H
+
+
+def nrlsh_query_candidates(index: Index, queries: torch.Tensor, probe_budget: int,
+                           flags: int = 0, cap: Optional[int] = None, stream=None):
+    """Probed item ids (nq, cap) int32 (rows valid up to count) and count (nq,) int64."""
+    lib = load()
+    queries = _queries(index, queries)
+    nq = queries.shape[0]
+    if cap is None:
+        cap = index.n if flags & NRLSH_WHOLE_BUCKETS else min(probe_budget, index.n)
+    cand = torch.full((nq, cap), -1, dtype=torch.int32, device=queries.device)
+    count = torch.empty(nq, dtype=torch.int64, device=queries.device)
+    _check(lib.nrlsh_query_candidates(index.handle, _ptr(queries), nq, probe_budget, flags, cap,
+                                      _ptr(cand), _ptr(count), _stream(queries, stream)))
+    return cand, count
+
+
+def nrlsh_get_codes(index: Index) -> torch.Tensor:
+    out = torch.empty(index.n, dtype=torch.int64)
+    _check(load().nrlsh_get_codes(index.handle, _ptr(out)))
+    return out
+
+
+def nrlsh_get_partition(index: Index):
+    sub = torch.empty(index.n, dtype=torch.int32)
+    U2 = torch.empty(index.m, dtype=torch.float64)
+    s = torch.empty(index.n, dtype=torch.float64)
+    _check(load().nrlsh_get_partition(index.handle, _ptr(sub), _ptr(U2), _ptr(s)))
+    return sub, U2, s
+
+
+def nrlsh_get_projections(index: Index) -> torch.Tensor:
+    A = torch.empty((index.d + 1, index.L), dtype=torch.float32)
+    _check(load().nrlsh_get_projections(index.handle, _ptr(A)))
+    return A
+
+
+def nrlsh_get_buckets(index: Index):
+    c = index.m * (index.L + 1)
+    bj = torch.empty(c, dtype=torch.int32)
+    bl = torch.empty(c, dtype=torch.int32)
+    sh = torch.empty(c, dtype=torch.float64)
+    _check(load().nrlsh_get_buckets(index.handle, _ptr(bj), _ptr(bl), _ptr(sh)))
+    return bj, bl, sh
+
+
+def nrlsh_get_info(index: Index) -> dict:
+    info = NrlshInfo()
+    _check(load().nrlsh_get_info(index.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in NrlshInfo._fields_}
+
+
+def nrlsh_free(index: Index):
+    index.free()
+
+
+def nrlsh_last_error() -> str:
+    return load().nrlsh_last_error().decode()
+
+
+def nrlsh_launch_count() -> int:
+    return int(load().nrlsh_launch_count())
+
+
+def nrlsh_set_profiling(enable: bool):
+    _check(load().nrlsh_set_profiling(1 if enable else 0))
+
+
+def nrlsh_profile_read() -> dict:
+    """{kernel name: (total ms, launches)} since the last read."""
+    lib = load()
+    cap = 256
+    names = ctypes.create_string_buffer(1 << 16)
+    ms = (ctypes.c_double * cap)()
+    la = (ctypes.c_int64 * cap)()
+    cnt = ctypes.c_int32()
+    _check(lib.nrlsh_profile_read(names, len(names), ms, la, cap, ctypes.byref(cnt)))
+    keys = [k for k in names.value.decode().split("\n") if k]
+    return {k: (ms[i], int(la[i])) for i, k in enumerate(keys[:cap])}

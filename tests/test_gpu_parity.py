@@ -1,0 +1,159 @@
+"""GPU (through the C ABI) versus the CPU oracle, element by element.
+
+Codes, partitions, bucket order, query codes, Hamming histograms, candidate
+lists and top-k ids must be identical; returned scores are the FP64 inner
+product rounded to fp32 on both sides, so they must be identical too (a tighter
+bar than the 1e-5 relative tolerance allowed for FP32 scores)."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+from paper_1809_08782_gb300 import workloads as W  # noqa: E402
+from tests.parity import build_pair, check_index, check_queries, f32  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1809_08782_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+
+
+def rand_items(n, d, seed, sigma=1.0, dtype="f32"):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((n, d))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    x32 = (x * rng.lognormal(0, sigma, n)[:, None]).astype(np.float32)
+    return W.bf16_bits_from_f32(x32) if dtype == "bf16" else x32
+
+
+def rand_q(nq, d, seed):
+    return W.gen_queries(nq, d, seed)
+
+
+# ------------------------------------------------------------ presets
+
+def test_small_preset_full():
+    """n=10,000, d=64 fp32, m=8, L=16, 1,000 queries, B=1,000, top-10."""
+    w = W.make_workload("small-n10k-d64")
+    lib, ref = build_pair(w.items, w.dtype, w.m, w.L, w.index_seed, 0.1)
+    check_index(lib, ref)
+    check_queries(lib, ref, w.queries[:300], w.k, w.budget)
+    check_queries(lib, ref, w.queries, w.k, w.budget, check_hist=False)
+
+
+@pytest.mark.parametrize("frac", [0.01, 0.03, 0.20])
+def test_netflix_preset(frac):
+    """n=17,770, d=300 fp32, m=32, L=32; budget swept 1%..20% of n."""
+    w = W.make_workload("netflix-n17770-d300", nq=200)
+    lib, ref = build_pair(w.items, w.dtype, w.m, w.L, w.index_seed, 0.3)
+    check_index(lib, ref)
+    check_queries(lib, ref, w.queries, w.k, int(round(frac * w.n)))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_yahoo_preset(dtype):
+    """n=136,736, d=300, m=32, L=64, stored fp32 and bf16; a 64-query subset."""
+    w = W.make_workload("yahoo-n136736-d300", nq=64, with_data=False)
+    items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, dtype)
+    Q = W.gen_queries(w.nq, w.d, w.query_seed)
+    lib, ref = build_pair(items, dtype, w.m, w.L, w.index_seed, 0.1)
+    check_index(lib, ref)
+    check_queries(lib, ref, Q, 10, w.budget)
+
+
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("n,d,m,L", [
+    (1, 3, 1, 8), (2, 5, 2, 1), (37, 9, 37, 17), (1000, 37, 7, 63), (1031, 64, 13, 64),
+    (4099, 8, 64, 32), (5000, 130, 1, 24),
+])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_ragged_shapes(n, d, m, L, dtype):
+    items = rand_items(n, d, n + d + m + L, dtype=dtype)
+    lib, ref = build_pair(items, dtype, m, L, seed=5, eps=0.2)
+    check_index(lib, ref)
+    Q = rand_q(9, d, 7)
+    for B in sorted({1, max(1, n // 3), n, n + 5}):
+        check_queries(lib, ref, Q, min(10, n + 2), B)
+
+
+def test_duplicates_zero_vectors_and_zero_subdatasets():
+    rng = np.random.default_rng(3)
+    base = rng.standard_normal((20, 16)).astype(np.float32)
+    items = np.concatenate([np.zeros((300, 16), np.float32), np.repeat(base, 40, axis=0)])
+    rng.shuffle(items)
+    lib, ref = build_pair(items, "f32", 16, 32, seed=9, eps=0.1)
+    assert ref.U2[0] == 0.0
+    check_index(lib, ref)
+    Q = rand_q(12, 16, 4)
+    Q[0] = 0.0          # zero query: every bit is 1
+    for B in (1, 50, 333, 1100):
+        check_queries(lib, ref, Q, 25, B)
+
+
+@pytest.mark.parametrize("eps", [1e-9, 0.5, 0.9])
+def test_eps_extremes(eps):
+    items = rand_items(3000, 24, 11)
+    lib, ref = build_pair(items, "f32", 8, 32, seed=2, eps=eps)
+    check_index(lib, ref)
+    check_queries(lib, ref, rand_q(20, 24, 12), 10, 400)
+
+
+def test_whole_bucket_probing():
+    items = rand_items(4000, 32, 21)
+    lib, ref = build_pair(items, "f32", 8, 16, seed=3, eps=0.2)
+    import paper_1809_08782_gb300.nrlsh as N
+    check_queries(lib, ref, rand_q(16, 32, 22), 10, 300, flags=N.NRLSH_WHOLE_BUCKETS)
+
+
+def test_budget_below_k_pads_with_minus_one():
+    items = rand_items(500, 16, 5)
+    lib, ref = build_pair(items, "f32", 4, 16, seed=3, eps=0.1)
+    check_queries(lib, ref, rand_q(5, 16, 6), 20, 7)
+
+
+def test_full_budget_is_exact_mips():
+    from oracle import exact
+    items = rand_items(2000, 20, 8)
+    lib, ref = build_pair(items, "f32", 8, 32, seed=4, eps=0.1)
+    Q = rand_q(10, 20, 9)
+    import paper_1809_08782_gb300.nrlsh as N
+    ids, _ = N.nrlsh_query_ex(lib, torch.from_numpy(Q).cuda(), 10, 2000)
+    truth = exact.brute_topk_fp64(items.astype(np.float64), Q, 10)
+    assert np.array_equal(ids.cpu().numpy(), truth)
+
+
+def test_host_buffers_and_streams():
+    """CPU tensors are staged by the library; a side stream gives the same result."""
+    import paper_1809_08782_gb300.nrlsh as N
+    items = rand_items(3000, 40, 31)
+    Q = rand_q(16, 40, 32)
+    eps = f32(0.2)
+    lib_h = N.nrlsh_build_ex(torch.from_numpy(items), 8, 32, 7, eps=eps)
+    lib_d = N.nrlsh_build_ex(torch.from_numpy(items).cuda(), 8, 32, 7, eps=eps)
+    assert torch.equal(N.nrlsh_get_codes(lib_h), N.nrlsh_get_codes(lib_d))
+    ids_h, sc_h = N.nrlsh_query_ex(lib_h, torch.from_numpy(Q), 10, 500)
+    assert ids_h.device.type == "cpu"
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ids_d, sc_d = N.nrlsh_query_ex(lib_d, torch.from_numpy(Q).cuda(), 10, 500)
+    s.synchronize()
+    assert torch.equal(ids_h, ids_d.cpu()) and torch.equal(sc_h, sc_d.cpu())
+    ids_s, sc_s = N.nrlsh_query(lib_d, torch.from_numpy(Q).cuda(), 10, 500)
+    torch.cuda.synchronize()
+    assert torch.equal(ids_s.cpu(), ids_h)
+
+
+def test_empty_query_batch_and_launch_count():
+    import paper_1809_08782_gb300.nrlsh as N
+    items = rand_items(100, 8, 1)
+    lib, _ = build_pair(items, "f32", 2, 8, 1, 0.1)
+    before = N.nrlsh_launch_count()
+    ids, sc = N.nrlsh_query_ex(lib, torch.zeros((0, 8), device="cuda"), 5, 10)
+    assert ids.shape == (0, 5) and N.nrlsh_launch_count() == before
+    N.nrlsh_query_ex(lib, torch.zeros((2, 8), device="cuda"), 5, 10)
+    assert N.nrlsh_launch_count() > before
