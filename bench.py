@@ -142,7 +142,12 @@ def gpu_arm(args):
 
     chosen = None
     best = (0.0, None, None)
-    for eps in EPS_CHOICES:
+    if args.eps is not None and args.budget is not None:
+        idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=float(np.float32(args.eps)))
+        ids, _ = N.nrlsh_query_ex(idx, Q, w.k, args.budget)
+        chosen = (args.eps, args.budget, recall(ids))
+        idx.free()
+    for eps in (EPS_CHOICES if chosen is None else ()):
         idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=float(np.float32(eps)))
         for B_ in w.budget_sweep:
             ids, _ = N.nrlsh_query_ex(idx, Q, w.k, B_)
@@ -375,6 +380,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eps", type=float, default=None, help="skip calibration: fixed eps")
+    ap.add_argument("--budget", type=int, default=None, help="skip calibration: fixed B")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -63,7 +63,7 @@ PRESETS = {
     "netflix-n17770-d300": dict(n=17_770, d=300, m=32, L=32, nq=1_000, k=10,
                                 budget=3_554, dtype="f32", norm_dist="lognormal",
                                 norm_param=0.8, cfg=2,
-                                sweep_frac=(0.01, 0.02, 0.05, 0.10, 0.15, 0.20)),
+                                sweep_frac=(0.01, 0.015, 0.02, 0.03, 0.04, 0.05, 0.075, 0.10, 0.15, 0.20)),
     # Yahoo!Music-sized: n=136,736, d=300, lognormal(0,1.0), m=32, L=64
     "yahoo-n136736-d300": dict(n=136_736, d=300, m=32, L=64, nq=10_000, k=10,
                                budget=4_096, dtype="f32", norm_dist="lognormal",
