@@ -131,6 +131,30 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* index, const float* que
                                       void* stream);
 
 /*
+ * Query processing without any device allocation.  The paper has no counterpart:
+ * this exists for callers that must not allocate device memory while they query,
+ * for example a serving process whose memory is owned by another allocator, or
+ * code whose latency budget cannot absorb an allocator call.  It computes exactly
+ * what nrlsh_query_ex computes (no flags), using as scratch one fixed array of
+ * NRLSH_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into the library; every GPU on
+ * which the library is used keeps that array until the process exits.
+ *   queries, ids, scores   DEVICE pointers only (host pointers: NRLSH_ERR_ARG)
+ *   the other arguments    as for nrlsh_query_ex
+ * Queries are processed in chunks that fit the array.  A probe budget whose single
+ * query needs more scratch than the array holds (about 1.4M candidates for the
+ * largest bucket tables) is rejected with NRLSH_ERR_ARG before any work is queued.
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and leave their contents in it, so calls whose GPU work
+ * overlaps (on different streams, or from different threads) race and must be
+ * serialised by the caller.  No allocation or free of any kind is made.
+ */
+#define NRLSH_NOALLOC_SCRATCH_BYTES (32u << 20)
+NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* index, const float* queries,
+                                           int64_t nq, int32_t k, int64_t probe_budget,
+                                           int64_t* ids, float* scores, void* stream);
+
+/*
  * Introspection of the query path, for testing against a reference.  Device or
  * host pointers as above.
  * nrlsh_hash_queries: codes (nq uint64; bit b of the code is hash bit b).

@@ -726,3 +726,129 @@ NRLSH_API nrlsh_status nrlsh_profile_read(char* names, int64_t names_cap, double
 }
 
 }  // extern "C"
+
+// ============================================================ no-allocation
+// nrlsh_query_noalloc: the query path of nrlsh_query_ex for callers that must
+// not allocate device memory while they query.  Its scratch is one fixed array
+// in this translation unit; host code must not use the array's name as a device
+// address, so the address is looked up once per device with that device current.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[NRLSH_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoallocMaxDevices] = {};
+
+nrlsh_status noalloc_base(void** out) {
+    int dev = 0;
+    NRLSH_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return arg_error("device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return NRLSH_OK;
+}
+
+constexpr size_t kArenaAlign = 256;
+
+size_t arena_round(size_t b) { return (b + kArenaAlign - 1) / kArenaAlign * kArenaAlign; }
+
+// Bytes of scratch one chunk of qc queries takes (every buffer 256-byte aligned).
+size_t noalloc_chunk_bytes(const nrlsh_index* ix, int64_t qc, int64_t cap) {
+    const size_t q = (size_t)qc, c = (size_t)cap;
+    return arena_round(q * sizeof(float))                      // qnorm
+         + arena_round(sizeof(unsigned long long))             // ambiguity counter
+         + arena_round(q * ix->code_bytes)                     // query codes
+         + arena_round(q * ix->ncls * sizeof(uint32_t))        // histograms
+         + arena_round(q * ix->m)                              // lam
+         + arena_round(q * sizeof(Boundary))                   // boundary buckets
+         + arena_round(q * c * sizeof(uint32_t))               // candidates
+         + 2 * arena_round(q * c * sizeof(float))              // lo, hi
+         + arena_round(q * c * sizeof(uint32_t))               // contenders
+         + arena_round(q * c * sizeof(double));                // contender scores
+}
+
+struct Arena {
+    char* base;
+    size_t off;
+    template <typename T>
+    T* take(size_t count) {
+        T* p = (T*)(base + off);
+        off += arena_round(count * sizeof(T));
+        return p;
+    }
+};
+
+}  // namespace
+
+extern "C" NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* ix, const float* queries,
+                                                      int64_t nq, int32_t k, int64_t probe_budget,
+                                                      int64_t* ids, float* scores, void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (k < 1 || k > NRLSH_MAX_K) return arg_error("need 1 <= k <= 1024");
+    if (probe_budget < 1) return arg_error("need probe_budget >= 1");
+    if (nq > 0 && (!ids || !scores)) return arg_error("ids/scores is NULL");
+    if (nq == 0) return NRLSH_OK;
+    if (!is_device_ptr(queries) || !is_device_ptr(ids) || !is_device_ptr(scores))
+        return arg_error("nrlsh_query_noalloc takes device pointers only");
+    const int64_t cap = std::min<int64_t>(probe_budget, ix->n);
+    if (noalloc_chunk_bytes(ix, 1, cap) > (size_t)NRLSH_NOALLOC_SCRATCH_BYTES)
+        return arg_error("probe budget too large for the 32 MiB no-allocation scratch");
+    void* base = nullptr;
+    NRLSH_CKS(noalloc_base(&base));
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    // the largest chunk of queries whose scratch fits the array
+    int64_t lo = 1, hi = nq;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (noalloc_chunk_bytes(ix, mid, cap) <= (size_t)NRLSH_NOALLOC_SCRATCH_BYTES)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int64_t chunk = lo;
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t qc = std::min(chunk, nq - q0);
+        const float* Qc = queries + q0 * ix->d;
+        Arena a{(char*)base, 0};
+        float* qnorm = a.take<float>(qc);
+        unsigned long long* qamb = a.take<unsigned long long>(1);
+        char* qcodes = a.take<char>((size_t)qc * ix->code_bytes);
+        uint32_t* H = a.take<uint32_t>((size_t)qc * ix->ncls);
+        uint8_t* lam = a.take<uint8_t>((size_t)qc * ix->m);
+        Boundary* bnd = a.take<Boundary>(qc);
+        uint32_t* cand = a.take<uint32_t>((size_t)qc * cap);
+        float* lo_s = a.take<float>((size_t)qc * cap);
+        float* hi_s = a.take<float>((size_t)qc * cap);
+        uint32_t* cont = a.take<uint32_t>((size_t)qc * cap);
+        double* cont_s = a.take<double>((size_t)qc * cap);
+        // everything that must start at zero is cleared: the array keeps the
+        // previous call's contents
+        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned long long), st));
+        NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
+        NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
+        NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
+                                     ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
+                                     qamb, st));
+        NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
+                             ix->ntiles, H, st));
+        NRLSH_CK(launch_threshold(H, ix->order, ix->m, ix->L, qc, ix->n, probe_budget, nullptr,
+                                  0u, lam, bnd, st));
+        NRLSH_CK(launch_select(ix->codes, qcodes, ix->code_bytes, ix->n, ix->m, ix->L, qc, lam,
+                               bnd, cand, cap, st));
+        NRLSH_CK(launch_rerank_fp32(ix->Xp, ix->dtype, ix->dp, ix->d, Qc, qc, cand, cap, bnd,
+                                    ix->xnorm, qnorm, lo_s, hi_s, st));
+        NRLSH_CK(launch_topk(lo_s, hi_s, cand, cap, bnd, qc, k, nullptr, ix->Xp, ix->dtype,
+                             ix->dp, ix->d, Qc, ix->perm, cont, cont_s, ids + q0 * k,
+                             scores + q0 * k, k, st));
+    }
+    return NRLSH_OK;
+}

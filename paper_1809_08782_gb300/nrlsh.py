@@ -34,6 +34,7 @@ SIGNATURES = {
     "nrlsh_build_ex": (_I32, [_P, _I64, _I32, _I32, _I32, _U64, _I32, _F32, _P, _P]),
     "nrlsh_query": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P]),
     "nrlsh_query_ex": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _P, _P, _P]),
+    "nrlsh_query_noalloc": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P]),
     "nrlsh_hash_queries": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_histograms": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_candidates": (_I32, [_P, _P, _I64, _I64, _U32, _I64, _P, _P, _P]),
@@ -192,6 +193,20 @@ def nrlsh_query(index: Index, queries: torch.Tensor, k: int, probe_budget: int):
     scores = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
     _check(lib.nrlsh_query(index.handle, _ptr(queries), nq, k, probe_budget, _ptr(ids),
                            _ptr(scores)))
+    return ids, scores
+
+
+def nrlsh_query_noalloc(index: Index, queries: torch.Tensor, k: int, probe_budget: int,
+                        ids: torch.Tensor, scores: torch.Tensor, stream=None):
+    """The query path without device allocation (for callers that cannot
+    allocate while querying).  queries, ids (nq, k) int64 and scores (nq, k) fp32
+    must be GPU tensors; the library's fixed 32 MiB scratch array is shared by
+    every call, so calls must not overlap on the GPU."""
+    lib = load()
+    queries = _queries(index, queries)
+    _check(lib.nrlsh_query_noalloc(index.handle, _ptr(queries), queries.shape[0], k,
+                                   probe_budget, _ptr(ids), _ptr(scores),
+                                   _stream(queries, stream)))
     return ids, scores
 
 
