@@ -39,7 +39,8 @@ struct nrlsh_index {
     double* shat_sorted = nullptr; // ncls
     nrlsh::PosTile* tiles = nullptr;
     int32_t ntiles = 0;
-    unsigned long long* ambiguous = nullptr;
+    std::vector<nrlsh::PosTile> tiles_host;  // source of the asynchronous upload
+    unsigned* ambiguous = nullptr;  // (item, bit) pairs the FP32 tier left undecided
 };
 
 namespace nrlsh {
@@ -263,7 +264,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     // histogram tiles: runs of positions inside one sub-dataset
     {
         const int64_t tile = 16384 / ix->code_bytes;
-        std::vector<PosTile> tl;
+        std::vector<PosTile>& tl = ix->tiles_host;
         for (int32_t j = 0; j < m; ++j) {
             const int64_t a = seg_start(j, n, m), b = seg_start(j + 1, n, m);
             for (int64_t s = a; s < b; s += tile) tl.push_back({s, (int32_t)std::min(tile, b - s), j});
@@ -272,7 +273,6 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(own(ix, &ix->tiles, tl.size()));
         B_CU(cudaMemcpyAsync(ix->tiles, tl.data(), tl.size() * sizeof(PosTile),
                              cudaMemcpyHostToDevice, st));
-        B_CU(cudaStreamSynchronize(st));  // tl is a host temporary
     }
 
     {
@@ -283,6 +283,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         uint32_t *vals, *vals_alt, *jkeys, *jkeys_alt;
         double* bucket_keys;
         char* sort_tmp;
+        unsigned long long* amb_list;
+        const size_t amb_cap = ambiguity_capacity(n, L);
         B_CK(sc.get(&keys, n));
         B_CK(sc.get(&keys_alt, n));
         B_CK(sc.get(&vals, n));
@@ -291,26 +293,24 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(sc.get(&jkeys_alt, n));
         B_CK(sc.get(&bucket_keys, ix->ncls));
         B_CK(sc.get(&sort_tmp, radix_sort_temp_bytes(n)));
+        B_CK(sc.get(&amb_list, amb_cap));
 
-        B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned long long), st));
+        B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned), st));
         B_CU(cudaMemsetAsync(ix->U2, 0, sizeof(double) * m, st));
         // A and the tiles of its columns (Eq. 4 projections)
-        B_CU(launch_gen_projections(ix->A, d, L, seed, st));
-        B_CU(launch_prepare_projections(ix->A, d, L, ix->Lp, ix->A_pad, ix->anorm, st));
+        B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, d, L, ix->Lp, seed, st));
         // Algorithm 1: rank by norm, percentile partition, U_j
-        B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, st));
-        B_CU(launch_iota_keys(ix->s_id, keys, vals, n, st));
+        B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
         bool alt = false;
         B_CU(radix_sort_u64(keys, vals, keys_alt, vals_alt, n, 64, sort_tmp, &alt, st));
-        B_CU(launch_segment_assign(alt ? keys_alt : keys, alt ? vals_alt : vals, n, m,
-                                   ix->sub_of_id, ix->U2, st));
         // storage order: stable sort of ids by sub-dataset
-        B_CU(cudaMemcpyAsync(jkeys, ix->sub_of_id, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
-                             st));
-        B_CU(launch_iota(vals, n, st));
+        uint32_t* jv = alt ? vals : vals_alt;       // the pair the sort did not end in
+        uint32_t* jv_alt = alt ? vals_alt : vals;
+        B_CU(launch_segment_assign(alt ? keys_alt : keys, alt ? vals_alt : vals, n, m,
+                                   ix->sub_of_id, ix->U2, jkeys, jv, st));
         const int jbits = (bits_for(m) + 7) / 8 * 8;
-        B_CU(radix_sort_u32(jkeys, vals, jkeys_alt, vals_alt, n, jbits, sort_tmp, &alt, st));
-        B_CU(cudaMemcpyAsync(ix->perm, alt ? vals_alt : vals, sizeof(uint32_t) * n,
+        B_CU(radix_sort_u32(jkeys, jv, jkeys_alt, jv_alt, n, jbits, sort_tmp, &alt, st));
+        B_CU(cudaMemcpyAsync(ix->perm, alt ? jv_alt : jv, sizeof(uint32_t) * n,
                              cudaMemcpyDeviceToDevice, st));
         // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
         B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, m, ix->s_id, ix->U2, ix->Xp,
@@ -318,7 +318,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         // Eq. 4: sign random projection codes
         B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
                                  ix->tau64, ix->tau32, ix->xnorm, ix->codes, ix->code_bytes,
-                                 ix->ambiguous, st));
+                                 amb_list, ix->ambiguous, (unsigned)amb_cap, st));
         // Eq. 12 and the sorted (U_j, l) structure
         B_CU(launch_bucket_order(ix->U2, m, L, eps, ix->shat_sorted, ix->order, bucket_keys, st));
     }
@@ -372,15 +372,19 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
         Scratch sc(st);
         float* qnorm;
         char* qcodes;
-        unsigned long long* qamb;
+        unsigned* qamb;
+        unsigned long long* qamb_list;
+        const size_t qamb_cap = ambiguity_capacity(qc, ix->L);
         NRLSH_CKS(sc.get(&qnorm, qc));
         NRLSH_CKS(sc.get(&qamb, 1));
+        NRLSH_CKS(sc.get(&qamb_list, qamb_cap));
+        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CKS(sc.get(&qcodes, qc * ix->code_bytes));
         NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
         // P(q) = [q; 0] (Eq. 8), hashed by Eq. 4
         NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
                                      ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
-                                     qamb, st));
+                                     qamb_list, qamb, (unsigned)qamb_cap, st));
         if (stage == Stage::Hash) {
             if (ix->code_bytes == 8) {
                 NRLSH_CK(cudaMemcpyAsync(o.codes + q0, qcodes, 8 * qc, cudaMemcpyDeviceToDevice, st));
@@ -402,6 +406,23 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
         NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
                              ix->ntiles, H, st));
         if (stage == Stage::Hist) continue;
+        if (stage == Stage::TopK && !whole) {
+            // one fused launch: walk, selection, re-rank, exact top-k
+            uint32_t *cand, *cont;
+            float *lo, *hi;
+            double* cont_s;
+            NRLSH_CKS(sc.get(&cand, qc * cap));
+            NRLSH_CKS(sc.get(&lo, qc * cap));
+            NRLSH_CKS(sc.get(&hi, qc * cap));
+            NRLSH_CKS(sc.get(&cont, qc * cap));
+            NRLSH_CKS(sc.get(&cont_s, qc * cap));
+            NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, n, qc, budget, nullptr, flags,
+                                         ix->codes, qcodes, ix->code_bytes, ix->Xp, ix->dtype,
+                                         ix->dp, ix->d, Qc, ix->xnorm, qnorm, ix->perm, k, nullptr,
+                                         cand, lo, hi, cont, cont_s, cap, o.ids + q0 * o.k_ld,
+                                         o.scores + q0 * o.k_ld, o.k_ld, st));
+            continue;
+        }
         uint8_t* lam;
         Boundary* bnd;
         NRLSH_CKS(sc.get(&lam, qc * ix->m));
@@ -649,7 +670,7 @@ NRLSH_API nrlsh_status nrlsh_get_buckets(const nrlsh_index* ix, int32_t* bucket_
 NRLSH_API nrlsh_status nrlsh_get_info(const nrlsh_index* ix, nrlsh_info* info) {
     if (!ix || !info) return arg_error("NULL argument");
     NRLSH_CK(cudaStreamSynchronize(ix->stream));
-    unsigned long long amb = 0;
+    unsigned amb = 0;
     NRLSH_CK(cudaMemcpy(&amb, ix->ambiguous, sizeof(amb), cudaMemcpyDeviceToHost));
     info->n = ix->n;
     info->d = ix->d;
@@ -764,11 +785,10 @@ size_t arena_round(size_t b) { return (b + kArenaAlign - 1) / kArenaAlign * kAre
 size_t noalloc_chunk_bytes(const nrlsh_index* ix, int64_t qc, int64_t cap) {
     const size_t q = (size_t)qc, c = (size_t)cap;
     return arena_round(q * sizeof(float))                      // qnorm
-         + arena_round(sizeof(unsigned long long))             // ambiguity counter
+         + arena_round(sizeof(unsigned))                       // ambiguity counter
+         + arena_round(ambiguity_capacity(qc, ix->L) * sizeof(unsigned long long))
          + arena_round(q * ix->code_bytes)                     // query codes
          + arena_round(q * ix->ncls * sizeof(uint32_t))        // histograms
-         + arena_round(q * ix->m)                              // lam
-         + arena_round(q * sizeof(Boundary))                   // boundary buckets
          + arena_round(q * c * sizeof(uint32_t))               // candidates
          + 2 * arena_round(q * c * sizeof(float))              // lo, hi
          + arena_round(q * c * sizeof(uint32_t))               // contenders
@@ -820,11 +840,11 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* ix, con
         const float* Qc = queries + q0 * ix->d;
         Arena a{(char*)base, 0};
         float* qnorm = a.take<float>(qc);
-        unsigned long long* qamb = a.take<unsigned long long>(1);
+        unsigned* qamb = a.take<unsigned>(1);
+        const size_t qamb_cap = ambiguity_capacity(qc, ix->L);
+        unsigned long long* qamb_list = a.take<unsigned long long>(qamb_cap);
         char* qcodes = a.take<char>((size_t)qc * ix->code_bytes);
         uint32_t* H = a.take<uint32_t>((size_t)qc * ix->ncls);
-        uint8_t* lam = a.take<uint8_t>((size_t)qc * ix->m);
-        Boundary* bnd = a.take<Boundary>(qc);
         uint32_t* cand = a.take<uint32_t>((size_t)qc * cap);
         float* lo_s = a.take<float>((size_t)qc * cap);
         float* hi_s = a.take<float>((size_t)qc * cap);
@@ -832,23 +852,18 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* ix, con
         double* cont_s = a.take<double>((size_t)qc * cap);
         // everything that must start at zero is cleared: the array keeps the
         // previous call's contents
-        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned long long), st));
+        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
         NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
         NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
                                      ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
-                                     qamb, st));
+                                     qamb_list, qamb, (unsigned)qamb_cap, st));
         NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
                              ix->ntiles, H, st));
-        NRLSH_CK(launch_threshold(H, ix->order, ix->m, ix->L, qc, ix->n, probe_budget, nullptr,
-                                  0u, lam, bnd, st));
-        NRLSH_CK(launch_select(ix->codes, qcodes, ix->code_bytes, ix->n, ix->m, ix->L, qc, lam,
-                               bnd, cand, cap, st));
-        NRLSH_CK(launch_rerank_fp32(ix->Xp, ix->dtype, ix->dp, ix->d, Qc, qc, cand, cap, bnd,
-                                    ix->xnorm, qnorm, lo_s, hi_s, st));
-        NRLSH_CK(launch_topk(lo_s, hi_s, cand, cap, bnd, qc, k, nullptr, ix->Xp, ix->dtype,
-                             ix->dp, ix->d, Qc, ix->perm, cont, cont_s, ids + q0 * k,
-                             scores + q0 * k, k, st));
+        NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, ix->n, qc, probe_budget, nullptr, 0u,
+                                     ix->codes, qcodes, ix->code_bytes, ix->Xp, ix->dtype, ix->dp,
+                                     ix->d, Qc, ix->xnorm, qnorm, ix->perm, k, nullptr, cand, lo_s,
+                                     hi_s, cont, cont_s, cap, ids + q0 * k, scores + q0 * k, k, st));
     }
     return NRLSH_OK;
 }

@@ -9,6 +9,7 @@
 //   bucket_order      the sorted (U_j, l) structure of Section 3.3
 #include "nrlsh_internal.cuh"
 
+#include <algorithm>
 #include <cfloat>
 
 namespace nrlsh {
@@ -49,24 +50,47 @@ __device__ double round_to_bf16(double z) {
     return ldexp(rint(mant * 256.0), ex - 8);
 }
 
-__global__ void gen_projections_kernel(float* A, int d, int L, uint64_t seed) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)(d + 1) * L) return;
-    uint64_t c[4] = {(uint64_t)(i / L), (uint64_t)(i % L), 0, 0};
+__device__ float projection_entry(int64_t r, int64_t b, uint64_t seed) {
+    uint64_t c[4] = {(uint64_t)r, (uint64_t)b, 0, 0};
     philox4x64_10(c, seed, 0);
     const double u1 = ((double)(c[0] >> 12) + 0.5) * 0x1p-52;
     const double u2 = ((double)(c[1] >> 12) + 0.5) * 0x1p-52;
-    const double r = sqrt(-2.0 * log(u1));
-    const double z = __dmul_rn(r, cos(__dmul_rn(6.283185307179586, u2)));
-    A[i] = (float)round_to_bf16(z);
+    const double rad = sqrt(-2.0 * log(u1));
+    const double z = __dmul_rn(rad, cos(__dmul_rn(6.283185307179586, u2)));
+    return (float)round_to_bf16(z);
+}
+
+// Block b fills column b of A ((d+1) x L) and of A_pad ((d+1) x Lp, zero for
+// b >= L) and writes anorm[b], an fp32 upper bound of ||a_{0..d-1, b}||_2.
+__global__ void __launch_bounds__(256)
+    projections_kernel(float* __restrict__ A, float* __restrict__ A_pad, float* __restrict__ anorm,
+                       int d, int L, int Lp, uint64_t seed) {
+    __shared__ double part[8];
+    const int b = blockIdx.x;
+    double ss = 0.0;
+    for (int r = threadIdx.x; r <= d; r += blockDim.x) {
+        const float a = b < L ? projection_entry(r, b, seed) : 0.0f;
+        if (b < L) A[(int64_t)r * L + b] = a;
+        A_pad[(int64_t)r * Lp + b] = a;
+        if (r < d) ss = fma((double)a, (double)a, ss);
+    }
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        // the sum's relative error (< d 2^-53) is far inside the 4x bound margin
+        anorm[b] = __fsqrt_ru(__double2float_ru(t));
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_gen_projections(float* A, int d, int L, uint64_t seed, cudaStream_t s) {
-    const int64_t total = (int64_t)(d + 1) * L;
-    return launch("gen_projections", gen_projections_kernel, dim3((unsigned)ceil_div(total, 256)),
-                  dim3(256), 0, s, A, d, L, seed);
+cudaError_t launch_projections(float* A, float* A_pad, float* anorm, int d, int L, int Lp,
+                               uint64_t seed, cudaStream_t s) {
+    return launch("projections", projections_kernel, dim3((unsigned)Lp), dim3(256), 0, s, A, A_pad,
+                  anorm, d, L, Lp, seed);
 }
 
 // =====================================================================
@@ -76,9 +100,21 @@ cudaError_t launch_gen_projections(float* A, int d, int L, uint64_t seed, cudaSt
 
 namespace {
 
+// The squared norm's IEEE bits order like the value (s >= 0, -0 folded to +0):
+// they are the partition's sort key, with the id as value.
+__device__ __forceinline__ void store_norm(int64_t row, double acc, double* s, uint64_t* keys,
+                                           uint32_t* vals) {
+    s[row] = acc;
+    if (keys) {
+        keys[row] = (uint64_t)__double_as_longlong(acc + 0.0);
+        vals[row] = (uint32_t)row;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) sqnorm_kernel(const T* __restrict__ X, int64_t n, int d,
-                                                     int64_t ld, double* __restrict__ s) {
+                                                     int64_t ld, double* __restrict__ s,
+                                                     uint64_t* keys, uint32_t* vals) {
     __shared__ float tile[128][33];
     const int64_t row0 = (int64_t)blockIdx.x * 128;
     double acc = 0.0;
@@ -98,88 +134,148 @@ __global__ void __launch_bounds__(128) sqnorm_kernel(const T* __restrict__ X, in
         __syncthreads();
     }
     const int64_t row = row0 + threadIdx.x;
-    if (row < n) s[row] = acc;
+    if (row < n) store_norm(row, acc, s, keys, vals);
+}
+
+// Same sums for fp32 rows with d % 4 == 0 (16-byte aligned rows): the tile is
+// loaded with float4 and the next 32-column chunk is prefetched into registers
+// while the current one is summed.
+__global__ void __launch_bounds__(128) sqnorm_f32v4_kernel(const float* __restrict__ X, int64_t n,
+                                                           int d, double* __restrict__ s,
+                                                           uint64_t* keys, uint32_t* vals) {
+    __shared__ float tile[128][33];
+    const int64_t row0 = (int64_t)blockIdx.x * 128;
+    const int d4 = d / 4;
+    float4 pre[8];
+    auto fetch = [&](int c0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = threadIdx.x + 128 * u;  // 1024 float4 per 128 x 32 chunk
+            const int r = i >> 3, c4 = (c0 >> 2) + (i & 7);
+            const int64_t row = row0 + r;
+            pre[u] = (row < n && c4 < d4) ? ((const float4*)(X + row * d))[c4]
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    double acc = 0.0;
+    fetch(0);
+    for (int c0 = 0; c0 < d; c0 += 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = threadIdx.x + 128 * u;
+            const int r = i >> 3, c = (i & 7) * 4;
+            tile[r][c] = pre[u].x;
+            tile[r][c + 1] = pre[u].y;
+            tile[r][c + 2] = pre[u].z;
+            tile[r][c + 3] = pre[u].w;
+        }
+        __syncthreads();
+        if (c0 + 32 < d) fetch(c0 + 32);
+        const int cmax = min(32, d - c0);
+        for (int c = 0; c < cmax; ++c) {
+            const double v = (double)tile[threadIdx.x][c];
+            acc = fma(v, v, acc);
+        }
+        __syncthreads();
+    }
+    const int64_t row = row0 + threadIdx.x;
+    if (row < n) store_norm(row, acc, s, keys, vals);
 }
 
 }  // namespace
 
 cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64_t ld, double* s,
-                          cudaStream_t st) {
+                          uint64_t* keys, uint32_t* vals, cudaStream_t st) {
     const dim3 grid((unsigned)ceil_div(n, 128));
     if (dt == NRLSH_BF16)
         return launch("sqnorm_bf16", sqnorm_kernel<__nv_bfloat16>, grid, dim3(128), 0, st,
-                      (const __nv_bfloat16*)X, n, d, ld, s);
+                      (const __nv_bfloat16*)X, n, d, ld, s, keys, vals);
+    if (ld == d && d % 4 == 0 && ((uintptr_t)X & 15) == 0)
+        return launch("sqnorm_f32", sqnorm_f32v4_kernel, grid, dim3(128), 0, st, (const float*)X, n,
+                      d, s, keys, vals);
     return launch("sqnorm_f32", sqnorm_kernel<float>, grid, dim3(128), 0, st, (const float*)X, n, d,
-                  ld, s);
+                  ld, s, keys, vals);
 }
 
 // =====================================================================
-// Stable LSD radix sort, 8-bit digits.  Per pass: tile histograms, one
-// exclusive scan over (digit, tile), and a stable scatter that ranks keys
-// inside a tile with warp match + per-warp digit counts.  A pass whose digit
-// is the same for every key (known from an OR-of-differences reduction) turns
-// into a plain copy, so the buffers alternate the same way in every case.
+// Stable LSD radix sort, 8-bit digits.  One tile histogram pass up front;
+// then per digit: one exclusive scan over (digit, tile) and one stable scatter
+// that ranks keys inside a tile (warp match + per-warp digit counts) and, on
+// the way, counts the next digit per destination tile for the next pass.  A pass
+// whose digit is the same for every key (known from an OR-of-differences
+// reduction) turns into a copy, so the buffers alternate the same way always.
+// Tiles are 1,024 keys up to 1M keys (more blocks for small inputs) and 4,096
+// beyond (a shorter scan).
 // =====================================================================
 
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;
-constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys per tile
 constexpr int kRadix = 256;
-
-template <typename K>
-__global__ void or_diff_kernel(const K* __restrict__ keys, int64_t n, unsigned long long* out) {
-    const K k0 = keys[0];
-    unsigned long long acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        acc |= (unsigned long long)(keys[i] ^ k0);
-    for (int o = 16; o; o >>= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, acc);
-}
 
 __device__ __forceinline__ bool digit_varies(const unsigned long long* varying, int shift) {
     return ((*varying >> shift) & 0xFFull) != 0;
 }
 
-template <typename K>
+// Tile histograms of digit 0 and, in the same sweep, the OR over all keys of
+// (key xor key[0]): the bits that vary, which tell later passes to skip.
+template <typename K, int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads)
-    radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shift,
-                      const unsigned long long* varying, uint32_t* __restrict__ counts,
-                      int ntiles) {
-    if (!digit_varies(varying, shift)) return;
+    radix_first_hist_kernel(const K* __restrict__ keys, int64_t n, unsigned long long* varying,
+                            uint32_t* __restrict__ counts, int ntiles) {
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
+    const K k0 = keys[0];
+    unsigned long long acc = 0;
+    const int64_t base = (int64_t)blockIdx.x * kSortThreads * ROUNDS;
+    for (int i = threadIdx.x; i < kSortThreads * ROUNDS; i += kSortThreads) {
         const int64_t p = base + i;
-        if (p < n) atomicAdd(&h[(uint32_t)(keys[p] >> shift) & 0xFFu], 1u);
+        if (p < n) {
+            const K key = keys[p];
+            acc |= (unsigned long long)(key ^ k0);
+            atomicAdd(&h[(uint32_t)key & 0xFFu], 1u);
+        }
     }
+    for (int o = 16; o; o >>= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicOr(varying, acc);
     __syncthreads();
     counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan in place over total = 256 * ntiles counters, one block.
+// Exclusive scan in place over total = 256 * ntiles counters, one block of
+// 1024 threads, each owning a contiguous run; warp shuffles, then one warp over
+// the 32 warp totals.  Also clears the next pass's counters when the scatter
+// will accumulate into them.
 __global__ void __launch_bounds__(1024)
-    radix_scan_kernel(uint32_t* counts, int64_t total, int shift,
-                      const unsigned long long* varying) {
+    radix_scan_kernel(uint32_t* counts, int64_t total, int shift, uint32_t* next_counts,
+                      int next_shift, const unsigned long long* varying) {
     if (!digit_varies(varying, shift)) return;
-    __shared__ uint32_t part[1024];
+    if (next_counts && digit_varies(varying, next_shift))
+        for (int64_t i = threadIdx.x; i < total; i += 1024) next_counts[i] = 0;
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t per = ceil_div(total, 1024);
     const int64_t b = threadIdx.x * per, e = min(total, b + per);
     uint32_t sum = 0;
     for (int64_t i = b; i < e; ++i) sum += counts[i];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    uint32_t incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    uint32_t run = part[threadIdx.x] - sum;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = (warp ? wsum[warp - 1] : 0) + incl - sum;
     for (int64_t i = b; i < e; ++i) {
         const uint32_t c = counts[i];
         counts[i] = run;
@@ -187,29 +283,38 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-template <typename K>
+template <typename K, int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads)
     radix_scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                          K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
                          const unsigned long long* varying, const uint32_t* __restrict__ offsets,
-                         int ntiles) {
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    if (!digit_varies(varying, shift)) {
-        for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
-            const int64_t p = base + i;
-            if (p < n) {
-                kout[p] = kin[p];
-                vout[p] = vin[p];
-            }
-        }
-        return;
-    }
+                         int ntiles, uint32_t* __restrict__ next_counts, int next_shift) {
+    constexpr int kTile = kSortThreads * ROUNDS;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const bool count_next = next_counts != nullptr && digit_varies(varying, next_shift);
     __shared__ uint32_t run_off[kRadix];
     __shared__ uint32_t warp_cnt[kSortThreads / 32][kRadix];
+    if (!digit_varies(varying, shift)) {
+        // keys keep their positions: this tile's next-digit histogram is local
+        if (count_next) run_off[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kTile; i += kSortThreads) {
+            const int64_t p = base + i;
+            if (p < n) {
+                const K key = kin[p];
+                kout[p] = key;
+                vout[p] = vin[p];
+                if (count_next) atomicAdd(&run_off[(uint32_t)(key >> next_shift) & 0xFFu], 1u);
+            }
+        }
+        __syncthreads();
+        if (count_next) next_counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = run_off[threadIdx.x];
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     run_off[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (int round = 0; round < kSortRounds; ++round) {
+    for (int round = 0; round < ROUNDS; ++round) {
         uint32_t* wc = &warp_cnt[0][0];
         for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads) wc[i] = 0;
         __syncthreads();
@@ -236,66 +341,86 @@ __global__ void __launch_bounds__(kSortThreads)
             const uint32_t dst = warp_cnt[warp][dg] + rank;
             kout[dst] = key;
             vout[dst] = vin[p];
+            if (count_next)
+                atomicAdd(&next_counts[(int64_t)((key >> next_shift) & 0xFFu) * ntiles + dst / kTile],
+                          1u);
         }
         __syncthreads();
     }
 }
 
-template <typename K>
-cudaError_t radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n,
-                            int key_bits, void* temp, bool* result_in_alt, cudaStream_t s,
-                            const char* tag) {
-    *result_in_alt = false;
-    if (n <= 1) return cudaSuccess;
-    const int ntiles = (int)ceil_div(n, kSortTile);
+template <typename K, int ROUNDS>
+cudaError_t radix_sort_rounds(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n,
+                              int key_bits, void* temp, bool* result_in_alt, cudaStream_t s) {
+    constexpr int kTile = kSortThreads * ROUNDS;
+    const int ntiles = (int)ceil_div(n, kTile);
+    const int64_t total = (int64_t)kRadix * ntiles;
     unsigned long long* varying = (unsigned long long*)temp;
-    uint32_t* counts = (uint32_t*)((char*)temp + 256);
+    uint32_t* counts[2] = {(uint32_t*)((char*)temp + 256),
+                           (uint32_t*)((char*)temp + 256) + total};
     cudaError_t e = cudaMemsetAsync(varying, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    const int or_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
-    e = launch(tag, or_diff_kernel<K>, dim3(or_blocks), dim3(256), 0, s, (const K*)keys, n,
-               varying);
+    e = launch("radix_hist", radix_first_hist_kernel<K, ROUNDS>, dim3(ntiles), dim3(kSortThreads), 0,
+               s, (const K*)keys, n, varying, counts[0], ntiles);
     if (e != cudaSuccess) return e;
     K* src_k = keys;
     uint32_t* src_v = vals;
     K* dst_k = keys_alt;
     uint32_t* dst_v = vals_alt;
+    int cur = 0;
     for (int shift = 0; shift < key_bits; shift += 8) {
-        e = launch("radix_hist", radix_hist_kernel<K>, dim3(ntiles), dim3(kSortThreads), 0, s,
-                   (const K*)src_k, n, shift, (const unsigned long long*)varying, counts, ntiles);
+        const bool last = shift + 8 >= key_bits;
+        uint32_t* nxt = last ? nullptr : counts[cur ^ 1];
+        e = launch("radix_scan", radix_scan_kernel, dim3(1), dim3(1024), 0, s, counts[cur], total,
+                   shift, nxt, shift + 8, (const unsigned long long*)varying);
         if (e != cudaSuccess) return e;
-        e = launch("radix_scan", radix_scan_kernel, dim3(1), dim3(1024), 0, s, counts,
-                   (int64_t)kRadix * ntiles, shift, (const unsigned long long*)varying);
-        if (e != cudaSuccess) return e;
-        e = launch("radix_scatter", radix_scatter_kernel<K>, dim3(ntiles), dim3(kSortThreads), 0,
-                   s, (const K*)src_k, (const uint32_t*)src_v, dst_k, dst_v, n, shift,
-                   (const unsigned long long*)varying, (const uint32_t*)counts, ntiles);
+        e = launch("radix_scatter", radix_scatter_kernel<K, ROUNDS>, dim3(ntiles),
+                   dim3(kSortThreads), 0, s, (const K*)src_k, (const uint32_t*)src_v, dst_k, dst_v,
+                   n, shift, (const unsigned long long*)varying, (const uint32_t*)counts[cur],
+                   ntiles, nxt, shift + 8);
         if (e != cudaSuccess) return e;
         std::swap(src_k, dst_k);
         std::swap(src_v, dst_v);
         *result_in_alt = !*result_in_alt;
+        cur ^= 1;
     }
     return cudaSuccess;
+}
+
+constexpr int64_t kSmallSort = 1 << 20;
+
+template <typename K>
+cudaError_t radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n,
+                            int key_bits, void* temp, bool* result_in_alt, cudaStream_t s) {
+    *result_in_alt = false;
+    if (n <= 1 || key_bits <= 0) return cudaSuccess;
+    if (n <= kSmallSort)
+        return radix_sort_rounds<K, 4>(keys, vals, keys_alt, vals_alt, n, key_bits, temp,
+                                       result_in_alt, s);
+    return radix_sort_rounds<K, 16>(keys, vals, keys_alt, vals_alt, n, key_bits, temp,
+                                    result_in_alt, s);
 }
 
 }  // namespace
 
 size_t radix_sort_temp_bytes(int64_t n) {
-    return 256 + sizeof(uint32_t) * (size_t)kRadix * (size_t)ceil_div(std::max<int64_t>(n, 1), kSortTile);
+    const int64_t tile = n <= kSmallSort ? 1024 : 4096;
+    return 256 + 2 * sizeof(uint32_t) * (size_t)kRadix *
+                     (size_t)ceil_div(std::max<int64_t>(n, 1), tile);
 }
 
 cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                            int64_t n, int key_bits, void* temp, bool* result_in_alt,
                            cudaStream_t s) {
     return radix_sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, key_bits, temp,
-                                     result_in_alt, s, "radix_or_diff_u64");
+                                     result_in_alt, s);
 }
 
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                            int64_t n, int key_bits, void* temp, bool* result_in_alt,
                            cudaStream_t s) {
     return radix_sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, key_bits, temp,
-                                     result_in_alt, s, "radix_or_diff_u32");
+                                     result_in_alt, s);
 }
 
 // =====================================================================
@@ -304,27 +429,19 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
 
 namespace {
 
-// s_x >= 0, so its IEEE bit pattern orders like the value (both zeros are +0).
-__global__ void iota_keys_kernel(const double* __restrict__ s, uint64_t* keys, uint32_t* vals,
-                                 int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    keys[i] = (uint64_t)__double_as_longlong(s[i] + 0.0);
-    vals[i] = (uint32_t)i;
-}
-
-__global__ void iota_kernel(uint32_t* v, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = (uint32_t)i;
-}
-
+// Rank r -> sub-dataset j; U_j^2 from the last rank of each range.  Also writes
+// the keys (j by id) and values (ids) of the stable sort into storage order.
 __global__ void segment_assign_kernel(const uint64_t* __restrict__ sorted_keys,
                                       const uint32_t* __restrict__ sorted_ids, int64_t n, int m,
-                                      uint32_t* sub_of_id, double* U2) {
+                                      uint32_t* sub_of_id, double* U2, uint32_t* jkeys,
+                                      uint32_t* jvals) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int32_t j = seg_of(r, n, m);
-    sub_of_id[sorted_ids[r]] = (uint32_t)j;
+    const uint32_t id = sorted_ids[r];
+    sub_of_id[id] = (uint32_t)j;
+    jkeys[id] = (uint32_t)j;
+    jvals[r] = (uint32_t)r;
     if (r == seg_start(j + 1, n, m) - 1) U2[j] = __longlong_as_double((long long)sorted_keys[r]);
 }
 
@@ -356,21 +473,11 @@ __global__ void gather_items_kernel(const T* __restrict__ X, int64_t ld, int d, 
 
 }  // namespace
 
-cudaError_t launch_iota_keys(const double* s, uint64_t* keys, uint32_t* vals, int64_t n,
-                             cudaStream_t st) {
-    return launch("iota_keys", iota_keys_kernel, dim3((unsigned)ceil_div(n, 256)), dim3(256), 0, st,
-                  s, keys, vals, n);
-}
-
-cudaError_t launch_iota(uint32_t* v, int64_t n, cudaStream_t st) {
-    return launch("iota", iota_kernel, dim3((unsigned)ceil_div(n, 256)), dim3(256), 0, st, v, n);
-}
-
 cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* sorted_ids,
                                   int64_t n, int m, uint32_t* sub_of_id, double* U2,
-                                  cudaStream_t st) {
+                                  uint32_t* jkeys, uint32_t* jvals, cudaStream_t st) {
     return launch("segment_assign", segment_assign_kernel, dim3((unsigned)ceil_div(n, 256)),
-                  dim3(256), 0, st, sorted_keys, sorted_ids, n, m, sub_of_id, U2);
+                  dim3(256), 0, st, sorted_keys, sorted_ids, n, m, sub_of_id, U2, jkeys, jvals);
 }
 
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
@@ -393,27 +500,11 @@ cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d
 
 namespace {
 
-// A_pad: (d+1) x Lp, columns b >= L zero.  anorm[b]: fp32 upper bound of
-// ||a_{0..d-1, b}||_2 (computed in FP64, rounded up).
-__global__ void prepare_projections_kernel(const float* __restrict__ A, int d, int L, int Lp,
-                                           float* A_pad, float* anorm) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= Lp) return;
-    double ss = 0.0;
-    for (int k = 0; k <= d; ++k) {
-        const float v = b < L ? A[(int64_t)k * L + b] : 0.0f;
-        A_pad[(int64_t)k * Lp + b] = v;
-        if (k < d) ss = fma((double)v, (double)v, ss);
-    }
-    anorm[b] = __fsqrt_ru(__double2float_ru(ss));
-}
-
-constexpr int kProjRows = 128;     // rows per block
 constexpr int kProjThreads = 256;  // 8 warps: warp w owns bit group w, lane owns rows
 constexpr int kProjKC = 32;        // columns of X staged per step
 
 // Bit b of row x, FP64 in the fixed order: sum_k a_kb x_k (k = 0..d-1) then
-// + fl(a_db * tau) for items.
+// + fl(a_db * tau) for items.  This is the canonical definition of the bit.
 template <typename T>
 __device__ bool project_bit_fp64(const T* __restrict__ xrow, const float* __restrict__ A_pad,
                                  int Lp, int d, int b, bool has_tail, double tau) {
@@ -424,35 +515,38 @@ __device__ bool project_bit_fp64(const T* __restrict__ xrow, const float* __rest
     return acc >= 0.0;
 }
 
-// Block: 128 rows x Lp bits.  Warp w owns bits [w BT, (w+1) BT), lane owns rows
-// lane + 32 i.  X and A are staged kProjKC columns at a time; every (row, bit)
-// accumulates in FP32 in column order.
-template <typename T, typename C, int BT>
+// Block: 32 RI rows x Lp bits.  Warp w owns bits [w BT, (w+1) BT), lane owns rows
+// lane + 32 i (i < RI).  X and A are staged kProjKC columns at a time; every
+// (row, bit) accumulates in FP32 in column order.  A bit whose FP32 value lies
+// inside the error bound is left 0 and its (row, bit) pair is appended to
+// `amb_list` for the resolve kernel (or, if the list is full, decided here by
+// the canonical FP64 evaluation).
+template <typename T, typename C, int BT, int RI>
 __global__ void __launch_bounds__(kProjThreads)
     project_fp32_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int L, int Lp,
                         const float* __restrict__ A_pad, const float* __restrict__ anorm,
                         const double* __restrict__ tau64, const float* __restrict__ tau32,
                         const float* __restrict__ xnorm, C* __restrict__ codes,
-                        unsigned long long* ambiguous, float kappa) {
+                        unsigned long long* __restrict__ amb_list, unsigned* amb_count,
+                        unsigned amb_cap, float kappa) {
+    constexpr int kRows = 32 * RI;
     __shared__ float As[kProjKC][8 * BT];
-    __shared__ float Xs[kProjKC][kProjRows + 1];
-    __shared__ unsigned long long code_s[kProjRows];
-    __shared__ unsigned amb_s;
+    __shared__ float Xs[kProjKC][kRows + 1];
+    __shared__ unsigned long long code_s[kRows];
 
     const int lane = threadIdx.x & 31, bg = threadIdx.x >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * kProjRows;
-    if (threadIdx.x < kProjRows) code_s[threadIdx.x] = 0ull;
-    if (threadIdx.x == 0) amb_s = 0;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    if (threadIdx.x < kRows) code_s[threadIdx.x] = 0ull;
 
-    float acc[4][BT];
+    float acc[RI][BT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RI; ++i)
 #pragma unroll
         for (int b = 0; b < BT; ++b) acc[i][b] = 0.0f;
 
     for (int k0 = 0; k0 < d; k0 += kProjKC) {
         __syncthreads();
-        for (int i = threadIdx.x; i < kProjRows * kProjKC; i += kProjThreads) {
+        for (int i = threadIdx.x; i < kRows * kProjKC; i += kProjThreads) {
             const int r = i / kProjKC, c = i % kProjKC;
             const int64_t row = row0 + r;
             const int col = k0 + c;
@@ -465,21 +559,21 @@ __global__ void __launch_bounds__(kProjThreads)
         __syncthreads();
         const int kc = min(kProjKC, d - k0);
         for (int c = 0; c < kc; ++c) {
-            float xv[4];
+            float xv[RI];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) xv[i] = Xs[c][lane + 32 * i];
+            for (int i = 0; i < RI; ++i) xv[i] = Xs[c][lane + 32 * i];
 #pragma unroll
             for (int b = 0; b < BT; ++b) {
                 const float a = As[c][bg * BT + b];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i][b] = fmaf(xv[i], a, acc[i][b]);
+                for (int i = 0; i < RI; ++i) acc[i][b] = fmaf(xv[i], a, acc[i][b]);
             }
         }
     }
 
     const bool has_tail = tau64 != nullptr;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RI; ++i) {
         const int r = lane + 32 * i;
         const int64_t row = row0 + r;
         if (row >= n) continue;
@@ -495,82 +589,158 @@ __global__ void __launch_bounds__(kProjThreads)
             // |v - v64| <= bound: FP32 summation error with Cauchy-Schwarz for
             // sum |a_k x_k|, the tau rounding, and a 4x margin (kappa = (d+2) 2^-22).
             const float bound = kappa * anorm[bit] * xn + 0x1p-20f * fabsf(ad) * t32;
-            bool set;
             if (fabsf(v) * (1.0f - 0x1p-21f) > bound) {
-                set = v > 0.0f;
+                if (v > 0.0f) word |= 1ull << bit;
             } else {
-                set = project_bit_fp64(X + row * ldx, A_pad, Lp, d, bit, has_tail,
-                                       has_tail ? tau64[row] : 0.0);
-                atomicAdd(&amb_s, 1u);
+                const unsigned slot = atomicAdd(amb_count, 1u);
+                if (slot < amb_cap) {
+                    amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
+                } else if (project_bit_fp64(X + row * ldx, A_pad, Lp, d, bit, has_tail,
+                                            has_tail ? tau64[row] : 0.0)) {
+                    word |= 1ull << bit;
+                }
             }
-            if (set) word |= 1ull << bit;
         }
         if (word) atomicOr(&code_s[r], word);
     }
     __syncthreads();
-    if (threadIdx.x < kProjRows) {
+    if (threadIdx.x < kRows) {
         const int64_t row = row0 + threadIdx.x;
         if (row < n) codes[row] = (C)code_s[threadIdx.x];
     }
-    if (threadIdx.x == 0 && amb_s) atomicAdd(ambiguous, (unsigned long long)amb_s);
+}
+
+__device__ __forceinline__ void or_bit(uint32_t* w, int bit) { atomicOr(w, 1u << bit); }
+__device__ __forceinline__ void or_bit(uint64_t* w, int bit) {
+    atomicOr((unsigned long long*)w, 1ull << bit);
+}
+
+// Warp per undecided (row, bit): FP64 dot in lane-strided order, then a tree.
+// Both that sum and the canonical in-order sum are within (d-1) 2^-53 sum|a_k x_k|
+// of the exact value, so outside (2d + 8) 2^-53 (sum|a_k x_k| + |tail|) plus the
+// final-add rounding the two have the same sign.  Otherwise lane 0 evaluates the
+// canonical sequential form.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    resolve_kernel(const T* __restrict__ X, int d, int ldx, int Lp, const float* __restrict__ A_pad,
+                   const double* __restrict__ tau64, const unsigned long long* __restrict__ list,
+                   const unsigned* __restrict__ count, unsigned cap, C* __restrict__ codes) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned cnt = min(*count, cap);
+    for (int64_t e = warp; e < cnt; e += nwarps) {
+        const unsigned long long entry = list[e];
+        const int64_t row = (int64_t)(entry >> 6);
+        const int bit = (int)(entry & 63);
+        const T* xr = X + row * ldx;
+        double s = 0.0, sa = 0.0;
+        for (int k = lane; k < d; k += 32) {
+            const double p = (double)to_f32(xr[k]) * (double)A_pad[(int64_t)k * Lp + bit];
+            s += p;
+            sa += fabs(p);
+        }
+        for (int o = 16; o; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        }
+        const bool has_tail = tau64 != nullptr;
+        const double tail = has_tail ? __dmul_rn((double)A_pad[(int64_t)d * Lp + bit], tau64[row]) : 0.0;
+        const double v = __dadd_rn(s, tail);
+        const double bound = (2.0 * d + 8.0) * 0x1p-53 * (sa + fabs(tail)) + 0x1p-50 * fabs(v);
+        bool set;
+        if (fabs(v) > bound) {
+            set = v > 0.0;
+        } else {
+            int r = 0;
+            if (lane == 0)
+                r = project_bit_fp64(xr, A_pad, Lp, d, bit, has_tail, has_tail ? tau64[row] : 0.0);
+            set = __shfl_sync(0xffffffffu, r, 0) != 0;
+        }
+        if (lane == 0 && set) or_bit(codes + row, bit);
+    }
+}
+
+template <typename T, typename C, int BT>
+cudaError_t project_rows(const void* X, int64_t n, int d, int ldx, int L, int Lp,
+                         const float* A_pad, const float* anorm, const double* tau64,
+                         const float* tau32, const float* xnorm, void* codes,
+                         unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
+                         float kappa, cudaStream_t st, const char* name) {
+    // 4 rows per thread when that still gives two blocks per SM, else 2
+    if (ceil_div(n, 128) >= 2 * 152)
+        return launch(name, project_fp32_kernel<T, C, BT, 4>, dim3((unsigned)ceil_div(n, 128)),
+                      dim3(kProjThreads), 0, st, (const T*)X, n, d, ldx, L, Lp, A_pad, anorm, tau64,
+                      tau32, xnorm, (C*)codes, amb_list, amb_count, amb_cap, kappa);
+    return launch(name, project_fp32_kernel<T, C, BT, 2>, dim3((unsigned)ceil_div(n, 64)),
+                  dim3(kProjThreads), 0, st, (const T*)X, n, d, ldx, L, Lp, A_pad, anorm, tau64,
+                  tau32, xnorm, (C*)codes, amb_list, amb_count, amb_cap, kappa);
 }
 
 template <typename T, typename C>
 cudaError_t project_dispatch(const void* X, int64_t n, int d, int ldx, int L, int Lp,
                              const float* A_pad, const float* anorm, const double* tau64,
                              const float* tau32, const float* xnorm, void* codes,
-                             unsigned long long* amb, cudaStream_t st, const char* name) {
+                             unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
+                             cudaStream_t st, const char* name) {
     const float kappa = (float)(d + 2) * 0x1p-22f;
-    const dim3 grid((unsigned)ceil_div(n, kProjRows));
+    cudaError_t e;
     switch (Lp / 8) {
         case 1:
-            return launch(name, project_fp32_kernel<T, C, 1>, grid, dim3(kProjThreads), 0, st,
-                          (const T*)X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
-                          (C*)codes, amb, kappa);
+            e = project_rows<T, C, 1>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
         case 2:
-            return launch(name, project_fp32_kernel<T, C, 2>, grid, dim3(kProjThreads), 0, st,
-                          (const T*)X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
-                          (C*)codes, amb, kappa);
+            e = project_rows<T, C, 2>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
         case 4:
-            return launch(name, project_fp32_kernel<T, C, 4>, grid, dim3(kProjThreads), 0, st,
-                          (const T*)X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
-                          (C*)codes, amb, kappa);
+            e = project_rows<T, C, 4>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
         case 8:
-            return launch(name, project_fp32_kernel<T, C, 8>, grid, dim3(kProjThreads), 0, st,
-                          (const T*)X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
-                          (C*)codes, amb, kappa);
+            e = project_rows<T, C, 8>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
         default:
             return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 256, 32), 8),
+                                                      8 * 152);
+    return launch("resolve_fp64", resolve_kernel<T, C>, dim3(grid), dim3(256), 0, st, (const T*)X, d,
+                  ldx, Lp, A_pad, tau64, (const unsigned long long*)amb_list,
+                  (const unsigned*)amb_count, amb_cap, (C*)codes);
 }
 
 }  // namespace
 
-cudaError_t launch_prepare_projections(const float* A, int d, int L, int Lp, float* A_pad,
-                                       float* anorm, cudaStream_t st) {
-    return launch("prepare_projections", prepare_projections_kernel,
-                  dim3((unsigned)ceil_div(Lp, 64)), dim3(64), 0, st, A, d, L, Lp, A_pad, anorm);
-}
-
 cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx,
                                 int L, int Lp, const float* A_pad, const float* anorm,
                                 const double* tau64, const float* tau32, const float* xnorm,
-                                void* codes, int code_bytes, unsigned long long* ambiguous,
-                                cudaStream_t st) {
+                                void* codes, int code_bytes, unsigned long long* amb_list,
+                                unsigned* amb_count, unsigned amb_cap, cudaStream_t st) {
     if (dt == NRLSH_BF16) {
         if (code_bytes == 4)
             return project_dispatch<__nv_bfloat16, uint32_t>(X, n, d, ldx, L, Lp, A_pad, anorm,
-                                                             tau64, tau32, xnorm, codes, ambiguous,
-                                                             st, "project_fp32_bf16");
+                                                             tau64, tau32, xnorm, codes, amb_list,
+                                                             amb_count, amb_cap, st,
+                                                             "project_fp32_bf16");
         return project_dispatch<__nv_bfloat16, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64,
-                                                         tau32, xnorm, codes, ambiguous, st,
-                                                         "project_fp32_bf16");
+                                                         tau32, xnorm, codes, amb_list, amb_count,
+                                                         amb_cap, st, "project_fp32_bf16");
     }
     if (code_bytes == 4)
         return project_dispatch<float, uint32_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32,
-                                                 xnorm, codes, ambiguous, st, "project_fp32");
-    return project_dispatch<float, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32,
-                                             xnorm, codes, ambiguous, st, "project_fp32");
+                                                 xnorm, codes, amb_list, amb_count, amb_cap, st,
+                                                 "project_fp32");
+    return project_dispatch<float, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
+                                             codes, amb_list, amb_count, amb_cap, st,
+                                             "project_fp32");
+}
+
+size_t ambiguity_capacity(int64_t rows, int L) {
+    return (size_t)std::max<int64_t>(4096, rows * L / 64);
 }
 
 // =====================================================================
@@ -627,24 +797,54 @@ __device__ __forceinline__ dd dd_div_d(dd a, double b) {
     return quick_two_sum(q1, q2);
 }
 
-// Taylor series on |x| <= pi/4; 1/(2i)! terms fall below 2^-110 well before i = 14.
+// 1/i! for i = 0..29 as double-double pairs (hi = 1/i! rounded to nearest,
+// lo = the rounded remainder), written out from the exact rationals.
+__constant__ dd kInvFact[30] = {
+    {0x1.0000000000000p+0, 0x0.0p+0},  // 1/0!
+    {0x1.0000000000000p+0, 0x0.0p+0},  // 1/1!
+    {0x1.0000000000000p-1, 0x0.0p+0},  // 1/2!
+    {0x1.5555555555555p-3, 0x1.5555555555555p-57},  // 1/3!
+    {0x1.5555555555555p-5, 0x1.5555555555555p-59},  // 1/4!
+    {0x1.1111111111111p-7, 0x1.1111111111111p-63},  // 1/5!
+    {0x1.6c16c16c16c17p-10, -0x1.f49f49f49f49fp-65},  // 1/6!
+    {0x1.a01a01a01a01ap-13, 0x1.a01a01a01a01ap-73},  // 1/7!
+    {0x1.a01a01a01a01ap-16, 0x1.a01a01a01a01ap-76},  // 1/8!
+    {0x1.71de3a556c734p-19, -0x1.c154f8ddc6c00p-73},  // 1/9!
+    {0x1.27e4fb7789f5cp-22, 0x1.cbbc05b4fa99ap-76},  // 1/10!
+    {0x1.ae64567f544e4p-26, -0x1.c062e06d1f209p-80},  // 1/11!
+    {0x1.1eed8eff8d898p-29, -0x1.2aec959e14c06p-83},  // 1/12!
+    {0x1.6124613a86d09p-33, 0x1.f28e0cc748ebep-87},  // 1/13!
+    {0x1.93974a8c07c9dp-37, 0x1.05d6f8a2efd1fp-92},  // 1/14!
+    {0x1.ae7f3e733b81fp-41, 0x1.1d8656b0ee8cbp-97},  // 1/15!
+    {0x1.ae7f3e733b81fp-45, 0x1.1d8656b0ee8cbp-101},  // 1/16!
+    {0x1.952c77030ad4ap-49, 0x1.ac981465ddc6cp-103},  // 1/17!
+    {0x1.6827863b97d97p-53, 0x1.eec01221a8b0bp-107},  // 1/18!
+    {0x1.2f49b46814157p-57, 0x1.2650f61dbdcb4p-112},  // 1/19!
+    {0x1.e542ba4020225p-62, 0x1.ea72b4afe3c2fp-120},  // 1/20!
+    {0x1.71b8ef6dcf572p-66, -0x1.d043ae40c4647p-120},  // 1/21!
+    {0x1.0ce396db7f853p-70, -0x1.aebcdbd20331cp-124},  // 1/22!
+    {0x1.761b41316381ap-75, -0x1.3423c7d91404fp-130},  // 1/23!
+    {0x1.f2cf01972f578p-80, -0x1.9ada5fcc1ab14p-135},  // 1/24!
+    {0x1.3f3ccdd165fa9p-84, -0x1.58ddadf344487p-139},  // 1/25!
+    {0x1.88e85fc6a4e5ap-89, -0x1.71c37ebd16540p-143},  // 1/26!
+    {0x1.d1ab1c2dccea3p-94, 0x1.054d0c78aea14p-149},  // 1/27!
+    {0x1.0a18a2635085dp-98, 0x1.b9e2e28e1aa54p-153},  // 1/28!
+    {0x1.259f98b4358adp-103, 0x1.eaf8c39dd9bc5p-157},  // 1/29!
+};
+
+// Taylor series on |x| <= pi/4 by Horner's rule in y = x^2; the first omitted
+// term, x^30/30!, is below 2^-120.
 __device__ dd dd_cos_small(dd x) {
-    const dd x2 = dd_mul(x, x);
-    dd term = {1.0, 0.0}, sum = {1.0, 0.0};
-    for (int i = 1; i < 16; ++i) {
-        term = dd_div_d(dd_mul(term, dd_neg(x2)), (double)((2 * i - 1) * (2 * i)));
-        sum = dd_add(sum, term);
-    }
-    return sum;
+    const dd my = dd_neg(dd_mul(x, x));
+    dd p = kInvFact[28];
+    for (int i = 13; i >= 0; --i) p = dd_add(kInvFact[2 * i], dd_mul(my, p));
+    return p;
 }
 __device__ dd dd_sin_small(dd x) {
-    const dd x2 = dd_mul(x, x);
-    dd term = x, sum = x;
-    for (int i = 1; i < 16; ++i) {
-        term = dd_div_d(dd_mul(term, dd_neg(x2)), (double)((2 * i) * (2 * i + 1)));
-        sum = dd_add(sum, term);
-    }
-    return sum;
+    const dd my = dd_neg(dd_mul(x, x));
+    dd p = kInvFact[29];
+    for (int i = 13; i >= 0; --i) p = dd_add(kInvFact[2 * i + 1], dd_mul(my, p));
+    return dd_mul(x, p);
 }
 
 // cos(pi (1 - eps) (L - l) / L) rounded to nearest.  The angle is exactly pi/2
@@ -671,60 +871,61 @@ __device__ double cos_class(int L, int l, double eps) {
     return __dadd_rn(r.hi, r.lo);
 }
 
-// key = (s_hat, l, j), compared descending.
-__global__ void bucket_keys_kernel(const double* __restrict__ U2, int m, int L, float eps,
-                                   double* shat) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m * (L + 1)) return;
-    const int j = c / (L + 1), l = c % (L + 1);
-    const double cl = cos_class(L, l, (double)eps);
-    const double U = sqrt(U2[j]);
-    shat[c] = __dadd_rn(__dmul_rn(U, cl), 0.0);  // +0.0 turns -0 into +0
+// Order-preserving image of a double as an unsigned integer.
+__device__ __forceinline__ unsigned long long double_order(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-__device__ __forceinline__ bool key_greater(double s1, int l1, int j1, double s0, int l0, int j0) {
-    if (s1 != s0) return s1 > s0;
-    if (l1 != l0) return l1 > l0;
-    return j1 > j0;
-}
+constexpr int kBucketThreads = 256;
 
-// rank(c) = number of buckets whose key is greater; order[rank] = c.
-__global__ void bucket_rank_kernel(const double* __restrict__ shat, int m, int L,
-                                   double* shat_sorted, uint32_t* order) {
-    __shared__ double ks[256];
+// One launch builds the probing order.  Every block computes the L+1 values c_l
+// (one thread each) and all m(L+1) keys s_hat = fl(U_j c_l) in shared memory;
+// each thread then ranks its own bucket by counting the buckets with a greater
+// key (s_hat, l, j), compared as integers.  order[rank] = j (L+1) + l.
+__global__ void __launch_bounds__(kBucketThreads)
+    bucket_order_kernel(const double* __restrict__ U2, int m, int L, float eps,
+                        double* __restrict__ shat_sorted, uint32_t* __restrict__ order) {
+    extern __shared__ unsigned long long keys[];     // ncls order keys
+    uint32_t* tie = (uint32_t*)(keys + m * (L + 1));  // ncls tie keys l 2^16 + j
+    double* cl = (double*)(tie + ((m * (L + 1) + 1) & ~1));  // L+1 cosines
     const int ncls = m * (L + 1);
+    for (int l = threadIdx.x; l <= L; l += blockDim.x) cl[l] = cos_class(L, l, (double)eps);
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
+        const int j = c / (L + 1), l = c % (L + 1);
+        const double sh = __dadd_rn(__dmul_rn(sqrt(U2[j]), cl[l]), 0.0);  // -0 -> +0
+        keys[c] = double_order(sh);
+        tie[c] = ((uint32_t)l << 16) | (uint32_t)j;
+    }
+    __syncthreads();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = c < ncls;
-    const double s0 = valid ? shat[c] : 0.0;
-    const int l0 = valid ? c % (L + 1) : 0, j0 = valid ? c / (L + 1) : 0;
+    if (c >= ncls) return;
+    const unsigned long long k0 = keys[c];
+    const uint32_t t0 = tie[c];
+    const int l0 = c % (L + 1), j0 = c / (L + 1);
     int rank = 0;
-    for (int b = 0; b < ncls; b += 256) {
-        __syncthreads();
-        if (b + threadIdx.x < ncls) ks[threadIdx.x] = shat[b + threadIdx.x];
-        __syncthreads();
-        const int lim = min(256, ncls - b);
-        for (int i = 0; i < lim; ++i) {
-            const int c1 = b + i;
-            rank += key_greater(ks[i], c1 % (L + 1), c1 / (L + 1), s0, l0, j0);
-        }
+    for (int c1 = 0; c1 < ncls; ++c1) {
+        const unsigned long long k1 = keys[c1];
+        rank += (k1 > k0) || (k1 == k0 && tie[c1] > t0);
     }
-    if (valid) {
-        order[rank] = (uint32_t)c;
-        shat_sorted[rank] = s0;
-    }
+    order[rank] = (uint32_t)c;
+    shat_sorted[rank] = __dadd_rn(__dmul_rn(sqrt(U2[j0]), cl[l0]), 0.0);
 }
 
 }  // namespace
 
 cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, double* shat_sorted,
-                                uint32_t* order, double* scratch_keys, cudaStream_t st) {
+                                uint32_t* order, double* /*unused*/, cudaStream_t st) {
     const int ncls = m * (L + 1);
-    const dim3 grid((unsigned)ceil_div(ncls, 256));
-    cudaError_t e = launch("bucket_keys", bucket_keys_kernel, grid, dim3(256), 0, st, U2, m, L, eps,
-                           scratch_keys);
+    const size_t smem = sizeof(unsigned long long) * ncls + sizeof(uint32_t) * ((ncls + 1) & ~1) +
+                        sizeof(double) * (L + 1);
+    cudaError_t e = cudaFuncSetAttribute(bucket_order_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch("bucket_rank", bucket_rank_kernel, grid, dim3(256), 0, st,
-                  (const double*)scratch_keys, m, L, shat_sorted, order);
+    return launch("bucket_order", bucket_order_kernel,
+                  dim3((unsigned)ceil_div(ncls, kBucketThreads)), dim3(kBucketThreads), smem, st,
+                  U2, m, L, eps, shat_sorted, order);
 }
 
 }  // namespace nrlsh

@@ -84,9 +84,12 @@ struct PosTile {
 // ----------------------------------------------------------- build launchers
 // All return cudaError_t of the last launch; pointers are device pointers.
 
-cudaError_t launch_gen_projections(float* A, int d, int L, uint64_t seed, cudaStream_t s);
+// A ((d+1) x L), its zero-padded copy A_pad ((d+1) x Lp) and column-norm bounds anorm.
+cudaError_t launch_projections(float* A, float* A_pad, float* anorm, int d, int L, int Lp,
+                               uint64_t seed, cudaStream_t s);
+// s_x in FP64; with keys/vals non-null also the partition's sort keys and ids.
 cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64_t ld, double* s,
-                          cudaStream_t st);
+                          uint64_t* keys, uint32_t* vals, cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of the key.
 // Buffers alternate; returns through *result_in_alt whether the result is in the alt pair.
 size_t radix_sort_temp_bytes(int64_t n);
@@ -96,25 +99,24 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                            int64_t n, int key_bits, void* temp, bool* result_in_alt,
                            cudaStream_t s);
-cudaError_t launch_iota_keys(const double* s, uint64_t* keys, uint32_t* vals, int64_t n,
-                             cudaStream_t st);
 cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* sorted_ids,
                                   int64_t n, int m, uint32_t* sub_of_id, double* U2,
-                                  cudaStream_t st);
-cudaError_t launch_iota(uint32_t* v, int64_t n, cudaStream_t st);
+                                  uint32_t* jkeys, uint32_t* jvals, cudaStream_t st);
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
                                 const uint32_t* perm, int64_t n, int m, const double* s_id,
                                 const double* U2, void* Xp, double* s_pos, double* tau64,
                                 float* tau32, float* xnorm, cudaStream_t st);
-cudaError_t launch_prepare_projections(const float* A, int d, int L, int Lp, float* A_pad,
-                                       float* anorm, cudaStream_t st);
-// Sign random projection of rows of X (n x dp, stored dtype) with the FP32 fast
-// tier and the FP64 recompute; items (tau != null) or queries (tau == null).
-cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int dp,
+// Sign random projection of rows of X (row stride ldx, stored dtype) with the FP32
+// fast tier; undecided (row, bit) pairs go through amb_list (capacity amb_cap,
+// count in *amb_count, which must start at 0) to the FP64 resolve kernel.
+// Items pass tau (tau64 != null); queries pass tau64 = tau32 = null.
+cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx,
                                 int L, int Lp, const float* A_pad, const float* anorm,
                                 const double* tau64, const float* tau32, const float* xnorm,
-                                void* codes, int code_bytes, unsigned long long* ambiguous,
-                                cudaStream_t st);
+                                void* codes, int code_bytes, unsigned long long* amb_list,
+                                unsigned* amb_count, unsigned amb_cap, cudaStream_t st);
+// Entries of the ambiguity list to reserve for `rows` rows of L bits.
+size_t ambiguity_capacity(int64_t rows, int L);
 cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, double* shat_sorted,
                                 uint32_t* order, double* scratch_keys, cudaStream_t st);
 
@@ -145,6 +147,16 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
                         const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
                         const uint32_t* perm, uint32_t* cont, double* cont_s,
                         int64_t* out_ids, float* out_scores, int out_ld, cudaStream_t st);
+// Threshold walk, candidate selection, FP32 re-rank and exact top-k, one block
+// per query (the main query path after the histograms).
+cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
+                                int64_t nq, int64_t budget, const int64_t* budgets, uint32_t flags,
+                                const void* codes, const void* qcodes, int code_bytes,
+                                const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
+                                const float* xnorm, const float* qnorm, const uint32_t* perm, int k,
+                                const int32_t* ks, uint32_t* cand, float* lo, float* hi,
+                                uint32_t* cont, double* cont_s, int64_t cap, int64_t* out_ids,
+                                float* out_scores, int out_ld, cudaStream_t st);
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
                                const uint32_t* perm, int64_t nq, int32_t* out, int64_t out_cap,
                                int64_t* count, cudaStream_t st);

@@ -69,61 +69,63 @@ __global__ void row_norm_bound_kernel(const float* __restrict__ Q, int64_t nq, i
 
 // --------------------------------------------------------------- histogram
 
-constexpr int kHistQ = 128;  // queries per block, one per thread
+constexpr int kHistQ = 64;  // queries per block, one per thread
 
-// Block: one position tile (inside one sub-dataset) x 128 queries.  The tile's
-// codes sit in shared memory and are read by broadcast; each thread keeps a
-// private histogram column (uint16, tile length <= 4096) indexed [l][thread],
-// so increments never conflict on a bank.
+// Block: one position tile (inside one sub-dataset) x 64 queries.  The tile's
+// codes sit in shared memory and are read by broadcast; each thread keeps two
+// private histogram columns (uint16, even and odd positions, so consecutive
+// increments do not wait on each other) indexed [l][thread], so increments
+// never conflict on a bank.  Tiles hold at most 4,096 codes.
 template <typename C>
 __global__ void __launch_bounds__(kHistQ)
     hist_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t nq, int m, int L,
                 const PosTile* __restrict__ tiles, uint32_t* __restrict__ H) {
     extern __shared__ unsigned char smem_raw[];
-    constexpr int kTile = 16384 / sizeof(C);
     C* cs = (C*)smem_raw;
-    uint16_t* hist = (uint16_t*)(smem_raw + 16384);
+    uint16_t* h0 = (uint16_t*)(smem_raw + 16384);
+    uint16_t* h1 = h0 + (L + 1) * kHistQ;
     const PosTile t = tiles[blockIdx.x];
     const int64_t q = (int64_t)blockIdx.y * kHistQ + threadIdx.x;
     for (int i = threadIdx.x; i < t.len; i += kHistQ) cs[i] = codes[t.start + i];
-    for (int l = 0; l <= L; ++l) hist[l * kHistQ + threadIdx.x] = 0;
+    for (int l = 0; l <= L; ++l) {
+        h0[l * kHistQ + threadIdx.x] = 0;
+        h1[l * kHistQ + threadIdx.x] = 0;
+    }
     __syncthreads();
     if (q >= nq) return;
     const C cq = qcodes[q];
-    for (int i = 0; i < t.len; ++i) {
-        const int l = L - popc_word(cq ^ cs[i]);
-        hist[l * kHistQ + threadIdx.x] += 1;
+    int i = 0;
+    for (; i + 1 < t.len; i += 2) {
+        const int l0 = L - popc_word(cq ^ cs[i]);
+        const int l1 = L - popc_word(cq ^ cs[i + 1]);
+        h0[l0 * kHistQ + threadIdx.x] += 1;
+        h1[l1 * kHistQ + threadIdx.x] += 1;
     }
+    if (i < t.len) h0[(L - popc_word(cq ^ cs[i])) * kHistQ + threadIdx.x] += 1;
     uint32_t* Hq = H + ((int64_t)q * m + t.seg) * (L + 1);
     for (int l = 0; l <= L; ++l) {
-        const uint32_t v = hist[l * kHistQ + threadIdx.x];
+        const uint32_t v = (uint32_t)h0[l * kHistQ + threadIdx.x] + h1[l * kHistQ + threadIdx.x];
         if (v) atomicAdd(&Hq[l], v);
     }
-    (void)kTile;
 }
 
 // --------------------------------------------------------------- threshold
 
-// Block per query.  Walks the buckets in probing order with a block scan of
-// their sizes until the running total reaches B' = min(B, n).  The boundary
-// bucket t* and everything before it define the probe: buckets before t* are
-// taken whole; within sub-dataset j they are l = L, L-1, ..., so
-// lam_j = L + 1 - (number of buckets of j before t*).
-__global__ void __launch_bounds__(256)
-    threshold_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order, int m,
-                     int L, int64_t nq, int64_t n, int64_t budget,
-                     const int64_t* __restrict__ budgets, uint32_t flags,
-                     uint8_t* __restrict__ lam, Boundary* __restrict__ bnd) {
-    extern __shared__ uint32_t cntj[];
+// Block phase (256 threads).  Walks the buckets in probing order with a block
+// scan of their sizes until the running total reaches B' = min(B, n).  Buckets
+// before the boundary bucket t* are taken whole; within sub-dataset j they are
+// l = L, L-1, ..., so lam_j = L + 1 - (number of buckets of j before t*).
+// cntj (m words) is scratch; lam_s receives lam_j; returns the boundary.
+__device__ Boundary dev_threshold(const uint32_t* __restrict__ Hq, const uint32_t* __restrict__ order,
+                                  int m, int L, int64_t n, int64_t B, uint32_t flags,
+                                  uint32_t* cntj, uint8_t* lam_s) {
     __shared__ uint32_t warp_tot[8];
     __shared__ int tstar_s;
     __shared__ uint32_t before_s;
-    const int64_t q = blockIdx.x;
+    __shared__ Boundary b_s;
     const int ncls = m * (L + 1);
-    const uint32_t* Hq = H + q * ncls;
-    int64_t B = budgets ? budgets[q] : budget;
     const uint32_t Bp = (uint32_t)(B < n ? B : n);
-    for (int j = threadIdx.x; j < m; j += 256) cntj[j] = 0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) cntj[j] = 0;
     if (threadIdx.x == 0) tstar_s = ncls;
     __syncthreads();
     uint32_t cum = 0;
@@ -141,9 +143,9 @@ __global__ void __launch_bounds__(256)
         cum += total;
     }
     const int tstar = tstar_s;
-    for (int t = threadIdx.x; t < tstar; t += 256) atomicAdd(&cntj[order[t] / (L + 1)], 1u);
+    for (int t = threadIdx.x; t < tstar; t += blockDim.x) atomicAdd(&cntj[order[t] / (L + 1)], 1u);
     __syncthreads();
-    for (int j = threadIdx.x; j < m; j += 256) lam[q * m + j] = (uint8_t)(L + 1 - cntj[j]);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) lam_s[j] = (uint8_t)(L + 1 - cntj[j]);
     if (threadIdx.x == 0) {
         const uint32_t cid = order[tstar];
         Boundary b;
@@ -151,119 +153,205 @@ __global__ void __launch_bounds__(256)
         b.l = (int32_t)(cid % (L + 1));
         b.full = (int32_t)before_s;
         b.r = (flags & NRLSH_WHOLE_BUCKETS) ? (int32_t)Hq[cid] : (int32_t)(Bp - before_s);
-        bnd[q] = b;
+        b_s = b;
     }
+    __syncthreads();
+    return b_s;
+}
+
+__global__ void __launch_bounds__(256)
+    threshold_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order, int m,
+                     int L, int64_t nq, int64_t n, int64_t budget,
+                     const int64_t* __restrict__ budgets, uint32_t flags,
+                     uint8_t* __restrict__ lam, Boundary* __restrict__ bnd) {
+    extern __shared__ uint32_t cntj[];
+    uint8_t* lam_s = (uint8_t*)(cntj + m);
+    const int64_t q = blockIdx.x;
+    const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n,
+                                     budgets ? budgets[q] : budget, flags, cntj, lam_s);
+    for (int j = threadIdx.x; j < m; j += 256) lam[q * m + j] = lam_s[j];
+    if (threadIdx.x == 0) bnd[q] = b;
 }
 
 // ------------------------------------------------------------------ select
 
-constexpr int kSelV = 4;  // consecutive positions per thread per step
+// Block phase (256 threads): ordered compaction of the probed items of one
+// query.  Only sub-datasets the walk reached (lam_j <= L, or the boundary's)
+// are swept.  Inside one, warp w owns a contiguous eighth: a counting sweep, a
+// scan over the 8 warps, and a writing sweep with ballot prefixes.  Items of
+// whole buckets go to out[0, full) in position order; boundary-bucket items go
+// to out[full, full + r), the first r of them in position (= id) order.
+template <typename C>
+__device__ void dev_select(const C* __restrict__ codes, C cq, int64_t n, int m, int L,
+                           const uint8_t* lam_s, const Boundary& b, uint32_t* __restrict__ out) {
+    __shared__ uint32_t wf[8], wb[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t of_blk = 0, ob_blk = 0;  // block-uniform running totals
+    for (int j = 0; j < m; ++j) {
+        const int lamj = lam_s[j];
+        const bool isb = j == b.j;
+        if (lamj > L && !isb) continue;                       // uniform
+        if (of_blk >= (uint32_t)b.full && ob_blk >= (uint32_t)b.r) break;
+        const int64_t s0 = seg_start(j, n, m), len = seg_start(j + 1, n, m) - s0;
+        const int64_t w0 = s0 + len * warp / 8, w1 = s0 + len * (warp + 1) / 8;
+        uint32_t cf = 0, cb = 0;
+        for (int64_t base = w0; base < w1; base += 32) {
+            const int64_t p = base + lane;
+            bool f = false, bb = false;
+            if (p < w1) {
+                const int l = L - popc_word(cq ^ codes[p]);
+                f = l >= lamj;
+                bb = isb && l == b.l;
+            }
+            cf += __popc(__ballot_sync(0xffffffffu, f));
+            cb += __popc(__ballot_sync(0xffffffffu, bb));
+        }
+        if (lane == 0) {
+            wf[warp] = cf;
+            wb[warp] = cb;
+        }
+        __syncthreads();
+        uint32_t of = of_blk, ob = ob_blk, tf = 0, tb = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) {
+                of += wf[w];
+                ob += wb[w];
+            }
+            tf += wf[w];
+            tb += wb[w];
+        }
+        __syncthreads();
+        if (cf || (cb && ob < (uint32_t)b.r)) {
+            for (int64_t base = w0; base < w1; base += 32) {
+                const int64_t p = base + lane;
+                bool f = false, bb = false;
+                if (p < w1) {
+                    const int l = L - popc_word(cq ^ codes[p]);
+                    f = l >= lamj;
+                    bb = isb && l == b.l;
+                }
+                const unsigned mf = __ballot_sync(0xffffffffu, f);
+                const unsigned mb = __ballot_sync(0xffffffffu, bb);
+                if (f) out[of + __popc(mf & lt)] = (uint32_t)p;
+                if (bb) {
+                    const uint32_t rank = ob + __popc(mb & lt);
+                    if (rank < (uint32_t)b.r) out[b.full + rank] = (uint32_t)p;
+                }
+                of += __popc(mf);
+                ob += __popc(mb);
+            }
+        }
+        of_blk += tf;
+        ob_blk += tb;
+    }
+}
 
-// Block per query, ordered compaction over all storage positions.  Items of
-// whole buckets go to cand[0, full) in position order; boundary-bucket items
-// go to cand[full, full + r), the first r of them in position (= id) order.
 template <typename C>
 __global__ void __launch_bounds__(256)
     select_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t n, int m, int L,
                   const uint8_t* __restrict__ lam, const Boundary* __restrict__ bnd,
                   uint32_t* __restrict__ cand, int64_t cap) {
     extern __shared__ uint8_t lam_s[];
-    __shared__ uint32_t warp_tot[8];
     const int64_t q = blockIdx.x;
     for (int j = threadIdx.x; j < m; j += 256) lam_s[j] = lam[q * m + j];
-    const Boundary b = bnd[q];
-    const C cq = qcodes[q];
-    uint32_t* out = cand + q * cap;
     __syncthreads();
-    uint32_t run_f = 0, run_b = 0;
-    for (int64_t base = 0; base < n; base += 256 * kSelV) {
-        const int64_t p0 = base + (int64_t)threadIdx.x * kSelV;
-        bool f[kSelV], bb[kSelV];
-        uint32_t tf = 0, tb = 0;
-        if (p0 < n) {
-            int32_t j = seg_of(p0, n, m);
-            int64_t next = seg_start(j + 1, n, m);
-#pragma unroll
-            for (int i = 0; i < kSelV; ++i) {
-                const int64_t p = p0 + i;
-                f[i] = bb[i] = false;
-                if (p < n) {
-                    while (p >= next) next = seg_start(++j + 1, n, m);
-                    const int l = L - popc_word(cq ^ codes[p]);
-                    f[i] = l >= (int)lam_s[j];
-                    bb[i] = (j == b.j) && (l == b.l);
-                }
-                tf += f[i];
-                tb += bb[i];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kSelV; ++i) f[i] = bb[i] = false;
-        }
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan(tf | (tb << 16), &total, warp_tot);
-        uint32_t ef = run_f + (ex & 0xFFFFu), eb = run_b + (ex >> 16);
-#pragma unroll
-        for (int i = 0; i < kSelV; ++i) {
-            const uint32_t p = (uint32_t)(p0 + i);
-            if (f[i]) out[ef++] = p;
-            if (bb[i]) {
-                if (eb < (uint32_t)b.r) out[b.full + eb] = p;
-                ++eb;
-            }
-        }
-        run_f += total & 0xFFFFu;
-        run_b += total >> 16;
-        if (run_f >= (uint32_t)b.full && run_b >= (uint32_t)b.r) break;  // uniform
-    }
+    dev_select(codes, qcodes[q], n, m, L, lam_s, bnd[q], cand + q * cap);
 }
 
 // ------------------------------------------------------------------ rerank
 
 constexpr int kRerankWarps = 8;
+constexpr int kRerankUnroll = 4;  // candidate rows in flight per warp
 
 template <typename T> struct RowDot;
 
 template <> struct RowDot<float> {
     // dp is a multiple of 8, rows are 16-byte aligned
-    __device__ static float dot(const float* __restrict__ row, const float* qs, int dp, int lane) {
-        const float4* r4 = (const float4*)row;
+    template <int U>
+    __device__ static void dot(const float* const* rows, const float* qs, int dp, int lane,
+                               float (&acc)[U]) {
         const float4* q4 = (const float4*)qs;
-        float acc = 0.0f;
         for (int c = lane; c < dp / 4; c += 32) {
-            const float4 x = r4[c], y = q4[c];
-            acc = fmaf(x.x, y.x, acc);
-            acc = fmaf(x.y, y.y, acc);
-            acc = fmaf(x.z, y.z, acc);
-            acc = fmaf(x.w, y.w, acc);
+            float4 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[u] = ((const float4*)rows[u])[c];
+            const float4 y = q4[c];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                acc[u] = fmaf(x[u].x, y.x, acc[u]);
+                acc[u] = fmaf(x[u].y, y.y, acc[u]);
+                acc[u] = fmaf(x[u].z, y.z, acc[u]);
+                acc[u] = fmaf(x[u].w, y.w, acc[u]);
+            }
         }
-        return acc;
     }
 };
 
 template <> struct RowDot<__nv_bfloat16> {
-    __device__ static float dot(const __nv_bfloat16* __restrict__ row, const float* qs, int dp,
-                                int lane) {
-        const uint4* r8 = (const uint4*)row;
-        float acc = 0.0f;
+    template <int U>
+    __device__ static void dot(const __nv_bfloat16* const* rows, const float* qs, int dp, int lane,
+                               float (&acc)[U]) {
         for (int c = lane; c < dp / 8; c += 32) {
-            const uint4 raw = r8[c];
-            const __nv_bfloat162* h = (const __nv_bfloat162*)&raw;
+            uint4 raw[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) raw[u] = ((const uint4*)rows[u])[c];
             const float* y = qs + c * 8;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float2 x = __bfloat1622float2(h[i]);
-                acc = fmaf(x.x, y[2 * i], acc);
-                acc = fmaf(x.y, y[2 * i + 1], acc);
+            for (int u = 0; u < U; ++u) {
+                const __nv_bfloat162* h = (const __nv_bfloat162*)&raw[u];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 x = __bfloat1622float2(h[i]);
+                    acc[u] = fmaf(x.x, y[2 * i], acc[u]);
+                    acc[u] = fmaf(x.y, y[2 * i + 1], acc[u]);
+                }
             }
         }
-        return acc;
     }
 };
 
-// grid (nq, chunks); a warp per candidate row; the score interval
-// [s - e, s + e] with e = kappa ||q|| ||x|| (FP32 summation bound, 4x margin)
-// is stored rounded outward.
+// Block phase: FP32 scores of candidates [i0, i1) of one query; a warp takes
+// kRerankUnroll rows at a time.  The score interval [s - e, s + e] with
+// e = kappa ||q|| ||x|| (FP32 summation bound, 4x margin) is stored rounded
+// outward.  qs holds q zero-padded to dp.
+template <typename T>
+__device__ void dev_rerank(const T* __restrict__ Xp, int dp, const float* qs,
+                           const uint32_t* __restrict__ candq, int64_t i0, int64_t i1,
+                           const float* __restrict__ xnorm, float qn, float kappa,
+                           float* __restrict__ loq, float* __restrict__ hiq) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int64_t i = i0 + (int64_t)warp * kRerankUnroll; i < i1;
+         i += (int64_t)nwarps * kRerankUnroll) {
+        const T* rows[kRerankUnroll];
+        uint32_t ps[kRerankUnroll];
+#pragma unroll
+        for (int u = 0; u < kRerankUnroll; ++u) {
+            ps[u] = candq[min(i + u, i1 - 1)];
+            rows[u] = Xp + (int64_t)ps[u] * dp;
+        }
+        float acc[kRerankUnroll];
+#pragma unroll
+        for (int u = 0; u < kRerankUnroll; ++u) acc[u] = 0.0f;
+        RowDot<T>::template dot<kRerankUnroll>(rows, qs, dp, lane, acc);
+#pragma unroll
+        for (int u = 0; u < kRerankUnroll; ++u) {
+            const float sc = warp_sum(acc[u]);
+            if (lane == u && i + u < i1) {
+                const float e = __fmul_ru(__fmul_ru(kappa, qn), xnorm[ps[u]]);
+                loq[i + u] = __fsub_rd(sc, e);
+                hiq[i + u] = __fadd_ru(sc, e);
+            }
+        }
+    }
+}
+
+__device__ void load_query(const float* __restrict__ Q, int64_t q, int d, int dp, float* qs) {
+    for (int c = threadIdx.x; c < dp; c += blockDim.x) qs[c] = c < d ? Q[q * d + c] : 0.0f;
+}
+
+// grid (nq, chunks): the re-rank alone, for very large budgets.
 template <typename T>
 __global__ void __launch_bounds__(kRerankWarps * 32)
     rerank_fp32_kernel(const T* __restrict__ Xp, int dp, int d, const float* __restrict__ Q,
@@ -273,23 +361,13 @@ __global__ void __launch_bounds__(kRerankWarps * 32)
                        float* __restrict__ hi) {
     extern __shared__ __align__(16) float qs[];
     const int64_t q = blockIdx.x;
-    for (int c = threadIdx.x; c < dp; c += blockDim.x) qs[c] = c < d ? Q[q * d + c] : 0.0f;
+    load_query(Q, q, d, dp, qs);
     __syncthreads();
     const Boundary b = bnd[q];
     const int64_t count = (int64_t)b.full + b.r;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i0 = (int64_t)blockIdx.y * per_block;
-    const int64_t i1 = min(count, i0 + per_block);
-    const float qn = qnorm[q];
-    for (int64_t i = i0 + warp; i < i1; i += kRerankWarps) {
-        const uint32_t p = cand[q * cap + i];
-        const float s = warp_sum(RowDot<T>::dot(Xp + (int64_t)p * dp, qs, dp, lane));
-        if (lane == 0) {
-            const float e = __fmul_ru(__fmul_ru(kappa, qn), xnorm[p]);
-            lo[q * cap + i] = __fsub_rd(s, e);
-            hi[q * cap + i] = __fadd_ru(s, e);
-        }
-    }
+    dev_rerank(Xp, dp, qs, cand + q * cap, i0, min(count, i0 + per_block), xnorm, qnorm[q], kappa,
+               lo + q * cap, hi + q * cap);
 }
 
 // ------------------------------------------------------------------- top-k
@@ -307,37 +385,61 @@ __device__ __forceinline__ bool better(double s, int64_t id, double s2, int64_t 
     return s > s2 || (s == s2 && id < id2);
 }
 
-// Block per query.  tau = k-th largest lower bound (MSD radix select on the
-// order-preserving integer image of the floats).  Every candidate whose upper
-// bound reaches tau is a contender; any true top-k member is one, because k
-// candidates have FP64 scores >= their lower bounds >= tau.  Contenders are
-// rescored in FP64 in the fixed order and the top k by (score desc, id asc)
-// are taken by k rounds of a block arg-max.
+// Find the digit holding the rem-th largest key: bins are scanned from 255
+// down; warp 0 sums 8 bins per lane, scans the lanes, and the crossing lane
+// walks its 8 bins.  Writes the digit and the rank left inside it.
+__device__ void select_digit(const uint32_t* hist, int rem, int* dg_out, int* rem_out) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    uint32_t part = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) part += hist[255 - (lane * 8 + i)];
+    uint32_t incl = part;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t excl = incl - part;
+    if (excl < (uint32_t)rem && incl >= (uint32_t)rem) {
+        int r = rem - (int)excl;
+        for (int i = 0; i < 8; ++i) {
+            const int dg = 255 - (lane * 8 + i);
+            const int c = (int)hist[dg];
+            if (c >= r) {
+                *dg_out = dg;
+                *rem_out = r;
+                break;
+            }
+            r -= c;
+        }
+    }
+}
+
+constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
+
+// Block phase (256 threads), one query.  tau = k-th largest lower bound (MSD
+// radix select on the order-preserving integer image of the floats).  Every
+// candidate whose upper bound reaches tau is a contender; any true top-k member
+// is one, because k candidates have FP64 scores >= their lower bounds >= tau.
+// Contenders are rescored in FP64 in the fixed order (rows staged in shared
+// memory) and the top k by (score desc, id asc) are taken by k rounds of a block
+// arg-max.  qs holds the query (fp32 values, exact in FP64).
 template <typename T>
-__global__ void __launch_bounds__(256)
-    topk_kernel(const float* __restrict__ lo, const float* __restrict__ hi,
-                const uint32_t* __restrict__ cand, int64_t cap, const Boundary* __restrict__ bnd,
-                int k, const int32_t* __restrict__ ks, const T* __restrict__ Xp, int dp, int d,
-                const float* __restrict__ Q, const uint32_t* __restrict__ perm,
-                uint32_t* __restrict__ cont, double* __restrict__ cont_s,
-                int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int out_ld) {
+__device__ void dev_topk(const float* __restrict__ loq, const float* __restrict__ hiq,
+                         const uint32_t* __restrict__ candq, int64_t count, int kq,
+                         const T* __restrict__ Xp, int dp, int d, const float* qs,
+                         const uint32_t* __restrict__ perm, uint32_t* __restrict__ contq,
+                         double* __restrict__ contsq, int64_t* __restrict__ ids_out,
+                         float* __restrict__ sc_out) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t prefix_s, mask_s;
-    __shared__ int rem_s;
+    __shared__ int rem_s, dg_s;
     __shared__ uint32_t nc_s;
     __shared__ double best_s[8];
     __shared__ int64_t bid_s[8];
     __shared__ int bc_s[8];
-    const int64_t q = blockIdx.x;
+    __shared__ __align__(16) float rows_s[kRescoreSmem / sizeof(float)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int kq = ks ? ks[q] : k;
-    const Boundary b = bnd[q];
-    const int64_t count = (int64_t)b.full + b.r;
-    const float* loq = lo + q * cap;
-    const float* hiq = hi + q * cap;
-    const uint32_t* candq = cand + q * cap;
-    uint32_t* contq = cont + q * cap;
-    double* contsq = cont_s + q * cap;
 
     float tau = -FLT_MAX;
     if (count > kq) {
@@ -350,23 +452,17 @@ __global__ void __launch_bounds__(256)
             hist[threadIdx.x] = 0;
             __syncthreads();
             const uint32_t prefix = prefix_s, mask = mask_s;
+            const int rem = rem_s;
             for (int64_t i = threadIdx.x; i < count; i += 256) {
                 const uint32_t key = float_order(loq[i]);
                 if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 0xFFu], 1u);
             }
             __syncthreads();
+            select_digit(hist, rem, &dg_s, &rem_s);
+            __syncthreads();
             if (threadIdx.x == 0) {
-                int rem = rem_s;
-                for (int dg = 255; dg >= 0; --dg) {
-                    const int c = (int)hist[dg];
-                    if (c >= rem) {
-                        prefix_s = prefix | ((uint32_t)dg << shift);
-                        mask_s = mask | (0xFFu << shift);
-                        break;
-                    }
-                    rem -= c;
-                }
-                rem_s = rem;
+                prefix_s = prefix | ((uint32_t)dg_s << shift);
+                mask_s = mask | (0xFFu << shift);
             }
             __syncthreads();
         }
@@ -379,14 +475,22 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const uint32_t nc = nc_s;
-    const float* qrow = Q + q * d;
-    for (uint32_t c = threadIdx.x; c < nc; c += 256) {
-        const T* xrow = Xp + (int64_t)candq[contq[c]] * dp;
-        double acc = 0.0;
-        for (int kk = 0; kk < d; ++kk) acc = fma((double)to_f32(xrow[kk]), (double)qrow[kk], acc);
-        contsq[c] = acc;
+    const int rb = max(1, min(256, kRescoreSmem / (int)(sizeof(float) * dp)));
+    for (uint32_t c0 = 0; c0 < nc; c0 += rb) {
+        const int nr = (int)min((uint32_t)rb, nc - c0);
+        for (int i = threadIdx.x; i < nr * dp; i += 256) {
+            const int r = i / dp, col = i % dp;
+            rows_s[r * dp + col] = to_f32(Xp[(int64_t)candq[contq[c0 + r]] * dp + col]);
+        }
+        __syncthreads();
+        if (threadIdx.x < nr) {
+            const float* xr = rows_s + threadIdx.x * dp;
+            double acc = 0.0;
+            for (int kk = 0; kk < d; ++kk) acc = fma((double)xr[kk], (double)qs[kk], acc);
+            contsq[c0 + threadIdx.x] = acc;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int kk_out = (int)min((int64_t)kq, (int64_t)nc);
     for (int r = 0; r < kk_out; ++r) {
         double bs = -DBL_MAX;
@@ -395,10 +499,10 @@ __global__ void __launch_bounds__(256)
         for (uint32_t c = threadIdx.x; c < nc; c += 256) {
             const uint32_t ci = contq[c];
             if (ci & 0x80000000u) continue;  // taken
-            const double s = contsq[c];
+            const double sc = contsq[c];
             const int64_t id = perm[candq[ci]];
-            if (bc < 0 || better(s, id, bs, bi)) {
-                bs = s;
+            if (bc < 0 || better(sc, id, bs, bi)) {
+                bs = sc;
                 bi = id;
                 bc = (int)c;
             }
@@ -425,16 +529,68 @@ __global__ void __launch_bounds__(256)
                 if (bc_s[w] < 0) continue;
                 if (w0 < 0 || better(best_s[w], bid_s[w], best_s[w0], bid_s[w0])) w0 = w;
             }
-            out_ids[q * out_ld + r] = bid_s[w0];
-            out_scores[q * out_ld + r] = __double2float_rn(best_s[w0]);
+            ids_out[r] = bid_s[w0];
+            sc_out[r] = __double2float_rn(best_s[w0]);
             contq[bc_s[w0]] |= 0x80000000u;
         }
         __syncthreads();
     }
     for (int r = kk_out + threadIdx.x; r < kq; r += 256) {
-        out_ids[q * out_ld + r] = -1;
-        out_scores[q * out_ld + r] = -INFINITY;
+        ids_out[r] = -1;
+        sc_out[r] = -INFINITY;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    topk_kernel(const float* __restrict__ lo, const float* __restrict__ hi,
+                const uint32_t* __restrict__ cand, int64_t cap, const Boundary* __restrict__ bnd,
+                int k, const int32_t* __restrict__ ks, const T* __restrict__ Xp, int dp, int d,
+                const float* __restrict__ Q, const uint32_t* __restrict__ perm,
+                uint32_t* __restrict__ cont, double* __restrict__ cont_s,
+                int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int out_ld) {
+    extern __shared__ __align__(16) float qs[];
+    const int64_t q = blockIdx.x;
+    load_query(Q, q, d, dp, qs);
+    __syncthreads();
+    const Boundary b = bnd[q];
+    dev_topk(lo + q * cap, hi + q * cap, cand + q * cap, (int64_t)b.full + b.r, ks ? ks[q] : k, Xp,
+             dp, d, qs, perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld,
+             out_scores + q * out_ld);
+}
+
+// ----------------------------------------------------- fused probe + rerank
+
+// Block per query: the bucket walk, the ordered candidate selection, the FP32
+// re-rank and the exact top-k back to back, with the query, lam and the walk's
+// scratch in shared memory (dynamic: dp floats, m words, m bytes).
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    probe_rerank_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order, int m,
+                        int L, int64_t n, int64_t budget, const int64_t* __restrict__ budgets,
+                        uint32_t flags, const C* __restrict__ codes, const C* __restrict__ qcodes,
+                        const T* __restrict__ Xp, int dp, int d, const float* __restrict__ Q,
+                        const float* __restrict__ xnorm, const float* __restrict__ qnorm,
+                        float kappa, const uint32_t* __restrict__ perm, int k,
+                        const int32_t* __restrict__ ks, uint32_t* __restrict__ cand,
+                        float* __restrict__ lo, float* __restrict__ hi, uint32_t* __restrict__ cont,
+                        double* __restrict__ cont_s, int64_t cap, int64_t* __restrict__ out_ids,
+                        float* __restrict__ out_scores, int out_ld) {
+    extern __shared__ __align__(16) float qs[];
+    uint32_t* cntj = (uint32_t*)(qs + dp);
+    uint8_t* lam_s = (uint8_t*)(cntj + m);
+    const int64_t q = blockIdx.x;
+    load_query(Q, q, d, dp, qs);
+    const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n,
+                                     budgets ? budgets[q] : budget, flags, cntj, lam_s);
+    uint32_t* candq = cand + q * cap;
+    dev_select(codes, qcodes[q], n, m, L, lam_s, b, candq);
+    __syncthreads();
+    const int64_t count = (int64_t)b.full + b.r;
+    dev_rerank(Xp, dp, qs, candq, 0, count, xnorm, qnorm[q], kappa, lo + q * cap, hi + q * cap);
+    __syncthreads();
+    dev_topk(lo + q * cap, hi + q * cap, candq, count, ks ? ks[q] : k, Xp, dp, d, qs, perm,
+             cont + q * cap, cont_s + q * cap, out_ids + q * out_ld, out_scores + q * out_ld);
 }
 
 __global__ void cand_to_ids_kernel(const uint32_t* __restrict__ cand, int64_t cap,
@@ -463,7 +619,7 @@ cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnor
 cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, int64_t nq, int m,
                         int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st) {
     const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nq, kHistQ));
-    const size_t smem = 16384 + sizeof(uint16_t) * (size_t)(L + 1) * kHistQ;
+    const size_t smem = 16384 + 2 * sizeof(uint16_t) * (size_t)(L + 1) * kHistQ;
     if (code_bytes == 4)
         return launch("hist_u32", hist_kernel<uint32_t>, grid, dim3(kHistQ), smem, st,
                       (const uint32_t*)codes, (const uint32_t*)qcodes, nq, m, L, tiles, H);
@@ -475,8 +631,8 @@ cudaError_t launch_threshold(const uint32_t* H, const uint32_t* order, int m, in
                              int64_t n, int64_t budget, const int64_t* budgets, uint32_t flags,
                              uint8_t* lam, Boundary* bnd, cudaStream_t st) {
     return launch("threshold", threshold_kernel, dim3((unsigned)nq), dim3(256),
-                  sizeof(uint32_t) * (size_t)m, st, H, order, m, L, nq, n, budget, budgets, flags,
-                  lam, bnd);
+                  (sizeof(uint32_t) + 1) * (size_t)m, st, H, order, m, L, nq, n, budget, budgets,
+                  flags, lam, bnd);
 }
 
 cudaError_t launch_select(const void* codes, const void* qcodes, int code_bytes, int64_t n, int m,
@@ -514,13 +670,47 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
                         const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
                         const uint32_t* perm, uint32_t* cont, double* cont_s,
                         int64_t* out_ids, float* out_scores, int out_ld, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)dp;
     if (dt == NRLSH_BF16)
-        return launch("topk_bf16", topk_kernel<__nv_bfloat16>, dim3((unsigned)nq), dim3(256), 0, st,
+        return launch("topk_bf16", topk_kernel<__nv_bfloat16>, dim3((unsigned)nq), dim3(256), smem, st,
                       lo, hi, cand, cap, bnd, k, ks, (const __nv_bfloat16*)Xp, dp, d, Q, perm, cont,
                       cont_s, out_ids, out_scores, out_ld);
-    return launch("topk", topk_kernel<float>, dim3((unsigned)nq), dim3(256), 0, st, lo, hi, cand,
+    return launch("topk", topk_kernel<float>, dim3((unsigned)nq), dim3(256), smem, st, lo, hi, cand,
                   cap, bnd, k, ks, (const float*)Xp, dp, d, Q, perm, cont, cont_s, out_ids,
                   out_scores, out_ld);
+}
+
+cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
+                                int64_t nq, int64_t budget, const int64_t* budgets, uint32_t flags,
+                                const void* codes, const void* qcodes, int code_bytes,
+                                const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
+                                const float* xnorm, const float* qnorm, const uint32_t* perm, int k,
+                                const int32_t* ks, uint32_t* cand, float* lo, float* hi,
+                                uint32_t* cont, double* cont_s, int64_t cap, int64_t* out_ids,
+                                float* out_scores, int out_ld, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)dp + (sizeof(uint32_t) + 1) * (size_t)m;
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+    const dim3 grid((unsigned)nq);
+#define NRLSH_PR(T_, C_, NAME)                                                                  \
+    {                                                                                           \
+        auto kern = probe_rerank_kernel<T_, C_>;                                                \
+        if (smem > 48 * 1024) {                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                 (int)smem);                                    \
+            if (e != cudaSuccess) return e;                                                     \
+        }                                                                                       \
+        return launch(NAME, kern, grid, dim3(256), smem, st, H, order, m, L, n, budget, budgets, \
+                      flags, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q, xnorm,\
+                      qnorm, kappa, perm, k, ks, cand, lo, hi, cont, cont_s, cap, out_ids,      \
+                      out_scores, out_ld);                                                      \
+    }
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_PR(__nv_bfloat16, uint32_t, "probe_rerank_bf16")
+        NRLSH_PR(__nv_bfloat16, uint64_t, "probe_rerank_bf16")
+    }
+    if (code_bytes == 4) NRLSH_PR(float, uint32_t, "probe_rerank")
+    NRLSH_PR(float, uint64_t, "probe_rerank")
+#undef NRLSH_PR
 }
 
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
