@@ -275,8 +275,9 @@ def algorithmic(name: str, w, budget: int):
     bytes for HBM-bound kernels, flops for ALU-bound ones (per launch of one step)."""
     n, d, L, nq, k = w.n, w.d, w.L, w.nq, w.k
     cb = 4 if L <= 32 else 8
-    if name.startswith("rerank_fp32"):
-        return "alu", 2.0 * nq * budget * d
+    if name.startswith("probe_rerank") or name.startswith("rerank_fp32"):
+        # candidate rows + their ids, the lower/upper bounds, the histogram row
+        return "hbm", float(nq * (budget * (4 * d + 4 + 8) + w.m * (L + 1) * 4))
     if name.startswith("project_fp32"):
         return "hbm", float(n * d * 4 + n * cb + n * 12)
     if name.startswith("hist"):

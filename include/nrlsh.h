@@ -84,6 +84,21 @@ typedef enum nrlsh_dtype {
 #define NRLSH_MAX_BUCKETS 16384  /* m * (L + 1) */
 #define NRLSH_MAX_K 1024
 
+/* How the item projections (Eq. 4 on the Eq. 8 transform) are computed. */
+typedef enum nrlsh_projection {
+    NRLSH_PROJECT_AUTO = 0,      /* tensor cores where the device has them, else CUDA cores */
+    NRLSH_PROJECT_SIMT = 1,      /* FP32 on CUDA cores, undecided bits in FP64 */
+    NRLSH_PROJECT_TENSOR = 2     /* bf16 tcgen05 MMA with FP32 accumulation, undecided bits
+                                    in FP32 (fp32 items) and then FP64 */
+} nrlsh_projection;
+
+typedef struct nrlsh_build_options {
+    int32_t dtype;               /* nrlsh_dtype of the items */
+    float eps;                   /* 0 < eps < 1 */
+    int32_t projection;          /* nrlsh_projection */
+    void* stream;                /* cudaStream_t; NULL = legacy default stream */
+} nrlsh_build_options;
+
 typedef struct nrlsh_info {
     int64_t n;
     int32_t d;
@@ -95,7 +110,9 @@ typedef struct nrlsh_info {
     int32_t code_bytes;          /* 4 for L <= 32, 8 otherwise */
     int32_t row_stride;          /* elements per stored item row (d rounded up to 8) */
     int64_t device_bytes;        /* device memory owned by the index */
-    int64_t ambiguous_bits;      /* (item, bit) pairs the fast tier left to FP64 */
+    int64_t ambiguous_bits;      /* (item, bit) pairs the first tier left undecided */
+    int32_t projection;          /* nrlsh_projection used (SIMT or TENSOR) */
+    int32_t device_error;        /* nonzero: a bounded device wait ran out during the build */
 } nrlsh_info;
 
 /*
@@ -112,6 +129,11 @@ NRLSH_API nrlsh_status nrlsh_build(const float* items, int64_t n, int32_t d, int
 NRLSH_API nrlsh_status nrlsh_build_ex(const void* items, int64_t n, int32_t d, int32_t m,
                                       int32_t L, uint64_t seed, nrlsh_dtype dtype, float eps,
                                       void* stream, nrlsh_index** out);
+/* As nrlsh_build_ex, with the projection path chosen by opts->projection.
+ * NRLSH_PROJECT_TENSOR on a device without tcgen05 returns NRLSH_ERR_UNSUPPORTED. */
+NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d, int32_t m,
+                                        int32_t L, uint64_t seed, const nrlsh_build_options* opts,
+                                        nrlsh_index** out);
 
 /*
  * Query processing (Section 3.3 multi-probe, exact re-rank, top-k; Eq. 1).

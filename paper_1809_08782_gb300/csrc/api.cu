@@ -40,7 +40,11 @@ struct nrlsh_index {
     nrlsh::PosTile* tiles = nullptr;
     int32_t ntiles = 0;
     std::vector<nrlsh::PosTile> tiles_host;  // source of the asynchronous upload
-    unsigned* ambiguous = nullptr;  // (item, bit) pairs the FP32 tier left undecided
+    unsigned* ambiguous = nullptr;  // (item, bit) pairs the first tier left undecided
+    int projection = NRLSH_PROJECT_SIMT;
+    __nv_bfloat16* At = nullptr;     // A^T in bf16, 64 x dp (tensor-core B operand)
+    __nv_bfloat16* Xb = nullptr;     // bf16 copy of fp32 items, n x dp (tensor-core A operand)
+    int* dev_err = nullptr;          // set by bounded device waits that ran out
 };
 
 namespace nrlsh {
@@ -195,7 +199,7 @@ nrlsh_status stage_in(Scratch& sc, const void* src, size_t bytes, const void** d
 }
 
 nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int32_t L,
-                        uint64_t seed, nrlsh_dtype dtype, float eps, void* stream,
+                        uint64_t seed, nrlsh_dtype dtype, float eps, void* stream, int projection,
                         nrlsh_index** out) {
     if (!out) return arg_error("out is NULL");
     *out = nullptr;
@@ -207,6 +211,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     if ((int64_t)m * (L + 1) > NRLSH_MAX_BUCKETS) return arg_error("need m * (L + 1) <= 16384");
     if (!(eps > 0.0f && eps < 1.0f)) return arg_error("need 0 < eps < 1");
     if (dtype != NRLSH_F32 && dtype != NRLSH_BF16) return arg_error("unknown dtype");
+    if (projection < NRLSH_PROJECT_AUTO || projection > NRLSH_PROJECT_TENSOR)
+        return arg_error("unknown projection path");
     const size_t esz = dtype == NRLSH_BF16 ? 2 : 4;
     if ((int64_t)d * (int64_t)esz * n / n != (int64_t)d * (int64_t)esz) return arg_error("n*d overflows");
 
@@ -226,6 +232,13 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     ix->stream = st;
     cudaGetDevice(&ix->device);
     keep_pool_memory(ix->device);
+    const bool tc_ok = project_tc_supported(d, L);
+    if (projection == NRLSH_PROJECT_TENSOR && !tc_ok) {
+        delete ix;
+        set_error("the tensor-core projection needs an sm_100-family GPU and d <= ~1000");
+        return NRLSH_ERR_UNSUPPORTED;
+    }
+    ix->projection = projection == NRLSH_PROJECT_AUTO ? NRLSH_PROJECT_SIMT : projection;
 
     auto fail = [&](nrlsh_status s) {
         destroy(ix);
@@ -260,6 +273,12 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     B_CK(own(ix, &ix->order, ix->ncls));
     B_CK(own(ix, &ix->shat_sorted, ix->ncls));
     B_CK(own(ix, &ix->ambiguous, 1));
+    B_CK(own(ix, &ix->dev_err, 1));
+    const bool tc = ix->projection == NRLSH_PROJECT_TENSOR;
+    if (tc) {
+        B_CK(own(ix, &ix->At, (size_t)64 * ix->dp));
+        if (dtype == NRLSH_F32) B_CK(own(ix, &ix->Xb, (size_t)n * ix->dp));
+    }
 
     // histogram tiles: runs of positions inside one sub-dataset
     {
@@ -283,8 +302,12 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         uint32_t *vals, *vals_alt, *jkeys, *jkeys_alt;
         double* bucket_keys;
         char* sort_tmp;
-        unsigned long long* amb_list;
-        const size_t amb_cap = ambiguity_capacity(n, L);
+        unsigned long long *amb_list, *amb_list2 = nullptr;
+        unsigned* amb_count2 = nullptr;
+        // the bf16 pass on fp32 items leaves a few percent of the bits to the FP32 tier
+        const size_t amb_cap = (tc && dtype == NRLSH_F32) ? std::max<size_t>(4096, (size_t)n * L / 8)
+                                                          : ambiguity_capacity(n, L);
+        const size_t amb_cap2 = ambiguity_capacity(n, L);
         B_CK(sc.get(&keys, n));
         B_CK(sc.get(&keys_alt, n));
         B_CK(sc.get(&vals, n));
@@ -294,11 +317,18 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(sc.get(&bucket_keys, ix->ncls));
         B_CK(sc.get(&sort_tmp, radix_sort_temp_bytes(n)));
         B_CK(sc.get(&amb_list, amb_cap));
+        if (tc && dtype == NRLSH_F32) {
+            B_CK(sc.get(&amb_list2, amb_cap2));
+            B_CK(sc.get(&amb_count2, 1));
+            B_CU(cudaMemsetAsync(amb_count2, 0, sizeof(unsigned), st));
+        }
+        B_CU(cudaMemsetAsync(ix->dev_err, 0, sizeof(int), st));
 
         B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned), st));
         B_CU(cudaMemsetAsync(ix->U2, 0, sizeof(double) * m, st));
         // A and the tiles of its columns (Eq. 4 projections)
-        B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, d, L, ix->Lp, seed, st));
+        B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, ix->At, ix->dp, d, L, ix->Lp, seed,
+                                st));
         // Algorithm 1: rank by norm, percentile partition, U_j
         B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
         bool alt = false;
@@ -314,11 +344,33 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                              cudaMemcpyDeviceToDevice, st));
         // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
         B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, m, ix->s_id, ix->U2, ix->Xp,
-                                 ix->s_pos, ix->tau64, ix->tau32, ix->xnorm, st));
+                                 ix->Xb, ix->s_pos, ix->tau64, ix->tau32, ix->xnorm, st));
         // Eq. 4: sign random projection codes
-        B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
-                                 ix->tau64, ix->tau32, ix->xnorm, ix->codes, ix->code_bytes,
-                                 amb_list, ix->ambiguous, (unsigned)amb_cap, st));
+        if (!tc) {
+            B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
+                                     ix->tau64, ix->tau32, ix->xnorm, ix->codes, ix->code_bytes,
+                                     amb_list, ix->ambiguous, (unsigned)amb_cap, st));
+        } else {
+            const __nv_bfloat16* xb = dtype == NRLSH_F32 ? ix->Xb : (const __nv_bfloat16*)ix->Xp;
+            B_CU(launch_project_tc(xb, ix->Xp, n, d, ix->dp, L, ix->Lp, ix->At, ix->A_pad,
+                                   ix->anorm, ix->tau32, ix->tau64, ix->xnorm, dtype == NRLSH_F32,
+                                   ix->codes, ix->code_bytes, amb_list, ix->ambiguous,
+                                   (unsigned)amb_cap, ix->dev_err, st));
+            if (dtype == NRLSH_F32) {
+                B_CU(launch_resolve_fp32((const float*)ix->Xp, n, d, ix->dp, L, ix->Lp, ix->A_pad,
+                                         ix->anorm, ix->xnorm, ix->tau32, ix->tau64, amb_list,
+                                         ix->ambiguous, (unsigned)amb_cap, ix->codes,
+                                         ix->code_bytes, amb_list2, amb_count2,
+                                         (unsigned)amb_cap2, st));
+                B_CU(launch_resolve_fp64(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad,
+                                         ix->tau64, amb_list2, amb_count2, (unsigned)amb_cap2,
+                                         ix->codes, ix->code_bytes, st));
+            } else {
+                B_CU(launch_resolve_fp64(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad,
+                                         ix->tau64, amb_list, ix->ambiguous, (unsigned)amb_cap,
+                                         ix->codes, ix->code_bytes, st));
+            }
+        }
         // Eq. 12 and the sorted (U_j, l) structure
         B_CU(launch_bucket_order(ix->U2, m, L, eps, ix->shat_sorted, ix->order, bucket_keys, st));
     }
@@ -507,13 +559,21 @@ extern "C" {
 
 NRLSH_API nrlsh_status nrlsh_build(const float* items, int64_t n, int32_t d, int32_t m, int32_t L,
                                    uint64_t seed, nrlsh_index** out) {
-    return build_impl(items, n, d, m, L, seed, NRLSH_F32, 0.1f, nullptr, out);
+    return build_impl(items, n, d, m, L, seed, NRLSH_F32, 0.1f, nullptr, NRLSH_PROJECT_AUTO, out);
 }
 
 NRLSH_API nrlsh_status nrlsh_build_ex(const void* items, int64_t n, int32_t d, int32_t m,
                                       int32_t L, uint64_t seed, nrlsh_dtype dtype, float eps,
                                       void* stream, nrlsh_index** out) {
-    return build_impl(items, n, d, m, L, seed, dtype, eps, stream, out);
+    return build_impl(items, n, d, m, L, seed, dtype, eps, stream, NRLSH_PROJECT_AUTO, out);
+}
+
+NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d, int32_t m,
+                                        int32_t L, uint64_t seed, const nrlsh_build_options* opts,
+                                        nrlsh_index** out) {
+    if (!opts) return arg_error("opts is NULL");
+    return build_impl(items, n, d, m, L, seed, (nrlsh_dtype)opts->dtype, opts->eps, opts->stream,
+                      opts->projection, out);
 }
 
 NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* queries, int64_t nq,
@@ -683,6 +743,10 @@ NRLSH_API nrlsh_status nrlsh_get_info(const nrlsh_index* ix, nrlsh_info* info) {
     info->row_stride = ix->dp;
     info->device_bytes = ix->device_bytes;
     info->ambiguous_bits = (int64_t)amb;
+    int derr = 0;
+    NRLSH_CK(cudaMemcpy(&derr, ix->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    info->projection = ix->projection;
+    info->device_error = derr;
     return NRLSH_OK;
 }
 

@@ -62,9 +62,12 @@ __device__ float projection_entry(int64_t r, int64_t b, uint64_t seed) {
 
 // Block b fills column b of A ((d+1) x L) and of A_pad ((d+1) x Lp, zero for
 // b >= L) and writes anorm[b], an fp32 upper bound of ||a_{0..d-1, b}||_2.
+// Block b also writes row b of At (bf16, K-major: At[b][k] = a_{k,b}, zero for
+// k >= d), the B operand of the tensor-core projection; At may be null.
 __global__ void __launch_bounds__(256)
     projections_kernel(float* __restrict__ A, float* __restrict__ A_pad, float* __restrict__ anorm,
-                       int d, int L, int Lp, uint64_t seed) {
+                       __nv_bfloat16* __restrict__ At, int dp, int d, int L, int Lp,
+                       uint64_t seed) {
     __shared__ double part[8];
     const int b = blockIdx.x;
     double ss = 0.0;
@@ -73,7 +76,10 @@ __global__ void __launch_bounds__(256)
         if (b < L) A[(int64_t)r * L + b] = a;
         A_pad[(int64_t)r * Lp + b] = a;
         if (r < d) ss = fma((double)a, (double)a, ss);
+        if (At && r < d) At[(int64_t)b * dp + r] = __float2bfloat16_rn(a);  // exact: a is bf16
     }
+    if (At)
+        for (int r = d + threadIdx.x; r < dp; r += blockDim.x) At[(int64_t)b * dp + r] = __float2bfloat16_rn(0.0f);
     for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ss;
     __syncthreads();
@@ -87,10 +93,10 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-cudaError_t launch_projections(float* A, float* A_pad, float* anorm, int d, int L, int Lp,
-                               uint64_t seed, cudaStream_t s) {
+cudaError_t launch_projections(float* A, float* A_pad, float* anorm, __nv_bfloat16* At, int dp,
+                               int d, int L, int Lp, uint64_t seed, cudaStream_t s) {
     return launch("projections", projections_kernel, dim3((unsigned)Lp), dim3(256), 0, s, A, A_pad,
-                  anorm, d, L, Lp, seed);
+                  anorm, At, dp, d, L, Lp, seed);
 }
 
 // =====================================================================
@@ -451,15 +457,19 @@ template <typename T>
 __global__ void gather_items_kernel(const T* __restrict__ X, int64_t ld, int d, int dp,
                                     const uint32_t* __restrict__ perm, int64_t n, int m,
                                     const double* __restrict__ s_id, const double* __restrict__ U2,
-                                    T* __restrict__ Xp, double* s_pos, double* tau64, float* tau32,
-                                    float* xnorm) {
+                                    T* __restrict__ Xp, __nv_bfloat16* __restrict__ Xb,
+                                    double* s_pos, double* tau64, float* tau32, float* xnorm) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= n) return;
     const uint32_t id = perm[p];
     const T* src = X + (int64_t)id * ld;
     T* dst = Xp + p * dp;
-    for (int c = lane; c < dp; c += 32) dst[c] = c < d ? src[c] : T(0.0f);
+    for (int c = lane; c < dp; c += 32) {
+        const T v = c < d ? src[c] : T(0.0f);
+        dst[c] = v;
+        if (Xb) Xb[p * dp + c] = __float2bfloat16_rn(to_f32(v));  // the tensor-core copy
+    }
     if (lane == 0) {
         const double s = s_id[id];
         const double u2 = U2[seg_of(p, n, m)];
@@ -482,16 +492,16 @@ cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* s
 
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
                                 const uint32_t* perm, int64_t n, int m, const double* s_id,
-                                const double* U2, void* Xp, double* s_pos, double* tau64,
-                                float* tau32, float* xnorm, cudaStream_t st) {
+                                const double* U2, void* Xp, __nv_bfloat16* Xb, double* s_pos,
+                                double* tau64, float* tau32, float* xnorm, cudaStream_t st) {
     const dim3 grid((unsigned)ceil_div(n * 32, 256));
     if (dt == NRLSH_BF16)
         return launch("gather_items_bf16", gather_items_kernel<__nv_bfloat16>, grid, dim3(256), 0,
                       st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, m, s_id, U2,
-                      (__nv_bfloat16*)Xp, s_pos, tau64, tau32, xnorm);
+                      (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr, s_pos, tau64, tau32, xnorm);
     return launch("gather_items_f32", gather_items_kernel<float>, grid, dim3(256), 0, st,
-                  (const float*)X, ld, d, dp, perm, n, m, s_id, U2, (float*)Xp, s_pos, tau64, tau32,
-                  xnorm);
+                  (const float*)X, ld, d, dp, perm, n, m, s_id, U2, (float*)Xp, Xb, s_pos, tau64,
+                  tau32, xnorm);
 }
 
 // =====================================================================
@@ -661,6 +671,49 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The FP32 tier for pairs the bf16 tensor-core pass left undecided (fp32 items):
+// warp per pair, FP32 dot of the exact fp32 row in lane-strided order and a
+// tree, decided against (d+2) 2^-22 ||a|| ||x|| (any summation order) plus the
+// tail rounding; still undecided pairs move on to the FP64 list.
+template <typename C>
+__global__ void __launch_bounds__(256)
+    resolve_fp32_kernel(const float* __restrict__ X, int d, int ldx, int Lp,
+                        const float* __restrict__ A_pad, const float* __restrict__ anorm,
+                        const float* __restrict__ xnorm, const float* __restrict__ tau32,
+                        const double* __restrict__ tau64, const unsigned long long* __restrict__ list,
+                        const unsigned* __restrict__ count, unsigned cap, C* __restrict__ codes,
+                        unsigned long long* __restrict__ list2, unsigned* count2, unsigned cap2,
+                        float kappa) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned cnt = min(*count, cap);
+    for (int64_t e = warp; e < cnt; e += nwarps) {
+        const unsigned long long entry = list[e];
+        const int64_t row = (int64_t)(entry >> 6);
+        const int bit = (int)(entry & 63);
+        const float* xr = X + row * ldx;
+        float s = 0.0f;
+        for (int k = lane; k < d; k += 32) s = fmaf(xr[k], A_pad[(int64_t)k * Lp + bit], s);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float ad = A_pad[(int64_t)d * Lp + bit];
+        const float t32 = tau32[row];
+        const float v = fmaf(ad, t32, s);
+        const float bound = kappa * anorm[bit] * xnorm[row] + 0x1p-20f * fabsf(ad) * t32;
+        if (lane == 0) {
+            if (fabsf(v) * (1.0f - 0x1p-21f) > bound) {
+                if (v > 0.0f) or_bit(codes + row, bit);
+            } else {
+                const unsigned slot = atomicAdd(count2, 1u);
+                if (slot < cap2)
+                    list2[slot] = entry;
+                else if (project_bit_fp64(xr, A_pad, Lp, d, bit, true, tau64[row]))
+                    or_bit(codes + row, bit);
+            }
+        }
+    }
+}
+
 template <typename T, typename C, int BT>
 cudaError_t project_rows(const void* X, int64_t n, int d, int ldx, int L, int Lp,
                          const float* A_pad, const float* anorm, const double* tau64,
@@ -737,6 +790,43 @@ cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
     return project_dispatch<float, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
                                              codes, amb_list, amb_count, amb_cap, st,
                                              "project_fp32");
+}
+
+cudaError_t launch_resolve_fp32(const float* X, int64_t n, int d, int ldx, int L, int Lp,
+                                const float* A_pad, const float* anorm, const float* xnorm,
+                                const float* tau32, const double* tau64,
+                                const unsigned long long* list, const unsigned* count,
+                                unsigned cap, void* codes, int code_bytes,
+                                unsigned long long* list2, unsigned* count2, unsigned cap2,
+                                cudaStream_t st) {
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 32, 32), 8),
+                                                      16 * 152);
+    if (code_bytes == 4)
+        return launch("resolve_fp32", resolve_fp32_kernel<uint32_t>, dim3(grid), dim3(256), 0, st, X,
+                      d, ldx, Lp, A_pad, anorm, xnorm, tau32, tau64, list, count, cap,
+                      (uint32_t*)codes, list2, count2, cap2, kappa);
+    return launch("resolve_fp32", resolve_fp32_kernel<uint64_t>, dim3(grid), dim3(256), 0, st, X, d,
+                  ldx, Lp, A_pad, anorm, xnorm, tau32, tau64, list, count, cap, (uint64_t*)codes,
+                  list2, count2, cap2, kappa);
+}
+
+cudaError_t launch_resolve_fp64(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                int Lp, const float* A_pad, const double* tau64,
+                                const unsigned long long* list, const unsigned* count,
+                                unsigned cap, void* codes, int code_bytes, cudaStream_t st) {
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 256, 32), 8),
+                                                      8 * 152);
+#define NRLSH_R64(T_, C_)                                                                    \
+    return launch("resolve_fp64", resolve_kernel<T_, C_>, dim3(grid), dim3(256), 0, st,       \
+                  (const T_*)X, d, ldx, Lp, A_pad, tau64, list, count, cap, (C_*)codes);
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_R64(__nv_bfloat16, uint32_t)
+        NRLSH_R64(__nv_bfloat16, uint64_t)
+    }
+    if (code_bytes == 4) NRLSH_R64(float, uint32_t)
+    NRLSH_R64(float, uint64_t)
+#undef NRLSH_R64
 }
 
 size_t ambiguity_capacity(int64_t rows, int L) {
@@ -879,23 +969,32 @@ __device__ __forceinline__ unsigned long long double_order(double v) {
 
 constexpr int kBucketThreads = 256;
 
-// One launch builds the probing order.  Every block computes the L+1 values c_l
-// (one thread each) and all m(L+1) keys s_hat = fl(U_j c_l) in shared memory;
-// each thread then ranks its own bucket by counting the buckets with a greater
-// key (s_hat, l, j), compared as integers.  order[rank] = j (L+1) + l.
+// One launch builds the probing order.  Every block computes, in shared memory,
+// the L+1 values c_l (thread 32 w + i for l = 8 w + i: one chain per warp lane
+// group, spread over the warps), U_j = sqrt(U_j^2), and all m(L+1) keys
+// s_hat = fl(U_j c_l); each thread then ranks its own bucket by counting the
+// buckets with a greater key (s_hat, l, j), compared as integers.
+// order[rank] = j (L+1) + l.
 __global__ void __launch_bounds__(kBucketThreads)
     bucket_order_kernel(const double* __restrict__ U2, int m, int L, float eps,
                         double* __restrict__ shat_sorted, uint32_t* __restrict__ order) {
-    extern __shared__ unsigned long long keys[];     // ncls order keys
-    uint32_t* tie = (uint32_t*)(keys + m * (L + 1));  // ncls tie keys l 2^16 + j
-    double* cl = (double*)(tie + ((m * (L + 1) + 1) & ~1));  // L+1 cosines
+    extern __shared__ unsigned long long keys[];          // ncls order keys
     const int ncls = m * (L + 1);
-    for (int l = threadIdx.x; l <= L; l += blockDim.x) cl[l] = cos_class(L, l, (double)eps);
+    uint32_t* tie = (uint32_t*)(keys + ncls);             // ncls tie keys l 2^16 + j
+    double* cl = (double*)(tie + ((ncls + 1) & ~1));      // L+1 cosines
+    double* Uj = cl + (L + 1);                            // m norms
+    // cosines: lanes 0..7 of each warp, so the FP64 chains run on all SM partitions
+    {
+        const int w = threadIdx.x >> 5, i = threadIdx.x & 31;
+        const int nw = blockDim.x >> 5;
+        if (i < 8)
+            for (int l = w * 8 + i; l <= L; l += nw * 8) cl[l] = cos_class(L, l, (double)eps);
+    }
+    for (int j = threadIdx.x; j < m; j += blockDim.x) Uj[j] = sqrt(U2[j]);
     __syncthreads();
     for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
         const int j = c / (L + 1), l = c % (L + 1);
-        const double sh = __dadd_rn(__dmul_rn(sqrt(U2[j]), cl[l]), 0.0);  // -0 -> +0
-        keys[c] = double_order(sh);
+        keys[c] = double_order(__dadd_rn(__dmul_rn(Uj[j], cl[l]), 0.0));  // -0 -> +0
         tie[c] = ((uint32_t)l << 16) | (uint32_t)j;
     }
     __syncthreads();
@@ -903,14 +1002,13 @@ __global__ void __launch_bounds__(kBucketThreads)
     if (c >= ncls) return;
     const unsigned long long k0 = keys[c];
     const uint32_t t0 = tie[c];
-    const int l0 = c % (L + 1), j0 = c / (L + 1);
     int rank = 0;
     for (int c1 = 0; c1 < ncls; ++c1) {
         const unsigned long long k1 = keys[c1];
         rank += (k1 > k0) || (k1 == k0 && tie[c1] > t0);
     }
     order[rank] = (uint32_t)c;
-    shat_sorted[rank] = __dadd_rn(__dmul_rn(sqrt(U2[j0]), cl[l0]), 0.0);
+    shat_sorted[rank] = __dadd_rn(__dmul_rn(Uj[c / (L + 1)], cl[c % (L + 1)]), 0.0);
 }
 
 }  // namespace
@@ -919,7 +1017,7 @@ cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, doubl
                                 uint32_t* order, double* /*unused*/, cudaStream_t st) {
     const int ncls = m * (L + 1);
     const size_t smem = sizeof(unsigned long long) * ncls + sizeof(uint32_t) * ((ncls + 1) & ~1) +
-                        sizeof(double) * (L + 1);
+                        sizeof(double) * (L + 1 + m);
     cudaError_t e = cudaFuncSetAttribute(bucket_order_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

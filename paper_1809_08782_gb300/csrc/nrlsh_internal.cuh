@@ -85,8 +85,8 @@ struct PosTile {
 // All return cudaError_t of the last launch; pointers are device pointers.
 
 // A ((d+1) x L), its zero-padded copy A_pad ((d+1) x Lp) and column-norm bounds anorm.
-cudaError_t launch_projections(float* A, float* A_pad, float* anorm, int d, int L, int Lp,
-                               uint64_t seed, cudaStream_t s);
+cudaError_t launch_projections(float* A, float* A_pad, float* anorm, __nv_bfloat16* At, int dp,
+                               int d, int L, int Lp, uint64_t seed, cudaStream_t s);
 // s_x in FP64; with keys/vals non-null also the partition's sort keys and ids.
 cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64_t ld, double* s,
                           uint64_t* keys, uint32_t* vals, cudaStream_t st);
@@ -104,8 +104,8 @@ cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* s
                                   uint32_t* jkeys, uint32_t* jvals, cudaStream_t st);
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
                                 const uint32_t* perm, int64_t n, int m, const double* s_id,
-                                const double* U2, void* Xp, double* s_pos, double* tau64,
-                                float* tau32, float* xnorm, cudaStream_t st);
+                                const double* U2, void* Xp, __nv_bfloat16* Xb, double* s_pos,
+                                double* tau64, float* tau32, float* xnorm, cudaStream_t st);
 // Sign random projection of rows of X (row stride ldx, stored dtype) with the FP32
 // fast tier; undecided (row, bit) pairs go through amb_list (capacity amb_cap,
 // count in *amb_count, which must start at 0) to the FP64 resolve kernel.
@@ -117,6 +117,27 @@ cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
                                 unsigned* amb_count, unsigned amb_cap, cudaStream_t st);
 // Entries of the ambiguity list to reserve for `rows` rows of L bits.
 size_t ambiguity_capacity(int64_t rows, int L);
+// FP32 tier (fp32 items after the bf16 tensor-core pass) and FP64 tier on a list
+// of undecided (row, bit) pairs; decided bits are OR-ed into the codes.
+cudaError_t launch_resolve_fp32(const float* X, int64_t n, int d, int ldx, int L, int Lp,
+                                const float* A_pad, const float* anorm, const float* xnorm,
+                                const float* tau32, const double* tau64,
+                                const unsigned long long* list, const unsigned* count,
+                                unsigned cap, void* codes, int code_bytes,
+                                unsigned long long* list2, unsigned* count2, unsigned cap2,
+                                cudaStream_t st);
+cudaError_t launch_resolve_fp64(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                int Lp, const float* A_pad, const double* tau64,
+                                const unsigned long long* list, const unsigned* count,
+                                unsigned cap, void* codes, int code_bytes, cudaStream_t st);
+// tcgen05 projection of the items (bf16 copy Xb, n x dp; At = A^T bf16, 64 x dp).
+bool project_tc_supported(int d, int L);
+cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const void* X_exact, int64_t n, int d, int dp,
+                              int L, int Lp, const __nv_bfloat16* At, const float* A_pad,
+                              const float* anorm, const float* tau32, const double* tau64,
+                              const float* xnorm, bool fp32_items, void* codes, int code_bytes,
+                              unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
+                              int* err, cudaStream_t st);
 cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, double* shat_sorted,
                                 uint32_t* order, double* scratch_keys, cudaStream_t st);
 

@@ -1,0 +1,454 @@
+// Sign random projection of the items on 5th-generation tensor cores
+// (Eq. 4 applied to the SIMPLE-LSH transform of Eq. 8): V = X~ A with X~ the
+// bfloat16 items (n x d, row stride dp) and A the bfloat16-valued projections,
+// accumulated in FP32 in tensor memory, then + a_d tau and the sign.
+//
+// Persistent warp-specialised CTAs (192 threads):
+//   warp 0   one thread issues TMA loads: all of A^T once (K-major, 128-byte
+//            swizzle), then a 4-stage ring of 128-item x 64-K tiles of X~;
+//   warp 1   allocates 128 TMEM columns (two accumulators of up to 64 columns)
+//            and one thread issues tcgen05.mma (M = 128, N = 16..64, K = 16);
+//   warps 2-5 read the accumulator rows (warp w reads TMEM lanes 32 (w % 4)..),
+//            add the tail term, decide each bit against a proven bound and
+//            write the code word; undecided (item, bit) pairs go to a list that
+//            the FP32 and FP64 tiers resolve.
+// Every mbarrier wait is bounded; on a timeout the kernel records an error in
+// *err, stops issuing work, waits (bounded) for its own copies, frees TMEM and
+// returns.
+#include "nrlsh_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace nrlsh {
+
+namespace {
+
+constexpr int kTcM = 128;            // items per tile (MMA M)
+constexpr int kTcKC = 64;            // K elements per stage: 128 bytes of bf16
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 192;
+constexpr uint32_t kTmemCols = 128;  // two accumulators of up to 64 fp32 columns
+constexpr uint32_t kXStageBytes = kTcM * kTcKC * 2;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+// D[tmem] (+)= A[smem] B[smem]^T, bf16 inputs, fp32 accumulation.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the mbarrier once all tcgen05.mma issued so far by this thread complete.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 32 TMEM lanes x 16 columns of 32 bits: thread t receives lane (base lane + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile laid out by TMA with
+// the 128-byte swizzle: rows of 128 bytes, 8-row groups 1,024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(const void* base) {
+    const uint32_t addr = smem_u32(base);
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: bf16 A and B (both K-major), fp32 D, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+struct TcSmem {
+    int nkc, N;
+    __device__ uint8_t* a_tile(uint8_t* base, int c) const { return base + (size_t)c * N * 128; }
+    __device__ uint8_t* x_stage(uint8_t* base, int s) const {
+        return base + (size_t)nkc * N * 128 + (size_t)s * kXStageBytes;
+    }
+    __device__ uint64_t* bars(uint8_t* base) const {
+        return (uint64_t*)(base + (size_t)nkc * N * 128 + (size_t)kTcStages * kXStageBytes);
+    }
+};
+
+template <typename C>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    project_tc_kernel(const __grid_constant__ CUtensorMap map_x,
+                      const __grid_constant__ CUtensorMap map_a, int64_t n, int nkc, int L, int N,
+                      int Lp, int d, const float* __restrict__ A_pad,
+                      const float* __restrict__ anorm, const float* __restrict__ tau32,
+                      const float* __restrict__ xnorm, float kappa_tc, float round_x,
+                      const void* __restrict__ X_exact, int fp32_items, int ldx,
+                      const double* __restrict__ tau64, C* __restrict__ codes,
+                      unsigned long long* __restrict__ amb_list, unsigned* amb_count,
+                      unsigned amb_cap, int* err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const TcSmem L_{nkc, N};
+    uint64_t* bars = L_.bars(base);
+    uint64_t* full = bars;                       // kTcStages
+    uint64_t* empty = bars + kTcStages;          // kTcStages
+    uint64_t* acc_full = bars + 2 * kTcStages;   // 2
+    uint64_t* acc_empty = acc_full + 2;          // 2
+    uint64_t* a_bar = acc_empty + 2;             // 1
+    uint64_t* drain = a_bar + 1;                 // 1: all MMAs of this CTA done
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_s = (volatile int*)(tmem_slot + 1);
+    float* s_anorm = (float*)(tmem_slot + 4);    // 64
+    float* s_ad = s_anorm + 64;                  // 64
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = ceil_div(n, kTcM);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        mbar_init(a_bar, 1);
+        mbar_init(drain, 1);
+        *abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (threadIdx.x < 64) {
+        const int b = threadIdx.x;
+        s_anorm[b] = b < L ? anorm[b] : 0.0f;
+        s_ad[b] = b < L ? A_pad[(int64_t)d * Lp + b] : 0.0f;
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer
+            mbar_expect_tx(a_bar, (uint32_t)(nkc * N * 128));
+            for (int c = 0; c < nkc; ++c) tma_load_2d(L_.a_tile(base, c), &map_a, a_bar, c * kTcKC, 0);
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[kTcStages] = {0, 0, 0, 0};
+            uint32_t issued_par[kTcStages] = {0, 0, 0, 0};
+            for (int64_t t = blockIdx.x; t < ntiles && !*abort_s; t += gridDim.x) {
+                for (int c = 0; c < nkc; ++c) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1)) {
+                        atomicExch(err, 1);
+                        *abort_s = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&full[stage], kXStageBytes);
+                    tma_load_2d(L_.x_stage(base, stage), &map_x, &full[stage], c * kTcKC,
+                                (int)(t * kTcM));
+                    issued[stage] = 1;
+                    issued_par[stage] = phase;
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            if (*abort_s) {
+                // let every copy in flight land before the CTA's memory goes away
+                mbar_wait(a_bar, 0);
+                for (int s = 0; s < kTcStages; ++s)
+                    if (issued[s]) mbar_wait(&full[s], issued_par[s]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            const uint32_t idesc = umma_idesc(kTcM, N);
+            bool ok = mbar_wait(a_bar, 0);
+            int stage = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            int buf = 0;
+            for (int64_t t = blockIdx.x; ok && t < ntiles && !*abort_s; t += gridDim.x) {
+                if (!mbar_wait(&acc_empty[buf], acc_phase ^ 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)buf * 64;
+                for (int c = 0; c < nkc; ++c) {
+                    if (!mbar_wait(&full[stage], phase)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t adesc = sw128_desc(L_.x_stage(base, stage));
+                    const uint64_t bdesc = sw128_desc(L_.a_tile(base, c));
+#pragma unroll
+                    for (int k = 0; k < kTcKC / 16; ++k)  // 32 bytes of K per MMA
+                        umma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc, (c | k) != 0);
+                    umma_commit(&empty[stage]);
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                umma_commit(&acc_full[buf]);
+                if (++buf == 2) {
+                    buf = 0;
+                    acc_phase ^= 1;
+                }
+            }
+            if (!ok) {
+                atomicExch(err, 2);
+                *abort_s = 1;
+            }
+            // every MMA this thread issued has finished before TMEM is freed
+            umma_commit(drain);
+            mbar_wait(drain, 0);
+        }
+    } else {
+        // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) + lane
+        const int sub = warp & 3;
+        int buf = 0;
+        uint32_t acc_phase = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if (*abort_s || !mbar_wait(&acc_full[buf], acc_phase)) {
+                atomicExch(err, 3);
+                *abort_s = 1;
+                break;
+            }
+            tc_fence_after();
+            const int64_t row = t * kTcM + 32 * sub + lane;
+            const bool valid = row < n;
+            const float xn = valid ? xnorm[row] : 0.0f;
+            const float t32 = valid ? tau32[row] : 0.0f;
+            unsigned long long word = 0;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem_base + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 64 + c0), r);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int bit = c0 + i;
+                    if (!valid || bit >= L) continue;
+                    const float ad = s_ad[bit];
+                    const float v = fmaf(ad, t32, __uint_as_float(r[i]));
+                    // accumulation bound (kappa_tc) plus, for fp32 items, the bf16
+                    // rounding of x (round_x); Cauchy-Schwarz for sum |a_k x_k|
+                    const float bound = (kappa_tc + round_x) * s_anorm[bit] * xn +
+                                        0x1p-20f * fabsf(ad) * t32;
+                    if (fabsf(v) * (1.0f - 0x1p-21f) > bound) {
+                        if (v > 0.0f) word |= 1ull << bit;
+                    } else {
+                        const unsigned slot = atomicAdd(amb_count, 1u);
+                        if (slot < amb_cap) {
+                            amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
+                        } else {
+                            // list full: the canonical FP64 evaluation, here
+                            double acc = 0.0;
+                            for (int k = 0; k < d; ++k) {
+                                const double xk =
+                                    fp32_items ? (double)((const float*)X_exact)[row * ldx + k]
+                                               : (double)__bfloat162float(
+                                                     ((const __nv_bfloat16*)X_exact)[row * ldx + k]);
+                                acc = fma(xk, (double)A_pad[(int64_t)k * Lp + bit], acc);
+                            }
+                            acc = __dadd_rn(acc, __dmul_rn((double)ad, tau64[row]));
+                            if (acc >= 0.0) word |= 1ull << bit;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
+            if (valid) codes[row] = (C)word;
+            if (++buf == 2) {
+                buf = 0;
+                acc_phase ^= 1;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D bf16 tensor map: rows of `inner` elements (row stride `stride_elems`),
+// `outer` rows; box of 64 x box_rows with the 128-byte swizzle; zeros outside.
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer,
+              uint64_t stride_elems, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {stride_elems * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcKC, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t project_tc_smem_bytes(int d, int N) {
+    const int nkc = (int)ceil_div(d, kTcKC);
+    return 1024 + (size_t)nkc * N * 128 + (size_t)kTcStages * kXStageBytes + 256 + 2 * 64 * 4;
+}
+
+bool project_tc_supported(int d, int L) {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaGetLastError();
+    if (major != 10) return false;
+    const int N = L <= 16 ? 16 : L <= 32 ? 32 : L <= 48 ? 48 : 64;
+    return project_tc_smem_bytes(d, N) <= 200 * 1024 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const void* X_exact, int64_t n, int d, int dp,
+                              int L, int Lp, const __nv_bfloat16* At, const float* A_pad,
+                              const float* anorm, const float* tau32, const double* tau64,
+                              const float* xnorm, bool fp32_items, void* codes, int code_bytes,
+                              unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
+                              int* err, cudaStream_t st) {
+    const int N = L <= 16 ? 16 : L <= 32 ? 32 : L <= 48 ? 48 : 64;
+    const int nkc = (int)ceil_div(d, kTcKC);
+    CUtensorMap map_x, map_a;
+    if (!make_map(&map_x, Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
+        !make_map(&map_a, At, (uint64_t)d, (uint64_t)N, (uint64_t)dp, (uint32_t)N))
+        return cudaErrorNotSupported;
+    const size_t smem = project_tc_smem_bytes(d, N);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = ceil_div(n, kTcM);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)sms);
+    // accumulation bound: 16x the first-order FP32 bound (the adder's rounding mode
+    // inside the tensor core is not assumed); bf16 rounding of fp32 items: 2^-8 |x|
+    const float kappa_tc = (float)(nkc * kTcKC + 8) * 0x1p-20f;
+    const float round_x = fp32_items ? 0x1p-8f * (1.0f + 0x1p-7f) : 0.0f;
+#define NRLSH_TC(C_)                                                                         \
+    {                                                                                        \
+        auto kern = project_tc_kernel<C_>;                                                   \
+        cudaError_t e =                                                                      \
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                      \
+        return launch("project_tc", kern, dim3(grid), dim3(kTcThreads), smem, st, map_x, map_a, \
+                      n, nkc, L, N, Lp, d, A_pad, anorm, tau32, xnorm, kappa_tc, round_x,    \
+                      X_exact, fp32_items ? 1 : 0, dp, tau64, (C_*)codes, amb_list, amb_count, \
+                      amb_cap, err);                                                         \
+    }
+    if (code_bytes == 4) NRLSH_TC(uint32_t)
+    NRLSH_TC(uint64_t)
+#undef NRLSH_TC
+}
+
+}  // namespace nrlsh

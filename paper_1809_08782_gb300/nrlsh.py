@@ -32,6 +32,7 @@ _I32, _I64, _U32, _U64, _F32 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
 SIGNATURES = {
     "nrlsh_build": (_I32, [_P, _I64, _I32, _I32, _I32, _U64, _P]),
     "nrlsh_build_ex": (_I32, [_P, _I64, _I32, _I32, _I32, _U64, _I32, _F32, _P, _P]),
+    "nrlsh_build_opts": (_I32, [_P, _I64, _I32, _I32, _I32, _U64, _P, _P]),
     "nrlsh_query": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P]),
     "nrlsh_query_ex": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _P, _P, _P]),
     "nrlsh_query_noalloc": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P]),
@@ -54,7 +55,17 @@ SIGNATURES = {
 class NrlshInfo(ctypes.Structure):
     _fields_ = [("n", _I64), ("d", _I32), ("m", _I32), ("L", _I32), ("dtype", _I32),
                 ("eps", _F32), ("seed", _U64), ("code_bytes", _I32), ("row_stride", _I32),
-                ("device_bytes", _I64), ("ambiguous_bits", _I64)]
+                ("device_bytes", _I64), ("ambiguous_bits", _I64), ("projection", _I32),
+                ("device_error", _I32)]
+
+
+class NrlshBuildOptions(ctypes.Structure):
+    _fields_ = [("dtype", _I32), ("eps", _F32), ("projection", _I32), ("stream", _P)]
+
+
+NRLSH_PROJECT_AUTO = 0
+NRLSH_PROJECT_SIMT = 1
+NRLSH_PROJECT_TENSOR = 2
 
 
 class NrlshError(RuntimeError):
@@ -136,16 +147,23 @@ def _items_dtype(items: torch.Tensor) -> int:
 
 
 def nrlsh_build_ex(items: torch.Tensor, m: int, L: int, seed: int, eps: float = 0.1,
-                   stream=None) -> Index:
-    """Index building (Algorithm 1).  items: (n, d) float32 or bfloat16, row-major."""
+                   stream=None, projection: Optional[int] = None) -> Index:
+    """Index building (Algorithm 1).  items: (n, d) float32 or bfloat16, row-major.
+    projection selects the projection path (nrlsh_build_opts) when given."""
     lib = load()
     if items.dim() != 2:
         raise ValueError("items must be 2-D (n, d)")
     items = items.contiguous()
     n, d = items.shape
     out = ctypes.c_void_p()
-    _check(lib.nrlsh_build_ex(_ptr(items), n, d, m, L, seed, _items_dtype(items), eps,
-                              _stream(items, stream), ctypes.byref(out)))
+    if projection is None:
+        _check(lib.nrlsh_build_ex(_ptr(items), n, d, m, L, seed, _items_dtype(items), eps,
+                                  _stream(items, stream), ctypes.byref(out)))
+    else:
+        st = _stream(items, stream)
+        opts = NrlshBuildOptions(_items_dtype(items), eps, projection, st)
+        _check(lib.nrlsh_build_opts(_ptr(items), n, d, m, L, seed, ctypes.byref(opts),
+                                    ctypes.byref(out)))
     return Index(out, n, d, m, L, items.device)
 
 

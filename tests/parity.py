@@ -19,16 +19,22 @@ def to_dev_items(items: np.ndarray, dtype: str):
     return torch.from_numpy(np.ascontiguousarray(items, dtype=np.float32)).to(DEV)
 
 
-def build_pair(items: np.ndarray, dtype: str, m: int, L: int, seed: int, eps: float):
-    """(library index, oracle index) on the same inputs."""
+def build_pair(items: np.ndarray, dtype: str, m: int, L: int, seed: int, eps: float,
+               projection=None):
+    """(library index, oracle index) on the same inputs; projection forces the
+    projection path (N.NRLSH_PROJECT_SIMT / N.NRLSH_PROJECT_TENSOR)."""
     from paper_1809_08782_gb300 import workloads as W
     eps = f32(eps)
-    lib = N.nrlsh_build_ex(to_dev_items(items, dtype), m, L, seed, eps=eps)
+    lib = N.nrlsh_build_ex(to_dev_items(items, dtype), m, L, seed, eps=eps, projection=projection)
     ref = O.build(W.items_to_f64(items, dtype), m, L, seed, eps=eps)
     return lib, ref
 
 
-def check_index(lib, ref):
+def check_index(lib, ref, projection=None):
+    info = N.nrlsh_get_info(lib)
+    assert info["device_error"] == 0, "a bounded device wait ran out"
+    if projection is not None:
+        assert info["projection"] == projection
     A = N.nrlsh_get_projections(lib).numpy().astype(np.float64)
     assert np.array_equal(A, ref.A), "projection matrix differs"
     sub, U2, s = N.nrlsh_get_partition(lib)

@@ -36,32 +36,37 @@ def rand_q(nq, d, seed):
 
 # ------------------------------------------------------------ presets
 
-def test_small_preset_full():
+SIMT, TENSOR = 1, 2
+
+
+@pytest.mark.parametrize("proj", [SIMT, TENSOR])
+def test_small_preset_full(proj):
     """n=10,000, d=64 fp32, m=8, L=16, 1,000 queries, B=1,000, top-10."""
     w = W.make_workload("small-n10k-d64")
-    lib, ref = build_pair(w.items, w.dtype, w.m, w.L, w.index_seed, 0.1)
-    check_index(lib, ref)
+    lib, ref = build_pair(w.items, w.dtype, w.m, w.L, w.index_seed, 0.1, projection=proj)
+    check_index(lib, ref, proj)
     check_queries(lib, ref, w.queries[:300], w.k, w.budget)
     check_queries(lib, ref, w.queries, w.k, w.budget, check_hist=False)
 
 
-@pytest.mark.parametrize("frac", [0.01, 0.03, 0.20])
-def test_netflix_preset(frac):
+@pytest.mark.parametrize("frac,proj", [(0.01, SIMT), (0.03, TENSOR), (0.20, SIMT)])
+def test_netflix_preset(frac, proj):
     """n=17,770, d=300 fp32, m=32, L=32; budget swept 1%..20% of n."""
     w = W.make_workload("netflix-n17770-d300", nq=200)
-    lib, ref = build_pair(w.items, w.dtype, w.m, w.L, w.index_seed, 0.3)
-    check_index(lib, ref)
+    lib, ref = build_pair(w.items, w.dtype, w.m, w.L, w.index_seed, 0.3, projection=proj)
+    check_index(lib, ref, proj)
     check_queries(lib, ref, w.queries, w.k, int(round(frac * w.n)))
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_yahoo_preset(dtype):
+@pytest.mark.parametrize("proj", [SIMT, TENSOR])
+def test_yahoo_preset(dtype, proj):
     """n=136,736, d=300, m=32, L=64, stored fp32 and bf16; a 64-query subset."""
     w = W.make_workload("yahoo-n136736-d300", nq=64, with_data=False)
     items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, dtype)
     Q = W.gen_queries(w.nq, w.d, w.query_seed)
-    lib, ref = build_pair(items, dtype, w.m, w.L, w.index_seed, 0.1)
-    check_index(lib, ref)
+    lib, ref = build_pair(items, dtype, w.m, w.L, w.index_seed, 0.1, projection=proj)
+    check_index(lib, ref, proj)
     check_queries(lib, ref, Q, 10, w.budget)
 
 
@@ -72,23 +77,25 @@ def test_yahoo_preset(dtype):
     (4099, 8, 64, 32), (5000, 130, 1, 24),
 ])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_ragged_shapes(n, d, m, L, dtype):
+@pytest.mark.parametrize("proj", [SIMT, TENSOR])
+def test_ragged_shapes(n, d, m, L, dtype, proj):
     items = rand_items(n, d, n + d + m + L, dtype=dtype)
-    lib, ref = build_pair(items, dtype, m, L, seed=5, eps=0.2)
-    check_index(lib, ref)
+    lib, ref = build_pair(items, dtype, m, L, seed=5, eps=0.2, projection=proj)
+    check_index(lib, ref, proj)
     Q = rand_q(9, d, 7)
     for B in sorted({1, max(1, n // 3), n, n + 5}):
         check_queries(lib, ref, Q, min(10, n + 2), B)
 
 
-def test_duplicates_zero_vectors_and_zero_subdatasets():
+@pytest.mark.parametrize("proj", [SIMT, TENSOR])
+def test_duplicates_zero_vectors_and_zero_subdatasets(proj):
     rng = np.random.default_rng(3)
     base = rng.standard_normal((20, 16)).astype(np.float32)
     items = np.concatenate([np.zeros((300, 16), np.float32), np.repeat(base, 40, axis=0)])
     rng.shuffle(items)
-    lib, ref = build_pair(items, "f32", 16, 32, seed=9, eps=0.1)
+    lib, ref = build_pair(items, "f32", 16, 32, seed=9, eps=0.1, projection=proj)
     assert ref.U2[0] == 0.0
-    check_index(lib, ref)
+    check_index(lib, ref, proj)
     Q = rand_q(12, 16, 4)
     Q[0] = 0.0          # zero query: every bit is 1
     for B in (1, 50, 333, 1100):
