@@ -164,45 +164,53 @@ def gpu_arm(args):
     eps, budget, rec = chosen
     eps = float(np.float32(eps))
 
-    def step():
-        ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps)
+    forms = {"plain_fp32": N.NRLSH_PROJECT_SIMT, "bf16_tc": N.NRLSH_PROJECT_TENSOR}
+    if args.form != "both":
+        forms = {k: v for k, v in forms.items() if k == args.form}
+
+    def step(proj):
+        ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=proj)
         ids, sc = N.nrlsh_query_ex(ix, Q, w.k, budget)
         return ix, ids
 
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    for _ in range(args.warmup):
-        ix, _ = step()
-        ix.free()
-    torch.cuda.synchronize()
+    def timed(proj):
+        for _ in range(args.warmup):
+            ix, _ = step(proj)
+            ix.free()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches0 = N.nrlsh_launch_count()
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix, ids = step(proj)
+            e1.record(stream)
+            ix.free()                       # synchronises; outside the timed region
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        return times, N.nrlsh_launch_count() - launches0
 
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    launches0 = N.nrlsh_launch_count()
-    times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ix, ids = step()
-        e1.record(stream)
-        ix.free()                       # synchronises; outside the timed region
-        times.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
-    launches = N.nrlsh_launch_count() - launches0
+    per_form = {}
+    for name, proj in forms.items():
+        times, launches = timed(proj)
+        t = torch.tensor([float(np.mean(times))], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        per_form[name] = (float(t.item()), times, launches, proj)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if rank == 0 else None
-    ms_step = float(np.mean(times))
-    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    best = min(per_form, key=lambda k: per_form[k][0])
+    ms_max, times, launches, best_proj = per_form[best]
     value = w.nq * world / (ms_max / 1e3)
 
     # -------- per-kernel times: the same steps again with event brackets on
@@ -210,7 +218,7 @@ def gpu_arm(args):
     N.nrlsh_profile_read()
     for _ in range(args.steps):
         flush.zero_()
-        ix, _ = step()
+        ix, _ = step(best_proj)
         ix.free()
     torch.cuda.synchronize()
     prof = N.nrlsh_profile_read()
@@ -226,7 +234,7 @@ def gpu_arm(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ix = N.nrlsh_build_ex(Xh, w.m, w.L, w.index_seed, eps=eps)
+        ix = N.nrlsh_build_ex(Xh, w.m, w.L, w.index_seed, eps=eps, projection=best_proj)
         N.nrlsh_query_ex(ix, Qp, w.k, budget, ids=ids_h, scores=sc_h)
         t1 = time.perf_counter()
         ix.free()
@@ -244,7 +252,11 @@ def gpu_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded Gaussian directions, lognormal norms)",
-            "form": "plain_fp32",
+            "form": best,
+            "forms": {k: {"queries_per_s": w.nq * world / (v[0] / 1e3), "ms_per_step": v[0],
+                          "p50_ms": float(np.percentile(v[1], 50)),
+                          "p99_ms": float(np.percentile(v[1], 99))}
+                      for k, v in per_form.items()},
             "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "m": w.m, "L": w.L,
                        "queries_per_gpu": w.nq, "k": w.k, "probe_budget": budget,
                        "eps": eps, "recall_at_10": rec,
@@ -374,6 +386,45 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Kernel-level timing run (not a bench line): builds (or queries) the named
+    preset a few times with the library's per-kernel event timing on, and prints
+    {kernel: ms per launch}.  Used for the ncu captures summarised in profiles/."""
+    import torch
+
+    import paper_1809_08782_gb300.nrlsh as N
+    from paper_1809_08782_gb300 import build as B
+    B.build()
+    N.load()
+    w = W.make_workload(args.workload, nq=args.queries, with_data=False)
+    items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, w.dtype)
+    X = W.to_torch(items, w.dtype, "cuda")
+    Q = torch.from_numpy(W.gen_queries(w.nq, w.d, w.query_seed)).cuda()
+    proj = {"plain_fp32": N.NRLSH_PROJECT_SIMT, "bf16_tc": N.NRLSH_PROJECT_TENSOR,
+            "both": N.NRLSH_PROJECT_TENSOR}[args.form]
+    eps = float(np.float32(args.eps if args.eps is not None else 0.2))
+    budget = args.budget if args.budget is not None else w.budget
+    ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=proj)
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            N.nrlsh_set_profiling(True)
+            N.nrlsh_profile_read()
+        if args.profile_case == "build":
+            ix.free()
+            ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=proj)
+        else:
+            N.nrlsh_query_ex(ix, Q, w.k, budget)
+    torch.cuda.synchronize()
+    prof = N.nrlsh_profile_read()
+    info = N.nrlsh_get_info(ix)
+    print(json.dumps({"profile_case": args.profile_case, "workload": w.name, "form": args.form,
+                      "n": w.n, "d": w.d, "L": w.L, "queries": w.nq, "budget": budget,
+                      "ambiguous_bits": info["ambiguous_bits"],
+                      "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items()},
+                      "launches": {k: v[1] for k, v in prof.items()}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,10 +432,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="both", choices=["both", "plain_fp32", "bf16_tc"],
+                    help="projection path(s) to time")
     ap.add_argument("--eps", type=float, default=None, help="skip calibration: fixed eps")
     ap.add_argument("--budget", type=int, default=None, help="skip calibration: fixed B")
+    ap.add_argument("--profile-case", default=None, choices=["build", "query"],
+                    help="kernel timing run of one phase instead of the bench line")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS))
+    ap.add_argument("--queries", type=int, default=1000, help="queries (profile runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ.setdefault(var, "1")

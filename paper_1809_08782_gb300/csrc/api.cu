@@ -43,7 +43,8 @@ struct nrlsh_index {
     unsigned* ambiguous = nullptr;  // (item, bit) pairs the first tier left undecided
     int projection = NRLSH_PROJECT_SIMT;
     __nv_bfloat16* At = nullptr;     // A^T in bf16, 64 x dp (tensor-core B operand)
-    __nv_bfloat16* Xb = nullptr;     // bf16 copy of fp32 items, n x dp (tensor-core A operand)
+    __nv_bfloat16* Xb = nullptr;     // fp32 items: bf16 high part, n x dp (tensor-core A operand)
+    __nv_bfloat16* Xb2 = nullptr;    // fp32 items: bf16 low part (x - hi rounded), n x dp
     int* dev_err = nullptr;          // set by bounded device waits that ran out
 };
 
@@ -277,7 +278,10 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     const bool tc = ix->projection == NRLSH_PROJECT_TENSOR;
     if (tc) {
         B_CK(own(ix, &ix->At, (size_t)64 * ix->dp));
-        if (dtype == NRLSH_F32) B_CK(own(ix, &ix->Xb, (size_t)n * ix->dp));
+        if (dtype == NRLSH_F32) {
+            B_CK(own(ix, &ix->Xb, (size_t)n * ix->dp));
+            B_CK(own(ix, &ix->Xb2, (size_t)n * ix->dp));
+        }
     }
 
     // histogram tiles: runs of positions inside one sub-dataset
@@ -305,8 +309,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         unsigned long long *amb_list, *amb_list2 = nullptr;
         unsigned* amb_count2 = nullptr;
         // the bf16 pass on fp32 items leaves a few percent of the bits to the FP32 tier
-        const size_t amb_cap = (tc && dtype == NRLSH_F32) ? std::max<size_t>(4096, (size_t)n * L / 8)
-                                                          : ambiguity_capacity(n, L);
+        const size_t amb_cap = tc ? std::max<size_t>(4096, (size_t)n * L / 16)
+                                  : ambiguity_capacity(n, L);
         const size_t amb_cap2 = ambiguity_capacity(n, L);
         B_CK(sc.get(&keys, n));
         B_CK(sc.get(&keys_alt, n));
@@ -317,7 +321,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(sc.get(&bucket_keys, ix->ncls));
         B_CK(sc.get(&sort_tmp, radix_sort_temp_bytes(n)));
         B_CK(sc.get(&amb_list, amb_cap));
-        if (tc && dtype == NRLSH_F32) {
+        if (tc) {
             B_CK(sc.get(&amb_list2, amb_cap2));
             B_CK(sc.get(&amb_count2, 1));
             B_CU(cudaMemsetAsync(amb_count2, 0, sizeof(unsigned), st));
@@ -344,7 +348,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                              cudaMemcpyDeviceToDevice, st));
         // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
         B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, m, ix->s_id, ix->U2, ix->Xp,
-                                 ix->Xb, ix->s_pos, ix->tau64, ix->tau32, ix->xnorm, st));
+                                 ix->Xb, ix->Xb2, ix->s_pos, ix->tau64, ix->tau32, ix->xnorm, st));
         // Eq. 4: sign random projection codes
         if (!tc) {
             B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
@@ -352,24 +356,18 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                      amb_list, ix->ambiguous, (unsigned)amb_cap, st));
         } else {
             const __nv_bfloat16* xb = dtype == NRLSH_F32 ? ix->Xb : (const __nv_bfloat16*)ix->Xp;
-            B_CU(launch_project_tc(xb, ix->Xp, n, d, ix->dp, L, ix->Lp, ix->At, ix->A_pad,
+            B_CU(launch_project_tc(xb, ix->Xb2, ix->Xp, n, d, ix->dp, L, ix->Lp, ix->At, ix->A_pad,
                                    ix->anorm, ix->tau32, ix->tau64, ix->xnorm, dtype == NRLSH_F32,
                                    ix->codes, ix->code_bytes, amb_list, ix->ambiguous,
                                    (unsigned)amb_cap, ix->dev_err, st));
-            if (dtype == NRLSH_F32) {
-                B_CU(launch_resolve_fp32((const float*)ix->Xp, n, d, ix->dp, L, ix->Lp, ix->A_pad,
-                                         ix->anorm, ix->xnorm, ix->tau32, ix->tau64, amb_list,
-                                         ix->ambiguous, (unsigned)amb_cap, ix->codes,
-                                         ix->code_bytes, amb_list2, amb_count2,
-                                         (unsigned)amb_cap2, st));
-                B_CU(launch_resolve_fp64(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad,
-                                         ix->tau64, amb_list2, amb_count2, (unsigned)amb_cap2,
-                                         ix->codes, ix->code_bytes, st));
-            } else {
-                B_CU(launch_resolve_fp64(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad,
-                                         ix->tau64, amb_list, ix->ambiguous, (unsigned)amb_cap,
-                                         ix->codes, ix->code_bytes, st));
-            }
+            // bits the tensor-core bound left open: FP32 on CUDA cores, then FP64
+            B_CU(launch_resolve_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
+                                     ix->xnorm, ix->tau32, ix->tau64, amb_list, ix->ambiguous,
+                                     (unsigned)amb_cap, ix->codes, ix->code_bytes, amb_list2,
+                                     amb_count2, (unsigned)amb_cap2, st));
+            B_CU(launch_resolve_fp64(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->tau64,
+                                     amb_list2, amb_count2, (unsigned)amb_cap2, ix->codes,
+                                     ix->code_bytes, st));
         }
         // Eq. 12 and the sorted (U_j, l) structure
         B_CU(launch_bucket_order(ix->U2, m, L, eps, ix->shat_sorted, ix->order, bucket_keys, st));

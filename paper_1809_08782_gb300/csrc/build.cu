@@ -188,14 +188,50 @@ __global__ void __launch_bounds__(128) sqnorm_f32v4_kernel(const float* __restri
     if (row < n) store_norm(row, acc, s, keys, vals);
 }
 
+// Same sums for bf16 rows with d and the row stride even (4-byte aligned rows):
+// the tile is loaded two elements per 32-bit load.
+__global__ void __launch_bounds__(128) sqnorm_bf16x2_kernel(const __nv_bfloat16* __restrict__ X,
+                                                            int64_t n, int d, int64_t ld,
+                                                            double* __restrict__ s, uint64_t* keys,
+                                                            uint32_t* vals) {
+    __shared__ float tile[128][33];
+    const int64_t row0 = (int64_t)blockIdx.x * 128;
+    const int d2 = d / 2;
+    double acc = 0.0;
+    for (int c0 = 0; c0 < d; c0 += 32) {
+        for (int i = threadIdx.x; i < 128 * 16; i += 128) {
+            const int r = i >> 4, w = i & 15;
+            const int64_t row = row0 + r;
+            const int c2 = (c0 >> 1) + w;
+            float2 v = make_float2(0.f, 0.f);
+            if (row < n && c2 < d2) v = __bfloat1622float2(((const __nv_bfloat162*)(X + row * ld))[c2]);
+            tile[r][2 * w] = v.x;
+            tile[r][2 * w + 1] = v.y;
+        }
+        __syncthreads();
+        const int cmax = min(32, d - c0);
+        for (int c = 0; c < cmax; ++c) {
+            const double v = (double)tile[threadIdx.x][c];
+            acc = fma(v, v, acc);
+        }
+        __syncthreads();
+    }
+    const int64_t row = row0 + threadIdx.x;
+    if (row < n) store_norm(row, acc, s, keys, vals);
+}
+
 }  // namespace
 
 cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64_t ld, double* s,
                           uint64_t* keys, uint32_t* vals, cudaStream_t st) {
     const dim3 grid((unsigned)ceil_div(n, 128));
-    if (dt == NRLSH_BF16)
+    if (dt == NRLSH_BF16) {
+        if (d % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X & 3) == 0)
+            return launch("sqnorm_bf16", sqnorm_bf16x2_kernel, grid, dim3(128), 0, st,
+                          (const __nv_bfloat16*)X, n, d, ld, s, keys, vals);
         return launch("sqnorm_bf16", sqnorm_kernel<__nv_bfloat16>, grid, dim3(128), 0, st,
                       (const __nv_bfloat16*)X, n, d, ld, s, keys, vals);
+    }
     if (ld == d && d % 4 == 0 && ((uintptr_t)X & 15) == 0)
         return launch("sqnorm_f32", sqnorm_f32v4_kernel, grid, dim3(128), 0, st, (const float*)X, n,
                       d, s, keys, vals);
@@ -458,7 +494,8 @@ __global__ void gather_items_kernel(const T* __restrict__ X, int64_t ld, int d, 
                                     const uint32_t* __restrict__ perm, int64_t n, int m,
                                     const double* __restrict__ s_id, const double* __restrict__ U2,
                                     T* __restrict__ Xp, __nv_bfloat16* __restrict__ Xb,
-                                    double* s_pos, double* tau64, float* tau32, float* xnorm) {
+                                    __nv_bfloat16* __restrict__ Xb2, double* s_pos, double* tau64,
+                                    float* tau32, float* xnorm) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= n) return;
@@ -468,7 +505,87 @@ __global__ void gather_items_kernel(const T* __restrict__ X, int64_t ld, int d, 
     for (int c = lane; c < dp; c += 32) {
         const T v = c < d ? src[c] : T(0.0f);
         dst[c] = v;
-        if (Xb) Xb[p * dp + c] = __float2bfloat16_rn(to_f32(v));  // the tensor-core copy
+        if (Xb) {  // tensor-core copies: x = hi + lo + r, |r| <= 2^-16 |x|
+            const float x = to_f32(v);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            Xb[p * dp + c] = hi;
+            if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        }
+    }
+    if (lane == 0) {
+        const double s = s_id[id];
+        const double u2 = U2[seg_of(p, n, m)];
+        const double t = (u2 == 0.0) ? 1.0 : sqrt(u2 - s);
+        s_pos[p] = s;
+        tau64[p] = t;
+        tau32[p] = (float)t;
+        xnorm[p] = __fsqrt_ru(__double2float_ru(s));
+    }
+}
+
+// Vectorised form of gather_items_kernel for rows whose length d is a multiple
+// of the vector width (fp32: 4 per 16-byte load; bf16: 2 per 4-byte load) and
+// whose source rows are aligned to it.  Same outputs.
+template <typename T>
+struct GatherVec;
+template <>
+struct GatherVec<float> {
+    using V = float4;
+    static constexpr int W = 4;
+    __device__ static void to_f(const V& v, float (&f)[4]) {
+        f[0] = v.x;
+        f[1] = v.y;
+        f[2] = v.z;
+        f[3] = v.w;
+    }
+};
+template <>
+struct GatherVec<__nv_bfloat16> {
+    using V = __nv_bfloat162;
+    static constexpr int W = 2;
+    __device__ static void to_f(const V& v, float (&f)[2]) {
+        const float2 t = __bfloat1622float2(v);
+        f[0] = t.x;
+        f[1] = t.y;
+    }
+};
+
+template <typename T>
+__global__ void gather_items_vec_kernel(const T* __restrict__ X, int64_t ld, int d, int dp,
+                                        const uint32_t* __restrict__ perm, int64_t n, int m,
+                                        const double* __restrict__ s_id,
+                                        const double* __restrict__ U2, T* __restrict__ Xp,
+                                        __nv_bfloat16* __restrict__ Xb,
+                                        __nv_bfloat16* __restrict__ Xb2, double* s_pos,
+                                        double* tau64, float* tau32, float* xnorm) {
+    using GV = GatherVec<T>;
+    using V = typename GV::V;
+    constexpr int W = GV::W;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= n) return;
+    const uint32_t id = perm[p];
+    const V* src = (const V*)(X + (int64_t)id * ld);
+    V* dst = (V*)(Xp + p * dp);
+    const int nv = d / W;
+    for (int c = lane; c < nv; c += 32) {
+        const V v = src[c];
+        dst[c] = v;
+        if (Xb) {  // tensor-core copies: x = hi + lo + r, |r| <= 2^-16 |x|
+            float f[W];
+            GV::to_f(v, f);
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(f[i]);
+                Xb[p * dp + c * W + i] = hi;
+                if (Xb2) Xb2[p * dp + c * W + i] = __float2bfloat16_rn(f[i] - __bfloat162float(hi));
+            }
+        }
+    }
+    for (int c = d + lane; c < dp; c += 32) {
+        Xp[p * dp + c] = T(0.0f);
+        if (Xb) Xb[p * dp + c] = __float2bfloat16_rn(0.0f);
+        if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(0.0f);
     }
     if (lane == 0) {
         const double s = s_id[id];
@@ -492,16 +609,28 @@ cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* s
 
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
                                 const uint32_t* perm, int64_t n, int m, const double* s_id,
-                                const double* U2, void* Xp, __nv_bfloat16* Xb, double* s_pos,
-                                double* tau64, float* tau32, float* xnorm, cudaStream_t st) {
+                                const double* U2, void* Xp, __nv_bfloat16* Xb, __nv_bfloat16* Xb2,
+                                double* s_pos, double* tau64, float* tau32, float* xnorm,
+                                cudaStream_t st) {
     const dim3 grid((unsigned)ceil_div(n * 32, 256));
-    if (dt == NRLSH_BF16)
+    if (dt == NRLSH_BF16) {
+        if (d % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X & 3) == 0)
+            return launch("gather_items_bf16", gather_items_vec_kernel<__nv_bfloat16>, grid,
+                          dim3(256), 0, st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, m, s_id,
+                          U2, (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr,
+                          (__nv_bfloat16*)nullptr, s_pos, tau64, tau32, xnorm);
         return launch("gather_items_bf16", gather_items_kernel<__nv_bfloat16>, grid, dim3(256), 0,
                       st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, m, s_id, U2,
-                      (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr, s_pos, tau64, tau32, xnorm);
+                      (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, s_pos,
+                      tau64, tau32, xnorm);
+    }
+    if (d % 4 == 0 && ld % 4 == 0 && ((uintptr_t)X & 15) == 0)
+        return launch("gather_items_f32", gather_items_vec_kernel<float>, grid, dim3(256), 0, st,
+                      (const float*)X, ld, d, dp, perm, n, m, s_id, U2, (float*)Xp, Xb, Xb2, s_pos,
+                      tau64, tau32, xnorm);
     return launch("gather_items_f32", gather_items_kernel<float>, grid, dim3(256), 0, st,
-                  (const float*)X, ld, d, dp, perm, n, m, s_id, U2, (float*)Xp, Xb, s_pos, tau64,
-                  tau32, xnorm);
+                  (const float*)X, ld, d, dp, perm, n, m, s_id, U2, (float*)Xp, Xb, Xb2, s_pos,
+                  tau64, tau32, xnorm);
 }
 
 // =====================================================================
@@ -675,9 +804,9 @@ __global__ void __launch_bounds__(256)
 // warp per pair, FP32 dot of the exact fp32 row in lane-strided order and a
 // tree, decided against (d+2) 2^-22 ||a|| ||x|| (any summation order) plus the
 // tail rounding; still undecided pairs move on to the FP64 list.
-template <typename C>
+template <typename T, typename C>
 __global__ void __launch_bounds__(256)
-    resolve_fp32_kernel(const float* __restrict__ X, int d, int ldx, int Lp,
+    resolve_fp32_kernel(const T* __restrict__ X, int d, int ldx, int Lp,
                         const float* __restrict__ A_pad, const float* __restrict__ anorm,
                         const float* __restrict__ xnorm, const float* __restrict__ tau32,
                         const double* __restrict__ tau64, const unsigned long long* __restrict__ list,
@@ -692,9 +821,9 @@ __global__ void __launch_bounds__(256)
         const unsigned long long entry = list[e];
         const int64_t row = (int64_t)(entry >> 6);
         const int bit = (int)(entry & 63);
-        const float* xr = X + row * ldx;
+        const T* xr = X + row * ldx;
         float s = 0.0f;
-        for (int k = lane; k < d; k += 32) s = fmaf(xr[k], A_pad[(int64_t)k * Lp + bit], s);
+        for (int k = lane; k < d; k += 32) s = fmaf(to_f32(xr[k]), A_pad[(int64_t)k * Lp + bit], s);
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const float ad = A_pad[(int64_t)d * Lp + bit];
         const float t32 = tau32[row];
@@ -792,8 +921,8 @@ cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
                                              "project_fp32");
 }
 
-cudaError_t launch_resolve_fp32(const float* X, int64_t n, int d, int ldx, int L, int Lp,
-                                const float* A_pad, const float* anorm, const float* xnorm,
+cudaError_t launch_resolve_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                int Lp, const float* A_pad, const float* anorm, const float* xnorm,
                                 const float* tau32, const double* tau64,
                                 const unsigned long long* list, const unsigned* count,
                                 unsigned cap, void* codes, int code_bytes,
@@ -802,13 +931,17 @@ cudaError_t launch_resolve_fp32(const float* X, int64_t n, int d, int ldx, int L
     const float kappa = (float)(d + 2) * 0x1p-22f;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 32, 32), 8),
                                                       16 * 152);
-    if (code_bytes == 4)
-        return launch("resolve_fp32", resolve_fp32_kernel<uint32_t>, dim3(grid), dim3(256), 0, st, X,
-                      d, ldx, Lp, A_pad, anorm, xnorm, tau32, tau64, list, count, cap,
-                      (uint32_t*)codes, list2, count2, cap2, kappa);
-    return launch("resolve_fp32", resolve_fp32_kernel<uint64_t>, dim3(grid), dim3(256), 0, st, X, d,
-                  ldx, Lp, A_pad, anorm, xnorm, tau32, tau64, list, count, cap, (uint64_t*)codes,
-                  list2, count2, cap2, kappa);
+#define NRLSH_R32(T_, C_)                                                                    \
+    return launch("resolve_fp32", resolve_fp32_kernel<T_, C_>, dim3(grid), dim3(256), 0, st,  \
+                  (const T_*)X, d, ldx, Lp, A_pad, anorm, xnorm, tau32, tau64, list, count,  \
+                  cap, (C_*)codes, list2, count2, cap2, kappa);
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_R32(__nv_bfloat16, uint32_t)
+        NRLSH_R32(__nv_bfloat16, uint64_t)
+    }
+    if (code_bytes == 4) NRLSH_R32(float, uint32_t)
+    NRLSH_R32(float, uint64_t)
+#undef NRLSH_R32
 }
 
 cudaError_t launch_resolve_fp64(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,

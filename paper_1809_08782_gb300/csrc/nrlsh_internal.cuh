@@ -104,8 +104,9 @@ cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* s
                                   uint32_t* jkeys, uint32_t* jvals, cudaStream_t st);
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
                                 const uint32_t* perm, int64_t n, int m, const double* s_id,
-                                const double* U2, void* Xp, __nv_bfloat16* Xb, double* s_pos,
-                                double* tau64, float* tau32, float* xnorm, cudaStream_t st);
+                                const double* U2, void* Xp, __nv_bfloat16* Xb, __nv_bfloat16* Xb2,
+                                double* s_pos, double* tau64, float* tau32, float* xnorm,
+                                cudaStream_t st);
 // Sign random projection of rows of X (row stride ldx, stored dtype) with the FP32
 // fast tier; undecided (row, bit) pairs go through amb_list (capacity amb_cap,
 // count in *amb_count, which must start at 0) to the FP64 resolve kernel.
@@ -119,7 +120,8 @@ cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
 size_t ambiguity_capacity(int64_t rows, int L);
 // FP32 tier (fp32 items after the bf16 tensor-core pass) and FP64 tier on a list
 // of undecided (row, bit) pairs; decided bits are OR-ed into the codes.
-cudaError_t launch_resolve_fp32(const float* X, int64_t n, int d, int ldx, int L, int Lp,
+cudaError_t launch_resolve_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                int Lp,
                                 const float* A_pad, const float* anorm, const float* xnorm,
                                 const float* tau32, const double* tau64,
                                 const unsigned long long* list, const unsigned* count,
@@ -132,12 +134,13 @@ cudaError_t launch_resolve_fp64(const void* X, nrlsh_dtype dt, int64_t n, int d,
                                 unsigned cap, void* codes, int code_bytes, cudaStream_t st);
 // tcgen05 projection of the items (bf16 copy Xb, n x dp; At = A^T bf16, 64 x dp).
 bool project_tc_supported(int d, int L);
-cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const void* X_exact, int64_t n, int d, int dp,
-                              int L, int Lp, const __nv_bfloat16* At, const float* A_pad,
-                              const float* anorm, const float* tau32, const double* tau64,
-                              const float* xnorm, bool fp32_items, void* codes, int code_bytes,
-                              unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
-                              int* err, cudaStream_t st);
+cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2, const void* X_exact,
+                              int64_t n, int d, int dp, int L, int Lp, const __nv_bfloat16* At,
+                              const float* A_pad, const float* anorm, const float* tau32,
+                              const double* tau64, const float* xnorm, bool fp32_items,
+                              void* codes, int code_bytes, unsigned long long* amb_list,
+                              unsigned* amb_count, unsigned amb_cap, int* err, cudaStream_t st);
+// The sorted (U_j, l) structure: probing order of the m (L+1) buckets.
 cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, double* shat_sorted,
                                 uint32_t* order, double* scratch_keys, cudaStream_t st);
 

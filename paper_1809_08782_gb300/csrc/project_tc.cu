@@ -5,7 +5,8 @@
 //
 // Persistent warp-specialised CTAs (192 threads):
 //   warp 0   one thread issues TMA loads: all of A^T once (K-major, 128-byte
-//            swizzle), then a 4-stage ring of 128-item x 64-K tiles of X~;
+//            swizzle), then a ring of stages, each a 128-item x 64-K tile of X~
+//            (fp32 items: two tiles, the bf16 high and low parts of x);
 //   warp 1   allocates 128 TMEM columns (two accumulators of up to 64 columns)
 //            and one thread issues tcgen05.mma (M = 128, N = 16..64, K = 16);
 //   warps 2-5 read the accumulator rows (warp w reads TMEM lanes 32 (w % 4)..),
@@ -28,7 +29,8 @@ namespace {
 
 constexpr int kTcM = 128;            // items per tile (MMA M)
 constexpr int kTcKC = 64;            // K elements per stage: 128 bytes of bf16
-constexpr int kTcStages = 4;
+constexpr int kTcStagesOne = 4;  // stages of one 16 KB tile
+constexpr int kTcStagesTwo = 3;  // stages of two 16 KB tiles (split fp32 items)
 constexpr int kTcThreads = 192;
 constexpr uint32_t kTmemCols = 128;  // two accumulators of up to 64 fp32 columns
 constexpr uint32_t kXStageBytes = kTcM * kTcKC * 2;
@@ -150,20 +152,22 @@ __host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
 }
 
 struct TcSmem {
-    int nkc, N;
+    int nkc, N, split, stages;
     __device__ uint8_t* a_tile(uint8_t* base, int c) const { return base + (size_t)c * N * 128; }
-    __device__ uint8_t* x_stage(uint8_t* base, int s) const {
-        return base + (size_t)nkc * N * 128 + (size_t)s * kXStageBytes;
+    __device__ uint8_t* x_stage(uint8_t* base, int s, int part) const {
+        return base + (size_t)nkc * N * 128 + ((size_t)s * split + part) * kXStageBytes;
     }
     __device__ uint64_t* bars(uint8_t* base) const {
-        return (uint64_t*)(base + (size_t)nkc * N * 128 + (size_t)kTcStages * kXStageBytes);
+        return (uint64_t*)(base + (size_t)nkc * N * 128 + (size_t)stages * split * kXStageBytes);
     }
 };
 
 template <typename C>
 __global__ void __launch_bounds__(kTcThreads, 1)
     project_tc_kernel(const __grid_constant__ CUtensorMap map_x,
-                      const __grid_constant__ CUtensorMap map_a, int64_t n, int nkc, int L, int N,
+                      const __grid_constant__ CUtensorMap map_x2,
+                      const __grid_constant__ CUtensorMap map_a, int split, int64_t n, int nkc, int L,
+                      int N,
                       int Lp, int d, const float* __restrict__ A_pad,
                       const float* __restrict__ anorm, const float* __restrict__ tau32,
                       const float* __restrict__ xnorm, float kappa_tc, float round_x,
@@ -173,7 +177,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                       unsigned amb_cap, int* err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const TcSmem L_{nkc, N};
+    const int kTcStages = split == 2 ? kTcStagesTwo : kTcStagesOne;
+    const TcSmem L_{nkc, N, split, kTcStages};
+    const uint32_t stage_bytes = (uint32_t)split * kXStageBytes;
     uint64_t* bars = L_.bars(base);
     uint64_t* full = bars;                       // kTcStages
     uint64_t* empty = bars + kTcStages;          // kTcStages
@@ -183,8 +189,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t* drain = a_bar + 1;                 // 1: all MMAs of this CTA done
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
     volatile int* abort_s = (volatile int*)(tmem_slot + 1);
-    float* s_anorm = (float*)(tmem_slot + 4);    // 64
-    float* s_ad = s_anorm + 64;                  // 64
+    float* s_c1 = (float*)(tmem_slot + 4);       // 64: (kappa_tc + round_x) ||a_b||
+    float* s_c2 = s_c1 + 64;                     // 64: 2^-20 |a_{d,b}|
+    float* s_ad = s_c2 + 64;                     // 64: a_{d,b}
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = ceil_div(n, kTcM);
@@ -206,8 +213,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (threadIdx.x < 64) {
         const int b = threadIdx.x;
-        s_anorm[b] = b < L ? anorm[b] : 0.0f;
-        s_ad[b] = b < L ? A_pad[(int64_t)d * Lp + b] : 0.0f;
+        const float ad = b < L ? A_pad[(int64_t)d * Lp + b] : 0.0f;
+        s_ad[b] = ad;
+        s_c1[b] = b < L ? (kappa_tc + round_x) * anorm[b] : 0.0f;
+        s_c2[b] = 0x1p-20f * fabsf(ad);
     }
     if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
@@ -222,8 +231,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int c = 0; c < nkc; ++c) tma_load_2d(L_.a_tile(base, c), &map_a, a_bar, c * kTcKC, 0);
             int stage = 0;
             uint32_t phase = 0;
-            int issued[kTcStages] = {0, 0, 0, 0};
-            uint32_t issued_par[kTcStages] = {0, 0, 0, 0};
+            int issued[kTcStagesOne] = {0, 0, 0, 0};
+            uint32_t issued_par[kTcStagesOne] = {0, 0, 0, 0};
             for (int64_t t = blockIdx.x; t < ntiles && !*abort_s; t += gridDim.x) {
                 for (int c = 0; c < nkc; ++c) {
                     if (!mbar_wait(&empty[stage], phase ^ 1)) {
@@ -231,9 +240,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         *abort_s = 1;
                         break;
                     }
-                    mbar_expect_tx(&full[stage], kXStageBytes);
-                    tma_load_2d(L_.x_stage(base, stage), &map_x, &full[stage], c * kTcKC,
+                    mbar_expect_tx(&full[stage], stage_bytes);
+                    tma_load_2d(L_.x_stage(base, stage, 0), &map_x, &full[stage], c * kTcKC,
                                 (int)(t * kTcM));
+                    if (split == 2)
+                        tma_load_2d(L_.x_stage(base, stage, 1), &map_x2, &full[stage], c * kTcKC,
+                                    (int)(t * kTcM));
                     issued[stage] = 1;
                     issued_par[stage] = phase;
                     if (++stage == kTcStages) {
@@ -270,11 +282,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t adesc = sw128_desc(L_.x_stage(base, stage));
                     const uint64_t bdesc = sw128_desc(L_.a_tile(base, c));
+                    for (int part = 0; part < split; ++part) {
+                        const uint64_t adesc = sw128_desc(L_.x_stage(base, stage, part));
 #pragma unroll
-                    for (int k = 0; k < kTcKC / 16; ++k)  // 32 bytes of K per MMA
-                        umma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc, (c | k) != 0);
+                        for (int k = 0; k < kTcKC / 16; ++k)  // 32 bytes of K per MMA
+                            umma_bf16(d_tmem, adesc + 2 * k, bdesc + 2 * k, idesc,
+                                      (c | k | part) != 0);
+                    }
                     umma_commit(&empty[stage]);
                     if (++stage == kTcStages) {
                         stage = 0;
@@ -312,7 +327,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool valid = row < n;
             const float xn = valid ? xnorm[row] : 0.0f;
             const float t32 = valid ? tau32[row] : 0.0f;
-            unsigned long long word = 0;
+            unsigned long long word = 0, undecided = 0;
             for (int c0 = 0; c0 < N; c0 += 16) {
                 uint32_t r[16];
                 tmem_ld16(tmem_base + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 64 + c0), r);
@@ -320,33 +335,47 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int i = 0; i < 16; ++i) {
                     const int bit = c0 + i;
                     if (!valid || bit >= L) continue;
-                    const float ad = s_ad[bit];
-                    const float v = fmaf(ad, t32, __uint_as_float(r[i]));
+                    const float v = fmaf(s_ad[bit], t32, __uint_as_float(r[i]));
                     // accumulation bound (kappa_tc) plus, for fp32 items, the bf16
                     // rounding of x (round_x); Cauchy-Schwarz for sum |a_k x_k|
-                    const float bound = (kappa_tc + round_x) * s_anorm[bit] * xn +
-                                        0x1p-20f * fabsf(ad) * t32;
+                    const float bound = fmaf(s_c1[bit], xn, s_c2[bit] * t32);
                     if (fabsf(v) * (1.0f - 0x1p-21f) > bound) {
                         if (v > 0.0f) word |= 1ull << bit;
                     } else {
-                        const unsigned slot = atomicAdd(amb_count, 1u);
-                        if (slot < amb_cap) {
-                            amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
-                        } else {
-                            // list full: the canonical FP64 evaluation, here
-                            double acc = 0.0;
-                            for (int k = 0; k < d; ++k) {
-                                const double xk =
-                                    fp32_items ? (double)((const float*)X_exact)[row * ldx + k]
-                                               : (double)__bfloat162float(
-                                                     ((const __nv_bfloat16*)X_exact)[row * ldx + k]);
-                                acc = fma(xk, (double)A_pad[(int64_t)k * Lp + bit], acc);
-                            }
-                            acc = __dadd_rn(acc, __dmul_rn((double)ad, tau64[row]));
-                            if (acc >= 0.0) word |= 1ull << bit;
-                        }
+                        undecided |= 1ull << bit;
                     }
                 }
+            }
+            // one list reservation per warp
+            const unsigned cnt = (unsigned)__popcll(undecided);
+            unsigned incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            unsigned wbase = 0;
+            if (lane == 31 && incl) wbase = atomicAdd(amb_count, incl);
+            wbase = __shfl_sync(0xffffffffu, wbase, 31);
+            unsigned slot = wbase + incl - cnt;
+            while (undecided) {
+                const int bit = __ffsll((long long)undecided) - 1;
+                undecided &= undecided - 1;
+                if (slot < amb_cap) {
+                    amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
+                } else {
+                    // list full: the canonical FP64 evaluation, here
+                    double acc = 0.0;
+                    for (int k = 0; k < d; ++k) {
+                        const double xk =
+                            fp32_items ? (double)((const float*)X_exact)[row * ldx + k]
+                                       : (double)__bfloat162float(
+                                             ((const __nv_bfloat16*)X_exact)[row * ldx + k]);
+                        acc = fma(xk, (double)A_pad[(int64_t)k * Lp + bit], acc);
+                    }
+                    acc = __dadd_rn(acc, __dmul_rn((double)s_ad[bit], tau64[row]));
+                    if (acc >= 0.0) word |= 1ull << bit;
+                }
+                ++slot;
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);
@@ -397,9 +426,10 @@ bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer,
 
 }  // namespace
 
-size_t project_tc_smem_bytes(int d, int N) {
+size_t project_tc_smem_bytes(int d, int N, int split) {
     const int nkc = (int)ceil_div(d, kTcKC);
-    return 1024 + (size_t)nkc * N * 128 + (size_t)kTcStages * kXStageBytes + 256 + 2 * 64 * 4;
+    const int stages = split == 2 ? kTcStagesTwo : kTcStagesOne;
+    return 1024 + (size_t)nkc * N * 128 + (size_t)stages * split * kXStageBytes + 256 + 3 * 64 * 4;
 }
 
 bool project_tc_supported(int d, int L) {
@@ -410,41 +440,45 @@ bool project_tc_supported(int d, int L) {
     cudaGetLastError();
     if (major != 10) return false;
     const int N = L <= 16 ? 16 : L <= 32 ? 32 : L <= 48 ? 48 : 64;
-    return project_tc_smem_bytes(d, N) <= 200 * 1024 && encode_fn() != nullptr;
+    return project_tc_smem_bytes(d, N, 2) <= 220 * 1024 && encode_fn() != nullptr;
 }
 
-cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const void* X_exact, int64_t n, int d, int dp,
-                              int L, int Lp, const __nv_bfloat16* At, const float* A_pad,
-                              const float* anorm, const float* tau32, const double* tau64,
-                              const float* xnorm, bool fp32_items, void* codes, int code_bytes,
-                              unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
-                              int* err, cudaStream_t st) {
+cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2, const void* X_exact,
+                              int64_t n, int d, int dp, int L, int Lp, const __nv_bfloat16* At,
+                              const float* A_pad, const float* anorm, const float* tau32,
+                              const double* tau64, const float* xnorm, bool fp32_items,
+                              void* codes, int code_bytes, unsigned long long* amb_list,
+                              unsigned* amb_count, unsigned amb_cap, int* err, cudaStream_t st) {
     const int N = L <= 16 ? 16 : L <= 32 ? 32 : L <= 48 ? 48 : 64;
     const int nkc = (int)ceil_div(d, kTcKC);
-    CUtensorMap map_x, map_a;
+    const int split = Xb2 ? 2 : 1;
+    CUtensorMap map_x, map_x2, map_a;
     if (!make_map(&map_x, Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
+        !make_map(&map_x2, Xb2 ? Xb2 : Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
         !make_map(&map_a, At, (uint64_t)d, (uint64_t)N, (uint64_t)dp, (uint32_t)N))
         return cudaErrorNotSupported;
-    const size_t smem = project_tc_smem_bytes(d, N);
+    const size_t smem = project_tc_smem_bytes(d, N, split);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = ceil_div(n, kTcM);
-    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)sms);
+    const int per_sm = smem * 2 <= 227 * 1024 ? 2 : 1;
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
     // accumulation bound: 16x the first-order FP32 bound (the adder's rounding mode
-    // inside the tensor core is not assumed); bf16 rounding of fp32 items: 2^-8 |x|
-    const float kappa_tc = (float)(nkc * kTcKC + 8) * 0x1p-20f;
-    const float round_x = fp32_items ? 0x1p-8f * (1.0f + 0x1p-7f) : 0.0f;
+    // inside the tensor core is not assumed).  fp32 items enter as x = hi + lo + r
+    // with hi, lo bf16 and |r| <= 2^-16 |x| (one bf16 part: |r| <= 2^-8 |x|).
+    const float kappa_tc = (float)(nkc * kTcKC * split + 8) * 0x1p-20f;
+    const float round_x = !fp32_items ? 0.0f : (split == 2 ? 0x1p-16f : 0x1p-8f) * (1.0f + 0x1p-7f);
 #define NRLSH_TC(C_)                                                                         \
     {                                                                                        \
         auto kern = project_tc_kernel<C_>;                                                   \
         cudaError_t e =                                                                      \
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                      \
-        return launch("project_tc", kern, dim3(grid), dim3(kTcThreads), smem, st, map_x, map_a, \
-                      n, nkc, L, N, Lp, d, A_pad, anorm, tau32, xnorm, kappa_tc, round_x,    \
-                      X_exact, fp32_items ? 1 : 0, dp, tau64, (C_*)codes, amb_list, amb_count, \
-                      amb_cap, err);                                                         \
+        return launch("project_tc", kern, dim3(grid), dim3(kTcThreads), smem, st, map_x, map_x2, \
+                      map_a, split, n, nkc, L, N, Lp, d, A_pad, anorm, tau32, xnorm, kappa_tc, \
+                      round_x, X_exact, fp32_items ? 1 : 0, dp, tau64, (C_*)codes, amb_list,  \
+                      amb_count, amb_cap, err);                                              \
     }
     if (code_bytes == 4) NRLSH_TC(uint32_t)
     NRLSH_TC(uint64_t)
