@@ -153,6 +153,36 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* index, const float* que
                                       void* stream);
 
 /*
+ * Batched query processing with per-query budgets and k (the batching form of the
+ * Section 3.3 multi-probe query): the queries are hashed, their Hamming histograms
+ * computed, and a persistent fused kernel takes queries from a device work
+ * counter, each CTA running the bucket walk, selection, FP32 re-rank and exact
+ * top-k in its own scratch slab.  Results equal nrlsh_query_ex per query.
+ *   ks            nq int32: k of each query, clamped into [1, k_max]
+ *   budgets       nq int64: probe budget of each query, clamped into [1, min(budget_max, n)]
+ *   k_max         1 <= k_max <= NRLSH_MAX_K; ids/scores rows are k_max wide, padded
+ *                 with (-1, -inf) past each query's k
+ *   budget_max    >= 1: the largest budget honoured (sizes the scratch slabs)
+ *   flags         NRLSH_QUERY_GRAPH: capture the launches in a CUDA graph on the first
+ *                 call with these pointers and sizes, and replay it on later identical
+ *                 calls (needs a non-NULL stream; the graph and its workspace live
+ *                 until nrlsh_free).
+ * The first call for a given (nq, k_max, budget_max) shape times a few tile
+ * configurations on a prefix of the batch (the autotuner) and keeps the fastest;
+ * make it before any stream capture of your own.  ks and budgets may be device or
+ * host pointers like the other arrays.
+ */
+#define NRLSH_QUERY_GRAPH 0x2u
+NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* index, const float* queries,
+                                           int64_t nq, const int32_t* ks, const int64_t* budgets,
+                                           int32_t k_max, int64_t budget_max, uint32_t flags,
+                                           int64_t* ids, float* scores, void* stream);
+/* The autotuned configuration last used for this index: histogram queries per
+ * block and persistent CTAs per SM (0, 0 before any batched call). */
+NRLSH_API nrlsh_status nrlsh_get_tuning(const nrlsh_index* index, int32_t* hist_queries_per_block,
+                                        int32_t* ctas_per_sm);
+
+/*
  * Query processing without any device allocation.  The paper has no counterpart:
  * this exists for callers that must not allocate device memory while they query,
  * for example a serving process whose memory is owned by another allocator, or

@@ -9,7 +9,22 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
+
+// Autotuned configuration of the batched query path.
+struct nrlsh_batch_cfg {
+    int hist_qb = 64;       // queries per histogram block
+    int ctas_per_sm = 2;    // persistent probe/re-rank CTAs per SM
+};
+
+// A captured batched-query launch sequence with its fixed workspace.
+struct nrlsh_graph_entry {
+    std::tuple<const void*, int64_t, const void*, const void*, int, int64_t, const void*,
+               const void*, void*> key;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> workspace;
+};
 
 struct nrlsh_index {
     int64_t n = 0;
@@ -46,6 +61,11 @@ struct nrlsh_index {
     __nv_bfloat16* Xb = nullptr;     // fp32 items: bf16 high part, n x dp (tensor-core A operand)
     __nv_bfloat16* Xb2 = nullptr;    // fp32 items: bf16 low part (x - hi rounded), n x dp
     int* dev_err = nullptr;          // set by bounded device waits that ran out
+    // batched queries: autotuned configurations per (nq, k_max, cap) and graph cache
+    mutable std::mutex batch_mu;
+    mutable std::map<std::tuple<int64_t, int, int64_t>, nrlsh_batch_cfg> tuned;
+    mutable nrlsh_batch_cfg last_cfg{0, 0};
+    mutable std::vector<nrlsh_graph_entry> graphs;
 };
 
 namespace nrlsh {
@@ -175,6 +195,11 @@ nrlsh_status own(nrlsh_index* ix, T** out, size_t count) {
 void destroy(nrlsh_index* ix) {
     if (!ix) return;
     cudaStreamSynchronize(ix->stream);
+    for (auto& g : ix->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (void* p : g.workspace) cudaFree(p);
+    }
+    cudaDeviceSynchronize();
     for (void* p : ix->owned) cudaFree(p);
     delete ix;
 }
@@ -809,6 +834,256 @@ NRLSH_API nrlsh_status nrlsh_profile_read(char* names, int64_t names_cap, double
 }
 
 }  // extern "C"
+
+
+// ------------------------------------------------------------- batched queries
+
+namespace {
+
+struct BatchWs {
+    float* qnorm = nullptr;
+    unsigned* qamb = nullptr;
+    unsigned long long* qamb_list = nullptr;
+    size_t qamb_cap = 0;
+    char* qcodes = nullptr;
+    uint32_t* H = nullptr;
+    int64_t hq = 0;           // queries per histogram chunk
+    unsigned* work = nullptr;
+    uint32_t* slabs = nullptr;
+    int ctas = 0;
+};
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Persistent CTAs for a configuration, limited so the slabs stay under 4 GB.
+int batch_ctas(const nrlsh_batch_cfg& cfg, int64_t cap) {
+    const int64_t by_mem = std::max<int64_t>(1, ((int64_t)4 << 30) / (24 * cap));
+    return (int)std::min<int64_t>((int64_t)cfg.ctas_per_sm * device_sms(), by_mem);
+}
+
+// Sizes of the workspace buffers (bytes), in BatchWs order.
+std::vector<size_t> batch_ws_sizes(const nrlsh_index* ix, int64_t nq, int64_t cap, int ctas) {
+    const int64_t hq = std::min<int64_t>(nq, std::max<int64_t>(1, ((int64_t)1 << 30) / (ix->ncls * 4)));
+    return {sizeof(float) * (size_t)nq, 16, sizeof(unsigned long long) * ambiguity_capacity(nq, ix->L),
+            (size_t)ix->code_bytes * nq, sizeof(uint32_t) * (size_t)hq * ix->ncls, 16,
+            (size_t)ctas * 24 * (size_t)cap};
+}
+
+void batch_ws_assign(BatchWs& w, const std::vector<void*>& p, const nrlsh_index* ix, int64_t nq,
+                     int ctas) {
+    w.qnorm = (float*)p[0];
+    w.qamb = (unsigned*)p[1];
+    w.qamb_list = (unsigned long long*)p[2];
+    w.qamb_cap = ambiguity_capacity(nq, ix->L);
+    w.qcodes = (char*)p[3];
+    w.H = (uint32_t*)p[4];
+    w.hq = std::min<int64_t>(nq, std::max<int64_t>(1, ((int64_t)1 << 30) / (ix->ncls * 4)));
+    w.work = (unsigned*)p[5];
+    w.slabs = (uint32_t*)p[6];
+    w.ctas = ctas;
+}
+
+// The launch sequence of a batch (device pointers only).
+nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, const int32_t* ks,
+                         const int64_t* budgets, int k_max, int64_t cap, const nrlsh_batch_cfg& cfg,
+                         const BatchWs& w, int64_t* ids, float* scores, cudaStream_t st) {
+    NRLSH_CK(cudaMemsetAsync(w.qamb, 0, sizeof(unsigned), st));
+    NRLSH_CK(launch_row_norm_bound(Q, nq, ix->d, w.qnorm, st));
+    NRLSH_CK(launch_project_fp32(Q, NRLSH_F32, nq, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
+                                 ix->anorm, nullptr, nullptr, w.qnorm, w.qcodes, ix->code_bytes,
+                                 w.qamb_list, w.qamb, (unsigned)w.qamb_cap, st));
+    for (int64_t q0 = 0; q0 < nq; q0 += w.hq) {
+        const int64_t qc = std::min(w.hq, nq - q0);
+        const char* qcodes = w.qcodes + q0 * ix->code_bytes;
+        NRLSH_CK(cudaMemsetAsync(w.H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
+        NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
+                             ix->ntiles, w.H, st, cfg.hist_qb));
+        NRLSH_CK(cudaMemsetAsync(w.work, 0, sizeof(unsigned), st));
+        NRLSH_CK(launch_probe_rerank_persistent(
+            w.H, ix->order, ix->m, ix->L, ix->n, budgets + q0, ix->codes, qcodes, ix->code_bytes,
+            ix->Xp, ix->dtype, ix->dp, ix->d, Q + q0 * ix->d, ix->xnorm, w.qnorm + q0, ix->perm,
+            ks + q0, k_max, w.slabs, cap, w.ctas, w.work, qc, ids + q0 * k_max,
+            scores + q0 * k_max, st));
+    }
+    return NRLSH_OK;
+}
+
+// Time the candidate configurations on a prefix of the batch; keep the fastest.
+nrlsh_status autotune(const nrlsh_index* ix, const float* Q, int64_t nq, const int32_t* ks,
+                      const int64_t* budgets, int k_max, int64_t cap, int64_t* ids, float* scores,
+                      cudaStream_t st, nrlsh_batch_cfg* best) {
+    const int64_t nt = std::min<int64_t>(nq, 2048);
+    cudaEvent_t e0, e1;
+    NRLSH_CK(cudaEventCreate(&e0));
+    NRLSH_CK(cudaEventCreate(&e1));
+    auto time_cfg = [&](const nrlsh_batch_cfg& c, float* ms) -> nrlsh_status {
+        Scratch sc(st);
+        const int ctas = batch_ctas(c, cap);
+        const auto sizes = batch_ws_sizes(ix, nt, cap, ctas);
+        std::vector<void*> p;
+        for (size_t b : sizes) {
+            char* q = nullptr;
+            NRLSH_CKS(sc.get(&q, b));
+            p.push_back(q);
+        }
+        BatchWs w;
+        batch_ws_assign(w, p, ix, nt, ctas);
+        NRLSH_CKS(run_batched(ix, Q, nt, ks, budgets, k_max, cap, c, w, ids, scores, st));  // warm
+        NRLSH_CK(cudaEventRecord(e0, st));
+        NRLSH_CKS(run_batched(ix, Q, nt, ks, budgets, k_max, cap, c, w, ids, scores, st));
+        NRLSH_CK(cudaEventRecord(e1, st));
+        NRLSH_CK(cudaEventSynchronize(e1));
+        NRLSH_CK(cudaEventElapsedTime(ms, e0, e1));
+        return NRLSH_OK;
+    };
+    nrlsh_batch_cfg c;
+    float best_ms = 1e30f;
+    for (int qb : {32, 64, 128}) {
+        c.hist_qb = qb;
+        c.ctas_per_sm = 2;
+        float ms;
+        NRLSH_CKS(time_cfg(c, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    for (int cps : {1, 4}) {
+        c = *best;
+        c.ctas_per_sm = cps;
+        float ms;
+        NRLSH_CKS(time_cfg(c, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return NRLSH_OK;
+}
+
+}  // namespace
+
+extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, const float* queries,
+                                                      int64_t nq, const int32_t* ks,
+                                                      const int64_t* budgets, int32_t k_max,
+                                                      int64_t budget_max, uint32_t flags,
+                                                      int64_t* ids, float* scores, void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (k_max < 1 || k_max > NRLSH_MAX_K) return arg_error("need 1 <= k_max <= 1024");
+    if (budget_max < 1) return arg_error("need budget_max >= 1");
+    if (flags & ~NRLSH_QUERY_GRAPH) return arg_error("unknown flags");
+    if (nq > 0 && (!ids || !scores || !ks || !budgets)) return arg_error("NULL array");
+    if (nq == 0) return NRLSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    const int64_t cap = std::min<int64_t>(budget_max, ix->n);
+    const bool graph = (flags & NRLSH_QUERY_GRAPH) && st != nullptr;
+    if (graph && !(is_device_ptr(queries) && is_device_ptr(ks) && is_device_ptr(budgets) &&
+                   is_device_ptr(ids) && is_device_ptr(scores)))
+        return arg_error("NRLSH_QUERY_GRAPH needs device pointers");
+    Scratch sc(st);
+    const void *Qd, *ksd, *bd;
+    NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    NRLSH_CKS(stage_in(sc, ks, sizeof(int32_t) * nq, &ksd));
+    NRLSH_CKS(stage_in(sc, budgets, sizeof(int64_t) * nq, &bd));
+    OutStage oi, os;
+    int64_t* idsd;
+    float* scd;
+    NRLSH_CKS(stage_out(sc, ids, (size_t)nq * k_max, oi, &idsd));
+    NRLSH_CKS(stage_out(sc, scores, (size_t)nq * k_max, os, &scd));
+
+    nrlsh_batch_cfg cfg;
+    {
+        std::lock_guard<std::mutex> g(ix->batch_mu);
+        const auto key = std::make_tuple(nq, (int)k_max, cap);
+        auto it = ix->tuned.find(key);
+        if (it != ix->tuned.end()) {
+            cfg = it->second;
+        } else {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (st) cudaStreamIsCapturing(st, &cs);
+            if (cs == cudaStreamCaptureStatusNone) {
+                NRLSH_CKS(autotune(ix, (const float*)Qd, nq, (const int32_t*)ksd,
+                                   (const int64_t*)bd, k_max, cap, idsd, scd, st, &cfg));
+                ix->tuned[key] = cfg;
+            }
+        }
+        ix->last_cfg = cfg;
+    }
+    const int ctas = batch_ctas(cfg, cap);
+    if (!graph) {
+        const auto sizes = batch_ws_sizes(ix, nq, cap, ctas);
+        std::vector<void*> p;
+        for (size_t b : sizes) {
+            char* q = nullptr;
+            NRLSH_CKS(sc.get(&q, b));
+            p.push_back(q);
+        }
+        BatchWs w;
+        batch_ws_assign(w, p, ix, nq, ctas);
+        NRLSH_CKS(run_batched(ix, (const float*)Qd, nq, (const int32_t*)ksd, (const int64_t*)bd,
+                              k_max, cap, cfg, w, idsd, scd, st));
+        return finish_out(st, {&oi, &os}, oi.host || os.host || Qd != queries || ksd != ks ||
+                                              bd != budgets);
+    }
+    // graph mode: replay a captured sequence for identical calls
+    std::lock_guard<std::mutex> g(ix->batch_mu);
+    const auto key = std::make_tuple((const void*)queries, nq, (const void*)ks, (const void*)budgets,
+                                     (int)k_max, cap, (const void*)ids, (const void*)scores, stream);
+    for (auto& e : ix->graphs)
+        if (e.key == key) {
+            NRLSH_CK(cudaGraphLaunch(e.exec, st));
+            return NRLSH_OK;
+        }
+    nrlsh_graph_entry e;
+    e.key = key;
+    for (size_t b : batch_ws_sizes(ix, nq, cap, ctas)) {
+        void* q = nullptr;
+        cudaError_t err = cudaMalloc(&q, std::max<size_t>(b, 16));
+        if (err != cudaSuccess) {
+            for (void* x : e.workspace) cudaFree(x);
+            return cuda_status(err, "cudaMalloc (graph workspace)");
+        }
+        e.workspace.push_back(q);
+    }
+    BatchWs w;
+    batch_ws_assign(w, e.workspace, ix, nq, ctas);
+    cudaGraph_t gr = nullptr;
+    NRLSH_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const nrlsh_status rs = run_batched(ix, queries, nq, ks, budgets, k_max, cap, cfg, w, ids,
+                                        scores, st);
+    const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+    if (rs != NRLSH_OK || ce != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        for (void* x : e.workspace) cudaFree(x);
+        return rs != NRLSH_OK ? rs : cuda_status(ce, "cudaStreamEndCapture");
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ie != cudaSuccess) {
+        for (void* x : e.workspace) cudaFree(x);
+        return cuda_status(ie, "cudaGraphInstantiate");
+    }
+    NRLSH_CK(cudaGraphLaunch(e.exec, st));
+    ix->graphs.push_back(std::move(e));
+    return NRLSH_OK;
+}
+
+extern "C" NRLSH_API nrlsh_status nrlsh_get_tuning(const nrlsh_index* ix, int32_t* hist_qb,
+                                                   int32_t* ctas_per_sm) {
+    if (!ix) return arg_error("index is NULL");
+    std::lock_guard<std::mutex> g(ix->batch_mu);
+    if (hist_qb) *hist_qb = ix->last_cfg.hist_qb;
+    if (ctas_per_sm) *ctas_per_sm = ix->last_cfg.ctas_per_sm;
+    return NRLSH_OK;
+}
 
 // ============================================================ no-allocation
 // nrlsh_query_noalloc: the query path of nrlsh_query_ex for callers that must

@@ -148,8 +148,10 @@ cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, doubl
 
 cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnorm,
                                   cudaStream_t st);
+// queries_per_block: 32, 64 or 128 (the autotuned tile).
 cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, int64_t nq, int m,
-                        int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st);
+                        int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st,
+                        int queries_per_block = 64);
 struct Boundary {
     int32_t j;       // boundary bucket (j*, l*)
     int32_t l;
@@ -181,6 +183,16 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
                                 const int32_t* ks, uint32_t* cand, float* lo, float* hi,
                                 uint32_t* cont, double* cont_s, int64_t cap, int64_t* out_ids,
                                 float* out_scores, int out_ld, cudaStream_t st);
+// Persistent batched form: `ctas` CTAs pull queries from *work (zeroed by the caller).
+cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
+                                           int64_t n, const int64_t* budgets, const void* codes,
+                                           const void* qcodes, int code_bytes, const void* Xp,
+                                           nrlsh_dtype dt, int dp, int d, const float* Q,
+                                           const float* xnorm, const float* qnorm,
+                                           const uint32_t* perm, const int32_t* ks, int k_max,
+                                           uint32_t* slabs, int64_t cap, int ctas, unsigned* work,
+                                           int64_t nq, int64_t* out_ids, float* out_scores,
+                                           cudaStream_t st);
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
                                const uint32_t* perm, int64_t nq, int32_t* out, int64_t out_cap,
                                int64_t* count, cudaStream_t st);

@@ -69,14 +69,13 @@ __global__ void row_norm_bound_kernel(const float* __restrict__ Q, int64_t nq, i
 
 // --------------------------------------------------------------- histogram
 
-constexpr int kHistQ = 64;  // queries per block, one per thread
 
-// Block: one position tile (inside one sub-dataset) x 64 queries.  The tile's
+// Block: one position tile (inside one sub-dataset) x kHistQ queries (one per thread).  The tile's
 // codes sit in shared memory and are read by broadcast; each thread keeps two
 // private histogram columns (uint16, even and odd positions, so consecutive
 // increments do not wait on each other) indexed [l][thread], so increments
 // never conflict on a bank.  Tiles hold at most 4,096 codes.
-template <typename C>
+template <typename C, int kHistQ>
 __global__ void __launch_bounds__(kHistQ)
     hist_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t nq, int m, int L,
                 const PosTile* __restrict__ tiles, uint32_t* __restrict__ H) {
@@ -426,7 +425,7 @@ constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
 // arg-max.  qs holds the query (fp32 values, exact in FP64).
 template <typename T>
 __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict__ hiq,
-                         const uint32_t* __restrict__ candq, int64_t count, int kq,
+                         const uint32_t* __restrict__ candq, int64_t count, int kq, int k_out,
                          const T* __restrict__ Xp, int dp, int d, const float* qs,
                          const uint32_t* __restrict__ perm, uint32_t* __restrict__ contq,
                          double* __restrict__ contsq, int64_t* __restrict__ ids_out,
@@ -535,7 +534,7 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
         }
         __syncthreads();
     }
-    for (int r = kk_out + threadIdx.x; r < kq; r += 256) {
+    for (int r = kk_out + threadIdx.x; r < k_out; r += 256) {
         ids_out[r] = -1;
         sc_out[r] = -INFINITY;
     }
@@ -554,8 +553,8 @@ __global__ void __launch_bounds__(256)
     load_query(Q, q, d, dp, qs);
     __syncthreads();
     const Boundary b = bnd[q];
-    dev_topk(lo + q * cap, hi + q * cap, cand + q * cap, (int64_t)b.full + b.r, ks ? ks[q] : k, Xp,
-             dp, d, qs, perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld,
+    dev_topk(lo + q * cap, hi + q * cap, cand + q * cap, (int64_t)b.full + b.r, ks ? ks[q] : k,
+             out_ld, Xp, dp, d, qs, perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld,
              out_scores + q * out_ld);
 }
 
@@ -589,8 +588,54 @@ __global__ void __launch_bounds__(256)
     const int64_t count = (int64_t)b.full + b.r;
     dev_rerank(Xp, dp, qs, candq, 0, count, xnorm, qnorm[q], kappa, lo + q * cap, hi + q * cap);
     __syncthreads();
-    dev_topk(lo + q * cap, hi + q * cap, candq, count, ks ? ks[q] : k, Xp, dp, d, qs, perm,
+    dev_topk(lo + q * cap, hi + q * cap, candq, count, ks ? ks[q] : k, out_ld, Xp, dp, d, qs, perm,
              cont + q * cap, cont_s + q * cap, out_ids + q * out_ld, out_scores + q * out_ld);
+}
+
+// Persistent form: CTAs take queries from a device work counter until it passes
+// nq, each reusing its own scratch slab (cand, lo, hi, cont: cap words each;
+// cont_s: cap doubles).  Per-query budgets and k; rows of the outputs are k_max
+// wide, padded with (-1, -inf).
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    probe_rerank_persistent_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order,
+                                   int m, int L, int64_t n, const int64_t* __restrict__ budgets,
+                                   const C* __restrict__ codes, const C* __restrict__ qcodes,
+                                   const T* __restrict__ Xp, int dp, int d,
+                                   const float* __restrict__ Q, const float* __restrict__ xnorm,
+                                   const float* __restrict__ qnorm, float kappa,
+                                   const uint32_t* __restrict__ perm, const int32_t* __restrict__ ks,
+                                   int k_max, uint32_t* __restrict__ slabs, int64_t cap,
+                                   unsigned* __restrict__ work, int64_t nq,
+                                   int64_t* __restrict__ out_ids, float* __restrict__ out_scores) {
+    extern __shared__ __align__(16) float qs[];
+    uint32_t* cntj = (uint32_t*)(qs + dp);
+    uint8_t* lam_s = (uint8_t*)(cntj + m);
+    __shared__ int64_t q_s;
+    uint32_t* slab = slabs + (size_t)blockIdx.x * 6 * cap;
+    uint32_t* cand = slab;
+    float* lo = (float*)(slab + cap);
+    float* hi = (float*)(slab + 2 * cap);
+    uint32_t* cont = slab + 3 * cap;
+    double* cont_s = (double*)(slab + 4 * cap);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) q_s = (int64_t)atomicAdd(work, 1u);
+        __syncthreads();
+        const int64_t q = q_s;
+        if (q >= nq) break;
+        load_query(Q, q, d, dp, qs);
+        const int64_t Bq = min(max(budgets[q], (int64_t)1), cap);
+        const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n, Bq, 0u, cntj, lam_s);
+        dev_select(codes, qcodes[q], n, m, L, lam_s, b, cand);
+        __syncthreads();
+        const int64_t count = (int64_t)b.full + b.r;
+        dev_rerank(Xp, dp, qs, cand, 0, count, xnorm, qnorm[q], kappa, lo, hi);
+        __syncthreads();
+        dev_topk(lo, hi, cand, count, min(max(ks[q], 1), k_max), k_max, Xp, dp, d, qs, perm, cont,
+                 cont_s,
+                 out_ids + q * k_max, out_scores + q * k_max);
+    }
 }
 
 __global__ void cand_to_ids_kernel(const uint32_t* __restrict__ cand, int64_t cap,
@@ -617,14 +662,32 @@ cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnor
 }
 
 cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, int64_t nq, int m,
-                        int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st) {
-    const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nq, kHistQ));
-    const size_t smem = 16384 + 2 * sizeof(uint16_t) * (size_t)(L + 1) * kHistQ;
-    if (code_bytes == 4)
-        return launch("hist_u32", hist_kernel<uint32_t>, grid, dim3(kHistQ), smem, st,
-                      (const uint32_t*)codes, (const uint32_t*)qcodes, nq, m, L, tiles, H);
-    return launch("hist_u64", hist_kernel<uint64_t>, grid, dim3(kHistQ), smem, st,
-                  (const uint64_t*)codes, (const uint64_t*)qcodes, nq, m, L, tiles, H);
+                        int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st,
+                        int queries_per_block) {
+    const int qb = queries_per_block;
+    const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nq, qb));
+    const size_t smem = 16384 + 2 * sizeof(uint16_t) * (size_t)(L + 1) * qb;
+#define NRLSH_H(C_, Q_)                                                                     \
+    {                                                                                       \
+        if (smem > 48 * 1024) {                                                             \
+            cudaError_t e = cudaFuncSetAttribute(hist_kernel<C_, Q_>,                       \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                 (int)smem);                                \
+            if (e != cudaSuccess) return e;                                                 \
+        }                                                                                   \
+        return launch(sizeof(C_) == 4 ? "hist_u32" : "hist_u64", hist_kernel<C_, Q_>, grid,  \
+                      dim3(Q_), smem, st, (const C_*)codes, (const C_*)qcodes, nq, m, L, tiles, \
+                      H);                                                                   \
+    }
+    if (code_bytes == 4) {
+        if (qb == 32) NRLSH_H(uint32_t, 32)
+        if (qb == 128) NRLSH_H(uint32_t, 128)
+        NRLSH_H(uint32_t, 64)
+    }
+    if (qb == 32) NRLSH_H(uint64_t, 32)
+    if (qb == 128) NRLSH_H(uint64_t, 128)
+    NRLSH_H(uint64_t, 64)
+#undef NRLSH_H
 }
 
 cudaError_t launch_threshold(const uint32_t* H, const uint32_t* order, int m, int L, int64_t nq,
@@ -711,6 +774,39 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
     if (code_bytes == 4) NRLSH_PR(float, uint32_t, "probe_rerank")
     NRLSH_PR(float, uint64_t, "probe_rerank")
 #undef NRLSH_PR
+}
+
+cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
+                                           int64_t n, const int64_t* budgets, const void* codes,
+                                           const void* qcodes, int code_bytes, const void* Xp,
+                                           nrlsh_dtype dt, int dp, int d, const float* Q,
+                                           const float* xnorm, const float* qnorm,
+                                           const uint32_t* perm, const int32_t* ks, int k_max,
+                                           uint32_t* slabs, int64_t cap, int ctas, unsigned* work,
+                                           int64_t nq, int64_t* out_ids, float* out_scores,
+                                           cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)dp + (sizeof(uint32_t) + 1) * (size_t)m;
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+#define NRLSH_PP(T_, C_, NAME)                                                                  \
+    {                                                                                           \
+        auto kern = probe_rerank_persistent_kernel<T_, C_>;                                     \
+        if (smem > 48 * 1024) {                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                 (int)smem);                                    \
+            if (e != cudaSuccess) return e;                                                     \
+        }                                                                                       \
+        return launch(NAME, kern, dim3((unsigned)ctas), dim3(256), smem, st, H, order, m, L, n,  \
+                      budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q,    \
+                      xnorm, qnorm, kappa, perm, ks, k_max, slabs, cap, work, nq, out_ids,      \
+                      out_scores);                                                              \
+    }
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_PP(__nv_bfloat16, uint32_t, "probe_rerank_persistent_bf16")
+        NRLSH_PP(__nv_bfloat16, uint64_t, "probe_rerank_persistent_bf16")
+    }
+    if (code_bytes == 4) NRLSH_PP(float, uint32_t, "probe_rerank_persistent")
+    NRLSH_PP(float, uint64_t, "probe_rerank_persistent")
+#undef NRLSH_PP
 }
 
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,

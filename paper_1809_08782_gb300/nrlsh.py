@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libnrlsh.so")
 NRLSH_F32 = 0
 NRLSH_BF16 = 1
 NRLSH_WHOLE_BUCKETS = 0x1
+NRLSH_QUERY_GRAPH = 0x2
 
 _STATUS = {0: "NRLSH_OK", -1: "NRLSH_ERR_ARG", -2: "NRLSH_ERR_OOM", -3: "NRLSH_ERR_CUDA",
            -4: "NRLSH_ERR_TIMEOUT", -5: "NRLSH_ERR_UNSUPPORTED"}
@@ -36,6 +37,8 @@ SIGNATURES = {
     "nrlsh_query": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P]),
     "nrlsh_query_ex": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _P, _P, _P]),
     "nrlsh_query_noalloc": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P]),
+    "nrlsh_query_batched": (_I32, [_P, _P, _I64, _P, _P, _I32, _I64, _U32, _P, _P, _P]),
+    "nrlsh_get_tuning": (_I32, [_P, _P, _P]),
     "nrlsh_hash_queries": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_histograms": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_candidates": (_I32, [_P, _P, _I64, _I64, _U32, _I64, _P, _P, _P]),
@@ -226,6 +229,34 @@ def nrlsh_query_noalloc(index: Index, queries: torch.Tensor, k: int, probe_budge
                                    probe_budget, _ptr(ids), _ptr(scores),
                                    _stream(queries, stream)))
     return ids, scores
+
+
+def nrlsh_query_batched(index: Index, queries: torch.Tensor, ks: torch.Tensor,
+                        budgets: torch.Tensor, k_max: int, budget_max: int, flags: int = 0,
+                        stream=None, ids: Optional[torch.Tensor] = None,
+                        scores: Optional[torch.Tensor] = None):
+    """Batched queries with per-query k (int32) and budgets (int64): persistent fused
+    probe/re-rank kernel, autotuned tiles, optional CUDA-graph replay
+    (NRLSH_QUERY_GRAPH).  Returns (ids, scores), rows k_max wide."""
+    lib = load()
+    queries = _queries(index, queries)
+    nq = queries.shape[0]
+    ks = ks.to(torch.int32).contiguous()
+    budgets = budgets.to(torch.int64).contiguous()
+    if ids is None:
+        ids = torch.empty((nq, k_max), dtype=torch.int64, device=queries.device)
+    if scores is None:
+        scores = torch.empty((nq, k_max), dtype=torch.float32, device=queries.device)
+    _check(lib.nrlsh_query_batched(index.handle, _ptr(queries), nq, _ptr(ks), _ptr(budgets),
+                                   k_max, budget_max, flags, _ptr(ids), _ptr(scores),
+                                   _stream(queries, stream)))
+    return ids, scores
+
+
+def nrlsh_get_tuning(index: Index):
+    qb, cps = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().nrlsh_get_tuning(index.handle, ctypes.byref(qb), ctypes.byref(cps)))
+    return {"hist_queries_per_block": qb.value, "ctas_per_sm": cps.value}
 
 
 def nrlsh_hash_queries(index: Index, queries: torch.Tensor, stream=None) -> torch.Tensor:
