@@ -437,6 +437,60 @@ def profile_case(args):
                       "launches": {k: v[1] for k, v in prof.items()}}))
 
 
+def serve_sweep(args):
+    """Serving run (not the bench line): the resident serving preset, Poisson
+    arrivals at geometrically increasing rates through the continuous-batching
+    server, p50/p99 latency and achieved queries/s per rate; and, as the plain
+    comparison, the same requests one at a time through nrlsh_query_ex."""
+    import torch
+
+    import paper_1809_08782_gb300.nrlsh as N
+    from paper_1809_08782_gb300 import build as B
+    from paper_1809_08782_gb300.serving import Request, Server, latency_summary
+    B.build()
+    N.load()
+    w = W.make_workload("serving-n10m-d128", n=args.serve_n, with_data=False)
+    items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, w.dtype)
+    X = W.to_torch(items, w.dtype, "cuda")
+    del items
+    eps = float(np.float32(0.2))
+    idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=N.NRLSH_PROJECT_TENSOR)
+    torch.cuda.synchronize()
+    nreq = args.serve_requests
+    Q = W.gen_queries(nreq, w.d, w.query_seed)
+    budgets, ks = W.per_query_budgets_and_k(nreq, w.n, 0.0005, 0.01, seed=5000)
+    # plain: one request at a time, single-query path, synchronous
+    plain_n = min(nreq, 300)
+    t0 = time.perf_counter()
+    for i in range(plain_n):
+        ids, sc = N.nrlsh_query_ex(idx, torch.from_numpy(Q[i:i + 1]).cuda(), int(ks[i]),
+                                   int(budgets[i]))
+        ids.cpu()
+    plain_qps = plain_n / (time.perf_counter() - t0)
+    # tune the batched tiles once on a full-size batch
+    N.nrlsh_query_batched(idx, torch.from_numpy(Q[:1024]).cuda(), torch.from_numpy(ks[:1024]).cuda(),
+                          torch.from_numpy(budgets[:1024]).cuda(), 100, int(budgets.max()))
+    torch.cuda.synchronize()
+    print(json.dumps({"serving": "plain_one_at_a_time", "n": w.n, "d": w.d,
+                      "queries_per_s": plain_qps, "requests": plain_n}), flush=True)
+    rng = np.random.default_rng(5001)
+    rate = args.serve_rate0
+    for _ in range(args.serve_rates):
+        reqs = [Request(i, Q[i], int(ks[i]), int(budgets[i])) for i in range(nreq)]
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        srv = Server(idx, slots=4, memory_budget=args.serve_memory << 20, max_batch=4096)
+        srv.serve(reqs, arrivals)
+        summ = latency_summary(reqs)
+        summ.update({"serving": "continuous_batching", "offered_queries_per_s": rate, "n": w.n,
+                     "d": w.d, "batches": srv.batches, "max_concurrent_batches": srv.max_concurrent,
+                     "memory_budget_mb": args.serve_memory,
+                     "tuning": N.nrlsh_get_tuning(idx)})
+        print(json.dumps(summ), flush=True)
+        if summ["p99_ms"] > 1000.0:
+            break
+        rate *= 2
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,10 +506,19 @@ def main():
                     help="kernel timing run of one phase instead of the bench line")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS))
     ap.add_argument("--queries", type=int, default=1000, help="queries (profile runs)")
+    ap.add_argument("--serve", action="store_true", help="serving sweep instead of the bench line")
+    ap.add_argument("--serve-n", type=int, default=10_000_000)
+    ap.add_argument("--serve-requests", type=int, default=20_000)
+    ap.add_argument("--serve-rate0", type=float, default=25_000.0)
+    ap.add_argument("--serve-rates", type=int, default=7)
+    ap.add_argument("--serve-memory", type=int, default=8192, help="admission budget, MB")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.profile_case:
         profile_case(args)
+        return
+    if args.serve:
+        serve_sweep(args)
         return
     if args.impl == "reference":
         for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):

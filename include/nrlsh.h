@@ -173,10 +173,17 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* index, const float* que
  * host pointers like the other arrays.
  */
 #define NRLSH_QUERY_GRAPH 0x2u
+#define NRLSH_QUERY_NO_TUNE 0x4u   /* skip the autotuner: last tuned (or default) tiles */
 NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* index, const float* queries,
                                            int64_t nq, const int32_t* ks, const int64_t* budgets,
                                            int32_t k_max, int64_t budget_max, uint32_t flags,
                                            int64_t* ids, float* scores, void* stream);
+/* Device scratch (bytes) one nrlsh_query_batched call with these sizes allocates
+ * from the stream-ordered pool (device-pointer arguments, no graph), for callers
+ * that admit work by memory. */
+NRLSH_API nrlsh_status nrlsh_batched_scratch_bytes(const nrlsh_index* index, int64_t nq,
+                                                   int32_t k_max, int64_t budget_max,
+                                                   int64_t* bytes);
 /* The autotuned configuration last used for this index: histogram queries per
  * block and persistent CTAs per SM (0, 0 before any batched call). */
 NRLSH_API nrlsh_status nrlsh_get_tuning(const nrlsh_index* index, int32_t* hist_queries_per_block,

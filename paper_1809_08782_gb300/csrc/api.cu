@@ -978,7 +978,7 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     NRLSH_CKS(check_query_args(ix, queries, nq));
     if (k_max < 1 || k_max > NRLSH_MAX_K) return arg_error("need 1 <= k_max <= 1024");
     if (budget_max < 1) return arg_error("need budget_max >= 1");
-    if (flags & ~NRLSH_QUERY_GRAPH) return arg_error("unknown flags");
+    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE)) return arg_error("unknown flags");
     if (nq > 0 && (!ids || !scores || !ks || !budgets)) return arg_error("NULL array");
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1006,6 +1006,8 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
         auto it = ix->tuned.find(key);
         if (it != ix->tuned.end()) {
             cfg = it->second;
+        } else if (flags & NRLSH_QUERY_NO_TUNE) {
+            if (ix->last_cfg.hist_qb) cfg = ix->last_cfg;
         } else {
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
             if (st) cudaStreamIsCapturing(st, &cs);
@@ -1073,6 +1075,25 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     }
     NRLSH_CK(cudaGraphLaunch(e.exec, st));
     ix->graphs.push_back(std::move(e));
+    return NRLSH_OK;
+}
+
+extern "C" NRLSH_API nrlsh_status nrlsh_batched_scratch_bytes(const nrlsh_index* ix, int64_t nq,
+                                                              int32_t k_max, int64_t budget_max,
+                                                              int64_t* bytes) {
+    if (!ix || !bytes) return arg_error("NULL argument");
+    if (nq < 0 || k_max < 1 || budget_max < 1) return arg_error("bad sizes");
+    nrlsh_batch_cfg cfg;
+    {
+        std::lock_guard<std::mutex> g(ix->batch_mu);
+        if (ix->last_cfg.hist_qb) cfg = ix->last_cfg;
+    }
+    const int64_t cap = std::min<int64_t>(budget_max, ix->n);
+    int64_t total = 0;
+    for (size_t b : batch_ws_sizes(ix, std::max<int64_t>(nq, 1), cap, batch_ctas(cfg, cap)))
+        total += (int64_t)((std::max<size_t>(b, 16) + 255) / 256 * 256);
+    (void)k_max;
+    *bytes = total;
     return NRLSH_OK;
 }
 

@@ -22,6 +22,7 @@ NRLSH_F32 = 0
 NRLSH_BF16 = 1
 NRLSH_WHOLE_BUCKETS = 0x1
 NRLSH_QUERY_GRAPH = 0x2
+NRLSH_QUERY_NO_TUNE = 0x4
 
 _STATUS = {0: "NRLSH_OK", -1: "NRLSH_ERR_ARG", -2: "NRLSH_ERR_OOM", -3: "NRLSH_ERR_CUDA",
            -4: "NRLSH_ERR_TIMEOUT", -5: "NRLSH_ERR_UNSUPPORTED"}
@@ -39,6 +40,7 @@ SIGNATURES = {
     "nrlsh_query_noalloc": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P]),
     "nrlsh_query_batched": (_I32, [_P, _P, _I64, _P, _P, _I32, _I64, _U32, _P, _P, _P]),
     "nrlsh_get_tuning": (_I32, [_P, _P, _P]),
+    "nrlsh_batched_scratch_bytes": (_I32, [_P, _I64, _I32, _I64, _P]),
     "nrlsh_hash_queries": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_histograms": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_candidates": (_I32, [_P, _P, _I64, _I64, _U32, _I64, _P, _P, _P]),
@@ -251,6 +253,13 @@ def nrlsh_query_batched(index: Index, queries: torch.Tensor, ks: torch.Tensor,
                                    k_max, budget_max, flags, _ptr(ids), _ptr(scores),
                                    _stream(queries, stream)))
     return ids, scores
+
+
+def nrlsh_batched_scratch_bytes(index: Index, nq: int, k_max: int, budget_max: int) -> int:
+    out = ctypes.c_int64()
+    _check(load().nrlsh_batched_scratch_bytes(index.handle, nq, k_max, budget_max,
+                                              ctypes.byref(out)))
+    return out.value
 
 
 def nrlsh_get_tuning(index: Index):
