@@ -52,6 +52,23 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def reduce_max(value: float, device=None) -> float:
+    """Max of a per-rank value over all ranks (identity without a process group).
+    Each rank times its own replica; the job is as slow as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job units per second: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -205,16 +222,13 @@ def gpu_arm(args):
     per_form = {}
     for name, proj in forms.items():
         times, launches = timed(proj)
-        t = torch.tensor([float(np.mean(times))], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        per_form[name] = (float(t.item()), times, launches, proj)
+        per_form[name] = (reduce_max(float(np.mean(times)), dev), times, launches, proj)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if rank == 0 else None
     best = min(per_form, key=lambda k: per_form[k][0])
     ms_max, times, launches, best_proj = per_form[best]
-    value = w.nq * world / (ms_max / 1e3)
+    value = job_throughput(w.nq, world, ms_max)
 
     # -------- per-kernel times: the same steps again with event brackets on
     N.nrlsh_set_profiling(True)
@@ -243,11 +257,7 @@ def gpu_arm(args):
         ix.free()
         if i >= args.warmup:
             e2e_t.append(t1 - t0)
-    e2e_ms = float(np.mean(e2e_t)) * 1e3
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = w.nq * world / (float(te.item()) / 1e3)
+    e2e_value = job_throughput(w.nq, world, reduce_max(float(np.mean(e2e_t)) * 1e3, dev))
 
     if rank == 0:
         line = {
@@ -256,7 +266,7 @@ def gpu_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded Gaussian directions, lognormal norms)",
             "form": best,
-            "forms": {k: {"queries_per_s": w.nq * world / (v[0] / 1e3), "ms_per_step": v[0],
+            "forms": {k: {"queries_per_s": job_throughput(w.nq, world, v[0]), "ms_per_step": v[0],
                           "p50_ms": float(np.percentile(v[1], 50)),
                           "p99_ms": float(np.percentile(v[1], 99))}
                       for k, v in per_form.items()},
