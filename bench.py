@@ -501,6 +501,99 @@ def serve_sweep(args):
         rate *= 2
 
 
+def batched_run(args):
+    """Batching form (not the bench line): the ImageNet-sized preset, 100,000
+    queries with per-query budgets uniform in [0.1%, 5%] of n and k in {1, 10, 100},
+    one nrlsh_query_batched call replayed as a CUDA graph; queries/s, recall@10 on
+    a subset, and the plain single-query path on a subset at the mean budget."""
+    import torch
+
+    import paper_1809_08782_gb300.nrlsh as N
+    from paper_1809_08782_gb300 import build as B
+    from paper_1809_08782_gb300 import curves as C
+    B.build()
+    N.load()
+    w = W.make_workload("imagenet-n2340373-d150", nq=args.queries, with_data=False)
+    items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, w.dtype)
+    X = W.to_torch(items, w.dtype, "cuda")
+    del items
+    eps = float(np.float32(args.eps if args.eps is not None else 0.3))
+    idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=N.NRLSH_PROJECT_TENSOR)
+    Qh = W.gen_queries(w.nq, w.d, w.query_seed)
+    budgets, ks = W.per_query_budgets_and_k(w.nq, w.n, 0.001, 0.05, seed=4000)
+    Q = torch.from_numpy(Qh).cuda()
+    ksd = torch.from_numpy(ks).cuda()
+    bd = torch.from_numpy(budgets).cuda()
+    k_max, bmax = int(ks.max()), int(budgets.max())
+    ids = torch.empty((w.nq, k_max), dtype=torch.int64, device="cuda")
+    sc = torch.empty((w.nq, k_max), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    times = []
+    with torch.cuda.stream(st):
+        for i in range(args.warmup + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            N.nrlsh_query_batched(idx, Q, ksd, bd, k_max, bmax, flags=N.NRLSH_QUERY_GRAPH, ids=ids,
+                                  scores=sc)
+            e1.record(st)
+            e1.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    sub = min(w.nq, 500)
+    truth = C.exact_topk(idx, Q[:sub])
+    got = ids[:sub, :10].cpu().numpy()
+    mask = ks[:sub] >= 10
+    rec = C.recall(got[mask], truth[mask])
+    # plain comparison: single-query path (FP32 CUDA-core projection index) at the mean budget
+    idx_plain = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=N.NRLSH_PROJECT_SIMT)
+    mb = int(budgets.mean())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    N.nrlsh_query_ex(idx_plain, Q[:2000], 10, mb)
+    torch.cuda.synchronize()
+    plain_qps = 2000 / (time.perf_counter() - t0)
+    print(json.dumps({"batched": True, "workload": w.name, "n": w.n, "d": w.d, "queries": w.nq,
+                      "ms_per_batch": ms, "queries_per_s": w.nq / (ms / 1e3),
+                      "recall_at_10_subset": rec, "eps": eps, "mean_budget": mb,
+                      "tuning": N.nrlsh_get_tuning(idx),
+                      "plain_single_query_path_queries_per_s_at_mean_budget": plain_qps}),
+          flush=True)
+
+
+def curves_run(args):
+    """Probed items vs recall@10 (Figure 2 protocol) on the synthetic stand-ins:
+    RANGE-LSH vs SIMPLE-LSH at L = 16/32/64 with m = 32/64/128 (Section 5), and an
+    m sweep at L = 32 (Figure 3b).  Prints JSON lines (not the bench line)."""
+    import torch
+
+    import paper_1809_08782_gb300.nrlsh as N
+    from paper_1809_08782_gb300 import build as B
+    from paper_1809_08782_gb300 import curves as C
+    B.build()
+    N.load()
+    for name in args.curve_workloads.split(","):
+        w = W.make_workload(name, nq=args.queries, with_data=False)
+        items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, w.dtype)
+        X = W.to_torch(items, w.dtype, "cuda")
+        Q = torch.from_numpy(W.gen_queries(w.nq, w.d, w.query_seed)).cuda()
+        idx = N.nrlsh_build_ex(X, 1, 8, w.index_seed)
+        truth = C.exact_topk(idx, Q)
+        idx.free()
+        eps = float(np.float32(args.eps if args.eps is not None else 0.1))
+        for L, m in ((16, 32), (32, 64), (64, 128)):
+            r = C.compare(X, Q, L, m, w.index_seed, eps, truth)
+            r.update({"workload": name, "queries": w.nq, "eps": eps})
+            print(json.dumps(r), flush=True)
+        if name.startswith("yahoo"):
+            for m in (32, 64, 128, 256):
+                r = C.compare(X, Q, 32, m, w.index_seed, eps, truth)
+                r.update({"workload": name, "queries": w.nq, "eps": eps, "m_sweep": True})
+                print(json.dumps(r), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -517,6 +610,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS))
     ap.add_argument("--queries", type=int, default=1000, help="queries (profile runs)")
     ap.add_argument("--serve", action="store_true", help="serving sweep instead of the bench line")
+    ap.add_argument("--curves", action="store_true", help="probed-item/recall curves")
+    ap.add_argument("--batched", action="store_true", help="batching-form run (ImageNet-sized)")
+    ap.add_argument("--curve-workloads", default="netflix-n17770-d300,yahoo-n136736-d300")
     ap.add_argument("--serve-n", type=int, default=10_000_000)
     ap.add_argument("--serve-requests", type=int, default=20_000)
     ap.add_argument("--serve-rate0", type=float, default=25_000.0)
@@ -529,6 +625,12 @@ def main():
         return
     if args.serve:
         serve_sweep(args)
+        return
+    if args.curves:
+        curves_run(args)
+        return
+    if args.batched:
+        batched_run(args)
         return
     if args.impl == "reference":
         for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):

@@ -1,0 +1,95 @@
+"""Probed-item / recall curves (the protocol of Figure 2 and Figure 3b of the
+paper) and bucket-balance statistics, run through the library.
+
+* SIMPLE-LSH is norm-ranging LSH with one sub-dataset (m = 1): one global U.
+* Codes are compared at equal total code length: as in Section 5, the
+  ceil(log2 m) bits that address a sub-dataset count against RANGE-LSH's
+  length, so it hashes L - ceil(log2 m) bits while SIMPLE-LSH hashes L.
+* Buckets are probed whole (NRLSH_WHOLE_BUCKETS) at budgets 2^i, so the probed
+  count can overshoot the budget exactly as the paper's x-values do; the
+  x-value reported is the mean number of probed items per query.
+* recall@10 = |returned top-10 and exact top-10| / 10, averaged over queries;
+  the exact top-10 is the library's own result at B = n (the full re-rank,
+  which the parity tests pin to exact MIPS).
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List
+
+import numpy as np
+import torch
+
+from . import nrlsh as N
+
+
+def exact_topk(idx: "N.Index", Q: torch.Tensor, k: int = 10, chunk: int = 256) -> np.ndarray:
+    out = []
+    for i in range(0, Q.shape[0], chunk):
+        ids, _ = N.nrlsh_query_ex(idx, Q[i:i + chunk], k, idx.n)
+        out.append(ids.cpu().numpy())
+    return np.concatenate(out)
+
+
+def recall(found: np.ndarray, truth: np.ndarray) -> float:
+    k = truth.shape[1]
+    return float(np.mean([len(set(found[i][found[i] >= 0]) & set(truth[i]))
+                          for i in range(len(truth))])) / k
+
+
+def probed_counts(idx: "N.Index", Q: torch.Tensor, B: int, chunk: int = 64) -> np.ndarray:
+    counts = []
+    for i in range(0, Q.shape[0], chunk):
+        _, c = N.nrlsh_query_candidates(idx, Q[i:i + chunk], B, flags=N.NRLSH_WHOLE_BUCKETS,
+                                        cap=idx.n)
+        counts.append(c.cpu().numpy())
+    return np.concatenate(counts)
+
+
+def curve(items: torch.Tensor, Q: torch.Tensor, truth: np.ndarray, m: int, L_hash: int, seed: int,
+          eps: float, budgets: List[int]) -> List[Dict]:
+    idx = N.nrlsh_build_ex(items, m, L_hash, seed, eps=eps)
+    pts = []
+    for B in budgets:
+        ids, _ = N.nrlsh_query_ex(idx, Q, 10, B, flags=N.NRLSH_WHOLE_BUCKETS)
+        pts.append({"budget": int(B), "probed": float(probed_counts(idx, Q, B).mean()),
+                    "recall": recall(ids.cpu().numpy(), truth)})
+        if pts[-1]["recall"] >= 0.999:
+            break
+    pts_stats = bucket_stats(idx)
+    idx.free()
+    return [{"points": pts, **pts_stats}]
+
+
+def bucket_stats(idx: "N.Index") -> Dict:
+    """Number of non-empty buckets (sub-dataset, code) and the largest bucket
+    (the bucket-balance figures of Sections 3.1 and 3.2)."""
+    codes = N.nrlsh_get_codes(idx).numpy().view(np.uint64)
+    sub, _, _ = N.nrlsh_get_partition(idx)
+    key = (sub.numpy().astype(np.uint64) << np.uint64(58)) ^ codes
+    _, counts = np.unique(key, return_counts=True)
+    return {"buckets": int(counts.size), "largest_bucket": int(counts.max())}
+
+
+def compare(items: torch.Tensor, Q: torch.Tensor, L: int, m: int, seed: int, eps: float,
+            truth: np.ndarray = None) -> Dict:
+    """RANGE-LSH (m sub-datasets, L - ceil(log2 m) hash bits) versus SIMPLE-LSH
+    (m = 1, L hash bits) at total code length L."""
+    n = items.shape[0]
+    if truth is None:
+        idx = N.nrlsh_build_ex(items, 1, 8, seed)
+        truth = exact_topk(idx, Q)
+        idx.free()
+    budgets = [2 ** i for i in range(4, int(math.ceil(math.log2(n))) + 1)]
+    L_range = L - int(math.ceil(math.log2(m)))
+    return {"L": L, "m": m, "L_hash_range": L_range,
+            "range_lsh": curve(items, Q, truth, m, L_range, seed, eps, budgets)[0],
+            "simple_lsh": curve(items, Q, truth, 1, L, seed, eps, budgets)[0]}
+
+
+def probed_at_recall(points: List[Dict], target: float = 0.9):
+    """First point (probed, recall) with recall >= target, like the paper's tables."""
+    for p in points:
+        if p["recall"] >= target:
+            return p["probed"], p["recall"]
+    return None, None
