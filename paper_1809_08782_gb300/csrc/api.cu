@@ -52,6 +52,7 @@ struct nrlsh_index {
     void* codes = nullptr;         // n code words, position order
     uint32_t* order = nullptr;     // ncls bucket ids j*(L+1)+l in probing order
     double* shat_sorted = nullptr; // ncls
+    double* ccos = nullptr;        // L+1 bucket cosines c_l
     nrlsh::PosTile* tiles = nullptr;
     int32_t ntiles = 0;
     std::vector<nrlsh::PosTile> tiles_host;  // source of the asynchronous upload
@@ -204,6 +205,47 @@ void destroy(nrlsh_index* ix) {
     delete ix;
 }
 
+// A per-thread side stream for the data-independent parts of the build.  The
+// fork makes it wait for everything queued on the main stream so far; the join
+// (recorded after the side work) makes the main stream wait for the side work
+// at the point where the main stream's next consumer is queued.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~SideStream() {
+        if (s) cudaStreamDestroy(s);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+    }
+};
+thread_local SideStream t_side;
+
+cudaStream_t side_stream() { return t_side.s; }
+
+cudaError_t side_stream_fork(cudaStream_t main) {
+    if (!t_side.s) {
+        cudaError_t e = cudaStreamCreateWithFlags(&t_side.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t_side.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t_side.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaEventRecord(t_side.fork, main);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(t_side.s, t_side.fork, 0);
+}
+
+// Records the end of the side work; the main stream waits for it right away
+// (its own earlier work is unaffected, and the side kernels run meanwhile).
+cudaError_t side_stream_join(cudaStream_t main) {
+    cudaError_t e = cudaEventRecord(t_side.join, t_side.s);
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t side_stream_wait(cudaStream_t main) {
+    return cudaStreamWaitEvent(main, t_side.join, 0);
+}
+
 int bits_for(int64_t v) {  // smallest b with 2^b >= v
     int b = 0;
     while (((int64_t)1 << b) < v) ++b;
@@ -298,6 +340,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     B_CK(own(ix, (char**)&ix->codes, (size_t)n * ix->code_bytes));
     B_CK(own(ix, &ix->order, ix->ncls));
     B_CK(own(ix, &ix->shat_sorted, ix->ncls));
+    B_CK(own(ix, &ix->ccos, L + 1));
     B_CK(own(ix, &ix->ambiguous, 1));
     B_CK(own(ix, &ix->dev_err, 1));
     const bool tc = ix->projection == NRLSH_PROJECT_TENSOR;
@@ -329,7 +372,6 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(stage_in(sc, items, (size_t)n * d * esz, &X));
         uint64_t *keys, *keys_alt;
         uint32_t *vals, *vals_alt, *jkeys, *jkeys_alt;
-        double* bucket_keys;
         char* sort_tmp;
         unsigned long long *amb_list, *amb_list2 = nullptr;
         unsigned* amb_count2 = nullptr;
@@ -343,7 +385,6 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(sc.get(&vals_alt, n));
         B_CK(sc.get(&jkeys, n));
         B_CK(sc.get(&jkeys_alt, n));
-        B_CK(sc.get(&bucket_keys, ix->ncls));
         B_CK(sc.get(&sort_tmp, radix_sort_temp_bytes(n)));
         B_CK(sc.get(&amb_list, amb_cap));
         if (tc) {
@@ -356,8 +397,14 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned), st));
         B_CU(cudaMemsetAsync(ix->U2, 0, sizeof(double) * m, st));
         // A and the tiles of its columns (Eq. 4 projections)
+        // A and the bucket cosines depend only on (seed, d, L, eps): a side stream
+        // computes them while the main stream ranks the items
+        B_CU(side_stream_fork(st));
+        cudaStream_t side = side_stream();
         B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, ix->At, ix->dp, d, L, ix->Lp, seed,
-                                st));
+                                side));
+        B_CU(launch_class_cos(L, eps, ix->ccos, side));
+        B_CU(side_stream_join(st));
         // Algorithm 1: rank by norm, percentile partition, U_j
         B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
         bool alt = false;
@@ -374,6 +421,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
         B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, m, ix->s_id, ix->U2, ix->Xp,
                                  ix->Xb, ix->Xb2, ix->s_pos, ix->tau64, ix->tau32, ix->xnorm, st));
+        B_CU(side_stream_wait(st));  // A and the cosines are ready
         // Eq. 4: sign random projection codes
         if (!tc) {
             B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
@@ -395,7 +443,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                      ix->code_bytes, st));
         }
         // Eq. 12 and the sorted (U_j, l) structure
-        B_CU(launch_bucket_order(ix->U2, m, L, eps, ix->shat_sorted, ix->order, bucket_keys, st));
+        B_CU(launch_bucket_order(ix->U2, ix->ccos, m, L, ix->shat_sorted, ix->order, st));
     }
     if (!is_device_ptr(items)) B_CU(cudaStreamSynchronize(st));
 #undef B_CK

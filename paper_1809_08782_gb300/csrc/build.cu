@@ -254,6 +254,7 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kRadix = 256;
+constexpr int kLocalOffsetTiles = 64;  // up to this many tiles, no separate scan launch
 
 __device__ __forceinline__ bool digit_varies(const unsigned long long* varying, int shift) {
     return ((*varying >> shift) & 0xFFull) != 0;
@@ -325,17 +326,26 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// With local_offsets, `offsets` holds the raw tile counts of this digit and each
+// block derives its own (digit, tile) offsets: the counts of earlier tiles plus
+// an exclusive scan of the digit totals (for few tiles, instead of a scan
+// launch); `zero` (same size) is cleared for the pass after next.
 template <typename K, int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads)
     radix_scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                          K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
                          const unsigned long long* varying, const uint32_t* __restrict__ offsets,
-                         int ntiles, uint32_t* __restrict__ next_counts, int next_shift) {
+                         int ntiles, uint32_t* __restrict__ next_counts, int next_shift,
+                         int local_offsets, uint32_t* __restrict__ zero) {
     constexpr int kTile = kSortThreads * ROUNDS;
     const int64_t base = (int64_t)blockIdx.x * kTile;
     const bool count_next = next_counts != nullptr && digit_varies(varying, next_shift);
     __shared__ uint32_t run_off[kRadix];
     __shared__ uint32_t warp_cnt[kSortThreads / 32][kRadix];
+    if (zero)
+        for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < (int64_t)kRadix * ntiles;
+             i += (int64_t)gridDim.x * kSortThreads)
+            zero[i] = 0;
     if (!digit_varies(varying, shift)) {
         // keys keep their positions: this tile's next-digit histogram is local
         if (count_next) run_off[threadIdx.x] = 0;
@@ -354,7 +364,29 @@ __global__ void __launch_bounds__(kSortThreads)
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run_off[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    if (local_offsets) {
+        // thread = digit: count of this digit in earlier tiles, and in all tiles
+        const uint32_t* row = offsets + (int64_t)threadIdx.x * ntiles;
+        uint32_t before = 0, total = 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const uint32_t c = row[t];
+            before += t < (int)blockIdx.x ? c : 0u;
+            total += c;
+        }
+        uint32_t incl = total;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_cnt[0][warp] = incl;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += warp_cnt[0][w];
+        run_off[threadIdx.x] = wbase + incl - total + before;
+        __syncthreads();
+    } else {
+        run_off[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    }
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int round = 0; round < ROUNDS; ++round) {
         uint32_t* wc = &warp_cnt[0][0];
@@ -397,11 +429,16 @@ cudaError_t radix_sort_rounds(K* keys, uint32_t* vals, K* keys_alt, uint32_t* va
     constexpr int kTile = kSortThreads * ROUNDS;
     const int ntiles = (int)ceil_div(n, kTile);
     const int64_t total = (int64_t)kRadix * ntiles;
+    const bool local = ntiles <= kLocalOffsetTiles;
     unsigned long long* varying = (unsigned long long*)temp;
-    uint32_t* counts[2] = {(uint32_t*)((char*)temp + 256),
-                           (uint32_t*)((char*)temp + 256) + total};
+    uint32_t* counts[3] = {(uint32_t*)((char*)temp + 256), (uint32_t*)((char*)temp + 256) + total,
+                           (uint32_t*)((char*)temp + 256) + 2 * total};
     cudaError_t e = cudaMemsetAsync(varying, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    if (local) {  // the write buffer of the first pass must start at zero
+        e = cudaMemsetAsync(counts[1], 0, sizeof(uint32_t) * total, s);
+        if (e != cudaSuccess) return e;
+    }
     e = launch("radix_hist", radix_first_hist_kernel<K, ROUNDS>, dim3(ntiles), dim3(kSortThreads), 0,
                s, (const K*)keys, n, varying, counts[0], ntiles);
     if (e != cudaSuccess) return e;
@@ -409,22 +446,31 @@ cudaError_t radix_sort_rounds(K* keys, uint32_t* vals, K* keys_alt, uint32_t* va
     uint32_t* src_v = vals;
     K* dst_k = keys_alt;
     uint32_t* dst_v = vals_alt;
-    int cur = 0;
+    int r = 0, w = 1, z = 2;  // read, write (next digit), zero (the pass after next)
     for (int shift = 0; shift < key_bits; shift += 8) {
         const bool last = shift + 8 >= key_bits;
-        uint32_t* nxt = last ? nullptr : counts[cur ^ 1];
-        e = launch("radix_scan", radix_scan_kernel, dim3(1), dim3(1024), 0, s, counts[cur], total,
-                   shift, nxt, shift + 8, (const unsigned long long*)varying);
-        if (e != cudaSuccess) return e;
+        uint32_t* nxt = last ? nullptr : counts[w];
+        if (!local) {
+            e = launch("radix_scan", radix_scan_kernel, dim3(1), dim3(1024), 0, s, counts[r], total,
+                       shift, nxt, shift + 8, (const unsigned long long*)varying);
+            if (e != cudaSuccess) return e;
+        }
         e = launch("radix_scatter", radix_scatter_kernel<K, ROUNDS>, dim3(ntiles),
                    dim3(kSortThreads), 0, s, (const K*)src_k, (const uint32_t*)src_v, dst_k, dst_v,
-                   n, shift, (const unsigned long long*)varying, (const uint32_t*)counts[cur],
-                   ntiles, nxt, shift + 8);
+                   n, shift, (const unsigned long long*)varying, (const uint32_t*)counts[r], ntiles,
+                   nxt, shift + 8, local ? 1 : 0, local && !last ? counts[z] : nullptr);
         if (e != cudaSuccess) return e;
         std::swap(src_k, dst_k);
         std::swap(src_v, dst_v);
         *result_in_alt = !*result_in_alt;
-        cur ^= 1;
+        if (local) {
+            const int r2 = w, w2 = z, z2 = r;
+            r = r2;
+            w = w2;
+            z = z2;
+        } else {
+            std::swap(r, w);
+        }
     }
     return cudaSuccess;
 }
@@ -447,7 +493,7 @@ cudaError_t radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
 
 size_t radix_sort_temp_bytes(int64_t n) {
     const int64_t tile = n <= kSmallSort ? 1024 : 4096;
-    return 256 + 2 * sizeof(uint32_t) * (size_t)kRadix *
+    return 256 + 3 * sizeof(uint32_t) * (size_t)kRadix *
                      (size_t)ceil_div(std::max<int64_t>(n, 1), tile);
 }
 
@@ -1102,27 +1148,26 @@ __device__ __forceinline__ unsigned long long double_order(double v) {
 
 constexpr int kBucketThreads = 256;
 
+// c_l for l = 0..L (one thread each); independent of the data, so the build
+// runs it on a side stream beside the norms and the sort.
+__global__ void class_cos_kernel(int L, float eps, double* __restrict__ cl) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l <= L) cl[l] = cos_class(L, l, (double)eps);
+}
+
 // One launch builds the probing order.  Every block computes, in shared memory,
-// the L+1 values c_l (thread 32 w + i for l = 8 w + i: one chain per warp lane
-// group, spread over the warps), U_j = sqrt(U_j^2), and all m(L+1) keys
-// s_hat = fl(U_j c_l); each thread then ranks its own bucket by counting the
-// buckets with a greater key (s_hat, l, j), compared as integers.
-// order[rank] = j (L+1) + l.
+// U_j = sqrt(U_j^2) and all m(L+1) keys s_hat = fl(U_j c_l); each thread then
+// ranks its own bucket by counting the buckets with a greater key
+// (s_hat, l, j), compared as integers.  order[rank] = j (L+1) + l.
 __global__ void __launch_bounds__(kBucketThreads)
-    bucket_order_kernel(const double* __restrict__ U2, int m, int L, float eps,
-                        double* __restrict__ shat_sorted, uint32_t* __restrict__ order) {
+    bucket_order_kernel(const double* __restrict__ U2, const double* __restrict__ cl_g, int m,
+                        int L, double* __restrict__ shat_sorted, uint32_t* __restrict__ order) {
     extern __shared__ unsigned long long keys[];          // ncls order keys
     const int ncls = m * (L + 1);
     uint32_t* tie = (uint32_t*)(keys + ncls);             // ncls tie keys l 2^16 + j
     double* cl = (double*)(tie + ((ncls + 1) & ~1));      // L+1 cosines
     double* Uj = cl + (L + 1);                            // m norms
-    // cosines: lanes 0..7 of each warp, so the FP64 chains run on all SM partitions
-    {
-        const int w = threadIdx.x >> 5, i = threadIdx.x & 31;
-        const int nw = blockDim.x >> 5;
-        if (i < 8)
-            for (int l = w * 8 + i; l <= L; l += nw * 8) cl[l] = cos_class(L, l, (double)eps);
-    }
+    for (int l = threadIdx.x; l <= L; l += blockDim.x) cl[l] = cl_g[l];
     for (int j = threadIdx.x; j < m; j += blockDim.x) Uj[j] = sqrt(U2[j]);
     __syncthreads();
     for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
@@ -1146,8 +1191,13 @@ __global__ void __launch_bounds__(kBucketThreads)
 
 }  // namespace
 
-cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, double* shat_sorted,
-                                uint32_t* order, double* /*unused*/, cudaStream_t st) {
+cudaError_t launch_class_cos(int L, float eps, double* cl, cudaStream_t st) {
+    return launch("class_cos", class_cos_kernel, dim3((unsigned)ceil_div(L + 1, 32)), dim3(32), 0, st,
+                  L, eps, cl);
+}
+
+cudaError_t launch_bucket_order(const double* U2, const double* cl, int m, int L,
+                                double* shat_sorted, uint32_t* order, cudaStream_t st) {
     const int ncls = m * (L + 1);
     const size_t smem = sizeof(unsigned long long) * ncls + sizeof(uint32_t) * ((ncls + 1) & ~1) +
                         sizeof(double) * (L + 1 + m);
@@ -1156,7 +1206,7 @@ cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, doubl
     if (e != cudaSuccess) return e;
     return launch("bucket_order", bucket_order_kernel,
                   dim3((unsigned)ceil_div(ncls, kBucketThreads)), dim3(kBucketThreads), smem, st,
-                  U2, m, L, eps, shat_sorted, order);
+                  U2, cl, m, L, shat_sorted, order);
 }
 
 }  // namespace nrlsh

@@ -140,9 +140,11 @@ cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2,
                               const double* tau64, const float* xnorm, bool fp32_items,
                               void* codes, int code_bytes, unsigned long long* amb_list,
                               unsigned* amb_count, unsigned amb_cap, int* err, cudaStream_t st);
+// c_l = cos(pi (1 - eps)(L - l) / L), correctly rounded, l = 0..L.
+cudaError_t launch_class_cos(int L, float eps, double* cl, cudaStream_t st);
 // The sorted (U_j, l) structure: probing order of the m (L+1) buckets.
-cudaError_t launch_bucket_order(const double* U2, int m, int L, float eps, double* shat_sorted,
-                                uint32_t* order, double* scratch_keys, cudaStream_t st);
+cudaError_t launch_bucket_order(const double* U2, const double* cl, int m, int L,
+                                double* shat_sorted, uint32_t* order, cudaStream_t st);
 
 // ----------------------------------------------------------- query launchers
 

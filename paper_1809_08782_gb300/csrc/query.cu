@@ -379,6 +379,12 @@ __device__ __forceinline__ float order_float(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
+// Order-preserving integer image of a double (larger value, larger key).
+__device__ __forceinline__ unsigned long long double_key(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
 // (s, id) beats (s', id') when s > s', or s == s' and id < id'.
 __device__ __forceinline__ bool better(double s, int64_t id, double s2, int64_t id2) {
     return s > s2 || (s == s2 && id < id2);
@@ -491,6 +497,31 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
         __syncthreads();
     }
     const int kk_out = (int)min((int64_t)kq, (int64_t)nc);
+    if (nc <= (uint32_t)(kRescoreSmem / 16)) {
+        // rank every contender by (score desc, id asc) against all others; ranks are
+        // unique (ids are), so rank < k places the item directly
+        unsigned long long* key_s = (unsigned long long*)rows_s;
+        int64_t* id_s = (int64_t*)(key_s + nc);
+        for (uint32_t c = threadIdx.x; c < nc; c += 256) {
+            key_s[c] = double_key(contsq[c]);
+            id_s[c] = perm[candq[contq[c]]];
+        }
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < nc; c += 256) {
+            const unsigned long long k0 = key_s[c];
+            const int64_t i0 = id_s[c];
+            int rank = 0;
+            for (uint32_t c1 = 0; c1 < nc; ++c1) {
+                const unsigned long long k1 = key_s[c1];
+                rank += (k1 > k0) || (k1 == k0 && id_s[c1] < i0);
+            }
+            if (rank < kq) {
+                ids_out[rank] = i0;
+                sc_out[rank] = __double2float_rn(contsq[c]);
+            }
+        }
+        __syncthreads();
+    } else {
     for (int r = 0; r < kk_out; ++r) {
         double bs = -DBL_MAX;
         int64_t bi = INT64_MAX;
@@ -533,6 +564,7 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
             contq[bc_s[w0]] |= 0x80000000u;
         }
         __syncthreads();
+    }
     }
     for (int r = kk_out + threadIdx.x; r < k_out; r += 256) {
         ids_out[r] = -1;
