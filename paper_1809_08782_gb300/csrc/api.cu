@@ -579,8 +579,8 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
         NRLSH_CK(launch_rerank_fp32(ix->Xp, ix->dtype, ix->dp, ix->d, Qc, qc, cand, ccap, bnd,
                                     ix->xnorm, qnorm, lo, hi, st));
         NRLSH_CK(launch_topk(lo, hi, cand, ccap, bnd, qc, k, nullptr, ix->Xp, ix->dtype, ix->dp,
-                             ix->d, Qc, ix->perm, cont, cont_s, o.ids + q0 * o.k_ld,
-                             o.scores + q0 * o.k_ld, o.k_ld, st));
+                             ix->d, Qc, ix->xnorm, qnorm, ix->perm, cont, cont_s,
+                             o.ids + q0 * o.k_ld, o.scores + q0 * o.k_ld, o.k_ld, st));
     }
     return NRLSH_OK;
 }

@@ -173,8 +173,9 @@ cudaError_t launch_rerank_fp32(const void* Xp, nrlsh_dtype dt, int dp, int d, co
 cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, int64_t cap,
                         const Boundary* bnd, int64_t nq, int k, const int32_t* ks,
                         const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
-                        const uint32_t* perm, uint32_t* cont, double* cont_s,
-                        int64_t* out_ids, float* out_scores, int out_ld, cudaStream_t st);
+                        const float* xnorm, const float* qnorm, const uint32_t* perm,
+                        uint32_t* cont, double* cont_s, int64_t* out_ids, float* out_scores,
+                        int out_ld, cudaStream_t st);
 // Threshold walk, candidate selection, FP32 re-rank and exact top-k, one block
 // per query (the main query path after the histograms).
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,

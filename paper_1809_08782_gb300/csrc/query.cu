@@ -421,6 +421,7 @@ __device__ void select_digit(const uint32_t* hist, int rem, int* dg_out, int* re
 }
 
 constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
+constexpr int kDot2Max = 512;        // contenders scored by the compensated FP32 tier
 
 // Block phase (256 threads), one query.  tau = k-th largest lower bound (MSD
 // radix select on the order-preserving integer image of the floats).  Every
@@ -432,10 +433,10 @@ constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
 template <typename T>
 __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict__ hiq,
                          const uint32_t* __restrict__ candq, int64_t count, int kq, int k_out,
-                         const T* __restrict__ Xp, int dp, int d, const float* qs,
-                         const uint32_t* __restrict__ perm, uint32_t* __restrict__ contq,
-                         double* __restrict__ contsq, int64_t* __restrict__ ids_out,
-                         float* __restrict__ sc_out) {
+                         const T* __restrict__ Xp, int dp, int d, const float* qs, float qn,
+                         const float* __restrict__ xnorm, const uint32_t* __restrict__ perm,
+                         uint32_t* __restrict__ contq, double* __restrict__ contsq,
+                         int64_t* __restrict__ ids_out, float* __restrict__ sc_out) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t prefix_s, mask_s;
     __shared__ int rem_s, dg_s;
@@ -444,6 +445,9 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __shared__ int64_t bid_s[8];
     __shared__ int bc_s[8];
     __shared__ __align__(16) float rows_s[kRescoreSmem / sizeof(float)];
+    __shared__ double rank_lo[kDot2Max], rank_hi[kDot2Max];
+    __shared__ uint16_t flagged[kDot2Max];
+    __shared__ uint32_t nflag_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     float tau = -FLT_MAX;
@@ -481,20 +485,93 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __syncthreads();
     const uint32_t nc = nc_s;
     const int rb = max(1, min(256, kRescoreSmem / (int)(sizeof(float) * dp)));
-    for (uint32_t c0 = 0; c0 < nc; c0 += rb) {
-        const int nr = (int)min((uint32_t)rb, nc - c0);
-        for (int i = threadIdx.x; i < nr * dp; i += 256) {
-            const int r = i / dp, col = i % dp;
-            rows_s[r * dp + col] = to_f32(Xp[(int64_t)candq[contq[c0 + r]] * dp + col]);
+    if (nc <= (uint32_t)kDot2Max) {
+        // Compensated FP32 tier (Ogita, Rump, Oishi, "Accurate sum and dot product",
+        // 2005): a warp per contender, TwoProduct by fma and TwoSum per lane, the
+        // same transformations across lanes.  With m = ceil(dp/32) terms per lane
+        // and 5 tree levels, |hi + lo - q^T x| <= u^2 (2m(m+1) + 10(dp+32)) sum|q x|,
+        // u = 2^-24; the bound below takes 4x that, plus the FP64 rounding of the
+        // canonical in-order sum ((d+2) 2^-53 sum|q x|) and of hi + lo.
+        const int mlane = (dp + 31) / 32;
+        const double c2 = 4.0 * 0x1p-48 * (2.0 * mlane * (mlane + 1) + 10.0 * (dp + 32)) +
+                          (double)(d + 2) * 0x1p-53;
+        for (uint32_t c = warp; c < nc; c += 8) {
+            const uint32_t pos = candq[contq[c]];
+            const T* xr = Xp + (int64_t)pos * dp;
+            float sh = 0.0f, sl = 0.0f;
+            for (int k = lane; k < dp; k += 32) {
+                const float x = to_f32(xr[k]), y = qs[k];
+                const float pr = __fmul_rn(x, y);
+                const float er = fmaf(x, y, -pr);            // pr + er = x y exactly
+                const float s2 = __fadd_rn(sh, pr);          // TwoSum(sh, pr)
+                const float bb = __fsub_rn(s2, sh);
+                const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));
+                sh = s2;
+                sl = __fadd_rn(__fadd_rn(sl, t), er);
+            }
+            for (int o = 16; o; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+                const float s2 = __fadd_rn(sh, oh);
+                const float bb = __fsub_rn(s2, sh);
+                const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(oh, bb));
+                sh = s2;
+                sl = __fadd_rn(__fadd_rn(sl, ol), t);
+            }
+            if (lane == 0) {
+                const double v = __dadd_rn((double)sh, (double)sl);
+                const double e = c2 * (double)qn * (double)xnorm[pos] * (1.0 + 0x1p-20) +
+                                 0x1p-52 * fabs(v) + 0x1p-120;
+                rank_lo[c] = __dsub_rd(v, e);
+                rank_hi[c] = __dadd_ru(v, e);
+                contsq[c] = v;
+            }
         }
         __syncthreads();
-        if (threadIdx.x < nr) {
-            const float* xr = rows_s + threadIdx.x * dp;
-            double acc = 0.0;
-            for (int kk = 0; kk < d; ++kk) acc = fma((double)xr[kk], (double)qs[kk], acc);
-            contsq[c0 + threadIdx.x] = acc;
+        // exact tier only where the interval could change the outcome: it straddles
+        // an fp32 rounding boundary, or it overlaps another contender's interval
+        if (threadIdx.x == 0) nflag_s = 0;
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < nc; c += 256) {
+            const double lo_c = rank_lo[c], hi_c = rank_hi[c];
+            bool flag = __double2float_rn(lo_c) != __double2float_rn(hi_c);
+            for (uint32_t c1 = 0; c1 < nc && !flag; ++c1)
+                flag = c1 != c && rank_lo[c1] <= hi_c && lo_c <= rank_hi[c1];
+            if (flag) flagged[atomicAdd(&nflag_s, 1u)] = (uint16_t)c;
         }
         __syncthreads();
+        const uint32_t nf = nflag_s;
+        for (uint32_t f0 = 0; f0 < nf; f0 += rb) {
+            const int nr = (int)min((uint32_t)rb, nf - f0);
+            for (int i = threadIdx.x; i < nr * dp; i += 256) {
+                const int r = i / dp, col = i % dp;
+                rows_s[r * dp + col] = to_f32(Xp[(int64_t)candq[contq[flagged[f0 + r]]] * dp + col]);
+            }
+            __syncthreads();
+            if (threadIdx.x < nr) {
+                const float* xr = rows_s + threadIdx.x * dp;
+                double acc = 0.0;
+                for (int kk = 0; kk < d; ++kk) acc = fma((double)xr[kk], (double)qs[kk], acc);
+                contsq[flagged[f0 + threadIdx.x]] = acc;
+            }
+            __syncthreads();
+        }
+    } else {
+        for (uint32_t c0 = 0; c0 < nc; c0 += rb) {
+            const int nr = (int)min((uint32_t)rb, nc - c0);
+            for (int i = threadIdx.x; i < nr * dp; i += 256) {
+                const int r = i / dp, col = i % dp;
+                rows_s[r * dp + col] = to_f32(Xp[(int64_t)candq[contq[c0 + r]] * dp + col]);
+            }
+            __syncthreads();
+            if (threadIdx.x < nr) {
+                const float* xr = rows_s + threadIdx.x * dp;
+                double acc = 0.0;
+                for (int kk = 0; kk < d; ++kk) acc = fma((double)xr[kk], (double)qs[kk], acc);
+                contsq[c0 + threadIdx.x] = acc;
+            }
+            __syncthreads();
+        }
     }
     const int kk_out = (int)min((int64_t)kq, (int64_t)nc);
     if (nc <= (uint32_t)(kRescoreSmem / 16)) {
@@ -577,7 +654,8 @@ __global__ void __launch_bounds__(256)
     topk_kernel(const float* __restrict__ lo, const float* __restrict__ hi,
                 const uint32_t* __restrict__ cand, int64_t cap, const Boundary* __restrict__ bnd,
                 int k, const int32_t* __restrict__ ks, const T* __restrict__ Xp, int dp, int d,
-                const float* __restrict__ Q, const uint32_t* __restrict__ perm,
+                const float* __restrict__ Q, const float* __restrict__ xnorm,
+                const float* __restrict__ qnorm, const uint32_t* __restrict__ perm,
                 uint32_t* __restrict__ cont, double* __restrict__ cont_s,
                 int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int out_ld) {
     extern __shared__ __align__(16) float qs[];
@@ -586,8 +664,8 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     const Boundary b = bnd[q];
     dev_topk(lo + q * cap, hi + q * cap, cand + q * cap, (int64_t)b.full + b.r, ks ? ks[q] : k,
-             out_ld, Xp, dp, d, qs, perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld,
-             out_scores + q * out_ld);
+             out_ld, Xp, dp, d, qs, qnorm[q], xnorm, perm, cont + q * cap, cont_s + q * cap,
+             out_ids + q * out_ld, out_scores + q * out_ld);
 }
 
 // ----------------------------------------------------- fused probe + rerank
@@ -620,8 +698,9 @@ __global__ void __launch_bounds__(256)
     const int64_t count = (int64_t)b.full + b.r;
     dev_rerank(Xp, dp, qs, candq, 0, count, xnorm, qnorm[q], kappa, lo + q * cap, hi + q * cap);
     __syncthreads();
-    dev_topk(lo + q * cap, hi + q * cap, candq, count, ks ? ks[q] : k, out_ld, Xp, dp, d, qs, perm,
-             cont + q * cap, cont_s + q * cap, out_ids + q * out_ld, out_scores + q * out_ld);
+    dev_topk(lo + q * cap, hi + q * cap, candq, count, ks ? ks[q] : k, out_ld, Xp, dp, d, qs,
+             qnorm[q], xnorm, perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld,
+             out_scores + q * out_ld);
 }
 
 // Persistent form: CTAs take queries from a device work counter until it passes
@@ -664,8 +743,8 @@ __global__ void __launch_bounds__(256)
         const int64_t count = (int64_t)b.full + b.r;
         dev_rerank(Xp, dp, qs, cand, 0, count, xnorm, qnorm[q], kappa, lo, hi);
         __syncthreads();
-        dev_topk(lo, hi, cand, count, min(max(ks[q], 1), k_max), k_max, Xp, dp, d, qs, perm, cont,
-                 cont_s,
+        dev_topk(lo, hi, cand, count, min(max(ks[q], 1), k_max), k_max, Xp, dp, d, qs, qnorm[q],
+                 xnorm, perm, cont, cont_s,
                  out_ids + q * k_max, out_scores + q * k_max);
     }
 }
@@ -763,16 +842,17 @@ cudaError_t launch_rerank_fp32(const void* Xp, nrlsh_dtype dt, int dp, int d, co
 cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, int64_t cap,
                         const Boundary* bnd, int64_t nq, int k, const int32_t* ks,
                         const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
-                        const uint32_t* perm, uint32_t* cont, double* cont_s,
-                        int64_t* out_ids, float* out_scores, int out_ld, cudaStream_t st) {
+                        const float* xnorm, const float* qnorm, const uint32_t* perm,
+                        uint32_t* cont, double* cont_s, int64_t* out_ids, float* out_scores,
+                        int out_ld, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)dp;
     if (dt == NRLSH_BF16)
         return launch("topk_bf16", topk_kernel<__nv_bfloat16>, dim3((unsigned)nq), dim3(256), smem, st,
-                      lo, hi, cand, cap, bnd, k, ks, (const __nv_bfloat16*)Xp, dp, d, Q, perm, cont,
-                      cont_s, out_ids, out_scores, out_ld);
+                      lo, hi, cand, cap, bnd, k, ks, (const __nv_bfloat16*)Xp, dp, d, Q, xnorm, qnorm,
+                      perm, cont, cont_s, out_ids, out_scores, out_ld);
     return launch("topk", topk_kernel<float>, dim3((unsigned)nq), dim3(256), smem, st, lo, hi, cand,
-                  cap, bnd, k, ks, (const float*)Xp, dp, d, Q, perm, cont, cont_s, out_ids,
-                  out_scores, out_ld);
+                  cap, bnd, k, ks, (const float*)Xp, dp, d, Q, xnorm, qnorm, perm, cont, cont_s,
+                  out_ids, out_scores, out_ld);
 }
 
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
