@@ -1,0 +1,482 @@
+// Projection of rows on CUDA cores (Eq. 4 on the Eq. 8 transform): the FP32
+// tier with a proven bound, and the FP32 and FP64 tiers that decide the bits a
+// first tier left open.
+//
+//   project_warp   warp per row, A^T in shared memory, transpose-reduction
+//   project_fp32   register-tiled form for rows longer than 1,024
+//   resolve_fp32   warp per undecided (row, bit): FP32, lane-strided
+//   resolve_fp64   warp per undecided (row, bit): FP64, then the canonical order
+#include "nrlsh_internal.cuh"
+
+#include <algorithm>
+
+namespace nrlsh {
+
+
+namespace {
+
+constexpr int kProjThreads = 256;  // 8 warps: warp w owns bit group w, lane owns rows
+constexpr int kProjKC = 32;        // columns of X staged per step
+
+// Bit b of row x, FP64 in the fixed order: sum_k a_kb x_k (k = 0..d-1) then
+// + fl(a_db * tau) for items.  This is the canonical definition of the bit.
+template <typename T>
+__device__ bool project_bit_fp64(const T* __restrict__ xrow, const float* __restrict__ A_pad,
+                                 int Lp, int d, int b, bool has_tail, double tau) {
+    double acc = 0.0;
+    for (int k = 0; k < d; ++k)
+        acc = fma((double)to_f32(xrow[k]), (double)A_pad[(int64_t)k * Lp + b], acc);
+    if (has_tail) acc = __dadd_rn(acc, __dmul_rn((double)A_pad[(int64_t)d * Lp + b], tau));
+    return acc >= 0.0;
+}
+
+// Block: 32 RI rows x Lp bits.  Warp w owns bits [w BT, (w+1) BT), lane owns rows
+// lane + 32 i (i < RI).  X and A are staged kProjKC columns at a time; every
+// (row, bit) accumulates in FP32 in column order.  A bit whose FP32 value lies
+// inside the error bound is left 0 and its (row, bit) pair is appended to
+// `amb_list` for the resolve kernel (or, if the list is full, decided here by
+// the canonical FP64 evaluation).
+template <typename T, typename C, int BT, int RI>
+__global__ void __launch_bounds__(kProjThreads)
+    project_fp32_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int L, int Lp,
+                        const float* __restrict__ A_pad, const float* __restrict__ anorm,
+                        const double* __restrict__ tau64, const float* __restrict__ tau32,
+                        const float* __restrict__ xnorm, C* __restrict__ codes,
+                        unsigned long long* __restrict__ amb_list, unsigned* amb_count,
+                        unsigned amb_cap, float kappa) {
+    constexpr int kRows = 32 * RI;
+    __shared__ float As[kProjKC][8 * BT];
+    __shared__ float Xs[kProjKC][kRows + 1];
+    __shared__ unsigned long long code_s[kRows];
+
+    const int lane = threadIdx.x & 31, bg = threadIdx.x >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    if (threadIdx.x < kRows) code_s[threadIdx.x] = 0ull;
+
+    float acc[RI][BT];
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int b = 0; b < BT; ++b) acc[i][b] = 0.0f;
+
+    for (int k0 = 0; k0 < d; k0 += kProjKC) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kRows * kProjKC; i += kProjThreads) {
+            const int r = i / kProjKC, c = i % kProjKC;
+            const int64_t row = row0 + r;
+            const int col = k0 + c;
+            Xs[c][r] = (row < n && col < d) ? to_f32(X[row * ldx + col]) : 0.0f;
+        }
+        for (int i = threadIdx.x; i < kProjKC * Lp; i += kProjThreads) {
+            const int c = i / Lp, b = i % Lp;
+            As[c][b] = (k0 + c < d) ? A_pad[(int64_t)(k0 + c) * Lp + b] : 0.0f;
+        }
+        __syncthreads();
+        const int kc = min(kProjKC, d - k0);
+        for (int c = 0; c < kc; ++c) {
+            float xv[RI];
+#pragma unroll
+            for (int i = 0; i < RI; ++i) xv[i] = Xs[c][lane + 32 * i];
+#pragma unroll
+            for (int b = 0; b < BT; ++b) {
+                const float a = As[c][bg * BT + b];
+#pragma unroll
+                for (int i = 0; i < RI; ++i) acc[i][b] = fmaf(xv[i], a, acc[i][b]);
+            }
+        }
+    }
+
+    const bool has_tail = tau64 != nullptr;
+#pragma unroll
+    for (int i = 0; i < RI; ++i) {
+        const int r = lane + 32 * i;
+        const int64_t row = row0 + r;
+        if (row >= n) continue;
+        const float xn = xnorm[row];
+        const float t32 = has_tail ? tau32[row] : 0.0f;
+        unsigned long long word = 0;
+#pragma unroll
+        for (int b = 0; b < BT; ++b) {
+            const int bit = bg * BT + b;
+            if (bit >= L) continue;
+            const float ad = has_tail ? A_pad[(int64_t)d * Lp + bit] : 0.0f;
+            const float v = has_tail ? fmaf(ad, t32, acc[i][b]) : acc[i][b];
+            // |v - v64| <= bound: FP32 summation error with Cauchy-Schwarz for
+            // sum |a_k x_k|, the tau rounding, and a 4x margin (kappa = (d+2) 2^-22).
+            const float bound = kappa * anorm[bit] * xn + 0x1p-20f * fabsf(ad) * t32;
+            if (fabsf(v) * (1.0f - 0x1p-21f) > bound) {
+                if (v > 0.0f) word |= 1ull << bit;
+            } else {
+                const unsigned slot = atomicAdd(amb_count, 1u);
+                if (slot < amb_cap) {
+                    amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
+                } else if (project_bit_fp64(X + row * ldx, A_pad, Lp, d, bit, has_tail,
+                                            has_tail ? tau64[row] : 0.0)) {
+                    word |= 1ull << bit;
+                }
+            }
+        }
+        if (word) atomicOr(&code_s[r], word);
+    }
+    __syncthreads();
+    if (threadIdx.x < kRows) {
+        const int64_t row = row0 + threadIdx.x;
+        if (row < n) codes[row] = (C)code_s[threadIdx.x];
+    }
+}
+
+__device__ __forceinline__ void or_bit(uint32_t* w, int bit) { atomicOr(w, 1u << bit); }
+__device__ __forceinline__ void or_bit(uint64_t* w, int bit) {
+    atomicOr((unsigned long long*)w, 1ull << bit);
+}
+
+// Warp per undecided (row, bit): FP64 dot in lane-strided order, then a tree.
+// Both that sum and the canonical in-order sum are within (d-1) 2^-53 sum|a_k x_k|
+// of the exact value, so outside (2d + 8) 2^-53 (sum|a_k x_k| + |tail|) plus the
+// final-add rounding the two have the same sign.  Otherwise lane 0 evaluates the
+// canonical sequential form.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    resolve_kernel(const T* __restrict__ X, int d, int ldx, int Lp, const float* __restrict__ A_pad,
+                   const double* __restrict__ tau64, const unsigned long long* __restrict__ list,
+                   const unsigned* __restrict__ count, unsigned cap, C* __restrict__ codes) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned cnt = min(*count, cap);
+    for (int64_t e = warp; e < cnt; e += nwarps) {
+        const unsigned long long entry = list[e];
+        const int64_t row = (int64_t)(entry >> 6);
+        const int bit = (int)(entry & 63);
+        const T* xr = X + row * ldx;
+        double s = 0.0, sa = 0.0;
+        for (int k = lane; k < d; k += 32) {
+            const double p = (double)to_f32(xr[k]) * (double)A_pad[(int64_t)k * Lp + bit];
+            s += p;
+            sa += fabs(p);
+        }
+        for (int o = 16; o; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        }
+        const bool has_tail = tau64 != nullptr;
+        const double tail = has_tail ? __dmul_rn((double)A_pad[(int64_t)d * Lp + bit], tau64[row]) : 0.0;
+        const double v = __dadd_rn(s, tail);
+        const double bound = (2.0 * d + 8.0) * 0x1p-53 * (sa + fabs(tail)) + 0x1p-50 * fabs(v);
+        bool set;
+        if (fabs(v) > bound) {
+            set = v > 0.0;
+        } else {
+            int r = 0;
+            if (lane == 0)
+                r = project_bit_fp64(xr, A_pad, Lp, d, bit, has_tail, has_tail ? tau64[row] : 0.0);
+            set = __shfl_sync(0xffffffffu, r, 0) != 0;
+        }
+        if (lane == 0 && set) or_bit(codes + row, bit);
+    }
+}
+
+// The FP32 tier for pairs the bf16 tensor-core pass left undecided (fp32 items):
+// warp per pair, FP32 dot of the exact fp32 row in lane-strided order and a
+// tree, decided against (d+2) 2^-22 ||a|| ||x|| (any summation order) plus the
+// tail rounding; still undecided pairs move on to the FP64 list.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    resolve_fp32_kernel(const T* __restrict__ X, int d, int ldx, int Lp,
+                        const float* __restrict__ A_pad, const float* __restrict__ anorm,
+                        const float* __restrict__ xnorm, const float* __restrict__ tau32,
+                        const double* __restrict__ tau64, const unsigned long long* __restrict__ list,
+                        const unsigned* __restrict__ count, unsigned cap, C* __restrict__ codes,
+                        unsigned long long* __restrict__ list2, unsigned* count2, unsigned cap2,
+                        float kappa) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned cnt = min(*count, cap);
+    for (int64_t e = warp; e < cnt; e += nwarps) {
+        const unsigned long long entry = list[e];
+        const int64_t row = (int64_t)(entry >> 6);
+        const int bit = (int)(entry & 63);
+        const T* xr = X + row * ldx;
+        float s = 0.0f;
+        for (int k = lane; k < d; k += 32) s = fmaf(to_f32(xr[k]), A_pad[(int64_t)k * Lp + bit], s);
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float ad = A_pad[(int64_t)d * Lp + bit];
+        const float t32 = tau32[row];
+        const float v = fmaf(ad, t32, s);
+        const float bound = kappa * anorm[bit] * xnorm[row] + 0x1p-20f * fabsf(ad) * t32;
+        if (lane == 0) {
+            if (fabsf(v) * (1.0f - 0x1p-21f) > bound) {
+                if (v > 0.0f) or_bit(codes + row, bit);
+            } else {
+                const unsigned slot = atomicAdd(count2, 1u);
+                if (slot < cap2)
+                    list2[slot] = entry;
+                else if (project_bit_fp64(xr, A_pad, Lp, d, bit, true, tau64[row]))
+                    or_bit(codes + row, bit);
+            }
+        }
+    }
+}
+
+// Warp-per-row form of the FP32 tier.  A^T (bit-major, zero-padded) sits in
+// shared memory; a warp keeps its row in registers (lane owns columns
+// lane + 32 i), forms 32 bit-partials per pass, and reduces them with a
+// transpose-reduction (31 shuffles) after which lane l holds the sum of bit
+// 32 pass + l.  Any summation order satisfies the same FP32 bound.
+template <typename T, int NREG>
+__global__ void __launch_bounds__(256)
+    project_warp_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int L, int Lp, int dpa,
+                        const float* __restrict__ A_pad, const float* __restrict__ anorm,
+                        const double* __restrict__ tau64, const float* __restrict__ tau32,
+                        const float* __restrict__ xnorm, void* __restrict__ codes, int code_bytes,
+                        unsigned long long* __restrict__ amb_list, unsigned* amb_count,
+                        unsigned amb_cap, float kappa) {
+    extern __shared__ float At_s[];          // Lr x dpa, Lr = Lp rounded up to 32
+    __shared__ float ad_s[64], an_s[64];
+    const int Lr = (Lp + 31) / 32 * 32;
+    for (int i = threadIdx.x; i < Lr * dpa; i += blockDim.x) {
+        const int b = i / dpa, k = i % dpa;
+        At_s[i] = (b < L && k < d) ? A_pad[(int64_t)k * Lp + b] : 0.0f;
+    }
+    if (threadIdx.x < 64) {
+        const int b = threadIdx.x;
+        ad_s[b] = (b < L && tau64) ? A_pad[(int64_t)d * Lp + b] : 0.0f;
+        an_s[b] = b < L ? anorm[b] : 0.0f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const bool has_tail = tau64 != nullptr;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n;
+         row += nwarps) {
+        float x[NREG];
+#pragma unroll
+        for (int i = 0; i < NREG; ++i) {
+            const int k = lane + 32 * i;
+            x[i] = k < d ? to_f32(X[row * ldx + k]) : 0.0f;
+        }
+        const float xn = xnorm[row];
+        const float t32 = has_tail ? tau32[row] : 0.0f;
+        unsigned long long word = 0, undecided = 0;
+        for (int pass = 0; pass < Lr / 32; ++pass) {
+            float acc[32];
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+                const float* ar = At_s + (pass * 32 + b) * dpa + lane;
+                float a = 0.0f;
+#pragma unroll
+                for (int i = 0; i < NREG; ++i) a = fmaf(x[i], ar[32 * i], a);
+                acc[b] = a;
+            }
+#pragma unroll
+            for (int w = 16; w >= 1; w >>= 1) {
+                const bool up = (lane & w) != 0;
+#pragma unroll
+                for (int j = 0; j < w; ++j) {
+                    const float send = up ? acc[j] : acc[j + w];
+                    const float keep = up ? acc[j + w] : acc[j];
+                    acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+                }
+            }
+            const int bit = pass * 32 + lane;
+            bool set = false, open = false;
+            if (bit < L) {
+                const float ad = ad_s[bit];
+                const float v = has_tail ? fmaf(ad, t32, acc[0]) : acc[0];
+                const float bound = kappa * an_s[bit] * xn + 0x1p-20f * fabsf(ad) * t32;
+                if (fabsf(v) * (1.0f - 0x1p-21f) > bound)
+                    set = v > 0.0f;
+                else
+                    open = true;
+            }
+            word |= (unsigned long long)__ballot_sync(0xffffffffu, set) << (32 * pass);
+            undecided |= (unsigned long long)__ballot_sync(0xffffffffu, open) << (32 * pass);
+        }
+        // undecided bits: one list reservation per row; if the list is full the
+        // lane owning the bit evaluates the canonical FP64 form itself
+        const int cnt = __popcll(undecided);
+        unsigned base = 0;
+        if (lane == 0 && cnt) base = atomicAdd(amb_count, (unsigned)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        bool fb0 = false, fb1 = false;
+        for (int pass = 0; pass < 2 && cnt; ++pass) {
+            const int b = pass * 32 + lane;
+            if ((undecided >> b) & 1ull) {
+                const unsigned slot = base + __popcll(undecided & ((1ull << b) - 1ull));
+                if (slot < amb_cap) {
+                    amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)b;
+                } else {
+                    const bool v = project_bit_fp64(X + row * ldx, A_pad, Lp, d, b, has_tail,
+                                                    has_tail ? tau64[row] : 0.0);
+                    if (pass == 0) fb0 = v; else fb1 = v;
+                }
+            }
+        }
+        word |= (unsigned long long)__ballot_sync(0xffffffffu, fb0) |
+                ((unsigned long long)__ballot_sync(0xffffffffu, fb1) << 32);
+        if (lane == 0) {
+            if (code_bytes == 4)
+                static_cast<uint32_t*>(codes)[row] = (uint32_t)word;
+            else
+                static_cast<uint64_t*>(codes)[row] = word;
+        }
+    }
+}
+
+template <typename T, typename C, int BT>
+cudaError_t project_rows(const void* X, int64_t n, int d, int ldx, int L, int Lp,
+                         const float* A_pad, const float* anorm, const double* tau64,
+                         const float* tau32, const float* xnorm, void* codes,
+                         unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
+                         float kappa, cudaStream_t st, const char* name) {
+    return launch(name, project_fp32_kernel<T, C, BT, 2>, dim3((unsigned)ceil_div(n, 64)),
+                  dim3(kProjThreads), 0, st, (const T*)X, n, d, ldx, L, Lp, A_pad, anorm, tau64,
+                  tau32, xnorm, (C*)codes, amb_list, amb_count, amb_cap, kappa);
+}
+
+template <typename T, typename C, int NREG>
+cudaError_t project_warp_launch(const void* X, int64_t n, int d, int ldx, int L, int Lp,
+                                const float* A_pad, const float* anorm, const double* tau64,
+                                const float* tau32, const float* xnorm, void* codes,
+                                unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
+                                float kappa, cudaStream_t st, const char* name) {
+    const int Lr = (Lp + 31) / 32 * 32, dpa = NREG * 32;
+    const size_t smem = sizeof(float) * (size_t)Lr * dpa;
+    auto kern = project_warp_kernel<T, NREG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int per_sm = smem <= 100 * 1024 ? 2 : 1;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 8), (int64_t)per_sm * 152);
+    return launch(name, kern, dim3(grid), dim3(256), smem, st, (const T*)X, n, d, ldx, L, Lp, dpa,
+                  A_pad, anorm, tau64, tau32, xnorm, codes, (int)sizeof(C), amb_list, amb_count,
+                  amb_cap, kappa);
+}
+
+template <typename T, typename C>
+cudaError_t project_dispatch(const void* X, int64_t n, int d, int ldx, int L, int Lp,
+                             const float* A_pad, const float* anorm, const double* tau64,
+                             const float* tau32, const float* xnorm, void* codes,
+                             unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
+                             cudaStream_t st, const char* name) {
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+    cudaError_t e;
+    const int nreg = (d + 31) / 32;
+    if (nreg <= 32) {
+#define NRLSH_PW(R_)                                                                          \
+    e = project_warp_launch<T, C, R_>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,  \
+                                      codes, amb_list, amb_count, amb_cap, kappa, st, name);   \
+    break;
+        switch (nreg <= 4 ? 4 : nreg <= 10 ? 10 : 32) {
+            case 4: NRLSH_PW(4)
+            case 10: NRLSH_PW(10)
+            default: NRLSH_PW(32)
+        }
+#undef NRLSH_PW
+        if (e != cudaSuccess) return e;
+        const unsigned rgrid = (unsigned)std::min<int64_t>(
+            ceil_div(std::max<int64_t>(n * L / 256, 32), 8), 8 * 152);
+        return launch("resolve_fp64", resolve_kernel<T, C>, dim3(rgrid), dim3(256), 0, st,
+                      (const T*)X, d, ldx, Lp, A_pad, tau64, (const unsigned long long*)amb_list,
+                      (const unsigned*)amb_count, amb_cap, (C*)codes);
+    }
+    switch (Lp / 8) {
+        case 1:
+            e = project_rows<T, C, 1>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
+        case 2:
+            e = project_rows<T, C, 2>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
+        case 4:
+            e = project_rows<T, C, 4>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
+        case 8:
+            e = project_rows<T, C, 8>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm, codes,
+                                      amb_list, amb_count, amb_cap, kappa, st, name);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 256, 32), 8),
+                                                      8 * 152);
+    return launch("resolve_fp64", resolve_kernel<T, C>, dim3(grid), dim3(256), 0, st, (const T*)X, d,
+                  ldx, Lp, A_pad, tau64, (const unsigned long long*)amb_list,
+                  (const unsigned*)amb_count, amb_cap, (C*)codes);
+}
+
+}  // namespace
+
+cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx,
+                                int L, int Lp, const float* A_pad, const float* anorm,
+                                const double* tau64, const float* tau32, const float* xnorm,
+                                void* codes, int code_bytes, unsigned long long* amb_list,
+                                unsigned* amb_count, unsigned amb_cap, cudaStream_t st) {
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4)
+            return project_dispatch<__nv_bfloat16, uint32_t>(X, n, d, ldx, L, Lp, A_pad, anorm,
+                                                             tau64, tau32, xnorm, codes, amb_list,
+                                                             amb_count, amb_cap, st,
+                                                             "project_fp32_bf16");
+        return project_dispatch<__nv_bfloat16, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64,
+                                                         tau32, xnorm, codes, amb_list, amb_count,
+                                                         amb_cap, st, "project_fp32_bf16");
+    }
+    if (code_bytes == 4)
+        return project_dispatch<float, uint32_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32,
+                                                 xnorm, codes, amb_list, amb_count, amb_cap, st,
+                                                 "project_fp32");
+    return project_dispatch<float, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
+                                             codes, amb_list, amb_count, amb_cap, st,
+                                             "project_fp32");
+}
+
+cudaError_t launch_resolve_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                int Lp, const float* A_pad, const float* anorm, const float* xnorm,
+                                const float* tau32, const double* tau64,
+                                const unsigned long long* list, const unsigned* count,
+                                unsigned cap, void* codes, int code_bytes,
+                                unsigned long long* list2, unsigned* count2, unsigned cap2,
+                                cudaStream_t st) {
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 32, 32), 8),
+                                                      16 * 152);
+#define NRLSH_R32(T_, C_)                                                                    \
+    return launch("resolve_fp32", resolve_fp32_kernel<T_, C_>, dim3(grid), dim3(256), 0, st,  \
+                  (const T_*)X, d, ldx, Lp, A_pad, anorm, xnorm, tau32, tau64, list, count,  \
+                  cap, (C_*)codes, list2, count2, cap2, kappa);
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_R32(__nv_bfloat16, uint32_t)
+        NRLSH_R32(__nv_bfloat16, uint64_t)
+    }
+    if (code_bytes == 4) NRLSH_R32(float, uint32_t)
+    NRLSH_R32(float, uint64_t)
+#undef NRLSH_R32
+}
+
+cudaError_t launch_resolve_fp64(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                int Lp, const float* A_pad, const double* tau64,
+                                const unsigned long long* list, const unsigned* count,
+                                unsigned cap, void* codes, int code_bytes, cudaStream_t st) {
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 256, 32), 8),
+                                                      8 * 152);
+#define NRLSH_R64(T_, C_)                                                                    \
+    return launch("resolve_fp64", resolve_kernel<T_, C_>, dim3(grid), dim3(256), 0, st,       \
+                  (const T_*)X, d, ldx, Lp, A_pad, tau64, list, count, cap, (C_*)codes);
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_R64(__nv_bfloat16, uint32_t)
+        NRLSH_R64(__nv_bfloat16, uint64_t)
+    }
+    if (code_bytes == 4) NRLSH_R64(float, uint32_t)
+    NRLSH_R64(float, uint64_t)
+#undef NRLSH_R64
+}
+
+size_t ambiguity_capacity(int64_t rows, int L) {
+    return (size_t)std::max<int64_t>(4096, rows * L / 64);
+}
+
+}  // namespace nrlsh
