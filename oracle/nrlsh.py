@@ -12,6 +12,9 @@ uses, so the two must agree bit for bit:
   way to "break ties arbitrarily"); sub-dataset j holds ranks
   [floor(j n / m), floor((j+1) n / m)).  U_j^2 = max s_x over S_j.
                                                              (Algorithm 1)
+  Or uniform norm ranges: j = min(m-1, floor(((nu - nu_min) / w) * m)) with
+  nu = sqrt(s_x), w = nu_max - nu_min, all FP64 round-to-nearest; empty S_j
+  have U_j^2 = 0.                                      (Section 5, Figure 3a)
 * code bit b of item x in S_j: [v >= 0] with
       v = fl(A_b + fl(a_{d,b} * tau_x)),  A_b = sum_{k<d} a_{k,b} x_k  (in order),
       tau_x = fl(sqrt(fl(U_j^2 - s_x)))  (tau_x = 1 when U_j^2 = 0).
@@ -73,6 +76,39 @@ def partition(s: np.ndarray, m: int):
         sub[members] = j
         U2[j] = s[members].max()
     return sub, U2, bounds, order
+
+
+def partition_uniform(s: np.ndarray, m: int):
+    """The alternative partition of Section 5 (Figure 3a): the domain of 2-norms
+    [nu_min, nu_max], nu_x = sqrt(s_x), is cut into m equally wide ranges and
+    S_j holds the items whose norm falls in range j:
+
+        j(x) = min(m - 1, floor(((nu_x - nu_min) / w) * m)),  w = nu_max - nu_min,
+
+    every operation in FP64, rounded to nearest, in this order (all items in
+    S_0 when w = 0).  Ranges may be empty; an empty S_j has U_j^2 = 0.  Returns
+    (sub_of_id, U2, bounds) with bounds the m+1 storage offsets of the
+    sub-datasets in (sub-dataset, id) order."""
+    n = s.shape[0]
+    if not 1 <= m <= n:
+        raise ValueError("need 1 <= m <= n")
+    nu = np.sqrt(np.asarray(s, dtype=np.float64))
+    lo, hi = nu.min(), nu.max()
+    w = hi - lo
+    if w > 0.0:
+        t = ((nu - lo) / w) * np.float64(m)
+        sub = np.minimum(np.floor(t), m - 1).astype(np.int32)
+    else:
+        sub = np.zeros(n, dtype=np.int32)
+    U2 = np.zeros(m, dtype=np.float64)
+    counts = np.zeros(m, dtype=np.int64)
+    for j in range(m):
+        members = np.flatnonzero(sub == j)
+        counts[j] = members.size
+        if members.size:
+            U2[j] = s[members].max()
+    bounds = [0] + np.cumsum(counts).tolist()
+    return sub, U2, bounds
 
 
 def tail_component(s: np.ndarray, sub: np.ndarray, U2: np.ndarray) -> np.ndarray:
@@ -200,8 +236,10 @@ class Index:
     X: np.ndarray            # (n, d) float64 copy of the items
 
 
-def build(X, m: int, L: int, seed: int, eps: float = 0.1, A: Optional[np.ndarray] = None) -> Index:
-    """Algorithm 1: partition by norm percentiles, normalise each S_j by its own U_j,
+def build(X, m: int, L: int, seed: int, eps: float = 0.1, A: Optional[np.ndarray] = None,
+          partition_scheme: str = "percentile") -> Index:
+    """Algorithm 1: partition by norm percentiles (or, with partition_scheme="uniform",
+    by the uniform norm ranges of Section 5), normalise each S_j by its own U_j,
     and hash with SIMPLE-LSH (Eq. 8 + Eq. 4) into L-bit codes."""
     X = np.asarray(X, dtype=np.float64)
     n, d = X.shape
@@ -210,7 +248,12 @@ def build(X, m: int, L: int, seed: int, eps: float = 0.1, A: Optional[np.ndarray
     if A is None:
         A = philox.projections(seed, d, L)
     s = sq_norms(X)
-    sub, U2, bounds, _ = partition(s, m)
+    if partition_scheme == "percentile":
+        sub, U2, bounds, _ = partition(s, m)
+    elif partition_scheme == "uniform":
+        sub, U2, bounds = partition_uniform(s, m)
+    else:
+        raise ValueError("partition_scheme is 'percentile' or 'uniform'")
     tau = tail_component(s, sub, U2)
     codes = item_codes(X, A, tau)
     table, shat, _ = class_table(U2, L, eps)

@@ -115,6 +115,98 @@ def test_partition_rejects_bad_m():
         O.partition(np.ones(3), 0)
 
 
+# ---------------------------------------- uniform norm ranges (Section 5)
+
+@pytest.mark.parametrize("lo,top,m", [(0, 64, 8), (5, 32, 4), (3, 16, 16), (0, 8, 1)])
+def test_uniform_partition_exact_dyadic_norms(lo, top, m):
+    """Integer norms lo..lo+top with a power-of-two width: every FP64 step is
+    exact, so j = min(m-1, floor((nu - lo) m / top)) in integers."""
+    nu = np.arange(lo, lo + top + 1, dtype=np.float64)
+    rng = np.random.default_rng(lo + top + m)
+    perm = rng.permutation(nu.size)
+    s = (nu * nu)[perm]
+    sub, U2, bounds = O.partition_uniform(s, m)
+    for i, p in enumerate(perm):
+        v = int(nu[p]) - lo
+        assert sub[i] == min(m - 1, (v * m) // top)
+    for j in range(m):
+        members = s[sub == j]
+        assert U2[j] == (members.max() if members.size else 0.0)
+    assert bounds == [0] + np.cumsum(np.bincount(sub, minlength=m)).tolist()
+
+
+def test_uniform_partition_matches_numpy_histogram():
+    """Bin counts equal numpy.histogram's equal-width bins over [min, max] (last
+    bin closed), away from bin edges where the two roundings may differ."""
+    rng = np.random.default_rng(11)
+    for trial in range(5):
+        nu = rng.lognormal(0.0, 0.8, 5000)
+        s = nu * nu
+        nu = np.sqrt(s)
+        m = [4, 16, 32, 64, 100][trial]
+        edges = np.linspace(nu.min(), nu.max(), m + 1)
+        gap = np.min(np.abs(nu[:, None] - edges[None, 1:-1]))
+        if gap < 1e-9 * nu.max():
+            continue
+        sub, _, _ = O.partition_uniform(s, m)
+        counts, _ = np.histogram(nu, bins=m, range=(nu.min(), nu.max()))
+        assert np.array_equal(np.bincount(sub, minlength=m), counts)
+
+
+def test_uniform_partition_against_exact_rationals():
+    """j from exact rational arithmetic on the same nu values agrees wherever the
+    exact t = (nu - nu_min) m / w is not within 1e-9 of an integer."""
+    rng = np.random.default_rng(12)
+    s = rng.lognormal(0.0, 1.0, 400) ** 2
+    m = 12
+    sub, _, _ = O.partition_uniform(s, m)
+    nu = np.sqrt(s)
+    lo, hi = Fraction(float(nu.min())), Fraction(float(nu.max()))
+    checked = 0
+    for i in range(s.size):
+        t = (Fraction(float(nu[i])) - lo) * m / (hi - lo)
+        if abs(t - round(t)) < Fraction(1, 10**9):
+            continue
+        assert sub[i] == min(m - 1, math.floor(t))
+        checked += 1
+    assert checked > 390
+
+
+def test_uniform_partition_invariants_and_degenerate_cases():
+    rng = np.random.default_rng(13)
+    s = np.concatenate([rng.uniform(0.5, 1.0, 300), rng.uniform(9.0, 16.0, 300)])  # a gap
+    sub, U2, bounds = O.partition_uniform(s, 10)
+    order = np.argsort(s, kind="stable")
+    assert np.all(np.diff(sub[order]) >= 0)                  # contiguous in ||x||
+    assert sub[np.argmin(s)] == 0 and sub[np.argmax(s)] == 9
+    sizes = np.bincount(sub, minlength=10)
+    assert (sizes == 0).any()                                 # the gap leaves empty ranges
+    assert np.all(U2[sizes == 0] == 0.0)
+    assert bounds[-1] == s.size
+    # equal norms: everything in S_0
+    sub, U2, _ = O.partition_uniform(np.full(50, 2.25), 8)
+    assert np.all(sub == 0) and U2[0] == 2.25 and np.all(U2[1:] == 0.0)
+    # m = 1 is the percentile partition with m = 1
+    s = rng.uniform(0, 4, 40)
+    a, Ua, _ = O.partition_uniform(s, 1)
+    b, Ub, _, _ = O.partition(s, 1)
+    assert np.array_equal(a, b) and np.array_equal(Ua, Ub)
+    # zero vectors alongside non-zero ones sit in S_0
+    s = np.concatenate([np.zeros(5), rng.uniform(1, 2, 20)])
+    sub, _, _ = O.partition_uniform(s, 4)
+    assert np.all(sub[:5] == 0)
+
+
+def test_uniform_index_full_budget_returns_exact_mips():
+    X = rand_items(60, 7, 31)
+    idx = O.build(X, 6, 12, seed=5, eps=0.2, partition_scheme="uniform")
+    assert idx.bounds[-1] == 60
+    Q = rand_queries(6, 7, 32)
+    ids, _ = O.query(idx, Q, 4, B=60)
+    for i in range(6):
+        assert np.array_equal(ids[i], exact.exact_topk(X, Q[i], 4))
+
+
 # ------------------------------------------------------------- Eq. 8 and 4
 
 def test_simple_lsh_transform_invariants():
