@@ -92,10 +92,23 @@ typedef enum nrlsh_projection {
                                     in FP32 (fp32 items) and then FP64 */
 } nrlsh_projection;
 
+/* How the items are split into the m sub-datasets. */
+typedef enum nrlsh_partition {
+    NRLSH_PARTITION_PERCENTILE = 0, /* Algorithm 1: rank by (||x||^2, id); S_j holds ranks
+                                       [floor(j n / m), floor((j + 1) n / m)) */
+    NRLSH_PARTITION_UNIFORM = 1     /* Section 5 (Figure 3a): the norm domain [nu_min, nu_max]
+                                       cut into m equal ranges, nu = sqrt(||x||^2),
+                                       j = min(m - 1, floor(((nu - nu_min) / w) * m)),
+                                       w = nu_max - nu_min, each operation rounded to
+                                       nearest in FP64 (all j = 0 when w = 0); sub-datasets
+                                       may be empty (U_j = 0) */
+} nrlsh_partition;
+
 typedef struct nrlsh_build_options {
     int32_t dtype;               /* nrlsh_dtype of the items */
     float eps;                   /* 0 < eps < 1 */
     int32_t projection;          /* nrlsh_projection */
+    int32_t partition;           /* nrlsh_partition (0 = percentile) */
     void* stream;                /* cudaStream_t; NULL = legacy default stream */
 } nrlsh_build_options;
 
@@ -113,6 +126,8 @@ typedef struct nrlsh_info {
     int64_t ambiguous_bits;      /* (item, bit) pairs the first tier left undecided */
     int32_t projection;          /* nrlsh_projection used (SIMT or TENSOR) */
     int32_t device_error;        /* nonzero: a bounded device wait ran out during the build */
+    int32_t partition;           /* nrlsh_partition used */
+    int32_t reserved;
 } nrlsh_info;
 
 /*
@@ -129,8 +144,10 @@ NRLSH_API nrlsh_status nrlsh_build(const float* items, int64_t n, int32_t d, int
 NRLSH_API nrlsh_status nrlsh_build_ex(const void* items, int64_t n, int32_t d, int32_t m,
                                       int32_t L, uint64_t seed, nrlsh_dtype dtype, float eps,
                                       void* stream, nrlsh_index** out);
-/* As nrlsh_build_ex, with the projection path chosen by opts->projection.
- * NRLSH_PROJECT_TENSOR on a device without tcgen05 returns NRLSH_ERR_UNSUPPORTED. */
+/* As nrlsh_build_ex, with the projection path chosen by opts->projection and the
+ * partition by opts->partition.  NRLSH_PROJECT_TENSOR on a device without tcgen05
+ * returns NRLSH_ERR_UNSUPPORTED; an unknown partition returns NRLSH_ERR_ARG.
+ * Storage order is (sub-dataset, id) under either partition. */
 NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d, int32_t m,
                                         int32_t L, uint64_t seed, const nrlsh_build_options* opts,
                                         nrlsh_index** out);
@@ -241,6 +258,8 @@ NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* index, const fl
  * nrlsh_get_codes:       n uint64 codes in original id order.
  * nrlsh_get_partition:   sub_of_id (n int32), U2 (m doubles, U_j^2), sqnorm (n doubles,
  *                        s_x in id order); any of the three may be NULL.
+ * nrlsh_get_segments:    seg (m+1 int64): S_j occupies storage positions
+ *                        [seg[j], seg[j+1]); seg[0] = 0, seg[m] = n.
  * nrlsh_get_projections: A ((d+1) x L floats, row-major; every value is bf16).
  * nrlsh_get_buckets:     the probing order: bucket_j, bucket_l (m(L+1) int32 each)
  *                        and s_hat (m(L+1) doubles) in probing order; any may be NULL.
@@ -249,6 +268,7 @@ NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* index, const fl
 NRLSH_API nrlsh_status nrlsh_get_codes(const nrlsh_index* index, uint64_t* codes);
 NRLSH_API nrlsh_status nrlsh_get_partition(const nrlsh_index* index, int32_t* sub_of_id,
                                            double* U2, double* sqnorm);
+NRLSH_API nrlsh_status nrlsh_get_segments(const nrlsh_index* index, int64_t* seg);
 NRLSH_API nrlsh_status nrlsh_get_projections(const nrlsh_index* index, float* A);
 NRLSH_API nrlsh_status nrlsh_get_buckets(const nrlsh_index* index, int32_t* bucket_j,
                                          int32_t* bucket_l, double* s_hat);

@@ -53,9 +53,12 @@ struct nrlsh_index {
     uint32_t* order = nullptr;     // ncls bucket ids j*(L+1)+l in probing order
     double* shat_sorted = nullptr; // ncls
     double* ccos = nullptr;        // L+1 bucket cosines c_l
+    int32_t partition = NRLSH_PARTITION_PERCENTILE;
+    int64_t* seg = nullptr;        // m+1 storage offsets of the sub-datasets
     nrlsh::PosTile* tiles = nullptr;
     int32_t ntiles = 0;
-    std::vector<nrlsh::PosTile> tiles_host;  // source of the asynchronous upload
+    std::vector<nrlsh::PosTile> tiles_host;  // sources of the asynchronous uploads
+    std::vector<int64_t> seg_host;
     unsigned* ambiguous = nullptr;  // (item, bit) pairs the first tier left undecided
     int projection = NRLSH_PROJECT_SIMT;
     __nv_bfloat16* At = nullptr;     // A^T in bf16, 64 x dp (tensor-core B operand)
@@ -268,7 +271,7 @@ nrlsh_status stage_in(Scratch& sc, const void* src, size_t bytes, const void** d
 
 nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int32_t L,
                         uint64_t seed, nrlsh_dtype dtype, float eps, void* stream, int projection,
-                        nrlsh_index** out) {
+                        int partition, nrlsh_index** out) {
     if (!out) return arg_error("out is NULL");
     *out = nullptr;
     if (!items) return arg_error("items is NULL");
@@ -281,6 +284,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     if (dtype != NRLSH_F32 && dtype != NRLSH_BF16) return arg_error("unknown dtype");
     if (projection < NRLSH_PROJECT_AUTO || projection > NRLSH_PROJECT_TENSOR)
         return arg_error("unknown projection path");
+    if (partition != NRLSH_PARTITION_PERCENTILE && partition != NRLSH_PARTITION_UNIFORM)
+        return arg_error("unknown partition");
     const size_t esz = dtype == NRLSH_BF16 ? 2 : 4;
     if ((int64_t)d * (int64_t)esz * n / n != (int64_t)d * (int64_t)esz) return arg_error("n*d overflows");
 
@@ -297,6 +302,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     ix->dtype = dtype;
     ix->eps = eps;
     ix->seed = seed;
+    ix->partition = partition;
     ix->stream = st;
     cudaGetDevice(&ix->device);
     keep_pool_memory(ix->device);
@@ -334,6 +340,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     B_CK(own(ix, &ix->tau32, n));
     B_CK(own(ix, &ix->xnorm, n));
     B_CK(own(ix, &ix->U2, m));
+    B_CK(own(ix, &ix->seg, (size_t)m + 1));
     B_CK(own(ix, &ix->A, (size_t)(d + 1) * L));
     B_CK(own(ix, &ix->A_pad, (size_t)(d + 1) * ix->Lp));
     B_CK(own(ix, &ix->anorm, ix->Lp));
@@ -352,18 +359,28 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         }
     }
 
-    // histogram tiles: runs of positions inside one sub-dataset
-    {
-        const int64_t tile = 16384 / ix->code_bytes;
+    // histogram tiles: runs of positions inside one sub-dataset.  Percentile
+    // ranges have known sizes: offsets and tiles are made here; uniform ranges
+    // get them from the device after the assignment (at most this many tiles).
+    const int64_t tile = 16384 / ix->code_bytes;
+    const bool uniform = partition == NRLSH_PARTITION_UNIFORM;
+    if (!uniform) {
         std::vector<PosTile>& tl = ix->tiles_host;
+        std::vector<int64_t>& sg = ix->seg_host;
+        for (int32_t j = 0; j <= m; ++j) sg.push_back(seg_start(j, n, m));
         for (int32_t j = 0; j < m; ++j) {
-            const int64_t a = seg_start(j, n, m), b = seg_start(j + 1, n, m);
+            const int64_t a = sg[j], b = sg[j + 1];
             for (int64_t s = a; s < b; s += tile) tl.push_back({s, (int32_t)std::min(tile, b - s), j});
         }
         ix->ntiles = (int32_t)tl.size();
         B_CK(own(ix, &ix->tiles, tl.size()));
         B_CU(cudaMemcpyAsync(ix->tiles, tl.data(), tl.size() * sizeof(PosTile),
                              cudaMemcpyHostToDevice, st));
+        B_CU(cudaMemcpyAsync(ix->seg, sg.data(), sg.size() * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, st));
+    } else {
+        ix->ntiles = (int32_t)(ceil_div(n, tile) + m);
+        B_CK(own(ix, &ix->tiles, (size_t)ix->ntiles));
     }
 
     {
@@ -379,13 +396,15 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         const size_t amb_cap = tc ? std::max<size_t>(4096, (size_t)n * L / 16)
                                   : ambiguity_capacity(n, L);
         const size_t amb_cap2 = ambiguity_capacity(n, L);
-        B_CK(sc.get(&keys, n));
-        B_CK(sc.get(&keys_alt, n));
+        B_CK(sc.get(&keys, std::max<int64_t>(n, 8)));      // uniform ranges: sizes (m words)
+        B_CK(sc.get(&keys_alt, std::max<int64_t>(n, 8)));  // uniform ranges: 6 range words
         B_CK(sc.get(&vals, n));
         B_CK(sc.get(&vals_alt, n));
         B_CK(sc.get(&jkeys, n));
         B_CK(sc.get(&jkeys_alt, n));
         B_CK(sc.get(&sort_tmp, radix_sort_temp_bytes(n)));
+        char* bo_tmp;
+        B_CK(sc.get(&bo_tmp, bucket_order_temp_bytes(m, L)));
         B_CK(sc.get(&amb_list, amb_cap));
         if (tc) {
             B_CK(sc.get(&amb_list2, amb_cap2));
@@ -405,22 +424,35 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                 side));
         B_CU(launch_class_cos(L, eps, ix->ccos, side));
         B_CU(side_stream_join(st));
-        // Algorithm 1: rank by norm, percentile partition, U_j
-        B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
-        bool alt = false;
-        B_CU(radix_sort_u64(keys, vals, keys_alt, vals_alt, n, 64, sort_tmp, &alt, st));
-        // storage order: stable sort of ids by sub-dataset
-        uint32_t* jv = alt ? vals : vals_alt;       // the pair the sort did not end in
-        uint32_t* jv_alt = alt ? vals_alt : vals;
-        B_CU(launch_segment_assign(alt ? keys_alt : keys, alt ? vals_alt : vals, n, m,
-                                   ix->sub_of_id, ix->U2, jkeys, jv, st));
         const int jbits = (bits_for(m) + 7) / 8 * 8;
+        bool alt = false;
+        uint32_t *jv, *jv_alt;
+        if (!uniform) {
+            // Algorithm 1: rank by norm, percentile partition, U_j
+            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
+            B_CU(radix_sort_u64(keys, vals, keys_alt, vals_alt, n, 64, sort_tmp, &alt, st));
+            // storage order: stable sort of ids by sub-dataset
+            jv = alt ? vals : vals_alt;       // the pair the sort did not end in
+            jv_alt = alt ? vals_alt : vals;
+            B_CU(launch_segment_assign(alt ? keys_alt : keys, alt ? vals_alt : vals, n, m,
+                                       ix->sub_of_id, ix->U2, jkeys, jv, st));
+        } else {
+            // Section 5: uniform norm ranges, then the same stable sort by sub-dataset
+            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, nullptr, nullptr, st));
+            jv = vals;
+            jv_alt = vals_alt;
+            B_CU(launch_uniform_assign(ix->s_id, n, m, (unsigned long long*)keys_alt, ix->sub_of_id,
+                                       ix->U2, jkeys, jv, (uint32_t*)keys, st));
+            B_CU(launch_segments((const uint32_t*)keys, m, tile, ix->seg, ix->tiles, ix->ntiles,
+                                 st));
+        }
         B_CU(radix_sort_u32(jkeys, jv, jkeys_alt, jv_alt, n, jbits, sort_tmp, &alt, st));
         B_CU(cudaMemcpyAsync(ix->perm, alt ? jv_alt : jv, sizeof(uint32_t) * n,
                              cudaMemcpyDeviceToDevice, st));
         // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
-        B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, m, ix->s_id, ix->U2, ix->Xp,
-                                 ix->Xb, ix->Xb2, ix->s_pos, ix->tau64, ix->tau32, ix->xnorm, st));
+        B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, ix->sub_of_id, ix->s_id,
+                                 ix->U2, ix->Xp, ix->Xb, ix->Xb2, ix->s_pos, ix->tau64, ix->tau32,
+                                 ix->xnorm, st));
         B_CU(side_stream_wait(st));  // A and the cosines are ready
         // Eq. 4: sign random projection codes
         if (!tc) {
@@ -443,7 +475,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                      ix->code_bytes, st));
         }
         // Eq. 12 and the sorted (U_j, l) structure
-        B_CU(launch_bucket_order(ix->U2, ix->ccos, m, L, ix->shat_sorted, ix->order, st));
+        B_CU(launch_bucket_order(ix->U2, ix->ccos, m, L, ix->shat_sorted, ix->order, bo_tmp, st));
     }
     if (!is_device_ptr(items)) B_CU(cudaStreamSynchronize(st));
 #undef B_CK
@@ -539,7 +571,7 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
             NRLSH_CKS(sc.get(&hi, qc * cap));
             NRLSH_CKS(sc.get(&cont, qc * cap));
             NRLSH_CKS(sc.get(&cont_s, qc * cap));
-            NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, n, qc, budget, nullptr, flags,
+            NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, n, ix->seg, qc, budget, nullptr, flags,
                                          ix->codes, qcodes, ix->code_bytes, ix->Xp, ix->dtype,
                                          ix->dp, ix->d, Qc, ix->xnorm, qnorm, ix->perm, k, nullptr,
                                          cand, lo, hi, cont, cont_s, cap, o.ids + q0 * o.k_ld,
@@ -562,7 +594,7 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
         }
         uint32_t* cand;
         NRLSH_CKS(sc.get(&cand, qc * ccap));
-        NRLSH_CK(launch_select(ix->codes, qcodes, ix->code_bytes, n, ix->m, ix->L, qc, lam, bnd,
+        NRLSH_CK(launch_select(ix->codes, qcodes, ix->code_bytes, ix->seg, ix->m, ix->L, qc, lam, bnd,
                                cand, ccap, st));
         if (stage == Stage::Cand) {
             NRLSH_CK(launch_cand_to_ids(cand, ccap, bnd, ix->perm, qc, o.cand + q0 * o.cand_cap,
@@ -630,13 +662,15 @@ extern "C" {
 
 NRLSH_API nrlsh_status nrlsh_build(const float* items, int64_t n, int32_t d, int32_t m, int32_t L,
                                    uint64_t seed, nrlsh_index** out) {
-    return build_impl(items, n, d, m, L, seed, NRLSH_F32, 0.1f, nullptr, NRLSH_PROJECT_AUTO, out);
+    return build_impl(items, n, d, m, L, seed, NRLSH_F32, 0.1f, nullptr, NRLSH_PROJECT_AUTO,
+                      NRLSH_PARTITION_PERCENTILE, out);
 }
 
 NRLSH_API nrlsh_status nrlsh_build_ex(const void* items, int64_t n, int32_t d, int32_t m,
                                       int32_t L, uint64_t seed, nrlsh_dtype dtype, float eps,
                                       void* stream, nrlsh_index** out) {
-    return build_impl(items, n, d, m, L, seed, dtype, eps, stream, NRLSH_PROJECT_AUTO, out);
+    return build_impl(items, n, d, m, L, seed, dtype, eps, stream, NRLSH_PROJECT_AUTO,
+                      NRLSH_PARTITION_PERCENTILE, out);
 }
 
 NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d, int32_t m,
@@ -644,7 +678,7 @@ NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d,
                                         nrlsh_index** out) {
     if (!opts) return arg_error("opts is NULL");
     return build_impl(items, n, d, m, L, seed, (nrlsh_dtype)opts->dtype, opts->eps, opts->stream,
-                      opts->projection, out);
+                      opts->projection, opts->partition, out);
 }
 
 NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* queries, int64_t nq,
@@ -776,6 +810,13 @@ NRLSH_API nrlsh_status nrlsh_get_partition(const nrlsh_index* ix, int32_t* sub_o
     return NRLSH_OK;
 }
 
+NRLSH_API nrlsh_status nrlsh_get_segments(const nrlsh_index* ix, int64_t* seg) {
+    if (!ix || !seg) return arg_error("NULL argument");
+    NRLSH_CK(cudaStreamSynchronize(ix->stream));
+    NRLSH_CK(cudaMemcpy(seg, ix->seg, sizeof(int64_t) * (ix->m + 1), cudaMemcpyDeviceToHost));
+    return NRLSH_OK;
+}
+
 NRLSH_API nrlsh_status nrlsh_get_projections(const nrlsh_index* ix, float* A) {
     if (!ix || !A) return arg_error("NULL argument");
     NRLSH_CK(cudaStreamSynchronize(ix->stream));
@@ -818,6 +859,8 @@ NRLSH_API nrlsh_status nrlsh_get_info(const nrlsh_index* ix, nrlsh_info* info) {
     NRLSH_CK(cudaMemcpy(&derr, ix->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     info->projection = ix->projection;
     info->device_error = derr;
+    info->partition = ix->partition;
+    info->reserved = 0;
     return NRLSH_OK;
 }
 
@@ -953,7 +996,7 @@ nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, cons
                              ix->ntiles, w.H, st, cfg.hist_qb));
         NRLSH_CK(cudaMemsetAsync(w.work, 0, sizeof(unsigned), st));
         NRLSH_CK(launch_probe_rerank_persistent(
-            w.H, ix->order, ix->m, ix->L, ix->n, budgets + q0, ix->codes, qcodes, ix->code_bytes,
+            w.H, ix->order, ix->m, ix->L, ix->n, ix->seg, budgets + q0, ix->codes, qcodes, ix->code_bytes,
             ix->Xp, ix->dtype, ix->dp, ix->d, Q + q0 * ix->d, ix->xnorm, w.qnorm + q0, ix->perm,
             ks + q0, k_max, w.slabs, cap, w.ctas, w.work, qc, ids + q0 * k_max,
             scores + q0 * k_max, st));
@@ -1266,7 +1309,7 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* ix, con
                                      qamb_list, qamb, (unsigned)qamb_cap, st));
         NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
                              ix->ntiles, H, st));
-        NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, ix->n, qc, probe_budget, nullptr, 0u,
+        NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, ix->n, ix->seg, qc, probe_budget, nullptr, 0u,
                                      ix->codes, qcodes, ix->code_bytes, ix->Xp, ix->dtype, ix->dp,
                                      ix->d, Qc, ix->xnorm, qnorm, ix->perm, k, nullptr, cand, lo_s,
                                      hi_s, cont, cont_s, cap, ids + q0 * k, scores + q0 * k, k, st));

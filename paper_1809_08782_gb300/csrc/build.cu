@@ -533,40 +533,176 @@ __global__ void segment_assign_kernel(const uint64_t* __restrict__ sorted_keys,
     if (r == seg_start(j + 1, n, m) - 1) U2[j] = __longlong_as_double((long long)sorted_keys[r]);
 }
 
-// One warp per storage position: copy the row (zero-padded to dp), the squared
-// norm, tau = sqrt(U_j^2 - s) (1 when U_j = 0) and an fp32 upper bound of ||x||.
-template <typename T>
-__global__ void gather_items_kernel(const T* __restrict__ X, int64_t ld, int d, int dp,
-                                    const uint32_t* __restrict__ perm, int64_t n, int m,
-                                    const double* __restrict__ s_id, const double* __restrict__ U2,
-                                    T* __restrict__ Xp, __nv_bfloat16* __restrict__ Xb,
-                                    __nv_bfloat16* __restrict__ Xb2, double* s_pos, double* tau64,
-                                    float* tau32, float* xnorm) {
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (p >= n) return;
-    const uint32_t id = perm[p];
-    const T* src = X + (int64_t)id * ld;
-    T* dst = Xp + p * dp;
-    for (int c = lane; c < dp; c += 32) {
-        const T v = c < d ? src[c] : T(0.0f);
-        dst[c] = v;
-        if (Xb) {  // tensor-core copies: x = hi + lo + r, |r| <= 2^-16 |x|
-            const float x = to_f32(v);
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            Xb[p * dp + c] = hi;
-            if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(x - __bfloat162float(hi));
+// Uniform norm ranges (the alternative partition of Section 5, Figure 3a):
+// nu_x = sqrt(s_x), [nu_min, nu_max] cut into m equal ranges,
+//   j(x) = min(m - 1, floor(fl(fl(fl(nu_x - nu_min) / w) * m))),  w = fl(nu_max - nu_min),
+// every operation IEEE round-to-nearest (j = 0 for all items when w = 0).  Each
+// step is monotone, so the ranges are contiguous in ||x||; some may be empty.
+//
+// First kernel: min and max of s (the bit patterns of non-negative doubles order
+// like the values); the last block to finish stores nu_min, nu_max and w as the
+// doubles range[2..4] (sqrt is monotone, so sqrt(min s) = min sqrt(s)).
+__global__ void __launch_bounds__(256)
+    norm_range_kernel(const double* __restrict__ s, int64_t n, unsigned long long* range,
+                      unsigned* done) {
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(s[i] + 0.0);
+        lo = u < lo ? u : lo;
+        hi = u > hi ? u : hi;
+    }
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&range[0], lo);
+        atomicMax(&range[1], hi);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            __threadfence();
+            const double nlo = sqrt(__longlong_as_double((long long)atomicAdd(&range[0], 0ull)));
+            const double nhi = sqrt(__longlong_as_double((long long)atomicAdd(&range[1], 0ull)));
+            range[2] = (unsigned long long)__double_as_longlong(nlo);
+            range[3] = (unsigned long long)__double_as_longlong(nhi);
+            range[4] = (unsigned long long)__double_as_longlong(__dsub_rn(nhi, nlo));
         }
     }
-    if (lane == 0) {
-        const double s = s_id[id];
-        const double u2 = U2[seg_of(p, n, m)];
-        const double t = (u2 == 0.0) ? 1.0 : sqrt(u2 - s);
-        s_pos[p] = s;
-        tau64[p] = t;
-        tau32[p] = (float)t;
-        xnorm[p] = __fsqrt_ru(__double2float_ru(s));
+}
+
+// Second kernel, one thread per id: j(x), the keys (j by id) and values (ids) of
+// the stable sort into storage order, the sub-dataset sizes, and U_j^2 = max s
+// over S_j (atomic max on the bit patterns; U2 starts at +0, so an empty S_j
+// keeps U_j = 0).
+__global__ void __launch_bounds__(256)
+    uniform_assign_kernel(const double* __restrict__ s_id, int64_t n, int m,
+                          const unsigned long long* __restrict__ range, uint32_t* sub_of_id,
+                          unsigned long long* U2_bits, uint32_t* jkeys, uint32_t* jvals,
+                          uint32_t* cnt) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const double s = s_id[id] + 0.0;
+    const double lo = __longlong_as_double((long long)range[2]);
+    const double w = __longlong_as_double((long long)range[4]);
+    int j = 0;
+    if (w > 0.0) {
+        const double t = __dmul_rn(__ddiv_rn(__dsub_rn(sqrt(s), lo), w), (double)m);
+        j = (int)fmin(floor(t), (double)(m - 1));
     }
+    sub_of_id[id] = (uint32_t)j;
+    jkeys[id] = (uint32_t)j;
+    jvals[id] = (uint32_t)id;
+    atomicAdd(&cnt[j], 1u);
+    atomicMax(&U2_bits[j], (unsigned long long)__double_as_longlong(s));
+}
+
+// Exclusive scan over one block of 1024 threads (one value per thread).
+__device__ int64_t block_scan_1024(int64_t v, int64_t* total, int64_t* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const int64_t ex = (warp ? wsum[warp - 1] : 0) + incl - v;
+    *total = wsum[31];
+    __syncthreads();
+    return ex;
+}
+
+// Segment offsets seg[0..m] (storage positions of each S_j: an exclusive scan of
+// the sizes) and the histogram tiles (runs of at most `tile` positions inside one
+// sub-dataset, in sub-dataset order); entries past the last tile, up to
+// ntiles_max, get length 0.  One block; thread t owns sub-datasets
+// [t per, (t + 1) per).
+__global__ void __launch_bounds__(1024)
+    segments_kernel(const uint32_t* __restrict__ cnt, int m, int64_t tile, int64_t* seg,
+                    PosTile* tiles, int ntiles_max) {
+    __shared__ int64_t wsum[32];
+    const int per = (m + 1023) / 1024;
+    const int b = min(m, (int)threadIdx.x * per), e = min(m, b + per);
+    int64_t items = 0, ntl = 0;
+    for (int j = b; j < e; ++j) {
+        items += cnt[j];
+        ntl += ceil_div((int64_t)cnt[j], tile);
+    }
+    int64_t items_total, tiles_total;
+    int64_t pos = block_scan_1024(items, &items_total, wsum);
+    int64_t t = block_scan_1024(ntl, &tiles_total, wsum);
+    for (int j = b; j < e; ++j) {
+        seg[j] = pos;
+        const int64_t len = cnt[j];
+        for (int64_t a = 0; a < len; a += tile) tiles[t++] = {pos + a, (int32_t)min(tile, len - a), j};
+        pos += len;
+    }
+    if (threadIdx.x == 0) seg[m] = items_total;
+    for (int64_t i = tiles_total + threadIdx.x; i < ntiles_max; i += 1024) tiles[i] = {0, 0, 0};
+}
+
+// Block of 256 threads per 32 storage positions: warp w copies rows w, w + 8, ...
+// (zero-padded to dp); then warp 0, lane i, writes position i's squared norm,
+// tau = sqrt(U_j^2 - s) (1 when U_j = 0) and an fp32 upper bound of ||x||, so
+// the FP64 square roots run on full warps.
+__device__ __forceinline__ void gather_tail(int64_t p, uint32_t id, const uint32_t* __restrict__ sub_of_id,
+                                            const double* __restrict__ s_id,
+                                            const double* __restrict__ U2, double* s_pos,
+                                            double* tau64, float* tau32, float* xnorm) {
+    const double s = s_id[id];
+    const double u2 = U2[sub_of_id[id]];
+    const double t = (u2 == 0.0) ? 1.0 : sqrt(u2 - s);
+    s_pos[p] = s;
+    tau64[p] = t;
+    tau32[p] = (float)t;
+    xnorm[p] = __fsqrt_ru(__double2float_ru(s));
+}
+
+constexpr int kGatherRows = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    gather_items_kernel(const T* __restrict__ X, int64_t ld, int d, int dp,
+                        const uint32_t* __restrict__ perm, int64_t n,
+                        const uint32_t* __restrict__ sub_of_id, const double* __restrict__ s_id,
+                        const double* __restrict__ U2, T* __restrict__ Xp,
+                        __nv_bfloat16* __restrict__ Xb, __nv_bfloat16* __restrict__ Xb2,
+                        double* s_pos, double* tau64, float* tau32, float* xnorm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p0 = (int64_t)blockIdx.x * kGatherRows;
+    for (int r = warp; r < kGatherRows; r += 8) {
+        const int64_t p = p0 + r;
+        if (p >= n) break;
+        const T* src = X + (int64_t)perm[p] * ld;
+        T* dst = Xp + p * dp;
+        for (int c = lane; c < dp; c += 32) {
+            const T v = c < d ? src[c] : T(0.0f);
+            dst[c] = v;
+            if (Xb) {  // tensor-core copies: x = hi + lo + r, |r| <= 2^-16 |x|
+                const float x = to_f32(v);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                Xb[p * dp + c] = hi;
+                if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
+        }
+    }
+    if (warp == 0 && p0 + lane < n)
+        gather_tail(p0 + lane, perm[p0 + lane], sub_of_id, s_id, U2, s_pos, tau64, tau32, xnorm);
 }
 
 // Vectorised form of gather_items_kernel for rows whose length d is a multiple
@@ -597,51 +733,48 @@ struct GatherVec<__nv_bfloat16> {
 };
 
 template <typename T>
-__global__ void gather_items_vec_kernel(const T* __restrict__ X, int64_t ld, int d, int dp,
-                                        const uint32_t* __restrict__ perm, int64_t n, int m,
-                                        const double* __restrict__ s_id,
-                                        const double* __restrict__ U2, T* __restrict__ Xp,
-                                        __nv_bfloat16* __restrict__ Xb,
-                                        __nv_bfloat16* __restrict__ Xb2, double* s_pos,
-                                        double* tau64, float* tau32, float* xnorm) {
+__global__ void __launch_bounds__(256)
+    gather_items_vec_kernel(const T* __restrict__ X, int64_t ld, int d, int dp,
+                            const uint32_t* __restrict__ perm, int64_t n,
+                            const uint32_t* __restrict__ sub_of_id,
+                            const double* __restrict__ s_id, const double* __restrict__ U2,
+                            T* __restrict__ Xp, __nv_bfloat16* __restrict__ Xb,
+                            __nv_bfloat16* __restrict__ Xb2, double* s_pos, double* tau64,
+                            float* tau32, float* xnorm) {
     using GV = GatherVec<T>;
     using V = typename GV::V;
     constexpr int W = GV::W;
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (p >= n) return;
-    const uint32_t id = perm[p];
-    const V* src = (const V*)(X + (int64_t)id * ld);
-    V* dst = (V*)(Xp + p * dp);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p0 = (int64_t)blockIdx.x * kGatherRows;
     const int nv = d / W;
-    for (int c = lane; c < nv; c += 32) {
-        const V v = src[c];
-        dst[c] = v;
-        if (Xb) {  // tensor-core copies: x = hi + lo + r, |r| <= 2^-16 |x|
-            float f[W];
-            GV::to_f(v, f);
+    for (int r = warp; r < kGatherRows; r += 8) {
+        const int64_t p = p0 + r;
+        if (p >= n) break;
+        const V* src = (const V*)(X + (int64_t)perm[p] * ld);
+        V* dst = (V*)(Xp + p * dp);
+        for (int c = lane; c < nv; c += 32) {
+            const V v = src[c];
+            dst[c] = v;
+            if (Xb) {  // tensor-core copies: x = hi + lo + r, |r| <= 2^-16 |x|
+                float f[W];
+                GV::to_f(v, f);
 #pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const __nv_bfloat16 hi = __float2bfloat16_rn(f[i]);
-                Xb[p * dp + c * W + i] = hi;
-                if (Xb2) Xb2[p * dp + c * W + i] = __float2bfloat16_rn(f[i] - __bfloat162float(hi));
+                for (int i = 0; i < W; ++i) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(f[i]);
+                    Xb[p * dp + c * W + i] = hi;
+                    if (Xb2)
+                        Xb2[p * dp + c * W + i] = __float2bfloat16_rn(f[i] - __bfloat162float(hi));
+                }
             }
         }
+        for (int c = d + lane; c < dp; c += 32) {
+            Xp[p * dp + c] = T(0.0f);
+            if (Xb) Xb[p * dp + c] = __float2bfloat16_rn(0.0f);
+            if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(0.0f);
+        }
     }
-    for (int c = d + lane; c < dp; c += 32) {
-        Xp[p * dp + c] = T(0.0f);
-        if (Xb) Xb[p * dp + c] = __float2bfloat16_rn(0.0f);
-        if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(0.0f);
-    }
-    if (lane == 0) {
-        const double s = s_id[id];
-        const double u2 = U2[seg_of(p, n, m)];
-        const double t = (u2 == 0.0) ? 1.0 : sqrt(u2 - s);
-        s_pos[p] = s;
-        tau64[p] = t;
-        tau32[p] = (float)t;
-        xnorm[p] = __fsqrt_ru(__double2float_ru(s));
-    }
+    if (warp == 0 && p0 + lane < n)
+        gather_tail(p0 + lane, perm[p0 + lane], sub_of_id, s_id, U2, s_pos, tau64, tau32, xnorm);
 }
 
 }  // namespace
@@ -653,30 +786,55 @@ cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* s
                   dim3(256), 0, st, sorted_keys, sorted_ids, n, m, sub_of_id, U2, jkeys, jvals);
 }
 
+cudaError_t launch_uniform_assign(const double* s_id, int64_t n, int m, unsigned long long* range,
+                                  uint32_t* sub_of_id, double* U2, uint32_t* jkeys,
+                                  uint32_t* jvals, uint32_t* cnt, cudaStream_t st) {
+    // range[0] = ~0 (min), range[1..4] = 0, done counter (range[5]) = 0
+    cudaError_t e = cudaMemsetAsync(range, 0xFF, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(range + 1, 0, 5 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * m, st);
+    if (e != cudaSuccess) return e;
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, 256), 2 * 152);
+    e = launch("norm_range", norm_range_kernel, dim3(g), dim3(256), 0, st, s_id, n, range,
+               (unsigned*)(range + 5));
+    if (e != cudaSuccess) return e;
+    return launch("uniform_assign", uniform_assign_kernel, dim3((unsigned)ceil_div(n, 256)),
+                  dim3(256), 0, st, s_id, n, m, (const unsigned long long*)range, sub_of_id,
+                  (unsigned long long*)U2, jkeys, jvals, cnt);
+}
+
+cudaError_t launch_segments(const uint32_t* cnt, int m, int64_t tile, int64_t* seg,
+                            PosTile* tiles, int ntiles_max, cudaStream_t st) {
+    return launch("segments", segments_kernel, dim3(1), dim3(1024), 0, st, cnt, m, tile, seg,
+                  tiles, ntiles_max);
+}
+
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
-                                const uint32_t* perm, int64_t n, int m, const double* s_id,
-                                const double* U2, void* Xp, __nv_bfloat16* Xb, __nv_bfloat16* Xb2,
-                                double* s_pos, double* tau64, float* tau32, float* xnorm,
-                                cudaStream_t st) {
-    const dim3 grid((unsigned)ceil_div(n * 32, 256));
+                                const uint32_t* perm, int64_t n, const uint32_t* sub_of_id,
+                                const double* s_id, const double* U2, void* Xp,
+                                __nv_bfloat16* Xb, __nv_bfloat16* Xb2, double* s_pos,
+                                double* tau64, float* tau32, float* xnorm, cudaStream_t st) {
+    const dim3 grid((unsigned)ceil_div(n, kGatherRows));
     if (dt == NRLSH_BF16) {
         if (d % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X & 3) == 0)
             return launch("gather_items_bf16", gather_items_vec_kernel<__nv_bfloat16>, grid,
-                          dim3(256), 0, st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, m, s_id,
-                          U2, (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr,
+                          dim3(256), 0, st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, sub_of_id,
+                          s_id, U2, (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr,
                           (__nv_bfloat16*)nullptr, s_pos, tau64, tau32, xnorm);
         return launch("gather_items_bf16", gather_items_kernel<__nv_bfloat16>, grid, dim3(256), 0,
-                      st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, m, s_id, U2,
+                      st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, sub_of_id, s_id, U2,
                       (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, s_pos,
                       tau64, tau32, xnorm);
     }
     if (d % 4 == 0 && ld % 4 == 0 && ((uintptr_t)X & 15) == 0)
         return launch("gather_items_f32", gather_items_vec_kernel<float>, grid, dim3(256), 0, st,
-                      (const float*)X, ld, d, dp, perm, n, m, s_id, U2, (float*)Xp, Xb, Xb2, s_pos,
-                      tau64, tau32, xnorm);
+                      (const float*)X, ld, d, dp, perm, n, sub_of_id, s_id, U2, (float*)Xp, Xb, Xb2,
+                      s_pos, tau64, tau32, xnorm);
     return launch("gather_items_f32", gather_items_kernel<float>, grid, dim3(256), 0, st,
-                  (const float*)X, ld, d, dp, perm, n, m, s_id, U2, (float*)Xp, Xb, Xb2, s_pos,
-                  tau64, tau32, xnorm);
+                  (const float*)X, ld, d, dp, perm, n, sub_of_id, s_id, U2, (float*)Xp, Xb, Xb2,
+                  s_pos, tau64, tau32, xnorm);
 }
 
 // =====================================================================
@@ -813,6 +971,10 @@ __device__ __forceinline__ unsigned long long double_order(double v) {
     return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+__device__ __forceinline__ double order_double(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
+
 constexpr int kBucketThreads = 256;
 
 // c_l for l = 0..L (one thread each); independent of the data, so the build
@@ -822,38 +984,49 @@ __global__ void class_cos_kernel(int L, float eps, double* __restrict__ cl) {
     if (l <= L) cl[l] = cos_class(L, l, (double)eps);
 }
 
-// One launch builds the probing order.  Every block computes, in shared memory,
-// U_j = sqrt(U_j^2) and all m(L+1) keys s_hat = fl(U_j c_l); each thread then
-// ranks its own bucket by counting the buckets with a greater key
-// (s_hat, l, j), compared as integers.  order[rank] = j (L+1) + l.
-__global__ void __launch_bounds__(kBucketThreads)
-    bucket_order_kernel(const double* __restrict__ U2, const double* __restrict__ cl_g, int m,
-                        int L, double* __restrict__ shat_sorted, uint32_t* __restrict__ order) {
-    extern __shared__ unsigned long long keys[];          // ncls order keys
-    const int ncls = m * (L + 1);
-    uint32_t* tie = (uint32_t*)(keys + ncls);             // ncls tie keys l 2^16 + j
-    double* cl = (double*)(tie + ((ncls + 1) & ~1));      // L+1 cosines
-    double* Uj = cl + (L + 1);                            // m norms
-    for (int l = threadIdx.x; l <= L; l += blockDim.x) cl[l] = cl_g[l];
-    for (int j = threadIdx.x; j < m; j += blockDim.x) Uj[j] = sqrt(U2[j]);
-    __syncthreads();
-    for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
-        const int j = c / (L + 1), l = c % (L + 1);
-        keys[c] = double_order(__dadd_rn(__dmul_rn(Uj[j], cl[l]), 0.0));  // -0 -> +0
-        tie[c] = ((uint32_t)l << 16) | (uint32_t)j;
-    }
-    __syncthreads();
+// The probing order in two launches.  First, one thread per bucket (j, l): the
+// key s_hat = fl(U_j c_l), U_j = fl(sqrt(U_j^2)), as an order-preserving
+// integer (-0 folded to +0), and the tie key l 2^16 + j.
+__global__ void bucket_keys_kernel(const double* __restrict__ U2, const double* __restrict__ cl,
+                                   int m, int L, unsigned long long* __restrict__ keys,
+                                   uint32_t* __restrict__ tie) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncls) return;
-    const unsigned long long k0 = keys[c];
-    const uint32_t t0 = tie[c];
-    int rank = 0;
-    for (int c1 = 0; c1 < ncls; ++c1) {
-        const unsigned long long k1 = keys[c1];
-        rank += (k1 > k0) || (k1 == k0 && tie[c1] > t0);
+    if (c >= m * (L + 1)) return;
+    const int j = c / (L + 1), l = c % (L + 1);
+    keys[c] = double_order(__dadd_rn(__dmul_rn(sqrt(U2[j]), cl[l]), 0.0));
+    tie[c] = ((uint32_t)l << 16) | (uint32_t)j;
+}
+
+// Then every block stages all keys in shared memory and each warp ranks buckets:
+// rank(c) = number of buckets with a greater (s_hat, l, j), counted by the lanes
+// over strided buckets and summed.  order[rank] = c, shat_sorted[rank] = s_hat.
+__global__ void __launch_bounds__(kBucketThreads)
+    bucket_rank_kernel(const unsigned long long* __restrict__ keys_g,
+                       const uint32_t* __restrict__ tie_g, int ncls,
+                       double* __restrict__ shat_sorted, uint32_t* __restrict__ order) {
+    extern __shared__ unsigned long long keys[];
+    uint32_t* tie = (uint32_t*)(keys + ncls);
+    for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
+        keys[c] = keys_g[c];
+        tie[c] = tie_g[c];
     }
-    order[rank] = (uint32_t)c;
-    shat_sorted[rank] = __dadd_rn(__dmul_rn(Uj[c / (L + 1)], cl[c % (L + 1)]), 0.0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < ncls; c += gridDim.x * wpb) {
+        const unsigned long long k0 = keys[c];
+        const uint32_t t0 = tie[c];
+        unsigned rank = 0;
+        for (int c1 = lane; c1 < ncls; c1 += 32) {
+            const unsigned long long k1 = keys[c1];
+            rank += (k1 > k0) || (k1 == k0 && tie[c1] > t0);
+        }
+        rank = __reduce_add_sync(0xffffffffu, rank);
+        if (lane == 0) {
+            order[rank] = (uint32_t)c;
+            shat_sorted[rank] = order_double(k0);
+        }
+    }
 }
 
 }  // namespace
@@ -863,17 +1036,27 @@ cudaError_t launch_class_cos(int L, float eps, double* cl, cudaStream_t st) {
                   L, eps, cl);
 }
 
+size_t bucket_order_temp_bytes(int m, int L) {
+    return (size_t)m * (L + 1) * (sizeof(unsigned long long) + sizeof(uint32_t));
+}
+
 cudaError_t launch_bucket_order(const double* U2, const double* cl, int m, int L,
-                                double* shat_sorted, uint32_t* order, cudaStream_t st) {
+                                double* shat_sorted, uint32_t* order, void* temp,
+                                cudaStream_t st) {
     const int ncls = m * (L + 1);
-    const size_t smem = sizeof(unsigned long long) * ncls + sizeof(uint32_t) * ((ncls + 1) & ~1) +
-                        sizeof(double) * (L + 1 + m);
-    cudaError_t e = cudaFuncSetAttribute(bucket_order_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    unsigned long long* keys = (unsigned long long*)temp;
+    uint32_t* tie = (uint32_t*)(keys + ncls);
+    cudaError_t e = launch("bucket_keys", bucket_keys_kernel, dim3((unsigned)ceil_div(ncls, 256)),
+                           dim3(256), 0, st, U2, cl, m, L, keys, tie);
     if (e != cudaSuccess) return e;
-    return launch("bucket_order", bucket_order_kernel,
-                  dim3((unsigned)ceil_div(ncls, kBucketThreads)), dim3(kBucketThreads), smem, st,
-                  U2, cl, m, L, shat_sorted, order);
+    const size_t smem = (sizeof(unsigned long long) + sizeof(uint32_t)) * ncls;
+    e = cudaFuncSetAttribute(bucket_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    const int wpb = kBucketThreads / 32;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ncls, wpb), 2 * 152);
+    return launch("bucket_order", bucket_rank_kernel, dim3(grid), dim3(kBucketThreads), smem, st,
+                  (const unsigned long long*)keys, (const uint32_t*)tie, ncls, shat_sorted, order);
 }
 
 }  // namespace nrlsh

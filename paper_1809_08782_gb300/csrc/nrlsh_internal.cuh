@@ -102,11 +102,20 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
 cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* sorted_ids,
                                   int64_t n, int m, uint32_t* sub_of_id, double* U2,
                                   uint32_t* jkeys, uint32_t* jvals, cudaStream_t st);
+// Uniform norm ranges (Section 5, Figure 3a): sub-dataset of every id, the
+// sort keys/values into storage order, sizes cnt[j] and U_j^2 (U2 zeroed by the
+// caller).  range: 6 words of scratch.
+cudaError_t launch_uniform_assign(const double* s_id, int64_t n, int m, unsigned long long* range,
+                                  uint32_t* sub_of_id, double* U2, uint32_t* jkeys,
+                                  uint32_t* jvals, uint32_t* cnt, cudaStream_t st);
+// Segment offsets seg[0..m] and histogram tiles from the sub-dataset sizes.
+cudaError_t launch_segments(const uint32_t* cnt, int m, int64_t tile, int64_t* seg,
+                            PosTile* tiles, int ntiles_max, cudaStream_t st);
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
-                                const uint32_t* perm, int64_t n, int m, const double* s_id,
-                                const double* U2, void* Xp, __nv_bfloat16* Xb, __nv_bfloat16* Xb2,
-                                double* s_pos, double* tau64, float* tau32, float* xnorm,
-                                cudaStream_t st);
+                                const uint32_t* perm, int64_t n, const uint32_t* sub_of_id,
+                                const double* s_id, const double* U2, void* Xp,
+                                __nv_bfloat16* Xb, __nv_bfloat16* Xb2, double* s_pos,
+                                double* tau64, float* tau32, float* xnorm, cudaStream_t st);
 // Sign random projection of rows of X (row stride ldx, stored dtype) with the FP32
 // fast tier; undecided (row, bit) pairs go through amb_list (capacity amb_cap,
 // count in *amb_count, which must start at 0) to the FP64 resolve kernel.
@@ -143,8 +152,11 @@ cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2,
 // c_l = cos(pi (1 - eps)(L - l) / L), correctly rounded, l = 0..L.
 cudaError_t launch_class_cos(int L, float eps, double* cl, cudaStream_t st);
 // The sorted (U_j, l) structure: probing order of the m (L+1) buckets.
+// temp: bucket_order_temp_bytes(m, L) bytes of scratch.
+size_t bucket_order_temp_bytes(int m, int L);
 cudaError_t launch_bucket_order(const double* U2, const double* cl, int m, int L,
-                                double* shat_sorted, uint32_t* order, cudaStream_t st);
+                                double* shat_sorted, uint32_t* order, void* temp,
+                                cudaStream_t st);
 
 // ----------------------------------------------------------- query launchers
 
@@ -163,7 +175,7 @@ struct Boundary {
 cudaError_t launch_threshold(const uint32_t* H, const uint32_t* order, int m, int L, int64_t nq,
                              int64_t n, int64_t budget, const int64_t* budgets, uint32_t flags,
                              uint8_t* lam, Boundary* bnd, cudaStream_t st);
-cudaError_t launch_select(const void* codes, const void* qcodes, int code_bytes, int64_t n, int m,
+cudaError_t launch_select(const void* codes, const void* qcodes, int code_bytes, const int64_t* seg, int m,
                           int L, int64_t nq, const uint8_t* lam, const Boundary* bnd,
                           uint32_t* cand, int64_t cap, cudaStream_t st);
 cudaError_t launch_rerank_fp32(const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
@@ -179,7 +191,7 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
 // Threshold walk, candidate selection, FP32 re-rank and exact top-k, one block
 // per query (the main query path after the histograms).
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
-                                int64_t nq, int64_t budget, const int64_t* budgets, uint32_t flags,
+                                const int64_t* seg, int64_t nq, int64_t budget, const int64_t* budgets, uint32_t flags,
                                 const void* codes, const void* qcodes, int code_bytes,
                                 const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
                                 const float* xnorm, const float* qnorm, const uint32_t* perm, int k,
@@ -188,7 +200,7 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
                                 float* out_scores, int out_ld, cudaStream_t st);
 // Persistent batched form: `ctas` CTAs pull queries from *work (zeroed by the caller).
 cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
-                                           int64_t n, const int64_t* budgets, const void* codes,
+                                           int64_t n, const int64_t* seg, const int64_t* budgets, const void* codes,
                                            const void* qcodes, int code_bytes, const void* Xp,
                                            nrlsh_dtype dt, int dp, int d, const float* Q,
                                            const float* xnorm, const float* qnorm,

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256)
 // whole buckets go to out[0, full) in position order; boundary-bucket items go
 // to out[full, full + r), the first r of them in position (= id) order.
 template <typename C>
-__device__ void dev_select(const C* __restrict__ codes, C cq, int64_t n, int m, int L,
+__device__ void dev_select(const C* __restrict__ codes, C cq, const int64_t* __restrict__ seg, int m, int L,
                            const uint8_t* lam_s, const Boundary& b, uint32_t* __restrict__ out) {
     __shared__ uint32_t wf[8], wb[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -192,7 +192,7 @@ __device__ void dev_select(const C* __restrict__ codes, C cq, int64_t n, int m, 
         const bool isb = j == b.j;
         if (lamj > L && !isb) continue;                       // uniform
         if (of_blk >= (uint32_t)b.full && ob_blk >= (uint32_t)b.r) break;
-        const int64_t s0 = seg_start(j, n, m), len = seg_start(j + 1, n, m) - s0;
+        const int64_t s0 = seg[j], len = seg[j + 1] - s0;
         const int64_t w0 = s0 + len * warp / 8, w1 = s0 + len * (warp + 1) / 8;
         uint32_t cf = 0, cb = 0;
         for (int64_t base = w0; base < w1; base += 32) {
@@ -248,14 +248,15 @@ __device__ void dev_select(const C* __restrict__ codes, C cq, int64_t n, int m, 
 
 template <typename C>
 __global__ void __launch_bounds__(256)
-    select_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t n, int m, int L,
+    select_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes,
+                  const int64_t* __restrict__ seg, int m, int L,
                   const uint8_t* __restrict__ lam, const Boundary* __restrict__ bnd,
                   uint32_t* __restrict__ cand, int64_t cap) {
     extern __shared__ uint8_t lam_s[];
     const int64_t q = blockIdx.x;
     for (int j = threadIdx.x; j < m; j += 256) lam_s[j] = lam[q * m + j];
     __syncthreads();
-    dev_select(codes, qcodes[q], n, m, L, lam_s, bnd[q], cand + q * cap);
+    dev_select(codes, qcodes[q], seg, m, L, lam_s, bnd[q], cand + q * cap);
 }
 
 // ------------------------------------------------------------------ rerank
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(256)
 template <typename T, typename C>
 __global__ void __launch_bounds__(256)
     probe_rerank_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order, int m,
-                        int L, int64_t n, int64_t budget, const int64_t* __restrict__ budgets,
+                        int L, int64_t n, const int64_t* __restrict__ seg, int64_t budget, const int64_t* __restrict__ budgets,
                         uint32_t flags, const C* __restrict__ codes, const C* __restrict__ qcodes,
                         const T* __restrict__ Xp, int dp, int d, const float* __restrict__ Q,
                         const float* __restrict__ xnorm, const float* __restrict__ qnorm,
@@ -693,7 +694,7 @@ __global__ void __launch_bounds__(256)
     const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n,
                                      budgets ? budgets[q] : budget, flags, cntj, lam_s);
     uint32_t* candq = cand + q * cap;
-    dev_select(codes, qcodes[q], n, m, L, lam_s, b, candq);
+    dev_select(codes, qcodes[q], seg, m, L, lam_s, b, candq);
     __syncthreads();
     const int64_t count = (int64_t)b.full + b.r;
     dev_rerank(Xp, dp, qs, candq, 0, count, xnorm, qnorm[q], kappa, lo + q * cap, hi + q * cap);
@@ -710,7 +711,8 @@ __global__ void __launch_bounds__(256)
 template <typename T, typename C>
 __global__ void __launch_bounds__(256)
     probe_rerank_persistent_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order,
-                                   int m, int L, int64_t n, const int64_t* __restrict__ budgets,
+                                   int m, int L, int64_t n, const int64_t* __restrict__ seg,
+                                   const int64_t* __restrict__ budgets,
                                    const C* __restrict__ codes, const C* __restrict__ qcodes,
                                    const T* __restrict__ Xp, int dp, int d,
                                    const float* __restrict__ Q, const float* __restrict__ xnorm,
@@ -738,7 +740,7 @@ __global__ void __launch_bounds__(256)
         load_query(Q, q, d, dp, qs);
         const int64_t Bq = min(max(budgets[q], (int64_t)1), cap);
         const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n, Bq, 0u, cntj, lam_s);
-        dev_select(codes, qcodes[q], n, m, L, lam_s, b, cand);
+        dev_select(codes, qcodes[q], seg, m, L, lam_s, b, cand);
         __syncthreads();
         const int64_t count = (int64_t)b.full + b.r;
         dev_rerank(Xp, dp, qs, cand, 0, count, xnorm, qnorm[q], kappa, lo, hi);
@@ -778,7 +780,7 @@ cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, i
     const int qb = queries_per_block;
     const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nq, qb));
     const size_t smem = 16384 + 2 * sizeof(uint16_t) * (size_t)(L + 1) * qb;
-#define NRLSH_H(C_, Q_)                                                                     \
+#define NRLSH_HIST_(C_, Q_)                                                                     \
     {                                                                                       \
         if (smem > 48 * 1024) {                                                             \
             cudaError_t e = cudaFuncSetAttribute(hist_kernel<C_, Q_>,                       \
@@ -791,14 +793,14 @@ cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, i
                       H);                                                                   \
     }
     if (code_bytes == 4) {
-        if (qb == 32) NRLSH_H(uint32_t, 32)
-        if (qb == 128) NRLSH_H(uint32_t, 128)
-        NRLSH_H(uint32_t, 64)
+        if (qb == 32) NRLSH_HIST_(uint32_t, 32)
+        if (qb == 128) NRLSH_HIST_(uint32_t, 128)
+        NRLSH_HIST_(uint32_t, 64)
     }
-    if (qb == 32) NRLSH_H(uint64_t, 32)
-    if (qb == 128) NRLSH_H(uint64_t, 128)
-    NRLSH_H(uint64_t, 64)
-#undef NRLSH_H
+    if (qb == 32) NRLSH_HIST_(uint64_t, 32)
+    if (qb == 128) NRLSH_HIST_(uint64_t, 128)
+    NRLSH_HIST_(uint64_t, 64)
+#undef NRLSH_HIST_
 }
 
 cudaError_t launch_threshold(const uint32_t* H, const uint32_t* order, int m, int L, int64_t nq,
@@ -809,15 +811,15 @@ cudaError_t launch_threshold(const uint32_t* H, const uint32_t* order, int m, in
                   flags, lam, bnd);
 }
 
-cudaError_t launch_select(const void* codes, const void* qcodes, int code_bytes, int64_t n, int m,
+cudaError_t launch_select(const void* codes, const void* qcodes, int code_bytes, const int64_t* seg, int m,
                           int L, int64_t nq, const uint8_t* lam, const Boundary* bnd,
                           uint32_t* cand, int64_t cap, cudaStream_t st) {
     if (code_bytes == 4)
         return launch("select_u32", select_kernel<uint32_t>, dim3((unsigned)nq), dim3(256),
-                      (size_t)m, st, (const uint32_t*)codes, (const uint32_t*)qcodes, n, m, L, lam,
+                      (size_t)m, st, (const uint32_t*)codes, (const uint32_t*)qcodes, seg, m, L, lam,
                       bnd, cand, cap);
     return launch("select_u64", select_kernel<uint64_t>, dim3((unsigned)nq), dim3(256), (size_t)m,
-                  st, (const uint64_t*)codes, (const uint64_t*)qcodes, n, m, L, lam, bnd, cand,
+                  st, (const uint64_t*)codes, (const uint64_t*)qcodes, seg, m, L, lam, bnd, cand,
                   cap);
 }
 
@@ -856,7 +858,7 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
 }
 
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
-                                int64_t nq, int64_t budget, const int64_t* budgets, uint32_t flags,
+                                const int64_t* seg, int64_t nq, int64_t budget, const int64_t* budgets, uint32_t flags,
                                 const void* codes, const void* qcodes, int code_bytes,
                                 const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
                                 const float* xnorm, const float* qnorm, const uint32_t* perm, int k,
@@ -874,7 +876,7 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
                                                  (int)smem);                                    \
             if (e != cudaSuccess) return e;                                                     \
         }                                                                                       \
-        return launch(NAME, kern, grid, dim3(256), smem, st, H, order, m, L, n, budget, budgets, \
+        return launch(NAME, kern, grid, dim3(256), smem, st, H, order, m, L, n, seg, budget, budgets, \
                       flags, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q, xnorm,\
                       qnorm, kappa, perm, k, ks, cand, lo, hi, cont, cont_s, cap, out_ids,      \
                       out_scores, out_ld);                                                      \
@@ -889,7 +891,7 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
 }
 
 cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
-                                           int64_t n, const int64_t* budgets, const void* codes,
+                                           int64_t n, const int64_t* seg, const int64_t* budgets, const void* codes,
                                            const void* qcodes, int code_bytes, const void* Xp,
                                            nrlsh_dtype dt, int dp, int d, const float* Q,
                                            const float* xnorm, const float* qnorm,
@@ -908,7 +910,7 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
             if (e != cudaSuccess) return e;                                                     \
         }                                                                                       \
         return launch(NAME, kern, dim3((unsigned)ctas), dim3(256), smem, st, H, order, m, L, n,  \
-                      budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q,    \
+                      seg, budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q,    \
                       xnorm, qnorm, kappa, perm, ks, k_max, slabs, cap, work, nq, out_ids,      \
                       out_scores);                                                              \
     }

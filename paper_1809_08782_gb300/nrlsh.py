@@ -46,6 +46,7 @@ SIGNATURES = {
     "nrlsh_query_candidates": (_I32, [_P, _P, _I64, _I64, _U32, _I64, _P, _P, _P]),
     "nrlsh_get_codes": (_I32, [_P, _P]),
     "nrlsh_get_partition": (_I32, [_P, _P, _P, _P]),
+    "nrlsh_get_segments": (_I32, [_P, _P]),
     "nrlsh_get_projections": (_I32, [_P, _P]),
     "nrlsh_get_buckets": (_I32, [_P, _P, _P, _P]),
     "nrlsh_get_info": (_I32, [_P, _P]),
@@ -61,16 +62,19 @@ class NrlshInfo(ctypes.Structure):
     _fields_ = [("n", _I64), ("d", _I32), ("m", _I32), ("L", _I32), ("dtype", _I32),
                 ("eps", _F32), ("seed", _U64), ("code_bytes", _I32), ("row_stride", _I32),
                 ("device_bytes", _I64), ("ambiguous_bits", _I64), ("projection", _I32),
-                ("device_error", _I32)]
+                ("device_error", _I32), ("partition", _I32), ("reserved", _I32)]
 
 
 class NrlshBuildOptions(ctypes.Structure):
-    _fields_ = [("dtype", _I32), ("eps", _F32), ("projection", _I32), ("stream", _P)]
+    _fields_ = [("dtype", _I32), ("eps", _F32), ("projection", _I32), ("partition", _I32),
+                ("stream", _P)]
 
 
 NRLSH_PROJECT_AUTO = 0
 NRLSH_PROJECT_SIMT = 1
 NRLSH_PROJECT_TENSOR = 2
+NRLSH_PARTITION_PERCENTILE = 0
+NRLSH_PARTITION_UNIFORM = 1
 
 
 class NrlshError(RuntimeError):
@@ -152,21 +156,25 @@ def _items_dtype(items: torch.Tensor) -> int:
 
 
 def nrlsh_build_ex(items: torch.Tensor, m: int, L: int, seed: int, eps: float = 0.1,
-                   stream=None, projection: Optional[int] = None) -> Index:
+                   stream=None, projection: Optional[int] = None,
+                   partition: Optional[int] = None) -> Index:
     """Index building (Algorithm 1).  items: (n, d) float32 or bfloat16, row-major.
-    projection selects the projection path (nrlsh_build_opts) when given."""
+    projection selects the projection path and partition the split into
+    sub-datasets (nrlsh_build_opts) when either is given."""
     lib = load()
     if items.dim() != 2:
         raise ValueError("items must be 2-D (n, d)")
     items = items.contiguous()
     n, d = items.shape
     out = ctypes.c_void_p()
-    if projection is None:
+    if projection is None and partition is None:
         _check(lib.nrlsh_build_ex(_ptr(items), n, d, m, L, seed, _items_dtype(items), eps,
                                   _stream(items, stream), ctypes.byref(out)))
     else:
         st = _stream(items, stream)
-        opts = NrlshBuildOptions(_items_dtype(items), eps, projection, st)
+        opts = NrlshBuildOptions(_items_dtype(items), eps,
+                                 NRLSH_PROJECT_AUTO if projection is None else projection,
+                                 NRLSH_PARTITION_PERCENTILE if partition is None else partition, st)
         _check(lib.nrlsh_build_opts(_ptr(items), n, d, m, L, seed, ctypes.byref(opts),
                                     ctypes.byref(out)))
     return Index(out, n, d, m, L, items.device)
@@ -314,6 +322,13 @@ def nrlsh_get_partition(index: Index):
     s = torch.empty(index.n, dtype=torch.float64)
     _check(load().nrlsh_get_partition(index.handle, _ptr(sub), _ptr(U2), _ptr(s)))
     return sub, U2, s
+
+
+def nrlsh_get_segments(index: Index) -> torch.Tensor:
+    """Storage offsets: S_j occupies positions [seg[j], seg[j+1])."""
+    seg = torch.empty(index.m + 1, dtype=torch.int64)
+    _check(load().nrlsh_get_segments(index.handle, _ptr(seg)))
+    return seg
 
 
 def nrlsh_get_projections(index: Index) -> torch.Tensor:

@@ -20,13 +20,16 @@ def to_dev_items(items: np.ndarray, dtype: str):
 
 
 def build_pair(items: np.ndarray, dtype: str, m: int, L: int, seed: int, eps: float,
-               projection=None):
+               projection=None, partition: str = "percentile"):
     """(library index, oracle index) on the same inputs; projection forces the
-    projection path (N.NRLSH_PROJECT_SIMT / N.NRLSH_PROJECT_TENSOR)."""
+    projection path (N.NRLSH_PROJECT_SIMT / N.NRLSH_PROJECT_TENSOR), partition
+    selects percentile or uniform norm ranges."""
     from paper_1809_08782_gb300 import workloads as W
     eps = f32(eps)
-    lib = N.nrlsh_build_ex(to_dev_items(items, dtype), m, L, seed, eps=eps, projection=projection)
-    ref = O.build(W.items_to_f64(items, dtype), m, L, seed, eps=eps)
+    part = {"percentile": None, "uniform": N.NRLSH_PARTITION_UNIFORM}[partition]
+    lib = N.nrlsh_build_ex(to_dev_items(items, dtype), m, L, seed, eps=eps, projection=projection,
+                           partition=part)
+    ref = O.build(W.items_to_f64(items, dtype), m, L, seed, eps=eps, partition_scheme=partition)
     return lib, ref
 
 
@@ -41,6 +44,7 @@ def check_index(lib, ref, projection=None):
     assert np.array_equal(s.numpy(), ref.s), "squared norms differ"
     assert np.array_equal(sub.numpy(), ref.sub), "partition differs"
     assert np.array_equal(U2.numpy(), ref.U2), "U_j^2 differs"
+    assert N.nrlsh_get_segments(lib).tolist() == list(ref.bounds), "segment offsets differ"
     codes = N.nrlsh_get_codes(lib).numpy().view(np.uint64)
     bad = np.flatnonzero(codes != ref.codes)
     assert bad.size == 0, f"{bad.size} codes differ, first ids {bad[:8]}"

@@ -84,3 +84,45 @@ def test_null_arguments(lib):
     assert lib.nrlsh_query(None, None, 1, 10, 10, None, None) == -1
     assert lib.nrlsh_get_codes(None, None) == -1
     lib.nrlsh_free(None)   # no-op
+
+
+def test_build_opts_rejects_unknown_partition_and_projection(lib):
+    import paper_1809_08782_gb300.nrlsh as N
+    buf = np.zeros(64, dtype=np.float32)
+    for proj, part in ((0, 7), (0, -1), (9, 0)):
+        opts = N.NrlshBuildOptions(0, 0.1, proj, part, None)
+        out = ctypes.c_void_p()
+        st = lib.nrlsh_build_opts(buf.ctypes.data, 16, 4, 2, 8, 1, ctypes.byref(opts),
+                                  ctypes.byref(out))
+        assert st == -1 and out.value is None
+    assert lib.nrlsh_build_opts(buf.ctypes.data, 16, 4, 2, 8, 1, None, ctypes.byref(out)) == -1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Offsets and sizes of the public structs, as a C compiler lays them out
+    from include/nrlsh.h, equal the binding's ctypes structures."""
+    import shutil
+    import subprocess
+    import paper_1809_08782_gb300.nrlsh as N
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"nrlsh_info": N.NrlshInfo, "nrlsh_build_options": N.NrlshBuildOptions}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nrlsh.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
