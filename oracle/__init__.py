@@ -11,6 +11,7 @@ library never imports it.  Only the tests, ``__graft_entry__.smoke()`` and
 Modules:
   philox       counter-based generator for the projection matrix A
   nrlsh        index build, query probing, re-rank and top-k
+  multitable   Algorithm 2 with T hash tables and one probe per table
   simple_lsh   SIMPLE-LSH with one global U (Eq. 8), written separately
   exact        exact MIPS by rational arithmetic (Eq. 1) and recall@k
 """
