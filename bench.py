@@ -565,8 +565,9 @@ def batched_run(args):
 
 def curves_run(args):
     """Probed items vs recall@10 (Figure 2 protocol) on the synthetic stand-ins:
-    RANGE-LSH vs SIMPLE-LSH at L = 16/32/64 with m = 32/64/128 (Section 5), and an
-    m sweep at L = 32 (Figure 3b).  Prints JSON lines (not the bench line)."""
+    RANGE-LSH vs SIMPLE-LSH at L = 16/32/64 with m = 32/64/128 (Section 5), an
+    m sweep at L = 32 (Figure 3b) and percentile vs uniform partitioning at L = 32,
+    m = 32 (Figure 3a).  Prints JSON lines (not the bench line)."""
     import torch
 
     import paper_1809_08782_gb300.nrlsh as N
@@ -583,14 +584,50 @@ def curves_run(args):
         truth = C.exact_topk(idx, Q)
         idx.free()
         eps = float(np.float32(args.eps if args.eps is not None else 0.1))
-        for L, m in ((16, 32), (32, 64), (64, 128)):
+        sets = args.curve_sets.split(",")
+        for L, m in (((16, 32), (32, 64), (64, 128)) if "fig2" in sets else ()):
             r = C.compare(X, Q, L, m, w.index_seed, eps, truth)
             r.update({"workload": name, "queries": w.nq, "eps": eps})
             print(json.dumps(r), flush=True)
-        if name.startswith("yahoo"):
+        if name.startswith("yahoo") and "fig3b" in sets:
             for m in (32, 64, 128, 256):
                 r = C.compare(X, Q, 32, m, w.index_seed, eps, truth)
                 r.update({"workload": name, "queries": w.nq, "eps": eps, "m_sweep": True})
+                print(json.dumps(r), flush=True)
+        # Figure 3a: percentile versus uniform norm ranges, code length 32, m = 32
+        if "fig3a" in sets:
+            r = C.compare_partitions(X, Q, 32, 32, w.index_seed, eps, truth)
+            r.update({"workload": name, "queries": w.nq, "eps": eps, "partitions": True})
+            print(json.dumps(r), flush=True)
+
+
+def multitable_run(args):
+    """Algorithm 2 with several single-probe tables (the variant of the paper's
+    supplementary comparison): probed items, recall@10 and device time per query as
+    the code is split into more, shorter tables; RANGE-LSH (m = 32) vs SIMPLE-LSH
+    (m = 1) at L = 32 and 64.  Prints JSON lines (not the bench line)."""
+    import torch
+
+    import paper_1809_08782_gb300.nrlsh as N
+    from paper_1809_08782_gb300 import build as B
+    from paper_1809_08782_gb300 import curves as C
+    B.build()
+    N.load()
+    for name in args.curve_workloads.split(","):
+        w = W.make_workload(name, nq=args.queries, with_data=False)
+        items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, w.dtype)
+        X = W.to_torch(items, w.dtype, "cuda")
+        Q = torch.from_numpy(W.gen_queries(w.nq, w.d, w.query_seed)).cuda()
+        idx = N.nrlsh_build_ex(X, 1, 8, w.index_seed)
+        truth = C.exact_topk(idx, Q)
+        idx.free()
+        eps = float(np.float32(args.eps if args.eps is not None else 0.1))
+        for L in (32, 64):
+            tables = [t for t in (1, 2, 4, 8, 16, 32, 64) if L % t == 0 and L // t >= 2]
+            for m in (32, 1):
+                r = C.multitable_curve(X, Q, truth, m, L, w.index_seed, eps, tables)
+                r.update({"workload": name, "queries": w.nq, "eps": eps,
+                          "method": "range_lsh" if m > 1 else "simple_lsh"})
                 print(json.dumps(r), flush=True)
 
 
@@ -612,7 +649,11 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving sweep instead of the bench line")
     ap.add_argument("--curves", action="store_true", help="probed-item/recall curves")
     ap.add_argument("--batched", action="store_true", help="batching-form run (ImageNet-sized)")
+    ap.add_argument("--multitable", action="store_true",
+                    help="multi-table single-probe curves (Algorithm 2)")
     ap.add_argument("--curve-workloads", default="netflix-n17770-d300,yahoo-n136736-d300")
+    ap.add_argument("--curve-sets", default="fig2,fig3a,fig3b",
+                    help="which curve families --curves runs")
     ap.add_argument("--serve-n", type=int, default=10_000_000)
     ap.add_argument("--serve-requests", type=int, default=20_000)
     ap.add_argument("--serve-rate0", type=float, default=25_000.0)
@@ -631,6 +672,9 @@ def main():
         return
     if args.batched:
         batched_run(args)
+        return
+    if args.multitable:
+        multitable_run(args)
         return
     if args.impl == "reference":
         for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):

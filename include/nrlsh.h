@@ -231,6 +231,35 @@ NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* index, const float
                                            int64_t* ids, float* scores, void* stream);
 
 /*
+ * Multi-table single-probe query (Algorithm 2 with several hash tables).  The L
+ * code bits of the index are read as `tables` hash tables of L / tables bits:
+ * table t holds bits [t L / tables, (t + 1) L / tables).  For every sub-dataset
+ * S_j, a single probe of each table visits the bucket equal to the query's code
+ * in that table, so the probed items are
+ *     C(q) = { x : code_t(x) = code_t(q) for some table t }  (all sub-datasets),
+ * and the result is the exact top-k of C(q) by q^T x (scores and tie rule as in
+ * nrlsh_query_ex): Algorithm 2's best item over the sub-datasets, extended to k.
+ *   tables          1 <= tables <= L, L % tables == 0
+ *   max_candidates  0: C(q) is re-ranked whole; > 0: only the first
+ *                   max_candidates items of C(q) in storage order (sub-dataset,
+ *                   then id) are re-ranked
+ *   ids, scores     nq x k, best first, padded with (-1, -inf) past |C(q)|
+ *   probed          nq int64 or NULL: |C(q)| before the cap
+ * Scratch of about 24 bytes per (query, candidate slot) is taken in chunks of
+ * queries of at most 1 GiB.
+ */
+NRLSH_API nrlsh_status nrlsh_query_multitable(const nrlsh_index* index, const float* queries,
+                                              int64_t nq, int32_t tables, int32_t k,
+                                              int64_t max_candidates, int64_t* ids,
+                                              float* scores, int64_t* probed, void* stream);
+/* The first min(|C(q)|, cap) items of C(q) of nrlsh_query_multitable, as original
+ * ids in storage order (cand: nq x cap int32), and |C(q)| (count: nq int64). */
+NRLSH_API nrlsh_status nrlsh_multitable_candidates(const nrlsh_index* index,
+                                                   const float* queries, int64_t nq,
+                                                   int32_t tables, int64_t cap, int32_t* cand,
+                                                   int64_t* count, void* stream);
+
+/*
  * Introspection of the query path, for testing against a reference.  Device or
  * host pointers as above.
  * nrlsh_hash_queries: codes (nq uint64; bit b of the code is hash bit b).

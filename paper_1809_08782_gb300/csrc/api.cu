@@ -617,6 +617,75 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
     return NRLSH_OK;
 }
 
+// Multi-table single probe (Algorithm 2) for queries [0, nq): hash, then select
+// C(q) and take the exact top-k of its first `cap` items (or, with cand_ids,
+// report their ids).  Queries go in chunks whose scratch stays within 1 GiB.
+constexpr int64_t kMultitableFusedCap = 4096;
+
+nrlsh_status run_multitable(const nrlsh_index* ix, const float* Q, int64_t nq, int32_t tables,
+                            int32_t k, int64_t cap, int64_t* ids, float* scores, int64_t* probed,
+                            int32_t* cand_ids, cudaStream_t st) {
+    const int64_t per_query = cap * (4 + 4 + 4 + 4 + 8) + ix->code_bytes + 64;
+    int64_t chunk = std::max<int64_t>(1, ((int64_t)1 << 30) / per_query);
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(nq, 1));
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t qc = std::min(chunk, nq - q0);
+        const float* Qc = Q + q0 * ix->d;
+        Scratch sc(st);
+        float* qnorm;
+        char* qcodes;
+        unsigned* qamb;
+        unsigned long long* qamb_list;
+        const size_t qamb_cap = ambiguity_capacity(qc, ix->L);
+        NRLSH_CKS(sc.get(&qnorm, qc));
+        NRLSH_CKS(sc.get(&qamb, 1));
+        NRLSH_CKS(sc.get(&qamb_list, qamb_cap));
+        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
+        NRLSH_CKS(sc.get(&qcodes, qc * ix->code_bytes));
+        NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
+        // P(q) = [q; 0] (Eq. 8), hashed by Eq. 4
+        NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
+                                     ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
+                                     qamb_list, qamb, (unsigned)qamb_cap, st));
+        uint32_t *cand, *cont = nullptr;
+        float *lo = nullptr, *hi = nullptr;
+        double* cont_s = nullptr;
+        NRLSH_CKS(sc.get(&cand, qc * cap));
+        if (!cand_ids) {
+            NRLSH_CKS(sc.get(&lo, qc * cap));
+            NRLSH_CKS(sc.get(&hi, qc * cap));
+            NRLSH_CKS(sc.get(&cont, qc * cap));
+            NRLSH_CKS(sc.get(&cont_s, qc * cap));
+        }
+        if (cand_ids || cap <= kMultitableFusedCap) {
+            // short lists: selection, re-rank and top-k in one block per query
+            NRLSH_CK(launch_multitable(ix->codes, qcodes, ix->code_bytes, ix->n, ix->L, tables,
+                                       ix->Xp, ix->dtype, ix->dp, ix->d, Qc, ix->xnorm, qnorm,
+                                       ix->perm, k, cand, lo, hi, cont, cont_s, cap, qc,
+                                       ids ? ids + q0 * k : nullptr,
+                                       scores ? scores + q0 * k : nullptr, k,
+                                       probed ? probed + q0 : nullptr,
+                                       cand_ids ? cand_ids + q0 * cap : nullptr, cap, st));
+            continue;
+        }
+        // long or uneven lists: the re-rank is spread over all SMs by a work list
+        Boundary* bnd;
+        int64_t* work_off;
+        unsigned long long* work_ctr;
+        NRLSH_CKS(sc.get(&bnd, qc));
+        NRLSH_CKS(sc.get(&work_off, qc + 1));
+        NRLSH_CKS(sc.get(&work_ctr, 1));
+        NRLSH_CK(launch_multitable_select(ix->codes, qcodes, ix->code_bytes, ix->n, ix->L, tables,
+                                          cand, cap, qc, bnd, probed ? probed + q0 : nullptr, st));
+        NRLSH_CK(launch_rerank_work(ix->Xp, ix->dtype, ix->dp, ix->d, Qc, qc, cand, cap, bnd,
+                                    work_off, work_ctr, ix->xnorm, qnorm, lo, hi, st));
+        NRLSH_CK(launch_topk(lo, hi, cand, cap, bnd, qc, k, nullptr, ix->Xp, ix->dtype, ix->dp,
+                             ix->d, Qc, ix->xnorm, qnorm, ix->perm, cont, cont_s, ids + q0 * k,
+                             scores + q0 * k, k, st));
+    }
+    return NRLSH_OK;
+}
+
 nrlsh_status check_query_args(const nrlsh_index* ix, const float* Q, int64_t nq) {
     if (!ix) return arg_error("index is NULL");
     if (nq < 0) return arg_error("need nq >= 0");
@@ -741,6 +810,58 @@ NRLSH_API nrlsh_status nrlsh_query_histograms(const nrlsh_index* ix, const float
     NRLSH_CKS(stage_out(sc, H, (size_t)nq * ix->ncls, oh, &o.H));
     NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, 1, 0u, Stage::Hist, o, st));
     return finish_out(st, {&oh}, oh.host || Qd != queries);
+}
+
+NRLSH_API nrlsh_status nrlsh_query_multitable(const nrlsh_index* ix, const float* queries,
+                                              int64_t nq, int32_t tables, int32_t k,
+                                              int64_t max_candidates, int64_t* ids,
+                                              float* scores, int64_t* probed, void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (tables < 1 || tables > ix->L || ix->L % tables != 0)
+        return arg_error("need 1 <= tables <= L with L % tables == 0");
+    if (k < 1 || k > NRLSH_MAX_K) return arg_error("need 1 <= k <= 1024");
+    if (max_candidates < 0) return arg_error("need max_candidates >= 0");
+    if (nq > 0 && (!ids || !scores)) return arg_error("ids/scores is NULL");
+    if (nq == 0) return NRLSH_OK;
+    const int64_t cap = max_candidates == 0 ? ix->n : std::min(max_candidates, ix->n);
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    Scratch sc(st);
+    const void* Qd;
+    NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    OutStage oi, os, op;
+    int64_t* di;
+    float* ds;
+    int64_t* dp = nullptr;
+    NRLSH_CKS(stage_out(sc, ids, (size_t)(nq * k), oi, &di));
+    NRLSH_CKS(stage_out(sc, scores, (size_t)(nq * k), os, &ds));
+    if (probed) NRLSH_CKS(stage_out(sc, probed, (size_t)nq, op, &dp));
+    NRLSH_CKS(run_multitable(ix, (const float*)Qd, nq, tables, k, cap, di, ds, dp, nullptr, st));
+    return finish_out(st, {&oi, &os, &op}, oi.host || os.host || op.host);
+}
+
+NRLSH_API nrlsh_status nrlsh_multitable_candidates(const nrlsh_index* ix, const float* queries,
+                                                   int64_t nq, int32_t tables, int64_t cap,
+                                                   int32_t* cand, int64_t* count, void* stream) {
+    NRLSH_CKS(check_query_args(ix, queries, nq));
+    if (tables < 1 || tables > ix->L || ix->L % tables != 0)
+        return arg_error("need 1 <= tables <= L with L % tables == 0");
+    if (cap < 1) return arg_error("need cap >= 1");
+    if (nq > 0 && (!cand || !count)) return arg_error("cand/count is NULL");
+    if (nq == 0) return NRLSH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    Scratch sc(st);
+    const void* Qd;
+    NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    OutStage oc, on;
+    int32_t* dc;
+    int64_t* dn;
+    NRLSH_CKS(stage_out(sc, cand, (size_t)(nq * cap), oc, &dc));
+    NRLSH_CKS(stage_out(sc, count, (size_t)nq, on, &dn));
+    NRLSH_CKS(run_multitable(ix, (const float*)Qd, nq, tables, 1, cap, nullptr, nullptr, dn, dc,
+                             st));
+    return finish_out(st, {&oc, &on}, oc.host || on.host);
 }
 
 NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* ix, const float* queries,

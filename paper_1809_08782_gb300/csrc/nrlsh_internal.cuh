@@ -208,6 +208,28 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
                                            uint32_t* slabs, int64_t cap, int ctas, unsigned* work,
                                            int64_t nq, int64_t* out_ids, float* out_scores,
                                            cudaStream_t st);
+// Multi-table single probe (Algorithm 2): L bits as `tables` tables of L / tables
+// bits; block per query selects C(q), re-ranks and takes the exact top-k of its
+// first min(|C(q)|, cap) items.  probed (may be null) receives |C(q)|; with
+// cand_ids non-null only the candidate ids are written instead.
+cudaError_t launch_multitable(const void* codes, const void* qcodes, int code_bytes, int64_t n,
+                              int L, int tables, const void* Xp, nrlsh_dtype dt, int dp, int d,
+                              const float* Q, const float* xnorm, const float* qnorm,
+                              const uint32_t* perm, int k, uint32_t* cand, float* lo, float* hi,
+                              uint32_t* cont, double* cont_s, int64_t cap, int64_t nq,
+                              int64_t* out_ids, float* out_scores, int out_ld, int64_t* probed,
+                              int32_t* cand_ids, int64_t cand_ld, cudaStream_t st);
+// The same selection alone (bnd[q].full = min(|C(q)|, cap)), and a persistent
+// FP32 re-rank whose blocks take 256-candidate chunks of any query from a work
+// list (work_off: nq + 1 int64 scratch, work_ctr: one word), for lists too
+// long or too uneven for a block per query.
+cudaError_t launch_multitable_select(const void* codes, const void* qcodes, int code_bytes,
+                                     int64_t n, int L, int tables, uint32_t* cand, int64_t cap,
+                                     int64_t nq, Boundary* bnd, int64_t* probed, cudaStream_t st);
+cudaError_t launch_rerank_work(const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
+                               int64_t nq, const uint32_t* cand, int64_t cap, const Boundary* bnd,
+                               int64_t* work_off, unsigned long long* work_ctr, const float* xnorm,
+                               const float* qnorm, float* lo, float* hi, cudaStream_t st);
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
                                const uint32_t* perm, int64_t nq, int32_t* out, int64_t out_cap,
                                int64_t* count, cudaStream_t st);

@@ -751,6 +751,183 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ------------------------------------------- multi-table single probe (Alg. 2)
+
+// The index's L bits read as T tables of Lt = L / T bits.  Item x is probed when
+// some table field of v = c_x xor c_q is zero, tested for all fields at once:
+// (v - ONES) & ~v & HIGHS != 0, ONES holding the low bit and HIGHS the high bit
+// of every field.  A borrow can only cross into a field above a zero field, so
+// the test is exact.
+template <typename C>
+__device__ __forceinline__ bool table_hit(C v, C ones, C highs) {
+    return ((C)(v - ones) & (C)~v & highs) != 0;
+}
+
+// Block phase (256 threads): ordered compaction of C(q) over all n positions
+// (storage order: sub-dataset, then id).  Warps own contiguous position ranges;
+// a counting sweep, a scan over the 8 warps, then a writing sweep with ballot
+// prefixes.  The first min(|C(q)|, cap) positions go to out; returns |C(q)|.
+template <typename C>
+__device__ int64_t dev_select_tables(const C* __restrict__ codes, C cq, int64_t n, C ones, C highs,
+                                     uint32_t* __restrict__ out, int64_t cap) {
+    __shared__ uint32_t wc[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t w0 = n * warp / 8, w1 = n * (warp + 1) / 8;
+    uint32_t c = 0;
+    for (int64_t base = w0; base < w1; base += 32) {
+        const int64_t p = base + lane;
+        const bool hit = p < w1 && table_hit<C>(cq ^ codes[p], ones, highs);
+        c += __popc(__ballot_sync(0xffffffffu, hit));
+    }
+    if (lane == 0) wc[warp] = c;
+    __syncthreads();
+    int64_t off = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+        off += w < warp ? wc[w] : 0u;
+        total += wc[w];
+    }
+    for (int64_t base = w0; base < w1 && off < cap; base += 32) {
+        const int64_t p = base + lane;
+        const bool hit = p < w1 && table_hit<C>(cq ^ codes[p], ones, highs);
+        const unsigned b = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int64_t slot = off + __popc(b & lt);
+            if (slot < cap) out[slot] = (uint32_t)p;
+        }
+        off += __popc(b);
+    }
+    __syncthreads();
+    return total;
+}
+
+// Block per query: C(q) only.  bnd[q].full = min(|C(q)|, cap) (r = 0), so the
+// re-rank and top-k kernels of the multi-probe path take the list as it is.
+template <typename C>
+__global__ void __launch_bounds__(256)
+    multitable_select_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t n,
+                             C ones, C highs, uint32_t* __restrict__ cand, int64_t cap,
+                             Boundary* __restrict__ bnd, int64_t* __restrict__ probed) {
+    const int64_t q = blockIdx.x;
+    const int64_t total = dev_select_tables<C>(codes, qcodes[q], n, ones, highs, cand + q * cap, cap);
+    if (threadIdx.x == 0) {
+        if (probed) probed[q] = total;
+        bnd[q] = Boundary{0, 0, 0, (int32_t)min(total, cap)};
+    }
+}
+
+// Work list of the re-rank: query q owns items [work_off[q], work_off[q+1]) of
+// ceil(count_q / kWorkChunk) chunks each (one block of 1,024 threads; exclusive
+// scan in tiles with a running carry).
+constexpr int kWorkChunk = 256;
+
+__global__ void __launch_bounds__(1024)
+    work_offsets_kernel(const Boundary* __restrict__ bnd, int64_t nq, int64_t* __restrict__ work_off) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nq; base += 1024) {
+        const int64_t q = base + threadIdx.x;
+        const int64_t v = q < nq ? ceil_div((int64_t)bnd[q].full + bnd[q].r, kWorkChunk) : 0;
+        int64_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const int64_t carry = carry_s;
+        if (q < nq) work_off[q] = carry + (warp ? wsum[warp - 1] : 0) + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = carry + wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) work_off[nq] = carry_s;
+}
+
+// Persistent FP32 re-rank over the work list: blocks take chunks from *work_ctr,
+// find their query by binary search in work_off and score kWorkChunk candidates,
+// so one query with a huge C(q) is spread over every SM.
+template <typename T>
+__global__ void __launch_bounds__(kRerankWarps * 32)
+    rerank_work_kernel(const T* __restrict__ Xp, int dp, int d, const float* __restrict__ Q,
+                       const uint32_t* __restrict__ cand, int64_t cap,
+                       const Boundary* __restrict__ bnd, const int64_t* __restrict__ work_off,
+                       int64_t nq, unsigned long long* __restrict__ work_ctr,
+                       const float* __restrict__ xnorm, const float* __restrict__ qnorm,
+                       float kappa, float* __restrict__ lo, float* __restrict__ hi) {
+    extern __shared__ __align__(16) float qs[];
+    __shared__ int64_t w_s;
+    const int64_t total = work_off[nq];
+    int64_t cur_q = -1;
+    for (;;) {
+        if (threadIdx.x == 0) w_s = (int64_t)atomicAdd(work_ctr, 1ull);
+        __syncthreads();
+        const int64_t w = w_s;
+        if (w >= total) break;
+        int64_t a = 0, b = nq;                 // work_off[a] <= w < work_off[b]
+        while (b - a > 1) {
+            const int64_t mid = (a + b) >> 1;
+            if (work_off[mid] <= w) a = mid; else b = mid;
+        }
+        const int64_t q = a;
+        if (q != cur_q) {
+            load_query(Q, q, d, dp, qs);
+            cur_q = q;
+        }
+        __syncthreads();
+        const int64_t count = (int64_t)bnd[q].full + bnd[q].r;
+        const int64_t i0 = (w - work_off[q]) * kWorkChunk;
+        dev_rerank(Xp, dp, qs, cand + q * cap, i0, min(count, i0 + kWorkChunk), xnorm, qnorm[q],
+                   kappa, lo + q * cap, hi + q * cap);
+        __syncthreads();
+    }
+}
+
+// Block per query: single-probe selection over the T tables, FP32 re-rank and the
+// exact top-k of the first min(|C(q)|, cap) candidates; probed[q] = |C(q)|.  With
+// cand_ids non-null only the candidates' ids are written (cand_ld per query).
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    multitable_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t n, C ones,
+                      C highs, const T* __restrict__ Xp, int dp, int d,
+                      const float* __restrict__ Q, const float* __restrict__ xnorm,
+                      const float* __restrict__ qnorm, float kappa,
+                      const uint32_t* __restrict__ perm, int k, uint32_t* __restrict__ cand,
+                      float* __restrict__ lo, float* __restrict__ hi, uint32_t* __restrict__ cont,
+                      double* __restrict__ cont_s, int64_t cap, int64_t* __restrict__ out_ids,
+                      float* __restrict__ out_scores, int out_ld, int64_t* __restrict__ probed,
+                      int32_t* __restrict__ cand_ids, int64_t cand_ld) {
+    extern __shared__ __align__(16) float qs[];
+    const int64_t q = blockIdx.x;
+    uint32_t* candq = cand + q * cap;
+    const int64_t total = dev_select_tables<C>(codes, qcodes[q], n, ones, highs, candq, cap);
+    const int64_t count = min(total, cap);
+    if (threadIdx.x == 0 && probed) probed[q] = total;
+    if (cand_ids) {
+        for (int64_t i = threadIdx.x; i < count; i += blockDim.x)
+            cand_ids[q * cand_ld + i] = (int32_t)perm[candq[i]];
+        return;
+    }
+    load_query(Q, q, d, dp, qs);
+    __syncthreads();
+    dev_rerank(Xp, dp, qs, candq, 0, count, xnorm, qnorm[q], kappa, lo + q * cap, hi + q * cap);
+    __syncthreads();
+    dev_topk(lo + q * cap, hi + q * cap, candq, count, k, out_ld, Xp, dp, d, qs, qnorm[q], xnorm,
+             perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld, out_scores + q * out_ld);
+}
+
 __global__ void cand_to_ids_kernel(const uint32_t* __restrict__ cand, int64_t cap,
                                    const Boundary* __restrict__ bnd,
                                    const uint32_t* __restrict__ perm, int32_t* out, int64_t out_cap,
@@ -921,6 +1098,66 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
     if (code_bytes == 4) NRLSH_PP(float, uint32_t, "probe_rerank_persistent")
     NRLSH_PP(float, uint64_t, "probe_rerank_persistent")
 #undef NRLSH_PP
+}
+
+cudaError_t launch_multitable(const void* codes, const void* qcodes, int code_bytes, int64_t n,
+                              int L, int tables, const void* Xp, nrlsh_dtype dt, int dp, int d,
+                              const float* Q, const float* xnorm, const float* qnorm,
+                              const uint32_t* perm, int k, uint32_t* cand, float* lo, float* hi,
+                              uint32_t* cont, double* cont_s, int64_t cap, int64_t nq,
+                              int64_t* out_ids, float* out_scores, int out_ld, int64_t* probed,
+                              int32_t* cand_ids, int64_t cand_ld, cudaStream_t st) {
+    const int Lt = L / tables;
+    uint64_t ones = 0;
+    for (int t = 0; t < tables; ++t) ones |= 1ull << (t * Lt);
+    const uint64_t highs = ones << (Lt - 1);
+    const size_t smem = sizeof(float) * (size_t)dp;
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+    const dim3 grid((unsigned)nq);
+#define NRLSH_MT(T_, C_, NAME)                                                                      {                                                                                                   auto kern = multitable_kernel<T_, C_>;                                                          if (smem > 48 * 1024) {                                                                             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,                                                  (int)smem);                                                if (e != cudaSuccess) return e;                                                             }                                                                                               return launch(NAME, kern, grid, dim3(256), smem, st, (const C_*)codes, (const C_*)qcodes,                       n, (C_)ones, (C_)highs, (const T_*)Xp, dp, d, Q, xnorm, qnorm, kappa, perm,                       k, cand, lo, hi, cont, cont_s, cap, out_ids, out_scores, out_ld, probed,                         cand_ids, cand_ld);                                                           }
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_MT(__nv_bfloat16, uint32_t, "multitable_bf16")
+        NRLSH_MT(__nv_bfloat16, uint64_t, "multitable_bf16")
+    }
+    if (code_bytes == 4) NRLSH_MT(float, uint32_t, "multitable")
+    NRLSH_MT(float, uint64_t, "multitable")
+#undef NRLSH_MT
+}
+
+cudaError_t launch_multitable_select(const void* codes, const void* qcodes, int code_bytes,
+                                     int64_t n, int L, int tables, uint32_t* cand, int64_t cap,
+                                     int64_t nq, Boundary* bnd, int64_t* probed, cudaStream_t st) {
+    const int Lt = L / tables;
+    uint64_t ones = 0;
+    for (int t = 0; t < tables; ++t) ones |= 1ull << (t * Lt);
+    const uint64_t highs = ones << (Lt - 1);
+    if (code_bytes == 4)
+        return launch("multitable_select", multitable_select_kernel<uint32_t>, dim3((unsigned)nq),
+                      dim3(256), 0, st, (const uint32_t*)codes, (const uint32_t*)qcodes, n,
+                      (uint32_t)ones, (uint32_t)highs, cand, cap, bnd, probed);
+    return launch("multitable_select", multitable_select_kernel<uint64_t>, dim3((unsigned)nq),
+                  dim3(256), 0, st, (const uint64_t*)codes, (const uint64_t*)qcodes, n, ones, highs,
+                  cand, cap, bnd, probed);
+}
+
+cudaError_t launch_rerank_work(const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
+                               int64_t nq, const uint32_t* cand, int64_t cap, const Boundary* bnd,
+                               int64_t* work_off, unsigned long long* work_ctr, const float* xnorm,
+                               const float* qnorm, float* lo, float* hi, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(work_ctr, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    e = launch("work_offsets", work_offsets_kernel, dim3(1), dim3(1024), 0, st, bnd, nq, work_off);
+    if (e != cudaSuccess) return e;
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+    const size_t smem = sizeof(float) * (size_t)dp;
+    const dim3 grid(4 * 152);
+    if (dt == NRLSH_BF16)
+        return launch("rerank_work_bf16", rerank_work_kernel<__nv_bfloat16>, grid,
+                      dim3(kRerankWarps * 32), smem, st, (const __nv_bfloat16*)Xp, dp, d, Q, cand,
+                      cap, bnd, (const int64_t*)work_off, nq, work_ctr, xnorm, qnorm, kappa, lo, hi);
+    return launch("rerank_work", rerank_work_kernel<float>, grid, dim3(kRerankWarps * 32), smem, st,
+                  (const float*)Xp, dp, d, Q, cand, cap, bnd, (const int64_t*)work_off, nq,
+                  work_ctr, xnorm, qnorm, kappa, lo, hi);
 }
 
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,

@@ -1,4 +1,4 @@
-"""Probed-item / recall curves (the protocol of Figure 2 and Figure 3b of the
+"""Probed-item / recall curves (the protocol of Figure 2 and Figure 3 of the
 paper) and bucket-balance statistics, run through the library.
 
 * SIMPLE-LSH is norm-ranging LSH with one sub-dataset (m = 1): one global U.
@@ -47,8 +47,8 @@ def probed_counts(idx: "N.Index", Q: torch.Tensor, B: int, chunk: int = 64) -> n
 
 
 def curve(items: torch.Tensor, Q: torch.Tensor, truth: np.ndarray, m: int, L_hash: int, seed: int,
-          eps: float, budgets: List[int]) -> List[Dict]:
-    idx = N.nrlsh_build_ex(items, m, L_hash, seed, eps=eps)
+          eps: float, budgets: List[int], partition: int = None) -> List[Dict]:
+    idx = N.nrlsh_build_ex(items, m, L_hash, seed, eps=eps, partition=partition)
     pts = []
     for B in budgets:
         ids, _ = N.nrlsh_query_ex(idx, Q, 10, B, flags=N.NRLSH_WHOLE_BUCKETS)
@@ -85,6 +85,42 @@ def compare(items: torch.Tensor, Q: torch.Tensor, L: int, m: int, seed: int, eps
     return {"L": L, "m": m, "L_hash_range": L_range,
             "range_lsh": curve(items, Q, truth, m, L_range, seed, eps, budgets)[0],
             "simple_lsh": curve(items, Q, truth, 1, L, seed, eps, budgets)[0]}
+
+
+def compare_partitions(items: torch.Tensor, Q: torch.Tensor, L: int, m: int, seed: int,
+                       eps: float, truth: np.ndarray) -> Dict:
+    """Percentile partitioning (Algorithm 1) versus uniform norm ranges (Section 5,
+    Figure 3a), both RANGE-LSH with m sub-datasets at total code length L."""
+    n = items.shape[0]
+    budgets = [2 ** i for i in range(4, int(math.ceil(math.log2(n))) + 1)]
+    L_range = L - int(math.ceil(math.log2(m)))
+    return {"L": L, "m": m, "L_hash_range": L_range,
+            "percentile": curve(items, Q, truth, m, L_range, seed, eps, budgets,
+                                N.NRLSH_PARTITION_PERCENTILE)[0],
+            "uniform": curve(items, Q, truth, m, L_range, seed, eps, budgets,
+                             N.NRLSH_PARTITION_UNIFORM)[0]}
+
+
+def multitable_curve(items: torch.Tensor, Q: torch.Tensor, truth: np.ndarray, m: int, L: int,
+                     seed: int, eps: float, tables: List[int], partition: int = None) -> Dict:
+    """Algorithm 2 with T single-probe tables of L/T bits each, for T in `tables`:
+    mean probed items |C(q)|, recall@10 and device time per query."""
+    idx = N.nrlsh_build_ex(items, m, L, seed, eps=eps, partition=partition)
+    pts = []
+    for T in tables:
+        N.nrlsh_query_multitable(idx, Q[:8], T, 10)         # warm-up
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        ids, _, probed = N.nrlsh_query_multitable(idx, Q, T, 10)
+        t1.record()
+        torch.cuda.synchronize()
+        pts.append({"tables": int(T), "bits_per_table": L // T,
+                    "probed": float(probed.float().mean().item()),
+                    "recall": recall(ids.cpu().numpy(), truth),
+                    "us_per_query": t0.elapsed_time(t1) * 1e3 / Q.shape[0]})
+    idx.free()
+    return {"m": m, "L": L, "points": pts}
 
 
 def probed_at_recall(points: List[Dict], target: float = 0.9):

@@ -44,6 +44,8 @@ SIGNATURES = {
     "nrlsh_hash_queries": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_histograms": (_I32, [_P, _P, _I64, _P, _P]),
     "nrlsh_query_candidates": (_I32, [_P, _P, _I64, _I64, _U32, _I64, _P, _P, _P]),
+    "nrlsh_query_multitable": (_I32, [_P, _P, _I64, _I32, _I32, _I64, _P, _P, _P, _P]),
+    "nrlsh_multitable_candidates": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P]),
     "nrlsh_get_codes": (_I32, [_P, _P]),
     "nrlsh_get_partition": (_I32, [_P, _P, _P, _P]),
     "nrlsh_get_segments": (_I32, [_P, _P]),
@@ -307,6 +309,37 @@ def nrlsh_query_candidates(index: Index, queries: torch.Tensor, probe_budget: in
     count = torch.empty(nq, dtype=torch.int64, device=queries.device)
     _check(lib.nrlsh_query_candidates(index.handle, _ptr(queries), nq, probe_budget, flags, cap,
                                       _ptr(cand), _ptr(count), _stream(queries, stream)))
+    return cand, count
+
+
+def nrlsh_query_multitable(index: Index, queries: torch.Tensor, tables: int, k: int,
+                           max_candidates: int = 0, stream=None):
+    """Algorithm 2 with `tables` hash tables of L / tables bits, one probe each:
+    (ids (nq, k) int64, scores (nq, k) float32, probed (nq,) int64 = |C(q)|)."""
+    lib = load()
+    queries = _queries(index, queries)
+    nq = queries.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+    scores = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    probed = torch.empty(nq, dtype=torch.int64, device=queries.device)
+    _check(lib.nrlsh_query_multitable(index.handle, _ptr(queries), nq, tables, k, max_candidates,
+                                      _ptr(ids), _ptr(scores), _ptr(probed),
+                                      _stream(queries, stream)))
+    return ids, scores, probed
+
+
+def nrlsh_multitable_candidates(index: Index, queries: torch.Tensor, tables: int,
+                                cap: Optional[int] = None, stream=None):
+    """The single-probe candidates C(q) as ids (nq, cap) int32 in storage order (rows
+    valid up to min(count, cap)) and count (nq,) int64 = |C(q)|."""
+    lib = load()
+    queries = _queries(index, queries)
+    nq = queries.shape[0]
+    cap = index.n if cap is None else cap
+    cand = torch.full((nq, cap), -1, dtype=torch.int32, device=queries.device)
+    count = torch.empty(nq, dtype=torch.int64, device=queries.device)
+    _check(lib.nrlsh_multitable_candidates(index.handle, _ptr(queries), nq, tables, cap,
+                                           _ptr(cand), _ptr(count), _stream(queries, stream)))
     return cand, count
 
 
