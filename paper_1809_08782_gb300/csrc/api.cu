@@ -184,17 +184,18 @@ struct Scratch {
     }
 };
 
-template <typename T>
-nrlsh_status own(nrlsh_index* ix, T** out, size_t count) {
-    void* p = nullptr;
-    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (index)");
-    ix->owned.push_back(p);
-    ix->device_bytes += (int64_t)bytes;
-    *out = (T*)p;
-    return NRLSH_OK;
-}
+// Carves the index's arrays out of one allocation: a first pass with base null
+// only adds up the (256-byte aligned) sizes, a second assigns the pointers.
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    void take(T** out, size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        if (base) *out = (T*)(base + off);
+        off += std::max<size_t>(count * sizeof(T), 16);
+    }
+};
 
 void destroy(nrlsh_index* ix) {
     if (!ix) return;
@@ -331,34 +332,6 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
 
     // sticky errors from earlier work surface here rather than mid-build
     B_CU(cudaGetLastError());
-    B_CK(own(ix, (char**)&ix->Xp, (size_t)n * ix->dp * esz));
-    B_CK(own(ix, &ix->perm, n));
-    B_CK(own(ix, &ix->sub_of_id, n));
-    B_CK(own(ix, &ix->s_id, n));
-    B_CK(own(ix, &ix->s_pos, n));
-    B_CK(own(ix, &ix->tau64, n));
-    B_CK(own(ix, &ix->tau32, n));
-    B_CK(own(ix, &ix->xnorm, n));
-    B_CK(own(ix, &ix->U2, m));
-    B_CK(own(ix, &ix->seg, (size_t)m + 1));
-    B_CK(own(ix, &ix->A, (size_t)(d + 1) * L));
-    B_CK(own(ix, &ix->A_pad, (size_t)(d + 1) * ix->Lp));
-    B_CK(own(ix, &ix->anorm, ix->Lp));
-    B_CK(own(ix, (char**)&ix->codes, (size_t)n * ix->code_bytes));
-    B_CK(own(ix, &ix->order, ix->ncls));
-    B_CK(own(ix, &ix->shat_sorted, ix->ncls));
-    B_CK(own(ix, &ix->ccos, L + 1));
-    B_CK(own(ix, &ix->ambiguous, 1));
-    B_CK(own(ix, &ix->dev_err, 1));
-    const bool tc = ix->projection == NRLSH_PROJECT_TENSOR;
-    if (tc) {
-        B_CK(own(ix, &ix->At, (size_t)64 * ix->dp));
-        if (dtype == NRLSH_F32) {
-            B_CK(own(ix, &ix->Xb, (size_t)n * ix->dp));
-            B_CK(own(ix, &ix->Xb2, (size_t)n * ix->dp));
-        }
-    }
-
     // histogram tiles: runs of positions inside one sub-dataset.  Percentile
     // ranges have known sizes: offsets and tiles are made here; uniform ranges
     // get them from the device after the assignment (at most this many tiles).
@@ -373,14 +346,57 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
             for (int64_t s = a; s < b; s += tile) tl.push_back({s, (int32_t)std::min(tile, b - s), j});
         }
         ix->ntiles = (int32_t)tl.size();
-        B_CK(own(ix, &ix->tiles, tl.size()));
-        B_CU(cudaMemcpyAsync(ix->tiles, tl.data(), tl.size() * sizeof(PosTile),
-                             cudaMemcpyHostToDevice, st));
-        B_CU(cudaMemcpyAsync(ix->seg, sg.data(), sg.size() * sizeof(int64_t),
-                             cudaMemcpyHostToDevice, st));
     } else {
         ix->ntiles = (int32_t)(ceil_div(n, tile) + m);
-        B_CK(own(ix, &ix->tiles, (size_t)ix->ntiles));
+    }
+
+    // the index's device arrays: one allocation, carved in 256-byte aligned pieces
+    const bool tc = ix->projection == NRLSH_PROJECT_TENSOR;
+    auto carve = [&](Carver& c) {
+        c.take((char**)&ix->Xp, (size_t)n * ix->dp * esz);
+        c.take(&ix->perm, n);
+        c.take(&ix->sub_of_id, n);
+        c.take(&ix->s_id, n);
+        c.take(&ix->s_pos, n);
+        c.take(&ix->tau64, n);
+        c.take(&ix->tau32, n);
+        c.take(&ix->xnorm, n);
+        c.take(&ix->U2, m);
+        c.take(&ix->seg, (size_t)m + 1);
+        c.take(&ix->A, (size_t)(d + 1) * L);
+        c.take(&ix->A_pad, (size_t)(d + 1) * ix->Lp);
+        c.take(&ix->anorm, ix->Lp);
+        c.take((char**)&ix->codes, (size_t)n * ix->code_bytes);
+        c.take(&ix->order, ix->ncls);
+        c.take(&ix->shat_sorted, ix->ncls);
+        c.take(&ix->ccos, L + 1);
+        c.take(&ix->ambiguous, 1);
+        c.take(&ix->dev_err, 1);
+        c.take(&ix->tiles, (size_t)ix->ntiles);
+        if (tc) {
+            c.take(&ix->At, (size_t)64 * ix->dp);
+            if (dtype == NRLSH_F32) {
+                c.take(&ix->Xb, (size_t)n * ix->dp);
+                c.take(&ix->Xb2, (size_t)n * ix->dp);
+            }
+        }
+    };
+    {
+        Carver sizing;
+        carve(sizing);
+        void* base = nullptr;
+        cudaError_t e = cudaMalloc(&base, sizing.off);
+        if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc (index)"));
+        ix->owned.push_back(base);
+        ix->device_bytes = (int64_t)sizing.off;
+        Carver real{(char*)base, 0};
+        carve(real);
+    }
+    if (!uniform) {
+        B_CU(cudaMemcpyAsync(ix->tiles, ix->tiles_host.data(), ix->tiles_host.size() * sizeof(PosTile),
+                             cudaMemcpyHostToDevice, st));
+        B_CU(cudaMemcpyAsync(ix->seg, ix->seg_host.data(), ix->seg_host.size() * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, st));
     }
 
     {
@@ -402,7 +418,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(sc.get(&vals_alt, n));
         B_CK(sc.get(&jkeys, n));
         B_CK(sc.get(&jkeys_alt, n));
-        B_CK(sc.get(&sort_tmp, radix_sort_temp_bytes(n)));
+        B_CK(sc.get(&sort_tmp, std::max(radix_sort_temp_bytes(n), small_rank_temp_bytes(n))));
         char* bo_tmp;
         B_CK(sc.get(&bo_tmp, bucket_order_temp_bytes(m, L)));
         B_CK(sc.get(&amb_list, amb_cap));
@@ -426,8 +442,14 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(side_stream_join(st));
         const int jbits = (bits_for(m) + 7) / 8 * 8;
         bool alt = false;
-        uint32_t *jv, *jv_alt;
-        if (!uniform) {
+        uint32_t *jv = nullptr, *jv_alt = nullptr;
+        const bool small = !uniform && small_rank_supported(n, m);
+        if (small) {
+            // Algorithm 1 for small inputs: tile sort, rank, per-range id sort
+            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
+            B_CU(launch_small_rank(keys, vals, keys_alt, vals_alt, n, m, sort_tmp, ix->perm,
+                                   ix->sub_of_id, ix->U2, st));
+        } else if (!uniform) {
             // Algorithm 1: rank by norm, percentile partition, U_j
             B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
             B_CU(radix_sort_u64(keys, vals, keys_alt, vals_alt, n, 64, sort_tmp, &alt, st));
@@ -446,9 +468,11 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
             B_CU(launch_segments((const uint32_t*)keys, m, tile, ix->seg, ix->tiles, ix->ntiles,
                                  st));
         }
-        B_CU(radix_sort_u32(jkeys, jv, jkeys_alt, jv_alt, n, jbits, sort_tmp, &alt, st));
-        B_CU(cudaMemcpyAsync(ix->perm, alt ? jv_alt : jv, sizeof(uint32_t) * n,
-                             cudaMemcpyDeviceToDevice, st));
+        if (!small) {
+            B_CU(radix_sort_u32(jkeys, jv, jkeys_alt, jv_alt, n, jbits, sort_tmp, &alt, st));
+            B_CU(cudaMemcpyAsync(ix->perm, alt ? jv_alt : jv, sizeof(uint32_t) * n,
+                                 cudaMemcpyDeviceToDevice, st));
+        }
         // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
         B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, ix->sub_of_id, ix->s_id,
                                  ix->U2, ix->Xp, ix->Xb, ix->Xb2, ix->s_pos, ix->tau64, ix->tau32,

@@ -512,6 +512,197 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
 }
 
 // =====================================================================
+// Ranking for small inputs (n <= 64 tiles of 1,024): sort each tile of (s_x, id)
+// keys in shared memory, rank every key against the other tiles by binary search
+// (one block per tile pair), and let the last block of each tile scatter it; then
+// one block per percentile range sorts that range's ids.  Three launches instead
+// of a radix pass per 8-bit digit plus a second sort.
+// =====================================================================
+
+namespace {
+
+constexpr int kRankTile = 1024;
+
+__device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// Block per tile: bitonic sort of up to 1,024 (key, id) pairs (padded with the
+// largest pair), one pair per thread, written back in place.  Exchanges between
+// threads less than 32 apart go through warp shuffles; wider ones through shared
+// memory.
+__global__ void __launch_bounds__(kRankTile)
+    tile_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ids, int64_t n) {
+    __shared__ uint64_t k_s[kRankTile];
+    __shared__ uint32_t i_s[kRankTile];
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kRankTile;
+    const bool in = base + t < n;
+    uint64_t k = in ? keys[base + t] : ~0ull;
+    uint32_t id = in ? ids[base + t] : 0xFFFFFFFFu;
+    for (int size = 2; size <= kRankTile; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            uint64_t k2;
+            uint32_t i2;
+            if (stride >= 32) {
+                k_s[t] = k;
+                i_s[t] = id;
+                __syncthreads();
+                k2 = k_s[t ^ stride];
+                i2 = i_s[t ^ stride];
+                __syncthreads();
+            } else {
+                k2 = __shfl_xor_sync(0xffffffffu, k, stride);
+                i2 = __shfl_xor_sync(0xffffffffu, id, stride);
+            }
+            // the lower thread of a pair keeps the smaller pair in an ascending run
+            const bool lower = (t & stride) == 0;
+            const bool ascending = (t & size) == 0;
+            const bool other_less = key_less(k2, i2, k, id);
+            if (other_less == (lower == ascending)) {
+                k = k2;
+                id = i2;
+            }
+        }
+    }
+    if (in) {
+        keys[base + t] = k;
+        ids[base + t] = id;
+    }
+}
+
+// Block (t, u): every key of sorted tile t counts the keys of sorted tile u that
+// are smaller (binary search in shared memory; for u = t its own index) and adds
+// the count to its rank.  The last of the T blocks of tile t to finish writes the
+// tile's keys and ids at their ranks.  rank (n words) and done (T words) start at 0.
+__global__ void __launch_bounds__(256)
+    tile_rank_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ids, int64_t n,
+                     unsigned* __restrict__ rank, unsigned* __restrict__ done,
+                     uint64_t* __restrict__ out_keys, uint32_t* __restrict__ out_ids) {
+    __shared__ uint64_t k_s[kRankTile];
+    __shared__ uint32_t i_s[kRankTile];
+    __shared__ bool last_s;
+    const int T = (int)gridDim.x;
+    const int t = blockIdx.x, u = blockIdx.y;
+    const int64_t tb = (int64_t)t * kRankTile, ub = (int64_t)u * kRankTile;
+    const int tlen = (int)min((int64_t)kRankTile, n - tb);
+    const int ulen = (int)min((int64_t)kRankTile, n - ub);
+    if (u != t) {
+        for (int i = threadIdx.x; i < ulen; i += blockDim.x) {
+            k_s[i] = keys[ub + i];
+            i_s[i] = ids[ub + i];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tlen; i += blockDim.x) {
+        unsigned c;
+        if (u == t) {
+            c = (unsigned)i;
+        } else {
+            const uint64_t k = keys[tb + i];
+            const uint32_t id = ids[tb + i];
+            int lo = 0, hi = ulen;                  // first index whose key is not smaller
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (key_less(k_s[mid], i_s[mid], k, id)) lo = mid + 1; else hi = mid;
+            }
+            c = (unsigned)lo;
+        }
+        if (c) atomicAdd(&rank[tb + i], c);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_s = atomicAdd(&done[t], 1u) == (unsigned)(T - 1);
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < tlen; i += blockDim.x) {
+        const unsigned r = atomicAdd(&rank[tb + i], 0u);
+        out_keys[r] = keys[tb + i];
+        out_ids[r] = ids[tb + i];
+    }
+}
+
+// Block per percentile range j (ranks [seg_start(j), seg_start(j+1)), at most
+// 4,096): the range's ids in ascending order, so that storage order is (j, id);
+// writes perm, sub_of_id and U_j^2 (the key at the range's last rank).  Up to
+// 1,024 ids each thread counts the smaller ids of the range (ids are distinct);
+// longer ranges use a bitonic sort in shared memory.
+__global__ void __launch_bounds__(1024)
+    range_sort_kernel(const uint64_t* __restrict__ sorted_keys,
+                      const uint32_t* __restrict__ sorted_ids, int64_t n, int m,
+                      uint32_t* __restrict__ perm, uint32_t* __restrict__ sub_of_id,
+                      double* __restrict__ U2) {
+    __shared__ uint32_t v[4096];
+    const int j = blockIdx.x;
+    const int64_t s0 = seg_start(j, n, m), s1 = seg_start(j + 1, n, m);
+    const int len = (int)(s1 - s0);
+    if (threadIdx.x == 0) U2[j] = __longlong_as_double((long long)sorted_keys[s1 - 1]);
+    if (len <= 1024) {
+        for (int i = threadIdx.x; i < len; i += blockDim.x) v[i] = sorted_ids[s0 + i];
+        __syncthreads();
+        if ((int)threadIdx.x < len) {
+            const uint32_t id = v[threadIdx.x];
+            int r = 0;
+            for (int i = 0; i < len; ++i) r += v[i] < id;
+            perm[s0 + r] = id;
+            sub_of_id[id] = (uint32_t)j;
+        }
+        return;
+    }
+    int size = 2;
+    while (size < len) size <<= 1;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) v[i] = i < len ? sorted_ids[s0 + i] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int sz = 2; sz <= size; sz <<= 1) {
+        for (int stride = sz >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < size / 2; t += blockDim.x) {
+                const int a = 2 * t - (t & (stride - 1));
+                const int b = a + stride;
+                const bool up = (a & sz) == 0;
+                const uint32_t x = v[a], y = v[b];
+                if ((y < x) == up) {
+                    v[a] = y;
+                    v[b] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        perm[s0 + i] = v[i];
+        sub_of_id[v[i]] = (uint32_t)j;
+    }
+}
+
+}  // namespace
+
+bool small_rank_supported(int64_t n, int m) {
+    return n >= 1 && n <= 64 * kRankTile && ceil_div(n, m) <= 4096;
+}
+
+size_t small_rank_temp_bytes(int64_t n) {
+    return sizeof(unsigned) * ((size_t)n + 64);
+}
+
+cudaError_t launch_small_rank(uint64_t* keys, uint32_t* ids, uint64_t* keys_out,
+                              uint32_t* ids_out, int64_t n, int m, void* temp, uint32_t* perm,
+                              uint32_t* sub_of_id, double* U2, cudaStream_t st) {
+    const int T = (int)ceil_div(n, kRankTile);
+    unsigned* rank = (unsigned*)temp;
+    unsigned* done = rank + n;
+    cudaError_t e = cudaMemsetAsync(temp, 0, small_rank_temp_bytes(n), st);
+    if (e != cudaSuccess) return e;
+    e = launch("tile_sort", tile_sort_kernel, dim3(T), dim3(kRankTile), 0, st, keys, ids, n);
+    if (e != cudaSuccess) return e;
+    e = launch("tile_rank", tile_rank_kernel, dim3(T, T), dim3(256), 0, st, (const uint64_t*)keys,
+               (const uint32_t*)ids, n, rank, done, keys_out, ids_out);
+    if (e != cudaSuccess) return e;
+    return launch("range_sort", range_sort_kernel, dim3(m), dim3(1024), 0, st,
+                  (const uint64_t*)keys_out, (const uint32_t*)ids_out, n, m, perm, sub_of_id, U2);
+}
+
+// =====================================================================
 // Partition helpers.
 // =====================================================================
 

@@ -223,15 +223,16 @@ __global__ void __launch_bounds__(256)
 // shared memory; a warp keeps its row in registers (lane owns columns
 // lane + 32 i), forms 32 bit-partials per pass, and reduces them with a
 // transpose-reduction (31 shuffles) after which lane l holds the sum of bit
-// 32 pass + l.  Any summation order satisfies the same FP32 bound.
-template <typename T, int NREG>
+// 32 pass + l.  Any summation order satisfies the same FP32 bound.  The warp then
+// settles its row's undecided bits in FP64 itself, so no list or second launch
+// is needed (amb_count still counts them).
+template <typename T, int NREG, int ROWS>
 __global__ void __launch_bounds__(256)
     project_warp_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int L, int Lp, int dpa,
                         const float* __restrict__ A_pad, const float* __restrict__ anorm,
                         const double* __restrict__ tau64, const float* __restrict__ tau32,
                         const float* __restrict__ xnorm, void* __restrict__ codes, int code_bytes,
-                        unsigned long long* __restrict__ amb_list, unsigned* amb_count,
-                        unsigned amb_cap, float kappa) {
+                        unsigned* amb_count, float kappa) {
     extern __shared__ float At_s[];          // Lr x dpa, Lr = Lp rounded up to 32
     __shared__ float ad_s[64], an_s[64];
     const int Lr = (Lp + 31) / 32 * 32;
@@ -248,78 +249,116 @@ __global__ void __launch_bounds__(256)
     const int lane = threadIdx.x & 31;
     const bool has_tail = tau64 != nullptr;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n;
-         row += nwarps) {
-        float x[NREG];
+    // a warp takes ROWS consecutive rows at a time: every A^T element read from
+    // shared memory serves all of them
+    for (int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * ROWS; row0 < n;
+         row0 += nwarps * ROWS) {
+        float x[ROWS][NREG];
 #pragma unroll
-        for (int i = 0; i < NREG; ++i) {
-            const int k = lane + 32 * i;
-            x[i] = k < d ? to_f32(X[row * ldx + k]) : 0.0f;
-        }
-        const float xn = xnorm[row];
-        const float t32 = has_tail ? tau32[row] : 0.0f;
-        unsigned long long word = 0, undecided = 0;
+        for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+            for (int i = 0; i < NREG; ++i) {
+                const int k = lane + 32 * i;
+                x[r][i] = (row0 + r < n && k < d) ? to_f32(X[(row0 + r) * ldx + k]) : 0.0f;
+            }
+        unsigned long long word[ROWS], undecided[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) word[r] = undecided[r] = 0;
         for (int pass = 0; pass < Lr / 32; ++pass) {
-            float acc[32];
+            float acc[ROWS][32];
 #pragma unroll
             for (int b = 0; b < 32; ++b) {
                 const float* ar = At_s + (pass * 32 + b) * dpa + lane;
-                float a = 0.0f;
+                float a[ROWS];
 #pragma unroll
-                for (int i = 0; i < NREG; ++i) a = fmaf(x[i], ar[32 * i], a);
-                acc[b] = a;
+                for (int r = 0; r < ROWS; ++r) a[r] = 0.0f;
+#pragma unroll
+                for (int i = 0; i < NREG; ++i) {
+                    const float av = ar[32 * i];
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) a[r] = fmaf(x[r][i], av, a[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) acc[r][b] = a[r];
             }
 #pragma unroll
             for (int w = 16; w >= 1; w >>= 1) {
                 const bool up = (lane & w) != 0;
 #pragma unroll
-                for (int j = 0; j < w; ++j) {
-                    const float send = up ? acc[j] : acc[j + w];
-                    const float keep = up ? acc[j + w] : acc[j];
-                    acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-                }
+                for (int j = 0; j < w; ++j)
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        const float send = up ? acc[r][j] : acc[r][j + w];
+                        const float keep = up ? acc[r][j + w] : acc[r][j];
+                        acc[r][j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+                    }
             }
             const int bit = pass * 32 + lane;
-            bool set = false, open = false;
-            if (bit < L) {
-                const float ad = ad_s[bit];
-                const float v = has_tail ? fmaf(ad, t32, acc[0]) : acc[0];
-                const float bound = kappa * an_s[bit] * xn + 0x1p-20f * fabsf(ad) * t32;
-                if (fabsf(v) * (1.0f - 0x1p-21f) > bound)
-                    set = v > 0.0f;
-                else
-                    open = true;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                bool set = false, open = false;
+                if (bit < L && row0 + r < n) {
+                    const float xn = xnorm[row0 + r];
+                    const float t32 = has_tail ? tau32[row0 + r] : 0.0f;
+                    const float ad = ad_s[bit];
+                    const float v = has_tail ? fmaf(ad, t32, acc[r][0]) : acc[r][0];
+                    const float bound = kappa * an_s[bit] * xn + 0x1p-20f * fabsf(ad) * t32;
+                    if (fabsf(v) * (1.0f - 0x1p-21f) > bound)
+                        set = v > 0.0f;
+                    else
+                        open = true;
+                }
+                word[r] |= (unsigned long long)__ballot_sync(0xffffffffu, set) << (32 * pass);
+                undecided[r] |= (unsigned long long)__ballot_sync(0xffffffffu, open) << (32 * pass);
             }
-            word |= (unsigned long long)__ballot_sync(0xffffffffu, set) << (32 * pass);
-            undecided |= (unsigned long long)__ballot_sync(0xffffffffu, open) << (32 * pass);
         }
-        // undecided bits: one list reservation per row; if the list is full the
-        // lane owning the bit evaluates the canonical FP64 form itself
-        const int cnt = __popcll(undecided);
-        unsigned base = 0;
-        if (lane == 0 && cnt) base = atomicAdd(amb_count, (unsigned)cnt);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        bool fb0 = false, fb1 = false;
-        for (int pass = 0; pass < 2 && cnt; ++pass) {
-            const int b = pass * 32 + lane;
-            if ((undecided >> b) & 1ull) {
-                const unsigned slot = base + __popcll(undecided & ((1ull << b) - 1ull));
-                if (slot < amb_cap) {
-                    amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)b;
-                } else {
-                    const bool v = project_bit_fp64(X + row * ldx, A_pad, Lp, d, b, has_tail,
-                                                    has_tail ? tau64[row] : 0.0);
-                    if (pass == 0) fb0 = v; else fb1 = v;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int64_t row = row0 + r;
+            if (row >= n) break;
+            // undecided bits, decided by this warp with the row still in registers:
+            // an FP64 lane-strided sum and a tree (within (2d + 8) 2^-53 (sum|a x| +
+            // |tail|) of the canonical in-order sum, as in resolve_kernel), and the
+            // canonical sequential form by lane 0 only inside that bound
+            if (undecided[r]) {
+                if (lane == 0) atomicAdd(amb_count, (unsigned)__popcll(undecided[r]));
+                const double tau = has_tail ? tau64[row] : 0.0;
+                for (unsigned long long u = undecided[r]; u; u &= u - 1) {
+                    const int b = __ffsll((long long)u) - 1;
+                    const float* ar = At_s + b * dpa + lane;
+                    double sd = 0.0, sa = 0.0;
+#pragma unroll
+                    for (int i = 0; i < NREG; ++i) {
+                        const double pr = (double)x[r][i] * (double)ar[32 * i];
+                        sd += pr;
+                        sa += fabs(pr);
+                    }
+                    for (int o = 16; o; o >>= 1) {
+                        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                    }
+                    const double tail = has_tail ? __dmul_rn((double)ad_s[b], tau) : 0.0;
+                    const double v = __dadd_rn(sd, tail);
+                    const double bound =
+                        (2.0 * d + 8.0) * 0x1p-53 * (sa + fabs(tail)) + 0x1p-50 * fabs(v);
+                    bool set;
+                    if (fabs(v) > bound) {
+                        set = v > 0.0;
+                    } else {
+                        int rr = 0;
+                        if (lane == 0)
+                            rr = project_bit_fp64(X + row * ldx, A_pad, Lp, d, b, has_tail, tau);
+                        set = __shfl_sync(0xffffffffu, rr, 0) != 0;
+                    }
+                    if (set) word[r] |= 1ull << b;
                 }
             }
-        }
-        word |= (unsigned long long)__ballot_sync(0xffffffffu, fb0) |
-                ((unsigned long long)__ballot_sync(0xffffffffu, fb1) << 32);
-        if (lane == 0) {
-            if (code_bytes == 4)
-                static_cast<uint32_t*>(codes)[row] = (uint32_t)word;
-            else
-                static_cast<uint64_t*>(codes)[row] = word;
+            if (lane == 0) {
+                if (code_bytes == 4)
+                    static_cast<uint32_t*>(codes)[row] = (uint32_t)word[r];
+                else
+                    static_cast<uint64_t*>(codes)[row] = word[r];
+            }
         }
     }
 }
@@ -335,22 +374,55 @@ cudaError_t project_rows(const void* X, int64_t n, int d, int ldx, int L, int Lp
                   tau32, xnorm, (C*)codes, amb_list, amb_count, amb_cap, kappa);
 }
 
-template <typename T, typename C, int NREG>
+// Per kernel (and thread): the dynamic shared memory the attribute allows so far
+// (only ever raised, since launches with other code widths share the kernel)
+// and the blocks per SM for the last size asked.
+template <typename T, int NREG, int ROWS>
+struct WarpKernelState {
+    static thread_local int dev;
+    static thread_local size_t attr, occ_smem;
+    static thread_local int per_sm;
+};
+template <typename T, int NREG, int ROWS> thread_local int WarpKernelState<T, NREG, ROWS>::dev = -1;
+template <typename T, int NREG, int ROWS> thread_local size_t WarpKernelState<T, NREG, ROWS>::attr = 0;
+template <typename T, int NREG, int ROWS> thread_local size_t WarpKernelState<T, NREG, ROWS>::occ_smem = 0;
+template <typename T, int NREG, int ROWS> thread_local int WarpKernelState<T, NREG, ROWS>::per_sm = 1;
+
+constexpr size_t kWarpProjMaxSmem = 227 * 1024;
+
+template <typename T, typename C, int NREG, int ROWS>
 cudaError_t project_warp_launch(const void* X, int64_t n, int d, int ldx, int L, int Lp,
                                 const float* A_pad, const float* anorm, const double* tau64,
                                 const float* tau32, const float* xnorm, void* codes,
-                                unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
-                                float kappa, cudaStream_t st, const char* name) {
+                                unsigned* amb_count, float kappa, cudaStream_t st,
+                                const char* name) {
+    using S = WarpKernelState<T, NREG, ROWS>;
     const int Lr = (Lp + 31) / 32 * 32, dpa = NREG * 32;
     const size_t smem = sizeof(float) * (size_t)Lr * dpa;
-    auto kern = project_warp_kernel<T, NREG>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = project_warp_kernel<T, NREG, ROWS>;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const int per_sm = smem <= 100 * 1024 ? 2 : 1;
-    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 8), (int64_t)per_sm * 152);
+    if (dev != S::dev) {
+        S::dev = dev;
+        S::attr = 0;
+        S::occ_smem = 0;
+    }
+    if (smem > S::attr) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        S::attr = smem;
+    }
+    if (smem != S::occ_smem) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&S::per_sm, kern, 256, smem);
+        if (e != cudaSuccess) return e;
+        S::per_sm = std::max(1, S::per_sm);
+        S::occ_smem = smem;
+    }
+    const unsigned grid =
+        (unsigned)std::min<int64_t>(ceil_div(n, 8 * ROWS), (int64_t)S::per_sm * 152);
     return launch(name, kern, dim3(grid), dim3(256), smem, st, (const T*)X, n, d, ldx, L, Lp, dpa,
-                  A_pad, anorm, tau64, tau32, xnorm, codes, (int)sizeof(C), amb_list, amb_count,
-                  amb_cap, kappa);
+                  A_pad, anorm, tau64, tau32, xnorm, codes, (int)sizeof(C), amb_count, kappa);
 }
 
 template <typename T, typename C>
@@ -362,23 +434,19 @@ cudaError_t project_dispatch(const void* X, int64_t n, int d, int ldx, int L, in
     const float kappa = (float)(d + 2) * 0x1p-22f;
     cudaError_t e;
     const int nreg = (d + 31) / 32;
-    if (nreg <= 32) {
-#define NRLSH_PW(R_)                                                                          \
-    e = project_warp_launch<T, C, R_>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,  \
-                                      codes, amb_list, amb_count, amb_cap, kappa, st, name);   \
+    const int nreg_t = nreg <= 4 ? 4 : nreg <= 10 ? 10 : 32;
+    if (nreg <= 32 && sizeof(float) * (size_t)((Lp + 31) / 32 * 32) * nreg_t * 32 <= kWarpProjMaxSmem) {
+#define NRLSH_PW(R_, ROWS_)                                                                   \
+    e = project_warp_launch<T, C, R_, ROWS_>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32,     \
+                                             xnorm, codes, amb_count, kappa, st, name);           \
     break;
-        switch (nreg <= 4 ? 4 : nreg <= 10 ? 10 : 32) {
-            case 4: NRLSH_PW(4)
-            case 10: NRLSH_PW(10)
-            default: NRLSH_PW(32)
+        switch (nreg_t) {
+            case 4: NRLSH_PW(4, 2)
+            case 10: NRLSH_PW(10, 2)
+            default: NRLSH_PW(32, 1)
         }
 #undef NRLSH_PW
-        if (e != cudaSuccess) return e;
-        const unsigned rgrid = (unsigned)std::min<int64_t>(
-            ceil_div(std::max<int64_t>(n * L / 256, 32), 8), 8 * 152);
-        return launch("resolve_fp64", resolve_kernel<T, C>, dim3(rgrid), dim3(256), 0, st,
-                      (const T*)X, d, ldx, Lp, A_pad, tau64, (const unsigned long long*)amb_list,
-                      (const unsigned*)amb_count, amb_cap, (C*)codes);
+        return e;
     }
     switch (Lp / 8) {
         case 1:

@@ -164,3 +164,29 @@ def test_empty_query_batch_and_launch_count():
     assert ids.shape == (0, 5) and N.nrlsh_launch_count() == before
     N.nrlsh_query_ex(lib, torch.zeros((2, 8), device="cuda"), 5, 10)
     assert N.nrlsh_launch_count() > before
+
+
+@pytest.mark.parametrize("n,m", [
+    (65_536, 16),     # 64 tiles, ranges of 4,096: the tile-rank path at its limits
+    (65_537, 17),     # 65 tiles: the radix path
+    (40_000, 9),      # ranges of 4,445: the radix path
+    (1_000, 900),     # ranges of one or two items
+])
+def test_ranking_paths_and_their_limits(n, m):
+    rng = np.random.default_rng(n + m)
+    items = rand_items(n, 16, n + 3 * m)
+    items[rng.choice(n, n // 5, replace=False)] = items[0]     # many equal norms
+    lib, ref = build_pair(items, "f32", m, 16, seed=5, eps=0.2, projection=SIMT)
+    check_index(lib, ref, SIMT)
+    check_queries(lib, ref, rand_q(8, 16, 3), 10, 700)
+
+
+@pytest.mark.parametrize("d,L", [(1000, 64), (1000, 32), (1030, 16), (700, 64)])
+def test_wide_rows(d, L):
+    """Rows up to 1,024 columns go through the warp-per-row projection while A^T
+    fits in shared memory (L = 32 at d = 1,000), else through the register-tiled
+    one (L = 64 at d = 1,000; d > 1,024)."""
+    items = rand_items(2500, d, d + L)
+    lib, ref = build_pair(items, "f32", 8, L, seed=3, eps=0.2, projection=SIMT)
+    check_index(lib, ref, SIMT)
+    check_queries(lib, ref, rand_q(6, d, 4), 10, 300)
