@@ -9,6 +9,9 @@
 //                    of the contenders, (score desc, id asc) selection
 #include "nrlsh_internal.cuh"
 
+#include <unordered_map>
+#include <utility>
+
 #include <cfloat>
 
 namespace nrlsh {
@@ -175,75 +178,139 @@ __global__ void __launch_bounds__(256)
 // ------------------------------------------------------------------ select
 
 // Block phase (256 threads): ordered compaction of the probed items of one
-// query.  Only sub-datasets the walk reached (lam_j <= L, or the boundary's)
-// are swept.  Inside one, warp w owns a contiguous eighth: a counting sweep, a
-// scan over the 8 warps, and a writing sweep with ballot prefixes.  Items of
-// whole buckets go to out[0, full) in position order; boundary-bucket items go
-// to out[full, full + r), the first r of them in position (= id) order.
+// query.  The positions from the first to the last sub-dataset the walk reached
+// are swept once as one range (an unreached sub-dataset inside it has
+// lam_j = L + 1 and contributes nothing); warp w owns a contiguous eighth and
+// follows the sub-dataset of each lane's position as it advances.  A counting
+// sweep, a scan over the 8 warps, and a writing sweep with ballot prefixes, each
+// with kSelUnroll code loads in flight per lane.  Items of whole buckets go to
+// out[0, full) in position order; boundary-bucket items go to
+// out[full, full + r), the first r of them in position (= id) order.
+constexpr int kSelUnroll = 4;
+
+__device__ __forceinline__ int seg_find(const int64_t* __restrict__ seg, int jlo, int jhi, int64_t p) {
+    // largest j in [jlo, jhi] with seg[j] <= p (then seg[j + 1] > p)
+    int a = jlo, b = jhi;
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (seg[mid] <= p) a = mid; else b = mid - 1;
+    }
+    return a;
+}
+
+// msk: shared scratch of 2 x 8 x kMaskChunks words (shared with dev_topk's rows).
+constexpr int kMaskChunks = 128;                // per warp: 32-position chunks whose masks are kept
+
 template <typename C>
 __device__ void dev_select(const C* __restrict__ codes, C cq, const int64_t* __restrict__ seg, int m, int L,
-                           const uint8_t* lam_s, const Boundary& b, uint32_t* __restrict__ out) {
+                           const uint8_t* lam_s, const Boundary& b, uint32_t* __restrict__ out,
+                           uint32_t* msk) {
     __shared__ uint32_t wf[8], wb[8];
+    uint32_t* mskf = msk;
+    uint32_t* mskb = msk + 8 * kMaskChunks;
+    __shared__ int jlo_s, jhi_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t of_blk = 0, ob_blk = 0;  // block-uniform running totals
-    for (int j = 0; j < m; ++j) {
-        const int lamj = lam_s[j];
-        const bool isb = j == b.j;
-        if (lamj > L && !isb) continue;                       // uniform
-        if (of_blk >= (uint32_t)b.full && ob_blk >= (uint32_t)b.r) break;
-        const int64_t s0 = seg[j], len = seg[j + 1] - s0;
-        const int64_t w0 = s0 + len * warp / 8, w1 = s0 + len * (warp + 1) / 8;
-        uint32_t cf = 0, cb = 0;
-        for (int64_t base = w0; base < w1; base += 32) {
-            const int64_t p = base + lane;
-            bool f = false, bb = false;
-            if (p < w1) {
-                const int l = L - popc_word(cq ^ codes[p]);
-                f = l >= lamj;
-                bb = isb && l == b.l;
+    if (threadIdx.x == 0) {
+        jlo_s = b.j;
+        jhi_s = b.j;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        if (lam_s[j] <= L) {
+            atomicMin(&jlo_s, j);
+            atomicMax(&jhi_s, j);
+        }
+    }
+    __syncthreads();
+    const int jlo = jlo_s, jhi = jhi_s;
+    const int64_t p_lo = seg[jlo], len = seg[jhi + 1] - p_lo;
+    const int64_t w0 = p_lo + len * warp / 8, w1 = p_lo + len * (warp + 1) / 8;
+    const int nchunk = (int)ceil_div(w1 - w0, 32);
+    const bool keep = nchunk <= kMaskChunks;    // warp-uniform
+    uint32_t* mf_w = mskf + warp * kMaskChunks;
+    uint32_t* mb_w = mskb + warp * kMaskChunks;
+    const int j_start = w0 + lane < w1 ? seg_find(seg, jlo, jhi, w0 + lane) : jlo;
+    // the predicates at position p (lane's sub-dataset jl advances with p)
+    auto test = [&](int64_t p, C cv, int& jl, int64_t& nxt, bool& f, bool& bb) {
+        while (p >= nxt) nxt = seg[++jl + 1];
+        const int l = L - popc_word(cq ^ cv);
+        f = l >= lam_s[jl];
+        bb = jl == b.j && l == b.l;
+    };
+    uint32_t cf = 0, cb = 0;
+    {
+        int jl = j_start;
+        int64_t nxt = seg[jl + 1];
+        for (int c0 = 0; c0 < nchunk; c0 += kSelUnroll) {
+            C cv[kSelUnroll];
+#pragma unroll
+            for (int u = 0; u < kSelUnroll; ++u) {
+                const int64_t p = w0 + 32 * (c0 + u) + lane;
+                cv[u] = p < w1 ? codes[p] : (C)0;
             }
-            cf += __popc(__ballot_sync(0xffffffffu, f));
-            cb += __popc(__ballot_sync(0xffffffffu, bb));
-        }
-        if (lane == 0) {
-            wf[warp] = cf;
-            wb[warp] = cb;
-        }
-        __syncthreads();
-        uint32_t of = of_blk, ob = ob_blk, tf = 0, tb = 0;
-        for (int w = 0; w < 8; ++w) {
-            if (w < warp) {
-                of += wf[w];
-                ob += wb[w];
-            }
-            tf += wf[w];
-            tb += wb[w];
-        }
-        __syncthreads();
-        if (cf || (cb && ob < (uint32_t)b.r)) {
-            for (int64_t base = w0; base < w1; base += 32) {
-                const int64_t p = base + lane;
+#pragma unroll
+            for (int u = 0; u < kSelUnroll; ++u) {
+                const int64_t p = w0 + 32 * (c0 + u) + lane;
                 bool f = false, bb = false;
-                if (p < w1) {
-                    const int l = L - popc_word(cq ^ codes[p]);
-                    f = l >= lamj;
-                    bb = isb && l == b.l;
-                }
+                if (p < w1) test(p, cv[u], jl, nxt, f, bb);
                 const unsigned mf = __ballot_sync(0xffffffffu, f);
                 const unsigned mb = __ballot_sync(0xffffffffu, bb);
-                if (f) out[of + __popc(mf & lt)] = (uint32_t)p;
-                if (bb) {
-                    const uint32_t rank = ob + __popc(mb & lt);
-                    if (rank < (uint32_t)b.r) out[b.full + rank] = (uint32_t)p;
+                cf += __popc(mf);
+                cb += __popc(mb);
+                if (keep && lane == 0 && c0 + u < nchunk) {
+                    mf_w[c0 + u] = mf;
+                    mb_w[c0 + u] = mb;
                 }
-                of += __popc(mf);
-                ob += __popc(mb);
             }
         }
-        of_blk += tf;
-        ob_blk += tb;
     }
+    if (lane == 0) {
+        wf[warp] = cf;
+        wb[warp] = cb;
+    }
+    __syncthreads();
+    uint32_t of = 0, ob = 0;
+    for (int w = 0; w < warp; ++w) {
+        of += wf[w];
+        ob += wb[w];
+    }
+    auto emit = [&](int64_t p, unsigned mf, unsigned mb) {
+        if ((mf >> lane) & 1u) out[of + __popc(mf & lt)] = (uint32_t)p;
+        if ((mb >> lane) & 1u) {
+            const uint32_t rank = ob + __popc(mb & lt);
+            if (rank < (uint32_t)b.r) out[b.full + rank] = (uint32_t)p;
+        }
+        of += __popc(mf);
+        ob += __popc(mb);
+    };
+    if (cf || (cb && ob < (uint32_t)b.r)) {
+        if (keep) {
+            for (int c = 0; c < nchunk; ++c) {
+                const unsigned mf = mf_w[c], mb = mb_w[c];
+                if (mf | mb) emit(w0 + 32 * c + lane, mf, mb);
+            }
+        } else {
+            int jl = j_start;
+            int64_t nxt = seg[jl + 1];
+            for (int c0 = 0; c0 < nchunk; c0 += kSelUnroll) {
+                C cv[kSelUnroll];
+#pragma unroll
+                for (int u = 0; u < kSelUnroll; ++u) {
+                    const int64_t p = w0 + 32 * (c0 + u) + lane;
+                    cv[u] = p < w1 ? codes[p] : (C)0;
+                }
+#pragma unroll
+                for (int u = 0; u < kSelUnroll; ++u) {
+                    const int64_t p = w0 + 32 * (c0 + u) + lane;
+                    bool f = false, bb = false;
+                    if (p < w1) test(p, cv[u], jl, nxt, f, bb);
+                    emit(p, __ballot_sync(0xffffffffu, f), __ballot_sync(0xffffffffu, bb));
+                }
+            }
+        }
+    }
+    __syncthreads();
 }
 
 template <typename C>
@@ -256,7 +323,8 @@ __global__ void __launch_bounds__(256)
     const int64_t q = blockIdx.x;
     for (int j = threadIdx.x; j < m; j += 256) lam_s[j] = lam[q * m + j];
     __syncthreads();
-    dev_select(codes, qcodes[q], seg, m, L, lam_s, bnd[q], cand + q * cap);
+    __shared__ __align__(16) uint32_t msk[16 * kMaskChunks];
+    dev_select(codes, qcodes[q], seg, m, L, lam_s, bnd[q], cand + q * cap, msk);
 }
 
 // ------------------------------------------------------------------ rerank
@@ -335,14 +403,29 @@ __device__ void dev_rerank(const T* __restrict__ Xp, int dp, const float* qs,
 #pragma unroll
         for (int u = 0; u < kRerankUnroll; ++u) acc[u] = 0.0f;
         RowDot<T>::template dot<kRerankUnroll>(rows, qs, dp, lane, acc);
-#pragma unroll
-        for (int u = 0; u < kRerankUnroll; ++u) {
-            const float sc = warp_sum(acc[u]);
-            if (lane == u && i + u < i1) {
-                const float e = __fmul_ru(__fmul_ru(kappa, qn), xnorm[ps[u]]);
-                loq[i + u] = __fsub_rd(sc, e);
-                hiq[i + u] = __fadd_ru(sc, e);
-            }
+        // transpose-reduction of the 4 row sums (6 shuffles): afterwards lane
+        // 8 r holds the sum of row r (any order meets the same FP32 bound)
+        static_assert(kRerankUnroll == 4, "the reduction below folds 4 rows");
+        {
+            const bool up = (lane & 16) != 0;
+            const float s0 = up ? acc[0] : acc[2], s1 = up ? acc[1] : acc[3];
+            const float k0 = up ? acc[2] : acc[0], k1 = up ? acc[3] : acc[1];
+            acc[0] = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+            acc[1] = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+        }
+        {
+            const bool up = (lane & 8) != 0;
+            const float sd = up ? acc[0] : acc[1], kp = up ? acc[1] : acc[0];
+            acc[0] = kp + __shfl_xor_sync(0xffffffffu, sd, 8);
+        }
+        for (int o = 4; o; o >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+        const int r = lane >> 3;
+        if ((lane & 7) == 0 && i + r < i1) {
+            const float sc = acc[0];
+            const uint32_t pr = r == 0 ? ps[0] : r == 1 ? ps[1] : r == 2 ? ps[2] : ps[3];
+            const float e = __fmul_ru(__fmul_ru(kappa, qn), xnorm[pr]);
+            loq[i + r] = __fsub_rd(sc, e);
+            hiq[i + r] = __fadd_ru(sc, e);
         }
     }
 }
@@ -437,7 +520,8 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
                          const T* __restrict__ Xp, int dp, int d, const float* qs, float qn,
                          const float* __restrict__ xnorm, const uint32_t* __restrict__ perm,
                          uint32_t* __restrict__ contq, double* __restrict__ contsq,
-                         int64_t* __restrict__ ids_out, float* __restrict__ sc_out) {
+                         int64_t* __restrict__ ids_out, float* __restrict__ sc_out,
+                         float* rows_s) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t prefix_s, mask_s;
     __shared__ int rem_s, dg_s;
@@ -445,7 +529,6 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __shared__ double best_s[8];
     __shared__ int64_t bid_s[8];
     __shared__ int bc_s[8];
-    __shared__ __align__(16) float rows_s[kRescoreSmem / sizeof(float)];
     __shared__ double rank_lo[kDot2Max], rank_hi[kDot2Max];
     __shared__ uint16_t flagged[kDot2Max];
     __shared__ uint32_t nflag_s;
@@ -664,9 +747,10 @@ __global__ void __launch_bounds__(256)
     load_query(Q, q, d, dp, qs);
     __syncthreads();
     const Boundary b = bnd[q];
+    __shared__ __align__(16) float rows_s[kRescoreSmem / sizeof(float)];
     dev_topk(lo + q * cap, hi + q * cap, cand + q * cap, (int64_t)b.full + b.r, ks ? ks[q] : k,
              out_ld, Xp, dp, d, qs, qnorm[q], xnorm, perm, cont + q * cap, cont_s + q * cap,
-             out_ids + q * out_ld, out_scores + q * out_ld);
+             out_ids + q * out_ld, out_scores + q * out_ld, rows_s);
 }
 
 // ----------------------------------------------------- fused probe + rerank
@@ -694,14 +778,15 @@ __global__ void __launch_bounds__(256)
     const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n,
                                      budgets ? budgets[q] : budget, flags, cntj, lam_s);
     uint32_t* candq = cand + q * cap;
-    dev_select(codes, qcodes[q], seg, m, L, lam_s, b, candq);
+    __shared__ __align__(16) float phase_s[kRescoreSmem / sizeof(float)];  // select masks, then top-k rows
+    dev_select(codes, qcodes[q], seg, m, L, lam_s, b, candq, (uint32_t*)phase_s);
     __syncthreads();
     const int64_t count = (int64_t)b.full + b.r;
     dev_rerank(Xp, dp, qs, candq, 0, count, xnorm, qnorm[q], kappa, lo + q * cap, hi + q * cap);
     __syncthreads();
     dev_topk(lo + q * cap, hi + q * cap, candq, count, ks ? ks[q] : k, out_ld, Xp, dp, d, qs,
              qnorm[q], xnorm, perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld,
-             out_scores + q * out_ld);
+             out_scores + q * out_ld, phase_s);
 }
 
 // Persistent form: CTAs take queries from a device work counter until it passes
@@ -725,6 +810,7 @@ __global__ void __launch_bounds__(256)
     uint32_t* cntj = (uint32_t*)(qs + dp);
     uint8_t* lam_s = (uint8_t*)(cntj + m);
     __shared__ int64_t q_s;
+    __shared__ __align__(16) float phase_s[kRescoreSmem / sizeof(float)];  // select masks, then top-k rows
     uint32_t* slab = slabs + (size_t)blockIdx.x * 6 * cap;
     uint32_t* cand = slab;
     float* lo = (float*)(slab + cap);
@@ -740,14 +826,14 @@ __global__ void __launch_bounds__(256)
         load_query(Q, q, d, dp, qs);
         const int64_t Bq = min(max(budgets[q], (int64_t)1), cap);
         const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n, Bq, 0u, cntj, lam_s);
-        dev_select(codes, qcodes[q], seg, m, L, lam_s, b, cand);
+        dev_select(codes, qcodes[q], seg, m, L, lam_s, b, cand, (uint32_t*)phase_s);
         __syncthreads();
         const int64_t count = (int64_t)b.full + b.r;
         dev_rerank(Xp, dp, qs, cand, 0, count, xnorm, qnorm[q], kappa, lo, hi);
         __syncthreads();
         dev_topk(lo, hi, cand, count, min(max(ks[q], 1), k_max), k_max, Xp, dp, d, qs, qnorm[q],
                  xnorm, perm, cont, cont_s,
-                 out_ids + q * k_max, out_scores + q * k_max);
+                 out_ids + q * k_max, out_scores + q * k_max, phase_s);
     }
 }
 
@@ -924,8 +1010,10 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     dev_rerank(Xp, dp, qs, candq, 0, count, xnorm, qnorm[q], kappa, lo + q * cap, hi + q * cap);
     __syncthreads();
+    __shared__ __align__(16) float rows_s[kRescoreSmem / sizeof(float)];
     dev_topk(lo + q * cap, hi + q * cap, candq, count, k, out_ld, Xp, dp, d, qs, qnorm[q], xnorm,
-             perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld, out_scores + q * out_ld);
+             perm, cont + q * cap, cont_s + q * cap, out_ids + q * out_ld, out_scores + q * out_ld,
+             rows_s);
 }
 
 __global__ void cand_to_ids_kernel(const uint32_t* __restrict__ cand, int64_t cap,
@@ -1034,28 +1122,41 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
                   out_ids, out_scores, out_ld);
 }
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize raised as needed, per kernel,
+// device and thread (the attribute only grows).
+cudaError_t ensure_dyn_smem(const void* kern, size_t bytes) {
+    static thread_local std::unordered_map<const void*, std::pair<int, size_t>> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    auto& s = set[kern];
+    if (s.first == dev && s.second >= bytes) return cudaSuccess;
+    if (s.first != dev) s = {dev, 0};
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) s.second = bytes;
+    return e;
+}
+
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
-                                const int64_t* seg, int64_t nq, int64_t budget, const int64_t* budgets, uint32_t flags,
-                                const void* codes, const void* qcodes, int code_bytes,
-                                const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
-                                const float* xnorm, const float* qnorm, const uint32_t* perm, int k,
-                                const int32_t* ks, uint32_t* cand, float* lo, float* hi,
-                                uint32_t* cont, double* cont_s, int64_t cap, int64_t* out_ids,
-                                float* out_scores, int out_ld, cudaStream_t st) {
+                                const int64_t* seg, int64_t nq, int64_t budget,
+                                const int64_t* budgets, uint32_t flags, const void* codes,
+                                const void* qcodes, int code_bytes, const void* Xp, nrlsh_dtype dt,
+                                int dp, int d, const float* Q, const float* xnorm,
+                                const float* qnorm, const uint32_t* perm, int k, const int32_t* ks,
+                                uint32_t* cand, float* lo, float* hi, uint32_t* cont,
+                                double* cont_s, int64_t cap, int64_t* out_ids, float* out_scores,
+                                int out_ld, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)dp + (sizeof(uint32_t) + 1) * (size_t)m;
     const float kappa = (float)(d + 2) * 0x1p-22f;
     const dim3 grid((unsigned)nq);
 #define NRLSH_PR(T_, C_, NAME)                                                                  \
     {                                                                                           \
         auto kern = probe_rerank_kernel<T_, C_>;                                                \
-        if (smem > 48 * 1024) {                                                                 \
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                 (int)smem);                                    \
-            if (e != cudaSuccess) return e;                                                     \
-        }                                                                                       \
+        cudaError_t e = ensure_dyn_smem((const void*)kern, smem);                               \
+        if (e != cudaSuccess) return e;                                                         \
         return launch(NAME, kern, grid, dim3(256), smem, st, H, order, m, L, n, seg, budget, budgets, \
                       flags, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q, xnorm,\
-                      qnorm, kappa, perm, k, ks, cand, lo, hi, cont, cont_s, cap, out_ids,      \
+                      qnorm, kappa, perm, k, ks, cand, lo, hi, cont, cont_s, cap, out_ids,       \
                       out_scores, out_ld);                                                      \
     }
     if (dt == NRLSH_BF16) {
@@ -1068,10 +1169,10 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
 }
 
 cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
-                                           int64_t n, const int64_t* seg, const int64_t* budgets, const void* codes,
-                                           const void* qcodes, int code_bytes, const void* Xp,
-                                           nrlsh_dtype dt, int dp, int d, const float* Q,
-                                           const float* xnorm, const float* qnorm,
+                                           int64_t n, const int64_t* seg, const int64_t* budgets,
+                                           const void* codes, const void* qcodes, int code_bytes,
+                                           const void* Xp, nrlsh_dtype dt, int dp, int d,
+                                           const float* Q, const float* xnorm, const float* qnorm,
                                            const uint32_t* perm, const int32_t* ks, int k_max,
                                            uint32_t* slabs, int64_t cap, int ctas, unsigned* work,
                                            int64_t nq, int64_t* out_ids, float* out_scores,
@@ -1081,11 +1182,8 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
 #define NRLSH_PP(T_, C_, NAME)                                                                  \
     {                                                                                           \
         auto kern = probe_rerank_persistent_kernel<T_, C_>;                                     \
-        if (smem > 48 * 1024) {                                                                 \
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                 (int)smem);                                    \
-            if (e != cudaSuccess) return e;                                                     \
-        }                                                                                       \
+        cudaError_t e = ensure_dyn_smem((const void*)kern, smem);                               \
+        if (e != cudaSuccess) return e;                                                         \
         return launch(NAME, kern, dim3((unsigned)ctas), dim3(256), smem, st, H, order, m, L, n,  \
                       seg, budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q,    \
                       xnorm, qnorm, kappa, perm, ks, k_max, slabs, cap, work, nq, out_ids,      \
