@@ -57,8 +57,6 @@ struct nrlsh_index {
     int64_t* seg = nullptr;        // m+1 storage offsets of the sub-datasets
     nrlsh::PosTile* tiles = nullptr;
     int32_t ntiles = 0;
-    std::vector<nrlsh::PosTile> tiles_host;  // sources of the asynchronous uploads
-    std::vector<int64_t> seg_host;
     unsigned* ambiguous = nullptr;  // (item, bit) pairs the first tier left undecided
     int projection = NRLSH_PROJECT_SIMT;
     __nv_bfloat16* At = nullptr;     // A^T in bf16, 64 x dp (tensor-core B operand)
@@ -153,8 +151,9 @@ bool is_device_ptr(const void* p) {
 // The stream-ordered pool keeps freed blocks for reuse instead of returning
 // them to the driver at every synchronisation.
 void keep_pool_memory(int device) {
-    static std::once_flag once;
-    std::call_once(once, [device] {
+    static std::once_flag once[64];
+    if (device < 0 || device >= 64) return;
+    std::call_once(once[device], [device] {
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
             uint64_t thr = UINT64_MAX;
@@ -164,22 +163,33 @@ void keep_pool_memory(int device) {
     });
 }
 
-// Scratch allocations of one call, released on its stream at scope exit.
+// Scratch memory of one call: bump-allocated (256-byte aligned) from blocks of the
+// stream-ordered pool, released on its stream at scope exit.
 struct Scratch {
+    static constexpr size_t kBlock = (size_t)8 << 20;
     cudaStream_t s;
-    std::vector<void*> ptrs;
+    std::vector<void*> blocks;
+    char* cur = nullptr;
+    size_t left = 0;
     explicit Scratch(cudaStream_t st) : s(st) {}
     ~Scratch() {
-        for (void* p : ptrs) cudaFreeAsync(p, s);
+        for (void* p : blocks) cudaFreeAsync(p, s);
     }
     template <typename T>
     nrlsh_status get(T** out, size_t count) {
-        void* p = nullptr;
-        const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-        cudaError_t e = cudaMallocAsync(&p, bytes, s);
-        if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync");
-        ptrs.push_back(p);
-        *out = (T*)p;
+        const size_t bytes = (std::max<size_t>(count * sizeof(T), 16) + 255) & ~(size_t)255;
+        if (bytes > left) {
+            void* p = nullptr;
+            const size_t bb = std::max(bytes, kBlock);
+            cudaError_t e = cudaMallocAsync(&p, bb, s);
+            if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync");
+            blocks.push_back(p);
+            cur = (char*)p;
+            left = bb;
+        }
+        *out = (T*)cur;
+        cur += bytes;
+        left -= bytes;
         return NRLSH_OK;
     }
 };
@@ -205,7 +215,8 @@ void destroy(nrlsh_index* ix) {
         for (void* p : g.workspace) cudaFree(p);
     }
     cudaDeviceSynchronize();
-    for (void* p : ix->owned) cudaFree(p);
+    for (void* p : ix->owned) cudaFreeAsync(p, ix->stream);
+    cudaStreamSynchronize(ix->stream);
     delete ix;
 }
 
@@ -338,14 +349,9 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     const int64_t tile = 16384 / ix->code_bytes;
     const bool uniform = partition == NRLSH_PARTITION_UNIFORM;
     if (!uniform) {
-        std::vector<PosTile>& tl = ix->tiles_host;
-        std::vector<int64_t>& sg = ix->seg_host;
-        for (int32_t j = 0; j <= m; ++j) sg.push_back(seg_start(j, n, m));
-        for (int32_t j = 0; j < m; ++j) {
-            const int64_t a = sg[j], b = sg[j + 1];
-            for (int64_t s = a; s < b; s += tile) tl.push_back({s, (int32_t)std::min(tile, b - s), j});
-        }
-        ix->ntiles = (int32_t)tl.size();
+        int64_t nt = 0;
+        for (int32_t j = 0; j < m; ++j) nt += ceil_div(seg_start(j + 1, n, m) - seg_start(j, n, m), tile);
+        ix->ntiles = (int32_t)nt;
     } else {
         ix->ntiles = (int32_t)(ceil_div(n, tile) + m);
     }
@@ -385,18 +391,12 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         Carver sizing;
         carve(sizing);
         void* base = nullptr;
-        cudaError_t e = cudaMalloc(&base, sizing.off);
-        if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc (index)"));
+        cudaError_t e = cudaMallocAsync(&base, sizing.off, st);
+        if (e != cudaSuccess) return fail(cuda_status(e, "cudaMallocAsync (index)"));
         ix->owned.push_back(base);
         ix->device_bytes = (int64_t)sizing.off;
         Carver real{(char*)base, 0};
         carve(real);
-    }
-    if (!uniform) {
-        B_CU(cudaMemcpyAsync(ix->tiles, ix->tiles_host.data(), ix->tiles_host.size() * sizeof(PosTile),
-                             cudaMemcpyHostToDevice, st));
-        B_CU(cudaMemcpyAsync(ix->seg, ix->seg_host.data(), ix->seg_host.size() * sizeof(int64_t),
-                             cudaMemcpyHostToDevice, st));
     }
 
     {
@@ -439,6 +439,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, ix->At, ix->dp, d, L, ix->Lp, seed,
                                 side));
         B_CU(launch_class_cos(L, eps, ix->ccos, side));
+        if (!uniform)  // percentile ranges: offsets and tiles follow from n and m
+            B_CU(launch_segments(nullptr, n, m, tile, ix->seg, ix->tiles, ix->ntiles, side));
         B_CU(side_stream_join(st));
         const int jbits = (bits_for(m) + 7) / 8 * 8;
         bool alt = false;
@@ -465,8 +467,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
             jv_alt = vals_alt;
             B_CU(launch_uniform_assign(ix->s_id, n, m, (unsigned long long*)keys_alt, ix->sub_of_id,
                                        ix->U2, jkeys, jv, (uint32_t*)keys, st));
-            B_CU(launch_segments((const uint32_t*)keys, m, tile, ix->seg, ix->tiles, ix->ntiles,
-                                 st));
+            B_CU(launch_segments((const uint32_t*)keys, n, m, tile, ix->seg, ix->tiles,
+                                 ix->ntiles, st));
         }
         if (!small) {
             B_CU(radix_sort_u32(jkeys, jv, jkeys_alt, jv_alt, n, jbits, sort_tmp, &alt, st));

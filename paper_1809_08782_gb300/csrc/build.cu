@@ -824,22 +824,26 @@ __device__ int64_t block_scan_1024(int64_t v, int64_t* total, int64_t* wsum) {
 // ntiles_max, get length 0.  One block; thread t owns sub-datasets
 // [t per, (t + 1) per).
 __global__ void __launch_bounds__(1024)
-    segments_kernel(const uint32_t* __restrict__ cnt, int m, int64_t tile, int64_t* seg,
+    segments_kernel(const uint32_t* __restrict__ cnt, int64_t n, int m, int64_t tile, int64_t* seg,
                     PosTile* tiles, int ntiles_max) {
     __shared__ int64_t wsum[32];
     const int per = (m + 1023) / 1024;
     const int b = min(m, (int)threadIdx.x * per), e = min(m, b + per);
+    // sizes: counted (uniform ranges) or floor((j+1)n/m) - floor(jn/m) (percentiles)
+    auto size_of = [&](int j) -> int64_t {
+        return cnt ? (int64_t)cnt[j] : seg_start(j + 1, n, m) - seg_start(j, n, m);
+    };
     int64_t items = 0, ntl = 0;
     for (int j = b; j < e; ++j) {
-        items += cnt[j];
-        ntl += ceil_div((int64_t)cnt[j], tile);
+        items += size_of(j);
+        ntl += ceil_div(size_of(j), tile);
     }
     int64_t items_total, tiles_total;
     int64_t pos = block_scan_1024(items, &items_total, wsum);
     int64_t t = block_scan_1024(ntl, &tiles_total, wsum);
     for (int j = b; j < e; ++j) {
         seg[j] = pos;
-        const int64_t len = cnt[j];
+        const int64_t len = size_of(j);
         for (int64_t a = 0; a < len; a += tile) tiles[t++] = {pos + a, (int32_t)min(tile, len - a), j};
         pos += len;
     }
@@ -996,9 +1000,9 @@ cudaError_t launch_uniform_assign(const double* s_id, int64_t n, int m, unsigned
                   (unsigned long long*)U2, jkeys, jvals, cnt);
 }
 
-cudaError_t launch_segments(const uint32_t* cnt, int m, int64_t tile, int64_t* seg,
+cudaError_t launch_segments(const uint32_t* cnt, int64_t n, int m, int64_t tile, int64_t* seg,
                             PosTile* tiles, int ntiles_max, cudaStream_t st) {
-    return launch("segments", segments_kernel, dim3(1), dim3(1024), 0, st, cnt, m, tile, seg,
+    return launch("segments", segments_kernel, dim3(1), dim3(1024), 0, st, cnt, n, m, tile, seg,
                   tiles, ntiles_max);
 }
 

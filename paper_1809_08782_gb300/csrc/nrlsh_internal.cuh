@@ -117,8 +117,9 @@ cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* s
 cudaError_t launch_uniform_assign(const double* s_id, int64_t n, int m, unsigned long long* range,
                                   uint32_t* sub_of_id, double* U2, uint32_t* jkeys,
                                   uint32_t* jvals, uint32_t* cnt, cudaStream_t st);
-// Segment offsets seg[0..m] and histogram tiles from the sub-dataset sizes.
-cudaError_t launch_segments(const uint32_t* cnt, int m, int64_t tile, int64_t* seg,
+// Segment offsets seg[0..m] and histogram tiles from the sub-dataset sizes
+// (cnt, or with cnt null the percentile sizes of n items in m ranges).
+cudaError_t launch_segments(const uint32_t* cnt, int64_t n, int m, int64_t tile, int64_t* seg,
                             PosTile* tiles, int ntiles_max, cudaStream_t st);
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
                                 const uint32_t* perm, int64_t n, const uint32_t* sub_of_id,
