@@ -60,6 +60,7 @@ struct nrlsh_index {
     unsigned* ambiguous = nullptr;  // (item, bit) pairs the first tier left undecided
     int projection = NRLSH_PROJECT_SIMT;
     __nv_bfloat16* At = nullptr;     // A^T in bf16, 64 x dp (tensor-core B operand)
+    float* At32 = nullptr;           // A^T in fp32, the warp-per-row projection's layout
     __nv_bfloat16* Xb = nullptr;     // fp32 items: bf16 high part, n x dp (tensor-core A operand)
     __nv_bfloat16* Xb2 = nullptr;    // fp32 items: bf16 low part (x - hi rounded), n x dp
     int* dev_err = nullptr;          // set by bounded device waits that ran out
@@ -379,6 +380,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         c.take(&ix->ambiguous, 1);
         c.take(&ix->dev_err, 1);
         c.take(&ix->tiles, (size_t)ix->ntiles);
+        if (warp_proj_stride(d, ix->Lp) > 0) c.take(&ix->At32, warp_proj_at_floats(d, ix->Lp));
         if (tc) {
             c.take(&ix->At, (size_t)64 * ix->dp);
             if (dtype == NRLSH_F32) {
@@ -439,6 +441,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, ix->At, ix->dp, d, L, ix->Lp, seed,
                                 side));
         B_CU(launch_class_cos(L, eps, ix->ccos, side));
+        if (ix->At32) B_CU(launch_transpose_a(ix->A_pad, d, L, ix->Lp, ix->At32, side));
         if (!uniform)  // percentile ranges: offsets and tiles follow from n and m
             B_CU(launch_segments(nullptr, n, m, tile, ix->seg, ix->tiles, ix->ntiles, side));
         B_CU(side_stream_join(st));
@@ -484,7 +487,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         if (!tc) {
             B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
                                      ix->tau64, ix->tau32, ix->xnorm, ix->codes, ix->code_bytes,
-                                     amb_list, ix->ambiguous, (unsigned)amb_cap, st));
+                                     amb_list, ix->ambiguous, (unsigned)amb_cap, ix->At32, st));
         } else {
             const __nv_bfloat16* xb = dtype == NRLSH_F32 ? ix->Xb : (const __nv_bfloat16*)ix->Xp;
             B_CU(launch_project_tc(xb, ix->Xb2, ix->Xp, n, d, ix->dp, L, ix->Lp, ix->At, ix->A_pad,
@@ -561,11 +564,9 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
         NRLSH_CKS(sc.get(&qamb_list, qamb_cap));
         NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CKS(sc.get(&qcodes, qc * ix->code_bytes));
-        NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
         // P(q) = [q; 0] (Eq. 8), hashed by Eq. 4
-        NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
-                                     ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
-                                     qamb_list, qamb, (unsigned)qamb_cap, st));
+        NRLSH_CK(launch_hash_queries(Qc, qc, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, qnorm,
+                                     qcodes, ix->code_bytes, qamb_list, qamb, (unsigned)qamb_cap, ix->At32, st));
         if (stage == Stage::Hash) {
             if (ix->code_bytes == 8) {
                 NRLSH_CK(cudaMemcpyAsync(o.codes + q0, qcodes, 8 * qc, cudaMemcpyDeviceToDevice, st));
@@ -668,11 +669,9 @@ nrlsh_status run_multitable(const nrlsh_index* ix, const float* Q, int64_t nq, i
         NRLSH_CKS(sc.get(&qamb_list, qamb_cap));
         NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CKS(sc.get(&qcodes, qc * ix->code_bytes));
-        NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
         // P(q) = [q; 0] (Eq. 8), hashed by Eq. 4
-        NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
-                                     ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
-                                     qamb_list, qamb, (unsigned)qamb_cap, st));
+        NRLSH_CK(launch_hash_queries(Qc, qc, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, qnorm,
+                                     qcodes, ix->code_bytes, qamb_list, qamb, (unsigned)qamb_cap, ix->At32, st));
         uint32_t *cand, *cont = nullptr;
         float *lo = nullptr, *hi = nullptr;
         double* cont_s = nullptr;
@@ -1131,10 +1130,9 @@ nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, cons
                          const int64_t* budgets, int k_max, int64_t cap, const nrlsh_batch_cfg& cfg,
                          const BatchWs& w, int64_t* ids, float* scores, cudaStream_t st) {
     NRLSH_CK(cudaMemsetAsync(w.qamb, 0, sizeof(unsigned), st));
-    NRLSH_CK(launch_row_norm_bound(Q, nq, ix->d, w.qnorm, st));
-    NRLSH_CK(launch_project_fp32(Q, NRLSH_F32, nq, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
-                                 ix->anorm, nullptr, nullptr, w.qnorm, w.qcodes, ix->code_bytes,
-                                 w.qamb_list, w.qamb, (unsigned)w.qamb_cap, st));
+    NRLSH_CK(launch_hash_queries(Q, nq, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, w.qnorm,
+                                 w.qcodes, ix->code_bytes, w.qamb_list, w.qamb,
+                                 (unsigned)w.qamb_cap, ix->At32, st));
     for (int64_t q0 = 0; q0 < nq; q0 += w.hq) {
         const int64_t qc = std::min(w.hq, nq - q0);
         const char* qcodes = w.qcodes + q0 * ix->code_bytes;
@@ -1450,10 +1448,8 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* ix, con
         // previous call's contents
         NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
-        NRLSH_CK(launch_row_norm_bound(Qc, qc, ix->d, qnorm, st));
-        NRLSH_CK(launch_project_fp32(Qc, NRLSH_F32, qc, ix->d, ix->d, ix->L, ix->Lp, ix->A_pad,
-                                     ix->anorm, nullptr, nullptr, qnorm, qcodes, ix->code_bytes,
-                                     qamb_list, qamb, (unsigned)qamb_cap, st));
+        NRLSH_CK(launch_hash_queries(Qc, qc, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, qnorm,
+                                     qcodes, ix->code_bytes, qamb_list, qamb, (unsigned)qamb_cap, ix->At32, st));
         NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
                              ix->ntiles, H, st));
         NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, ix->n, ix->seg, qc, probe_budget, nullptr, 0u,

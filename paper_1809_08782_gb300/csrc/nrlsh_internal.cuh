@@ -130,11 +130,26 @@ cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d
 // fast tier; undecided (row, bit) pairs go through amb_list (capacity amb_cap,
 // count in *amb_count, which must start at 0) to the FP64 resolve kernel.
 // Items pass tau (tau64 != null); queries pass tau64 = tau32 = null.
+// At32 (may be null): A^T as written by launch_transpose_a, copied straight into
+// shared memory by the warp-per-row kernel.
 cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx,
                                 int L, int Lp, const float* A_pad, const float* anorm,
                                 const double* tau64, const float* tau32, const float* xnorm,
                                 void* codes, int code_bytes, unsigned long long* amb_list,
-                                unsigned* amb_count, unsigned amb_cap, cudaStream_t st);
+                                unsigned* amb_count, unsigned amb_cap, const float* At32,
+                                cudaStream_t st);
+// A^T for the warp-per-row projection (warp_proj_at_floats(d, Lp) floats; no-op
+// when that projection does not apply).
+int warp_proj_stride(int d, int Lp);
+size_t warp_proj_at_floats(int d, int Lp);
+cudaError_t launch_transpose_a(const float* A_pad, int d, int L, int Lp, float* At32,
+                               cudaStream_t st);
+// Query codes (P(q) = [q; 0]) and the queries' fp32 norm bounds (qnorm, written
+// here) in one pass where the warp-per-row projection applies.
+cudaError_t launch_hash_queries(const float* Q, int64_t nq, int d, int L, int Lp,
+                                const float* A_pad, const float* anorm, float* qnorm, void* codes,
+                                int code_bytes, unsigned long long* amb_list, unsigned* amb_count,
+                                unsigned amb_cap, const float* At32, cudaStream_t st);
 // Entries of the ambiguity list to reserve for `rows` rows of L bits.
 size_t ambiguity_capacity(int64_t rows, int L);
 // FP32 tier (fp32 items after the bf16 tensor-core pass) and FP64 tier on a list

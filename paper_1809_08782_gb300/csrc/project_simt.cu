@@ -232,13 +232,19 @@ __global__ void __launch_bounds__(256)
                         const float* __restrict__ A_pad, const float* __restrict__ anorm,
                         const double* __restrict__ tau64, const float* __restrict__ tau32,
                         const float* __restrict__ xnorm, void* __restrict__ codes, int code_bytes,
-                        unsigned* amb_count, float kappa) {
-    extern __shared__ float At_s[];          // Lr x dpa, Lr = Lp rounded up to 32
+                        unsigned* amb_count, float kappa, float* __restrict__ norm_out,
+                        const float* __restrict__ At32) {
+    extern __shared__ __align__(16) float At_s[];  // Lr x dpa, Lr = Lp rounded up to 32
     __shared__ float ad_s[64], an_s[64];
     const int Lr = (Lp + 31) / 32 * 32;
-    for (int i = threadIdx.x; i < Lr * dpa; i += blockDim.x) {
-        const int b = i / dpa, k = i % dpa;
-        At_s[i] = (b < L && k < d) ? A_pad[(int64_t)k * Lp + b] : 0.0f;
+    if (At32) {  // the index keeps A^T in this layout: a straight vector copy
+        for (int i = threadIdx.x; i < Lr * dpa / 4; i += blockDim.x)
+            ((float4*)At_s)[i] = ((const float4*)At32)[i];
+    } else {
+        for (int i = threadIdx.x; i < Lr * dpa; i += blockDim.x) {
+            const int b = i / dpa, k = i % dpa;
+            At_s[i] = (b < L && k < d) ? A_pad[(int64_t)k * Lp + b] : 0.0f;
+        }
     }
     if (threadIdx.x < 64) {
         const int b = threadIdx.x;
@@ -261,6 +267,22 @@ __global__ void __launch_bounds__(256)
                 const int k = lane + 32 * i;
                 x[r][i] = (row0 + r < n && k < d) ? to_f32(X[(row0 + r) * ldx + k]) : 0.0f;
             }
+        // fp32 upper bound of ||x||: given (items), or computed here from the row
+        // in registers (queries; FP64 squares in lane-strided order and a tree)
+        float xn[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            if (norm_out) {
+                double ss = 0.0;
+#pragma unroll
+                for (int i = 0; i < NREG; ++i) ss = fma((double)x[r][i], (double)x[r][i], ss);
+                for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                xn[r] = __fsqrt_ru(__double2float_ru(ss));
+                if (lane == 0 && row0 + r < n) norm_out[row0 + r] = xn[r];
+            } else {
+                xn[r] = row0 + r < n ? xnorm[row0 + r] : 0.0f;
+            }
+        }
         unsigned long long word[ROWS], undecided[ROWS];
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) word[r] = undecided[r] = 0;
@@ -298,11 +320,10 @@ __global__ void __launch_bounds__(256)
             for (int r = 0; r < ROWS; ++r) {
                 bool set = false, open = false;
                 if (bit < L && row0 + r < n) {
-                    const float xn = xnorm[row0 + r];
                     const float t32 = has_tail ? tau32[row0 + r] : 0.0f;
                     const float ad = ad_s[bit];
                     const float v = has_tail ? fmaf(ad, t32, acc[r][0]) : acc[r][0];
-                    const float bound = kappa * an_s[bit] * xn + 0x1p-20f * fabsf(ad) * t32;
+                    const float bound = kappa * an_s[bit] * xn[r] + 0x1p-20f * fabsf(ad) * t32;
                     if (fabsf(v) * (1.0f - 0x1p-21f) > bound)
                         set = v > 0.0f;
                     else
@@ -374,6 +395,34 @@ cudaError_t project_rows(const void* X, int64_t n, int d, int ldx, int L, int Lp
                   tau32, xnorm, (C*)codes, amb_list, amb_count, amb_cap, kappa);
 }
 
+constexpr size_t kWarpProjMaxSmem = 227 * 1024;
+
+}  // namespace
+
+// Row stride (columns) of A^T for the warp-per-row projection, or 0 when it does
+// not apply (rows longer than 1,024, or A^T beyond the shared memory of a block).
+int warp_proj_stride(int d, int Lp) {
+    const int nreg = (d + 31) / 32;
+    if (nreg > 32) return 0;
+    const int dpa = (nreg <= 4 ? 4 : nreg <= 10 ? 10 : 32) * 32;
+    const size_t lr = (size_t)(Lp + 31) / 32 * 32;
+    return sizeof(float) * lr * dpa <= kWarpProjMaxSmem ? dpa : 0;
+}
+
+size_t warp_proj_at_floats(int d, int Lp) {
+    return (size_t)(Lp + 31) / 32 * 32 * warp_proj_stride(d, Lp);
+}
+
+namespace {
+
+// A^T for the warp-per-row projection: row b holds a_{k,b}, k < d, zero-padded.
+__global__ void transpose_a_kernel(const float* __restrict__ A_pad, int d, int L, int Lp, int dpa,
+                                   float* __restrict__ At32) {
+    const int b = blockIdx.x;
+    for (int k = threadIdx.x; k < dpa; k += blockDim.x)
+        At32[(int64_t)b * dpa + k] = (b < L && k < d) ? A_pad[(int64_t)k * Lp + b] : 0.0f;
+}
+
 // Per kernel (and thread): the dynamic shared memory the attribute allows so far
 // (only ever raised, since launches with other code widths share the kernel)
 // and the blocks per SM for the last size asked.
@@ -388,14 +437,12 @@ template <typename T, int NREG, int ROWS> thread_local size_t WarpKernelState<T,
 template <typename T, int NREG, int ROWS> thread_local size_t WarpKernelState<T, NREG, ROWS>::occ_smem = 0;
 template <typename T, int NREG, int ROWS> thread_local int WarpKernelState<T, NREG, ROWS>::per_sm = 1;
 
-constexpr size_t kWarpProjMaxSmem = 227 * 1024;
-
 template <typename T, typename C, int NREG, int ROWS>
 cudaError_t project_warp_launch(const void* X, int64_t n, int d, int ldx, int L, int Lp,
                                 const float* A_pad, const float* anorm, const double* tau64,
                                 const float* tau32, const float* xnorm, void* codes,
-                                unsigned* amb_count, float kappa, cudaStream_t st,
-                                const char* name) {
+                                unsigned* amb_count, float kappa, float* norm_out,
+                                const float* At32, cudaStream_t st, const char* name) {
     using S = WarpKernelState<T, NREG, ROWS>;
     const int Lr = (Lp + 31) / 32 * 32, dpa = NREG * 32;
     const size_t smem = sizeof(float) * (size_t)Lr * dpa;
@@ -422,7 +469,8 @@ cudaError_t project_warp_launch(const void* X, int64_t n, int d, int ldx, int L,
     const unsigned grid =
         (unsigned)std::min<int64_t>(ceil_div(n, 8 * ROWS), (int64_t)S::per_sm * 152);
     return launch(name, kern, dim3(grid), dim3(256), smem, st, (const T*)X, n, d, ldx, L, Lp, dpa,
-                  A_pad, anorm, tau64, tau32, xnorm, codes, (int)sizeof(C), amb_count, kappa);
+                  A_pad, anorm, tau64, tau32, xnorm, codes, (int)sizeof(C), amb_count, kappa,
+                  norm_out, At32);
 }
 
 template <typename T, typename C>
@@ -430,15 +478,16 @@ cudaError_t project_dispatch(const void* X, int64_t n, int d, int ldx, int L, in
                              const float* A_pad, const float* anorm, const double* tau64,
                              const float* tau32, const float* xnorm, void* codes,
                              unsigned long long* amb_list, unsigned* amb_count, unsigned amb_cap,
-                             cudaStream_t st, const char* name) {
+                             cudaStream_t st, const char* name, float* norm_out,
+                             const float* At32) {
     const float kappa = (float)(d + 2) * 0x1p-22f;
     cudaError_t e;
-    const int nreg = (d + 31) / 32;
-    const int nreg_t = nreg <= 4 ? 4 : nreg <= 10 ? 10 : 32;
-    if (nreg <= 32 && sizeof(float) * (size_t)((Lp + 31) / 32 * 32) * nreg_t * 32 <= kWarpProjMaxSmem) {
+    const int nreg_t = warp_proj_stride(d, Lp) / 32;
+    if (nreg_t > 0) {
 #define NRLSH_PW(R_, ROWS_)                                                                   \
     e = project_warp_launch<T, C, R_, ROWS_>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32,     \
-                                             xnorm, codes, amb_count, kappa, st, name);           \
+                                             xnorm, codes, amb_count, kappa, norm_out, At32, st,  \
+                                             name);                                               \
     break;
         switch (nreg_t) {
             case 4: NRLSH_PW(4, 2)
@@ -447,6 +496,11 @@ cudaError_t project_dispatch(const void* X, int64_t n, int d, int ldx, int L, in
         }
 #undef NRLSH_PW
         return e;
+    }
+    if (norm_out) {  // the register-tiled kernel reads the norm bounds
+        e = launch_row_norm_bound((const float*)X, n, d, norm_out, st);
+        if (e != cudaSuccess) return e;
+        xnorm = norm_out;
     }
     switch (Lp / 8) {
         case 1:
@@ -478,28 +532,51 @@ cudaError_t project_dispatch(const void* X, int64_t n, int d, int ldx, int L, in
 
 }  // namespace
 
+cudaError_t launch_transpose_a(const float* A_pad, int d, int L, int Lp, float* At32,
+                               cudaStream_t st) {
+    const int dpa = warp_proj_stride(d, Lp);
+    if (dpa == 0) return cudaSuccess;
+    return launch("transpose_a", transpose_a_kernel, dim3((unsigned)((Lp + 31) / 32 * 32)),
+                  dim3(256), 0, st, A_pad, d, L, Lp, dpa, At32);
+}
+
 cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx,
                                 int L, int Lp, const float* A_pad, const float* anorm,
                                 const double* tau64, const float* tau32, const float* xnorm,
                                 void* codes, int code_bytes, unsigned long long* amb_list,
-                                unsigned* amb_count, unsigned amb_cap, cudaStream_t st) {
+                                unsigned* amb_count, unsigned amb_cap, const float* At32,
+                                cudaStream_t st) {
     if (dt == NRLSH_BF16) {
         if (code_bytes == 4)
             return project_dispatch<__nv_bfloat16, uint32_t>(X, n, d, ldx, L, Lp, A_pad, anorm,
                                                              tau64, tau32, xnorm, codes, amb_list,
                                                              amb_count, amb_cap, st,
-                                                             "project_fp32_bf16");
+                                                             "project_fp32_bf16", nullptr, At32);
         return project_dispatch<__nv_bfloat16, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64,
                                                          tau32, xnorm, codes, amb_list, amb_count,
-                                                         amb_cap, st, "project_fp32_bf16");
+                                                         amb_cap, st, "project_fp32_bf16", nullptr,
+                                                         At32);
     }
     if (code_bytes == 4)
         return project_dispatch<float, uint32_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32,
                                                  xnorm, codes, amb_list, amb_count, amb_cap, st,
-                                                 "project_fp32");
+                                                 "project_fp32", nullptr, At32);
     return project_dispatch<float, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
                                              codes, amb_list, amb_count, amb_cap, st,
-                                             "project_fp32");
+                                             "project_fp32", nullptr, At32);
+}
+
+cudaError_t launch_hash_queries(const float* Q, int64_t nq, int d, int L, int Lp,
+                                const float* A_pad, const float* anorm, float* qnorm, void* codes,
+                                int code_bytes, unsigned long long* amb_list, unsigned* amb_count,
+                                unsigned amb_cap, const float* At32, cudaStream_t st) {
+    if (code_bytes == 4)
+        return project_dispatch<float, uint32_t>(Q, nq, d, d, L, Lp, A_pad, anorm, nullptr, nullptr,
+                                                 nullptr, codes, amb_list, amb_count, amb_cap, st,
+                                                 "hash_queries", qnorm, At32);
+    return project_dispatch<float, uint64_t>(Q, nq, d, d, L, Lp, A_pad, anorm, nullptr, nullptr,
+                                             nullptr, codes, amb_list, amb_count, amb_cap, st,
+                                             "hash_queries", qnorm, At32);
 }
 
 cudaError_t launch_resolve_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
