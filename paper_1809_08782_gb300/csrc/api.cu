@@ -420,7 +420,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CK(sc.get(&vals_alt, n));
         B_CK(sc.get(&jkeys, n));
         B_CK(sc.get(&jkeys_alt, n));
-        B_CK(sc.get(&sort_tmp, std::max(radix_sort_temp_bytes(n), small_rank_temp_bytes(n))));
+        B_CK(sc.get(&sort_tmp, std::max(radix_sort_temp_bytes(n),
+                                        small_rank_supported(n, m) ? small_rank_temp_bytes(n, m) : 0)));
         char* bo_tmp;
         B_CK(sc.get(&bo_tmp, bucket_order_temp_bytes(m, L)));
         B_CK(sc.get(&amb_list, amb_cap));
@@ -452,8 +453,8 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         if (small) {
             // Algorithm 1 for small inputs: tile sort, rank, per-range id sort
             B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
-            B_CU(launch_small_rank(keys, vals, keys_alt, vals_alt, n, m, sort_tmp, ix->perm,
-                                   ix->sub_of_id, ix->U2, st));
+            B_CU(launch_small_rank(keys, vals, n, m, sort_tmp, ix->perm, ix->sub_of_id, ix->U2,
+                                   st));
         } else if (!uniform) {
             // Algorithm 1: rank by norm, percentile partition, U_j
             B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));

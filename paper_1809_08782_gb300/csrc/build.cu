@@ -512,11 +512,12 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
 }
 
 // =====================================================================
-// Ranking for small inputs (n <= 64 tiles of 1,024): sort each tile of (s_x, id)
-// keys in shared memory, rank every key against the other tiles by binary search
-// (one block per tile pair), and let the last block of each tile scatter it; then
-// one block per percentile range sorts that range's ids.  Three launches instead
-// of a radix pass per 8-bit digit plus a second sort.
+// Ranking for small inputs (n <= 64 tiles of 1,024): each tile of (s_x, id) keys
+// is sorted in shared memory; a key's rank is the number of smaller keys,
+// counted tile pair by tile pair by binary search; ranks give each item's
+// percentile range, U_j^2 and a per-range bitmap of ids, and one block per range
+// reads its bitmap in id order to lay out storage.  Four launches instead of a
+// radix pass per 8-bit digit plus a second sort.
 // =====================================================================
 
 namespace {
@@ -527,10 +528,9 @@ __device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ia, uint64_t kb, 
     return ka < kb || (ka == kb && ia < ib);
 }
 
-// Block per tile: bitonic sort of up to 1,024 (key, id) pairs (padded with the
-// largest pair), one pair per thread, written back in place.  Exchanges between
-// threads less than 32 apart go through warp shuffles; wider ones through shared
-// memory.
+// Block per tile, one key per thread: bitonic sort of up to 1,024 (key, id) pairs
+// in place (padded with the largest pair; exchanges less than 32 apart through
+// warp shuffles, wider ones through shared memory).
 __global__ void __launch_bounds__(kRankTile)
     tile_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ids, int64_t n) {
     __shared__ uint64_t k_s[kRankTile];
@@ -558,8 +558,7 @@ __global__ void __launch_bounds__(kRankTile)
             // the lower thread of a pair keeps the smaller pair in an ascending run
             const bool lower = (t & stride) == 0;
             const bool ascending = (t & size) == 0;
-            const bool other_less = key_less(k2, i2, k, id);
-            if (other_less == (lower == ascending)) {
+            if (key_less(k2, i2, k, id) == (lower == ascending)) {
                 k = k2;
                 id = i2;
             }
@@ -571,135 +570,126 @@ __global__ void __launch_bounds__(kRankTile)
     }
 }
 
-// Block (t, u): every key of sorted tile t counts the keys of sorted tile u that
-// are smaller (binary search in shared memory; for u = t its own index) and adds
-// the count to its rank.  The last of the T blocks of tile t to finish writes the
-// tile's keys and ids at their ranks.  rank (n words) and done (T words) start at 0.
-__global__ void __launch_bounds__(256)
+// Block (t, u) over sorted tiles: each key of tile t adds the number of smaller
+// keys of tile u (binary search in shared memory; its own index when u = t) to
+// its rank (rank: n words starting at 0).
+__global__ void __launch_bounds__(512)
     tile_rank_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ids, int64_t n,
-                     unsigned* __restrict__ rank, unsigned* __restrict__ done,
-                     uint64_t* __restrict__ out_keys, uint32_t* __restrict__ out_ids) {
+                     unsigned* __restrict__ rank) {
     __shared__ uint64_t k_s[kRankTile];
     __shared__ uint32_t i_s[kRankTile];
-    __shared__ bool last_s;
-    const int T = (int)gridDim.x;
-    const int t = blockIdx.x, u = blockIdx.y;
-    const int64_t tb = (int64_t)t * kRankTile, ub = (int64_t)u * kRankTile;
+    const int64_t tb = (int64_t)blockIdx.x * kRankTile, ub = (int64_t)blockIdx.y * kRankTile;
     const int tlen = (int)min((int64_t)kRankTile, n - tb);
     const int ulen = (int)min((int64_t)kRankTile, n - ub);
-    if (u != t) {
+    const bool self = blockIdx.x == blockIdx.y;
+    if (!self) {
         for (int i = threadIdx.x; i < ulen; i += blockDim.x) {
             k_s[i] = keys[ub + i];
             i_s[i] = ids[ub + i];
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int i = threadIdx.x; i < tlen; i += blockDim.x) {
-        unsigned c;
-        if (u == t) {
-            c = (unsigned)i;
-        } else {
-            const uint64_t k = keys[tb + i];
-            const uint32_t id = ids[tb + i];
-            int lo = 0, hi = ulen;                  // first index whose key is not smaller
+        int lo = i;
+        if (!self) {
+            const uint64_t kq = keys[tb + i];
+            const uint32_t iq = ids[tb + i];
+            int hi = ulen;  // first index whose pair is not smaller
+            lo = 0;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (key_less(k_s[mid], i_s[mid], k, id)) lo = mid + 1; else hi = mid;
+                if (key_less(k_s[mid], i_s[mid], kq, iq)) lo = mid + 1; else hi = mid;
             }
-            c = (unsigned)lo;
         }
-        if (c) atomicAdd(&rank[tb + i], c);
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last_s = atomicAdd(&done[t], 1u) == (unsigned)(T - 1);
-    __syncthreads();
-    if (!last_s) return;
-    __threadfence();
-    for (int i = threadIdx.x; i < tlen; i += blockDim.x) {
-        const unsigned r = atomicAdd(&rank[tb + i], 0u);
-        out_keys[r] = keys[tb + i];
-        out_ids[r] = ids[tb + i];
+        if (lo) atomicAdd(&rank[tb + i], (unsigned)lo);
     }
 }
 
-// Block per percentile range j (ranks [seg_start(j), seg_start(j+1)), at most
-// 4,096): the range's ids in ascending order, so that storage order is (j, id);
-// writes perm, sub_of_id and U_j^2 (the key at the range's last rank).  Up to
-// 1,024 ids each thread counts the smaller ids of the range (ids are distinct);
-// longer ranges use a bitonic sort in shared memory.
-__global__ void __launch_bounds__(1024)
-    range_sort_kernel(const uint64_t* __restrict__ sorted_keys,
-                      const uint32_t* __restrict__ sorted_ids, int64_t n, int m,
-                      uint32_t* __restrict__ perm, uint32_t* __restrict__ sub_of_id,
+// Thread per key: its range j from its rank, sub_of_id, the bit of its id in
+// range j's bitmap (W words per range, zeroed), and U_j^2 from the key at the
+// range's last rank.
+__global__ void __launch_bounds__(256)
+    rank_place_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ids,
+                      const unsigned* __restrict__ rank, int64_t n, int m, int64_t W,
+                      uint32_t* __restrict__ bitmap, uint32_t* __restrict__ sub_of_id,
                       double* __restrict__ U2) {
-    __shared__ uint32_t v[4096];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int64_t r = rank[e];
+    const int j = seg_of(r, n, m);
+    const uint32_t id = ids[e];
+    sub_of_id[id] = (uint32_t)j;
+    atomicOr(&bitmap[(int64_t)j * W + id / 32], 1u << (id % 32));
+    if (r == seg_start(j + 1, n, m) - 1) U2[j] = __longlong_as_double((long long)keys[e]);
+}
+
+// Block per range j: exclusive scan of the bitmap's popcounts, then every set bit
+// in increasing id order goes to perm[seg_start(j) + its index].
+__global__ void __launch_bounds__(256)
+    range_order_kernel(const uint32_t* __restrict__ bitmap, int64_t n, int m, int64_t W,
+                       uint32_t* __restrict__ perm) {
+    __shared__ uint32_t wsum[8];
+    __shared__ uint32_t carry_s;
     const int j = blockIdx.x;
-    const int64_t s0 = seg_start(j, n, m), s1 = seg_start(j + 1, n, m);
-    const int len = (int)(s1 - s0);
-    if (threadIdx.x == 0) U2[j] = __longlong_as_double((long long)sorted_keys[s1 - 1]);
-    if (len <= 1024) {
-        for (int i = threadIdx.x; i < len; i += blockDim.x) v[i] = sorted_ids[s0 + i];
-        __syncthreads();
-        if ((int)threadIdx.x < len) {
-            const uint32_t id = v[threadIdx.x];
-            int r = 0;
-            for (int i = 0; i < len; ++i) r += v[i] < id;
-            perm[s0 + r] = id;
-            sub_of_id[id] = (uint32_t)j;
-        }
-        return;
-    }
-    int size = 2;
-    while (size < len) size <<= 1;
-    for (int i = threadIdx.x; i < size; i += blockDim.x) v[i] = i < len ? sorted_ids[s0 + i] : 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t* bm = bitmap + (int64_t)j * W;
+    uint32_t* out = perm + seg_start(j, n, m);
+    if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
-    for (int sz = 2; sz <= size; sz <<= 1) {
-        for (int stride = sz >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < size / 2; t += blockDim.x) {
-                const int a = 2 * t - (t & (stride - 1));
-                const int b = a + stride;
-                const bool up = (a & sz) == 0;
-                const uint32_t x = v[a], y = v[b];
-                if ((y < x) == up) {
-                    v[a] = y;
-                    v[b] = x;
-                }
-            }
-            __syncthreads();
+    for (int64_t w0 = 0; w0 < W; w0 += blockDim.x) {
+        const int64_t w = w0 + threadIdx.x;
+        const uint32_t bits = w < W ? bm[w] : 0u;
+        const uint32_t c = __popc(bits);
+        uint32_t incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-    }
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        perm[s0 + i] = v[i];
-        sub_of_id[v[i]] = (uint32_t)j;
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t base = carry_s;
+        for (int i = 0; i < warp; ++i) base += wsum[i];
+        uint32_t pos = base + incl - c;
+        for (uint32_t b = bits; b; b &= b - 1) out[pos++] = (uint32_t)(w * 32 + __ffs(b) - 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int i = 0; i < 8; ++i) tot += wsum[i];
+            carry_s += tot;
+        }
+        __syncthreads();
     }
 }
 
 }  // namespace
 
 bool small_rank_supported(int64_t n, int m) {
-    return n >= 1 && n <= 64 * kRankTile && ceil_div(n, m) <= 4096;
+    return n >= 1 && n <= 64 * kRankTile && (int64_t)m * ceil_div(n, 32) <= ((int64_t)1 << 22);
 }
 
-size_t small_rank_temp_bytes(int64_t n) {
-    return sizeof(unsigned) * ((size_t)n + 64);
+size_t small_rank_temp_bytes(int64_t n, int m) {
+    return sizeof(unsigned) * ((size_t)n + (size_t)m * ceil_div(n, 32));
 }
 
-cudaError_t launch_small_rank(uint64_t* keys, uint32_t* ids, uint64_t* keys_out,
-                              uint32_t* ids_out, int64_t n, int m, void* temp, uint32_t* perm,
-                              uint32_t* sub_of_id, double* U2, cudaStream_t st) {
+cudaError_t launch_small_rank(uint64_t* keys, uint32_t* ids, int64_t n, int m,
+                              void* temp, uint32_t* perm, uint32_t* sub_of_id, double* U2,
+                              cudaStream_t st) {
     const int T = (int)ceil_div(n, kRankTile);
+    const int64_t W = ceil_div(n, 32);
     unsigned* rank = (unsigned*)temp;
-    unsigned* done = rank + n;
-    cudaError_t e = cudaMemsetAsync(temp, 0, small_rank_temp_bytes(n), st);
+    uint32_t* bitmap = rank + n;
+    cudaError_t e = cudaMemsetAsync(temp, 0, small_rank_temp_bytes(n, m), st);
     if (e != cudaSuccess) return e;
     e = launch("tile_sort", tile_sort_kernel, dim3(T), dim3(kRankTile), 0, st, keys, ids, n);
     if (e != cudaSuccess) return e;
-    e = launch("tile_rank", tile_rank_kernel, dim3(T, T), dim3(256), 0, st, (const uint64_t*)keys,
-               (const uint32_t*)ids, n, rank, done, keys_out, ids_out);
+    e = launch("tile_rank", tile_rank_kernel, dim3(T, T), dim3(512), 0, st, (const uint64_t*)keys,
+               (const uint32_t*)ids, n, rank);
     if (e != cudaSuccess) return e;
-    return launch("range_sort", range_sort_kernel, dim3(m), dim3(1024), 0, st,
-                  (const uint64_t*)keys_out, (const uint32_t*)ids_out, n, m, perm, sub_of_id, U2);
+    e = launch("rank_place", rank_place_kernel, dim3((unsigned)ceil_div(n, 256)), dim3(256), 0, st,
+               keys, ids, (const unsigned*)rank, n, m, W, bitmap, sub_of_id, U2);
+    if (e != cudaSuccess) return e;
+    return launch("range_order", range_order_kernel, dim3(m), dim3(256), 0, st,
+                  (const uint32_t*)bitmap, n, m, W, perm);
 }
 
 // =====================================================================

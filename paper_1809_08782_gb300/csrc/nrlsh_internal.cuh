@@ -99,15 +99,14 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                            int64_t n, int key_bits, void* temp, bool* result_in_alt,
                            cudaStream_t s);
-// Percentile partition for small inputs (n <= 65,536, ranges of at most 4,096):
-// sorts (keys, ids) by tiles, ranks them into keys_out/ids_out, then sorts each
-// range's ids; writes perm (storage order), sub_of_id and U2.  keys/ids are
-// overwritten (tile-sorted).  temp: small_rank_temp_bytes(n).
+// Percentile partition for small inputs (n <= 65,536 and m ceil(n/32) <= 4M):
+// ranks the (keys, ids) pairs (sorting them by tiles in place), then writes perm
+// (storage order), sub_of_id and U2.  temp: small_rank_temp_bytes(n, m).
 bool small_rank_supported(int64_t n, int m);
-size_t small_rank_temp_bytes(int64_t n);
-cudaError_t launch_small_rank(uint64_t* keys, uint32_t* ids, uint64_t* keys_out,
-                              uint32_t* ids_out, int64_t n, int m, void* temp, uint32_t* perm,
-                              uint32_t* sub_of_id, double* U2, cudaStream_t st);
+size_t small_rank_temp_bytes(int64_t n, int m);
+cudaError_t launch_small_rank(uint64_t* keys, uint32_t* ids, int64_t n, int m,
+                              void* temp, uint32_t* perm, uint32_t* sub_of_id, double* U2,
+                              cudaStream_t st);
 cudaError_t launch_segment_assign(const uint64_t* sorted_keys, const uint32_t* sorted_ids,
                                   int64_t n, int m, uint32_t* sub_of_id, double* U2,
                                   uint32_t* jkeys, uint32_t* jvals, cudaStream_t st);

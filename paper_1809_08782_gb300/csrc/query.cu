@@ -73,41 +73,56 @@ __global__ void row_norm_bound_kernel(const float* __restrict__ Q, int64_t nq, i
 // --------------------------------------------------------------- histogram
 
 
-// Block: one position tile (inside one sub-dataset) x kHistQ queries (one per thread).  The tile's
-// codes sit in shared memory and are read by broadcast; each thread keeps two
-// private histogram columns (uint16, even and odd positions, so consecutive
-// increments do not wait on each other) indexed [l][thread], so increments
-// never conflict on a bank.  Tiles hold at most 4,096 codes.
+// Block of 256 threads: one position tile (inside one sub-dataset, at most 4,096
+// codes, staged in shared memory) x kHistQ queries, with kSplit = 256 / kHistQ
+// threads per query each taking every kSplit-th code (a warp reads one code by
+// broadcast).  Every thread keeps private uint16 histogram columns indexed
+// [l][thread] (two for 32-bit codes, alternating so consecutive increments do not
+// wait on each other), so increments never conflict on a bank; the columns of a
+// query are summed at the end and added to H.
+constexpr int kHistThreads = 256;
+
 template <typename C, int kHistQ>
-__global__ void __launch_bounds__(kHistQ)
+__global__ void __launch_bounds__(kHistThreads)
     hist_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t nq, int m, int L,
                 const PosTile* __restrict__ tiles, uint32_t* __restrict__ H) {
+    constexpr int kSplit = kHistThreads / kHistQ;
+    constexpr int kSub = sizeof(C) == 4 ? 2 : 1;
     extern __shared__ unsigned char smem_raw[];
     C* cs = (C*)smem_raw;
-    uint16_t* h0 = (uint16_t*)(smem_raw + 16384);
-    uint16_t* h1 = h0 + (L + 1) * kHistQ;
+    uint16_t* h = (uint16_t*)(smem_raw + 16384);        // [kSub][L+1][kHistThreads]
+    const int tid = threadIdx.x;
+    const int qi = tid % kHistQ, sp = tid / kHistQ;
     const PosTile t = tiles[blockIdx.x];
-    const int64_t q = (int64_t)blockIdx.y * kHistQ + threadIdx.x;
-    for (int i = threadIdx.x; i < t.len; i += kHistQ) cs[i] = codes[t.start + i];
-    for (int l = 0; l <= L; ++l) {
-        h0[l * kHistQ + threadIdx.x] = 0;
-        h1[l * kHistQ + threadIdx.x] = 0;
+    const int64_t q0 = (int64_t)blockIdx.y * kHistQ;
+    const int64_t q = q0 + qi;
+    for (int i = tid; i < t.len; i += kHistThreads) cs[i] = codes[t.start + i];
+    for (int i = tid; i < kSub * (L + 1) * kHistThreads; i += kHistThreads) h[i] = 0;
+    __syncthreads();
+    if (q < nq) {
+        const C cq = qcodes[q];
+        uint16_t* h0 = h + tid;
+        uint16_t* h1 = h + (kSub - 1) * (L + 1) * kHistThreads + tid;
+        int i = sp;
+        for (; i + kSplit < t.len; i += 2 * kSplit) {
+            const int l0 = L - popc_word(cq ^ cs[i]);
+            const int l1 = L - popc_word(cq ^ cs[i + kSplit]);
+            h0[l0 * kHistThreads] += 1;
+            h1[l1 * kHistThreads] += 1;
+        }
+        if (i < t.len) h0[(L - popc_word(cq ^ cs[i])) * kHistThreads] += 1;
     }
     __syncthreads();
-    if (q >= nq) return;
-    const C cq = qcodes[q];
-    int i = 0;
-    for (; i + 1 < t.len; i += 2) {
-        const int l0 = L - popc_word(cq ^ cs[i]);
-        const int l1 = L - popc_word(cq ^ cs[i + 1]);
-        h0[l0 * kHistQ + threadIdx.x] += 1;
-        h1[l1 * kHistQ + threadIdx.x] += 1;
-    }
-    if (i < t.len) h0[(L - popc_word(cq ^ cs[i])) * kHistQ + threadIdx.x] += 1;
-    uint32_t* Hq = H + ((int64_t)q * m + t.seg) * (L + 1);
-    for (int l = 0; l <= L; ++l) {
-        const uint32_t v = (uint32_t)h0[l * kHistQ + threadIdx.x] + h1[l * kHistQ + threadIdx.x];
-        if (v) atomicAdd(&Hq[l], v);
+    for (int e = tid; e < (L + 1) * kHistQ; e += kHistThreads) {
+        const int l = e / kHistQ, qe = e % kHistQ;
+        if (q0 + qe >= nq) continue;
+        uint32_t v = 0;
+#pragma unroll
+        for (int sub = 0; sub < kSub; ++sub)
+#pragma unroll
+            for (int s2 = 0; s2 < kSplit; ++s2)
+                v += h[(sub * (L + 1) + l) * kHistThreads + s2 * kHistQ + qe];
+        if (v) atomicAdd(&H[((q0 + qe) * m + t.seg) * (L + 1) + l], v);
     }
 }
 
@@ -1033,6 +1048,21 @@ __global__ void cand_to_ids_kernel(const uint32_t* __restrict__ cand, int64_t ca
 
 // ---------------------------------------------------------------- launchers
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize raised as needed, per kernel,
+// device and thread (the attribute only grows).
+cudaError_t ensure_dyn_smem(const void* kern, size_t bytes) {
+    static thread_local std::unordered_map<const void*, std::pair<int, size_t>> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    auto& s = set[kern];
+    if (s.first == dev && s.second >= bytes) return cudaSuccess;
+    if (s.first != dev) s = {dev, 0};
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) s.second = bytes;
+    return e;
+}
+
 cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnorm,
                                   cudaStream_t st) {
     return launch("row_norm_bound", row_norm_bound_kernel, dim3((unsigned)ceil_div(nq * 32, 256)),
@@ -1044,18 +1074,15 @@ cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, i
                         int queries_per_block) {
     const int qb = queries_per_block;
     const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nq, qb));
-    const size_t smem = 16384 + 2 * sizeof(uint16_t) * (size_t)(L + 1) * qb;
+    const int sub = code_bytes == 4 ? 2 : 1;
+    const size_t smem = 16384 + sub * sizeof(uint16_t) * (size_t)(L + 1) * kHistThreads;
 #define NRLSH_HIST_(C_, Q_)                                                                     \
     {                                                                                       \
-        if (smem > 48 * 1024) {                                                             \
-            cudaError_t e = cudaFuncSetAttribute(hist_kernel<C_, Q_>,                       \
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                 (int)smem);                                \
-            if (e != cudaSuccess) return e;                                                 \
-        }                                                                                   \
+        cudaError_t e = ensure_dyn_smem((const void*)hist_kernel<C_, Q_>, smem);            \
+        if (e != cudaSuccess) return e;                                                     \
         return launch(sizeof(C_) == 4 ? "hist_u32" : "hist_u64", hist_kernel<C_, Q_>, grid,  \
-                      dim3(Q_), smem, st, (const C_*)codes, (const C_*)qcodes, nq, m, L, tiles, \
-                      H);                                                                   \
+                      dim3(kHistThreads), smem, st, (const C_*)codes, (const C_*)qcodes, nq, m, \
+                      L, tiles, H);                                                         \
     }
     if (code_bytes == 4) {
         if (qb == 32) NRLSH_HIST_(uint32_t, 32)
@@ -1120,21 +1147,6 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
     return launch("topk", topk_kernel<float>, dim3((unsigned)nq), dim3(256), smem, st, lo, hi, cand,
                   cap, bnd, k, ks, (const float*)Xp, dp, d, Q, xnorm, qnorm, perm, cont, cont_s,
                   out_ids, out_scores, out_ld);
-}
-
-// cudaFuncAttributeMaxDynamicSharedMemorySize raised as needed, per kernel,
-// device and thread (the attribute only grows).
-cudaError_t ensure_dyn_smem(const void* kern, size_t bytes) {
-    static thread_local std::unordered_map<const void*, std::pair<int, size_t>> set;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    auto& s = set[kern];
-    if (s.first == dev && s.second >= bytes) return cudaSuccess;
-    if (s.first != dev) s = {dev, 0};
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) s.second = bytes;
-    return e;
 }
 
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
