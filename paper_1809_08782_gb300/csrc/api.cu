@@ -590,20 +590,19 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
                              ix->ntiles, H, st));
         if (stage == Stage::Hist) continue;
         if (stage == Stage::TopK && !whole) {
-            // one fused launch: walk, selection, re-rank, exact top-k
-            uint32_t *cand, *cont;
-            float *lo, *hi;
-            double* cont_s;
-            NRLSH_CKS(sc.get(&cand, qc * cap));
-            NRLSH_CKS(sc.get(&lo, qc * cap));
-            NRLSH_CKS(sc.get(&hi, qc * cap));
-            NRLSH_CKS(sc.get(&cont, qc * cap));
-            NRLSH_CKS(sc.get(&cont_s, qc * cap));
-            NRLSH_CK(launch_probe_rerank(H, ix->order, ix->m, ix->L, n, ix->seg, qc, budget, nullptr, flags,
-                                         ix->codes, qcodes, ix->code_bytes, ix->Xp, ix->dtype,
-                                         ix->dp, ix->d, Qc, ix->xnorm, qnorm, ix->perm, k, nullptr,
-                                         cand, lo, hi, cont, cont_s, cap, o.ids + q0 * o.k_ld,
-                                         o.scores + q0 * o.k_ld, o.k_ld, st));
+            // one fused launch: walk, selection, re-rank, exact top-k, by CTAs that
+            // stay resident and take queries from a counter
+            const int ctas = probe_rerank_ctas(ix->dtype, ix->code_bytes, ix->dp, ix->m, qc);
+            uint32_t* slabs;
+            unsigned* work;
+            NRLSH_CKS(sc.get(&slabs, (size_t)ctas * 6 * cap));
+            NRLSH_CKS(sc.get(&work, 1));
+            NRLSH_CK(cudaMemsetAsync(work, 0, sizeof(unsigned), st));
+            NRLSH_CK(launch_probe_rerank_persistent(
+                H, ix->order, ix->m, ix->L, n, ix->seg, budget, nullptr, ix->codes, qcodes,
+                ix->code_bytes, ix->Xp, ix->dtype, ix->dp, ix->d, Qc, ix->xnorm, qnorm, ix->perm,
+                nullptr, k, slabs, cap, ctas, work, qc, o.ids + q0 * o.k_ld,
+                o.scores + q0 * o.k_ld, st));
             continue;
         }
         uint8_t* lam;
@@ -1142,7 +1141,8 @@ nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, cons
                              ix->ntiles, w.H, st, cfg.hist_qb));
         NRLSH_CK(cudaMemsetAsync(w.work, 0, sizeof(unsigned), st));
         NRLSH_CK(launch_probe_rerank_persistent(
-            w.H, ix->order, ix->m, ix->L, ix->n, ix->seg, budgets + q0, ix->codes, qcodes, ix->code_bytes,
+            w.H, ix->order, ix->m, ix->L, ix->n, ix->seg, 0, budgets + q0, ix->codes, qcodes,
+            ix->code_bytes,
             ix->Xp, ix->dtype, ix->dp, ix->d, Q + q0 * ix->d, ix->xnorm, w.qnorm + q0, ix->perm,
             ks + q0, k_max, w.slabs, cap, w.ctas, w.work, qc, ids + q0 * k_max,
             scores + q0 * k_max, st));

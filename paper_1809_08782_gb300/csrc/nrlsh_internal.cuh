@@ -222,9 +222,12 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
                                 const int32_t* ks, uint32_t* cand, float* lo, float* hi,
                                 uint32_t* cont, double* cont_s, int64_t cap, int64_t* out_ids,
                                 float* out_scores, int out_ld, cudaStream_t st);
-// Persistent batched form: `ctas` CTAs pull queries from *work (zeroed by the caller).
+// Persistent form: `ctas` CTAs pull queries from *work (zeroed by the caller).
+// budgets/ks may be null: then every query uses budget / k_max.  ctas <= 0: as many
+// CTAs as fit on the device at once.  slabs: ctas x 6 cap words.
 cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
-                                           int64_t n, const int64_t* seg, const int64_t* budgets, const void* codes,
+                                           int64_t n, const int64_t* seg, int64_t budget,
+                                           const int64_t* budgets, const void* codes,
                                            const void* qcodes, int code_bytes, const void* Xp,
                                            nrlsh_dtype dt, int dp, int d, const float* Q,
                                            const float* xnorm, const float* qnorm,
@@ -254,6 +257,8 @@ cudaError_t launch_rerank_work(const void* Xp, nrlsh_dtype dt, int dp, int d, co
                                int64_t nq, const uint32_t* cand, int64_t cap, const Boundary* bnd,
                                int64_t* work_off, unsigned long long* work_ctr, const float* xnorm,
                                const float* qnorm, float* lo, float* hi, cudaStream_t st);
+// CTAs of the persistent re-rank kernel resident at once (at most nq).
+int probe_rerank_ctas(nrlsh_dtype dt, int code_bytes, int dp, int m, int64_t nq);
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
                                const uint32_t* perm, int64_t nq, int32_t* out, int64_t out_cap,
                                int64_t* count, cudaStream_t st);

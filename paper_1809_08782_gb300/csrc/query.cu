@@ -404,16 +404,25 @@ __device__ void dev_rerank(const T* __restrict__ Xp, int dp, const float* qs,
                            const float* __restrict__ xnorm, float qn, float kappa,
                            float* __restrict__ loq, float* __restrict__ hiq) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    for (int64_t i = i0 + (int64_t)warp * kRerankUnroll; i < i1;
-         i += (int64_t)nwarps * kRerankUnroll) {
+    const int64_t stride = (int64_t)(blockDim.x >> 5) * kRerankUnroll;
+    int64_t i = i0 + (int64_t)warp * kRerankUnroll;
+    // candidate positions one iteration ahead, so a row's address never waits
+    uint32_t ps[kRerankUnroll];
+#pragma unroll
+    for (int u = 0; u < kRerankUnroll; ++u) ps[u] = i < i1 ? candq[min(i + u, i1 - 1)] : 0u;
+    for (; i < i1; i += stride) {
         const T* rows[kRerankUnroll];
-        uint32_t ps[kRerankUnroll];
+        float xn[kRerankUnroll];
 #pragma unroll
         for (int u = 0; u < kRerankUnroll; ++u) {
-            ps[u] = candq[min(i + u, i1 - 1)];
             rows[u] = Xp + (int64_t)ps[u] * dp;
+            xn[u] = xnorm[ps[u]];
         }
+        const int64_t inext = i + stride;
+        uint32_t nps[kRerankUnroll];
+#pragma unroll
+        for (int u = 0; u < kRerankUnroll; ++u)
+            nps[u] = inext < i1 ? candq[min(inext + u, i1 - 1)] : 0u;
         float acc[kRerankUnroll];
 #pragma unroll
         for (int u = 0; u < kRerankUnroll; ++u) acc[u] = 0.0f;
@@ -437,11 +446,13 @@ __device__ void dev_rerank(const T* __restrict__ Xp, int dp, const float* qs,
         const int r = lane >> 3;
         if ((lane & 7) == 0 && i + r < i1) {
             const float sc = acc[0];
-            const uint32_t pr = r == 0 ? ps[0] : r == 1 ? ps[1] : r == 2 ? ps[2] : ps[3];
-            const float e = __fmul_ru(__fmul_ru(kappa, qn), xnorm[pr]);
+            const float xr = r == 0 ? xn[0] : r == 1 ? xn[1] : r == 2 ? xn[2] : xn[3];
+            const float e = __fmul_ru(__fmul_ru(kappa, qn), xr);
             loq[i + r] = __fsub_rd(sc, e);
             hiq[i + r] = __fadd_ru(sc, e);
         }
+#pragma unroll
+        for (int u = 0; u < kRerankUnroll; ++u) ps[u] = nps[u];
     }
 }
 
@@ -522,6 +533,87 @@ __device__ void select_digit(const uint32_t* hist, int rem, int* dg_out, int* re
 constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
 constexpr int kDot2Max = 512;        // contenders scored by the compensated FP32 tier
 
+// One lane's part of the compensated dot product (Ogita, Rump, Oishi 2005):
+// TwoProduct by fma and TwoSum for each of its terms in order; terms are taken
+// lane-strided in groups of 4 (fp32, one 16-byte load) or 8 (bf16).
+__device__ __forceinline__ void dot2_step(float x, float y, float& sh, float& sl) {
+    const float pr = __fmul_rn(x, y);
+    const float er = fmaf(x, y, -pr);            // pr + er = x y exactly
+    const float s2 = __fadd_rn(sh, pr);          // TwoSum(sh, pr)
+    const float bb = __fsub_rn(s2, sh);
+    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));
+    sh = s2;
+    sl = __fadd_rn(__fadd_rn(sl, t), er);
+}
+template <typename T> struct RowDot2;
+template <> struct RowDot2<float> {
+    __device__ static void dot(const float* xr, const float* qs, int dp, int lane, float& sh,
+                               float& sl) {
+        const float4* x4 = (const float4*)xr;
+        const float4* q4 = (const float4*)qs;
+#pragma unroll 4
+        for (int c = lane; c < dp / 4; c += 32) {
+            const float4 x = x4[c], y = q4[c];
+            dot2_step(x.x, y.x, sh, sl);
+            dot2_step(x.y, y.y, sh, sl);
+            dot2_step(x.z, y.z, sh, sl);
+            dot2_step(x.w, y.w, sh, sl);
+        }
+    }
+};
+template <> struct RowDot2<__nv_bfloat16> {
+    __device__ static void dot(const __nv_bfloat16* xr, const float* qs, int dp, int lane,
+                               float& sh, float& sl) {
+#pragma unroll 2
+        for (int c = lane; c < dp / 8; c += 32) {
+            const uint4 raw = ((const uint4*)xr)[c];
+            const __nv_bfloat162* h = (const __nv_bfloat162*)&raw;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 x = __bfloat1622float2(h[i]);
+                dot2_step(x.x, qs[c * 8 + 2 * i], sh, sl);
+                dot2_step(x.y, qs[c * 8 + 2 * i + 1], sh, sl);
+            }
+        }
+    }
+};
+
+// FP64 dot product of one stored row with the query (both zero-padded to dp, a
+// multiple of 8): lane-strided over float4 / 8 x bf16 groups, exact products,
+// returns the lane's sum and its sum of magnitudes.
+template <typename T> struct RowDot64;
+template <> struct RowDot64<float> {
+    __device__ static void dot(const float* xr, const float* qs, int dp, int lane, double& sd,
+                               double& sa) {
+        const float4* x4 = (const float4*)xr;
+        const float4* q4 = (const float4*)qs;
+        for (int c = lane; c < dp / 4; c += 32) {
+            const float4 x = x4[c], y = q4[c];
+            const double p0 = (double)x.x * y.x, p1 = (double)x.y * y.y;
+            const double p2 = (double)x.z * y.z, p3 = (double)x.w * y.w;
+            sd += p0; sd += p1; sd += p2; sd += p3;
+            sa += fabs(p0) + fabs(p1) + fabs(p2) + fabs(p3);
+        }
+    }
+};
+template <> struct RowDot64<__nv_bfloat16> {
+    __device__ static void dot(const __nv_bfloat16* xr, const float* qs, int dp, int lane,
+                               double& sd, double& sa) {
+        for (int c = lane; c < dp / 8; c += 32) {
+            const uint4 raw = ((const uint4*)xr)[c];
+            const __nv_bfloat162* h = (const __nv_bfloat162*)&raw;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 x = __bfloat1622float2(h[i]);
+                const double p0 = (double)x.x * qs[c * 8 + 2 * i];
+                const double p1 = (double)x.y * qs[c * 8 + 2 * i + 1];
+                sd += p0; sd += p1;
+                sa += fabs(p0) + fabs(p1);
+            }
+        }
+    }
+};
+
 // Block phase (256 threads), one query.  tau = k-th largest lower bound (MSD
 // radix select on the order-preserving integer image of the floats).  Every
 // candidate whose upper bound reaches tau is a contender; any true top-k member
@@ -545,8 +637,8 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __shared__ int64_t bid_s[8];
     __shared__ int bc_s[8];
     __shared__ double rank_lo[kDot2Max], rank_hi[kDot2Max];
-    __shared__ uint16_t flagged[kDot2Max];
-    __shared__ uint32_t nflag_s;
+    __shared__ uint16_t flagged[kDot2Max], flagged2[kDot2Max];
+    __shared__ uint32_t nflag_s, nflag2_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     float tau = -FLT_MAX;
@@ -587,27 +679,17 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     if (nc <= (uint32_t)kDot2Max) {
         // Compensated FP32 tier (Ogita, Rump, Oishi, "Accurate sum and dot product",
         // 2005): a warp per contender, TwoProduct by fma and TwoSum per lane, the
-        // same transformations across lanes.  With m = ceil(dp/32) terms per lane
-        // and 5 tree levels, |hi + lo - q^T x| <= u^2 (2m(m+1) + 10(dp+32)) sum|q x|,
+        // same transformations across lanes.  With m terms per lane (mlane) and 5
+        // tree levels, |hi + lo - q^T x| <= u^2 (2m(m+1) + 10(dp+32)) sum|q x|,
         // u = 2^-24; the bound below takes 4x that, plus the FP64 rounding of the
         // canonical in-order sum ((d+2) 2^-53 sum|q x|) and of hi + lo.
-        const int mlane = (dp + 31) / 32;
+        const int mlane = sizeof(T) == 4 ? 4 * ((dp / 4 + 31) / 32) : 8 * ((dp / 8 + 31) / 32);
         const double c2 = 4.0 * 0x1p-48 * (2.0 * mlane * (mlane + 1) + 10.0 * (dp + 32)) +
                           (double)(d + 2) * 0x1p-53;
         for (uint32_t c = warp; c < nc; c += 8) {
             const uint32_t pos = candq[contq[c]];
-            const T* xr = Xp + (int64_t)pos * dp;
             float sh = 0.0f, sl = 0.0f;
-            for (int k = lane; k < dp; k += 32) {
-                const float x = to_f32(xr[k]), y = qs[k];
-                const float pr = __fmul_rn(x, y);
-                const float er = fmaf(x, y, -pr);            // pr + er = x y exactly
-                const float s2 = __fadd_rn(sh, pr);          // TwoSum(sh, pr)
-                const float bb = __fsub_rn(s2, sh);
-                const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));
-                sh = s2;
-                sl = __fadd_rn(__fadd_rn(sl, t), er);
-            }
+            RowDot2<T>::dot(Xp + (int64_t)pos * dp, qs, dp, lane, sh, sl);
             for (int o = 16; o; o >>= 1) {
                 const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
                 const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
@@ -639,7 +721,50 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
             if (flag) flagged[atomicAdd(&nflag_s, 1u)] = (uint16_t)c;
         }
         __syncthreads();
-        const uint32_t nf = nflag_s;
+        uint32_t nf = nflag_s;
+        if (nf) {
+            // FP64 warp tier for the flagged: exact products summed lane-strided
+            // (per_lane terms per lane) and by a 5-level tree, at most per_lane + 5
+            // rounded additions deep; the canonical in-order sum is within (d - 1) u
+            // sum|q x| of the exact value, u = 2^-53, so an interval of
+            // (d + per_lane + 8) u sum|q x| (1 + 2^-30) each side holds it.  Each
+            // interval is narrowed to its intersection with the FP32 one.
+            const int per_lane = sizeof(T) == 4 ? 4 * ((dp / 4 + 31) / 32) : 8 * ((dp / 8 + 31) / 32);
+            const double cw = (double)(d + per_lane + 8) * 0x1p-53 * (1.0 + 0x1p-30);
+            for (uint32_t f = warp; f < nf; f += 8) {
+                const uint32_t c = flagged[f];
+                double sd = 0.0, sa = 0.0;
+                RowDot64<T>::dot(Xp + (int64_t)candq[contq[c]] * dp, qs, dp, lane, sd, sa);
+                for (int o = 16; o; o >>= 1) {
+                    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                }
+                if (lane == 0) {
+                    const double e = __dmul_ru(cw, sa);
+                    rank_lo[c] = fmax(rank_lo[c], __dsub_rd(sd, e));
+                    rank_hi[c] = fmin(rank_hi[c], __dadd_ru(sd, e));
+                    contsq[c] = sd;
+                }
+            }
+            __syncthreads();
+            // still undecided: the interval straddles an fp32 rounding boundary or
+            // overlaps another contender's (intervals only shrank, so contenders not
+            // flagged before stay decided)
+            if (threadIdx.x == 0) nflag2_s = 0;
+            __syncthreads();
+            for (uint32_t f = threadIdx.x; f < nf; f += 256) {
+                const uint32_t c = flagged[f];
+                const double lo_c = rank_lo[c], hi_c = rank_hi[c];
+                bool flag = __double2float_rn(lo_c) != __double2float_rn(hi_c);
+                for (uint32_t c1 = 0; c1 < nc && !flag; ++c1)
+                    flag = c1 != c && rank_lo[c1] <= hi_c && lo_c <= rank_hi[c1];
+                if (flag) flagged2[atomicAdd(&nflag2_s, 1u)] = (uint16_t)c;
+            }
+            __syncthreads();
+            nf = nflag2_s;
+            for (uint32_t f = threadIdx.x; f < nf; f += 256) flagged[f] = flagged2[f];
+            __syncthreads();
+        }
         for (uint32_t f0 = 0; f0 < nf; f0 += rb) {
             const int nr = (int)min((uint32_t)rb, nf - f0);
             for (int i = threadIdx.x; i < nr * dp; i += 256) {
@@ -774,7 +899,7 @@ __global__ void __launch_bounds__(256)
 // re-rank and the exact top-k back to back, with the query, lam and the walk's
 // scratch in shared memory (dynamic: dp floats, m words, m bytes).
 template <typename T, typename C>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     probe_rerank_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order, int m,
                         int L, int64_t n, const int64_t* __restrict__ seg, int64_t budget, const int64_t* __restrict__ budgets,
                         uint32_t flags, const C* __restrict__ codes, const C* __restrict__ qcodes,
@@ -809,10 +934,10 @@ __global__ void __launch_bounds__(256)
 // cont_s: cap doubles).  Per-query budgets and k; rows of the outputs are k_max
 // wide, padded with (-1, -inf).
 template <typename T, typename C>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     probe_rerank_persistent_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order,
                                    int m, int L, int64_t n, const int64_t* __restrict__ seg,
-                                   const int64_t* __restrict__ budgets,
+                                   int64_t budget, const int64_t* __restrict__ budgets,
                                    const C* __restrict__ codes, const C* __restrict__ qcodes,
                                    const T* __restrict__ Xp, int dp, int d,
                                    const float* __restrict__ Q, const float* __restrict__ xnorm,
@@ -839,14 +964,15 @@ __global__ void __launch_bounds__(256)
         const int64_t q = q_s;
         if (q >= nq) break;
         load_query(Q, q, d, dp, qs);
-        const int64_t Bq = min(max(budgets[q], (int64_t)1), cap);
+        const int64_t Bq = min(max(budgets ? budgets[q] : budget, (int64_t)1), cap);
         const Boundary b = dev_threshold(H + q * m * (L + 1), order, m, L, n, Bq, 0u, cntj, lam_s);
         dev_select(codes, qcodes[q], seg, m, L, lam_s, b, cand, (uint32_t*)phase_s);
         __syncthreads();
         const int64_t count = (int64_t)b.full + b.r;
         dev_rerank(Xp, dp, qs, cand, 0, count, xnorm, qnorm[q], kappa, lo, hi);
         __syncthreads();
-        dev_topk(lo, hi, cand, count, min(max(ks[q], 1), k_max), k_max, Xp, dp, d, qs, qnorm[q],
+        dev_topk(lo, hi, cand, count, ks ? min(max(ks[q], 1), k_max) : k_max, k_max, Xp, dp, d,
+                 qs, qnorm[q],
                  xnorm, perm, cont, cont_s,
                  out_ids + q * k_max, out_scores + q * k_max, phase_s);
     }
@@ -1063,6 +1189,17 @@ cudaError_t ensure_dyn_smem(const void* kern, size_t bytes) {
     return e;
 }
 
+// CTAs of 256 threads that fit on the device at once (at most nq).
+cudaError_t resident_ctas(const void* kern, size_t smem, int64_t nq, int* ctas) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    *ctas = (int)std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)std::max(per_sm, 1) * sms));
+    return cudaSuccess;
+}
+
 cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnorm,
                                   cudaStream_t st) {
     return launch("row_norm_bound", row_norm_bound_kernel, dim3((unsigned)ceil_div(nq * 32, 256)),
@@ -1181,7 +1318,8 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
 }
 
 cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
-                                           int64_t n, const int64_t* seg, const int64_t* budgets,
+                                           int64_t n, const int64_t* seg, int64_t budget,
+                                           const int64_t* budgets,
                                            const void* codes, const void* qcodes, int code_bytes,
                                            const void* Xp, nrlsh_dtype dt, int dp, int d,
                                            const float* Q, const float* xnorm, const float* qnorm,
@@ -1196,8 +1334,13 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
         auto kern = probe_rerank_persistent_kernel<T_, C_>;                                     \
         cudaError_t e = ensure_dyn_smem((const void*)kern, smem);                               \
         if (e != cudaSuccess) return e;                                                         \
+        if (ctas <= 0) {                                                                        \
+            e = resident_ctas((const void*)kern, smem, nq, &ctas);                              \
+            if (e != cudaSuccess) return e;                                                     \
+        }                                                                                       \
         return launch(NAME, kern, dim3((unsigned)ctas), dim3(256), smem, st, H, order, m, L, n,  \
-                      seg, budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, d, Q,    \
+                      seg, budget, budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, \
+                      d, Q,                                                                     \
                       xnorm, qnorm, kappa, perm, ks, k_max, slabs, cap, work, nq, out_ids,      \
                       out_scores);                                                              \
     }
@@ -1268,6 +1411,20 @@ cudaError_t launch_rerank_work(const void* Xp, nrlsh_dtype dt, int dp, int d, co
     return launch("rerank_work", rerank_work_kernel<float>, grid, dim3(kRerankWarps * 32), smem, st,
                   (const float*)Xp, dp, d, Q, cand, cap, bnd, (const int64_t*)work_off, nq,
                   work_ctr, xnorm, qnorm, kappa, lo, hi);
+}
+
+int probe_rerank_ctas(nrlsh_dtype dt, int code_bytes, int dp, int m, int64_t nq) {
+    const size_t smem = sizeof(float) * (size_t)dp + (sizeof(uint32_t) + 1) * (size_t)m;
+    const void* kern =
+        dt == NRLSH_BF16
+            ? (code_bytes == 4 ? (const void*)probe_rerank_persistent_kernel<__nv_bfloat16, uint32_t>
+                               : (const void*)probe_rerank_persistent_kernel<__nv_bfloat16, uint64_t>)
+            : (code_bytes == 4 ? (const void*)probe_rerank_persistent_kernel<float, uint32_t>
+                               : (const void*)probe_rerank_persistent_kernel<float, uint64_t>);
+    int ctas = 1;
+    if (ensure_dyn_smem(kern, smem) != cudaSuccess || resident_ctas(kern, smem, nq, &ctas) != cudaSuccess)
+        return (int)std::max<int64_t>(1, std::min<int64_t>(nq, 152));
+    return ctas;
 }
 
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
