@@ -5,9 +5,8 @@ that decides an integer (a code bit, a bucket order, a top-k order) is computed
 in FP64 in a fixed order, which the CUDA library's last precision tier also
 uses, so the two must agree bit for bit:
 
-* s_x = ||x||^2: FP64 sum of x_k * x_k for k = 0, 1, ..., d-1 in that order.  For
-  fp32/bf16 items every product is exact in FP64, so fused multiply-adds give
-  the same value.                                           (Algorithm 1)
+* s_x = ||x||^2: the exact sum of the x_k * x_k (each exact in FP64 for fp32/bf16
+  items) rounded once to FP64, round-to-nearest-even.       (Algorithm 1)
 * partition: rank items by (s_x, id) ascending (ties broken by id, one valid
   way to "break ties arbitrarily"); sub-dataset j holds ranks
   [floor(j n / m), floor((j+1) n / m)).  U_j^2 = max s_x over S_j.
@@ -45,13 +44,14 @@ from . import philox
 # ---------------------------------------------------------------- index build
 
 def sq_norms(X: np.ndarray) -> np.ndarray:
-    """s_x = ||x||^2, summed over k = 0..d-1 in order (Algorithm 1, "rank the items
-    according to their 2-norms": s_x orders items exactly as ||x|| does)."""
+    """s_x = ||x||^2 correctly rounded to FP64 (Algorithm 1, "rank the items
+    according to their 2-norms": s_x orders items exactly as ||x|| does).  Every
+    x_k^2 of an fp32/bf16 value is exact in FP64; math.fsum returns their sum
+    rounded once, so s_x does not depend on a summation order."""
+    import math
     X = np.asarray(X, dtype=np.float64)
-    s = np.zeros(X.shape[0], dtype=np.float64)
-    for k in range(X.shape[1]):
-        s = s + X[:, k] * X[:, k]
-    return s
+    sq = X * X
+    return np.array([math.fsum(row) for row in sq.tolist()], dtype=np.float64)
 
 
 def percentile_bounds(n: int, m: int) -> list:

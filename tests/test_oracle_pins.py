@@ -82,14 +82,43 @@ def test_projection_entries_are_standard_normal():
 
 # -------------------------------------------------------------- Algorithm 1
 
-def test_sq_norms_against_fsum_and_exact_integers():
-    X = rand_items(200, 37, 3)
+def test_sq_norms_are_the_exact_sum_rounded_once():
+    """Against exact rational arithmetic (Fraction sums, converted by Python's
+    correctly rounded int/int division), integer rows, and order independence."""
+    X = rand_items(60, 37, 3)
     s = O.sq_norms(X)
-    for i in range(0, 200, 17):
-        ref = math.fsum(float(v) * float(v) for v in X[i])
-        assert abs(s[i] - ref) <= 37 * 2.0 ** -53 * ref
+    for i in range(60):
+        exact = sum((Fraction(float(v)) ** 2 for v in X[i]), Fraction(0))
+        assert s[i] == float(exact)
+    rng = np.random.default_rng(4)
+    for i in range(0, 60, 7):
+        perm = rng.permutation(37)
+        assert O.sq_norms(X[i:i + 1, perm])[0] == s[i]
     Xi = np.array([[1.0, 2.0, 3.0], [0.0, 0.0, 0.0], [-4.0, 0.5, 0.25]])
     assert list(O.sq_norms(Xi)) == [14.0, 0.0, 16.3125]
+
+
+def squares_near_a_tie(t: int):
+    """A row whose exact ||x||^2 is 1 + 2^-53 - 2^-106 + t 2^-108: the in-range
+    part sits one 2^-106 unit below the half-way point between 1 and 1 + 2^-52,
+    and t squares of 2^-54 (2^-108 each) decide the rounding: t < 4 rounds down,
+    t = 4 is an exact tie (to even, 1.0), t > 4 rounds up.  The terms:
+    (11863283 2^-50)^2 = 2^-53 - 4817239 2^-100, and 17558, 141, 7, 1 times
+    2^-53 squared make up 4817239 2^-100 - 2^-106 exactly."""
+    row = [1.0, 11863283 * 2.0 ** -50, 17558 * 2.0 ** -53, 141 * 2.0 ** -53,
+           7 * 2.0 ** -53, 1 * 2.0 ** -53] + [2.0 ** -54] * t
+    return np.array(row, dtype=np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("t,expected", [(0, 1.0), (3, 1.0), (4, 1.0), (5, 1.0 + 2.0 ** -52),
+                                        (9, 1.0 + 2.0 ** -52)])
+def test_sq_norms_ties_and_far_below_terms(t, expected):
+    row = squares_near_a_tie(t)
+    exact = sum((Fraction(float(v)) ** 2 for v in row), Fraction(0))
+    assert exact == 1 + Fraction(1, 2 ** 53) - Fraction(1, 2 ** 106) + t * Fraction(1, 2 ** 108)
+    assert O.sq_norms(row[None, :])[0] == expected == float(exact)
+    rng = np.random.default_rng(t)
+    assert O.sq_norms(row[None, rng.permutation(row.size)])[0] == expected
 
 
 @pytest.mark.parametrize("n,m", [(1, 1), (7, 3), (10, 10), (33, 4), (64, 5)])
