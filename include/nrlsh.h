@@ -14,7 +14,7 @@
  *
  * Determinism.  Every floating-point value that decides an integer result is
  * fixed by a rule, so results are a deterministic function of the inputs:
- *   - squared norms s_x: FP64 sum of x_k^2 over k = 0..d-1 in order;
+ *   - squared norms s_x: the exact sum of the x_k^2 rounded once to FP64;
  *   - ranking for the partition: (s_x, id) ascending; sub-dataset j holds ranks
  *     [floor(j n / m), floor((j+1) n / m)); U_j^2 = max s_x in S_j;
  *   - code bit b of x in S_j: [fl(sum_k a_{k,b} x_k + fl(a_{d,b} tau_x)) >= 0] in
@@ -127,7 +127,7 @@ typedef struct nrlsh_info {
     int32_t projection;          /* nrlsh_projection used (SIMT or TENSOR) */
     int32_t device_error;        /* nonzero: a bounded device wait ran out during the build */
     int32_t partition;           /* nrlsh_partition used */
-    int32_t reserved;
+    int32_t norm_fallbacks;      /* rows whose squared norm needed the exact slow path */
 } nrlsh_info;
 
 /*

@@ -58,6 +58,7 @@ struct nrlsh_index {
     nrlsh::PosTile* tiles = nullptr;
     int32_t ntiles = 0;
     unsigned* ambiguous = nullptr;  // (item, bit) pairs the first tier left undecided
+    unsigned* norm_fb = nullptr;    // rows whose squared norm took the exact slow path
     int projection = NRLSH_PROJECT_SIMT;
     __nv_bfloat16* At = nullptr;     // A^T in bf16, 64 x dp (tensor-core B operand)
     float* At32 = nullptr;           // A^T in fp32, the warp-per-row projection's layout
@@ -378,6 +379,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         c.take(&ix->shat_sorted, ix->ncls);
         c.take(&ix->ccos, L + 1);
         c.take(&ix->ambiguous, 1);
+        c.take(&ix->norm_fb, 1);
         c.take(&ix->dev_err, 1);
         c.take(&ix->tiles, (size_t)ix->ntiles);
         if (warp_proj_stride(d, ix->Lp) > 0) c.take(&ix->At32, warp_proj_at_floats(d, ix->Lp));
@@ -433,6 +435,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(cudaMemsetAsync(ix->dev_err, 0, sizeof(int), st));
 
         B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned), st));
+        B_CU(cudaMemsetAsync(ix->norm_fb, 0, sizeof(unsigned), st));
         B_CU(cudaMemsetAsync(ix->U2, 0, sizeof(double) * m, st));
         // A and the tiles of its columns (Eq. 4 projections)
         // A and the bucket cosines depend only on (seed, d, L, eps): a side stream
@@ -452,12 +455,12 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         const bool small = !uniform && small_rank_supported(n, m);
         if (small) {
             // Algorithm 1 for small inputs: tile sort, rank, per-range id sort
-            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
+            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, ix->norm_fb, st));
             B_CU(launch_small_rank(keys, vals, n, m, sort_tmp, ix->perm, ix->sub_of_id, ix->U2,
                                    st));
         } else if (!uniform) {
             // Algorithm 1: rank by norm, percentile partition, U_j
-            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, st));
+            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, ix->norm_fb, st));
             B_CU(radix_sort_u64(keys, vals, keys_alt, vals_alt, n, 64, sort_tmp, &alt, st));
             // storage order: stable sort of ids by sub-dataset
             jv = alt ? vals : vals_alt;       // the pair the sort did not end in
@@ -466,7 +469,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                        ix->sub_of_id, ix->U2, jkeys, jv, st));
         } else {
             // Section 5: uniform norm ranges, then the same stable sort by sub-dataset
-            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, nullptr, nullptr, st));
+            B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, nullptr, nullptr, ix->norm_fb, st));
             jv = vals;
             jv_alt = vals_alt;
             B_CU(launch_uniform_assign(ix->s_id, n, m, (unsigned long long*)keys_alt, ix->sub_of_id,
@@ -1006,7 +1009,9 @@ NRLSH_API nrlsh_status nrlsh_get_info(const nrlsh_index* ix, nrlsh_info* info) {
     info->projection = ix->projection;
     info->device_error = derr;
     info->partition = ix->partition;
-    info->reserved = 0;
+    unsigned nfb = 0;
+    NRLSH_CK(cudaMemcpy(&nfb, ix->norm_fb, sizeof(nfb), cudaMemcpyDeviceToHost));
+    info->norm_fallbacks = (int32_t)nfb;
     return NRLSH_OK;
 }
 

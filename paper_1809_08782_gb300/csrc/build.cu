@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 
 namespace nrlsh {
 
@@ -100,143 +101,230 @@ cudaError_t launch_projections(float* A, float* A_pad, float* anorm, __nv_bfloat
 }
 
 // =====================================================================
-// Squared norms: one thread per row, rows staged through shared memory so the
-// global loads are coalesced; FP64 accumulation in column order.
+// Squared norms: s_x = sum_k x_k^2 exactly, rounded once to FP64.  A warp per
+// row; every x_k = M 2^E (M < 2^24) has x_k^2 = M^2 2^2E exactly.  The lanes
+// add their terms into a 128-bit integer window [W0, W0 + 128) placed under the
+// row's largest term with bitlen(d) + 1 bits of headroom, so at least 53 bits
+// lie below the result's rounding bit inside the window; bits of terms below
+// W0 are dropped and noted.  The dropped total is less than d units of 2^W0, so
+// it can change the rounding only if the kept remainder lies within d units
+// below the half-way point; such a row (none in practice; constructed tests
+// have them) is summed again exactly in a 576-bit accumulator by one lane.
 // =====================================================================
 
 namespace {
 
-// The squared norm's IEEE bits order like the value (s >= 0, -0 folded to +0):
-// they are the partition's sort key, with the id as value.
-__device__ __forceinline__ void store_norm(int64_t row, double acc, double* s, uint64_t* keys,
-                                           uint32_t* vals) {
-    s[row] = acc;
-    if (keys) {
-        keys[row] = (uint64_t)__double_as_longlong(acc + 0.0);
-        vals[row] = (uint32_t)row;
-    }
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ void f32_fields(float x, uint64_t& M2, int& E2) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xFFu, f = u & 0x7FFFFFu;
+    const uint64_t M = e ? (f | 0x800000u) : f;
+    M2 = M * M;                              // < 2^48
+    E2 = 2 * (e ? (int)e - 150 : -149);      // x^2 = M2 2^E2
 }
 
+__device__ __forceinline__ int bitlen64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
+
+// The exact sum of the row's squares in 9 words (bit i of the array has weight
+// 2^(i - 298)), rounded to nearest even.  Slow; for ambiguous rows only.
 template <typename T>
-__global__ void __launch_bounds__(128) sqnorm_kernel(const T* __restrict__ X, int64_t n, int d,
-                                                     int64_t ld, double* __restrict__ s,
-                                                     uint64_t* keys, uint32_t* vals) {
-    __shared__ float tile[128][33];
-    const int64_t row0 = (int64_t)blockIdx.x * 128;
-    double acc = 0.0;
-    for (int c0 = 0; c0 < d; c0 += 32) {
-        for (int i = threadIdx.x; i < 128 * 32; i += 128) {
-            const int r = i >> 5, c = i & 31;
-            const int64_t row = row0 + r;
-            const int col = c0 + c;
-            tile[r][c] = (row < n && col < d) ? to_f32(X[row * ld + col]) : 0.0f;
+__device__ double sqnorm_exact_slow(const T* __restrict__ xr, int d) {
+    uint64_t w[9];
+    for (int i = 0; i < 9; ++i) w[i] = 0;
+    for (int k = 0; k < d; ++k) {
+        uint64_t M2;
+        int E2;
+        f32_fields(to_f32(xr[k]), M2, E2);
+        if (!M2) continue;
+        const int off = E2 + 298, wi = off >> 6, b = off & 63;
+        uint64_t add_lo = M2 << b, add_hi = b ? (M2 >> (64 - b)) : 0;
+        uint64_t old = w[wi];
+        w[wi] += add_lo;
+        uint64_t carry = w[wi] < old;
+        for (int j = wi + 1; j < 9 && (add_hi | carry); ++j) {
+            old = w[j];
+            w[j] += add_hi + carry;
+            carry = (w[j] < old) || (carry && add_hi == ~0ull);
+            add_hi = 0;
         }
-        __syncthreads();
-        const int cmax = min(32, d - c0);
-        for (int c = 0; c < cmax; ++c) {
-            const double v = (double)tile[threadIdx.x][c];
-            acc = fma(v, v, acc);  // v*v is exact in FP64: same as add after multiply
-        }
-        __syncthreads();
     }
-    const int64_t row = row0 + threadIdx.x;
-    if (row < n) store_norm(row, acc, s, keys, vals);
+    int top = -1;
+    for (int j = 8; j >= 0 && top < 0; --j)
+        if (w[j]) top = 64 * j + 63 - __clzll((long long)w[j]);
+    if (top < 0) return 0.0;
+    auto bit = [&](int i) -> uint64_t { return i < 0 ? 0 : (w[i >> 6] >> (i & 63)) & 1ull; };
+    uint64_t mant = 0;
+    for (int i = top; i > top - 53; --i) mant = (mant << 1) | bit(i);
+    const uint64_t rb = bit(top - 53);
+    bool sticky = false;
+    for (int i = top - 54; i >= 0 && !sticky; --i)
+        if ((i & 63) == 63 && !w[i >> 6]) i -= 63; else sticky = bit(i) != 0;
+    int ex = top - 298;                      // value in [2^ex, 2^(ex+1))
+    if (rb && (sticky || (mant & 1))) {
+        if (++mant == (1ull << 53)) {
+            mant >>= 1;
+            ++ex;
+        }
+    }
+    return __longlong_as_double((long long)(((uint64_t)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1))));
 }
 
-// Same sums for fp32 rows with d % 4 == 0 (16-byte aligned rows): the tile is
-// loaded with float4 and the next 32-column chunk is prefetched into registers
-// while the current one is summed.
-__global__ void __launch_bounds__(128) sqnorm_f32v4_kernel(const float* __restrict__ X, int64_t n,
-                                                           int d, double* __restrict__ s,
-                                                           uint64_t* keys, uint32_t* vals) {
-    __shared__ float tile[128][33];
-    const int64_t row0 = (int64_t)blockIdx.x * 128;
-    const int d4 = d / 4;
-    float4 pre[8];
-    auto fetch = [&](int c0) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = threadIdx.x + 128 * u;  // 1024 float4 per 128 x 32 chunk
-            const int r = i >> 3, c4 = (c0 >> 2) + (i & 7);
-            const int64_t row = row0 + r;
-            pre[u] = (row < n && c4 < d4) ? ((const float4*)(X + row * d))[c4]
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    double acc = 0.0;
-    fetch(0);
-    for (int c0 = 0; c0 < d; c0 += 32) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = threadIdx.x + 128 * u;
-            const int r = i >> 3, c = (i & 7) * 4;
-            tile[r][c] = pre[u].x;
-            tile[r][c + 1] = pre[u].y;
-            tile[r][c + 2] = pre[u].z;
-            tile[r][c + 3] = pre[u].w;
-        }
-        __syncthreads();
-        if (c0 + 32 < d) fetch(c0 + 32);
-        const int cmax = min(32, d - c0);
-        for (int c = 0; c < cmax; ++c) {
-            const double v = (double)tile[threadIdx.x][c];
-            acc = fma(v, v, acc);
-        }
-        __syncthreads();
+// The row's elements as lane-strided groups of VEC consecutive values (one
+// vector load each when VEC > 1).
+template <typename T, int VEC>
+struct RowGroups;
+template <typename T>
+struct RowGroups<T, 1> {
+    static constexpr int kVec = 1;
+    __device__ static void load(const T* xr, int g, float (&v)[1]) { v[0] = to_f32(xr[g]); }
+};
+template <>
+struct RowGroups<float, 4> {
+    static constexpr int kVec = 4;
+    __device__ static void load(const float* xr, int g, float (&v)[4]) {
+        const float4 f = ((const float4*)xr)[g];
+        v[0] = f.x;
+        v[1] = f.y;
+        v[2] = f.z;
+        v[3] = f.w;
     }
-    const int64_t row = row0 + threadIdx.x;
-    if (row < n) store_norm(row, acc, s, keys, vals);
-}
+};
+template <>
+struct RowGroups<__nv_bfloat16, 4> {
+    static constexpr int kVec = 4;
+    __device__ static void load(const __nv_bfloat16* xr, int g, float (&v)[4]) {
+        const uint2 raw = ((const uint2*)xr)[g];
+        const float2 a = __bfloat1622float2(*(const __nv_bfloat162*)&raw.x);
+        const float2 b = __bfloat1622float2(*(const __nv_bfloat162*)&raw.y);
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+    }
+};
 
-// Same sums for bf16 rows with d and the row stride even (4-byte aligned rows):
-// the tile is loaded two elements per 32-bit load.
-__global__ void __launch_bounds__(128) sqnorm_bf16x2_kernel(const __nv_bfloat16* __restrict__ X,
-                                                            int64_t n, int d, int64_t ld,
-                                                            double* __restrict__ s, uint64_t* keys,
-                                                            uint32_t* vals) {
-    __shared__ float tile[128][33];
-    const int64_t row0 = (int64_t)blockIdx.x * 128;
-    const int d2 = d / 2;
-    double acc = 0.0;
-    for (int c0 = 0; c0 < d; c0 += 32) {
-        for (int i = threadIdx.x; i < 128 * 16; i += 128) {
-            const int r = i >> 4, w = i & 15;
-            const int64_t row = row0 + r;
-            const int c2 = (c0 >> 1) + w;
-            float2 v = make_float2(0.f, 0.f);
-            if (row < n && c2 < d2) v = __bfloat1622float2(((const __nv_bfloat162*)(X + row * ld))[c2]);
-            tile[r][2 * w] = v.x;
-            tile[r][2 * w + 1] = v.y;
+template <typename T, int VEC>
+__global__ void __launch_bounds__(256)
+    sqnorm_kernel(const T* __restrict__ X, int64_t n, int d, int64_t ld, double* __restrict__ s,
+                  uint64_t* keys, uint32_t* vals, unsigned* fallbacks) {
+    using G = RowGroups<T, VEC>;
+    const int lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const T* xr = X + row * ld;
+    const int ng = d / VEC;
+    // the window: the row's largest term ends below 2^top
+    int top = INT_MIN;
+#pragma unroll 4
+    for (int g = lane; g < ng; g += 32) {
+        float v[VEC];
+        G::load(xr, g, v);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            uint64_t M2;
+            int E2;
+            f32_fields(v[i], M2, E2);
+            if (M2) top = max(top, E2 + bitlen64(M2));
         }
-        __syncthreads();
-        const int cmax = min(32, d - c0);
-        for (int c = 0; c < cmax; ++c) {
-            const double v = (double)tile[threadIdx.x][c];
-            acc = fma(v, v, acc);
-        }
-        __syncthreads();
     }
-    const int64_t row = row0 + threadIdx.x;
-    if (row < n) store_norm(row, acc, s, keys, vals);
+    for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+    double res = 0.0;
+    if (top != INT_MIN) {
+        const int W0 = top + (32 - __clz(d)) + 1 - 128;
+        u128 acc = 0;
+        bool dropped = false;
+#pragma unroll 4
+        for (int g = lane; g < ng; g += 32) {
+            float v[VEC];
+            G::load(xr, g, v);
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) {
+                uint64_t M2;
+                int E2;
+                f32_fields(v[i], M2, E2);
+                const int sh = E2 - W0;
+                if (sh >= 0) {
+                    acc += (u128)M2 << sh;
+                } else if (M2) {
+                    const int r = -sh;
+                    if (r < 64) {
+                        acc += (u128)(M2 >> r);
+                        dropped |= (M2 & ((1ull << r) - 1)) != 0;
+                    } else {
+                        dropped = true;
+                    }
+                }
+            }
+        }
+        uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
+        for (int o = 16; o; o >>= 1) {
+            const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
+            const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+            const uint64_t nlo = lo + olo;
+            hi = hi + ohi + (nlo < lo);
+            lo = nlo;
+        }
+        dropped = __any_sync(0xffffffffu, dropped);
+        if (lane == 0) {
+            const u128 A = ((u128)hi << 64) | lo;
+            const int pos = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+            const int cut = pos - 52;                 // >= 53: the bits below the mantissa
+            uint64_t mant = (uint64_t)(A >> cut);
+            const u128 rem = A & (((u128)1 << cut) - 1), half = (u128)1 << (cut - 1);
+            int ex = W0 + pos;
+            bool up, exact_needed = false;
+            if (rem > half) {
+                up = true;
+            } else if (rem == half) {
+                up = dropped || (mant & 1);
+            } else {
+                up = false;
+                exact_needed = dropped && half - rem <= (u128)d;
+            }
+            if (exact_needed) {
+                atomicAdd(fallbacks, 1u);
+                res = sqnorm_exact_slow(xr, d);
+            } else {
+                if (up && ++mant == (1ull << 53)) {
+                    mant >>= 1;
+                    ++ex;
+                }
+                res = __longlong_as_double(
+                    (long long)(((uint64_t)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1))));
+            }
+        }
+    }
+    if (lane == 0) {
+        s[row] = res;
+        if (keys) {
+            keys[row] = (uint64_t)__double_as_longlong(res);
+            vals[row] = (uint32_t)row;
+        }
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64_t ld, double* s,
-                          uint64_t* keys, uint32_t* vals, cudaStream_t st) {
-    const dim3 grid((unsigned)ceil_div(n, 128));
+                          uint64_t* keys, uint32_t* vals, unsigned* fallbacks, cudaStream_t st) {
+    const dim3 grid((unsigned)ceil_div(n * 32, 256));
+    // four values per load when every row starts on a 16-byte (fp32) or 8-byte
+    // (bf16) boundary and d is a multiple of 4
+    const size_t esz = dt == NRLSH_BF16 ? 2 : 4;
+    const bool vec = d % 4 == 0 && (ld * esz) % (4 * esz) == 0 && ((uintptr_t)X % (4 * esz)) == 0;
     if (dt == NRLSH_BF16) {
-        if (d % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X & 3) == 0)
-            return launch("sqnorm_bf16", sqnorm_bf16x2_kernel, grid, dim3(128), 0, st,
-                          (const __nv_bfloat16*)X, n, d, ld, s, keys, vals);
-        return launch("sqnorm_bf16", sqnorm_kernel<__nv_bfloat16>, grid, dim3(128), 0, st,
-                      (const __nv_bfloat16*)X, n, d, ld, s, keys, vals);
+        if (vec)
+            return launch("sqnorm_bf16", sqnorm_kernel<__nv_bfloat16, 4>, grid, dim3(256), 0, st,
+                          (const __nv_bfloat16*)X, n, d, ld, s, keys, vals, fallbacks);
+        return launch("sqnorm_bf16", sqnorm_kernel<__nv_bfloat16, 1>, grid, dim3(256), 0, st,
+                      (const __nv_bfloat16*)X, n, d, ld, s, keys, vals, fallbacks);
     }
-    if (ld == d && d % 4 == 0 && ((uintptr_t)X & 15) == 0)
-        return launch("sqnorm_f32", sqnorm_f32v4_kernel, grid, dim3(128), 0, st, (const float*)X, n,
-                      d, s, keys, vals);
-    return launch("sqnorm_f32", sqnorm_kernel<float>, grid, dim3(128), 0, st, (const float*)X, n, d,
-                  ld, s, keys, vals);
+    if (vec)
+        return launch("sqnorm_f32", sqnorm_kernel<float, 4>, grid, dim3(256), 0, st, (const float*)X,
+                      n, d, ld, s, keys, vals, fallbacks);
+    return launch("sqnorm_f32", sqnorm_kernel<float, 1>, grid, dim3(256), 0, st, (const float*)X, n,
+                  d, ld, s, keys, vals, fallbacks);
 }
 
 // =====================================================================

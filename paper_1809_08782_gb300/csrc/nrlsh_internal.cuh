@@ -87,9 +87,10 @@ struct PosTile {
 // A ((d+1) x L), its zero-padded copy A_pad ((d+1) x Lp) and column-norm bounds anorm.
 cudaError_t launch_projections(float* A, float* A_pad, float* anorm, __nv_bfloat16* At, int dp,
                                int d, int L, int Lp, uint64_t seed, cudaStream_t s);
-// s_x in FP64; with keys/vals non-null also the partition's sort keys and ids.
+// s_x = ||x||^2 rounded once to FP64; with keys/vals non-null also the partition's
+// sort keys and ids.  *fallbacks counts rows summed by the exact slow path.
 cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64_t ld, double* s,
-                          uint64_t* keys, uint32_t* vals, cudaStream_t st);
+                          uint64_t* keys, uint32_t* vals, unsigned* fallbacks, cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of the key.
 // Buffers alternate; returns through *result_in_alt whether the result is in the alt pair.
 size_t radix_sort_temp_bytes(int64_t n);

@@ -64,7 +64,7 @@ class NrlshInfo(ctypes.Structure):
     _fields_ = [("n", _I64), ("d", _I32), ("m", _I32), ("L", _I32), ("dtype", _I32),
                 ("eps", _F32), ("seed", _U64), ("code_bytes", _I32), ("row_stride", _I32),
                 ("device_bytes", _I64), ("ambiguous_bits", _I64), ("projection", _I32),
-                ("device_error", _I32), ("partition", _I32), ("reserved", _I32)]
+                ("device_error", _I32), ("partition", _I32), ("norm_fallbacks", _I32)]
 
 
 class NrlshBuildOptions(ctypes.Structure):

@@ -190,3 +190,42 @@ def test_wide_rows(d, L):
     lib, ref = build_pair(items, "f32", 8, L, seed=3, eps=0.2, projection=SIMT)
     check_index(lib, ref, SIMT)
     check_queries(lib, ref, rand_q(6, d, 4), 10, 300)
+
+
+def _window_tie_row(t, d=15):
+    """A row built for the squared-norm kernel's 128-bit window: W0 = top +
+    bitlen(d) + 1 - 128 with top = 1 for the term 1.0, so W0 = -122 for
+    8 <= d <= 15.  The in-window part is 1 + 2^-53 - 2^W0 (one unit below the
+    half-way point); t terms of 2^(W0 - 2) each (dropped by the window) decide it."""
+    import math
+    W0 = 1 + d.bit_length() + 1 - 128
+    row = [1.0, 11863283 * 2.0 ** -50]
+    rem = 4817239 * 2 ** (-100 - W0) - 1                # in units of 2^W0
+    while rem > 0:
+        j = max(0, (rem.bit_length() - 46) // 2)       # M^2 = rem / 4^j below 2^48
+        M = min(math.isqrt(rem // 4 ** j), 2 ** 24 - 1)
+        row.append(M * 2.0 ** (j + W0 // 2))
+        rem -= M * M * 4 ** j
+    row += [2.0 ** ((W0 - 2) // 2)] * t
+    assert len(row) <= d
+    row += [0.0] * (d - len(row))
+    return np.array(row, dtype=np.float32)
+
+
+def test_exact_squared_norms_and_the_slow_path():
+    """s_x is the exact sum of squares rounded once: rows with a wide exponent
+    range, and rows built to land next to a rounding tie inside the kernel's
+    window (those take the exact slow path), against the oracle."""
+    from oracle import nrlsh as O
+    import paper_1809_08782_gb300.nrlsh as N
+    rng = np.random.default_rng(77)
+    wide = (rng.standard_normal((500, 15)) * 2.0 ** rng.integers(-60, 60, (500, 15))).astype(np.float32)
+    ties = np.stack([_window_tie_row(t) for t in (0, 3, 4, 5, 9)] * 4)
+    items = np.concatenate([wide, ties, np.zeros((3, 15), np.float32)])
+    s_ref = O.sq_norms(items.astype(np.float64))
+    assert list(s_ref[500:505]) == [1.0, 1.0, 1.0, 1.0 + 2.0 ** -52, 1.0 + 2.0 ** -52]
+    lib = N.nrlsh_build_ex(torch.from_numpy(items).cuda(), 4, 16, 3, eps=f32(0.2),
+                           projection=SIMT)
+    _, _, s = N.nrlsh_get_partition(lib)
+    assert np.array_equal(s.numpy(), s_ref)
+    assert N.nrlsh_get_info(lib)["norm_fallbacks"] >= 12   # the tie rows with t > 0
