@@ -222,10 +222,10 @@ void destroy(nrlsh_index* ix) {
     delete ix;
 }
 
-// A per-thread side stream for the data-independent parts of the build.  The
-// fork makes it wait for everything queued on the main stream so far; the join
-// (recorded after the side work) makes the main stream wait for the side work
-// at the point where the main stream's next consumer is queued.
+// Per-thread side streams for the data-independent parts of the build.  A fork
+// makes a side stream wait for everything queued on the main stream so far; its
+// join event (recorded after the side work) is what the main stream waits for at
+// the point where the side work's first consumer is queued.
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -235,32 +235,30 @@ struct SideStream {
         if (join) cudaEventDestroy(join);
     }
 };
-thread_local SideStream t_side;
+thread_local SideStream t_side[2];
 
-cudaStream_t side_stream() { return t_side.s; }
+cudaStream_t side_stream(int i) { return t_side[i].s; }
 
-cudaError_t side_stream_fork(cudaStream_t main) {
-    if (!t_side.s) {
-        cudaError_t e = cudaStreamCreateWithFlags(&t_side.s, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t_side.fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t_side.join, cudaEventDisableTiming);
+cudaError_t side_stream_fork(cudaStream_t main, int i) {
+    SideStream& t = t_side[i];
+    if (!t.s) {
+        cudaError_t e = cudaStreamCreateWithFlags(&t.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaEventRecord(t_side.fork, main);
+    cudaError_t e = cudaEventRecord(t.fork, main);
     if (e != cudaSuccess) return e;
-    return cudaStreamWaitEvent(t_side.s, t_side.fork, 0);
+    return cudaStreamWaitEvent(t.s, t.fork, 0);
 }
 
-// Records the end of the side work; the main stream waits for it right away
-// (its own earlier work is unaffected, and the side kernels run meanwhile).
-cudaError_t side_stream_join(cudaStream_t main) {
-    cudaError_t e = cudaEventRecord(t_side.join, t_side.s);
-    if (e != cudaSuccess) return e;
-    return cudaSuccess;
-}
+// Records the end of the side work queued so far.
+cudaError_t side_stream_join(int i) { return cudaEventRecord(t_side[i].join, t_side[i].s); }
 
-cudaError_t side_stream_wait(cudaStream_t main) {
-    return cudaStreamWaitEvent(main, t_side.join, 0);
+// The main stream's later work waits for the side work (its earlier work is
+// unaffected, and the side kernels run meanwhile).
+cudaError_t side_stream_wait(cudaStream_t main, int i) {
+    return cudaStreamWaitEvent(main, t_side[i].join, 0);
 }
 
 int bits_for(int64_t v) {  // smallest b with 2^b >= v
@@ -437,18 +435,20 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned), st));
         B_CU(cudaMemsetAsync(ix->norm_fb, 0, sizeof(unsigned), st));
         B_CU(cudaMemsetAsync(ix->U2, 0, sizeof(double) * m, st));
-        // A and the tiles of its columns (Eq. 4 projections)
-        // A and the bucket cosines depend only on (seed, d, L, eps): a side stream
-        // computes them while the main stream ranks the items
-        B_CU(side_stream_fork(st));
-        cudaStream_t side = side_stream();
+        // Side stream 0: A and A^T, needed by the projection.  Side stream 1: the
+        // bucket cosines and the percentile offsets, needed by the bucket order
+        // and the queries.  Both run while the main stream ranks the items.
+        B_CU(side_stream_fork(st, 0));
+        B_CU(side_stream_fork(st, 1));
+        cudaStream_t side0 = side_stream(0), side1 = side_stream(1);
         B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, ix->At, ix->dp, d, L, ix->Lp, seed,
-                                side));
-        B_CU(launch_class_cos(L, eps, ix->ccos, side));
-        if (ix->At32) B_CU(launch_transpose_a(ix->A_pad, d, L, ix->Lp, ix->At32, side));
+                                side0));
+        if (ix->At32) B_CU(launch_transpose_a(ix->A_pad, d, L, ix->Lp, ix->At32, side0));
+        B_CU(side_stream_join(0));
+        B_CU(launch_class_cos(L, eps, ix->ccos, side1));
         if (!uniform)  // percentile ranges: offsets and tiles follow from n and m
-            B_CU(launch_segments(nullptr, n, m, tile, ix->seg, ix->tiles, ix->ntiles, side));
-        B_CU(side_stream_join(st));
+            B_CU(launch_segments(nullptr, n, m, tile, ix->seg, ix->tiles, ix->ntiles, side1));
+        B_CU(side_stream_join(1));
         const int jbits = (bits_for(m) + 7) / 8 * 8;
         bool alt = false;
         uint32_t *jv = nullptr, *jv_alt = nullptr;
@@ -486,7 +486,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, ix->sub_of_id, ix->s_id,
                                  ix->U2, ix->Xp, ix->Xb, ix->Xb2, ix->s_pos, ix->tau64, ix->tau32,
                                  ix->xnorm, st));
-        B_CU(side_stream_wait(st));  // A and the cosines are ready
+        B_CU(side_stream_wait(st, 0));  // A and A^T are ready
         // Eq. 4: sign random projection codes
         if (!tc) {
             B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
@@ -507,7 +507,9 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                      amb_list2, amb_count2, (unsigned)amb_cap2, ix->codes,
                                      ix->code_bytes, st));
         }
-        // Eq. 12 and the sorted (U_j, l) structure
+        // Eq. 12 and the sorted (U_j, l) structure (the cosines, and for the
+        // queries the offsets, come from side stream 1)
+        B_CU(side_stream_wait(st, 1));
         B_CU(launch_bucket_order(ix->U2, ix->ccos, m, L, ix->shat_sorted, ix->order, bo_tmp, st));
     }
     if (!is_device_ptr(items)) B_CU(cudaStreamSynchronize(st));

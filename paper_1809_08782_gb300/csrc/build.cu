@@ -214,25 +214,24 @@ __global__ void __launch_bounds__(256)
     if (row >= n) return;
     const T* xr = X + row * ld;
     const int ng = d / VEC;
-    // the window: the row's largest term ends below 2^top
-    int top = INT_MIN;
+    // the window: the row's largest term is the square of its largest |x_k|
+    float amax = 0.0f;
 #pragma unroll 4
     for (int g = lane; g < ng; g += 32) {
         float v[VEC];
         G::load(xr, g, v);
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) {
-            uint64_t M2;
-            int E2;
-            f32_fields(v[i], M2, E2);
-            if (M2) top = max(top, E2 + bitlen64(M2));
-        }
+        for (int i = 0; i < VEC; ++i) amax = fmaxf(amax, fabsf(v[i]));
     }
-    for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     double res = 0.0;
-    if (top != INT_MIN) {
+    if (amax > 0.0f) {
+        uint64_t M2m;
+        int E2m;
+        f32_fields(amax, M2m, E2m);
+        const int top = E2m + bitlen64(M2m);          // the largest term ends below 2^top
         const int W0 = top + (32 - __clz(d)) + 1 - 128;
-        u128 acc = 0;
+        uint64_t lo = 0, hi = 0;                      // the window, 2 x 64 bits
         bool dropped = false;
 #pragma unroll 4
         for (int g = lane; g < ng; g += 32) {
@@ -243,21 +242,28 @@ __global__ void __launch_bounds__(256)
                 uint64_t M2;
                 int E2;
                 f32_fields(v[i], M2, E2);
-                const int sh = E2 - W0;
-                if (sh >= 0) {
-                    acc += (u128)M2 << sh;
-                } else if (M2) {
+                if (!M2) continue;
+                const int sh = E2 - W0;               // < 80: the term ends inside
+                uint64_t l, h;
+                if (sh >= 64) {
+                    l = 0;
+                    h = M2 << (sh - 64);
+                } else if (sh > 0) {
+                    l = M2 << sh;
+                    h = M2 >> (64 - sh);
+                } else if (sh == 0) {
+                    l = M2;
+                    h = 0;
+                } else {
                     const int r = -sh;
-                    if (r < 64) {
-                        acc += (u128)(M2 >> r);
-                        dropped |= (M2 & ((1ull << r) - 1)) != 0;
-                    } else {
-                        dropped = true;
-                    }
+                    l = r < 64 ? M2 >> r : 0;
+                    h = 0;
+                    dropped |= r >= 64 || (M2 << (64 - r)) != 0;
                 }
+                lo += l;
+                hi += h + (lo < l);
             }
         }
-        uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
         for (int o = 16; o; o >>= 1) {
             const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
             const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
