@@ -57,6 +57,7 @@ struct nrlsh_index {
     int64_t* seg = nullptr;        // m+1 storage offsets of the sub-datasets
     nrlsh::PosTile* tiles = nullptr;
     int32_t ntiles = 0;
+    bool tiles_exclusive = false;  // every sub-dataset is exactly one histogram tile
     unsigned* ambiguous = nullptr;  // (item, bit) pairs the first tier left undecided
     unsigned* norm_fb = nullptr;    // rows whose squared norm took the exact slow path
     int projection = NRLSH_PROJECT_SIMT;
@@ -352,6 +353,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         int64_t nt = 0;
         for (int32_t j = 0; j < m; ++j) nt += ceil_div(seg_start(j + 1, n, m) - seg_start(j, n, m), tile);
         ix->ntiles = (int32_t)nt;
+        ix->tiles_exclusive = nt == m;
     } else {
         ix->ntiles = (int32_t)(ceil_div(n, tile) + m);
     }
@@ -428,13 +430,19 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         if (tc) {
             B_CK(sc.get(&amb_list2, amb_cap2));
             B_CK(sc.get(&amb_count2, 1));
-            B_CU(cudaMemsetAsync(amb_count2, 0, sizeof(unsigned), st));
         }
-        B_CU(cudaMemsetAsync(ix->dev_err, 0, sizeof(int), st));
-
-        B_CU(cudaMemsetAsync(ix->ambiguous, 0, sizeof(unsigned), st));
-        B_CU(cudaMemsetAsync(ix->norm_fb, 0, sizeof(unsigned), st));
-        B_CU(cudaMemsetAsync(ix->U2, 0, sizeof(double) * m, st));
+        // everything that starts at zero, in one launch
+        const bool small = !uniform && small_rank_supported(n, m);
+        {
+            ZeroList z;
+            z.add(ix->dev_err, 1);
+            z.add(ix->ambiguous, 1);
+            z.add(ix->norm_fb, 1);
+            z.add(ix->U2, 2 * (size_t)m);
+            if (tc) z.add(amb_count2, 1);
+            if (small) z.add(sort_tmp, small_rank_temp_bytes(n, m) / 4);
+            B_CU(launch_zero(z, st));
+        }
         // Side stream 0: A and A^T, needed by the projection.  Side stream 1: the
         // bucket cosines and the percentile offsets, needed by the bucket order
         // and the queries.  Both run while the main stream ranks the items.
@@ -452,7 +460,6 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         const int jbits = (bits_for(m) + 7) / 8 * 8;
         bool alt = false;
         uint32_t *jv = nullptr, *jv_alt = nullptr;
-        const bool small = !uniform && small_rank_supported(n, m);
         if (small) {
             // Algorithm 1 for small inputs: tile sort, rank, per-range id sort
             B_CU(launch_sqnorm(X, dtype, n, d, d, ix->s_id, keys, vals, ix->norm_fb, st));
@@ -568,7 +575,6 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
         NRLSH_CKS(sc.get(&qnorm, qc));
         NRLSH_CKS(sc.get(&qamb, 1));
         NRLSH_CKS(sc.get(&qamb_list, qamb_cap));
-        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CKS(sc.get(&qcodes, qc * ix->code_bytes));
         // P(q) = [q; 0] (Eq. 8), hashed by Eq. 4
         NRLSH_CK(launch_hash_queries(Qc, qc, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, qnorm,
@@ -590,9 +596,10 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
         } else {
             NRLSH_CKS(sc.get(&H, qc * ix->ncls));
         }
-        NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
+        if (!ix->tiles_exclusive)
+            NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
         NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
-                             ix->ntiles, H, st));
+                             ix->ntiles, H, st, 64, ix->tiles_exclusive));
         if (stage == Stage::Hist) continue;
         if (stage == Stage::TopK && !whole) {
             // one fused launch: walk, selection, re-rank, exact top-k, by CTAs that
@@ -672,7 +679,6 @@ nrlsh_status run_multitable(const nrlsh_index* ix, const float* Q, int64_t nq, i
         NRLSH_CKS(sc.get(&qnorm, qc));
         NRLSH_CKS(sc.get(&qamb, 1));
         NRLSH_CKS(sc.get(&qamb_list, qamb_cap));
-        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CKS(sc.get(&qcodes, qc * ix->code_bytes));
         // P(q) = [q; 0] (Eq. 8), hashed by Eq. 4
         NRLSH_CK(launch_hash_queries(Qc, qc, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, qnorm,
@@ -1136,16 +1142,16 @@ void batch_ws_assign(BatchWs& w, const std::vector<void*>& p, const nrlsh_index*
 nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, const int32_t* ks,
                          const int64_t* budgets, int k_max, int64_t cap, const nrlsh_batch_cfg& cfg,
                          const BatchWs& w, int64_t* ids, float* scores, cudaStream_t st) {
-    NRLSH_CK(cudaMemsetAsync(w.qamb, 0, sizeof(unsigned), st));
     NRLSH_CK(launch_hash_queries(Q, nq, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, w.qnorm,
                                  w.qcodes, ix->code_bytes, w.qamb_list, w.qamb,
                                  (unsigned)w.qamb_cap, ix->At32, st));
     for (int64_t q0 = 0; q0 < nq; q0 += w.hq) {
         const int64_t qc = std::min(w.hq, nq - q0);
         const char* qcodes = w.qcodes + q0 * ix->code_bytes;
-        NRLSH_CK(cudaMemsetAsync(w.H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
+        if (!ix->tiles_exclusive)
+            NRLSH_CK(cudaMemsetAsync(w.H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
         NRLSH_CK(launch_hist(ix->codes, qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
-                             ix->ntiles, w.H, st, cfg.hist_qb));
+                             ix->ntiles, w.H, st, cfg.hist_qb, ix->tiles_exclusive));
         NRLSH_CK(cudaMemsetAsync(w.work, 0, sizeof(unsigned), st));
         NRLSH_CK(launch_probe_rerank_persistent(
             w.H, ix->order, ix->m, ix->L, ix->n, ix->seg, 0, budgets + q0, ix->codes, qcodes,
@@ -1454,7 +1460,6 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* ix, con
         double* cont_s = a.take<double>((size_t)qc * cap);
         // everything that must start at zero is cleared: the array keeps the
         // previous call's contents
-        NRLSH_CK(cudaMemsetAsync(qamb, 0, sizeof(unsigned), st));
         NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
         NRLSH_CK(launch_hash_queries(Qc, qc, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, qnorm,
                                      qcodes, ix->code_bytes, qamb_list, qamb, (unsigned)qamb_cap, ix->At32, st));

@@ -101,6 +101,31 @@ cudaError_t launch_projections(float* A, float* A_pad, float* anorm, __nv_bfloat
 }
 
 // =====================================================================
+// Zeroing of several small arrays in one launch.
+// =====================================================================
+
+namespace {
+
+__global__ void zero_kernel(ZeroList z) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int i = 0; i < z.k; ++i) {
+        uint32_t* p = (uint32_t*)z.p[i];
+        for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (int64_t)z.words[i];
+             w += stride)
+            p[w] = 0u;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_zero(const ZeroList& z, cudaStream_t st) {
+    size_t most = 1;
+    for (int i = 0; i < z.k; ++i) most = std::max(most, z.words[i]);
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div((int64_t)most, 256), 2 * 152);
+    return launch("zero", zero_kernel, dim3(grid), dim3(256), 0, st, z);
+}
+
+// =====================================================================
 // Squared norms: s_x = sum_k x_k^2 exactly, rounded once to FP64.  A warp per
 // row; every x_k = M 2^E (M < 2^24) has x_k^2 = M^2 2^2E exactly.  The lanes
 // add their terms into a 128-bit integer window [W0, W0 + 128) placed under the
@@ -772,9 +797,7 @@ cudaError_t launch_small_rank(uint64_t* keys, uint32_t* ids, int64_t n, int m,
     const int64_t W = ceil_div(n, 32);
     unsigned* rank = (unsigned*)temp;
     uint32_t* bitmap = rank + n;
-    cudaError_t e = cudaMemsetAsync(temp, 0, small_rank_temp_bytes(n, m), st);
-    if (e != cudaSuccess) return e;
-    e = launch("tile_sort", tile_sort_kernel, dim3(T), dim3(kRankTile), 0, st, keys, ids, n);
+    cudaError_t e = launch("tile_sort", tile_sort_kernel, dim3(T), dim3(kRankTile), 0, st, keys, ids, n);
     if (e != cudaSuccess) return e;
     e = launch("tile_rank", tile_rank_kernel, dim3(T, T), dim3(512), 0, st, (const uint64_t*)keys,
                (const uint32_t*)ids, n, rank);
@@ -1279,15 +1302,32 @@ __global__ void bucket_keys_kernel(const double* __restrict__ U2, const double* 
 // Then every block stages all keys in shared memory and each warp ranks buckets:
 // rank(c) = number of buckets with a greater (s_hat, l, j), counted by the lanes
 // over strided buckets and summed.  order[rank] = c, shat_sorted[rank] = s_hat.
+// With keys_g null the block computes the keys itself from U2 and the cosines
+// (staged in shared memory behind the keys), saving the first launch.
 __global__ void __launch_bounds__(kBucketThreads)
     bucket_rank_kernel(const unsigned long long* __restrict__ keys_g,
                        const uint32_t* __restrict__ tie_g, int ncls,
-                       double* __restrict__ shat_sorted, uint32_t* __restrict__ order) {
+                       double* __restrict__ shat_sorted, uint32_t* __restrict__ order,
+                       const double* __restrict__ U2, const double* __restrict__ cl_g, int m,
+                       int L) {
     extern __shared__ unsigned long long keys[];
     uint32_t* tie = (uint32_t*)(keys + ncls);
-    for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
-        keys[c] = keys_g[c];
-        tie[c] = tie_g[c];
+    if (keys_g) {
+        for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
+            keys[c] = keys_g[c];
+            tie[c] = tie_g[c];
+        }
+    } else {
+        double* Uj = (double*)(tie + ((ncls + 1) & ~1));   // m norms, then L+1 cosines
+        double* cl = Uj + m;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) Uj[j] = sqrt(U2[j]);
+        for (int l = threadIdx.x; l <= L; l += blockDim.x) cl[l] = cl_g[l];
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncls; c += blockDim.x) {
+            const int j = c / (L + 1), l = c % (L + 1);
+            keys[c] = double_order(__dadd_rn(__dmul_rn(Uj[j], cl[l]), 0.0));
+            tie[c] = ((uint32_t)l << 16) | (uint32_t)j;
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -1323,19 +1363,28 @@ cudaError_t launch_bucket_order(const double* U2, const double* cl, int m, int L
                                 double* shat_sorted, uint32_t* order, void* temp,
                                 cudaStream_t st) {
     const int ncls = m * (L + 1);
-    unsigned long long* keys = (unsigned long long*)temp;
-    uint32_t* tie = (uint32_t*)(keys + ncls);
-    cudaError_t e = launch("bucket_keys", bucket_keys_kernel, dim3((unsigned)ceil_div(ncls, 256)),
-                           dim3(256), 0, st, U2, cl, m, L, keys, tie);
-    if (e != cudaSuccess) return e;
-    const size_t smem = (sizeof(unsigned long long) + sizeof(uint32_t)) * ncls;
+    const size_t key_bytes = (sizeof(unsigned long long) + sizeof(uint32_t)) * ncls + 8;
+    const size_t fused_bytes = key_bytes + sizeof(double) * (m + L + 1);
+    const bool fused = fused_bytes <= 200 * 1024;
+    const size_t smem = fused ? fused_bytes : key_bytes;
+    unsigned long long* keys = nullptr;
+    uint32_t* tie = nullptr;
+    cudaError_t e;
+    if (!fused) {  // keys in global memory first (m (L+1) shared words would not fit)
+        keys = (unsigned long long*)temp;
+        tie = (uint32_t*)(keys + ncls);
+        e = launch("bucket_keys", bucket_keys_kernel, dim3((unsigned)ceil_div(ncls, 256)), dim3(256),
+                   0, st, U2, cl, m, L, keys, tie);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(bucket_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     const int wpb = kBucketThreads / 32;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(ncls, wpb), 2 * 152);
     return launch("bucket_order", bucket_rank_kernel, dim3(grid), dim3(kBucketThreads), smem, st,
-                  (const unsigned long long*)keys, (const uint32_t*)tie, ncls, shat_sorted, order);
+                  (const unsigned long long*)keys, (const uint32_t*)tie, ncls, shat_sorted, order,
+                  U2, cl, m, L);
 }
 
 }  // namespace nrlsh

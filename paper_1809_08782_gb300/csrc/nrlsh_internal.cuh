@@ -82,6 +82,19 @@ struct PosTile {
 };
 
 // ----------------------------------------------------------- build launchers
+
+// Up to eight arrays of 4-byte words to clear with one launch.
+struct ZeroList {
+    void* p[8];
+    size_t words[8];
+    int k = 0;
+    void add(void* ptr, size_t w) {
+        p[k] = ptr;
+        words[k] = w;
+        ++k;
+    }
+};
+cudaError_t launch_zero(const ZeroList& z, cudaStream_t st);
 // All return cudaError_t of the last launch; pointers are device pointers.
 
 // A ((d+1) x L), its zero-padded copy A_pad ((d+1) x Lp) and column-norm bounds anorm.
@@ -102,7 +115,8 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, u
                            cudaStream_t s);
 // Percentile partition for small inputs (n <= 65,536 and m ceil(n/32) <= 4M):
 // ranks the (keys, ids) pairs (sorting them by tiles in place), then writes perm
-// (storage order), sub_of_id and U2.  temp: small_rank_temp_bytes(n, m).
+// (storage order), sub_of_id and U2.  temp: small_rank_temp_bytes(n, m), zeroed
+// by the caller.
 bool small_rank_supported(int64_t n, int m);
 size_t small_rank_temp_bytes(int64_t n, int m);
 cudaError_t launch_small_rank(uint64_t* keys, uint32_t* ids, int64_t n, int m,
@@ -145,7 +159,8 @@ size_t warp_proj_at_floats(int d, int Lp);
 cudaError_t launch_transpose_a(const float* A_pad, int d, int L, int Lp, float* At32,
                                cudaStream_t st);
 // Query codes (P(q) = [q; 0]) and the queries' fp32 norm bounds (qnorm, written
-// here) in one pass where the warp-per-row projection applies.
+// here) in one pass where the warp-per-row projection applies.  amb_count need
+// not be zeroed by the caller.
 cudaError_t launch_hash_queries(const float* Q, int64_t nq, int d, int L, int Lp,
                                 const float* A_pad, const float* anorm, float* qnorm, void* codes,
                                 int code_bytes, unsigned long long* amb_list, unsigned* amb_count,
@@ -187,10 +202,12 @@ cudaError_t launch_bucket_order(const double* U2, const double* cl, int m, int L
 
 cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnorm,
                                   cudaStream_t st);
-// queries_per_block: 32, 64 or 128 (the autotuned tile).
+// queries_per_block: 32, 64 or 128 (the autotuned tile).  exclusive: every
+// sub-dataset is exactly one tile, so H is stored whole and need not be cleared;
+// otherwise H must start at zero.
 cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, int64_t nq, int m,
                         int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st,
-                        int queries_per_block = 64);
+                        int queries_per_block = 64, bool exclusive = false);
 struct Boundary {
     int32_t j;       // boundary bucket (j*, l*)
     int32_t l;

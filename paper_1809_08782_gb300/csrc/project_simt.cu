@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(256)
             // |tail|) of the canonical in-order sum, as in resolve_kernel), and the
             // canonical sequential form by lane 0 only inside that bound
             if (undecided[r]) {
-                if (lane == 0) atomicAdd(amb_count, (unsigned)__popcll(undecided[r]));
+                if (lane == 0 && amb_count) atomicAdd(amb_count, (unsigned)__popcll(undecided[r]));
                 const double tau = has_tail ? tau64[row] : 0.0;
                 for (unsigned long long u = undecided[r]; u; u &= u - 1) {
                     const int b = __ffsll((long long)u) - 1;
@@ -570,6 +570,12 @@ cudaError_t launch_hash_queries(const float* Q, int64_t nq, int d, int L, int Lp
                                 const float* A_pad, const float* anorm, float* qnorm, void* codes,
                                 int code_bytes, unsigned long long* amb_list, unsigned* amb_count,
                                 unsigned amb_cap, const float* At32, cudaStream_t st) {
+    if (warp_proj_stride(d, Lp) > 0) {
+        amb_count = nullptr;  // the warp kernel settles its bits itself: nothing to count
+    } else {
+        cudaError_t e = cudaMemsetAsync(amb_count, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+    }
     if (code_bytes == 4)
         return project_dispatch<float, uint32_t>(Q, nq, d, d, L, Lp, A_pad, anorm, nullptr, nullptr,
                                                  nullptr, codes, amb_list, amb_count, amb_cap, st,

@@ -79,13 +79,14 @@ __global__ void row_norm_bound_kernel(const float* __restrict__ Q, int64_t nq, i
 // broadcast).  Every thread keeps private uint16 histogram columns indexed
 // [l][thread] (two for 32-bit codes, alternating so consecutive increments do not
 // wait on each other), so increments never conflict on a bank; the columns of a
-// query are summed at the end and added to H.
+// query are summed at the end and added to H (stored, when every sub-dataset is
+// one tile).
 constexpr int kHistThreads = 256;
 
 template <typename C, int kHistQ>
 __global__ void __launch_bounds__(kHistThreads)
     hist_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t nq, int m, int L,
-                const PosTile* __restrict__ tiles, uint32_t* __restrict__ H) {
+                const PosTile* __restrict__ tiles, uint32_t* __restrict__ H, int exclusive) {
     constexpr int kSplit = kHistThreads / kHistQ;
     constexpr int kSub = sizeof(C) == 4 ? 2 : 1;
     extern __shared__ unsigned char smem_raw[];
@@ -122,7 +123,11 @@ __global__ void __launch_bounds__(kHistThreads)
 #pragma unroll
             for (int s2 = 0; s2 < kSplit; ++s2)
                 v += h[(sub * (L + 1) + l) * kHistThreads + s2 * kHistQ + qe];
-        if (v) atomicAdd(&H[((q0 + qe) * m + t.seg) * (L + 1) + l], v);
+        uint32_t* dst = &H[((q0 + qe) * m + t.seg) * (L + 1) + l];
+        if (exclusive)
+            *dst = v;                 // the only tile of its sub-dataset: H needs no clearing
+        else if (v)
+            atomicAdd(dst, v);
     }
 }
 
@@ -1208,7 +1213,7 @@ cudaError_t launch_row_norm_bound(const float* Q, int64_t nq, int d, float* qnor
 
 cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, int64_t nq, int m,
                         int L, const PosTile* tiles, int ntiles, uint32_t* H, cudaStream_t st,
-                        int queries_per_block) {
+                        int queries_per_block, bool exclusive) {
     const int qb = queries_per_block;
     const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nq, qb));
     const int sub = code_bytes == 4 ? 2 : 1;
@@ -1219,7 +1224,7 @@ cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, i
         if (e != cudaSuccess) return e;                                                     \
         return launch(sizeof(C_) == 4 ? "hist_u32" : "hist_u64", hist_kernel<C_, Q_>, grid,  \
                       dim3(kHistThreads), smem, st, (const C_*)codes, (const C_*)qcodes, nq, m, \
-                      L, tiles, H);                                                         \
+                      L, tiles, H, exclusive ? 1 : 0);                                      \
     }
     if (code_bytes == 4) {
         if (qb == 32) NRLSH_HIST_(uint32_t, 32)
