@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(kHistThreads)
     const int64_t q0 = (int64_t)blockIdx.y * kHistQ;
     const int64_t q = q0 + qi;
     for (int i = tid; i < t.len; i += kHistThreads) cs[i] = codes[t.start + i];
-    for (int i = tid; i < kSub * (L + 1) * kHistThreads; i += kHistThreads) h[i] = 0;
+    // the columns are kSub (L+1) x 256 uint16: a multiple of 8, cleared 16 bytes at a time
+    for (int i = tid; i < kSub * (L + 1) * kHistThreads / 8; i += kHistThreads)
+        ((uint4*)h)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (q < nq) {
         const C cq = qcodes[q];
@@ -432,26 +434,28 @@ __device__ void dev_rerank(const T* __restrict__ Xp, int dp, const float* qs,
 #pragma unroll
         for (int u = 0; u < kRerankUnroll; ++u) acc[u] = 0.0f;
         RowDot<T>::template dot<kRerankUnroll>(rows, qs, dp, lane, acc);
-        // transpose-reduction of the 4 row sums (6 shuffles): afterwards lane
-        // 8 r holds the sum of row r (any order meets the same FP32 bound)
-        static_assert(kRerankUnroll == 4, "the reduction below folds 4 rows");
-        {
-            const bool up = (lane & 16) != 0;
-            const float s0 = up ? acc[0] : acc[2], s1 = up ? acc[1] : acc[3];
-            const float k0 = up ? acc[2] : acc[0], k1 = up ? acc[3] : acc[1];
-            acc[0] = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
-            acc[1] = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+        // transpose-reduction of the kRerankUnroll row sums: each level halves the
+        // values a lane holds, then plain butterflies; afterwards lane
+        // (32 / kRerankUnroll) r holds the sum of row r (any order meets the same
+        // FP32 bound)
+#pragma unroll
+        for (int w = 16, cnt = kRerankUnroll; cnt > 1; w >>= 1, cnt >>= 1) {
+            const bool up = (lane & w) != 0;
+#pragma unroll
+            for (int j = 0; j < cnt / 2; ++j) {
+                const float send = up ? acc[j] : acc[j + cnt / 2];
+                const float keep = up ? acc[j + cnt / 2] : acc[j];
+                acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+            }
         }
-        {
-            const bool up = (lane & 8) != 0;
-            const float sd = up ? acc[0] : acc[1], kp = up ? acc[1] : acc[0];
-            acc[0] = kp + __shfl_xor_sync(0xffffffffu, sd, 8);
-        }
-        for (int o = 4; o; o >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
-        const int r = lane >> 3;
-        if ((lane & 7) == 0 && i + r < i1) {
+        for (int o = 16 / kRerankUnroll; o; o >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+        constexpr int kLanesPerRow = 32 / kRerankUnroll;
+        const int r = lane / kLanesPerRow;
+        if (lane % kLanesPerRow == 0 && i + r < i1) {
             const float sc = acc[0];
-            const float xr = r == 0 ? xn[0] : r == 1 ? xn[1] : r == 2 ? xn[2] : xn[3];
+            float xr = xn[0];
+#pragma unroll
+            for (int u = 1; u < kRerankUnroll; ++u) xr = r == u ? xn[u] : xr;
             const float e = __fmul_ru(__fmul_ru(kappa, qn), xr);
             loq[i + r] = __fsub_rd(sc, e);
             hiq[i + r] = __fadd_ru(sc, e);
