@@ -76,11 +76,11 @@ __global__ void row_norm_bound_kernel(const float* __restrict__ Q, int64_t nq, i
 // Block of 256 threads: one position tile (inside one sub-dataset, at most 4,096
 // codes, staged in shared memory) x kHistQ queries, with kSplit = 256 / kHistQ
 // threads per query each taking every kSplit-th code (a warp reads one code by
-// broadcast).  Every thread keeps private uint16 histogram columns indexed
-// [l][thread] (two for 32-bit codes, alternating so consecutive increments do not
-// wait on each other), so increments never conflict on a bank; the columns of a
-// query are summed at the end and added to H (stored, when every sub-dataset is
-// one tile).
+// broadcast).  Every thread keeps a private uint32 histogram column indexed
+// [l][thread], so increments never conflict on a bank; they are shared-memory
+// reductions (no returned value), so consecutive increments of a thread do not
+// wait on each other.  The columns of a query are summed at the end and added to
+// H (stored, when every sub-dataset is one tile).
 constexpr int kHistThreads = 256;
 
 template <typename C, int kHistQ>
@@ -88,32 +88,34 @@ __global__ void __launch_bounds__(kHistThreads)
     hist_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t nq, int m, int L,
                 const PosTile* __restrict__ tiles, uint32_t* __restrict__ H, int exclusive) {
     constexpr int kSplit = kHistThreads / kHistQ;
-    constexpr int kSub = sizeof(C) == 4 ? 2 : 1;
     extern __shared__ unsigned char smem_raw[];
     C* cs = (C*)smem_raw;
-    uint16_t* h = (uint16_t*)(smem_raw + 16384);        // [kSub][L+1][kHistThreads]
+    uint32_t* h = (uint32_t*)(smem_raw + 16384);        // [L+1][kHistThreads]
     const int tid = threadIdx.x;
     const int qi = tid % kHistQ, sp = tid / kHistQ;
     const PosTile t = tiles[blockIdx.x];
     const int64_t q0 = (int64_t)blockIdx.y * kHistQ;
     const int64_t q = q0 + qi;
     for (int i = tid; i < t.len; i += kHistThreads) cs[i] = codes[t.start + i];
-    // the columns are kSub (L+1) x 256 uint16: a multiple of 8, cleared 16 bytes at a time
-    for (int i = tid; i < kSub * (L + 1) * kHistThreads / 8; i += kHistThreads)
+    // (L+1) x 256 words: a multiple of 4, cleared 16 bytes at a time
+    for (int i = tid; i < (L + 1) * kHistThreads / 4; i += kHistThreads)
         ((uint4*)h)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (q < nq) {
         const C cq = qcodes[q];
-        uint16_t* h0 = h + tid;
-        uint16_t* h1 = h + (kSub - 1) * (L + 1) * kHistThreads + tid;
+        uint32_t* hc = h + tid;
         int i = sp;
-        for (; i + kSplit < t.len; i += 2 * kSplit) {
+        for (; i + 3 * kSplit < t.len; i += 4 * kSplit) {
             const int l0 = L - popc_word(cq ^ cs[i]);
             const int l1 = L - popc_word(cq ^ cs[i + kSplit]);
-            h0[l0 * kHistThreads] += 1;
-            h1[l1 * kHistThreads] += 1;
+            const int l2 = L - popc_word(cq ^ cs[i + 2 * kSplit]);
+            const int l3 = L - popc_word(cq ^ cs[i + 3 * kSplit]);
+            atomicAdd(&hc[l0 * kHistThreads], 1u);
+            atomicAdd(&hc[l1 * kHistThreads], 1u);
+            atomicAdd(&hc[l2 * kHistThreads], 1u);
+            atomicAdd(&hc[l3 * kHistThreads], 1u);
         }
-        if (i < t.len) h0[(L - popc_word(cq ^ cs[i])) * kHistThreads] += 1;
+        for (; i < t.len; i += kSplit) atomicAdd(&hc[(L - popc_word(cq ^ cs[i])) * kHistThreads], 1u);
     }
     __syncthreads();
     for (int e = tid; e < (L + 1) * kHistQ; e += kHistThreads) {
@@ -121,10 +123,7 @@ __global__ void __launch_bounds__(kHistThreads)
         if (q0 + qe >= nq) continue;
         uint32_t v = 0;
 #pragma unroll
-        for (int sub = 0; sub < kSub; ++sub)
-#pragma unroll
-            for (int s2 = 0; s2 < kSplit; ++s2)
-                v += h[(sub * (L + 1) + l) * kHistThreads + s2 * kHistQ + qe];
+        for (int s2 = 0; s2 < kSplit; ++s2) v += h[l * kHistThreads + s2 * kHistQ + qe];
         uint32_t* dst = &H[((q0 + qe) * m + t.seg) * (L + 1) + l];
         if (exclusive)
             *dst = v;                 // the only tile of its sub-dataset: H needs no clearing
@@ -1220,8 +1219,7 @@ cudaError_t launch_hist(const void* codes, const void* qcodes, int code_bytes, i
                         int queries_per_block, bool exclusive) {
     const int qb = queries_per_block;
     const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(nq, qb));
-    const int sub = code_bytes == 4 ? 2 : 1;
-    const size_t smem = 16384 + sub * sizeof(uint16_t) * (size_t)(L + 1) * kHistThreads;
+    const size_t smem = 16384 + sizeof(uint32_t) * (size_t)(L + 1) * kHistThreads;
 #define NRLSH_HIST_(C_, Q_)                                                                     \
     {                                                                                       \
         cudaError_t e = ensure_dyn_smem((const void*)hist_kernel<C_, Q_>, smem);            \
