@@ -431,6 +431,10 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
             B_CK(sc.get(&amb_list2, amb_cap2));
             B_CK(sc.get(&amb_count2, 1));
         }
+        // FP32 sums of the item projection, computed in id order beside the partition
+        const bool split = !tc && split_projection_supported(d, ix->Lp);
+        float* vsum = nullptr;
+        if (split) B_CK(sc.get(&vsum, (size_t)n * ((ix->Lp + 31) / 32 * 32)));
         // everything that starts at zero, in one launch
         const bool small = !uniform && small_rank_supported(n, m);
         {
@@ -452,6 +456,9 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, ix->At, ix->dp, d, L, ix->Lp, seed,
                                 side0));
         if (ix->At32) B_CU(launch_transpose_a(ix->A_pad, d, L, ix->Lp, ix->At32, side0));
+        // the FP32 part of the item projection needs no partition: it runs here too
+        if (split)
+            B_CU(launch_project_dots(X, dtype, n, d, d, ix->Lp, ix->At32, vsum, side0));
         B_CU(side_stream_join(0));
         B_CU(launch_class_cos(L, eps, ix->ccos, side1));
         if (!uniform)  // percentile ranges: offsets and tiles follow from n and m
@@ -495,7 +502,11 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                  ix->xnorm, st));
         B_CU(side_stream_wait(st, 0));  // A and A^T are ready
         // Eq. 4: sign random projection codes
-        if (!tc) {
+        if (split) {
+            B_CU(launch_finalize_codes(vsum, ix->perm, n, d, ix->dp, L, ix->Lp, ix->Xp, dtype,
+                                       ix->A_pad, ix->At32, ix->anorm, ix->tau64, ix->tau32,
+                                       ix->xnorm, ix->codes, ix->code_bytes, ix->ambiguous, st));
+        } else if (!tc) {
             B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
                                      ix->tau64, ix->tau32, ix->xnorm, ix->codes, ix->code_bytes,
                                      amb_list, ix->ambiguous, (unsigned)amb_cap, ix->At32, st));

@@ -126,15 +126,17 @@ cudaError_t launch_zero(const ZeroList& z, cudaStream_t st) {
 }
 
 // =====================================================================
-// Squared norms: s_x = sum_k x_k^2 exactly, rounded once to FP64.  A warp per
-// row; every x_k = M 2^E (M < 2^24) has x_k^2 = M^2 2^2E exactly.  The lanes
+// Squared norms: s_x = sum_k x_k^2 exactly, rounded once to FP64.  16 lanes per
+// row (rows of up to 512 values) or a warp per row; every x_k = M 2^E (M < 2^24)
+// has x_k^2 = M^2 2^2E exactly.  The lanes
 // add their terms into a 128-bit integer window [W0, W0 + 128) placed under the
-// row's largest term with bitlen(d) + 1 bits of headroom, so at least 53 bits
+// row's largest term with bitlen(d) + 1 bits of headroom, so 73 - bitlen(d) bits
 // lie below the result's rounding bit inside the window; bits of terms below
 // W0 are dropped and noted.  The dropped total is less than d units of 2^W0, so
 // it can change the rounding only if the kept remainder lies within d units
 // below the half-way point; such a row (none in practice; constructed tests
-// have them) is summed again exactly in a 576-bit accumulator by one lane.
+// have them) is summed again exactly in a 576-bit accumulator by one lane, and
+// so is a row whose values are all subnormal.
 // =====================================================================
 
 namespace {
@@ -150,6 +152,22 @@ __device__ __forceinline__ void f32_fields(float x, uint64_t& M2, int& E2) {
 }
 
 __device__ __forceinline__ int bitlen64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
+
+// 64-bit shifts whose amounts of 64 and more give 0 (the PTX shift semantics).
+__device__ __forceinline__ uint64_t shl_clamped(uint64_t a, uint32_t s) {
+    uint64_t r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "r"(s));
+    return r;
+}
+__device__ __forceinline__ uint64_t shr_clamped(uint64_t a, uint32_t s) {
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "r"(s));
+    return r;
+}
+// (hi:lo) += (h:l), 128-bit
+__device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t l, uint64_t h) {
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(l), "l"(h));
+}
 
 // The exact sum of the row's squares in 9 words (bit i of the array has weight
 // 2^(i - 298)), rounded to nearest even.  Slow; for ambiguous rows only.
@@ -229,6 +247,68 @@ struct RowGroups<__nv_bfloat16, 4> {
     }
 };
 
+// The window for a row whose largest |x_k| is amax (normal): x^2 = T 2^(W0 + t)
+// with T = M^2 2^16 and t = 2 max(e, 1) + tbase < 64.
+struct SqWindow {
+    int W0, tbase;
+};
+__device__ __forceinline__ SqWindow sq_window(float amax, int d) {
+    uint64_t M2m;
+    int E2m;
+    f32_fields(amax, M2m, E2m);
+    const int top = E2m + bitlen64(M2m);          // the largest term ends below 2^top
+    const int W0 = top + (32 - __clz(d)) + 1 - 128;
+    return {W0, -300 - W0 - 16};
+}
+
+// x^2 added into the 128-bit window (hi:lo); its bits below the window are ORed
+// into `dropped`.
+__device__ __forceinline__ void sq_add(float x, int tbase, uint64_t& lo, uint64_t& hi,
+                                       uint64_t& dropped) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xFFu, f = u & 0x7FFFFFu;
+    const uint32_t M8 = (e ? (f | 0x800000u) : f) << 8;   // M 2^8 < 2^32
+    const uint64_t T = (uint64_t)M8 * M8;                // M^2 2^16, exact
+    const int t = 2 * (int)max(e, 1u) + tbase;
+    const uint32_t tp = (uint32_t)max(t, 0), tn = (uint32_t)max(-t, 0);
+    const uint64_t l = shr_clamped(shl_clamped(T, tp), tn);
+    const uint64_t h = shr_clamped(T, 64u - tp);
+    dropped |= T & ~shl_clamped(~0ull, tn);
+    add128(lo, hi, l, h);
+}
+
+// The row's s_x from its reduced window: round A 2^W0 (plus the dropped bits) to
+// nearest even, or sum the row again exactly where the dropped bits could decide.
+template <typename T>
+__device__ double sq_finish(uint64_t lo, uint64_t hi, bool dropped, int W0, int d,
+                            const T* __restrict__ xr, unsigned* fallbacks) {
+    const u128 A = ((u128)hi << 64) | lo;
+    const int pos = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    const int cut = pos - 52;                 // >= 1: the bits below the mantissa
+    uint64_t mant = (uint64_t)(A >> cut);
+    const u128 rem = A & (((u128)1 << cut) - 1), half = (u128)1 << (cut - 1);
+    int ex = W0 + pos;
+    bool up;
+    if (rem > half) {
+        up = true;
+    } else if (rem == half) {
+        up = dropped || (mant & 1);
+    } else {
+        up = false;
+        if (dropped && half - rem <= (u128)d) {
+            atomicAdd(fallbacks, 1u);
+            return sqnorm_exact_slow(xr, d);
+        }
+    }
+    if (up && ++mant == (1ull << 53)) {
+        mant >>= 1;
+        ++ex;
+    }
+    return __longlong_as_double((long long)(((uint64_t)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+// Any row length: one warp per row, the row read twice (its maximum, then the
+// window sums).
 template <typename T, int VEC>
 __global__ void __launch_bounds__(256)
     sqnorm_kernel(const T* __restrict__ X, int64_t n, int d, int64_t ld, double* __restrict__ s,
@@ -250,83 +330,96 @@ __global__ void __launch_bounds__(256)
     }
     for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     double res = 0.0;
-    if (amax > 0.0f) {
-        uint64_t M2m;
-        int E2m;
-        f32_fields(amax, M2m, E2m);
-        const int top = E2m + bitlen64(M2m);          // the largest term ends below 2^top
-        const int W0 = top + (32 - __clz(d)) + 1 - 128;
-        uint64_t lo = 0, hi = 0;                      // the window, 2 x 64 bits
-        bool dropped = false;
+    if (amax > 0.0f && amax < 0x1p-126f) {   // every value subnormal: outside the window's range
+        if (lane == 0) {
+            atomicAdd(fallbacks, 1u);
+            res = sqnorm_exact_slow(xr, d);
+        }
+    } else if (amax > 0.0f) {
+        const SqWindow w = sq_window(amax, d);
+        uint64_t lo = 0, hi = 0, dropped = 0;
 #pragma unroll 4
         for (int g = lane; g < ng; g += 32) {
             float v[VEC];
             G::load(xr, g, v);
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) {
-                uint64_t M2;
-                int E2;
-                f32_fields(v[i], M2, E2);
-                if (!M2) continue;
-                const int sh = E2 - W0;               // < 80: the term ends inside
-                uint64_t l, h;
-                if (sh >= 64) {
-                    l = 0;
-                    h = M2 << (sh - 64);
-                } else if (sh > 0) {
-                    l = M2 << sh;
-                    h = M2 >> (64 - sh);
-                } else if (sh == 0) {
-                    l = M2;
-                    h = 0;
-                } else {
-                    const int r = -sh;
-                    l = r < 64 ? M2 >> r : 0;
-                    h = 0;
-                    dropped |= r >= 64 || (M2 << (64 - r)) != 0;
-                }
-                lo += l;
-                hi += h + (lo < l);
-            }
+            for (int i = 0; i < VEC; ++i) sq_add(v[i], w.tbase, lo, hi, dropped);
         }
         for (int o = 16; o; o >>= 1) {
             const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
             const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-            const uint64_t nlo = lo + olo;
-            hi = hi + ohi + (nlo < lo);
-            lo = nlo;
+            add128(lo, hi, olo, ohi);
         }
-        dropped = __any_sync(0xffffffffu, dropped);
-        if (lane == 0) {
-            const u128 A = ((u128)hi << 64) | lo;
-            const int pos = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-            const int cut = pos - 52;                 // >= 53: the bits below the mantissa
-            uint64_t mant = (uint64_t)(A >> cut);
-            const u128 rem = A & (((u128)1 << cut) - 1), half = (u128)1 << (cut - 1);
-            int ex = W0 + pos;
-            bool up, exact_needed = false;
-            if (rem > half) {
-                up = true;
-            } else if (rem == half) {
-                up = dropped || (mant & 1);
-            } else {
-                up = false;
-                exact_needed = dropped && half - rem <= (u128)d;
-            }
-            if (exact_needed) {
-                atomicAdd(fallbacks, 1u);
-                res = sqnorm_exact_slow(xr, d);
-            } else {
-                if (up && ++mant == (1ull << 53)) {
-                    mant >>= 1;
-                    ++ex;
-                }
-                res = __longlong_as_double(
-                    (long long)(((uint64_t)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1))));
-            }
-        }
+        const bool any_dropped = __any_sync(0xffffffffu, dropped != 0);
+        if (lane == 0) res = sq_finish(lo, hi, any_dropped, w.W0, d, xr, fallbacks);
     }
     if (lane == 0) {
+        s[row] = res;
+        if (keys) {
+            keys[row] = (uint64_t)__double_as_longlong(res);
+            vals[row] = (uint32_t)row;
+        }
+    }
+}
+
+// Rows of up to 16 NG VEC values: 16 lanes per row (two rows per warp), each lane
+// holding its NG groups in registers, so the row is read once with all its loads
+// in flight together.
+template <typename T, int VEC, int NG>
+__global__ void __launch_bounds__(256)
+    sqnorm_half_kernel(const T* __restrict__ X, int64_t n, int d, int64_t ld,
+                       double* __restrict__ s, uint64_t* keys, uint32_t* vals,
+                       unsigned* fallbacks) {
+    using G = RowGroups<T, VEC>;
+    const int lane = threadIdx.x & 31, li = lane & 15;
+    const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2;
+    if (row0 >= n) return;
+    const int64_t row = row0 + (lane >> 4);
+    const bool valid = row < n;
+    const T* xr = X + (valid ? row : row0) * ld;
+    const int ng = d / VEC;
+    float v[NG][VEC];
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+        const int g = li + 16 * j;
+        if (valid && g < ng) {
+            G::load(xr, g, v[j]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) v[j][i] = 0.0f;
+        }
+    }
+    float amax = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) amax = fmaxf(amax, fabsf(v[j][i]));
+    for (int o = 8; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    // both halves run the sums and reductions whatever their rows hold; a row with
+    // no normal value takes no window below
+    const SqWindow w = sq_window(fmaxf(amax, 0x1p-126f), d);
+    uint64_t lo = 0, hi = 0, dropped = 0;
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+        if (li + 16 * j < ng) {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) sq_add(v[j][i], w.tbase, lo, hi, dropped);
+        }
+    for (int o = 8; o; o >>= 1) {
+        const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const uint64_t odr = __shfl_xor_sync(0xffffffffu, dropped, o);
+        add128(lo, hi, olo, ohi);
+        dropped |= odr;
+    }
+    if (li == 0 && valid) {
+        double res = 0.0;
+        if (amax > 0.0f && amax < 0x1p-126f) {
+            atomicAdd(fallbacks, 1u);
+            res = sqnorm_exact_slow(xr, d);
+        } else if (amax > 0.0f) {
+            res = sq_finish(lo, hi, dropped != 0, w.W0, d, xr, fallbacks);
+        }
         s[row] = res;
         if (keys) {
             keys[row] = (uint64_t)__double_as_longlong(res);
@@ -344,6 +437,24 @@ cudaError_t launch_sqnorm(const void* X, nrlsh_dtype dt, int64_t n, int d, int64
     // (bf16) boundary and d is a multiple of 4
     const size_t esz = dt == NRLSH_BF16 ? 2 : 4;
     const bool vec = d % 4 == 0 && (ld * esz) % (4 * esz) == 0 && ((uintptr_t)X % (4 * esz)) == 0;
+    // rows of up to 512 values in four-value groups: 16 lanes per row
+    const int ng = d / 4;
+    const int NG = ng <= 32 ? 2 : ng <= 64 ? 4 : ng <= 128 ? 8 : 0;
+    if (vec && NG) {
+        const dim3 hgrid((unsigned)ceil_div(ceil_div(n, 2) * 32, 256));
+#define NRLSH_SQH(T_, NG_)                                                                  \
+    return launch("sqnorm_half", sqnorm_half_kernel<T_, 4, NG_>, hgrid, dim3(256), 0, st,    \
+                  (const T_*)X, n, d, ld, s, keys, vals, fallbacks);
+        if (dt == NRLSH_BF16) {
+            if (NG == 2) NRLSH_SQH(__nv_bfloat16, 2)
+            if (NG == 4) NRLSH_SQH(__nv_bfloat16, 4)
+            NRLSH_SQH(__nv_bfloat16, 8)
+        }
+        if (NG == 2) NRLSH_SQH(float, 2)
+        if (NG == 4) NRLSH_SQH(float, 4)
+        NRLSH_SQH(float, 8)
+#undef NRLSH_SQH
+    }
     if (dt == NRLSH_BF16) {
         if (vec)
             return launch("sqnorm_bf16", sqnorm_kernel<__nv_bfloat16, 4>, grid, dim3(256), 0, st,

@@ -152,6 +152,19 @@ cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
                                 void* codes, int code_bytes, unsigned long long* amb_list,
                                 unsigned* amb_count, unsigned amb_cap, const float* At32,
                                 cudaStream_t st);
+// The item projection in two parts (where the warp-per-row projection applies):
+// the FP32 sums a_b^T x of every item in id order (vsum: n x Lr floats, Lr = Lp
+// rounded up to 32), which need no partition and run beside it, then the signs
+// once tau is known, in storage order, each undecided bit settled in FP64 by the
+// position's warp (amb_count counts them; zeroed by the caller).
+bool split_projection_supported(int d, int Lp);
+cudaError_t launch_project_dots(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int Lp,
+                                const float* At32, float* vsum, cudaStream_t st);
+cudaError_t launch_finalize_codes(const float* vsum, const uint32_t* perm, int64_t n, int d, int dp,
+                                  int L, int Lp, const void* Xp, nrlsh_dtype dt, const float* A_pad,
+                                  const float* At32, const float* anorm, const double* tau64,
+                                  const float* tau32, const float* xnorm, void* codes,
+                                  int code_bytes, unsigned* amb_count, cudaStream_t st);
 // A^T for the warp-per-row projection (warp_proj_at_floats(d, Lp) floats; no-op
 // when that projection does not apply).
 int warp_proj_stride(int d, int Lp);

@@ -9,6 +9,7 @@
 #include "nrlsh_internal.cuh"
 
 #include <algorithm>
+#include <unordered_map>
 
 namespace nrlsh {
 
@@ -226,6 +227,150 @@ __global__ void __launch_bounds__(256)
 // 32 pass + l.  Any summation order satisfies the same FP32 bound.  The warp then
 // settles its row's undecided bits in FP64 itself, so no list or second launch
 // is needed (amb_count still counts them).
+// One pass of the warp-per-row projection: FP32 sums a_b^T x of bits 32 pass
+// .. 32 pass + 31 for ROWS rows held in registers (lane owns columns lane + 32 i),
+// A^T read from shared memory (row stride dpa) once for all rows, and a
+// transpose-reduction (31 shuffles) after which lane l holds bit 32 pass + l.
+template <int NREG, int ROWS>
+__device__ __forceinline__ void pass_sums(const float (&x)[ROWS][NREG], const float* At_s, int dpa,
+                                          int pass, int lane, float (&out)[ROWS][1]) {
+    float acc[ROWS][32];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        const float* ar = At_s + (pass * 32 + b) * dpa + lane;
+        float a[ROWS];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) a[r] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NREG; ++i) {
+            const float av = ar[32 * i];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) a[r] = fmaf(x[r][i], av, a[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) acc[r][b] = a[r];
+    }
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int j = 0; j < w; ++j)
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const float send = up ? acc[r][j] : acc[r][j + w];
+                const float keep = up ? acc[r][j + w] : acc[r][j];
+                acc[r][j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) out[r][0] = acc[r][0];
+}
+
+// The FP32 sums a_b^T x of every row and bit (no tail, no decision), in id order:
+// vsum[row Lr + b].  Run beside the partition; the signs are taken once tau is
+// known (finalize_codes_kernel).  A^T comes from the index's copy (At32).
+template <typename T, int NREG, int ROWS>
+__global__ void __launch_bounds__(256)
+    project_dots_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int Lp, int dpa,
+                        const float* __restrict__ At32, float* __restrict__ vsum) {
+    extern __shared__ __align__(16) float At_s[];
+    const int Lr = (Lp + 31) / 32 * 32;
+    for (int i = threadIdx.x; i < Lr * dpa / 4; i += blockDim.x)
+        ((float4*)At_s)[i] = ((const float4*)At32)[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * ROWS; row0 < n;
+         row0 += nwarps * ROWS) {
+        float x[ROWS][NREG];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+            for (int i = 0; i < NREG; ++i) {
+                const int k = lane + 32 * i;
+                x[r][i] = (row0 + r < n && k < d) ? to_f32(X[(row0 + r) * ldx + k]) : 0.0f;
+            }
+        for (int pass = 0; pass < Lr / 32; ++pass) {
+            float acc[ROWS][1];
+            pass_sums<NREG, ROWS>(x, At_s, dpa, pass, lane, acc);
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r)
+                if (row0 + r < n) vsum[(row0 + r) * Lr + pass * 32 + lane] = acc[r][0];
+        }
+    }
+}
+
+// Warp per storage position p: bit b = [fl(a_db tau + sum_b) >= 0] from the FP32
+// sum of its item (id perm[p]) and the FP32 tail, decided against the same bound
+// as the one-pass kernel.  The warp settles its undecided bits itself: an FP64
+// lane-strided sum over the row and A^T (both coalesced) within (2d + 8) 2^-53
+// (sum|a x| + |tail|) of the canonical in-order sum, and the canonical
+// sequential form by lane 0 only inside that bound.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    finalize_codes_kernel(const float* __restrict__ vsum, int Lr, const uint32_t* __restrict__ perm,
+                          int64_t n, int d, int ldx, int L, int Lp, int dpa,
+                          const T* __restrict__ Xp, const float* __restrict__ A_pad,
+                          const float* __restrict__ At32, const float* __restrict__ anorm,
+                          const double* __restrict__ tau64, const float* __restrict__ tau32,
+                          const float* __restrict__ xnorm, C* __restrict__ codes,
+                          unsigned* amb_count, float kappa) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= n) return;
+    const float* v = vsum + (int64_t)perm[p] * Lr;
+    const float xn = xnorm[p], t32 = tau32[p];
+    unsigned long long word = 0, undecided = 0;
+    for (int pass = 0; pass < Lr / 32; ++pass) {
+        const int b = pass * 32 + lane;
+        bool set = false, open = false;
+        if (b < L) {
+            const float ad = A_pad[(int64_t)d * Lp + b];
+            const float s = fmaf(ad, t32, v[b]);
+            const float bound = kappa * anorm[b] * xn + 0x1p-20f * fabsf(ad) * t32;
+            if (fabsf(s) * (1.0f - 0x1p-21f) > bound)
+                set = s > 0.0f;
+            else
+                open = true;
+        }
+        word |= (unsigned long long)__ballot_sync(0xffffffffu, set) << (32 * pass);
+        undecided |= (unsigned long long)__ballot_sync(0xffffffffu, open) << (32 * pass);
+    }
+    if (undecided) {
+        if (lane == 0) atomicAdd(amb_count, (unsigned)__popcll(undecided));
+        const T* xr = Xp + p * ldx;
+        const double tau = tau64[p];
+        for (unsigned long long u = undecided; u; u &= u - 1) {
+            const int b = __ffsll((long long)u) - 1;
+            const float* ar = At32 + (int64_t)b * dpa;
+            double sd = 0.0, sa = 0.0;
+#pragma unroll 4
+            for (int k = lane; k < d; k += 32) {
+                const double pr = (double)to_f32(xr[k]) * (double)ar[k];
+                sd += pr;
+                sa += fabs(pr);
+            }
+            for (int o = 16; o; o >>= 1) {
+                sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            }
+            const double tail = __dmul_rn((double)A_pad[(int64_t)d * Lp + b], tau);
+            const double val = __dadd_rn(sd, tail);
+            const double bound = (2.0 * d + 8.0) * 0x1p-53 * (sa + fabs(tail)) + 0x1p-50 * fabs(val);
+            bool set;
+            if (fabs(val) > bound) {
+                set = val > 0.0;
+            } else {
+                int r = 0;
+                if (lane == 0) r = project_bit_fp64(xr, A_pad, Lp, d, b, true, tau);
+                set = __shfl_sync(0xffffffffu, r, 0) != 0;
+            }
+            if (set) word |= 1ull << b;
+        }
+    }
+    if (lane == 0) codes[p] = (C)word;
+}
+
 template <typename T, int NREG, int ROWS>
 __global__ void __launch_bounds__(256)
     project_warp_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int L, int Lp, int dpa,
@@ -287,34 +432,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) word[r] = undecided[r] = 0;
         for (int pass = 0; pass < Lr / 32; ++pass) {
-            float acc[ROWS][32];
-#pragma unroll
-            for (int b = 0; b < 32; ++b) {
-                const float* ar = At_s + (pass * 32 + b) * dpa + lane;
-                float a[ROWS];
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) a[r] = 0.0f;
-#pragma unroll
-                for (int i = 0; i < NREG; ++i) {
-                    const float av = ar[32 * i];
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r) a[r] = fmaf(x[r][i], av, a[r]);
-                }
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) acc[r][b] = a[r];
-            }
-#pragma unroll
-            for (int w = 16; w >= 1; w >>= 1) {
-                const bool up = (lane & w) != 0;
-#pragma unroll
-                for (int j = 0; j < w; ++j)
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r) {
-                        const float send = up ? acc[r][j] : acc[r][j + w];
-                        const float keep = up ? acc[r][j + w] : acc[r][j];
-                        acc[r][j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-                    }
-            }
+            float acc[ROWS][1];
+            pass_sums<NREG, ROWS>(x, At_s, dpa, pass, lane, acc);
             const int bit = pass * 32 + lane;
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
@@ -564,6 +683,92 @@ cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
     return project_dispatch<float, uint64_t>(X, n, d, ldx, L, Lp, A_pad, anorm, tau64, tau32, xnorm,
                                              codes, amb_list, amb_count, amb_cap, st,
                                              "project_fp32", nullptr, At32);
+}
+
+namespace {
+
+// cudaFuncAttributeMaxDynamicSharedMemorySize raised as needed per kernel, device
+// and thread, and the blocks per SM at the last size asked.
+cudaError_t dyn_smem_blocks(const void* kern, size_t smem, int* per_sm) {
+    struct St {
+        int dev = -1;
+        size_t attr = 0, occ = 0;
+        int per_sm = 1;
+    };
+    static thread_local std::unordered_map<const void*, St> states;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    St& st = states[kern];
+    if (st.dev != dev) st = St{dev, 0, 0, 1};
+    if (smem > st.attr) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        st.attr = smem;
+    }
+    if (smem != st.occ) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&st.per_sm, kern, 256, smem);
+        if (e != cudaSuccess) return e;
+        st.per_sm = std::max(1, st.per_sm);
+        st.occ = smem;
+    }
+    *per_sm = st.per_sm;
+    return cudaSuccess;
+}
+
+template <typename T, int NREG, int ROWS>
+cudaError_t dots_launch(const void* X, int64_t n, int d, int ldx, int Lp, const float* At32,
+                        float* vsum, cudaStream_t st) {
+    const int Lr = (Lp + 31) / 32 * 32, dpa = NREG * 32;
+    const size_t smem = sizeof(float) * (size_t)Lr * dpa;
+    auto kern = project_dots_kernel<T, NREG, ROWS>;
+    int per_sm = 1;
+    cudaError_t e = dyn_smem_blocks((const void*)kern, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 8 * ROWS), (int64_t)per_sm * 152);
+    return launch("project_dots", kern, dim3(grid), dim3(256), smem, st, (const T*)X, n, d, ldx, Lp,
+                  dpa, At32, vsum);
+}
+
+}  // namespace
+
+bool split_projection_supported(int d, int Lp) { return warp_proj_stride(d, Lp) > 0; }
+
+cudaError_t launch_project_dots(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int Lp,
+                                const float* At32, float* vsum, cudaStream_t st) {
+    const int nreg_t = warp_proj_stride(d, Lp) / 32;
+    if (nreg_t == 0) return cudaErrorInvalidValue;
+#define NRLSH_DOTS(T_)                                                                      \
+    switch (nreg_t) {                                                                       \
+        case 4: return dots_launch<T_, 4, 2>(X, n, d, ldx, Lp, At32, vsum, st);             \
+        case 10: return dots_launch<T_, 10, 2>(X, n, d, ldx, Lp, At32, vsum, st);           \
+        default: return dots_launch<T_, 32, 1>(X, n, d, ldx, Lp, At32, vsum, st);           \
+    }
+    if (dt == NRLSH_BF16) NRLSH_DOTS(__nv_bfloat16)
+    NRLSH_DOTS(float)
+#undef NRLSH_DOTS
+}
+
+cudaError_t launch_finalize_codes(const float* vsum, const uint32_t* perm, int64_t n, int d, int dp,
+                                  int L, int Lp, const void* Xp, nrlsh_dtype dt, const float* A_pad,
+                                  const float* At32, const float* anorm, const double* tau64,
+                                  const float* tau32, const float* xnorm, void* codes,
+                                  int code_bytes, unsigned* amb_count, cudaStream_t st) {
+    const int Lr = (Lp + 31) / 32 * 32, dpa = warp_proj_stride(d, Lp);
+    if (dpa == 0) return cudaErrorInvalidValue;
+    const float kappa = (float)(d + 2) * 0x1p-22f;
+    const dim3 grid((unsigned)ceil_div(n * 32, 256));
+#define NRLSH_FIN(T_, C_)                                                                   \
+    return launch("finalize_codes", finalize_codes_kernel<T_, C_>, grid, dim3(256), 0, st, vsum, \
+                  Lr, perm, n, d, dp, L, Lp, dpa, (const T_*)Xp, A_pad, At32, anorm, tau64, tau32, \
+                  xnorm, (C_*)codes, amb_count, kappa);
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_FIN(__nv_bfloat16, uint32_t)
+        NRLSH_FIN(__nv_bfloat16, uint64_t)
+    }
+    if (code_bytes == 4) NRLSH_FIN(float, uint32_t)
+    NRLSH_FIN(float, uint64_t)
+#undef NRLSH_FIN
 }
 
 cudaError_t launch_hash_queries(const float* Q, int64_t nq, int d, int L, int Lp,

@@ -193,12 +193,14 @@ def test_wide_rows(d, L):
 
 
 def _window_tie_row(t, d=15):
-    """A row built for the squared-norm kernel's 128-bit window: W0 = top +
-    bitlen(d) + 1 - 128 with top = 1 for the term 1.0, so W0 = -122 for
-    8 <= d <= 15.  The in-window part is 1 + 2^-53 - 2^W0 (one unit below the
-    half-way point); t terms of 2^(W0 - 2) each (dropped by the window) decide it."""
+    """A row built for the squared-norm kernels' 128-bit window: W0 = top +
+    bitlen(d) + 1 - 128 with top = 1 for the term 1.0 (W0 = -122 for
+    8 <= d <= 15, even whenever bitlen(d) is).  The in-window part is
+    1 + 2^-53 - 2^W0 (one unit below the half-way point); t terms of 2^(W0 - 2)
+    each (dropped by the window) decide it."""
     import math
     W0 = 1 + d.bit_length() + 1 - 128
+    assert W0 % 2 == 0
     row = [1.0, 11863283 * 2.0 ** -50]
     rem = 4817239 * 2 ** (-100 - W0) - 1                # in units of 2^W0
     while rem > 0:
@@ -212,16 +214,27 @@ def _window_tie_row(t, d=15):
     return np.array(row, dtype=np.float32)
 
 
-def test_exact_squared_norms_and_the_slow_path():
+@pytest.mark.parametrize("d", [
+    15,     # a warp per row, one value per load
+    32,     # 16 lanes per row, 2 groups of 4 per lane
+    200,    # 16 lanes per row, 4 groups per lane
+    512,    # 16 lanes per row at its limit, 8 groups per lane
+    516,    # a warp per row, four values per load
+])
+def test_exact_squared_norms_and_the_slow_path(d):
     """s_x is the exact sum of squares rounded once: rows with a wide exponent
-    range, and rows built to land next to a rounding tie inside the kernel's
-    window (those take the exact slow path), against the oracle."""
+    range, rows of subnormal values (alone and beside normal ones), and rows built
+    to land next to a rounding tie inside the kernels' window (those take the
+    exact slow path), against the oracle."""
     from oracle import nrlsh as O
     import paper_1809_08782_gb300.nrlsh as N
-    rng = np.random.default_rng(77)
-    wide = (rng.standard_normal((500, 15)) * 2.0 ** rng.integers(-60, 60, (500, 15))).astype(np.float32)
-    ties = np.stack([_window_tie_row(t) for t in (0, 3, 4, 5, 9)] * 4)
-    items = np.concatenate([wide, ties, np.zeros((3, 15), np.float32)])
+    rng = np.random.default_rng(77 + d)
+    wide = (rng.standard_normal((500, d)) * 2.0 ** rng.integers(-60, 60, (500, d))).astype(np.float32)
+    ties = np.stack([_window_tie_row(t, d) for t in (0, 3, 4, 5, 9)] * 4)
+    sub = (rng.standard_normal((6, d)) * 2.0 ** -135).astype(np.float32)
+    sub[3:, 0] = 2.0 ** -125                                 # one normal value beside them
+    assert np.all(np.abs(sub[:3]) < 2.0 ** -126) and np.any(sub[:3] != 0)
+    items = np.concatenate([wide, ties, sub, np.zeros((3, d), np.float32)])
     s_ref = O.sq_norms(items.astype(np.float64))
     assert list(s_ref[500:505]) == [1.0, 1.0, 1.0, 1.0 + 2.0 ** -52, 1.0 + 2.0 ** -52]
     lib = N.nrlsh_build_ex(torch.from_numpy(items).cuda(), 4, 16, 3, eps=f32(0.2),
