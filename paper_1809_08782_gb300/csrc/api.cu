@@ -497,15 +497,32 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                  cudaMemcpyDeviceToDevice, st));
         }
         // Eq. 8 per sub-dataset: sub-dataset-major copy and tau = sqrt(U_j^2 - s)
+        // with the projection split, the gather takes the signs: it waits for the
+        // FP32 sums (side stream 0)
+        GatherCodes gc;
+        if (split) {
+            B_CU(side_stream_wait(st, 0));
+            gc.vsum = vsum;
+            gc.Lr = (ix->Lp + 31) / 32 * 32;
+            gc.d = d;
+            gc.L = L;
+            gc.Lp = ix->Lp;
+            gc.dpa = warp_proj_stride(d, ix->Lp);
+            gc.code_bytes = ix->code_bytes;
+            gc.A_pad = ix->A_pad;
+            gc.At32 = ix->At32;
+            gc.anorm = ix->anorm;
+            gc.codes = ix->codes;
+            gc.amb_count = ix->ambiguous;
+            gc.kappa = (float)(d + 2) * 0x1p-22f;
+        }
         B_CU(launch_gather_items(X, dtype, d, d, ix->dp, ix->perm, n, ix->sub_of_id, ix->s_id,
                                  ix->U2, ix->Xp, ix->Xb, ix->Xb2, ix->s_pos, ix->tau64, ix->tau32,
-                                 ix->xnorm, st));
+                                 ix->xnorm, gc, st));
         B_CU(side_stream_wait(st, 0));  // A and A^T are ready
         // Eq. 4: sign random projection codes
         if (split) {
-            B_CU(launch_finalize_codes(vsum, ix->perm, n, d, ix->dp, L, ix->Lp, ix->Xp, dtype,
-                                       ix->A_pad, ix->At32, ix->anorm, ix->tau64, ix->tau32,
-                                       ix->xnorm, ix->codes, ix->code_bytes, ix->ambiguous, st));
+            // the codes were taken in the gather
         } else if (!tc) {
             B_CU(launch_project_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
                                      ix->tau64, ix->tau32, ix->xnorm, ix->codes, ix->code_bytes,

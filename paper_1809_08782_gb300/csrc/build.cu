@@ -8,6 +8,7 @@
 //   project_fp32      sign(a^T [x; tau]) with an FP32 tier and an FP64 recompute
 //   bucket_order      the sorted (U_j, l) structure of Section 3.3
 #include "nrlsh_internal.cuh"
+#include "sign_tiers.cuh"
 
 #include <algorithm>
 #include <cfloat>
@@ -164,11 +165,6 @@ __device__ __forceinline__ uint64_t shr_clamped(uint64_t a, uint32_t s) {
     asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "r"(s));
     return r;
 }
-// (hi:lo) += (h:l), 128-bit
-__device__ __forceinline__ void add128(uint64_t& lo, uint64_t& hi, uint64_t l, uint64_t h) {
-    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(l), "l"(h));
-}
-
 // The exact sum of the row's squares in 9 words (bit i of the array has weight
 // 2^(i - 298)), rounded to nearest even.  Slow; for ambiguous rows only.
 template <typename T>
@@ -248,9 +244,12 @@ struct RowGroups<__nv_bfloat16, 4> {
 };
 
 // The window for a row whose largest |x_k| is amax (normal): x^2 = T 2^(W0 + t)
-// with T = M^2 2^16 and t = 2 max(e, 1) + tbase < 64.
+// with T = M^2 2^16 and t = 2 max(e, 1) + tbase < 64.  Values whose t is at least
+// 32 (all but values far below the row's largest) take the fast form; thr1 picks
+// out the others: 0 < |x| with t < 32, and subnormal values.
 struct SqWindow {
     int W0, tbase;
+    uint32_t thr1;
 };
 __device__ __forceinline__ SqWindow sq_window(float amax, int d) {
     uint64_t M2m;
@@ -258,30 +257,78 @@ __device__ __forceinline__ SqWindow sq_window(float amax, int d) {
     f32_fields(amax, M2m, E2m);
     const int top = E2m + bitlen64(M2m);          // the largest term ends below 2^top
     const int W0 = top + (32 - __clz(d)) + 1 - 128;
-    return {W0, -300 - W0 - 16};
+    const int tbase = -300 - W0 - 16;
+    const int e32 = max((33 - tbase) >> 1, 1);    // the least exponent field with t >= 32
+    return {W0, tbase, ((uint32_t)e32 << 23) - 1u};
 }
 
-// x^2 added into the 128-bit window (hi:lo); its bits below the window are ORed
-// into `dropped`.
-__device__ __forceinline__ void sq_add(float x, int tbase, uint64_t& lo, uint64_t& hi,
-                                       uint64_t& dropped) {
-    const uint32_t u = __float_as_uint(x);
-    const uint32_t e = (u >> 23) & 0xFFu, f = u & 0x7FFFFFu;
-    const uint32_t M8 = (e ? (f | 0x800000u) : f) << 8;   // M 2^8 < 2^32
-    const uint64_t T = (uint64_t)M8 * M8;                // M^2 2^16, exact
+// The 128-bit window as four 32-bit words, least significant first.
+struct SqAcc {
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+    uint64_t dropped = 0;
+};
+__device__ __forceinline__ void add4(SqAcc& a, uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3) {
+    asm("add.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, %5;\n\taddc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, %7;"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
+        : "r"(x0), "r"(x1), "r"(x2), "r"(x3));
+}
+
+// x^2 (bits u) for any t < 64: the window part (h:l) and the bits below it.
+struct SqTerm {
+    uint64_t l, h, dropped;
+};
+__device__ __noinline__ SqTerm sq_term_any(uint32_t u, int tbase) {
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint32_t M8 = (u << 8) | (e ? 0x80000000u : 0u);   // M 2^8 < 2^32
+    const uint64_t T = (uint64_t)M8 * M8;                    // M^2 2^16, exact
     const int t = 2 * (int)max(e, 1u) + tbase;
     const uint32_t tp = (uint32_t)max(t, 0), tn = (uint32_t)max(-t, 0);
-    const uint64_t l = shr_clamped(shl_clamped(T, tp), tn);
-    const uint64_t h = shr_clamped(T, 64u - tp);
-    dropped |= T & ~shl_clamped(~0ull, tn);
-    add128(lo, hi, l, h);
+    return {shr_clamped(shl_clamped(T, tp), tn), shr_clamped(T, 64u - tp),
+            T & ~shl_clamped(~0ull, tn)};
+}
+
+// x^2 added into the window: for t in [32, 64) the term T 2^(t - 32) spans the
+// words 1..3 (three funnel shifts and a three-word add); the rest go through sq_term_any.
+__device__ __forceinline__ void sq_add(float x, const SqWindow& w, SqAcc& a) {
+    const uint32_t u = __float_as_uint(x), mag = u & 0x7FFFFFFFu;
+    if (mag - 1u < w.thr1) {
+        const SqTerm r = sq_term_any(u, w.tbase);
+        a.dropped |= r.dropped;
+        add4(a, (uint32_t)r.l, (uint32_t)(r.l >> 32), (uint32_t)r.h, (uint32_t)(r.h >> 32));
+        return;
+    }
+    const uint32_t e = mag >> 23;                            // 0 only for x = 0 here
+    const uint32_t M8 = (u << 8) | (e ? 0x80000000u : 0u);
+    const uint64_t T = (uint64_t)M8 * M8;
+    const uint32_t T0 = (uint32_t)T, T1 = (uint32_t)(T >> 32);
+    const uint32_t sh = 2 * e + (uint32_t)(w.tbase - 32);    // t - 32 (mod 32 in the shifts)
+    const uint32_t x0 = __funnelshift_l(0u, T0, sh), x1 = __funnelshift_l(T0, T1, sh),
+                   x2 = __funnelshift_l(T1, 0u, sh);
+    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+        : "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
+        : "r"(x0), "r"(x1), "r"(x2));
+}
+
+// Sum of the windows of the lanes xor-paired up to `width` (a power of two).
+__device__ __forceinline__ void sq_reduce(SqAcc& a, int width) {
+    for (int o = width / 2; o; o >>= 1) {
+        const uint32_t x0 = __shfl_xor_sync(0xffffffffu, a.w0, o);
+        const uint32_t x1 = __shfl_xor_sync(0xffffffffu, a.w1, o);
+        const uint32_t x2 = __shfl_xor_sync(0xffffffffu, a.w2, o);
+        const uint32_t x3 = __shfl_xor_sync(0xffffffffu, a.w3, o);
+        a.dropped |= __shfl_xor_sync(0xffffffffu, a.dropped, o);
+        add4(a, x0, x1, x2, x3);
+    }
 }
 
 // The row's s_x from its reduced window: round A 2^W0 (plus the dropped bits) to
 // nearest even, or sum the row again exactly where the dropped bits could decide.
 template <typename T>
-__device__ double sq_finish(uint64_t lo, uint64_t hi, bool dropped, int W0, int d,
-                            const T* __restrict__ xr, unsigned* fallbacks) {
+__device__ double sq_finish(const SqAcc& acc, int W0, int d, const T* __restrict__ xr,
+                            unsigned* fallbacks) {
+    const uint64_t lo = ((uint64_t)acc.w1 << 32) | acc.w0, hi = ((uint64_t)acc.w3 << 32) | acc.w2;
+    const bool dropped = acc.dropped != 0;
     const u128 A = ((u128)hi << 64) | lo;
     const int pos = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
     const int cut = pos - 52;                 // >= 1: the bits below the mantissa
@@ -337,21 +384,16 @@ __global__ void __launch_bounds__(256)
         }
     } else if (amax > 0.0f) {
         const SqWindow w = sq_window(amax, d);
-        uint64_t lo = 0, hi = 0, dropped = 0;
+        SqAcc acc;
 #pragma unroll 4
         for (int g = lane; g < ng; g += 32) {
             float v[VEC];
             G::load(xr, g, v);
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) sq_add(v[i], w.tbase, lo, hi, dropped);
+            for (int i = 0; i < VEC; ++i) sq_add(v[i], w, acc);
         }
-        for (int o = 16; o; o >>= 1) {
-            const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
-            const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-            add128(lo, hi, olo, ohi);
-        }
-        const bool any_dropped = __any_sync(0xffffffffu, dropped != 0);
-        if (lane == 0) res = sq_finish(lo, hi, any_dropped, w.W0, d, xr, fallbacks);
+        sq_reduce(acc, 32);
+        if (lane == 0) res = sq_finish(acc, w.W0, d, xr, fallbacks);
     }
     if (lane == 0) {
         s[row] = res;
@@ -398,27 +440,21 @@ __global__ void __launch_bounds__(256)
     // both halves run the sums and reductions whatever their rows hold; a row with
     // no normal value takes no window below
     const SqWindow w = sq_window(fmaxf(amax, 0x1p-126f), d);
-    uint64_t lo = 0, hi = 0, dropped = 0;
+    SqAcc acc;
 #pragma unroll
     for (int j = 0; j < NG; ++j)
         if (li + 16 * j < ng) {
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) sq_add(v[j][i], w.tbase, lo, hi, dropped);
+            for (int i = 0; i < VEC; ++i) sq_add(v[j][i], w, acc);
         }
-    for (int o = 8; o; o >>= 1) {
-        const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o);
-        const uint64_t ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-        const uint64_t odr = __shfl_xor_sync(0xffffffffu, dropped, o);
-        add128(lo, hi, olo, ohi);
-        dropped |= odr;
-    }
+    sq_reduce(acc, 16);
     if (li == 0 && valid) {
         double res = 0.0;
         if (amax > 0.0f && amax < 0x1p-126f) {
             atomicAdd(fallbacks, 1u);
             res = sqnorm_exact_slow(xr, d);
         } else if (amax > 0.0f) {
-            res = sq_finish(lo, hi, dropped != 0, w.W0, d, xr, fallbacks);
+            res = sq_finish(acc, w.W0, d, xr, fallbacks);
         }
         s[row] = res;
         if (keys) {
@@ -1069,24 +1105,113 @@ __global__ void __launch_bounds__(1024)
     for (int64_t i = tiles_total + threadIdx.x; i < ntiles_max; i += 1024) tiles[i] = {0, 0, 0};
 }
 
-// Block of 256 threads per 32 storage positions: warp w copies rows w, w + 8, ...
-// (zero-padded to dp); then warp 0, lane i, writes position i's squared norm,
-// tau = sqrt(U_j^2 - s) (1 when U_j = 0) and an fp32 upper bound of ||x||, so
-// the FP64 square roots run on full warps.
-__device__ __forceinline__ void gather_tail(int64_t p, uint32_t id, const uint32_t* __restrict__ sub_of_id,
-                                            const double* __restrict__ s_id,
-                                            const double* __restrict__ U2, double* s_pos,
-                                            double* tau64, float* tau32, float* xnorm) {
+// Block of 256 threads per 32 storage positions.  Warp 0, lane i, first writes
+// position i's squared norm, tau = sqrt(U_j^2 - s) (1 when U_j = 0) and an fp32
+// upper bound of ||x||, so the FP64 square roots run on full warps; then warp w
+// copies rows w, w + 8, ... (zero-padded to dp) and, when the FP32 sums of the
+// item projection were computed beside the partition, decides the position's
+// code bits (code_of_position).
+struct GatherTail {
+    double tau;
+    float tau32, xn;
+};
+__device__ __forceinline__ GatherTail gather_tail(int64_t p, uint32_t id,
+                                                  const uint32_t* __restrict__ sub_of_id,
+                                                  const double* __restrict__ s_id,
+                                                  const double* __restrict__ U2, double* s_pos,
+                                                  double* tau64, float* tau32, float* xnorm) {
     const double s = s_id[id];
     const double u2 = U2[sub_of_id[id]];
     const double t = (u2 == 0.0) ? 1.0 : sqrt(u2 - s);
+    const float xn = __fsqrt_ru(__double2float_ru(s));
     s_pos[p] = s;
     tau64[p] = t;
     tau32[p] = (float)t;
-    xnorm[p] = __fsqrt_ru(__double2float_ru(s));
+    xnorm[p] = xn;
+    return {t, (float)t, xn};
 }
 
 constexpr int kGatherRows = 32;
+
+// Per block: the tails of its positions, and each lane's tail coefficient a_db and
+// ||a_b|| for bits b = lane and 32 + lane.
+struct GatherShared {
+    double tau64[kGatherRows];
+    float tau32[kGatherRows], xn[kGatherRows];
+};
+
+__device__ __forceinline__ void gather_prologue(const GatherCodes& gc, int64_t p0, int64_t n,
+                                                const uint32_t* __restrict__ perm,
+                                                const uint32_t* __restrict__ sub_of_id,
+                                                const double* __restrict__ s_id,
+                                                const double* __restrict__ U2, double* s_pos,
+                                                double* tau64, float* tau32, float* xnorm,
+                                                GatherShared& sh, float (&ad)[2], float (&an)[2]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0 && p0 + lane < n) {
+        const GatherTail t =
+            gather_tail(p0 + lane, perm[p0 + lane], sub_of_id, s_id, U2, s_pos, tau64, tau32, xnorm);
+        sh.tau64[lane] = t.tau;
+        sh.tau32[lane] = t.tau32;
+        sh.xn[lane] = t.xn;
+    }
+    if (gc.vsum) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int b = 32 * h + lane;
+            ad[h] = b < gc.L ? gc.A_pad[(int64_t)gc.d * gc.Lp + b] : 0.0f;
+            an[h] = b < gc.L ? gc.anorm[b] : 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+// Eq. 4 on the item of Eq. 8 at storage position p (item id, row src): bit b =
+// [fl(a_db tau + sum_b) >= 0] with sum_b the FP32 sum a_b^T x computed beside the
+// partition, decided where it lies outside (d + 2) 2^-22 ||a_b|| ||x|| + the tail's
+// rounding; the other bits are settled by the warp (settle_bit_warp).
+template <typename T>
+__device__ void code_of_position(const GatherCodes& gc, int64_t p, uint32_t id,
+                                 const T* __restrict__ src, const GatherShared& sh, int r,
+                                 const float (&ad)[2], const float (&an)[2]) {
+    const int lane = threadIdx.x & 31;
+    const float* v = gc.vsum + (int64_t)id * gc.Lr;
+    const float t32 = sh.tau32[r], xn = sh.xn[r];
+    unsigned long long word = 0, undecided = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (32 * h >= gc.Lr) break;
+        const int b = 32 * h + lane;
+        bool set = false, open = false;
+        if (b < gc.L) {
+            const float s = fmaf(ad[h], t32, v[b]);
+            const float bound = gc.kappa * an[h] * xn + 0x1p-20f * fabsf(ad[h]) * t32;
+            if (fabsf(s) * (1.0f - 0x1p-21f) > bound)
+                set = s > 0.0f;
+            else
+                open = true;
+        }
+        word |= (unsigned long long)__ballot_sync(0xffffffffu, set) << (32 * h);
+        undecided |= (unsigned long long)__ballot_sync(0xffffffffu, open) << (32 * h);
+    }
+    if (undecided) {
+        if (lane == 0) atomicAdd(gc.amb_count, (unsigned)__popcll(undecided));
+        for (unsigned long long u = undecided; u; u &= u - 1) {
+            const int b = __ffsll((long long)u) - 1;
+            const float adb = __shfl_sync(0xffffffffu, b < 32 ? ad[0] : ad[1], b & 31);
+            const float anb = __shfl_sync(0xffffffffu, b < 32 ? an[0] : an[1], b & 31);
+            if (settle_bit_warp(src, gc.d, gc.At32 + (int64_t)b * gc.dpa, adb, sh.tau64[r], true, xn,
+                                anb, gc.A_pad, gc.Lp, b))
+                word |= 1ull << b;
+        }
+    }
+    if (lane == 0) {
+        if (gc.code_bytes == 4)
+            static_cast<uint32_t*>(gc.codes)[p] = (uint32_t)word;
+        else
+            static_cast<uint64_t*>(gc.codes)[p] = word;
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -1095,13 +1220,18 @@ __global__ void __launch_bounds__(256)
                         const uint32_t* __restrict__ sub_of_id, const double* __restrict__ s_id,
                         const double* __restrict__ U2, T* __restrict__ Xp,
                         __nv_bfloat16* __restrict__ Xb, __nv_bfloat16* __restrict__ Xb2,
-                        double* s_pos, double* tau64, float* tau32, float* xnorm) {
+                        double* s_pos, double* tau64, float* tau32, float* xnorm,
+                        const GatherCodes gc) {
+    __shared__ GatherShared sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * kGatherRows;
+    float ad[2], an[2];
+    gather_prologue(gc, p0, n, perm, sub_of_id, s_id, U2, s_pos, tau64, tau32, xnorm, sh, ad, an);
     for (int r = warp; r < kGatherRows; r += 8) {
         const int64_t p = p0 + r;
         if (p >= n) break;
-        const T* src = X + (int64_t)perm[p] * ld;
+        const uint32_t id = perm[p];
+        const T* src = X + (int64_t)id * ld;
         T* dst = Xp + p * dp;
         for (int c = lane; c < dp; c += 32) {
             const T v = c < d ? src[c] : T(0.0f);
@@ -1113,9 +1243,8 @@ __global__ void __launch_bounds__(256)
                 if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(x - __bfloat162float(hi));
             }
         }
+        if (gc.vsum) code_of_position(gc, p, id, src, sh, r, ad, an);
     }
-    if (warp == 0 && p0 + lane < n)
-        gather_tail(p0 + lane, perm[p0 + lane], sub_of_id, s_id, U2, s_pos, tau64, tau32, xnorm);
 }
 
 // Vectorised form of gather_items_kernel for rows whose length d is a multiple
@@ -1153,17 +1282,21 @@ __global__ void __launch_bounds__(256)
                             const double* __restrict__ s_id, const double* __restrict__ U2,
                             T* __restrict__ Xp, __nv_bfloat16* __restrict__ Xb,
                             __nv_bfloat16* __restrict__ Xb2, double* s_pos, double* tau64,
-                            float* tau32, float* xnorm) {
+                            float* tau32, float* xnorm, const GatherCodes gc) {
     using GV = GatherVec<T>;
     using V = typename GV::V;
     constexpr int W = GV::W;
+    __shared__ GatherShared sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * kGatherRows;
+    float ad[2], an[2];
+    gather_prologue(gc, p0, n, perm, sub_of_id, s_id, U2, s_pos, tau64, tau32, xnorm, sh, ad, an);
     const int nv = d / W;
     for (int r = warp; r < kGatherRows; r += 8) {
         const int64_t p = p0 + r;
         if (p >= n) break;
-        const V* src = (const V*)(X + (int64_t)perm[p] * ld);
+        const uint32_t id = perm[p];
+        const V* src = (const V*)(X + (int64_t)id * ld);
         V* dst = (V*)(Xp + p * dp);
         for (int c = lane; c < nv; c += 32) {
             const V v = src[c];
@@ -1185,9 +1318,8 @@ __global__ void __launch_bounds__(256)
             if (Xb) Xb[p * dp + c] = __float2bfloat16_rn(0.0f);
             if (Xb2) Xb2[p * dp + c] = __float2bfloat16_rn(0.0f);
         }
+        if (gc.vsum) code_of_position(gc, p, id, X + (int64_t)id * ld, sh, r, ad, an);
     }
-    if (warp == 0 && p0 + lane < n)
-        gather_tail(p0 + lane, perm[p0 + lane], sub_of_id, s_id, U2, s_pos, tau64, tau32, xnorm);
 }
 
 }  // namespace
@@ -1228,26 +1360,28 @@ cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d
                                 const uint32_t* perm, int64_t n, const uint32_t* sub_of_id,
                                 const double* s_id, const double* U2, void* Xp,
                                 __nv_bfloat16* Xb, __nv_bfloat16* Xb2, double* s_pos,
-                                double* tau64, float* tau32, float* xnorm, cudaStream_t st) {
+                                double* tau64, float* tau32, float* xnorm, const GatherCodes& gc,
+                                cudaStream_t st) {
     const dim3 grid((unsigned)ceil_div(n, kGatherRows));
+    if (gc.vsum && (gc.Lr > 64 || gc.d != d)) return cudaErrorInvalidValue;
     if (dt == NRLSH_BF16) {
         if (d % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X & 3) == 0)
             return launch("gather_items_bf16", gather_items_vec_kernel<__nv_bfloat16>, grid,
                           dim3(256), 0, st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, sub_of_id,
                           s_id, U2, (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr,
-                          (__nv_bfloat16*)nullptr, s_pos, tau64, tau32, xnorm);
+                          (__nv_bfloat16*)nullptr, s_pos, tau64, tau32, xnorm, gc);
         return launch("gather_items_bf16", gather_items_kernel<__nv_bfloat16>, grid, dim3(256), 0,
                       st, (const __nv_bfloat16*)X, ld, d, dp, perm, n, sub_of_id, s_id, U2,
                       (__nv_bfloat16*)Xp, (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, s_pos,
-                      tau64, tau32, xnorm);
+                      tau64, tau32, xnorm, gc);
     }
     if (d % 4 == 0 && ld % 4 == 0 && ((uintptr_t)X & 15) == 0)
         return launch("gather_items_f32", gather_items_vec_kernel<float>, grid, dim3(256), 0, st,
                       (const float*)X, ld, d, dp, perm, n, sub_of_id, s_id, U2, (float*)Xp, Xb, Xb2,
-                      s_pos, tau64, tau32, xnorm);
+                      s_pos, tau64, tau32, xnorm, gc);
     return launch("gather_items_f32", gather_items_kernel<float>, grid, dim3(256), 0, st,
                   (const float*)X, ld, d, dp, perm, n, sub_of_id, s_id, U2, (float*)Xp, Xb, Xb2,
-                  s_pos, tau64, tau32, xnorm);
+                  s_pos, tau64, tau32, xnorm, gc);
 }
 
 // =====================================================================

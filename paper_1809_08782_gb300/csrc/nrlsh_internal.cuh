@@ -135,11 +135,25 @@ cudaError_t launch_uniform_assign(const double* s_id, int64_t n, int m, unsigned
 // (cnt, or with cnt null the percentile sizes of n items in m ranges).
 cudaError_t launch_segments(const uint32_t* cnt, int64_t n, int m, int64_t tile, int64_t* seg,
                             PosTile* tiles, int ntiles_max, cudaStream_t st);
+// Code decisions fused into the gather (vsum null: none).  vsum holds the FP32
+// sums a_b^T x of every item in id order (n x Lr floats, Lr = Lp rounded up to 32,
+// at most 64); At32 is A^T (Lr x dpa); undecided bits are counted in amb_count.
+struct GatherCodes {
+    const float* vsum = nullptr;
+    int Lr = 0, d = 0, L = 0, Lp = 0, dpa = 0, code_bytes = 4;
+    const float* A_pad = nullptr;
+    const float* At32 = nullptr;
+    const float* anorm = nullptr;
+    void* codes = nullptr;
+    unsigned* amb_count = nullptr;
+    float kappa = 0.0f;
+};
 cudaError_t launch_gather_items(const void* X, nrlsh_dtype dt, int64_t ld, int d, int dp,
                                 const uint32_t* perm, int64_t n, const uint32_t* sub_of_id,
                                 const double* s_id, const double* U2, void* Xp,
                                 __nv_bfloat16* Xb, __nv_bfloat16* Xb2, double* s_pos,
-                                double* tau64, float* tau32, float* xnorm, cudaStream_t st);
+                                double* tau64, float* tau32, float* xnorm, const GatherCodes& gc,
+                                cudaStream_t st);
 // Sign random projection of rows of X (row stride ldx, stored dtype) with the FP32
 // fast tier; undecided (row, bit) pairs go through amb_list (capacity amb_cap,
 // count in *amb_count, which must start at 0) to the FP64 resolve kernel.
@@ -154,17 +168,11 @@ cudaError_t launch_project_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
                                 cudaStream_t st);
 // The item projection in two parts (where the warp-per-row projection applies):
 // the FP32 sums a_b^T x of every item in id order (vsum: n x Lr floats, Lr = Lp
-// rounded up to 32), which need no partition and run beside it, then the signs
-// once tau is known, in storage order, each undecided bit settled in FP64 by the
-// position's warp (amb_count counts them; zeroed by the caller).
+// rounded up to 32), which need no partition and run beside it; the signs are
+// taken in the gather once tau is known (GatherCodes).
 bool split_projection_supported(int d, int Lp);
 cudaError_t launch_project_dots(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int Lp,
                                 const float* At32, float* vsum, cudaStream_t st);
-cudaError_t launch_finalize_codes(const float* vsum, const uint32_t* perm, int64_t n, int d, int dp,
-                                  int L, int Lp, const void* Xp, nrlsh_dtype dt, const float* A_pad,
-                                  const float* At32, const float* anorm, const double* tau64,
-                                  const float* tau32, const float* xnorm, void* codes,
-                                  int code_bytes, unsigned* amb_count, cudaStream_t st);
 // A^T for the warp-per-row projection (warp_proj_at_floats(d, Lp) floats; no-op
 // when that projection does not apply).
 int warp_proj_stride(int d, int Lp);

@@ -7,29 +7,17 @@
 //   resolve_fp32   warp per undecided (row, bit): FP32, lane-strided
 //   resolve_fp64   warp per undecided (row, bit): FP64, then the canonical order
 #include "nrlsh_internal.cuh"
+#include "sign_tiers.cuh"
 
 #include <algorithm>
 #include <unordered_map>
 
 namespace nrlsh {
 
-
 namespace {
 
 constexpr int kProjThreads = 256;  // 8 warps: warp w owns bit group w, lane owns rows
 constexpr int kProjKC = 32;        // columns of X staged per step
-
-// Bit b of row x, FP64 in the fixed order: sum_k a_kb x_k (k = 0..d-1) then
-// + fl(a_db * tau) for items.  This is the canonical definition of the bit.
-template <typename T>
-__device__ bool project_bit_fp64(const T* __restrict__ xrow, const float* __restrict__ A_pad,
-                                 int Lp, int d, int b, bool has_tail, double tau) {
-    double acc = 0.0;
-    for (int k = 0; k < d; ++k)
-        acc = fma((double)to_f32(xrow[k]), (double)A_pad[(int64_t)k * Lp + b], acc);
-    if (has_tail) acc = __dadd_rn(acc, __dmul_rn((double)A_pad[(int64_t)d * Lp + b], tau));
-    return acc >= 0.0;
-}
 
 // Block: 32 RI rows x Lp bits.  Warp w owns bits [w BT, (w+1) BT), lane owns rows
 // lane + 32 i (i < RI).  X and A are staged kProjKC columns at a time; every
@@ -111,7 +99,7 @@ __global__ void __launch_bounds__(kProjThreads)
                 const unsigned slot = atomicAdd(amb_count, 1u);
                 if (slot < amb_cap) {
                     amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
-                } else if (project_bit_fp64(X + row * ldx, A_pad, Lp, d, bit, has_tail,
+                } else if (project_bit_canonical(X + row * ldx, A_pad, Lp, d, bit, has_tail,
                                             has_tail ? tau64[row] : 0.0)) {
                     word |= 1ull << bit;
                 }
@@ -170,7 +158,7 @@ __global__ void __launch_bounds__(256)
         } else {
             int r = 0;
             if (lane == 0)
-                r = project_bit_fp64(xr, A_pad, Lp, d, bit, has_tail, has_tail ? tau64[row] : 0.0);
+                r = project_bit_canonical(xr, A_pad, Lp, d, bit, has_tail, has_tail ? tau64[row] : 0.0);
             set = __shfl_sync(0xffffffffu, r, 0) != 0;
         }
         if (lane == 0 && set) or_bit(codes + row, bit);
@@ -213,7 +201,7 @@ __global__ void __launch_bounds__(256)
                 const unsigned slot = atomicAdd(count2, 1u);
                 if (slot < cap2)
                     list2[slot] = entry;
-                else if (project_bit_fp64(xr, A_pad, Lp, d, bit, true, tau64[row]))
+                else if (project_bit_canonical(xr, A_pad, Lp, d, bit, true, tau64[row]))
                     or_bit(codes + row, bit);
             }
         }
@@ -298,77 +286,6 @@ __global__ void __launch_bounds__(256)
                 if (row0 + r < n) vsum[(row0 + r) * Lr + pass * 32 + lane] = acc[r][0];
         }
     }
-}
-
-// Warp per storage position p: bit b = [fl(a_db tau + sum_b) >= 0] from the FP32
-// sum of its item (id perm[p]) and the FP32 tail, decided against the same bound
-// as the one-pass kernel.  The warp settles its undecided bits itself: an FP64
-// lane-strided sum over the row and A^T (both coalesced) within (2d + 8) 2^-53
-// (sum|a x| + |tail|) of the canonical in-order sum, and the canonical
-// sequential form by lane 0 only inside that bound.
-template <typename T, typename C>
-__global__ void __launch_bounds__(256)
-    finalize_codes_kernel(const float* __restrict__ vsum, int Lr, const uint32_t* __restrict__ perm,
-                          int64_t n, int d, int ldx, int L, int Lp, int dpa,
-                          const T* __restrict__ Xp, const float* __restrict__ A_pad,
-                          const float* __restrict__ At32, const float* __restrict__ anorm,
-                          const double* __restrict__ tau64, const float* __restrict__ tau32,
-                          const float* __restrict__ xnorm, C* __restrict__ codes,
-                          unsigned* amb_count, float kappa) {
-    const int lane = threadIdx.x & 31;
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (p >= n) return;
-    const float* v = vsum + (int64_t)perm[p] * Lr;
-    const float xn = xnorm[p], t32 = tau32[p];
-    unsigned long long word = 0, undecided = 0;
-    for (int pass = 0; pass < Lr / 32; ++pass) {
-        const int b = pass * 32 + lane;
-        bool set = false, open = false;
-        if (b < L) {
-            const float ad = A_pad[(int64_t)d * Lp + b];
-            const float s = fmaf(ad, t32, v[b]);
-            const float bound = kappa * anorm[b] * xn + 0x1p-20f * fabsf(ad) * t32;
-            if (fabsf(s) * (1.0f - 0x1p-21f) > bound)
-                set = s > 0.0f;
-            else
-                open = true;
-        }
-        word |= (unsigned long long)__ballot_sync(0xffffffffu, set) << (32 * pass);
-        undecided |= (unsigned long long)__ballot_sync(0xffffffffu, open) << (32 * pass);
-    }
-    if (undecided) {
-        if (lane == 0) atomicAdd(amb_count, (unsigned)__popcll(undecided));
-        const T* xr = Xp + p * ldx;
-        const double tau = tau64[p];
-        for (unsigned long long u = undecided; u; u &= u - 1) {
-            const int b = __ffsll((long long)u) - 1;
-            const float* ar = At32 + (int64_t)b * dpa;
-            double sd = 0.0, sa = 0.0;
-#pragma unroll 4
-            for (int k = lane; k < d; k += 32) {
-                const double pr = (double)to_f32(xr[k]) * (double)ar[k];
-                sd += pr;
-                sa += fabs(pr);
-            }
-            for (int o = 16; o; o >>= 1) {
-                sd += __shfl_xor_sync(0xffffffffu, sd, o);
-                sa += __shfl_xor_sync(0xffffffffu, sa, o);
-            }
-            const double tail = __dmul_rn((double)A_pad[(int64_t)d * Lp + b], tau);
-            const double val = __dadd_rn(sd, tail);
-            const double bound = (2.0 * d + 8.0) * 0x1p-53 * (sa + fabs(tail)) + 0x1p-50 * fabs(val);
-            bool set;
-            if (fabs(val) > bound) {
-                set = val > 0.0;
-            } else {
-                int r = 0;
-                if (lane == 0) r = project_bit_fp64(xr, A_pad, Lp, d, b, true, tau);
-                set = __shfl_sync(0xffffffffu, r, 0) != 0;
-            }
-            if (set) word |= 1ull << b;
-        }
-    }
-    if (lane == 0) codes[p] = (C)word;
 }
 
 template <typename T, int NREG, int ROWS>
@@ -457,15 +374,28 @@ __global__ void __launch_bounds__(256)
             const int64_t row = row0 + r;
             if (row >= n) break;
             // undecided bits, decided by this warp with the row still in registers:
-            // an FP64 lane-strided sum and a tree (within (2d + 8) 2^-53 (sum|a x| +
-            // |tail|) of the canonical in-order sum, as in resolve_kernel), and the
-            // canonical sequential form by lane 0 only inside that bound
+            // the compensated FP32 tier (dot2_decides), then an FP64 lane-strided sum
+            // and a tree (within (2d + 8) 2^-53 (sum|a x| + |tail|) of the canonical
+            // in-order sum, as in resolve_kernel), and the canonical sequential form
+            // by lane 0 only inside that bound
             if (undecided[r]) {
                 if (lane == 0 && amb_count) atomicAdd(amb_count, (unsigned)__popcll(undecided[r]));
                 const double tau = has_tail ? tau64[row] : 0.0;
                 for (unsigned long long u = undecided[r]; u; u &= u - 1) {
                     const int b = __ffsll((long long)u) - 1;
                     const float* ar = At_s + b * dpa + lane;
+                    {
+                        float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < NREG; ++i) dot2_step(x[r][i], ar[32 * i], sh, sl);
+                        dot2_warp_reduce(sh, sl);
+                        const double tail1 = has_tail ? __dmul_rn((double)ad_s[b], tau) : 0.0;
+                        bool set1;
+                        if (dot2_decides(sh, sl, tail1, NREG, d, xn[r], an_s[b], set1)) {
+                            if (set1) word[r] |= 1ull << b;
+                            continue;
+                        }
+                    }
                     double sd = 0.0, sa = 0.0;
 #pragma unroll
                     for (int i = 0; i < NREG; ++i) {
@@ -487,7 +417,7 @@ __global__ void __launch_bounds__(256)
                     } else {
                         int rr = 0;
                         if (lane == 0)
-                            rr = project_bit_fp64(X + row * ldx, A_pad, Lp, d, b, has_tail, tau);
+                            rr = project_bit_canonical(X + row * ldx, A_pad, Lp, d, b, has_tail, tau);
                         set = __shfl_sync(0xffffffffu, rr, 0) != 0;
                     }
                     if (set) word[r] |= 1ull << b;
@@ -747,28 +677,6 @@ cudaError_t launch_project_dots(const void* X, nrlsh_dtype dt, int64_t n, int d,
     if (dt == NRLSH_BF16) NRLSH_DOTS(__nv_bfloat16)
     NRLSH_DOTS(float)
 #undef NRLSH_DOTS
-}
-
-cudaError_t launch_finalize_codes(const float* vsum, const uint32_t* perm, int64_t n, int d, int dp,
-                                  int L, int Lp, const void* Xp, nrlsh_dtype dt, const float* A_pad,
-                                  const float* At32, const float* anorm, const double* tau64,
-                                  const float* tau32, const float* xnorm, void* codes,
-                                  int code_bytes, unsigned* amb_count, cudaStream_t st) {
-    const int Lr = (Lp + 31) / 32 * 32, dpa = warp_proj_stride(d, Lp);
-    if (dpa == 0) return cudaErrorInvalidValue;
-    const float kappa = (float)(d + 2) * 0x1p-22f;
-    const dim3 grid((unsigned)ceil_div(n * 32, 256));
-#define NRLSH_FIN(T_, C_)                                                                   \
-    return launch("finalize_codes", finalize_codes_kernel<T_, C_>, grid, dim3(256), 0, st, vsum, \
-                  Lr, perm, n, d, dp, L, Lp, dpa, (const T_*)Xp, A_pad, At32, anorm, tau64, tau32, \
-                  xnorm, (C_*)codes, amb_count, kappa);
-    if (dt == NRLSH_BF16) {
-        if (code_bytes == 4) NRLSH_FIN(__nv_bfloat16, uint32_t)
-        NRLSH_FIN(__nv_bfloat16, uint64_t)
-    }
-    if (code_bytes == 4) NRLSH_FIN(float, uint32_t)
-    NRLSH_FIN(float, uint64_t)
-#undef NRLSH_FIN
 }
 
 cudaError_t launch_hash_queries(const float* Q, int64_t nq, int d, int L, int Lp,

@@ -8,6 +8,7 @@
 //   topk             exact top-k: radix-select on the lower bounds, FP64 rescoring
 //                    of the contenders, (score desc, id asc) selection
 #include "nrlsh_internal.cuh"
+#include "sign_tiers.cuh"
 
 #include <unordered_map>
 #include <utility>
@@ -541,18 +542,6 @@ __device__ void select_digit(const uint32_t* hist, int rem, int* dg_out, int* re
 constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
 constexpr int kDot2Max = 512;        // contenders scored by the compensated FP32 tier
 
-// One lane's part of the compensated dot product (Ogita, Rump, Oishi 2005):
-// TwoProduct by fma and TwoSum for each of its terms in order; terms are taken
-// lane-strided in groups of 4 (fp32, one 16-byte load) or 8 (bf16).
-__device__ __forceinline__ void dot2_step(float x, float y, float& sh, float& sl) {
-    const float pr = __fmul_rn(x, y);
-    const float er = fmaf(x, y, -pr);            // pr + er = x y exactly
-    const float s2 = __fadd_rn(sh, pr);          // TwoSum(sh, pr)
-    const float bb = __fsub_rn(s2, sh);
-    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(pr, bb));
-    sh = s2;
-    sl = __fadd_rn(__fadd_rn(sl, t), er);
-}
 template <typename T> struct RowDot2;
 template <> struct RowDot2<float> {
     __device__ static void dot(const float* xr, const float* qs, int dp, int lane, float& sh,

@@ -242,3 +242,49 @@ def test_exact_squared_norms_and_the_slow_path(d):
     _, _, s = N.nrlsh_get_partition(lib)
     assert np.array_equal(s.numpy(), s_ref)
     assert N.nrlsh_get_info(lib)["norm_fallbacks"] >= 12   # the tie rows with t > 0
+
+
+def _hyperplane_queries(A, d, bits, seed):
+    """Queries on and next to the hyperplanes a_b^T q = 0 (Eq. 4 with P(q) = [q; 0]):
+    q_k1 = a_k2b, q_k2 = -a_k1b (bf16 values, so q^T a_b = 0 exactly) plus
+    delta at k3 > k2 with |delta a_k3b| = r ||q|| ||a_b||.  r = 0 and 2^-60 reach the
+    canonical sequential sum, 2^-42 the FP64 tier, 2^-30 the compensated FP32
+    tier; in-order partial sums are exact here, so the canonical sign is the
+    exact one."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for b in bits:
+        for r in (0.0, 2.0 ** -60, 2.0 ** -42, 2.0 ** -30):
+            for sign in (1.0, -1.0):
+                k1, k2, k3 = sorted(rng.choice(d, 3, replace=False))
+                q = np.zeros(d)
+                q[k1], q[k2] = A[k2, b], -A[k1, b]
+                scale = np.linalg.norm(q) * np.linalg.norm(A[:d, b])
+                q[k3] = np.float32(sign * r * scale / A[k3, b])
+                rows.append(q)
+    return np.array(rows, dtype=np.float32)
+
+
+@pytest.mark.parametrize("proj", [SIMT, TENSOR])
+def test_code_bits_on_and_near_the_hyperplanes(proj):
+    """Bits that only the later precision tiers can decide: query codes on and
+    next to a_b^T q = 0, and an item with a_b^T x = 0 exactly and tau = 0 (the
+    largest norm, so U = ||x||): its canonical value is 0 and the bit is 1."""
+    import paper_1809_08782_gb300.nrlsh as N
+    from oracle import nrlsh as O, philox
+    d, L, seed = 40, 32, 9
+    A = philox.projections(seed, d, L)
+    items = rand_items(300, d, 5)
+    planted = np.zeros(d, np.float32)
+    planted[3], planted[17] = A[17, 0] * 64.0, -A[3, 0] * 64.0
+    assert np.linalg.norm(planted) > np.linalg.norm(items, axis=1).max()
+    items = np.concatenate([items, planted[None, :]])
+    lib, ref = build_pair(items, "f32", 4, L, seed, 0.2, projection=proj)
+    assert np.array_equal(ref.A, A)
+    check_index(lib, ref, proj)
+    assert int(ref.codes[300]) & 1                       # canonical value 0 -> bit 1
+    Q = _hyperplane_queries(A, d, [0, 5, 31], 11)
+    got = N.nrlsh_hash_queries(lib, torch.from_numpy(Q).cuda()).cpu().numpy().view(np.uint64)
+    want = O.query_codes(Q.astype(np.float64), A)
+    assert np.array_equal(got, want)
+    check_queries(lib, ref, Q, 5, 120)

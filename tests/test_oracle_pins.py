@@ -516,3 +516,25 @@ def test_workload_generator_shapes_and_determinism():
     assert wb.items.dtype == np.uint16
     x = W.items_to_f64(wb.items, "bf16")
     assert np.all(np.linalg.norm(x, axis=1) >= 0.99)      # Pareto norms are >= 1
+
+
+def test_query_code_bits_on_the_hyperplanes_are_exact_signs():
+    """Eq. 4 on P(q) = [q; 0] at and next to a_b^T q = 0: queries whose in-order
+    partial sums are exact, so the canonical FP64 sum has the sign of the exact
+    rational value, [0 >= 0] = 1 included."""
+    d, L = 40, 32
+    A = philox.projections(9, d, L)
+    rng = np.random.default_rng(11)
+    for b in (0, 5, 31):
+        for r in (0.0, 2.0 ** -60, 2.0 ** -42, 2.0 ** -30):
+            for sign in (1.0, -1.0):
+                k1, k2, k3 = sorted(rng.choice(d, 3, replace=False))
+                q = np.zeros(d)
+                q[k1], q[k2] = A[k2, b], -A[k1, b]
+                scale = np.linalg.norm(q) * np.linalg.norm(A[:d, b])
+                q[k3] = np.float32(sign * r * scale / A[k3, b])
+                exact_val = sum(Fraction(float(q[k])) * Fraction(float(A[k, b])) for k in range(d))
+                bit = (int(O.query_codes(q[None, :], A)[0]) >> b) & 1
+                assert bit == int(exact_val >= 0), (b, r, sign)
+                if r == 0.0:
+                    assert exact_val == 0 and bit == 1
