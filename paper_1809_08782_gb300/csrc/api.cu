@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -115,6 +116,16 @@ nrlsh_status cuda_status(cudaError_t e, const char* what) {
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Programmatic dependent launches are on unless NRLSH_NO_PDL is set (to 1) in the
+// environment when the library first launches a kernel.
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("NRLSH_NO_PDL");
+        return !(v && v[0] == '1');
+    }();
+    return on;
+}
 
 void prof_begin(const char*, cudaStream_t s) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
@@ -573,6 +584,7 @@ struct QueryOut {
 enum class Stage { Hash, Hist, Cand, TopK };
 
 __global__ void widen_codes_kernel(const uint32_t* in, uint64_t* out, int64_t nq) {
+    NRLSH_PDL_ENTRY();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nq) out[i] = in[i];
 }
@@ -611,10 +623,8 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
             if (ix->code_bytes == 8) {
                 NRLSH_CK(cudaMemcpyAsync(o.codes + q0, qcodes, 8 * qc, cudaMemcpyDeviceToDevice, st));
             } else {
-                count_launch();
-                widen_codes_kernel<<<(unsigned)ceil_div(qc, 256), 256, 0, st>>>(
-                    (const uint32_t*)qcodes, o.codes + q0, qc);
-                NRLSH_CK(cudaGetLastError());
+                NRLSH_CK(launch("widen_codes", widen_codes_kernel, dim3((unsigned)ceil_div(qc, 256)),
+                                dim3(256), 0, st, (const uint32_t*)qcodes, o.codes + q0, qc));
             }
             continue;
         }

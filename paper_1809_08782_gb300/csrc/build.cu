@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256)
     projections_kernel(float* __restrict__ A, float* __restrict__ A_pad, float* __restrict__ anorm,
                        __nv_bfloat16* __restrict__ At, int dp, int d, int L, int Lp,
                        uint64_t seed) {
+    NRLSH_PDL_ENTRY();
     __shared__ double part[8];
     const int b = blockIdx.x;
     double ss = 0.0;
@@ -108,6 +109,7 @@ cudaError_t launch_projections(float* A, float* A_pad, float* anorm, __nv_bfloat
 namespace {
 
 __global__ void zero_kernel(ZeroList z) {
+    NRLSH_PDL_ENTRY();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int i = 0; i < z.k; ++i) {
         uint32_t* p = (uint32_t*)z.p[i];
@@ -360,6 +362,7 @@ template <typename T, int VEC>
 __global__ void __launch_bounds__(256)
     sqnorm_kernel(const T* __restrict__ X, int64_t n, int d, int64_t ld, double* __restrict__ s,
                   uint64_t* keys, uint32_t* vals, unsigned* fallbacks) {
+    NRLSH_PDL_ENTRY();
     using G = RowGroups<T, VEC>;
     const int lane = threadIdx.x & 31;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -412,6 +415,7 @@ __global__ void __launch_bounds__(256)
     sqnorm_half_kernel(const T* __restrict__ X, int64_t n, int d, int64_t ld,
                        double* __restrict__ s, uint64_t* keys, uint32_t* vals,
                        unsigned* fallbacks) {
+    NRLSH_PDL_ENTRY();
     using G = RowGroups<T, VEC>;
     const int lane = threadIdx.x & 31, li = lane & 15;
     const int64_t row0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2;
@@ -532,6 +536,7 @@ template <typename K, int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads)
     radix_first_hist_kernel(const K* __restrict__ keys, int64_t n, unsigned long long* varying,
                             uint32_t* __restrict__ counts, int ntiles) {
+    NRLSH_PDL_ENTRY();
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -559,6 +564,7 @@ __global__ void __launch_bounds__(kSortThreads)
 __global__ void __launch_bounds__(1024)
     radix_scan_kernel(uint32_t* counts, int64_t total, int shift, uint32_t* next_counts,
                       int next_shift, const unsigned long long* varying) {
+    NRLSH_PDL_ENTRY();
     if (!digit_varies(varying, shift)) return;
     if (next_counts && digit_varies(varying, next_shift))
         for (int64_t i = threadIdx.x; i < total; i += 1024) next_counts[i] = 0;
@@ -603,6 +609,7 @@ __global__ void __launch_bounds__(kSortThreads)
                          const unsigned long long* varying, const uint32_t* __restrict__ offsets,
                          int ntiles, uint32_t* __restrict__ next_counts, int next_shift,
                          int local_offsets, uint32_t* __restrict__ zero) {
+    NRLSH_PDL_ENTRY();
     constexpr int kTile = kSortThreads * ROUNDS;
     const int64_t base = (int64_t)blockIdx.x * kTile;
     const bool count_next = next_counts != nullptr && digit_varies(varying, next_shift);
@@ -799,6 +806,7 @@ __device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ia, uint64_t kb, 
 // warp shuffles, wider ones through shared memory).
 __global__ void __launch_bounds__(kRankTile)
     tile_sort_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ ids, int64_t n) {
+    NRLSH_PDL_ENTRY();
     __shared__ uint64_t k_s[kRankTile];
     __shared__ uint32_t i_s[kRankTile];
     const int t = threadIdx.x;
@@ -842,6 +850,7 @@ __global__ void __launch_bounds__(kRankTile)
 __global__ void __launch_bounds__(512)
     tile_rank_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ ids, int64_t n,
                      unsigned* __restrict__ rank) {
+    NRLSH_PDL_ENTRY();
     __shared__ uint64_t k_s[kRankTile];
     __shared__ uint32_t i_s[kRankTile];
     const int64_t tb = (int64_t)blockIdx.x * kRankTile, ub = (int64_t)blockIdx.y * kRankTile;
@@ -879,6 +888,7 @@ __global__ void __launch_bounds__(256)
                       const unsigned* __restrict__ rank, int64_t n, int m, int64_t W,
                       uint32_t* __restrict__ bitmap, uint32_t* __restrict__ sub_of_id,
                       double* __restrict__ U2) {
+    NRLSH_PDL_ENTRY();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int64_t r = rank[e];
@@ -894,6 +904,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     range_order_kernel(const uint32_t* __restrict__ bitmap, int64_t n, int m, int64_t W,
                        uint32_t* __restrict__ perm) {
+    NRLSH_PDL_ENTRY();
     __shared__ uint32_t wsum[8];
     __shared__ uint32_t carry_s;
     const int j = blockIdx.x;
@@ -968,6 +979,7 @@ __global__ void segment_assign_kernel(const uint64_t* __restrict__ sorted_keys,
                                       const uint32_t* __restrict__ sorted_ids, int64_t n, int m,
                                       uint32_t* sub_of_id, double* U2, uint32_t* jkeys,
                                       uint32_t* jvals) {
+    NRLSH_PDL_ENTRY();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int32_t j = seg_of(r, n, m);
@@ -990,6 +1002,7 @@ __global__ void segment_assign_kernel(const uint64_t* __restrict__ sorted_keys,
 __global__ void __launch_bounds__(256)
     norm_range_kernel(const double* __restrict__ s, int64_t n, unsigned long long* range,
                       unsigned* done) {
+    NRLSH_PDL_ENTRY();
     unsigned long long lo = ~0ull, hi = 0ull;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -1030,6 +1043,7 @@ __global__ void __launch_bounds__(256)
                           const unsigned long long* __restrict__ range, uint32_t* sub_of_id,
                           unsigned long long* U2_bits, uint32_t* jkeys, uint32_t* jvals,
                           uint32_t* cnt) {
+    NRLSH_PDL_ENTRY();
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n) return;
     const double s = s_id[id] + 0.0;
@@ -1080,6 +1094,7 @@ __device__ int64_t block_scan_1024(int64_t v, int64_t* total, int64_t* wsum) {
 __global__ void __launch_bounds__(1024)
     segments_kernel(const uint32_t* __restrict__ cnt, int64_t n, int m, int64_t tile, int64_t* seg,
                     PosTile* tiles, int ntiles_max) {
+    NRLSH_PDL_ENTRY();
     __shared__ int64_t wsum[32];
     const int per = (m + 1023) / 1024;
     const int b = min(m, (int)threadIdx.x * per), e = min(m, b + per);
@@ -1222,6 +1237,7 @@ __global__ void __launch_bounds__(256)
                         __nv_bfloat16* __restrict__ Xb, __nv_bfloat16* __restrict__ Xb2,
                         double* s_pos, double* tau64, float* tau32, float* xnorm,
                         const GatherCodes gc) {
+    NRLSH_PDL_ENTRY();
     __shared__ GatherShared sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * kGatherRows;
@@ -1283,6 +1299,7 @@ __global__ void __launch_bounds__(256)
                             T* __restrict__ Xp, __nv_bfloat16* __restrict__ Xb,
                             __nv_bfloat16* __restrict__ Xb2, double* s_pos, double* tau64,
                             float* tau32, float* xnorm, const GatherCodes gc) {
+    NRLSH_PDL_ENTRY();
     using GV = GatherVec<T>;
     using V = typename GV::V;
     constexpr int W = GV::W;
@@ -1527,6 +1544,7 @@ constexpr int kBucketThreads = 256;
 // c_l for l = 0..L (one thread each); independent of the data, so the build
 // runs it on a side stream beside the norms and the sort.
 __global__ void class_cos_kernel(int L, float eps, double* __restrict__ cl) {
+    NRLSH_PDL_ENTRY();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l <= L) cl[l] = cos_class(L, l, (double)eps);
 }
@@ -1537,6 +1555,7 @@ __global__ void class_cos_kernel(int L, float eps, double* __restrict__ cl) {
 __global__ void bucket_keys_kernel(const double* __restrict__ U2, const double* __restrict__ cl,
                                    int m, int L, unsigned long long* __restrict__ keys,
                                    uint32_t* __restrict__ tie) {
+    NRLSH_PDL_ENTRY();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m * (L + 1)) return;
     const int j = c / (L + 1), l = c % (L + 1);
@@ -1555,6 +1574,7 @@ __global__ void __launch_bounds__(kBucketThreads)
                        double* __restrict__ shat_sorted, uint32_t* __restrict__ order,
                        const double* __restrict__ U2, const double* __restrict__ cl_g, int m,
                        int L) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ unsigned long long keys[];
     uint32_t* tie = (uint32_t*)(keys + ncls);
     if (keys_g) {

@@ -33,10 +33,20 @@ nrlsh_status cuda_status(cudaError_t e, const char* what);
 // ------------------------------------------------------- launch accounting
 
 // Every kernel goes through launch(): it counts the launch and, when
-// profiling is on, brackets it with CUDA events on its stream.
+// profiling is on, brackets it with CUDA events on its stream.  Kernels are
+// launched as programmatic dependents of their predecessor on the stream: a
+// kernel may be scheduled while the previous one drains, and waits at its
+// entry (NRLSH_PDL_ENTRY) until that grid has completed and its writes are
+// visible, so the launch latency between dependent kernels is hidden.
 void prof_begin(const char* name, cudaStream_t s);
 void prof_end(const char* name, cudaStream_t s);
 void count_launch();
+bool pdl_enabled();
+
+// First statement of every kernel: wait for the predecessor grid (a no-op when
+// launched without the attribute), then let the successor be scheduled.
+#define NRLSH_PDL_ENTRY() \
+    asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block,
@@ -44,8 +54,18 @@ inline cudaError_t launch(const char* name, void (*kernel)(KArgs...), dim3 grid,
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
     count_launch();
     prof_begin(name, s);
-    kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
-    cudaError_t e = cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e == cudaSuccess) e = cudaGetLastError();
     prof_end(name, s);
     return e;
 }

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kProjThreads)
                         const float* __restrict__ xnorm, C* __restrict__ codes,
                         unsigned long long* __restrict__ amb_list, unsigned* amb_count,
                         unsigned amb_cap, float kappa) {
+    NRLSH_PDL_ENTRY();
     constexpr int kRows = 32 * RI;
     __shared__ float As[kProjKC][8 * BT];
     __shared__ float Xs[kProjKC][kRows + 1];
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(256)
     resolve_kernel(const T* __restrict__ X, int d, int ldx, int Lp, const float* __restrict__ A_pad,
                    const double* __restrict__ tau64, const unsigned long long* __restrict__ list,
                    const unsigned* __restrict__ count, unsigned cap, C* __restrict__ codes) {
+    NRLSH_PDL_ENTRY();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(256)
                         const unsigned* __restrict__ count, unsigned cap, C* __restrict__ codes,
                         unsigned long long* __restrict__ list2, unsigned* count2, unsigned cap2,
                         float kappa) {
+    NRLSH_PDL_ENTRY();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -261,6 +264,7 @@ template <typename T, int NREG, int ROWS>
 __global__ void __launch_bounds__(256)
     project_dots_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int Lp, int dpa,
                         const float* __restrict__ At32, float* __restrict__ vsum) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float At_s[];
     const int Lr = (Lp + 31) / 32 * 32;
     for (int i = threadIdx.x; i < Lr * dpa / 4; i += blockDim.x)
@@ -296,6 +300,7 @@ __global__ void __launch_bounds__(256)
                         const float* __restrict__ xnorm, void* __restrict__ codes, int code_bytes,
                         unsigned* amb_count, float kappa, float* __restrict__ norm_out,
                         const float* __restrict__ At32) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float At_s[];  // Lr x dpa, Lr = Lp rounded up to 32
     __shared__ float ad_s[64], an_s[64];
     const int Lr = (Lp + 31) / 32 * 32;
@@ -467,6 +472,7 @@ namespace {
 // A^T for the warp-per-row projection: row b holds a_{k,b}, k < d, zero-padded.
 __global__ void transpose_a_kernel(const float* __restrict__ A_pad, int d, int L, int Lp, int dpa,
                                    float* __restrict__ At32) {
+    NRLSH_PDL_ENTRY();
     const int b = blockIdx.x;
     for (int k = threadIdx.x; k < dpa; k += blockDim.x)
         At32[(int64_t)b * dpa + k] = (b < L && k < d) ? A_pad[(int64_t)k * Lp + b] : 0.0f;

@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                       const double* __restrict__ tau64, C* __restrict__ codes,
                       unsigned long long* __restrict__ amb_list, unsigned* amb_count,
                       unsigned amb_cap, int* err) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int kTcStages = split == 2 ? kTcStagesTwo : kTcStagesOne;

@@ -58,6 +58,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total, uint32_t* 
 
 __global__ void row_norm_bound_kernel(const float* __restrict__ Q, int64_t nq, int d,
                                       float* qnorm) {
+    NRLSH_PDL_ENTRY();
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= nq) return;
@@ -88,6 +89,7 @@ template <typename C, int kHistQ>
 __global__ void __launch_bounds__(kHistThreads)
     hist_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t nq, int m, int L,
                 const PosTile* __restrict__ tiles, uint32_t* __restrict__ H, int exclusive) {
+    NRLSH_PDL_ENTRY();
     constexpr int kSplit = kHistThreads / kHistQ;
     extern __shared__ unsigned char smem_raw[];
     C* cs = (C*)smem_raw;
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(256)
                      int L, int64_t nq, int64_t n, int64_t budget,
                      const int64_t* __restrict__ budgets, uint32_t flags,
                      uint8_t* __restrict__ lam, Boundary* __restrict__ bnd) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ uint32_t cntj[];
     uint8_t* lam_s = (uint8_t*)(cntj + m);
     const int64_t q = blockIdx.x;
@@ -341,6 +344,7 @@ __global__ void __launch_bounds__(256)
                   const int64_t* __restrict__ seg, int m, int L,
                   const uint8_t* __restrict__ lam, const Boundary* __restrict__ bnd,
                   uint32_t* __restrict__ cand, int64_t cap) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ uint8_t lam_s[];
     const int64_t q = blockIdx.x;
     for (int j = threadIdx.x; j < m; j += 256) lam_s[j] = lam[q * m + j];
@@ -477,6 +481,7 @@ __global__ void __launch_bounds__(kRerankWarps * 32)
                        const Boundary* __restrict__ bnd, const float* __restrict__ xnorm,
                        const float* __restrict__ qnorm, float kappa, float* __restrict__ lo,
                        float* __restrict__ hi) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float qs[];
     const int64_t q = blockIdx.x;
     load_query(Q, q, d, dp, qs);
@@ -879,6 +884,7 @@ __global__ void __launch_bounds__(256)
                 const float* __restrict__ qnorm, const uint32_t* __restrict__ perm,
                 uint32_t* __restrict__ cont, double* __restrict__ cont_s,
                 int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int out_ld) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float qs[];
     const int64_t q = blockIdx.x;
     load_query(Q, q, d, dp, qs);
@@ -907,6 +913,7 @@ __global__ void __launch_bounds__(256, 4)
                         float* __restrict__ lo, float* __restrict__ hi, uint32_t* __restrict__ cont,
                         double* __restrict__ cont_s, int64_t cap, int64_t* __restrict__ out_ids,
                         float* __restrict__ out_scores, int out_ld) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float qs[];
     uint32_t* cntj = (uint32_t*)(qs + dp);
     uint8_t* lam_s = (uint8_t*)(cntj + m);
@@ -943,6 +950,7 @@ __global__ void __launch_bounds__(256, 4)
                                    int k_max, uint32_t* __restrict__ slabs, int64_t cap,
                                    unsigned* __restrict__ work, int64_t nq,
                                    int64_t* __restrict__ out_ids, float* __restrict__ out_scores) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float qs[];
     uint32_t* cntj = (uint32_t*)(qs + dp);
     uint8_t* lam_s = (uint8_t*)(cntj + m);
@@ -1032,6 +1040,7 @@ __global__ void __launch_bounds__(256)
     multitable_select_kernel(const C* __restrict__ codes, const C* __restrict__ qcodes, int64_t n,
                              C ones, C highs, uint32_t* __restrict__ cand, int64_t cap,
                              Boundary* __restrict__ bnd, int64_t* __restrict__ probed) {
+    NRLSH_PDL_ENTRY();
     const int64_t q = blockIdx.x;
     const int64_t total = dev_select_tables<C>(codes, qcodes[q], n, ones, highs, cand + q * cap, cap);
     if (threadIdx.x == 0) {
@@ -1047,6 +1056,7 @@ constexpr int kWorkChunk = 256;
 
 __global__ void __launch_bounds__(1024)
     work_offsets_kernel(const Boundary* __restrict__ bnd, int64_t nq, int64_t* __restrict__ work_off) {
+    NRLSH_PDL_ENTRY();
     __shared__ int64_t wsum[32];
     __shared__ int64_t carry_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1091,6 +1101,7 @@ __global__ void __launch_bounds__(kRerankWarps * 32)
                        int64_t nq, unsigned long long* __restrict__ work_ctr,
                        const float* __restrict__ xnorm, const float* __restrict__ qnorm,
                        float kappa, float* __restrict__ lo, float* __restrict__ hi) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float qs[];
     __shared__ int64_t w_s;
     const int64_t total = work_off[nq];
@@ -1133,6 +1144,7 @@ __global__ void __launch_bounds__(256)
                       double* __restrict__ cont_s, int64_t cap, int64_t* __restrict__ out_ids,
                       float* __restrict__ out_scores, int out_ld, int64_t* __restrict__ probed,
                       int32_t* __restrict__ cand_ids, int64_t cand_ld) {
+    NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float qs[];
     const int64_t q = blockIdx.x;
     uint32_t* candq = cand + q * cap;
@@ -1158,6 +1170,7 @@ __global__ void cand_to_ids_kernel(const uint32_t* __restrict__ cand, int64_t ca
                                    const Boundary* __restrict__ bnd,
                                    const uint32_t* __restrict__ perm, int32_t* out, int64_t out_cap,
                                    int64_t* count) {
+    NRLSH_PDL_ENTRY();
     const int64_t q = blockIdx.x;
     const Boundary b = bnd[q];
     const int64_t cnt = (int64_t)b.full + b.r;
