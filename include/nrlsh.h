@@ -32,9 +32,12 @@
  *
  * Memory and streams.  Unless stated otherwise pointers may be device pointers
  * (any CUDA allocation of the current device, e.g. from PyTorch) or host
- * pointers; host buffers are staged through device memory and the call then
- * synchronises its stream before returning.  With device pointers only, calls
- * are asynchronous on `stream` (NULL = the legacy default stream).  The caller
+ * pointers.  Host inputs are copied into device memory before the call returns
+ * (a build waits for that copy only and leaves its work queued); a call with a
+ * host output synchronises its stream before returning.  With device pointers
+ * only, calls are asynchronous on `stream` (NULL = the legacy default stream);
+ * a query call on another stream than the index's build makes its stream wait
+ * for the end of the build (an event recorded by the build).  The caller
  * keeps ownership of every buffer it passes; the index owns a copy of the items
  * and everything it derives from them.  Query calls allocate their scratch
  * with the stream-ordered allocator and free it on the same stream.

@@ -34,6 +34,7 @@ struct nrlsh_index {
     float eps = 0.1f;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t built = nullptr;   // recorded on `stream` at the end of the build
     int device = 0;
     int64_t device_bytes = 0;
     std::vector<void*> owned;
@@ -231,6 +232,7 @@ void destroy(nrlsh_index* ix) {
     cudaDeviceSynchronize();
     for (void* p : ix->owned) cudaFreeAsync(p, ix->stream);
     cudaStreamSynchronize(ix->stream);
+    if (ix->built) cudaEventDestroy(ix->built);
     delete ix;
 }
 
@@ -264,6 +266,17 @@ cudaError_t side_stream_fork(cudaStream_t main, int i) {
     return cudaStreamWaitEvent(t.s, t.fork, 0);
 }
 
+// Marks the end of the copy of a host input, which is all a call must wait for
+// before its caller may reuse that buffer.
+thread_local cudaEvent_t t_staged = nullptr;
+cudaError_t record_staged(cudaStream_t st) {
+    if (!t_staged) {
+        cudaError_t e = cudaEventCreateWithFlags(&t_staged, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaEventRecord(t_staged, st);
+}
+
 // Records the end of the side work queued so far.
 cudaError_t side_stream_join(int i) { return cudaEventRecord(t_side[i].join, t_side[i].s); }
 
@@ -271,6 +284,13 @@ cudaError_t side_stream_join(int i) { return cudaEventRecord(t_side[i].join, t_s
 // unaffected, and the side kernels run meanwhile).
 cudaError_t side_stream_wait(cudaStream_t main, int i) {
     return cudaStreamWaitEvent(main, t_side[i].join, 0);
+}
+
+// Work queued on another stream than the index's build stream waits for the
+// build to finish (on the same stream, stream order suffices).
+cudaError_t wait_for_build(const nrlsh_index* ix, cudaStream_t st) {
+    if (st == ix->stream || !ix->built) return cudaSuccess;
+    return cudaStreamWaitEvent(st, ix->built, 0);
 }
 
 int bits_for(int64_t v) {  // smallest b with 2^b >= v
@@ -314,6 +334,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     if ((int64_t)d * (int64_t)esz * n / n != (int64_t)d * (int64_t)esz) return arg_error("n*d overflows");
 
     cudaStream_t st = (cudaStream_t)stream;
+    const bool host_items = !is_device_ptr(items);
     nrlsh_index* ix = new nrlsh_index();
     ix->n = n;
     ix->d = d;
@@ -418,6 +439,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         Scratch sc(st);
         const void* X = nullptr;
         B_CK(stage_in(sc, items, (size_t)n * d * esz, &X));
+        if (host_items) B_CU(record_staged(st));
         uint64_t *keys, *keys_alt;
         uint32_t *vals, *vals_alt, *jkeys, *jkeys_alt;
         char* sort_tmp;
@@ -558,7 +580,11 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(side_stream_wait(st, 1));
         B_CU(launch_bucket_order(ix->U2, ix->ccos, m, L, ix->shat_sorted, ix->order, bo_tmp, st));
     }
-    if (!is_device_ptr(items)) B_CU(cudaStreamSynchronize(st));
+    B_CU(cudaEventCreateWithFlags(&ix->built, cudaEventDisableTiming));
+    B_CU(cudaEventRecord(ix->built, st));
+    // the caller may reuse a host item buffer once its copy is done; the build
+    // itself stays queued
+    if (host_items) B_CU(cudaEventSynchronize(t_staged));
 #undef B_CK
 #undef B_CU
     *out = ix;
@@ -835,6 +861,7 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* querie
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -859,6 +886,7 @@ NRLSH_API nrlsh_status nrlsh_hash_queries(const nrlsh_index* ix, const float* qu
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -876,6 +904,7 @@ NRLSH_API nrlsh_status nrlsh_query_histograms(const nrlsh_index* ix, const float
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -900,6 +929,7 @@ NRLSH_API nrlsh_status nrlsh_query_multitable(const nrlsh_index* ix, const float
     const int64_t cap = max_candidates == 0 ? ix->n : std::min(max_candidates, ix->n);
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -925,6 +955,7 @@ NRLSH_API nrlsh_status nrlsh_multitable_candidates(const nrlsh_index* ix, const 
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -950,6 +981,7 @@ NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* ix, const float
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -1271,6 +1303,7 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     const int64_t cap = std::min<int64_t>(budget_max, ix->n);
     const bool graph = (flags & NRLSH_QUERY_GRAPH) && st != nullptr;
     if (graph && !(is_device_ptr(queries) && is_device_ptr(ks) && is_device_ptr(budgets) &&
@@ -1471,6 +1504,7 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_noalloc(const nrlsh_index* ix, con
     NRLSH_CKS(noalloc_base(&base));
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
+    NRLSH_CK(wait_for_build(ix, st));
     // the largest chunk of queries whose scratch fits the array
     int64_t lo = 1, hi = nq;
     while (lo < hi) {
