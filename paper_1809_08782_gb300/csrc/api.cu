@@ -437,9 +437,11 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
 
     {
         Scratch sc(st);
-        const void* X = nullptr;
-        B_CK(stage_in(sc, items, (size_t)n * d * esz, &X));
-        if (host_items) B_CU(record_staged(st));
+        // host items: the copy is queued after the side streams fork, so that
+        // their item-independent work runs while it is in flight
+        const void* X = items;
+        char* X_stage = nullptr;
+        if (host_items) B_CK(sc.get(&X_stage, (size_t)n * d * esz));
         uint64_t *keys, *keys_alt;
         uint32_t *vals, *vals_alt, *jkeys, *jkeys_alt;
         char* sort_tmp;
@@ -486,12 +488,20 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         B_CU(side_stream_fork(st, 0));
         B_CU(side_stream_fork(st, 1));
         cudaStream_t side0 = side_stream(0), side1 = side_stream(1);
+        if (host_items) {
+            B_CU(cudaMemcpyAsync(X_stage, items, (size_t)n * d * esz, cudaMemcpyHostToDevice, st));
+            B_CU(record_staged(st));
+            X = X_stage;
+        }
         B_CU(launch_projections(ix->A, ix->A_pad, ix->anorm, ix->At, ix->dp, d, L, ix->Lp, seed,
                                 side0));
         if (ix->At32) B_CU(launch_transpose_a(ix->A_pad, d, L, ix->Lp, ix->At32, side0));
         // the FP32 part of the item projection needs no partition: it runs here too
-        if (split)
+        // (after the items' copy, when they come from the host)
+        if (split) {
+            if (host_items) B_CU(cudaStreamWaitEvent(side0, t_staged, 0));
             B_CU(launch_project_dots(X, dtype, n, d, d, ix->Lp, ix->At32, vsum, side0));
+        }
         B_CU(side_stream_join(0));
         B_CU(launch_class_cos(L, eps, ix->ccos, side1));
         if (!uniform)  // percentile ranges: offsets and tiles follow from n and m

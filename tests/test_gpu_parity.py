@@ -288,3 +288,31 @@ def test_code_bits_on_and_near_the_hyperplanes(proj):
     want = O.query_codes(Q.astype(np.float64), A)
     assert np.array_equal(got, want)
     check_queries(lib, ref, Q, 5, 120)
+
+
+def test_queries_opposite_to_every_item():
+    """Queries opposite to a tight cluster of items: every item matches few bits,
+    so the walk reaches the buckets of few matching bits before it has B items.
+    Results equal the oracle's, through the single-budget and the batched entry
+    points."""
+    import paper_1809_08782_gb300.nrlsh as N
+    from oracle import nrlsh as O
+    rng = np.random.default_rng(41)
+    d = 24
+    u = rng.standard_normal(d)
+    u /= np.linalg.norm(u)
+    items = (u[None, :] + 0.05 * rng.standard_normal((3000, d))) * rng.lognormal(0, 0.5, (3000, 1))
+    items = items.astype(np.float32)
+    lib, ref = build_pair(items, "f32", 8, 32, seed=3, eps=0.2)
+    check_index(lib, ref)
+    Q = np.concatenate([np.tile(-u, (6, 1)) + 0.01 * rng.standard_normal((6, d)),
+                        rng.standard_normal((6, d))]).astype(np.float32)
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    for B in (1, 40, 700):
+        check_queries(lib, ref, Q, 10, B)
+    ks = np.array([10] * 12, np.int32)
+    budgets = np.array([40, 700, 5, 3000, 1, 90] * 2, np.int64)
+    ids, sc = N.nrlsh_query_batched(lib, torch.from_numpy(Q).cuda(), torch.from_numpy(ks).cuda(),
+                                    torch.from_numpy(budgets).cuda(), 10, int(budgets.max()))
+    rids, rsc = O.query(ref, Q.astype(np.float64), ks, budgets)
+    assert np.array_equal(ids.cpu().numpy(), rids) and np.array_equal(sc.cpu().numpy(), rsc)
