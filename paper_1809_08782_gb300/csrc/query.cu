@@ -77,13 +77,32 @@ __global__ void row_norm_bound_kernel(const float* __restrict__ Q, int64_t nq, i
 
 // Block of 256 threads: one position tile (inside one sub-dataset, at most 4,096
 // codes, staged in shared memory) x kHistQ queries, with kSplit = 256 / kHistQ
-// threads per query each taking every kSplit-th code (a warp reads one code by
-// broadcast).  Every thread keeps a private uint32 histogram column indexed
-// [l][thread], so increments never conflict on a bank; they are shared-memory
-// reductions (no returned value), so consecutive increments of a thread do not
-// wait on each other.  The columns of a query are summed at the end and added to
+// threads per query each taking a contiguous share of the tile (a warp reads
+// 16 bytes of codes at a time by broadcast).  Every thread keeps a private uint32
+// histogram column indexed [l][thread], so increments never conflict on a bank;
+// they are shared-memory reductions (no returned value), so consecutive
+// increments of a thread do not wait on each other.  The columns of a query are summed at the end and added to
 // H (stored, when every sub-dataset is one tile).
 constexpr int kHistThreads = 256;
+
+// The codes of one 16-byte vector counted into a thread's histogram column.
+template <typename C>
+__device__ __forceinline__ void hist_count_vec(const uint4& a, C cq, int L, uint32_t* hc);
+template <>
+__device__ __forceinline__ void hist_count_vec<uint32_t>(const uint4& a, uint32_t cq, int L,
+                                                         uint32_t* hc) {
+    atomicAdd(&hc[(L - __popc(cq ^ a.x)) * kHistThreads], 1u);
+    atomicAdd(&hc[(L - __popc(cq ^ a.y)) * kHistThreads], 1u);
+    atomicAdd(&hc[(L - __popc(cq ^ a.z)) * kHistThreads], 1u);
+    atomicAdd(&hc[(L - __popc(cq ^ a.w)) * kHistThreads], 1u);
+}
+template <>
+__device__ __forceinline__ void hist_count_vec<uint64_t>(const uint4& a, uint64_t cq, int L,
+                                                         uint32_t* hc) {
+    const uint64_t c0 = ((uint64_t)a.y << 32) | a.x, c1 = ((uint64_t)a.w << 32) | a.z;
+    atomicAdd(&hc[(L - __popcll(cq ^ c0)) * kHistThreads], 1u);
+    atomicAdd(&hc[(L - __popcll(cq ^ c1)) * kHistThreads], 1u);
+}
 
 template <typename C, int kHistQ>
 __global__ void __launch_bounds__(kHistThreads)
@@ -105,20 +124,24 @@ __global__ void __launch_bounds__(kHistThreads)
         ((uint4*)h)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (q < nq) {
+        // thread sp of a query takes a contiguous share of the tile's 16-byte code
+        // vectors (a warp shares sp, so every vector load is a broadcast); the
+        // codes past the last whole vector are taken strided
         const C cq = qcodes[q];
         uint32_t* hc = h + tid;
-        int i = sp;
-        for (; i + 3 * kSplit < t.len; i += 4 * kSplit) {
-            const int l0 = L - popc_word(cq ^ cs[i]);
-            const int l1 = L - popc_word(cq ^ cs[i + kSplit]);
-            const int l2 = L - popc_word(cq ^ cs[i + 2 * kSplit]);
-            const int l3 = L - popc_word(cq ^ cs[i + 3 * kSplit]);
-            atomicAdd(&hc[l0 * kHistThreads], 1u);
-            atomicAdd(&hc[l1 * kHistThreads], 1u);
-            atomicAdd(&hc[l2 * kHistThreads], 1u);
-            atomicAdd(&hc[l3 * kHistThreads], 1u);
+        constexpr int kPer = 16 / sizeof(C);
+        const int nvec = t.len / kPer;
+        const int v1 = (int)((int64_t)nvec * (sp + 1) / kSplit);
+        const uint4* cs4 = (const uint4*)cs;
+        int v = (int)((int64_t)nvec * sp / kSplit);
+        for (; v + 1 < v1; v += 2) {
+            const uint4 a = cs4[v], b = cs4[v + 1];
+            hist_count_vec<C>(a, cq, L, hc);
+            hist_count_vec<C>(b, cq, L, hc);
         }
-        for (; i < t.len; i += kSplit) atomicAdd(&hc[(L - popc_word(cq ^ cs[i])) * kHistThreads], 1u);
+        if (v < v1) hist_count_vec<C>(cs4[v], cq, L, hc);
+        for (int i = nvec * kPer + sp; i < t.len; i += kSplit)
+            atomicAdd(&hc[(L - popc_word(cq ^ cs[i])) * kHistThreads], 1u);
     }
     __syncthreads();
     for (int e = tid; e < (L + 1) * kHistQ; e += kHistThreads) {
