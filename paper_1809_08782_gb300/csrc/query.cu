@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kHistThreads)
     const PosTile t = tiles[blockIdx.x];
     const int64_t q0 = (int64_t)blockIdx.y * kHistQ;
     const int64_t q = q0 + qi;
+#pragma unroll 4
     for (int i = tid; i < t.len; i += kHistThreads) cs[i] = codes[t.start + i];
     // (L+1) x 256 words: a multiple of 4, cleared 16 bytes at a time
     for (int i = tid; i < (L + 1) * kHistThreads / 4; i += kHistThreads)
@@ -134,12 +135,14 @@ __global__ void __launch_bounds__(kHistThreads)
         const int v1 = (int)((int64_t)nvec * (sp + 1) / kSplit);
         const uint4* cs4 = (const uint4*)cs;
         int v = (int)((int64_t)nvec * sp / kSplit);
-        for (; v + 1 < v1; v += 2) {
-            const uint4 a = cs4[v], b = cs4[v + 1];
+        for (; v + 3 < v1; v += 4) {
+            const uint4 a = cs4[v], b = cs4[v + 1], c = cs4[v + 2], e = cs4[v + 3];
             hist_count_vec<C>(a, cq, L, hc);
             hist_count_vec<C>(b, cq, L, hc);
+            hist_count_vec<C>(c, cq, L, hc);
+            hist_count_vec<C>(e, cq, L, hc);
         }
-        if (v < v1) hist_count_vec<C>(cs4[v], cq, L, hc);
+        for (; v < v1; ++v) hist_count_vec<C>(cs4[v], cq, L, hc);
         for (int i = nvec * kPer + sp; i < t.len; i += kSplit)
             atomicAdd(&hc[(L - popc_word(cq ^ cs[i])) * kHistThreads], 1u);
     }
