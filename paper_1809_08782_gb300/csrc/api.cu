@@ -192,6 +192,7 @@ struct Scratch {
     }
     template <typename T>
     nrlsh_status get(T** out, size_t count) {
+        *out = nullptr;
         const size_t bytes = (std::max<size_t>(count * sizeof(T), 16) + 255) & ~(size_t)255;
         if (bytes > left) {
             void* p = nullptr;

@@ -217,12 +217,10 @@ template <typename T, int VEC>
 struct RowGroups;
 template <typename T>
 struct RowGroups<T, 1> {
-    static constexpr int kVec = 1;
     __device__ static void load(const T* xr, int g, float (&v)[1]) { v[0] = to_f32(xr[g]); }
 };
 template <>
 struct RowGroups<float, 4> {
-    static constexpr int kVec = 4;
     __device__ static void load(const float* xr, int g, float (&v)[4]) {
         const float4 f = ((const float4*)xr)[g];
         v[0] = f.x;
@@ -233,7 +231,6 @@ struct RowGroups<float, 4> {
 };
 template <>
 struct RowGroups<__nv_bfloat16, 4> {
-    static constexpr int kVec = 4;
     __device__ static void load(const __nv_bfloat16* xr, int g, float (&v)[4]) {
         const uint2 raw = ((const uint2*)xr)[g];
         const float2 a = __bfloat1622float2(*(const __nv_bfloat162*)&raw.x);
