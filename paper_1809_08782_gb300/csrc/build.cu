@@ -1145,8 +1145,8 @@ __device__ __forceinline__ GatherTail gather_tail(int64_t p, uint32_t id,
 
 constexpr int kGatherRows = 32;
 
-// Per block: the tails of its positions, and each lane's tail coefficient a_db and
-// ||a_b|| for bits b = lane and 32 + lane.
+// Per block: tau (FP64 and FP32) and the norm bound of each of its positions,
+// written by warp 0 for the code decisions of all warps.
 struct GatherShared {
     double tau64[kGatherRows];
     float tau32[kGatherRows], xn[kGatherRows];

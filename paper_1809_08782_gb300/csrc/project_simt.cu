@@ -259,7 +259,8 @@ __device__ __forceinline__ void pass_sums(const float (&x)[ROWS][NREG], const fl
 
 // The FP32 sums a_b^T x of every row and bit (no tail, no decision), in id order:
 // vsum[row Lr + b].  Run beside the partition; the signs are taken once tau is
-// known (finalize_codes_kernel).  A^T comes from the index's copy (At32).
+// known, by the gather that places each item.  A^T comes from the index's copy
+// (At32).
 template <typename T, int NREG, int ROWS>
 __global__ void __launch_bounds__(256)
     project_dots_kernel(const T* __restrict__ X, int64_t n, int d, int ldx, int Lp, int dpa,
