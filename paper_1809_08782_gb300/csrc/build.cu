@@ -1152,6 +1152,9 @@ struct GatherShared {
     float tau32[kGatherRows], xn[kGatherRows];
 };
 
+// Warp 0 writes the tails of the block's positions (global arrays and sh); with
+// code bits to take, every lane also loads a_db and ||a_b|| of bits lane and
+// 32 + lane, and the block waits for the tails.
 __device__ __forceinline__ void gather_prologue(const GatherCodes& gc, int64_t p0, int64_t n,
                                                 const uint32_t* __restrict__ perm,
                                                 const uint32_t* __restrict__ sub_of_id,
