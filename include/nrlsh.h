@@ -46,6 +46,13 @@
  * and returns a status; a thread-local message is available from
  * nrlsh_last_error().  A CUDA error (including a sticky error left by earlier
  * work) is reported as NRLSH_ERR_CUDA.  No entry point aborts the process.
+ * Every wait of the tensor-core kernels is bounded: one that runs out makes
+ * the kernel stop, let its own copies and MMAs land and return, and records an
+ * error word in the index, which nrlsh_get_info (and, for the build,
+ * nrlsh_get_codes) report as NRLSH_ERR_TIMEOUT.  Test hook: the environment
+ * variable NRLSH_TEST_SPIN_FIRST, read at each call, sets how many polls the
+ * first such wait of the MMA thread takes (normally 4,194,304; 0 makes it run
+ * out at once).
  */
 #ifndef NRLSH_H
 #define NRLSH_H
@@ -131,6 +138,8 @@ typedef struct nrlsh_info {
     int32_t device_error;        /* nonzero: a bounded device wait ran out during the build */
     int32_t partition;           /* nrlsh_partition used */
     int32_t norm_fallbacks;      /* rows whose squared norm needed the exact slow path */
+    int32_t query_error;         /* nonzero: a tensor-core query kernel's bounded wait ran
+                                    out, or it found other candidates than it counted */
 } nrlsh_info;
 
 /*
@@ -162,8 +171,22 @@ NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d,
  *   ids           nq x k int64: original item ids, best first; -1 past the end
  *                 when fewer than k items were probed
  *   scores        nq x k fp32: the matching inner products; -inf past the end
+ *   flags         NRLSH_WHOLE_BUCKETS: the boundary bucket is probed whole;
+ *                 NRLSH_QUERY_TENSOR: the probing and the re-rank run on tensor
+ *                 cores (below); results are the same
  * nrlsh_query runs on the legacy default stream with no flags.
+ *
+ * The tensor-core path handles every (query, item) pair of a probed sub-dataset
+ * as one entry of a dense product of a 128-query tile with 128-item tiles:
+ * match counts l(q, x) from the +-1 sign vectors of the codes (bf16 products,
+ * exact in the FP32 accumulator) and scores from the bf16-rounded query and
+ * items with FP32 accumulation, kept as intervals [s - e, s + e] that provably
+ * hold the FP64 score; the exact top-k then rescores the contenders.  It needs
+ * an sm_100-family GPU (else NRLSH_ERR_UNSUPPORTED).  Its first call on an index
+ * makes the index's sign matrix (n x 128 bytes, kept until nrlsh_free) on that
+ * call's stream; make it before any stream capture.
  */
+#define NRLSH_QUERY_TENSOR 0x8u
 NRLSH_API nrlsh_status nrlsh_query(const nrlsh_index* index, const float* queries, int64_t nq,
                                    int32_t k, int64_t probe_budget, int64_t* ids,
                                    float* scores);
@@ -187,27 +210,36 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* index, const float* que
  *                 call with these pointers and sizes, and replay it on later identical
  *                 calls (needs a non-NULL stream; the graph and its workspace live
  *                 until nrlsh_free).
- * The first call for a given (nq, k_max, budget_max) shape times a few tile
- * configurations on a prefix of the batch (the autotuner) and keeps the fastest;
- * make it before any stream capture of your own.  ks and budgets may be device or
- * host pointers like the other arrays.
+ * The first call for a given (nq, k_max, budget_max) shape times the candidate
+ * configurations on a prefix of the batch (the autotuner) and keeps the fastest:
+ * the FP32 path (popcount histograms with 32, 64 or 128 queries per block, the
+ * persistent re-rank at 1, 2 or 4 CTAs per SM) and the tensor-core path of
+ * nrlsh_query_ex's NRLSH_QUERY_TENSOR (histograms on tensor cores or by popcount);
+ * NRLSH_QUERY_TENSOR / NRLSH_QUERY_FP32 restrict it to one path.  Make that call
+ * before any stream capture of your own.  ks and budgets may be device or host
+ * pointers like the other arrays.
  */
 #define NRLSH_QUERY_GRAPH 0x2u
 #define NRLSH_QUERY_NO_TUNE 0x4u   /* skip the autotuner: last tuned (or default) tiles */
+#define NRLSH_QUERY_FP32 0x10u     /* the FP32 CUDA-core path only (NRLSH_QUERY_TENSOR: the
+                                      tensor-core path only; neither: the autotuner picks) */
 NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* index, const float* queries,
                                            int64_t nq, const int32_t* ks, const int64_t* budgets,
                                            int32_t k_max, int64_t budget_max, uint32_t flags,
                                            int64_t* ids, float* scores, void* stream);
-/* Device scratch (bytes) one nrlsh_query_batched call with these sizes allocates
- * from the stream-ordered pool (device-pointer arguments, no graph), for callers
- * that admit work by memory. */
+/* Device scratch (bytes) one nrlsh_query_batched call with these sizes and flags
+ * allocates from the stream-ordered pool (device-pointer arguments, no graph), for
+ * callers that admit work by memory.  It follows the configuration that call would
+ * use: the tuned one for these sizes, else the last one used. */
 NRLSH_API nrlsh_status nrlsh_batched_scratch_bytes(const nrlsh_index* index, int64_t nq,
                                                    int32_t k_max, int64_t budget_max,
-                                                   int64_t* bytes);
+                                                   uint32_t flags, int64_t* bytes);
 /* The autotuned configuration last used for this index: histogram queries per
- * block and persistent CTAs per SM (0, 0 before any batched call). */
+ * block and persistent CTAs per SM (0, 0 before any batched call), and in
+ * *tensor bit 0 = histograms on tensor cores, bit 1 = re-rank on tensor cores.
+ * Any output may be NULL. */
 NRLSH_API nrlsh_status nrlsh_get_tuning(const nrlsh_index* index, int32_t* hist_queries_per_block,
-                                        int32_t* ctas_per_sm);
+                                        int32_t* ctas_per_sm, int32_t* tensor);
 
 /*
  * Query processing without any device allocation.  The paper has no counterpart:
@@ -267,18 +299,22 @@ NRLSH_API nrlsh_status nrlsh_multitable_candidates(const nrlsh_index* index,
  * host pointers as above.
  * nrlsh_hash_queries: codes (nq uint64; bit b of the code is hash bit b).
  * nrlsh_query_histograms: H (nq x m x (L+1) uint32), H[q][j][l] = number of
- *   items of sub-dataset j sharing exactly l hash bits with query q.
+ *   items of sub-dataset j sharing exactly l hash bits with query q; flags
+ *   NRLSH_QUERY_TENSOR counts them on tensor cores (the same numbers).
  * nrlsh_query_candidates: the probed items of each query (Section 3.3):
  *   cand (nq x cap int32 original ids) and count (nq int64).  For each query the
  *   ids of the buckets probed whole come first, in storage order (sub-dataset,
  *   then id), followed by the items taken from the boundary bucket, by id.  Fails
  *   with NRLSH_ERR_ARG if a query has more than `cap` candidates (count is still
- *   written).  Without NRLSH_WHOLE_BUCKETS, count = min(B, n).
+ *   written).  Without NRLSH_WHOLE_BUCKETS, count = min(B, n).  With
+ *   NRLSH_QUERY_TENSOR the candidates come from the tensor-core path: the same
+ *   set, grouped by ascending sub-dataset but in no set order inside one.
  */
 NRLSH_API nrlsh_status nrlsh_hash_queries(const nrlsh_index* index, const float* queries,
                                           int64_t nq, uint64_t* codes, void* stream);
 NRLSH_API nrlsh_status nrlsh_query_histograms(const nrlsh_index* index, const float* queries,
-                                              int64_t nq, uint32_t* H, void* stream);
+                                              int64_t nq, uint32_t* H, uint32_t flags,
+                                              void* stream);
 NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* index, const float* queries,
                                               int64_t nq, int64_t probe_budget, uint32_t flags,
                                               int64_t cap, int32_t* cand, int64_t* count,
@@ -295,7 +331,8 @@ NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* index, const fl
  * nrlsh_get_projections: A ((d+1) x L floats, row-major; every value is bf16).
  * nrlsh_get_buckets:     the probing order: bucket_j, bucket_l (m(L+1) int32 each)
  *                        and s_hat (m(L+1) doubles) in probing order; any may be NULL.
- * nrlsh_get_info:        sizes and build statistics.
+ * nrlsh_get_info:        sizes and build statistics; NRLSH_ERR_TIMEOUT (info still
+ *                        filled) when device_error or query_error is set.
  */
 NRLSH_API nrlsh_status nrlsh_get_codes(const nrlsh_index* index, uint64_t* codes);
 NRLSH_API nrlsh_status nrlsh_get_partition(const nrlsh_index* index, int32_t* sub_of_id,

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrlsh.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "build.cu", "query.cu", "project_tc.cu", "project_simt.cu"]
+SOURCES = ["api.cu", "build.cu", "query.cu", "query_tc.cu", "project_tc.cu", "project_simt.cu"]
 
 
 def nvcc() -> str:

@@ -15,8 +15,10 @@
 
 // Autotuned configuration of the batched query path.
 struct nrlsh_batch_cfg {
-    int hist_qb = 64;       // queries per histogram block
-    int ctas_per_sm = 2;    // persistent probe/re-rank CTAs per SM
+    int hist_qb = 64;       // queries per histogram block (popcount histogram)
+    int ctas_per_sm = 2;    // persistent probe/re-rank CTAs per SM (FP32 re-rank)
+    int hist_tc = 0;        // 1: histograms on tensor cores (sign products)
+    int rerank_tc = 0;      // 1: candidates and score intervals on tensor cores
 };
 
 // A captured batched-query launch sequence with its fixed workspace.
@@ -25,6 +27,7 @@ struct nrlsh_graph_entry {
                const void*, void*> key;
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> workspace;
+    int rerank_tc = 0, hist_tc = 0, hist_qb = 0, ctas_per_sm = 0;   // the captured configuration
 };
 
 struct nrlsh_index {
@@ -54,7 +57,7 @@ struct nrlsh_index {
     void* codes = nullptr;         // n code words, position order
     uint32_t* order = nullptr;     // ncls bucket ids j*(L+1)+l in probing order
     double* shat_sorted = nullptr; // ncls
-    double* ccos = nullptr;        // L+1 bucket cosines c_l
+    const double* ccos = nullptr;  // L+1 bucket cosines c_l (the library's cache, not owned)
     int32_t partition = NRLSH_PARTITION_PERCENTILE;
     int64_t* seg = nullptr;        // m+1 storage offsets of the sub-datasets
     nrlsh::PosTile* tiles = nullptr;
@@ -68,10 +71,18 @@ struct nrlsh_index {
     __nv_bfloat16* Xb = nullptr;     // fp32 items: bf16 high part, n x dp (tensor-core A operand)
     __nv_bfloat16* Xb2 = nullptr;    // fp32 items: bf16 low part (x - hi rounded), n x dp
     int* dev_err = nullptr;          // set by bounded device waits that ran out
+    int* query_err = nullptr;        // the same for the tensor-core query kernels
+    // tensor-core query operands, made on first use: the +-1 signs of the codes
+    // (n x 64 bf16) and, for fp32 items, their bf16 rounding (n x dp)
+    mutable std::mutex tc_mu;
+    mutable __nv_bfloat16* tc_xs = nullptr;
+    mutable __nv_bfloat16* tc_xb = nullptr;
+    mutable cudaEvent_t tc_ready = nullptr;
+    mutable std::vector<void*> tc_owned;
     // batched queries: autotuned configurations per (nq, k_max, cap) and graph cache
     mutable std::mutex batch_mu;
-    mutable std::map<std::tuple<int64_t, int, int64_t>, nrlsh_batch_cfg> tuned;
-    mutable nrlsh_batch_cfg last_cfg{0, 0};
+    mutable std::map<std::tuple<int64_t, int, int64_t, int>, nrlsh_batch_cfg> tuned;
+    mutable nrlsh_batch_cfg last_cfg{0, 0, 0, 0};
     mutable std::vector<nrlsh_graph_entry> graphs;
 };
 
@@ -126,6 +137,15 @@ bool pdl_enabled() {
         return !(v && v[0] == '1');
     }();
     return on;
+}
+
+// Polls of the tensor-core kernels' first wait for an operand stage: the
+// NRLSH_TEST_SPIN_FIRST environment variable when set (a test hook that makes a
+// bounded wait run out on purpose), else the kernels' normal limit.
+uint32_t test_spin_first() {
+    const char* v = std::getenv("NRLSH_TEST_SPIN_FIRST");
+    if (!v || !*v) return 1u << 22;
+    return (uint32_t)std::strtoul(v, nullptr, 10);
 }
 
 void prof_begin(const char*, cudaStream_t s) {
@@ -233,7 +253,10 @@ void destroy(nrlsh_index* ix) {
     cudaDeviceSynchronize();
     for (void* p : ix->owned) cudaFreeAsync(p, ix->stream);
     cudaStreamSynchronize(ix->stream);
+    for (void* p : ix->tc_owned) cudaFreeAsync(p, ix->stream);
+    cudaStreamSynchronize(ix->stream);
     if (ix->built) cudaEventDestroy(ix->built);
+    if (ix->tc_ready) cudaEventDestroy(ix->tc_ready);
     delete ix;
 }
 
@@ -276,6 +299,44 @@ cudaError_t record_staged(cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     return cudaEventRecord(t_staged, st);
+}
+
+// The bucket cosines c_l = cos(pi (1 - eps)(L - l) / L) depend on (L, eps) alone:
+// each (device, L, eps) is computed once, into an array the library keeps until
+// the process exits, and later builds wait for its event instead of recomputing it.
+struct CosEntry {
+    double* cl = nullptr;
+    cudaEvent_t ready = nullptr;
+};
+std::mutex g_cos_mu;
+std::map<std::tuple<int, int, uint32_t>, CosEntry> g_cos;
+
+// *cl receives the cached array; the cosines are queued on `side` the first time
+// and `wait_on` waits for them.
+nrlsh_status class_cos_cached(int device, int L, float eps, cudaStream_t side,
+                              cudaStream_t wait_on, const double** cl) {
+    uint32_t eb;
+    std::memcpy(&eb, &eps, 4);
+    std::lock_guard<std::mutex> g(g_cos_mu);
+    CosEntry& e = g_cos[std::make_tuple(device, L, eb)];
+    if (!e.cl) {
+        void* p = nullptr;
+        NRLSH_CK(cudaMalloc(&p, sizeof(double) * (L + 1)));
+        cudaEvent_t ev = nullptr;
+        cudaError_t er = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (er == cudaSuccess) er = launch_class_cos(L, eps, (double*)p, side);
+        if (er == cudaSuccess) er = cudaEventRecord(ev, side);
+        if (er != cudaSuccess) {
+            cudaFree(p);
+            if (ev) cudaEventDestroy(ev);
+            return cuda_status(er, "bucket cosines");
+        }
+        e.cl = (double*)p;
+        e.ready = ev;
+    }
+    NRLSH_CK(cudaStreamWaitEvent(wait_on, e.ready, 0));
+    *cl = e.cl;
+    return NRLSH_OK;
 }
 
 // Records the end of the side work queued so far.
@@ -410,10 +471,10 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         c.take((char**)&ix->codes, (size_t)n * ix->code_bytes);
         c.take(&ix->order, ix->ncls);
         c.take(&ix->shat_sorted, ix->ncls);
-        c.take(&ix->ccos, L + 1);
         c.take(&ix->ambiguous, 1);
         c.take(&ix->norm_fb, 1);
         c.take(&ix->dev_err, 1);
+        c.take(&ix->query_err, 1);
         c.take(&ix->tiles, (size_t)ix->ntiles);
         if (warp_proj_stride(d, ix->Lp) > 0) c.take(&ix->At32, warp_proj_at_floats(d, ix->Lp));
         if (tc) {
@@ -476,6 +537,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
         {
             ZeroList z;
             z.add(ix->dev_err, 1);
+            z.add(ix->query_err, 1);
             z.add(ix->ambiguous, 1);
             z.add(ix->norm_fb, 1);
             z.add(ix->U2, 2 * (size_t)m);
@@ -504,7 +566,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
             B_CU(launch_project_dots(X, dtype, n, d, d, ix->Lp, ix->At32, vsum, side0));
         }
         B_CU(side_stream_join(0));
-        B_CU(launch_class_cos(L, eps, ix->ccos, side1));
+        B_CK(class_cos_cached(ix->device, L, eps, side1, side1, &ix->ccos));
         if (!uniform)  // percentile ranges: offsets and tiles follow from n and m
             B_CU(launch_segments(nullptr, n, m, tile, ix->seg, ix->tiles, ix->ntiles, side1));
         B_CU(side_stream_join(1));
@@ -576,7 +638,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
             B_CU(launch_project_tc(xb, ix->Xb2, ix->Xp, n, d, ix->dp, L, ix->Lp, ix->At, ix->A_pad,
                                    ix->anorm, ix->tau32, ix->tau64, ix->xnorm, dtype == NRLSH_F32,
                                    ix->codes, ix->code_bytes, amb_list, ix->ambiguous,
-                                   (unsigned)amb_cap, ix->dev_err, st));
+                                   (unsigned)amb_cap, ix->dev_err, st, test_spin_first()));
             // bits the tensor-core bound left open: FP32 on CUDA cores, then FP64
             B_CU(launch_resolve_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
                                      ix->xnorm, ix->tau32, ix->tau64, amb_list, ix->ambiguous,
@@ -731,6 +793,232 @@ nrlsh_status run_queries(const nrlsh_index* ix, const float* Q, int64_t nq, int3
     return NRLSH_OK;
 }
 
+// ------------------------------------------------- tensor-core query path
+
+// Workspace of one chunk of qc queries on the tensor-core path.
+struct TcWs {
+    float* qnorm = nullptr;
+    unsigned* qamb = nullptr;
+    unsigned long long* qamb_list = nullptr;
+    size_t qamb_cap = 0;
+    char* qcodes = nullptr;
+    __nv_bfloat16* Qb = nullptr;
+    __nv_bfloat16* Qs = nullptr;
+    uint32_t* H = nullptr;
+    uint8_t* lam = nullptr;
+    uint32_t* off = nullptr;
+    TcBoundary* tb = nullptr;
+    Boundary* bnd = nullptr;
+    uint8_t* flag = nullptr;
+    uint32_t* list = nullptr;
+    uint32_t* nlist = nullptr;
+    uint32_t* cand = nullptr;
+    float* lo = nullptr;
+    float* hi = nullptr;
+    uint32_t* cont = nullptr;
+    double* cont_s = nullptr;
+    int* err = nullptr;           // the call's error word (copied into the index's at the end)
+    int64_t qc = 0;
+    int64_t cap = 0;
+};
+
+int tc_nqt(int64_t qc) { return (int)ceil_div(qc, 128); }
+
+// Buffer sizes (bytes) of a TcWs for qc queries and list capacity cap, in TcWs order.
+std::vector<size_t> tc_ws_sizes(const nrlsh_index* ix, int64_t qc, int64_t cap) {
+    const size_t q = (size_t)qc, c = (size_t)cap;
+    const size_t Kq = 64 * (size_t)tc_query_k_chunks(ix->d);
+    const size_t nw = (size_t)ix->m * tc_nqt(qc);
+    return {q * 4, 16, ambiguity_capacity(qc, ix->L) * 8, q * ix->code_bytes, q * Kq * 2, q * 128,
+            q * ix->ncls * 4, q * ix->m, q * (ix->m + 1) * 4, q * sizeof(TcBoundary),
+            q * sizeof(Boundary), nw, nw * 4, 16, q * c * 4, q * c * 4, q * c * 4, q * c * 4,
+            q * c * 8, 16};
+}
+
+size_t tc_ws_bytes(const nrlsh_index* ix, int64_t qc, int64_t cap) {
+    size_t t = 0;
+    for (size_t b : tc_ws_sizes(ix, qc, cap)) t += (std::max<size_t>(b, 16) + 255) / 256 * 256;
+    return t;
+}
+
+void tc_ws_assign(TcWs& w, const std::vector<void*>& p, const nrlsh_index* ix, int64_t qc,
+                  int64_t cap) {
+    w.qnorm = (float*)p[0];
+    w.qamb = (unsigned*)p[1];
+    w.qamb_list = (unsigned long long*)p[2];
+    w.qamb_cap = ambiguity_capacity(qc, ix->L);
+    w.qcodes = (char*)p[3];
+    w.Qb = (__nv_bfloat16*)p[4];
+    w.Qs = (__nv_bfloat16*)p[5];
+    w.H = (uint32_t*)p[6];
+    w.lam = (uint8_t*)p[7];
+    w.off = (uint32_t*)p[8];
+    w.tb = (TcBoundary*)p[9];
+    w.bnd = (Boundary*)p[10];
+    w.flag = (uint8_t*)p[11];
+    w.list = (uint32_t*)p[12];
+    w.nlist = (uint32_t*)p[13];
+    w.cand = (uint32_t*)p[14];
+    w.lo = (float*)p[15];
+    w.hi = (float*)p[16];
+    w.cont = (uint32_t*)p[17];
+    w.cont_s = (double*)p[18];
+    w.err = (int*)p[19];
+    w.qc = qc;
+    w.cap = cap;
+}
+
+nrlsh_status tc_ws_scratch(Scratch& sc, TcWs& w, const nrlsh_index* ix, int64_t qc, int64_t cap) {
+    std::vector<void*> p;
+    for (size_t b : tc_ws_sizes(ix, qc, cap)) {
+        char* q = nullptr;
+        NRLSH_CKS(sc.get(&q, b));
+        p.push_back(q);
+    }
+    tc_ws_assign(w, p, ix, qc, cap);
+    return NRLSH_OK;
+}
+
+// Queries per chunk of the tensor-core path: the chunk's workspace within 8 GiB.
+int64_t tc_chunk(const nrlsh_index* ix, int64_t nq, int64_t cap) {
+    const int64_t per = (int64_t)tc_ws_bytes(ix, 128, cap) / 128 + 1;
+    int64_t c = std::max<int64_t>(128, ((int64_t)8 << 30) / per);
+    return std::min<int64_t>(c, std::max<int64_t>(nq, 1));
+}
+
+bool tc_path_supported(const nrlsh_index* ix) { return tc_query_supported(ix->d, ix->L); }
+
+// The index's tensor-path operands (the sign matrix of the codes, the bf16 copy
+// of fp32 items), made on the first call on stream st: later calls on other
+// streams wait for them (not during a stream capture, which must come after
+// the first call).
+nrlsh_status ensure_tc_items(const nrlsh_index* ix, cudaStream_t st, bool capturing) {
+    std::lock_guard<std::mutex> g(ix->tc_mu);
+    if (ix->tc_xs) {
+        if (!capturing) NRLSH_CK(cudaStreamWaitEvent(st, ix->tc_ready, 0));
+        return NRLSH_OK;
+    }
+    if (capturing) {
+        set_error("the first tensor-core query on an index must come before any stream capture");
+        return NRLSH_ERR_UNSUPPORTED;
+    }
+    void* xs = nullptr;
+    void* xb = nullptr;
+    NRLSH_CK(cudaMallocAsync(&xs, (size_t)ix->n * 64 * 2, st));
+    ix->tc_owned.push_back(xs);
+    if (ix->dtype == NRLSH_F32 && !ix->Xb) {
+        NRLSH_CK(cudaMallocAsync(&xb, (size_t)ix->n * ix->dp * 2, st));
+        ix->tc_owned.push_back(xb);
+    }
+    NRLSH_CK(launch_item_signs(ix->codes, ix->code_bytes, ix->n, ix->L, (__nv_bfloat16*)xs, st));
+    if (xb) NRLSH_CK(launch_to_bf16((const float*)ix->Xp, ix->n * ix->dp, (__nv_bfloat16*)xb, st));
+    if (!ix->tc_ready) NRLSH_CK(cudaEventCreateWithFlags(&ix->tc_ready, cudaEventDisableTiming));
+    NRLSH_CK(cudaEventRecord(ix->tc_ready, st));
+    ix->tc_xs = (__nv_bfloat16*)xs;
+    ix->tc_xb = ix->dtype == NRLSH_BF16 ? (__nv_bfloat16*)ix->Xp
+                                         : (ix->Xb ? ix->Xb : (__nv_bfloat16*)xb);
+    return NRLSH_OK;
+}
+
+nrlsh_status cuda_status_ok(cudaError_t e) {
+    return e == cudaSuccess ? NRLSH_OK : cuda_status(e, "kernel launch");
+}
+
+nrlsh_status tensor_query_prologue(const nrlsh_index* ix, cudaStream_t st) {
+    if (!tc_path_supported(ix)) {
+        set_error("the tensor-core query path needs an sm_100-family GPU and rows that fit its tiles");
+        return NRLSH_ERR_UNSUPPORTED;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st) NRLSH_CK(cudaStreamIsCapturing(st, &cs));
+    return ensure_tc_items(ix, st, cs != cudaStreamCaptureStatusNone);
+}
+
+// One chunk of queries [0, qc) on the tensor-core path (device pointers): hash,
+// histograms (tensor cores when hist_tc, else the popcount kernel with hist_qb
+// queries per block), walk with the list offsets, the dense candidate re-rank on
+// tensor cores, and the exact top-k.  ks / budgets may be null (one k / budget).
+// With H_out the histograms are written there and the chunk stops; with cand_out
+// the candidates' ids (grouped by ascending sub-dataset, unordered inside one)
+// and their number are written instead of the top-k.
+nrlsh_status run_tc_chunk(const nrlsh_index* ix, const float* Q, int64_t qc, const int32_t* ks,
+                          int k, const int64_t* budgets, int64_t budget, uint32_t flags,
+                          bool hist_tc, int hist_qb, const TcWs& w, int64_t* ids, float* scores,
+                          int out_ld, cudaStream_t st, uint32_t* H_out = nullptr,
+                          int32_t* cand_out = nullptr, int64_t cand_cap = 0,
+                          int64_t* count_out = nullptr) {
+    uint32_t* H = H_out ? H_out : w.H;
+    const int Kq = 64 * tc_query_k_chunks(ix->d);
+    const int nqt = tc_nqt(qc);
+    NRLSH_CK(launch_hash_queries(Q, qc, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, w.qnorm,
+                                 w.qcodes, ix->code_bytes, w.qamb_list, w.qamb, (unsigned)w.qamb_cap,
+                                 ix->At32, st));
+    NRLSH_CK(launch_prep_queries(Q, qc, ix->d, Kq, w.qcodes, ix->code_bytes, ix->L, w.Qb, w.Qs,
+                                 w.err, st));
+    if (hist_tc) {
+        NRLSH_CK(launch_pairs_tc(false, w.Qb, w.Qs, qc, ix->tc_xb, ix->tc_xs, ix->n, ix->d, ix->dp,
+                                 ix->m, ix->L, ix->seg, nullptr, nullptr, H, nullptr, nullptr,
+                                 nullptr, nullptr, nullptr, 0.0f, nullptr, nullptr, nullptr, 0,
+                                 w.err, st, test_spin_first()));
+    } else {
+        if (!ix->tiles_exclusive)
+            NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
+        NRLSH_CK(launch_hist(ix->codes, w.qcodes, ix->code_bytes, qc, ix->m, ix->L, ix->tiles,
+                             ix->ntiles, H, st, hist_qb, ix->tiles_exclusive));
+    }
+    if (H_out) return cuda_status_ok(launch_report_err(w.err, ix->query_err, st));
+    NRLSH_CK(cudaMemsetAsync(w.flag, 0, (size_t)ix->m * nqt, st));
+    NRLSH_CK(launch_tc_walk(H, ix->order, ix->m, ix->L, ix->n, ix->seg, qc, budget, budgets, w.cap,
+                            flags, ix->codes, w.qcodes, ix->code_bytes, w.lam, w.off, w.tb, w.bnd,
+                            w.flag, nqt, w.err, st));
+    NRLSH_CK(launch_work_list(w.flag, ix->m * nqt, w.list, w.nlist, st));
+    const float c_tc = tc_score_bound(ix->d, ix->dtype == NRLSH_F32);
+    NRLSH_CK(launch_pairs_tc(true, w.Qb, w.Qs, qc, ix->tc_xb, ix->tc_xs, ix->n, ix->d, ix->dp,
+                             ix->m, ix->L, ix->seg, w.list, w.nlist, nullptr, w.lam, w.off, w.tb,
+                             ix->xnorm, w.qnorm, c_tc, w.cand, w.lo, w.hi, w.cap, w.err,
+                             st, test_spin_first()));
+    // the last kernel skips its work when the call's error word is set and
+    // copies that word into the index's
+    if (cand_out)
+        return cuda_status_ok(launch_cand_to_ids(w.cand, w.cap, w.bnd, ix->perm, qc, cand_out,
+                                                 cand_cap, count_out, st, w.err, ix->query_err));
+    NRLSH_CK(launch_topk(w.lo, w.hi, w.cand, w.cap, w.bnd, qc, k, ks, ix->Xp, ix->dtype, ix->dp,
+                         ix->d, Q, ix->xnorm, w.qnorm, ix->perm, w.cont, w.cont_s, ids, scores,
+                         out_ld, st, w.err, ix->query_err));
+    return NRLSH_OK;
+}
+
+// The query path on tensor cores up to `stage` (TopK, Cand or Hist; outputs as
+// for run_queries): chunks of queries, scratch from the pool.
+nrlsh_status run_queries_tc(const nrlsh_index* ix, const float* Q, int64_t nq, int32_t k,
+                            int64_t budget, uint32_t flags, Stage stage, const QueryOut& o,
+                            cudaStream_t st) {
+    const bool whole = (flags & NRLSH_WHOLE_BUCKETS) != 0;
+    // with whole buckets a query's list can exceed B: room for all n items
+    const int64_t cap = stage == Stage::Hist ? 1 : whole ? ix->n : std::min(budget, ix->n);
+    const int64_t chunk = tc_chunk(ix, nq, cap);
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t qc = std::min(chunk, nq - q0);
+        Scratch sc(st);
+        TcWs w;
+        NRLSH_CKS(tc_ws_scratch(sc, w, ix, qc, cap));
+        const float* Qc = Q + q0 * ix->d;
+        const uint32_t fl = flags & NRLSH_WHOLE_BUCKETS;
+        if (stage == Stage::Hist) {
+            NRLSH_CKS(run_tc_chunk(ix, Qc, qc, nullptr, 1, nullptr, 1, fl, true, 64, w, nullptr,
+                                   nullptr, 1, st, o.H + q0 * ix->ncls));
+        } else if (stage == Stage::Cand) {
+            NRLSH_CKS(run_tc_chunk(ix, Qc, qc, nullptr, 1, nullptr, budget, fl, true, 64, w,
+                                   nullptr, nullptr, 1, st, nullptr, o.cand + q0 * o.cand_cap,
+                                   o.cand_cap, o.count + q0));
+        } else {
+            NRLSH_CKS(run_tc_chunk(ix, Qc, qc, nullptr, k, nullptr, budget, fl, true, 64, w,
+                                   o.ids + q0 * o.k_ld, o.scores + q0 * o.k_ld, o.k_ld, st));
+        }
+    }
+    return NRLSH_OK;
+}
+
 // Multi-table single probe (Algorithm 2) for queries [0, nq): hash, then select
 // C(q) and take the exact top-k of its first `cap` items (or, with cand_ids,
 // report their ids).  Queries go in chunks whose scratch stays within 1 GiB.
@@ -867,12 +1155,18 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* querie
     NRLSH_CKS(check_query_args(ix, queries, nq));
     if (k < 1 || k > NRLSH_MAX_K) return arg_error("need 1 <= k <= 1024");
     if (probe_budget < 1) return arg_error("need probe_budget >= 1");
-    if (flags & ~NRLSH_WHOLE_BUCKETS) return arg_error("unknown flags");
+    if (flags & ~(NRLSH_WHOLE_BUCKETS | NRLSH_QUERY_TENSOR)) return arg_error("unknown flags");
     if (nq > 0 && (!ids || !scores)) return arg_error("ids/scores is NULL");
+    const bool tensor = (flags & NRLSH_QUERY_TENSOR) != 0;
+    if (tensor && !tc_path_supported(ix)) {
+        set_error("the tensor-core query path needs an sm_100-family GPU and rows that fit its tiles");
+        return NRLSH_ERR_UNSUPPORTED;
+    }
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
     NRLSH_CK(wait_for_build(ix, st));
+    if (tensor) NRLSH_CKS(tensor_query_prologue(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -881,7 +1175,10 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* querie
     NRLSH_CKS(stage_out(sc, ids, (size_t)nq * k, oi, &o.ids));
     NRLSH_CKS(stage_out(sc, scores, (size_t)nq * k, os, &o.scores));
     o.k_ld = k;
-    NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, k, probe_budget, flags, Stage::TopK, o, st));
+    if (tensor)
+        NRLSH_CKS(run_queries_tc(ix, (const float*)Qd, nq, k, probe_budget, flags, Stage::TopK, o, st));
+    else
+        NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, k, probe_budget, flags, Stage::TopK, o, st));
     return finish_out(st, {&oi, &os}, oi.host || os.host || Qd != queries);
 }
 
@@ -909,20 +1206,27 @@ NRLSH_API nrlsh_status nrlsh_hash_queries(const nrlsh_index* ix, const float* qu
 }
 
 NRLSH_API nrlsh_status nrlsh_query_histograms(const nrlsh_index* ix, const float* queries,
-                                              int64_t nq, uint32_t* H, void* stream) {
+                                              int64_t nq, uint32_t* H, uint32_t flags,
+                                              void* stream) {
     NRLSH_CKS(check_query_args(ix, queries, nq));
     if (nq > 0 && !H) return arg_error("H is NULL");
+    if (flags & ~NRLSH_QUERY_TENSOR) return arg_error("unknown flags");
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
     NRLSH_CK(wait_for_build(ix, st));
+    const bool tensor = (flags & NRLSH_QUERY_TENSOR) != 0;
+    if (tensor) NRLSH_CKS(tensor_query_prologue(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
     OutStage oh;
     QueryOut o;
     NRLSH_CKS(stage_out(sc, H, (size_t)nq * ix->ncls, oh, &o.H));
-    NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, 1, 0u, Stage::Hist, o, st));
+    if (tensor)
+        NRLSH_CKS(run_queries_tc(ix, (const float*)Qd, nq, 1, 1, 0u, Stage::Hist, o, st));
+    else
+        NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, 1, 0u, Stage::Hist, o, st));
     return finish_out(st, {&oh}, oh.host || Qd != queries);
 }
 
@@ -987,12 +1291,14 @@ NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* ix, const float
     NRLSH_CKS(check_query_args(ix, queries, nq));
     if (probe_budget < 1) return arg_error("need probe_budget >= 1");
     if (cap < 1) return arg_error("need cap >= 1");
-    if (flags & ~NRLSH_WHOLE_BUCKETS) return arg_error("unknown flags");
+    if (flags & ~(NRLSH_WHOLE_BUCKETS | NRLSH_QUERY_TENSOR)) return arg_error("unknown flags");
     if (nq > 0 && (!cand || !count)) return arg_error("cand/count is NULL");
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
     NRLSH_CK(wait_for_build(ix, st));
+    const bool tensor = (flags & NRLSH_QUERY_TENSOR) != 0;
+    if (tensor) NRLSH_CKS(tensor_query_prologue(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -1001,7 +1307,10 @@ NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* ix, const float
     NRLSH_CKS(stage_out(sc, cand, (size_t)(nq * cap), oc, &o.cand));
     NRLSH_CKS(stage_out(sc, count, (size_t)nq, on, &o.count));
     o.cand_cap = cap;
-    NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, probe_budget, flags, Stage::Cand, o, st));
+    if (tensor)
+        NRLSH_CKS(run_queries_tc(ix, (const float*)Qd, nq, 1, probe_budget, flags, Stage::Cand, o, st));
+    else
+        NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, 1, probe_budget, flags, Stage::Cand, o, st));
     NRLSH_CKS(finish_out(st, {&oc, &on}, true));
     // counts are needed on the host to report an overflow of `cap`
     std::vector<int64_t> hc(nq);
@@ -1018,6 +1327,12 @@ NRLSH_API nrlsh_status nrlsh_query_candidates(const nrlsh_index* ix, const float
 NRLSH_API nrlsh_status nrlsh_get_codes(const nrlsh_index* ix, uint64_t* codes) {
     if (!ix || !codes) return arg_error("NULL argument");
     NRLSH_CK(cudaStreamSynchronize(ix->stream));
+    int derr = 0;
+    NRLSH_CK(cudaMemcpy(&derr, ix->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (derr) {
+        set_error("a bounded device wait of the index build ran out: its codes are incomplete");
+        return NRLSH_ERR_TIMEOUT;
+    }
     const int64_t n = ix->n;
     std::vector<uint32_t> perm(n);
     std::vector<unsigned char> raw((size_t)n * ix->code_bytes);
@@ -1101,6 +1416,24 @@ NRLSH_API nrlsh_status nrlsh_get_info(const nrlsh_index* ix, nrlsh_info* info) {
     unsigned nfb = 0;
     NRLSH_CK(cudaMemcpy(&nfb, ix->norm_fb, sizeof(nfb), cudaMemcpyDeviceToHost));
     info->norm_fallbacks = (int32_t)nfb;
+    int qerr = 0;
+    NRLSH_CK(cudaMemcpy(&qerr, ix->query_err, sizeof(int), cudaMemcpyDeviceToHost));
+    info->query_error = qerr;
+    // the statistics are filled either way; the status reports what went wrong
+    if (derr) {
+        set_error("a bounded device wait of the index build ran out (code " +
+                  std::to_string(derr) + "): its codes are incomplete");
+        return NRLSH_ERR_TIMEOUT;
+    }
+    if (qerr == 15) {
+        set_error("a tensor-core query kernel found other candidates than it counted");
+        return NRLSH_ERR_CUDA;
+    }
+    if (qerr) {
+        set_error("a bounded device wait of a tensor-core query kernel ran out (code " +
+                  std::to_string(qerr) + "): that call's results are invalid");
+        return NRLSH_ERR_TIMEOUT;
+    }
     return NRLSH_OK;
 }
 
@@ -1219,10 +1552,32 @@ void batch_ws_assign(BatchWs& w, const std::vector<void*>& p, const nrlsh_index*
     w.ctas = ctas;
 }
 
-// The launch sequence of a batch (device pointers only).
+// Workspace buffers of a configuration: the persistent FP32 path's, or one chunk
+// of the tensor-core path's.
+std::vector<size_t> cfg_ws_sizes(const nrlsh_index* ix, const nrlsh_batch_cfg& cfg, int64_t nq,
+                                 int64_t cap) {
+    if (cfg.rerank_tc) return tc_ws_sizes(ix, tc_chunk(ix, nq, cap), cap);
+    return batch_ws_sizes(ix, nq, cap, batch_ctas(cfg, cap));
+}
+
+// The launch sequence of a batch (device pointers only) in workspace p.
 nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, const int32_t* ks,
                          const int64_t* budgets, int k_max, int64_t cap, const nrlsh_batch_cfg& cfg,
-                         const BatchWs& w, int64_t* ids, float* scores, cudaStream_t st) {
+                         const std::vector<void*>& p, int64_t* ids, float* scores, cudaStream_t st) {
+    if (cfg.rerank_tc) {
+        const int64_t chunk = tc_chunk(ix, nq, cap);
+        TcWs w;
+        tc_ws_assign(w, p, ix, chunk, cap);
+        for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+            const int64_t qc = std::min(chunk, nq - q0);
+            NRLSH_CKS(run_tc_chunk(ix, Q + q0 * ix->d, qc, ks + q0, k_max, budgets + q0, 0, 0u,
+                                   cfg.hist_tc != 0, cfg.hist_qb, w, ids + q0 * k_max,
+                                   scores + q0 * k_max, k_max, st));
+        }
+        return NRLSH_OK;
+    }
+    BatchWs w;
+    batch_ws_assign(w, p, ix, nq, batch_ctas(cfg, cap));
     NRLSH_CK(launch_hash_queries(Q, nq, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, w.qnorm,
                                  w.qcodes, ix->code_bytes, w.qamb_list, w.qamb,
                                  (unsigned)w.qamb_cap, ix->At32, st));
@@ -1244,54 +1599,85 @@ nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, cons
     return NRLSH_OK;
 }
 
+// Which paths a batched call may use: 0 either (autotuned), 1 tensor cores only,
+// 2 FP32 CUDA cores only.
+int batch_mode(uint32_t flags) {
+    return (flags & NRLSH_QUERY_TENSOR) ? 1 : (flags & NRLSH_QUERY_FP32) ? 2 : 0;
+}
+
 // Time the candidate configurations on a prefix of the batch; keep the fastest.
+// FP32 path: the popcount histogram's query tile (32, 64, 128) and the persistent
+// re-rank's CTAs per SM (1, 2, 4).  Tensor-core path: histograms on tensor cores
+// or by popcount (best tile), candidates and scores on tensor cores.
 nrlsh_status autotune(const nrlsh_index* ix, const float* Q, int64_t nq, const int32_t* ks,
-                      const int64_t* budgets, int k_max, int64_t cap, int64_t* ids, float* scores,
-                      cudaStream_t st, nrlsh_batch_cfg* best) {
+                      const int64_t* budgets, int k_max, int64_t cap, int mode, int64_t* ids,
+                      float* scores, cudaStream_t st, nrlsh_batch_cfg* best) {
     const int64_t nt = std::min<int64_t>(nq, 2048);
     cudaEvent_t e0, e1;
     NRLSH_CK(cudaEventCreate(&e0));
     NRLSH_CK(cudaEventCreate(&e1));
     auto time_cfg = [&](const nrlsh_batch_cfg& c, float* ms) -> nrlsh_status {
         Scratch sc(st);
-        const int ctas = batch_ctas(c, cap);
-        const auto sizes = batch_ws_sizes(ix, nt, cap, ctas);
         std::vector<void*> p;
-        for (size_t b : sizes) {
+        for (size_t b : cfg_ws_sizes(ix, c, nt, cap)) {
             char* q = nullptr;
             NRLSH_CKS(sc.get(&q, b));
             p.push_back(q);
         }
-        BatchWs w;
-        batch_ws_assign(w, p, ix, nt, ctas);
-        NRLSH_CKS(run_batched(ix, Q, nt, ks, budgets, k_max, cap, c, w, ids, scores, st));  // warm
+        NRLSH_CKS(run_batched(ix, Q, nt, ks, budgets, k_max, cap, c, p, ids, scores, st));  // warm
         NRLSH_CK(cudaEventRecord(e0, st));
-        NRLSH_CKS(run_batched(ix, Q, nt, ks, budgets, k_max, cap, c, w, ids, scores, st));
+        NRLSH_CKS(run_batched(ix, Q, nt, ks, budgets, k_max, cap, c, p, ids, scores, st));
         NRLSH_CK(cudaEventRecord(e1, st));
         NRLSH_CK(cudaEventSynchronize(e1));
         NRLSH_CK(cudaEventElapsedTime(ms, e0, e1));
         return NRLSH_OK;
     };
-    nrlsh_batch_cfg c;
     float best_ms = 1e30f;
-    for (int qb : {32, 64, 128}) {
-        c.hist_qb = qb;
-        c.ctas_per_sm = 2;
+    auto consider = [&](const nrlsh_batch_cfg& c) -> nrlsh_status {
         float ms;
         NRLSH_CKS(time_cfg(c, &ms));
         if (ms < best_ms) {
             best_ms = ms;
             *best = c;
         }
+        return NRLSH_OK;
+    };
+    nrlsh_batch_cfg c;
+    int best_qb = 64;
+    {
+        // the popcount histogram's tile (FP32 re-rank at 2 CTAs per SM)
+        float qb_ms = 1e30f;
+        for (int qb : {32, 64, 128}) {
+            c = nrlsh_batch_cfg{};
+            c.hist_qb = qb;
+            c.ctas_per_sm = 2;
+            float ms;
+            NRLSH_CKS(time_cfg(c, &ms));
+            if (ms < qb_ms) {
+                qb_ms = ms;
+                best_qb = qb;
+            }
+            if (mode != 1 && ms < best_ms) {
+                best_ms = ms;
+                *best = c;
+            }
+        }
     }
-    for (int cps : {1, 4}) {
-        c = *best;
-        c.ctas_per_sm = cps;
-        float ms;
-        NRLSH_CKS(time_cfg(c, &ms));
-        if (ms < best_ms) {
-            best_ms = ms;
-            *best = c;
+    if (mode != 1) {
+        for (int cps : {1, 4}) {
+            c = nrlsh_batch_cfg{};
+            c.hist_qb = best_qb;
+            c.ctas_per_sm = cps;
+            NRLSH_CKS(consider(c));
+        }
+    }
+    if (mode != 2 && tc_path_supported(ix)) {
+        for (int htc : {1, 0}) {
+            c = nrlsh_batch_cfg{};
+            c.hist_qb = best_qb;
+            c.rerank_tc = 1;
+            c.hist_tc = htc;
+            NRLSH_CKS(consider(c));
         }
     }
     cudaEventDestroy(e0);
@@ -1309,8 +1695,16 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     NRLSH_CKS(check_query_args(ix, queries, nq));
     if (k_max < 1 || k_max > NRLSH_MAX_K) return arg_error("need 1 <= k_max <= 1024");
     if (budget_max < 1) return arg_error("need budget_max >= 1");
-    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE)) return arg_error("unknown flags");
+    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE | NRLSH_QUERY_TENSOR | NRLSH_QUERY_FP32))
+        return arg_error("unknown flags");
+    if ((flags & NRLSH_QUERY_TENSOR) && (flags & NRLSH_QUERY_FP32))
+        return arg_error("NRLSH_QUERY_TENSOR and NRLSH_QUERY_FP32 exclude each other");
     if (nq > 0 && (!ids || !scores || !ks || !budgets)) return arg_error("NULL array");
+    const int mode = batch_mode(flags);
+    if (mode == 1 && !tc_path_supported(ix)) {
+        set_error("the tensor-core query path needs an sm_100-family GPU and rows that fit its tiles");
+        return NRLSH_ERR_UNSUPPORTED;
+    }
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
@@ -1320,6 +1714,11 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     if (graph && !(is_device_ptr(queries) && is_device_ptr(ks) && is_device_ptr(budgets) &&
                    is_device_ptr(ids) && is_device_ptr(scores)))
         return arg_error("NRLSH_QUERY_GRAPH needs device pointers");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st) NRLSH_CK(cudaStreamIsCapturing(st, &cs));
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    // the tensor path's index operands exist before any tuning or capture
+    if (mode != 2 && tc_path_supported(ix)) NRLSH_CKS(ensure_tc_items(ix, st, capturing));
     Scratch sc(st);
     const void *Qd, *ksd, *bd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
@@ -1332,38 +1731,35 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     NRLSH_CKS(stage_out(sc, scores, (size_t)nq * k_max, os, &scd));
 
     nrlsh_batch_cfg cfg;
+    if (mode == 1) {
+        cfg.rerank_tc = 1;
+        cfg.hist_tc = 1;
+    }
     {
         std::lock_guard<std::mutex> g(ix->batch_mu);
-        const auto key = std::make_tuple(nq, (int)k_max, cap);
+        const auto key = std::make_tuple(nq, (int)k_max, cap, mode);
         auto it = ix->tuned.find(key);
         if (it != ix->tuned.end()) {
             cfg = it->second;
         } else if (flags & NRLSH_QUERY_NO_TUNE) {
-            if (ix->last_cfg.hist_qb) cfg = ix->last_cfg;
-        } else {
-            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-            if (st) cudaStreamIsCapturing(st, &cs);
-            if (cs == cudaStreamCaptureStatusNone) {
-                NRLSH_CKS(autotune(ix, (const float*)Qd, nq, (const int32_t*)ksd,
-                                   (const int64_t*)bd, k_max, cap, idsd, scd, st, &cfg));
-                ix->tuned[key] = cfg;
-            }
+            const nrlsh_batch_cfg& l = ix->last_cfg;
+            if (l.hist_qb && (mode == 0 || (mode == 1) == (l.rerank_tc != 0))) cfg = l;
+        } else if (!capturing) {
+            NRLSH_CKS(autotune(ix, (const float*)Qd, nq, (const int32_t*)ksd, (const int64_t*)bd,
+                               k_max, cap, mode, idsd, scd, st, &cfg));
+            ix->tuned[key] = cfg;
         }
         ix->last_cfg = cfg;
     }
-    const int ctas = batch_ctas(cfg, cap);
     if (!graph) {
-        const auto sizes = batch_ws_sizes(ix, nq, cap, ctas);
         std::vector<void*> p;
-        for (size_t b : sizes) {
+        for (size_t b : cfg_ws_sizes(ix, cfg, nq, cap)) {
             char* q = nullptr;
             NRLSH_CKS(sc.get(&q, b));
             p.push_back(q);
         }
-        BatchWs w;
-        batch_ws_assign(w, p, ix, nq, ctas);
         NRLSH_CKS(run_batched(ix, (const float*)Qd, nq, (const int32_t*)ksd, (const int64_t*)bd,
-                              k_max, cap, cfg, w, idsd, scd, st));
+                              k_max, cap, cfg, p, idsd, scd, st));
         return finish_out(st, {&oi, &os}, oi.host || os.host || Qd != queries || ksd != ks ||
                                               bd != budgets);
     }
@@ -1372,13 +1768,18 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     const auto key = std::make_tuple((const void*)queries, nq, (const void*)ks, (const void*)budgets,
                                      (int)k_max, cap, (const void*)ids, (const void*)scores, stream);
     for (auto& e : ix->graphs)
-        if (e.key == key) {
+        if (e.key == key && e.rerank_tc == cfg.rerank_tc && e.hist_tc == cfg.hist_tc &&
+            e.hist_qb == cfg.hist_qb && e.ctas_per_sm == cfg.ctas_per_sm) {
             NRLSH_CK(cudaGraphLaunch(e.exec, st));
             return NRLSH_OK;
         }
     nrlsh_graph_entry e;
     e.key = key;
-    for (size_t b : batch_ws_sizes(ix, nq, cap, ctas)) {
+    e.rerank_tc = cfg.rerank_tc;
+    e.hist_tc = cfg.hist_tc;
+    e.hist_qb = cfg.hist_qb;
+    e.ctas_per_sm = cfg.ctas_per_sm;
+    for (size_t b : cfg_ws_sizes(ix, cfg, nq, cap)) {
         void* q = nullptr;
         cudaError_t err = cudaMalloc(&q, std::max<size_t>(b, 16));
         if (err != cudaSuccess) {
@@ -1387,12 +1788,10 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
         }
         e.workspace.push_back(q);
     }
-    BatchWs w;
-    batch_ws_assign(w, e.workspace, ix, nq, ctas);
     cudaGraph_t gr = nullptr;
     NRLSH_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    const nrlsh_status rs = run_batched(ix, queries, nq, ks, budgets, k_max, cap, cfg, w, ids,
-                                        scores, st);
+    const nrlsh_status rs = run_batched(ix, queries, nq, ks, budgets, k_max, cap, cfg, e.workspace,
+                                        ids, scores, st);
     const cudaError_t ce = cudaStreamEndCapture(st, &gr);
     if (rs != NRLSH_OK || ce != cudaSuccess) {
         if (gr) cudaGraphDestroy(gr);
@@ -1412,29 +1811,51 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
 
 extern "C" NRLSH_API nrlsh_status nrlsh_batched_scratch_bytes(const nrlsh_index* ix, int64_t nq,
                                                               int32_t k_max, int64_t budget_max,
-                                                              int64_t* bytes) {
+                                                              uint32_t flags, int64_t* bytes) {
     if (!ix || !bytes) return arg_error("NULL argument");
     if (nq < 0 || k_max < 1 || budget_max < 1) return arg_error("bad sizes");
-    nrlsh_batch_cfg cfg;
+    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE | NRLSH_QUERY_TENSOR | NRLSH_QUERY_FP32))
+        return arg_error("unknown flags");
+    const int mode = batch_mode(flags);
+    const int64_t cap = std::min<int64_t>(budget_max, ix->n);
+    const int64_t qn = std::max<int64_t>(nq, 1);
+    // the configuration nrlsh_query_batched would use for these sizes and flags: a
+    // tuned one for (nq, k_max, cap) when it exists (with no path restriction, the
+    // largest of them), else the last one used when it is allowed, else the
+    // path's default
+    std::vector<nrlsh_batch_cfg> cfgs;
     {
         std::lock_guard<std::mutex> g(ix->batch_mu);
-        if (ix->last_cfg.hist_qb) cfg = ix->last_cfg;
+        for (const auto& kv : ix->tuned)
+            if (std::get<0>(kv.first) == nq && std::get<1>(kv.first) == (int)k_max &&
+                std::get<2>(kv.first) == cap && (mode == 0 || std::get<3>(kv.first) == mode))
+                cfgs.push_back(kv.second);
+        if (cfgs.empty()) {
+            const nrlsh_batch_cfg& l = ix->last_cfg;
+            nrlsh_batch_cfg c;
+            if (mode == 1) c.rerank_tc = c.hist_tc = 1;
+            if (l.hist_qb && (mode == 0 || (mode == 1) == (l.rerank_tc != 0))) c = l;
+            cfgs.push_back(c);
+        }
     }
-    const int64_t cap = std::min<int64_t>(budget_max, ix->n);
     int64_t total = 0;
-    for (size_t b : batch_ws_sizes(ix, std::max<int64_t>(nq, 1), cap, batch_ctas(cfg, cap)))
-        total += (int64_t)((std::max<size_t>(b, 16) + 255) / 256 * 256);
-    (void)k_max;
+    for (const auto& cfg : cfgs) {
+        int64_t t = 0;
+        for (size_t b : cfg_ws_sizes(ix, cfg, qn, cap))
+            t += (int64_t)((std::max<size_t>(b, 16) + 255) / 256 * 256);
+        total = std::max(total, t);
+    }
     *bytes = total;
     return NRLSH_OK;
 }
 
 extern "C" NRLSH_API nrlsh_status nrlsh_get_tuning(const nrlsh_index* ix, int32_t* hist_qb,
-                                                   int32_t* ctas_per_sm) {
+                                                   int32_t* ctas_per_sm, int32_t* tensor) {
     if (!ix) return arg_error("index is NULL");
     std::lock_guard<std::mutex> g(ix->batch_mu);
     if (hist_qb) *hist_qb = ix->last_cfg.hist_qb;
     if (ctas_per_sm) *ctas_per_sm = ix->last_cfg.ctas_per_sm;
+    if (tensor) *tensor = (ix->last_cfg.hist_tc ? 1 : 0) | (ix->last_cfg.rerank_tc ? 2 : 0);
     return NRLSH_OK;
 }
 

@@ -229,7 +229,8 @@ cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2,
                               const float* A_pad, const float* anorm, const float* tau32,
                               const double* tau64, const float* xnorm, bool fp32_items,
                               void* codes, int code_bytes, unsigned long long* amb_list,
-                              unsigned* amb_count, unsigned amb_cap, int* err, cudaStream_t st);
+                              unsigned* amb_count, unsigned amb_cap, int* err, cudaStream_t st,
+                              uint32_t spin_first = 1u << 22);
 // c_l = cos(pi (1 - eps)(L - l) / L), correctly rounded, l = 0..L.
 cudaError_t launch_class_cos(int L, float eps, double* cl, cudaStream_t st);
 // The sorted (U_j, l) structure: probing order of the m (L+1) buckets.
@@ -270,7 +271,8 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
                         const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
                         const float* xnorm, const float* qnorm, const uint32_t* perm,
                         uint32_t* cont, double* cont_s, int64_t* out_ids, float* out_scores,
-                        int out_ld, cudaStream_t st);
+                        int out_ld, cudaStream_t st, const int* skip = nullptr,
+                        int* report = nullptr);
 // Threshold walk, candidate selection, FP32 re-rank and exact top-k, one block
 // per query (the main query path after the histograms).
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
@@ -318,8 +320,63 @@ cudaError_t launch_rerank_work(const void* Xp, nrlsh_dtype dt, int dp, int d, co
                                const float* qnorm, float* lo, float* hi, cudaStream_t st);
 // CTAs of the persistent re-rank kernel resident at once (at most nq).
 int probe_rerank_ctas(nrlsh_dtype dt, int code_bytes, int dp, int m, int64_t nq);
+// ---------------------------------------------- tensor-core query path
+
+// Boundary bucket of a query for the tensor-core re-rank: (j*, l*) and the
+// storage position of the last item taken from it (-1: none).
+struct TcBoundary {
+    int32_t j;
+    int32_t l;
+    int64_t pcut;
+};
+// sm_100-family device, and the operands of rows of d values fit shared memory.
+bool tc_query_supported(int d, int L);
+// 64-element K chunks of a row of d values.
+int tc_query_k_chunks(int d);
+// c_tc: |score_tc - score_fp64| <= c_tc ||q|| ||x|| for the bf16 tensor-core scores.
+float tc_score_bound(int d, bool fp32_items);
+// Qb (nq x 64 tc_query_k_chunks(d) bf16) and Qs (nq x 64 bf16 +-1 signs of the codes).
+// Also clears the call's error word *err (the tensor-path kernels' timeouts).
+cudaError_t launch_prep_queries(const float* Q, int64_t nq, int d, int Kq, const void* qcodes,
+                                int code_bytes, int L, __nv_bfloat16* Qb, __nv_bfloat16* Qs,
+                                int* err, cudaStream_t st);
+// *report = *err when *report is still 0 and *err is not.
+cudaError_t launch_report_err(const int* err, int* report, cudaStream_t st);
+// Xs (n x 64 bf16): the +-1 signs of the item codes, storage order.
+cudaError_t launch_item_signs(const void* codes, int code_bytes, int64_t n, int L,
+                              __nv_bfloat16* Xs, cudaStream_t st);
+cudaError_t launch_to_bf16(const float* X, int64_t count, __nv_bfloat16* Xb, cudaStream_t st);
+// The dense (query tile x item tile) tcgen05 kernel over the sub-datasets:
+// rerank = false: the Hamming histograms H (every entry written; list may be null
+// for all work items); rerank = true: the candidates of the work items in list
+// (nlist entries, on the device) with their score intervals.
+cudaError_t launch_pairs_tc(bool rerank, const __nv_bfloat16* Qb, const __nv_bfloat16* Qs,
+                            int64_t nq, const __nv_bfloat16* Xb, const __nv_bfloat16* Xs,
+                            int64_t n, int d, int dp, int m, int L, const int64_t* seg,
+                            const uint32_t* list, const uint32_t* nlist, uint32_t* H,
+                            const uint8_t* lam, const uint32_t* off, const TcBoundary* tb,
+                            const float* xnorm, const float* qnorm, float c_tc, uint32_t* cand,
+                            float* lo, float* hi, int64_t cap, int* err, cudaStream_t st,
+                            uint32_t spin_first = 1u << 22);
+// Bucket walk of every query (budgets per query or one budget, clamped to [1, cap]),
+// then per sub-dataset the probed counts as list offsets off (nq x (m + 1)), the
+// boundary cut (tb), bnd[q].full = min(B, n) (r = 0) for the top-k pass, and
+// work_flag[j * nqt + q / 128] = 1 where query q probes S_j (flags zeroed first).
+// With *err set (the histograms are incomplete) nothing is probed.
+cudaError_t launch_tc_walk(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
+                           const int64_t* seg, int64_t nq, int64_t budget, const int64_t* budgets,
+                           int64_t cap, uint32_t flags, const void* codes, const void* qcodes,
+                           int code_bytes, uint8_t* lam, uint32_t* off, TcBoundary* tb,
+                           Boundary* bnd, uint8_t* work_flag, int nqt, const int* err,
+                           cudaStream_t st);
+// Indices of the nonzero flags, ascending (list), and their number (*count).
+cudaError_t launch_work_list(const uint8_t* flag, int nflag, uint32_t* list, uint32_t* count,
+                             cudaStream_t st);
+
+// skip / report (may be null): as for launch_topk.
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
                                const uint32_t* perm, int64_t nq, int32_t* out, int64_t out_cap,
-                               int64_t* count, cudaStream_t st);
+                               int64_t* count, cudaStream_t st, const int* skip = nullptr,
+                               int* report = nullptr);
 
 }  // namespace nrlsh

@@ -17,13 +17,13 @@
 // *err, stops issuing work, waits (bounded) for its own copies, frees TMEM and
 // returns.
 #include "nrlsh_internal.cuh"
-
-#include <cuda.h>
-#include <cudaTypedefs.h>
+#include "tc_ops.cuh"
 
 #include <mutex>
 
 namespace nrlsh {
+
+using namespace tc;
 
 namespace {
 
@@ -34,122 +34,7 @@ constexpr int kTcStagesTwo = 3;  // stages of two 16 KB tiles (split fp32 items)
 constexpr int kTcThreads = 192;
 constexpr uint32_t kTmemCols = 128;  // two accumulators of up to 64 fp32 columns
 constexpr uint32_t kXStageBytes = kTcM * kTcKC * 2;
-constexpr uint32_t kSpinLimit = 1u << 22;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(dst)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
-}
-
-// D[tmem] (+)= A[smem] B[smem]^T, bf16 inputs, fp32 accumulation.
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// Arrive on the mbarrier once all tcgen05.mma issued so far by this thread complete.
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-
-// 32 TMEM lanes x 16 columns of 32 bits: thread t receives lane (base lane + t).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile laid out by TMA with
-// the 128-byte swizzle: rows of 128 bytes, 8-row groups 1,024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(const void* base) {
-    const uint32_t addr = smem_u32(base);
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
-    d |= (uint64_t)1 << 16;                   // leading byte offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
-    d |= (uint64_t)1 << 46;                   // descriptor version
-    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: bf16 A and B (both K-major), fp32 D, M x N.
-__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
 
 struct TcSmem {
     int nkc, N, split, stages;
@@ -174,7 +59,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                       const void* __restrict__ X_exact, int fp32_items, int ldx,
                       const double* __restrict__ tau64, C* __restrict__ codes,
                       unsigned long long* __restrict__ amb_list, unsigned* amb_count,
-                      unsigned amb_cap, int* err) {
+                      unsigned amb_cap, int* err, uint32_t spin_first) {
     NRLSH_PDL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -220,9 +105,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         s_c2[b] = 0x1p-20f * fabsf(ad);
     }
     if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
@@ -270,19 +155,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int stage = 0;
             uint32_t phase = 0, acc_phase = 0;
             int buf = 0;
+            bool first = true;  // the first wait for a stage takes spin_first polls at most
             for (int64_t t = blockIdx.x; ok && t < ntiles && !*abort_s; t += gridDim.x) {
                 if (!mbar_wait(&acc_empty[buf], acc_phase ^ 1)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
+                fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)buf * 64;
                 for (int c = 0; c < nkc; ++c) {
-                    if (!mbar_wait(&full[stage], phase)) {
+                    const uint32_t lim = first ? spin_first : kSpinLimit;
+                    first = false;
+                    if (!mbar_wait(&full[stage], phase, lim)) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
+                    fence_after();
                     const uint64_t bdesc = sw128_desc(L_.a_tile(base, c));
                     for (int part = 0; part < split; ++part) {
                         const uint64_t adesc = sw128_desc(L_.x_stage(base, stage, part));
@@ -323,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 *abort_s = 1;
                 break;
             }
-            tc_fence_after();
+            fence_after();
             const int64_t row = t * kTcM + 32 * sub + lane;
             const bool valid = row < n;
             const float xn = valid ? xnorm[row] : 0.0f;
@@ -378,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 ++slot;
             }
-            tc_fence_before();
+            fence_before();
             mbar_arrive(&acc_empty[buf]);
             if (valid) codes[row] = (C)word;
             if (++buf == 2) {
@@ -387,15 +275,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 1) {
-        tc_fence_after();
+        fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -410,22 +300,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D bf16 tensor map: rows of `inner` elements (row stride `stride_elems`),
-// `outer` rows; box of 64 x box_rows with the 128-byte swizzle; zeros outside.
-bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer,
-              uint64_t stride_elems, uint32_t box_rows) {
-    auto fn = encode_fn();
+bool make_map_bf16(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer,
+                   uint64_t stride_elems, uint32_t box_rows) {
+    auto fn = tensor_map_encoder();
     if (!fn) return false;
     const cuuint64_t dims[2] = {inner, outer};
     const cuuint64_t strides[1] = {stride_elems * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kTcKC, box_rows};
+    const cuuint32_t box[2] = {64u, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 size_t project_tc_smem_bytes(int d, int N, int split) {
     const int nkc = (int)ceil_div(d, kTcKC);
@@ -441,7 +327,7 @@ bool project_tc_supported(int d, int L) {
     cudaGetLastError();
     if (major != 10) return false;
     const int N = L <= 16 ? 16 : L <= 32 ? 32 : L <= 48 ? 48 : 64;
-    return project_tc_smem_bytes(d, N, 2) <= 220 * 1024 && encode_fn() != nullptr;
+    return project_tc_smem_bytes(d, N, 2) <= 220 * 1024 && tensor_map_encoder() != nullptr;
 }
 
 cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2, const void* X_exact,
@@ -449,14 +335,15 @@ cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2,
                               const float* A_pad, const float* anorm, const float* tau32,
                               const double* tau64, const float* xnorm, bool fp32_items,
                               void* codes, int code_bytes, unsigned long long* amb_list,
-                              unsigned* amb_count, unsigned amb_cap, int* err, cudaStream_t st) {
+                              unsigned* amb_count, unsigned amb_cap, int* err, cudaStream_t st,
+                              uint32_t spin_first) {
     const int N = L <= 16 ? 16 : L <= 32 ? 32 : L <= 48 ? 48 : 64;
     const int nkc = (int)ceil_div(d, kTcKC);
     const int split = Xb2 ? 2 : 1;
     CUtensorMap map_x, map_x2, map_a;
-    if (!make_map(&map_x, Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
-        !make_map(&map_x2, Xb2 ? Xb2 : Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
-        !make_map(&map_a, At, (uint64_t)d, (uint64_t)N, (uint64_t)dp, (uint32_t)N))
+    if (!make_map_bf16(&map_x, Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
+        !make_map_bf16(&map_x2, Xb2 ? Xb2 : Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
+        !make_map_bf16(&map_a, At, (uint64_t)d, (uint64_t)N, (uint64_t)dp, (uint32_t)N))
         return cudaErrorNotSupported;
     const size_t smem = project_tc_smem_bytes(d, N, split);
     int dev = 0, sms = 0;
@@ -479,7 +366,7 @@ cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2,
         return launch("project_tc", kern, dim3(grid), dim3(kTcThreads), smem, st, map_x, map_x2, \
                       map_a, split, n, nkc, L, N, Lp, d, A_pad, anorm, tau32, xnorm, kappa_tc, \
                       round_x, X_exact, fp32_items ? 1 : 0, dp, tau64, (C_*)codes, amb_list,  \
-                      amb_count, amb_cap, err);                                              \
+                      amb_count, amb_cap, err, spin_first);                                  \
     }
     if (code_bytes == 4) NRLSH_TC(uint32_t)
     NRLSH_TC(uint64_t)

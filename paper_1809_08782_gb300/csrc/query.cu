@@ -226,6 +226,122 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) bnd[q] = b;
 }
 
+// ------------------------------------------------ walk for the tensor path
+
+// Block per query (256 threads): the bucket walk of dev_threshold, then for every
+// sub-dataset S_j the number of probed items, cnt_j = sum_{l >= lam_j} H[q][j][l]
+// (+ r for the boundary sub-dataset), whose exclusive prefix over j is where the
+// re-rank writes S_j's candidates (off[q][j], off[q][m] = min(B, n)).  The
+// boundary bucket's first r items in storage (= id) order are the ones at
+// positions <= pcut, found by one ordered sweep of S_j*.
+template <typename C>
+__global__ void __launch_bounds__(256)
+    tc_walk_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order, int m, int L,
+                   int64_t n, const int64_t* __restrict__ seg, int64_t budget,
+                   const int64_t* __restrict__ budgets, int64_t cap, uint32_t flags,
+                   const C* __restrict__ codes, const C* __restrict__ qcodes,
+                   uint8_t* __restrict__ lam, uint32_t* __restrict__ off, TcBoundary* __restrict__ tb,
+                   Boundary* __restrict__ bnd, uint8_t* __restrict__ work_flag, int nqt,
+                   const int* __restrict__ err) {
+    NRLSH_PDL_ENTRY();
+    extern __shared__ uint32_t cntj[];
+    uint8_t* lam_s = (uint8_t*)(cntj + m);
+    __shared__ uint32_t warp_tot[8];
+    __shared__ int64_t pcut_s;
+    const int64_t q = blockIdx.x;
+    if (*err) {
+        // the histograms are incomplete (a bounded wait ran out): nothing is probed,
+        // so no later kernel of the call reads past what it owns
+        for (int j = threadIdx.x; j <= m; j += blockDim.x) {
+            off[q * (m + 1) + j] = 0;
+            if (j < m) lam[q * m + j] = (uint8_t)(L + 1);
+        }
+        if (threadIdx.x == 0) {
+            tb[q] = TcBoundary{0, 0, -1};
+            bnd[q] = Boundary{0, 0, 0, 0};
+        }
+        return;
+    }
+    const int64_t Bq = min(max(budgets ? budgets[q] : budget, (int64_t)1), cap);
+    const uint32_t* Hq = H + q * m * (L + 1);
+    const Boundary b = dev_threshold(Hq, order, m, L, n, Bq, flags, cntj, lam_s);
+    uint32_t run = 0;
+    for (int base = 0; base < m; base += 256) {
+        const int j = base + threadIdx.x;
+        uint32_t c = 0;
+        if (j < m) {
+            const uint32_t* Hj = Hq + (int64_t)j * (L + 1);
+            for (int l = lam_s[j]; l <= L; ++l) c += Hj[l];
+            if (j == b.j) c += (uint32_t)b.r;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(c, &tot, warp_tot);
+        if (j < m) {
+            off[q * (m + 1) + j] = run + ex;
+            lam[q * m + j] = lam_s[j];
+            if (c) work_flag[(int64_t)j * nqt + q / 128] = 1;
+        }
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        off[q * (m + 1) + m] = run;
+        pcut_s = -1;
+    }
+    __syncthreads();
+    const int64_t p_lo = seg[b.j], p_hi = seg[b.j + 1];
+    const uint32_t in_bucket = Hq[(int64_t)b.j * (L + 1) + b.l];
+    if ((uint32_t)b.r >= in_bucket) {
+        if (threadIdx.x == 0) pcut_s = p_hi - 1;      // the whole bucket is probed
+    } else {
+        const C cq = qcodes[q];
+        uint32_t cum = 0;
+        for (int64_t p0 = p_lo; p0 < p_hi; p0 += 256) {
+            const int64_t p = p0 + threadIdx.x;
+            const uint32_t hit = p < p_hi && L - popc_word(cq ^ codes[p]) == b.l;
+            uint32_t tot;
+            const uint32_t ex = block_exclusive_scan(hit, &tot, warp_tot);
+            if (hit && cum + ex + 1 == (uint32_t)b.r) pcut_s = p;
+            cum += tot;
+            if (cum >= (uint32_t)b.r) break;          // the same decision in every thread
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tb[q] = TcBoundary{b.j, b.l, pcut_s};
+        bnd[q] = Boundary{b.j, b.l, 0, (int32_t)run};
+    }
+}
+
+// One block of 1,024 threads: indices of the nonzero flags in ascending order.
+__global__ void __launch_bounds__(1024)
+    work_list_kernel(const uint8_t* __restrict__ flag, int nflag, uint32_t* __restrict__ list,
+                     uint32_t* __restrict__ count) {
+    NRLSH_PDL_ENTRY();
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < nflag; base += 1024) {
+        const int i = base + threadIdx.x;
+        const bool f = i < nflag && flag[i] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t before = carry_s;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        if (f) list[before + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < 32; ++w) t += wsum[w];
+            carry_s += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = carry_s;
+}
+
 // ------------------------------------------------------------------ select
 
 // Block phase (256 threads): ordered compaction of the probed items of one
@@ -909,15 +1025,29 @@ __global__ void __launch_bounds__(256)
                 const float* __restrict__ Q, const float* __restrict__ xnorm,
                 const float* __restrict__ qnorm, const uint32_t* __restrict__ perm,
                 uint32_t* __restrict__ cont, double* __restrict__ cont_s,
-                int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int out_ld) {
+                int64_t* __restrict__ out_ids, float* __restrict__ out_scores, int out_ld,
+                const int* __restrict__ skip, int* __restrict__ report) {
     NRLSH_PDL_ENTRY();
     extern __shared__ __align__(16) float qs[];
     const int64_t q = blockIdx.x;
+    // skip != null: the candidate lists come from a call whose kernels may have
+    // stopped early (a bounded wait ran out); the row is then padded and the
+    // error passed on to *report
+    const int e = skip ? *skip : 0;
+    if (e) {
+        for (int r = threadIdx.x; r < out_ld; r += blockDim.x) {
+            out_ids[q * out_ld + r] = -1;
+            out_scores[q * out_ld + r] = -INFINITY;
+        }
+        if (q == 0 && threadIdx.x == 0) atomicCAS(report, 0, e);
+        return;
+    }
     load_query(Q, q, d, dp, qs);
     __syncthreads();
     const Boundary b = bnd[q];
     __shared__ __align__(16) float rows_s[kRescoreSmem / sizeof(float)];
-    dev_topk(lo + q * cap, hi + q * cap, cand + q * cap, (int64_t)b.full + b.r, ks ? ks[q] : k,
+    dev_topk(lo + q * cap, hi + q * cap, cand + q * cap, (int64_t)b.full + b.r,
+             ks ? min(max(ks[q], 1), k) : k,
              out_ld, Xp, dp, d, qs, qnorm[q], xnorm, perm, cont + q * cap, cont_s + q * cap,
              out_ids + q * out_ld, out_scores + q * out_ld, rows_s);
 }
@@ -1195,9 +1325,16 @@ __global__ void __launch_bounds__(256)
 __global__ void cand_to_ids_kernel(const uint32_t* __restrict__ cand, int64_t cap,
                                    const Boundary* __restrict__ bnd,
                                    const uint32_t* __restrict__ perm, int32_t* out, int64_t out_cap,
-                                   int64_t* count) {
+                                   int64_t* count, const int* __restrict__ skip,
+                                   int* __restrict__ report) {
     NRLSH_PDL_ENTRY();
     const int64_t q = blockIdx.x;
+    const int e = skip ? *skip : 0;     // as in topk_kernel
+    if (e) {
+        if (threadIdx.x == 0) count[q] = 0;
+        if (q == 0 && threadIdx.x == 0) atomicCAS(report, 0, e);
+        return;
+    }
     const Boundary b = bnd[q];
     const int64_t cnt = (int64_t)b.full + b.r;
     if (threadIdx.x == 0) count[q] = cnt;
@@ -1275,6 +1412,28 @@ cudaError_t launch_threshold(const uint32_t* H, const uint32_t* order, int m, in
                   flags, lam, bnd);
 }
 
+cudaError_t launch_tc_walk(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
+                           const int64_t* seg, int64_t nq, int64_t budget, const int64_t* budgets,
+                           int64_t cap, uint32_t flags, const void* codes, const void* qcodes,
+                           int code_bytes, uint8_t* lam, uint32_t* off, TcBoundary* tb,
+                           Boundary* bnd, uint8_t* work_flag, int nqt, const int* err,
+                           cudaStream_t st) {
+    const size_t smem = (sizeof(uint32_t) + 1) * (size_t)m;
+    if (code_bytes == 4)
+        return launch("tc_walk", tc_walk_kernel<uint32_t>, dim3((unsigned)nq), dim3(256), smem, st, H,
+                      order, m, L, n, seg, budget, budgets, cap, flags, (const uint32_t*)codes,
+                      (const uint32_t*)qcodes, lam, off, tb, bnd, work_flag, nqt, err);
+    return launch("tc_walk", tc_walk_kernel<uint64_t>, dim3((unsigned)nq), dim3(256), smem, st, H,
+                  order, m, L, n, seg, budget, budgets, cap, flags, (const uint64_t*)codes,
+                  (const uint64_t*)qcodes, lam, off, tb, bnd, work_flag, nqt, err);
+}
+
+cudaError_t launch_work_list(const uint8_t* flag, int nflag, uint32_t* list, uint32_t* count,
+                             cudaStream_t st) {
+    return launch("work_list", work_list_kernel, dim3(1), dim3(1024), 0, st, flag, nflag, list,
+                  count);
+}
+
 cudaError_t launch_select(const void* codes, const void* qcodes, int code_bytes, const int64_t* seg, int m,
                           int L, int64_t nq, const uint8_t* lam, const Boundary* bnd,
                           uint32_t* cand, int64_t cap, cudaStream_t st) {
@@ -1310,15 +1469,15 @@ cudaError_t launch_topk(const float* lo, const float* hi, const uint32_t* cand, 
                         const void* Xp, nrlsh_dtype dt, int dp, int d, const float* Q,
                         const float* xnorm, const float* qnorm, const uint32_t* perm,
                         uint32_t* cont, double* cont_s, int64_t* out_ids, float* out_scores,
-                        int out_ld, cudaStream_t st) {
+                        int out_ld, cudaStream_t st, const int* skip, int* report) {
     const size_t smem = sizeof(float) * (size_t)dp;
     if (dt == NRLSH_BF16)
         return launch("topk_bf16", topk_kernel<__nv_bfloat16>, dim3((unsigned)nq), dim3(256), smem, st,
                       lo, hi, cand, cap, bnd, k, ks, (const __nv_bfloat16*)Xp, dp, d, Q, xnorm, qnorm,
-                      perm, cont, cont_s, out_ids, out_scores, out_ld);
+                      perm, cont, cont_s, out_ids, out_scores, out_ld, skip, report);
     return launch("topk", topk_kernel<float>, dim3((unsigned)nq), dim3(256), smem, st, lo, hi, cand,
                   cap, bnd, k, ks, (const float*)Xp, dp, d, Q, xnorm, qnorm, perm, cont, cont_s,
-                  out_ids, out_scores, out_ld);
+                  out_ids, out_scores, out_ld, skip, report);
 }
 
 cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m, int L, int64_t n,
@@ -1402,7 +1561,16 @@ cudaError_t launch_multitable(const void* codes, const void* qcodes, int code_by
     const size_t smem = sizeof(float) * (size_t)dp;
     const float kappa = (float)(d + 2) * 0x1p-22f;
     const dim3 grid((unsigned)nq);
-#define NRLSH_MT(T_, C_, NAME)                                                                      {                                                                                                   auto kern = multitable_kernel<T_, C_>;                                                          if (smem > 48 * 1024) {                                                                             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,                                                  (int)smem);                                                if (e != cudaSuccess) return e;                                                             }                                                                                               return launch(NAME, kern, grid, dim3(256), smem, st, (const C_*)codes, (const C_*)qcodes,                       n, (C_)ones, (C_)highs, (const T_*)Xp, dp, d, Q, xnorm, qnorm, kappa, perm,                       k, cand, lo, hi, cont, cont_s, cap, out_ids, out_scores, out_ld, probed,                         cand_ids, cand_ld);                                                           }
+#define NRLSH_MT(T_, C_, NAME)                                                                 \
+    {                                                                                          \
+        auto kern = multitable_kernel<T_, C_>;                                                 \
+        cudaError_t e = ensure_dyn_smem((const void*)kern, smem);                              \
+        if (e != cudaSuccess) return e;                                                        \
+        return launch(NAME, kern, grid, dim3(256), smem, st, (const C_*)codes,                 \
+                      (const C_*)qcodes, n, (C_)ones, (C_)highs, (const T_*)Xp, dp, d, Q,      \
+                      xnorm, qnorm, kappa, perm, k, cand, lo, hi, cont, cont_s, cap, out_ids,  \
+                      out_scores, out_ld, probed, cand_ids, cand_ld);                          \
+    }
     if (dt == NRLSH_BF16) {
         if (code_bytes == 4) NRLSH_MT(__nv_bfloat16, uint32_t, "multitable_bf16")
         NRLSH_MT(__nv_bfloat16, uint64_t, "multitable_bf16")
@@ -1464,9 +1632,9 @@ int probe_rerank_ctas(nrlsh_dtype dt, int code_bytes, int dp, int m, int64_t nq)
 
 cudaError_t launch_cand_to_ids(const uint32_t* cand, int64_t cap, const Boundary* bnd,
                                const uint32_t* perm, int64_t nq, int32_t* out, int64_t out_cap,
-                               int64_t* count, cudaStream_t st) {
+                               int64_t* count, cudaStream_t st, const int* skip, int* report) {
     return launch("cand_to_ids", cand_to_ids_kernel, dim3((unsigned)nq), dim3(256), 0, st, cand,
-                  cap, bnd, perm, out, out_cap, count);
+                  cap, bnd, perm, out, out_cap, count, skip, report);
 }
 
 }  // namespace nrlsh

@@ -23,6 +23,8 @@ NRLSH_BF16 = 1
 NRLSH_WHOLE_BUCKETS = 0x1
 NRLSH_QUERY_GRAPH = 0x2
 NRLSH_QUERY_NO_TUNE = 0x4
+NRLSH_QUERY_TENSOR = 0x8
+NRLSH_QUERY_FP32 = 0x10
 
 _STATUS = {0: "NRLSH_OK", -1: "NRLSH_ERR_ARG", -2: "NRLSH_ERR_OOM", -3: "NRLSH_ERR_CUDA",
            -4: "NRLSH_ERR_TIMEOUT", -5: "NRLSH_ERR_UNSUPPORTED"}
@@ -39,10 +41,10 @@ SIGNATURES = {
     "nrlsh_query_ex": (_I32, [_P, _P, _I64, _I32, _I64, _U32, _P, _P, _P]),
     "nrlsh_query_noalloc": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P]),
     "nrlsh_query_batched": (_I32, [_P, _P, _I64, _P, _P, _I32, _I64, _U32, _P, _P, _P]),
-    "nrlsh_get_tuning": (_I32, [_P, _P, _P]),
-    "nrlsh_batched_scratch_bytes": (_I32, [_P, _I64, _I32, _I64, _P]),
+    "nrlsh_get_tuning": (_I32, [_P, _P, _P, _P]),
+    "nrlsh_batched_scratch_bytes": (_I32, [_P, _I64, _I32, _I64, _U32, _P]),
     "nrlsh_hash_queries": (_I32, [_P, _P, _I64, _P, _P]),
-    "nrlsh_query_histograms": (_I32, [_P, _P, _I64, _P, _P]),
+    "nrlsh_query_histograms": (_I32, [_P, _P, _I64, _P, _U32, _P]),
     "nrlsh_query_candidates": (_I32, [_P, _P, _I64, _I64, _U32, _I64, _P, _P, _P]),
     "nrlsh_query_multitable": (_I32, [_P, _P, _I64, _I32, _I32, _I64, _P, _P, _P, _P]),
     "nrlsh_multitable_candidates": (_I32, [_P, _P, _I64, _I32, _I64, _P, _P, _P]),
@@ -64,7 +66,8 @@ class NrlshInfo(ctypes.Structure):
     _fields_ = [("n", _I64), ("d", _I32), ("m", _I32), ("L", _I32), ("dtype", _I32),
                 ("eps", _F32), ("seed", _U64), ("code_bytes", _I32), ("row_stride", _I32),
                 ("device_bytes", _I64), ("ambiguous_bits", _I64), ("projection", _I32),
-                ("device_error", _I32), ("partition", _I32), ("norm_fallbacks", _I32)]
+                ("device_error", _I32), ("partition", _I32), ("norm_fallbacks", _I32),
+                ("query_error", _I32)]
 
 
 class NrlshBuildOptions(ctypes.Structure):
@@ -200,18 +203,38 @@ def _queries(index: Index, queries: torch.Tensor) -> torch.Tensor:
     return queries.contiguous()
 
 
+def _check_out(t: torch.Tensor, name: str, dtype: torch.dtype, shape: tuple, device):
+    """A caller-supplied output tensor must be exactly what the kernels write: they
+    store rows of shape[1] elements at that stride, so another dtype, a smaller
+    shape or a strided view would be written past its end."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+
+
 def nrlsh_query_ex(index: Index, queries: torch.Tensor, k: int, probe_budget: int,
                    flags: int = 0, stream=None, ids: Optional[torch.Tensor] = None,
                    scores: Optional[torch.Tensor] = None):
     """Multi-probe query + exact re-rank + top-k.  Returns (ids int64, scores fp32),
     both (nq, k), on the queries' device unless output tensors are given."""
-    lib = load()
     queries = _queries(index, queries)
     nq = queries.shape[0]
     if ids is None:
         ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
+    else:
+        _check_out(ids, "ids", torch.int64, (nq, k), queries.device)
     if scores is None:
         scores = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    else:
+        _check_out(scores, "scores", torch.float32, (nq, k), queries.device)
+    lib = load()
     _check(lib.nrlsh_query_ex(index.handle, _ptr(queries), nq, k, probe_budget, flags,
                               _ptr(ids), _ptr(scores), _stream(queries, stream)))
     return ids, scores
@@ -235,9 +258,14 @@ def nrlsh_query_noalloc(index: Index, queries: torch.Tensor, k: int, probe_budge
     allocate while querying).  queries, ids (nq, k) int64 and scores (nq, k) fp32
     must be GPU tensors; the library's fixed 32 MiB scratch array is shared by
     every call, so calls must not overlap on the GPU."""
-    lib = load()
     queries = _queries(index, queries)
-    _check(lib.nrlsh_query_noalloc(index.handle, _ptr(queries), queries.shape[0], k,
+    nq = queries.shape[0]
+    _check_out(ids, "ids", torch.int64, (nq, k), queries.device)
+    _check_out(scores, "scores", torch.float32, (nq, k), queries.device)
+    if not queries.is_cuda:
+        raise ValueError("nrlsh_query_noalloc takes GPU tensors only")
+    lib = load()
+    _check(lib.nrlsh_query_noalloc(index.handle, _ptr(queries), nq, k,
                                    probe_budget, _ptr(ids), _ptr(scores),
                                    _stream(queries, stream)))
     return ids, scores
@@ -250,32 +278,44 @@ def nrlsh_query_batched(index: Index, queries: torch.Tensor, ks: torch.Tensor,
     """Batched queries with per-query k (int32) and budgets (int64): persistent fused
     probe/re-rank kernel, autotuned tiles, optional CUDA-graph replay
     (NRLSH_QUERY_GRAPH).  Returns (ids, scores), rows k_max wide."""
-    lib = load()
     queries = _queries(index, queries)
     nq = queries.shape[0]
+    if ks.numel() != nq or budgets.numel() != nq:
+        raise ValueError(f"ks and budgets must hold {nq} entries")
     ks = ks.to(torch.int32).contiguous()
     budgets = budgets.to(torch.int64).contiguous()
     if ids is None:
         ids = torch.empty((nq, k_max), dtype=torch.int64, device=queries.device)
+    else:
+        _check_out(ids, "ids", torch.int64, (nq, k_max), queries.device)
     if scores is None:
         scores = torch.empty((nq, k_max), dtype=torch.float32, device=queries.device)
+    else:
+        _check_out(scores, "scores", torch.float32, (nq, k_max), queries.device)
+    lib = load()
     _check(lib.nrlsh_query_batched(index.handle, _ptr(queries), nq, _ptr(ks), _ptr(budgets),
                                    k_max, budget_max, flags, _ptr(ids), _ptr(scores),
                                    _stream(queries, stream)))
     return ids, scores
 
 
-def nrlsh_batched_scratch_bytes(index: Index, nq: int, k_max: int, budget_max: int) -> int:
+def nrlsh_batched_scratch_bytes(index: Index, nq: int, k_max: int, budget_max: int,
+                                flags: int = 0) -> int:
+    """Device scratch of one nrlsh_query_batched call with these sizes and flags."""
     out = ctypes.c_int64()
-    _check(load().nrlsh_batched_scratch_bytes(index.handle, nq, k_max, budget_max,
+    _check(load().nrlsh_batched_scratch_bytes(index.handle, nq, k_max, budget_max, flags,
                                               ctypes.byref(out)))
     return out.value
 
 
 def nrlsh_get_tuning(index: Index):
-    qb, cps = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().nrlsh_get_tuning(index.handle, ctypes.byref(qb), ctypes.byref(cps)))
-    return {"hist_queries_per_block": qb.value, "ctas_per_sm": cps.value}
+    """The autotuned batched configuration: popcount histogram tile, persistent
+    CTAs per SM, and whether the histograms / the re-rank run on tensor cores."""
+    qb, cps, tc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().nrlsh_get_tuning(index.handle, ctypes.byref(qb), ctypes.byref(cps),
+                                   ctypes.byref(tc)))
+    return {"hist_queries_per_block": qb.value, "ctas_per_sm": cps.value,
+            "hist_tensor": bool(tc.value & 1), "rerank_tensor": bool(tc.value & 2)}
 
 
 def nrlsh_hash_queries(index: Index, queries: torch.Tensor, stream=None) -> torch.Tensor:
@@ -287,13 +327,16 @@ def nrlsh_hash_queries(index: Index, queries: torch.Tensor, stream=None) -> torc
     return codes
 
 
-def nrlsh_query_histograms(index: Index, queries: torch.Tensor, stream=None) -> torch.Tensor:
+def nrlsh_query_histograms(index: Index, queries: torch.Tensor, flags: int = 0,
+                           stream=None) -> torch.Tensor:
+    """H (nq, m, L+1): items of sub-dataset j sharing exactly l bits with each query
+    (flags NRLSH_QUERY_TENSOR: counted on tensor cores)."""
     lib = load()
     queries = _queries(index, queries)
     H = torch.empty((queries.shape[0], index.m, index.L + 1), dtype=torch.int32,
                     device=queries.device)
     _check(lib.nrlsh_query_histograms(index.handle, _ptr(queries), queries.shape[0], _ptr(H),
-                                      _stream(queries, stream)))
+                                      flags, _stream(queries, stream)))
     return H
 
 
@@ -379,9 +422,14 @@ def nrlsh_get_buckets(index: Index):
     return bj, bl, sh
 
 
-def nrlsh_get_info(index: Index) -> dict:
+def nrlsh_get_info(index: Index, check: bool = True) -> dict:
+    """Sizes and statistics of the index.  The library reports a run-out device
+    wait as NRLSH_ERR_TIMEOUT; with check=False the statistics (device_error,
+    query_error) are returned instead of raising."""
     info = NrlshInfo()
-    _check(load().nrlsh_get_info(index.handle, ctypes.byref(info)))
+    st = load().nrlsh_get_info(index.handle, ctypes.byref(info))
+    if check or st not in (0, -4, -3) or (st == -3 and info.query_error != 15):
+        _check(st)
     return {name: getattr(info, name) for name, _ in NrlshInfo._fields_}
 
 

@@ -5,7 +5,7 @@ order into batches as soon as a slot (a CUDA stream) is free and the batch's
 device scratch fits the memory left in the budget; the scratch size is the
 library's own figure (``nrlsh_batched_scratch_bytes``).  Batches on different
 slots run concurrently on the device.  Each batch goes through
-``nrlsh_query_batched`` (the persistent fused probe/re-rank kernel), with its
+``nrlsh_query_batched`` (the tensor-core path or the persistent FP32 re-rank), with its
 inputs copied from pinned host memory and its results copied back on the slot's
 stream; a request completes when its batch's event has fired.
 
@@ -62,10 +62,17 @@ class Server:
     slots          concurrent batches (one CUDA stream each)
     memory_budget  bytes of device scratch all in-flight batches may use
     max_batch      requests per batch at most
+    path           "auto": the configuration the index's autotuner chose last;
+                   "tensor": the tensor-core path; "fp32": the FP32 CUDA-core path
     """
 
+    _PATH_FLAGS = {"auto": 0, "tensor": N.NRLSH_QUERY_TENSOR, "fp32": N.NRLSH_QUERY_FP32}
+
     def __init__(self, index: "N.Index", slots: int = 3, memory_budget: int = 1 << 30,
-                 max_batch: int = 4096):
+                 max_batch: int = 4096, path: str = "auto"):
+        if path not in self._PATH_FLAGS:
+            raise ValueError(f"path must be one of {sorted(self._PATH_FLAGS)}")
+        self.flags = N.NRLSH_QUERY_NO_TUNE | self._PATH_FLAGS[path]
         self.index = index
         self.d = index.d
         self.device = index.device if index.device.type == "cuda" else torch.device("cuda")
@@ -92,7 +99,7 @@ class Server:
         return req
 
     def _batch_bytes(self, nq: int, k_max: int, budget_max: int) -> int:
-        scratch = N.nrlsh_batched_scratch_bytes(self.index, nq, k_max, budget_max)
+        scratch = N.nrlsh_batched_scratch_bytes(self.index, nq, k_max, budget_max, self.flags)
         io = nq * (self.d * 4 + 4 + 8) + nq * k_max * (8 + 4)     # device inputs and outputs
         return scratch + io
 
@@ -139,8 +146,7 @@ class Server:
             ids_d = torch.empty((nq, k_max), dtype=torch.int64, device=self.device)
             sc_d = torch.empty((nq, k_max), dtype=torch.float32, device=self.device)
             N.nrlsh_query_batched(self.index, q_d, k_d, b_d, k_max, budget_max,
-                                  flags=N.NRLSH_QUERY_NO_TUNE, stream=st, ids=ids_d,
-                                  scores=sc_d)
+                                  flags=self.flags, stream=st, ids=ids_d, scores=sc_d)
             ids_h.copy_(ids_d, non_blocking=True)
             sc_h.copy_(sc_d, non_blocking=True)
             ev = torch.cuda.Event()

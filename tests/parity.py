@@ -81,3 +81,41 @@ def check_queries(lib, ref, Q: np.ndarray, k: int, B: int, flags: int = 0,
     bad = np.flatnonzero((ids != rids).any(axis=1))
     assert bad.size == 0, f"top-k ids differ for queries {bad[:8]}"
     assert np.array_equal(sc, rsc), "top-k scores differ"
+
+
+def check_queries_tc(lib, ref, Q: np.ndarray, k: int, B: int, flags: int = 0,
+                     check_hist: bool = True):
+    """The tensor-core query path against the oracle: histograms element by
+    element, candidate sets (the path groups them by sub-dataset, in no order
+    inside one), then top-k ids and scores bit for bit."""
+    T = N.NRLSH_QUERY_TENSOR
+    Qd = torch.from_numpy(np.ascontiguousarray(Q, dtype=np.float32)).to(DEV)
+    Q64 = Q.astype(np.float32).astype(np.float64)
+    cq = O.query_codes(Q64, ref.A)
+    whole = bool(flags & N.NRLSH_WHOLE_BUCKETS)
+    if check_hist:
+        H = N.nrlsh_query_histograms(lib, Qd, flags=T).cpu().numpy()
+        for i in range(Q.shape[0]):
+            assert np.array_equal(H[i], O.histogram(ref, int(cq[i]))), f"TC histogram {i} differs"
+    cand, count = N.nrlsh_query_candidates(lib, Qd, B, flags=flags | T)
+    cand = cand.cpu().numpy()
+    count = count.cpu().numpy()
+    order = O.storage_order(ref)
+    rank_of = np.empty(ref.n, dtype=np.int64)
+    rank_of[order] = np.arange(ref.n)
+    for i in range(Q.shape[0]):
+        exp = O.candidates(ref, int(cq[i]), B, whole_class=whole)
+        assert count[i] == exp.size, f"query {i}: {count[i]} TC candidates, expected {exp.size}"
+        got = cand[i, :count[i]].astype(np.int64)
+        assert np.array_equal(np.sort(got), np.sort(exp)), f"TC candidates of query {i} differ"
+        subs = ref.sub[got]
+        assert np.all(np.diff(subs) >= 0), f"TC candidates of query {i} not grouped by sub-dataset"
+    ids, sc = N.nrlsh_query_ex(lib, Qd, k, B, flags=flags | T)
+    rids, rsc = O.query(ref, Q64, k, B, whole_class=whole)
+    ids = ids.cpu().numpy()
+    sc = sc.cpu().numpy()
+    bad = np.flatnonzero((ids != rids).any(axis=1))
+    assert bad.size == 0, f"TC top-k ids differ for queries {bad[:8]}"
+    assert np.array_equal(sc, rsc), "TC top-k scores differ"
+    info = N.nrlsh_get_info(lib)
+    assert info["query_error"] == 0, f"tensor-core query kernel error {info['query_error']}"

@@ -126,3 +126,38 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_binding_rejects_output_tensors_the_kernels_would_overrun():
+    """Caller-supplied ids/scores must be (nq, k) int64 / float32, contiguous and on
+    the queries' device: anything else raises ValueError before the library is
+    called (the index handle here is NULL, which the library would reject with
+    NrlshError instead)."""
+    import torch
+    import paper_1809_08782_gb300.nrlsh as N
+    fake = N.Index(None, n=100, d=8, m=2, L=16, device=torch.device("cpu"))
+    Q = torch.zeros((3, 8), dtype=torch.float32)
+    good_ids = torch.empty((3, 5), dtype=torch.int64)
+    good_sc = torch.empty((3, 5), dtype=torch.float32)
+    bad = [
+        (torch.empty((3, 5), dtype=torch.int32), good_sc),        # int32 ids
+        (good_ids, torch.empty((3, 5), dtype=torch.float64)),     # float64 scores
+        (torch.empty((3, 4), dtype=torch.int64), good_sc),        # k' < k
+        (torch.empty((2, 5), dtype=torch.int64), good_sc),        # fewer rows
+        (torch.empty((5, 3), dtype=torch.int64).t(), good_sc),    # strided view
+        (good_ids, torch.empty((3, 5), dtype=torch.float32, device="meta")),  # other device
+    ]
+    for ids, sc in bad:
+        with pytest.raises(ValueError):
+            N.nrlsh_query_ex(fake, Q, 5, 10, ids=ids, scores=sc)
+        with pytest.raises(ValueError):
+            N.nrlsh_query_noalloc(fake, Q, 5, 10, ids, sc)
+    with pytest.raises(ValueError, match="GPU tensors only"):
+        N.nrlsh_query_noalloc(fake, Q, 5, 10, good_ids, good_sc)
+    ks = torch.ones(3, dtype=torch.int32)
+    bs = torch.ones(3, dtype=torch.int64)
+    with pytest.raises(ValueError):
+        N.nrlsh_query_batched(fake, Q, ks, bs, 5, 10, ids=torch.empty((3, 4), dtype=torch.int64))
+    with pytest.raises(ValueError):
+        N.nrlsh_query_batched(fake, Q, ks[:2], bs, 5, 10)
+    fake.handle = None

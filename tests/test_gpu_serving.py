@@ -73,3 +73,25 @@ def test_background_thread_mode(setup):
     r = reqs[42]
     ids, _ = alone(N, idx, r.query, r.k, r.budget)
     assert np.array_equal(r.ids, ids)
+
+
+def test_admission_budget_smaller_than_one_request(setup):
+    """A memory budget below any single request's scratch: the server still makes
+    progress by running each request alone (never two batches at once), and every
+    result equals the request run alone."""
+    from paper_1809_08782_gb300.serving import Request, Server
+    N, idx, Q, ks, budgets = setup
+    reqs = [Request(i, Q[i], int(ks[i]), int(budgets[i])) for i in range(40)]
+    srv = Server(idx, slots=3, memory_budget=1, max_batch=16)
+    done = srv.serve(reqs, np.zeros(len(reqs)))
+    assert srv.max_concurrent == 1 and srv.batches == len(reqs)
+    for r in done[::5]:
+        ids, sc = alone(N, idx, r.query, r.k, r.budget)
+        assert np.array_equal(r.ids, ids) and np.array_equal(r.scores, sc)
+
+
+def test_server_rejects_unknown_path(setup):
+    from paper_1809_08782_gb300.serving import Server
+    _, idx, _, _, _ = setup
+    with pytest.raises(ValueError):
+        Server(idx, path="fp16")

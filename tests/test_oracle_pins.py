@@ -338,6 +338,43 @@ def test_cos_class_values():
     assert O.cos_class(4, 2, 0.5) == pytest.approx(math.sqrt(0.5), abs=0, rel=2.0 ** -52)
 
 
+def _cos_correctly_rounded(L, l, eps):
+    """cos(pi (1 - eps)(L - l) / L) correctly rounded to FP64 (Eq. 12's c_l): mpmath
+    at 200 bits, then the exact binary value of that result rounded once through
+    a Fraction (Python's int division rounds to nearest); 0 exactly at pi/2."""
+    import mpmath
+    from fractions import Fraction
+    fe = Fraction(eps)
+    if 2 * (1 - fe) * (L - l) == L:
+        return 0.0, True
+    with mpmath.workprec(200):
+        v = mpmath.cos(mpmath.pi * (1 - mpmath.mpf(eps)) * (L - l) / L)
+        sign, man, exp, _ = v._mpf_                 # v = (-1)^sign man 2^exp exactly
+        exact = (-1) ** sign * Fraction(int(man)) * Fraction(2) ** int(exp)
+        r = float(exact)
+        # unambiguous: the 200-bit value is far from the midpoint between doubles
+        lo_nb, hi_nb = math.nextafter(r, -math.inf), math.nextafter(r, math.inf)
+        mid = min(abs(exact - (Fraction(r) + Fraction(lo_nb)) / 2),
+                  abs(exact - (Fraction(r) + Fraction(hi_nb)) / 2))
+        ok = mid > abs(exact) * Fraction(2) ** -150 + Fraction(2) ** -1000
+    return r, ok
+
+
+def test_cos_class_is_correctly_rounded():
+    """c_l against an independent 200-bit evaluation rounded once, for the code
+    lengths and eps values the tests and presets use (eps as its float32 value,
+    which is what the C ABI receives), every l."""
+    pytest.importorskip("mpmath")
+    import numpy as _np
+    for L in (1, 2, 8, 16, 17, 24, 32, 48, 63, 64):
+        for e in (1e-9, 0.1, 0.2, 0.3, 0.5, 0.9):
+            eps = float(_np.float32(e))
+            for l in range(L + 1):
+                want, ok = _cos_correctly_rounded(L, l, eps)
+                assert ok
+                assert O.cos_class(L, l, eps) == want, (L, l, eps)
+
+
 def test_negative_region_matches_paper_bound():
     """cos < 0 exactly when l < L [1/2 - eps / (2 (1 - eps))] (Section 3.3)."""
     for L, eps in ((32, 0.1), (64, 0.2), (16, 0.3)):

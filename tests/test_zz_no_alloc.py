@@ -61,8 +61,15 @@ def test_noalloc_rejects_oversized_budget_and_host_pointers(N):
     with pytest.raises(N.NrlshError) as e:
         N.nrlsh_query_noalloc(idx, Q, 5, 1_500_000, ids, sc)
     assert e.value.status == -1 and "32 MiB" in str(e.value)
-    with pytest.raises(N.NrlshError):
-        N.nrlsh_query_noalloc(idx, Q.cpu(), 5, 100, ids, sc)
+    with pytest.raises(ValueError):                  # the binding refuses host queries
+        N.nrlsh_query_noalloc(idx, Q.cpu(), 5, 100, ids.cpu(), sc.cpu())
+    # and so does the C entry point itself, before any work is queued
+    import ctypes
+    Qh = Q.cpu().contiguous()
+    st = N.load().nrlsh_query_noalloc(idx.handle, ctypes.c_void_p(Qh.data_ptr()), 2, 5, 100,
+                                      ctypes.c_void_p(ids.data_ptr()),
+                                      ctypes.c_void_p(sc.data_ptr()), None)
+    assert st == -1 and "device pointers" in N.nrlsh_last_error()
     N.nrlsh_query_noalloc(idx, Q, 5, 1000, ids, sc)    # a budget that fits still works
     ref_ids, _ = N.nrlsh_query_ex(idx, Q, 5, 1000)
     torch.cuda.synchronize()
