@@ -418,7 +418,8 @@ def profile_case(args):
     from paper_1809_08782_gb300 import build as B
     B.build()
     N.load()
-    w = W.make_workload(args.workload, nq=args.queries, with_data=False)
+    kw = {"n": args.n} if args.n else {}
+    w = W.make_workload(args.workload, nq=args.queries, with_data=False, **kw)
     items = W.gen_items(w.n, w.d, w.item_seed, w.norm_dist, w.norm_param, w.dtype)
     X = W.to_torch(items, w.dtype, "cuda")
     Q = torch.from_numpy(W.gen_queries(w.nq, w.d, w.query_seed)).cuda()
@@ -436,7 +437,7 @@ def profile_case(args):
             ix.free()
             ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=proj)
         else:
-            N.nrlsh_query_ex(ix, Q, w.k, budget)
+            N.nrlsh_query_ex(ix, Q, w.k, budget, flags=N.NRLSH_QUERY_TENSOR if args.tensor else 0)
     torch.cuda.synchronize()
     prof = N.nrlsh_profile_read()
     info = N.nrlsh_get_info(ix)
@@ -646,6 +647,9 @@ def main():
                     help="kernel timing run of one phase instead of the bench line")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.PRESETS))
     ap.add_argument("--queries", type=int, default=1000, help="queries (profile runs)")
+    ap.add_argument("--n", type=int, default=None, help="profile runs: items of the preset")
+    ap.add_argument("--tensor", action="store_true",
+                    help="profile runs: queries through the tensor-core path")
     ap.add_argument("--serve", action="store_true", help="serving sweep instead of the bench line")
     ap.add_argument("--curves", action="store_true", help="probed-item/recall curves")
     ap.add_argument("--batched", action="store_true", help="batching-form run (ImageNet-sized)")

@@ -75,14 +75,17 @@ struct PairsArgs {
     uint32_t spin_first;        // polls of the MMA thread's first wait for a stage
 };
 
-// Shared-memory address of the counter of l = (L + v) / 2 for the sign product v
-// (an integer of L's parity in [-L, L]): with f = v + 1.5 2^23 the bits of f are
-// 0x4B400000 + v, so the address is bits * 256 + k (k folds in the row, the
-// counters' base and L).  v is clamped to [-L, L] first (fmaxf also maps a NaN to
-// -L), so no value can address outside the counters.
-__device__ __forceinline__ uint32_t hist_addr(uint32_t vbits, float fL, uint32_t k) {
-    const float v = fminf(fmaxf(__uint_as_float(vbits), -fL), fL);
-    return __float_as_uint(v + 12582912.0f) * 256u + k;
+// The histogram kernel's sign accumulators start at 1.5 2^23 instead of 0 (the
+// epilogue writes that value back into each accumulator it has read), so the
+// accumulated f = 1.5 2^23 + v, v = s_q . s_x an integer of L's parity in [-L, L],
+// is exact and its bits are 0x4B400000 + v.  The counter of l = (L + v) / 2 in the
+// [l][half][row] counters (1,024 bytes per l) is then at bits * 512 + k, k folding
+// in the half, the row, the counters' base and L.  The unsigned min with the last
+// counter keeps any value inside this CTA's shared memory.
+constexpr uint32_t kSignBias = 0x4B400000u;   // 1.5 2^23 as an fp32 bit pattern
+
+__device__ __forceinline__ uint32_t hist_addr(uint32_t fbits, uint32_t k, uint32_t last) {
+    return min(fbits * 512u + k, last);
 }
 
 __device__ __forceinline__ void epi_sync() {
@@ -113,10 +116,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
     volatile int* abort_s = (volatile int*)(tmem_slot + 1);
     uint32_t* extra = (uint32_t*)(tmem_slot + 4);
-    // HIST: counters [l][row]; RERANK: staged xnorm [warp][64] and counts [2][128]
+    // HIST: counters [l][half][row]; RERANK: staged xnorm [warp][64], counts
+    // [2][128] and per-warp 32 x 33 transposition buffers
     uint32_t* hist = extra;
     float* xn_s = (float*)extra;
     uint32_t* cnt_x = extra + kEpiWarps * 64;
+    float* tr_s = (float*)(cnt_x + 2 * kPM);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ int nwork_s;
@@ -140,16 +145,35 @@ __global__ void __launch_bounds__(kPThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (!kRerank && warp >= 2)
-        for (int i = threadIdx.x - 64; i < (a.L + 1) * kPM; i += kEpiThreads) hist[i] = 0;
+        for (int i = threadIdx.x - 64; i < (a.L + 1) * 2 * kPM; i += kEpiThreads) hist[i] = 0;
     if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const int nwork = nwork_s;            // one value for every role
+    if (!kRerank) {
+        // the sign accumulators of both buffers start at the bias (see hist_addr)
+        if (warp >= 2) {
+            const uint32_t la = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) +
+                                128u + 64u * (uint32_t)((warp - 2) >> 2);
+            for (int b = 0; b < 2; ++b) {
+                tmem_fill32(la + 256u * b, kSignBias);
+                tmem_fill32(la + 256u * b + 32u, kSignBias);
+            }
+            tmem_wait_st();
+        }
+        fence_before();
+        __syncthreads();
+        fence_after();
+    }
 
+    // Work items are taken from the end of the (sub-dataset major, ascending) order:
+    // the highest-norm sub-datasets, whose tiles hold the most candidates, go first,
+    // so the static round-robin spreads them over all CTAs.
     auto decode = [&](int i, int& j, int& qt, int64_t& p0, int& ntile) {
-        const uint32_t w = a.list ? a.list[i] : (uint32_t)i;
+        const int ir = nwork - 1 - i;
+        const uint32_t w = a.list ? a.list[ir] : (uint32_t)ir;
         j = (int)(w / (uint32_t)a.nqt);
         qt = (int)(w % (uint32_t)a.nqt);
         p0 = a.seg[j];
@@ -255,9 +279,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
                             for (int k = 0; k < ks; ++k)
                                 umma_bf16(d_score, adesc + 2 * k, bdesc + 2 * k, idesc, (c | k) != 0);
                         } else {
+                            // (histograms: accumulate onto the bias left by the epilogue)
                             const uint64_t adesc = sw128_desc(a_tile + (size_t)(na - 1) * kChunk);
                             for (int k = 0; k < ks_sign; ++k)
-                                umma_bf16(d_sign, adesc + 2 * k, bdesc + 2 * k, idesc, k != 0);
+                                umma_bf16(d_sign, adesc + 2 * k, bdesc + 2 * k, idesc,
+                                          !kRerank || k != 0);
                         }
                         umma_commit(&empty[stage]);
                         if (++stage == S) {
@@ -288,7 +314,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const int row = 32 * quad + lane;       // query row of the tile
         const int et = threadIdx.x - 64;        // epilogue thread index
         const int col_lo = 64 * half;
+        const unsigned lt = (1u << lane) - 1u;
         float* xn_w = xn_s + (warp - 2) * 64;
+        float* tr_w = tr_s + (warp - 2) * 32 * 33;
         const uint32_t lane_addr = (uint32_t)(32 * quad) << 16;
         int buf = 0;
         uint32_t acc_phase = 0;
@@ -300,9 +328,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
             const int64_t q = (int64_t)qt * kPM + row;
             const bool qv = q < a.nq;
             const int64_t p1 = a.seg[j + 1];
-            // per (query, sub-dataset) state of the candidate test
+            // per (query, sub-dataset) state of the candidate test; slots are
+            // relative to the query's list (half 0 fills forward from the front of
+            // the sub-dataset's range, half 1 backward from its end)
             float thrf = 3.0e38f, thrb = 3.0e38f, ce = 0.0f;
-            int64_t pcut = -1, base_j = 0, cnt_j = 0, slot_f = 0, slot_b = -1;
+            int64_t pcut = -1;
+            int32_t base_j = 0, cnt_j = 0, slot = -1;
             if (kRerank && qv) {
                 thrf = (float)(2 * (int)a.lam[q * a.m + j] - a.L);
                 const TcBoundary b = a.tb[q];
@@ -310,25 +341,36 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     thrb = (float)(2 * b.l - a.L);
                     pcut = b.pcut;
                 }
-                base_j = a.off[q * (a.m + 1) + j];
-                cnt_j = (int64_t)a.off[q * (a.m + 1) + j + 1] - base_j;
-                slot_f = base_j;
-                slot_b = base_j + cnt_j - 1;
+                base_j = (int32_t)a.off[q * (a.m + 1) + j];
+                cnt_j = (int32_t)(a.off[q * (a.m + 1) + j + 1] - (uint32_t)base_j);
+                slot = half == 0 ? base_j : base_j + cnt_j - 1;
                 ce = __fmul_ru(a.c_tc, a.qnorm[q]);
             }
-            const uint32_t hist_k = smem_u32(hist) + 4u * (uint32_t)row +
-                                    ((uint32_t)a.L - 0x4B400000u) * 256u;
-            const float fL = (float)a.L;
+            bool overflow = false;
+            const uint32_t hist_k = smem_u32(hist) + 4u * (uint32_t)(half * kPM + row) +
+                                    ((uint32_t)a.L - kSignBias) * 512u;
+            const uint32_t hist_last = smem_u32(hist) + (uint32_t)(a.L + 1) * 2u * kPM * 4u - 4u;
+            // the norms of the first tile's columns; each tile then fetches the next's
+            float xn_next[2] = {0.0f, 0.0f};
+            if (kRerank && ntile > 0) {
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const int c = col_lo + 32 * c2 + lane;
+                    xn_next[c2] = p0 + c < p1 ? a.xnorm[p0 + c] : 0.0f;
+                }
+            }
             for (int t = 0; t < ntile; ++t) {
                 const int64_t pos0 = p0 + (int64_t)t * kPN;
                 const int ncols = (int)min((int64_t)kPN, p1 - pos0);
                 if (kRerank) {
                     __syncwarp();
-                    for (int c2 = lane; c2 < 64; c2 += 32) {
-                        const int c = col_lo + c2;
-                        xn_w[c2] = c < ncols ? a.xnorm[pos0 + c] : 0.0f;
-                    }
+                    xn_w[lane] = xn_next[0];
+                    xn_w[32 + lane] = xn_next[1];
                     __syncwarp();
+                    const int64_t pn = pos0 + kPN;
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        const int c = col_lo + 32 * c2 + lane;
+                        xn_next[c2] = t + 1 < ntile && pn + c < p1 ? a.xnorm[pn + c] : 0.0f;
+                    }
                 }
                 if (!aborted && (*abort_s || !mbar_wait(&acc_full[buf], acc_phase))) {
                     aborted = true;
@@ -338,58 +380,131 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 fence_after();
                 const uint32_t t_score = tmem_base + lane_addr + (uint32_t)buf * 256;
                 const uint32_t t_sign = t_score + 128;
-                for (int g = 0; g < 2 && !aborted; ++g) {
-                    const int col = col_lo + 32 * g;
-                    if (col >= ncols) break;                       // warp-uniform
-                    const int lim = min(32, ncols - col);
-                    uint32_t sg[32];
-                    tmem_ld32_nowait(t_sign + (uint32_t)col, sg);
-                    if (!kRerank) {
+                if (!kRerank) {
+                    // both 32-column groups of this warp's half, then the counters
+                    if (!aborted) {
+                        uint32_t sg0[32], sg1[32];
+                        tmem_ld32_nowait(t_sign + (uint32_t)col_lo, sg0);
+                        tmem_ld32_nowait(t_sign + (uint32_t)(col_lo + 32), sg1);
                         tmem_wait_ld();
+                        // the bias back in for the MMA that reuses this buffer
+                        tmem_fill32(t_sign + (uint32_t)col_lo, kSignBias);
+                        tmem_fill32(t_sign + (uint32_t)(col_lo + 32), kSignBias);
+                        const int lim0 = min(32, ncols - col_lo), lim1 = min(32, ncols - col_lo - 32);
+                        // (every index below is a constant after unrolling, so the
+                        // values stay in registers; the ragged tail is predicated)
                         if (qv) {
-                            if (lim == 32) {
+                            if (lim0 == 32 && lim1 == 32) {
 #pragma unroll
-                                for (int ii = 0; ii < 32; ++ii)
+                                for (int ii = 0; ii < 32; ++ii) {
                                     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(
-                                        hist_addr(sg[ii], fL, hist_k)));
+                                        hist_addr(sg0[ii], hist_k, hist_last)));
+                                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(
+                                        hist_addr(sg1[ii], hist_k, hist_last)));
+                                }
                             } else {
-                                for (int ii = 0; ii < lim; ++ii)
-                                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(
-                                        hist_addr(sg[ii], fL, hist_k)));
+#pragma unroll
+                                for (int ii = 0; ii < 32; ++ii) {
+                                    if (ii < lim0)
+                                        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(
+                                            hist_addr(sg0[ii], hist_k, hist_last)));
+                                    if (ii < lim1)
+                                        asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(
+                                            hist_addr(sg1[ii], hist_k, hist_last)));
+                                }
                             }
                         }
-                    } else {
-                        uint32_t sc[32];
+                        tmem_wait_st();
+                    }
+                } else {
+                    for (int g = 0; g < 2 && !aborted; ++g) {
+                        const int col = col_lo + 32 * g;
+                        if (col >= ncols) break;                   // warp-uniform
+                        const int lim = min(32, ncols - col);
+                        uint32_t sg[32], sc[32];
+                        tmem_ld32_nowait(t_sign + (uint32_t)col, sg);
                         tmem_ld32_nowait(t_score + (uint32_t)col, sc);
                         tmem_wait_ld();
-                        if (qv) {
+                        // this lane's candidates among the group's columns, as a mask:
+                        // the buckets probed whole, then (only in warps where some
+                        // lane's boundary bucket reaches into the group) the cut of
+                        // the boundary bucket
+                        const int64_t pc64 = pcut - (pos0 + col);
+                        const int pc = (int)max((int64_t)-1, min((int64_t)31, pc64));
+                        // (four independent partial masks: no 32-long dependency chain)
+                        uint32_t mp[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                            for (int ii = 0; ii < 32; ++ii) {
-                                if (ii >= lim) break;
-                                const float v = __uint_as_float(sg[ii]);
-                                const int64_t pos = pos0 + col + ii;
-                                if (v >= thrf || (v == thrb && pos <= pcut)) {
-                                    int64_t slot;
-                                    if (half == 0) {
-                                        slot = slot_f < base_j + cnt_j ? slot_f++ : -1;
-                                    } else {
-                                        slot = slot_b >= base_j ? slot_b-- : -1;
-                                    }
-                                    if (slot >= 0) {
-                                        const float s = __uint_as_float(sc[ii]);
-                                        const float e = __fmul_ru(ce, xn_w[col - col_lo + ii]);
-                                        const int64_t gi = q * a.cap + slot;
-                                        a.cand[gi] = (uint32_t)pos;
-                                        a.lo[gi] = __fsub_rd(s, e);
-                                        a.hi[gi] = __fadd_ru(s, e);
-                                    } else {
-                                        thrb = 3.0e38f;   // more hits than counted: reported below
-                                        thrf = 3.0e38f;
-                                        cnt_j = -1;
+                        for (int ii = 0; ii < 32; ++ii)
+                            mp[ii & 3] |= (uint32_t)(__uint_as_float(sg[ii]) >= thrf) << ii;
+                        const bool bact = thrb < 1.0e30f && pc >= 0;
+                        if (__any_sync(0xffffffffu, bact) && bact) {
+#pragma unroll
+                            for (int ii = 0; ii < 32; ++ii)
+                                mp[ii & 3] |= (uint32_t)(__uint_as_float(sg[ii]) == thrb && ii <= pc)
+                                              << ii;
+                        }
+                        uint32_t msk = (mp[0] | mp[1]) | (mp[2] | mp[3]);
+                        if (lim < 32) msk &= (1u << lim) - 1u;
+                        if (!qv) msk = 0;
+                        const int cnt = __popc(msk);
+                        // room in this half's share of the query's range
+                        const bool room = half == 0 ? slot + cnt <= base_j + cnt_j
+                                                    : slot - cnt + 1 >= base_j;
+                        if (!room && cnt) {
+                            overflow = true;
+                            msk = 0;
+                        }
+                        const int tot = __reduce_add_sync(0xffffffffu, room ? cnt : 0);
+                        if (tot == 0) continue;
+                        // the scores through shared memory (row stride 33: no bank
+                        // conflicts either way)
+#pragma unroll
+                        for (int ii = 0; ii < 32; ++ii) tr_w[lane * 33 + ii] = __uint_as_float(sc[ii]);
+                        __syncwarp();
+                        const int64_t row0 = (int64_t)qt * kPM + 32 * quad;
+                        if (tot < 256) {
+                            // sparse: every lane writes its own few candidates
+                            uint32_t mm = msk;
+                            int32_t sl = half == 0 ? slot : slot - cnt + 1;
+                            while (mm) {
+                                const int ii = __ffs(mm) - 1;
+                                mm &= mm - 1;
+                                const int64_t gi = (row0 + lane) * a.cap + sl++;
+                                const float sv = tr_w[lane * 33 + ii];
+                                const float e = __fmul_ru(ce, xn_w[col - col_lo + ii]);
+                                a.cand[gi] = (uint32_t)(pos0 + col + ii);
+                                a.lo[gi] = __fsub_rd(sv, e);
+                                a.hi[gi] = __fadd_ru(sv, e);
+                            }
+                        } else {
+                            // dense: one query's run at a time, written by consecutive
+                            // lanes into consecutive slots, four queries per step
+                            unsigned any = __ballot_sync(0xffffffffu, msk != 0);
+                            const int64_t posl = pos0 + col + lane;
+                            const float xl = xn_w[col - col_lo + lane];
+                            for (int r0 = 0; r0 < 32; r0 += 4) {
+                                if (!((any >> r0) & 0xFu)) continue;
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const int r = r0 + u;
+                                    const uint32_t mr = __shfl_sync(0xffffffffu, msk, r);
+                                    const int32_t sr = __shfl_sync(0xffffffffu, slot, r);
+                                    const float cer = __shfl_sync(0xffffffffu, ce, r);
+                                    const int32_t first = half == 0 ? sr : sr - __popc(mr) + 1;
+                                    if ((mr >> lane) & 1u) {
+                                        const int64_t gi =
+                                            (row0 + r) * a.cap + first + __popc(mr & lt);
+                                        const float sv = tr_w[r * 33 + lane];
+                                        const float e = __fmul_ru(cer, xl);
+                                        a.cand[gi] = (uint32_t)posl;
+                                        a.lo[gi] = __fsub_rd(sv, e);
+                                        a.hi[gi] = __fadd_ru(sv, e);
                                     }
                                 }
                             }
                         }
+                        slot += half == 0 ? cnt : -cnt;
+                        __syncwarp();
                     }
                 }
                 fence_before();
@@ -401,25 +516,28 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             // end of the work item: the same two barriers on every path
             if (kRerank) {
-                const int64_t got = half == 0 ? slot_f - base_j : base_j + cnt_j - 1 - slot_b;
-                cnt_x[half * kPM + row] = qv ? (uint32_t)(cnt_j < 0 ? 0xFFFFFFFFu : got) : 0u;
+                const int32_t got = half == 0 ? slot - base_j : base_j + cnt_j - 1 - slot;
+                cnt_x[half * kPM + row] = qv ? (overflow ? 0xFFFFFFFFu : (uint32_t)got) : 0u;
                 epi_sync();
                 if (half == 0 && qv && !aborted) {
                     const uint32_t other = cnt_x[kPM + row];
-                    if (cnt_j < 0 || other == 0xFFFFFFFFu ||
-                        (int64_t)cnt_x[row] + (int64_t)other != cnt_j)
+                    if (overflow || other == 0xFFFFFFFFu ||
+                        (int64_t)cnt_x[row] + (int64_t)other != (int64_t)cnt_j)
                         atomicCAS(a.err, 0, 15);               // not the counted candidates
                 }
                 epi_sync();
             } else {
                 epi_sync();
+                // the two halves' counters of a query row add up to its histogram
                 for (int idx = et; idx < kPM * (a.L + 1); idx += kEpiThreads) {
                     const int r = idx / (a.L + 1), l = idx - r * (a.L + 1);
                     const int64_t qq = (int64_t)qt * kPM + r;
-                    uint32_t* h = &hist[l * kPM + r];
+                    uint32_t* h0 = &hist[l * 2 * kPM + r];
+                    uint32_t* h1 = h0 + kPM;
                     if (qq < a.nq && !aborted)
-                        a.H[(qq * a.m + j) * (a.L + 1) + l] = *h;
-                    *h = 0;
+                        a.H[(qq * a.m + j) * (a.L + 1) + l] = *h0 + *h1;
+                    *h0 = 0;
+                    *h1 = 0;
                 }
                 epi_sync();
             }
@@ -499,7 +617,8 @@ int grid_for(int64_t work) {
 
 size_t pairs_smem_bytes(bool rerank, int nkc, int L, int stages) {
     const int na = rerank ? nkc + 1 : 1;
-    const size_t extra = rerank ? (size_t)(kEpiWarps * 64 + 2 * kPM) * 4 : (size_t)(L + 1) * kPM * 4;
+    const size_t extra = rerank ? (size_t)(kEpiWarps * 64 + 2 * kPM + kEpiWarps * 32 * 33) * 4
+                                : (size_t)(L + 1) * 2 * kPM * 4;
     return 1024 + (size_t)(na + stages) * kChunk + (2 * (size_t)stages + 7) * 8 + 16 + extra;
 }
 
