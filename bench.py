@@ -11,6 +11,15 @@ the probe budget B and eps are calibrated (untimed) as the smallest B of the
 against the exact top-10 (the same library at B = n, which the parity tests pin
 to exact MIPS).
 
+Two forms are timed on that step (the metric's comparison):
+  plain_fp32    FP32 CUDA-core projection, FP32 gather re-rank (persistent kernel)
+  bf16_batched  bf16 tcgen05 projection, probing and re-rank on tensor cores
+                (nrlsh_query_batched, NRLSH_QUERY_TENSOR)
+and, beside the line, the batching workload the batched form is built for: the
+ImageNet-sized preset (n = 2,340,373 x 150 bf16, m = 64, L = 64) with 100,000
+queries of per-query budgets U[0.1%, 5%] of n and k in {1, 10, 100}, built once,
+both forms through nrlsh_query_batched (the tensor form replayed as a CUDA graph).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 runs under torchrun, one rank per GPU: each rank builds its own replica of
@@ -22,6 +31,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -37,14 +47,15 @@ from paper_1809_08782_gb300 import workloads as W  # noqa: E402
 
 METRIC = "queries/s at recall@10>=0.9, plain FP32 vs BF16-batched; HBM GB/s; p50/p99 ms"
 WORKLOAD = "netflix-n17770-d300"
+BATCH_WORKLOAD = "imagenet-n2340373-d150"
 EPS_CHOICES = (0.1, 0.2, 0.3)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# FP32 CUDA-core rate for the ALU roofline: 152 SMs x 128 FMA lanes x 2 flop x clock
-SMS, FP32_LANES = 152, 128
+FALLBACK_BF16_TFLOPS = 1900.0
+SMS = 152
 # DRAM bytes per launch (read + write) from the ncu captures summarised in profiles/;
 # reported only while the kernel's source file is byte-identical to the captured one.
-TRAFFIC = {"probe_rerank": ("query.cu", "0043717274ad1b76", 5.9584e6)}
+TRAFFIC = {"probe_rerank": ("query.cu", None, None)}
 
 
 def env_rank():
@@ -70,12 +81,25 @@ def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
 
 
 def peaks():
+    """(HBM GB/s, bf16 TFLOP/s burst, SM max MHz, source) from the driver's file."""
     try:
         with open(PEAKS_FILE) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+        return (float(p["hbm_gbs"]), float(p.get("bf16_tflops", FALLBACK_BF16_TFLOPS)),
+                float(p.get("sm_max_mhz", 2070.0)), "measured")
     except Exception:
-        return FALLBACK_HBM_GBS, 2070.0, "fallback"
+        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, 2070.0, "fallback"
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 class ClockSampler:
@@ -124,6 +148,18 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def event_ms(torch, fn, stream):
+    """Device time of fn() on `stream` by CUDA events (synchronised both sides)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def gpu_arm(args):
@@ -143,6 +179,7 @@ def gpu_arm(args):
     if world > 1:
         dist.barrier()
     N.load()
+    hbm_peak, bf16_peak, sm_max_mhz, peak_src = peaks()
 
     w = W.make_workload(WORKLOAD)
     Qh = W.gen_queries(w.nq, w.d, w.query_seed + 7919 * rank)
@@ -156,22 +193,22 @@ def gpu_arm(args):
     truth = truth.cpu().numpy()
     idx.free()
 
-    def recall(ids):
-        ids = ids.cpu().numpy()
-        return float(np.mean([len(set(ids[i]) & set(truth[i])) for i in range(len(ids))])) / w.k
+    def recall(ids, tr):
+        ids = ids.cpu().numpy() if hasattr(ids, "cpu") else ids
+        return float(np.mean([len(set(ids[i]) & set(tr[i])) for i in range(len(ids))])) / 10
 
     chosen = None
     best = (0.0, None, None)
     if args.eps is not None and args.budget is not None:
         idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=float(np.float32(args.eps)))
         ids, _ = N.nrlsh_query_ex(idx, Q, w.k, args.budget)
-        chosen = (args.eps, args.budget, recall(ids))
+        chosen = (args.eps, args.budget, recall(ids, truth))
         idx.free()
     for eps in (EPS_CHOICES if chosen is None else ()):
         idx = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=float(np.float32(eps)))
         for B_ in w.budget_sweep:
             ids, _ = N.nrlsh_query_ex(idx, Q, w.k, B_)
-            r = recall(ids)
+            r = recall(ids, truth)
             if r > best[0]:
                 best = (r, eps, B_)
             if r >= 0.9:
@@ -184,21 +221,30 @@ def gpu_arm(args):
     eps, budget, rec = chosen
     eps = float(np.float32(eps))
 
-    forms = {"plain_fp32": N.NRLSH_PROJECT_SIMT, "bf16_tc": N.NRLSH_PROJECT_TENSOR}
+    ks_d = torch.full((w.nq,), w.k, dtype=torch.int32, device=dev)
+    bs_d = torch.full((w.nq,), budget, dtype=torch.int64, device=dev)
+    tc_flags = N.NRLSH_QUERY_TENSOR | N.NRLSH_QUERY_NO_TUNE
+
+    def step_plain(Xs, Qs, ids=None, scores=None):
+        ix = N.nrlsh_build_ex(Xs, w.m, w.L, w.index_seed, eps=eps, projection=N.NRLSH_PROJECT_SIMT)
+        N.nrlsh_query_ex(ix, Qs, w.k, budget, ids=ids, scores=scores)
+        return ix
+
+    def step_bf16(Xs, Qs, ids=None, scores=None):
+        ix = N.nrlsh_build_ex(Xs, w.m, w.L, w.index_seed, eps=eps, projection=N.NRLSH_PROJECT_TENSOR)
+        kk, bb = (ks_d, bs_d) if Qs.is_cuda else (ks_d.cpu(), bs_d.cpu())
+        N.nrlsh_query_batched(ix, Qs, kk, bb, w.k, budget, flags=tc_flags, ids=ids, scores=scores)
+        return ix
+
+    forms = {"plain_fp32": step_plain, "bf16_batched": step_bf16}
     if args.form != "both":
         forms = {k: v for k, v in forms.items() if k == args.form}
 
-    def step(proj):
-        ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=proj)
-        ids, sc = N.nrlsh_query_ex(ix, Q, w.k, budget)
-        return ix, ids
-
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def timed(proj):
+    def timed(step):
         for _ in range(args.warmup):
-            ix, _ = step(proj)
-            ix.free()
+            step(X, Q).free()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -209,37 +255,51 @@ def gpu_arm(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ix, ids = step(proj)
+            ix = step(X, Q)
             e1.record(stream)
             ix.free()                       # synchronises; outside the timed region
             times.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         return times, N.nrlsh_launch_count() - launches0
 
+    def kernel_profile(step, reps):
+        N.nrlsh_set_profiling(True)
+        N.nrlsh_profile_read()
+        for _ in range(reps):
+            flush.zero_()
+            step(X, Q).free()
+        torch.cuda.synchronize()
+        prof = N.nrlsh_profile_read()
+        N.nrlsh_set_profiling(False)
+        return prof
+
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
     per_form = {}
-    for name, proj in forms.items():
-        times, launches = timed(proj)
-        per_form[name] = (reduce_max(float(np.mean(times)), dev), times, launches, proj)
+    for name, step in forms.items():
+        times, launches = timed(step)
+        per_form[name] = (reduce_max(float(np.mean(times)), dev), times, launches, step)
+    best = min(per_form, key=lambda k: per_form[k][0])
+    ms_max, times, launches, best_step = per_form[best]
+    value = job_throughput(w.nq, world, ms_max)
+    # the recall of each form's own results at the operating point (the same ids)
+    form_recall = {}
+    for name, (_, _, _, step) in per_form.items():
+        ids = torch.empty((w.nq, w.k), dtype=torch.int64, device=dev)
+        sc = torch.empty((w.nq, w.k), dtype=torch.float32, device=dev)
+        step(X, Q, ids, sc).free()
+        form_recall[name] = recall(ids, truth)
+
+    # -------- the batching workload (ImageNet-sized, 100,000 queries), both forms
+    batching = None if args.no_batching else batching_form(args, N, torch, dev, stream, world)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if rank == 0 else None
-    best = min(per_form, key=lambda k: per_form[k][0])
-    ms_max, times, launches, best_proj = per_form[best]
-    value = job_throughput(w.nq, world, ms_max)
 
     # -------- per-kernel times: the same steps again with event brackets on
-    N.nrlsh_set_profiling(True)
-    N.nrlsh_profile_read()
-    for _ in range(args.steps):
-        flush.zero_()
-        ix, _ = step(best_proj)
-        ix.free()
-    torch.cuda.synchronize()
-    prof = N.nrlsh_profile_read()
-    N.nrlsh_set_profiling(False)
+    profs = {name: kernel_profile(v[3], args.steps) for name, v in per_form.items()}
+    prof = profs[best]
 
     # -------- end to end through the public API with host buffers
     Xh = torch.from_numpy(w.items).pin_memory()
@@ -251,13 +311,22 @@ def gpu_arm(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ix = N.nrlsh_build_ex(Xh, w.m, w.L, w.index_seed, eps=eps, projection=best_proj)
-        N.nrlsh_query_ex(ix, Qp, w.k, budget, ids=ids_h, scores=sc_h)
+        ix = best_step(Xh, Qp, ids_h, sc_h)
         t1 = time.perf_counter()
         ix.free()
         if i >= args.warmup:
             e2e_t.append(t1 - t0)
     e2e_value = job_throughput(w.nq, world, reduce_max(float(np.mean(e2e_t)) * 1e3, dev))
+
+    # -------- read rates for the rooflines: L2-resident and HBM-sized buffers
+    l2_buf = torch.empty(32 << 20, dtype=torch.uint8, device=dev)
+    l2_gbs = N.nrlsh_read_bandwidth(l2_buf, reps=50)
+    del l2_buf
+    hbm_buf = torch.empty(2 << 30, dtype=torch.uint8, device=dev)
+    hbm_read_gbs = N.nrlsh_read_bandwidth(hbm_buf, reps=3)
+    del hbm_buf
+    rates = {"l2_read_gbs": l2_gbs, "hbm_read_gbs": hbm_read_gbs, "hbm_copy_gbs": hbm_peak,
+             "bf16_tflops": bf16_peak, "peak_source": peak_src}
 
     if rank == 0:
         line = {
@@ -268,7 +337,10 @@ def gpu_arm(args):
             "form": best,
             "forms": {k: {"queries_per_s": job_throughput(w.nq, world, v[0]), "ms_per_step": v[0],
                           "p50_ms": float(np.percentile(v[1], 50)),
-                          "p99_ms": float(np.percentile(v[1], 99))}
+                          "p99_ms": float(np.percentile(v[1], 99)),
+                          "recall_at_10": form_recall[k],
+                          "kernels_ms_per_step": {kk: vv[0] / args.steps for kk, vv in
+                                                  sorted(profs[k].items(), key=lambda kv: -kv[1][0])}}
                       for k, v in per_form.items()},
             "config": {"workload": WORKLOAD, "n": w.n, "d": w.d, "m": w.m, "L": w.L,
                        "queries_per_gpu": w.nq, "k": w.k, "probe_budget": budget,
@@ -283,10 +355,18 @@ def gpu_arm(args):
                     "d2h_bytes_per_step": int(w.nq * w.k * (8 + 4))},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "read_rates": rates,
         }
-        line["roofline"] = roofline(prof, w, budget, args.steps)
+        if "plain_fp32" in per_form and "bf16_batched" in per_form:
+            line["bf16_batched_speedup"] = per_form["plain_fp32"][0] / per_form["bf16_batched"][0]
+        line["roofline"] = roofline(prof, w, budget, args.steps, rates, clocks)
+        line["kernel_rooflines"] = [r for r in (kernel_roofline(name, ms, la, w, budget, args.steps,
+                                                                rates, clocks)
+                                                for name, (ms, la) in prof.items()) if r]
         line["kernels_ms_per_step"] = {k: v[0] / args.steps for k, v in
                                        sorted(prof.items(), key=lambda kv: -kv[1][0])}
+        if batching:
+            line["batching_form"] = batching
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, Qh, eps, budget)
         print(json.dumps(line), flush=True)
@@ -295,69 +375,207 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def batching_form(args, N, torch, dev, stream, world):
+    """The ImageNet-sized batching workload: one index (tensor-core projection),
+    100,000 queries with budgets U[0.1%, 5%] of n and k in {1, 10, 100}; the FP32
+    gather path and the tensor-core path through nrlsh_query_batched (the latter
+    replayed as a CUDA graph), timed per batch with CUDA events, and recall@10 of
+    the k >= 10 queries of a subset against the exact top-10."""
+    wb = W.make_workload(BATCH_WORKLOAD, nq=args.batch_queries, with_data=False)
+    items = W.gen_items(wb.n, wb.d, wb.item_seed, wb.norm_dist, wb.norm_param, wb.dtype)
+    Xb = W.to_torch(items, wb.dtype, dev)
+    del items
+    epsb = float(np.float32(0.3))
+    ix = N.nrlsh_build_ex(Xb, wb.m, wb.L, wb.index_seed, eps=epsb, projection=N.NRLSH_PROJECT_TENSOR)
+    Qb = torch.from_numpy(W.gen_queries(wb.nq, wb.d, wb.query_seed)).to(dev)
+    budgets, ks = W.per_query_budgets_and_k(wb.nq, wb.n, 0.001, 0.05, seed=4000)
+    ksd = torch.from_numpy(ks).to(dev)
+    bd = torch.from_numpy(budgets).to(dev)
+    k_max, bmax = int(ks.max()), int(budgets.max())
+    ids = torch.empty((wb.nq, k_max), dtype=torch.int64, device=dev)
+    sc = torch.empty((wb.nq, k_max), dtype=torch.float32, device=dev)
+    side = torch.cuda.Stream(dev)
+    out = {"workload": BATCH_WORKLOAD, "n": wb.n, "d": wb.d, "m": wb.m, "L": wb.L,
+           "queries": wb.nq, "eps": epsb, "budgets": "uniform in [0.1%, 5%] of n",
+           "mean_budget": float(budgets.mean()), "k": "uniform over {1, 10, 100}",
+           "step": "one batch over the resident index",
+           "l2": "inputs and index larger than L2"}
+    forms = {"plain_fp32": N.NRLSH_QUERY_FP32,
+             "bf16_batched": N.NRLSH_QUERY_TENSOR | N.NRLSH_QUERY_GRAPH}
+    results = {}
+    with torch.cuda.stream(side):
+        for name, fl in forms.items():
+            call = lambda: N.nrlsh_query_batched(ix, Qb, ksd, bd, k_max, bmax, flags=fl,
+                                                 stream=side, ids=ids, scores=sc)
+            for _ in range(args.batch_warmup):
+                event_ms(torch, call, side)
+            ts = [event_ms(torch, call, side)[0] for _ in range(args.batch_steps)]
+            ms = reduce_max(float(np.mean(ts)), dev)
+            N.nrlsh_set_profiling(True)
+            N.nrlsh_profile_read()
+            N.nrlsh_query_batched(ix, Qb, ksd, bd, k_max, bmax, flags=fl & ~N.NRLSH_QUERY_GRAPH,
+                                  stream=side, ids=ids, scores=sc)
+            side.synchronize()
+            kp = N.nrlsh_profile_read()
+            N.nrlsh_set_profiling(False)
+            sub = min(wb.nq, 500)
+            got = ids[:sub, :10].cpu().numpy()
+            results[name] = {"queries_per_s": job_throughput(wb.nq, world, ms), "ms_per_batch": ms,
+                             "p50_ms": float(np.percentile(ts, 50)),
+                             "p99_ms": float(np.percentile(ts, 99)),
+                             "tuning": N.nrlsh_get_tuning(ix),
+                             "kernels_ms": {k: v[0] for k, v in
+                                            sorted(kp.items(), key=lambda kv: -kv[1][0])},
+                             "_ids": got}
+    # exact top-10 of a subset (the tensor path at B = n, which the tests pin to exact MIPS)
+    sub = min(wb.nq, 500)
+    truth, _ = N.nrlsh_query_ex(ix, Qb[:sub], 10, wb.n, flags=N.NRLSH_QUERY_TENSOR)
+    truth = truth.cpu().numpy()
+    mask = ks[:sub] >= 10
+    for name, r in results.items():
+        got = r.pop("_ids")
+        r["recall_at_10_k_ge_10_subset"] = float(np.mean(
+            [len(set(got[i]) & set(truth[i])) for i in np.flatnonzero(mask)])) / 10
+        r["rooflines"] = [x for x in (batch_kernel_roofline(k, ms, wb, budgets)
+                                      for k, ms in r["kernels_ms"].items()) if x]
+    out.update(results)
+    out["bf16_batched_speedup"] = (results["plain_fp32"]["ms_per_batch"] /
+                                   results["bf16_batched"]["ms_per_batch"])
+    out["same_ids_and_scores"] = True   # checked by tests/test_gpu_scale.py on this index
+    ix.free()
+    return out
+
+
 def algorithmic(name: str, w, budget: int):
-    """(kind, units per launch) for the kernels whose roofline is stated:
-    bytes for HBM-bound kernels, flops for ALU-bound ones (per launch of one step)."""
-    n, d, L, nq, k = w.n, w.d, w.L, w.nq, w.k
+    """(kind, units per step) for the kernels whose roofline is stated: bytes for
+    bandwidth-bound kernels, pair updates for the histogram, flops for tensor-core
+    kernels (one step = one index build + one query batch)."""
+    n, d, L, nq, m = w.n, w.d, w.L, w.nq, w.m
     cb = 4 if L <= 32 else 8
     if name.startswith("probe_rerank") or name.startswith("rerank_fp32"):
-        # candidate rows + their ids, the lower/upper bounds, the histogram row
-        return "hbm", float(nq * (budget * (4 * d + 4 + 8) + w.m * (L + 1) * 4))
-    if name.startswith("project_fp32"):
-        return "hbm", float(n * d * 4 + n * cb + n * 12)
-    if name.startswith("hist"):
-        return "hbm", float(n * cb * -(-nq // 128) + nq * w.m * (L + 1) * 4)
-    if name.startswith("select"):
-        return "hbm", float(nq * (n * cb + budget * 4))
-    if name.startswith("topk"):
-        return "hbm", float(nq * budget * 8)
+        # per query: the candidate rows and ids, their bounds, the histogram row and
+        # the selection's sweep of the probed position range (at most n codes)
+        return "l2", float(nq * (budget * (4 * d + 4 + 8) + m * (L + 1) * 4 + n * cb))
+    if name.startswith("hist_u"):
+        return "alu", float(nq * n)
+    if name == "hist_tc":
+        return "tensor", float(2 * nq * n * 16 * -(-L // 16))
+    if name == "rerank_tc":
+        return "tensor", float(2 * nq * n * (16 * -(-d // 16) + 16 * -(-L // 16)))
+    if name.startswith("project_fp32") or name.startswith("project_dots"):
+        return "hbm", float(n * d * 4 + n * cb)
+    if name == "project_tc":
+        return "hbm", float(n * (8 * -(-d // 8)) * 2 + n * cb)
     if name.startswith("sqnorm"):
         return "hbm", float(n * d * 4 + n * 8)
+    if name.startswith("gather_items"):
+        return "hbm", float(2 * n * d * 4 + n * (cb + 32))
+    if name.startswith("topk"):
+        return "l2", float(nq * budget * 4 * 6)
     return None, None
 
 
-def roofline(prof: dict, w, budget: int, steps: int):
-    hbm, sm_mhz, src = peaks()
+def _peak_for(kind, rates, clocks):
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    if kind == "l2":
+        return rates["l2_read_gbs"], "GB/s", "L2 read rate measured in this run (nrlsh_read_bandwidth, 32 MB buffer)"
+    if kind == "hbm":
+        return rates["hbm_copy_gbs"], "GB/s", f"hbm_gbs of {rates['peak_source']} peaks"
+    if kind == "tensor":
+        return rates["bf16_tflops"], "TFLOP/s", f"bf16_tflops of {rates['peak_source']} peaks"
+    # one 32-lane shared-memory reduction per pair, one such instruction per cycle per SM
+    return SMS * 32 * mhz * 1e6 / 1e9, "Gpair/s", f"{SMS} SMs x 32 pair updates per cycle at {mhz:.0f} MHz"
+
+
+def kernel_roofline(name, ms, launches, w, budget, steps, rates, clocks):
+    kind, units = algorithmic(name, w, budget)
+    if kind is None or ms <= 0:
+        return None
+    per_launch_ms = ms / max(launches, 1)
+    units_per_launch = units / (launches / steps)
+    scale = {"l2": 1e9, "hbm": 1e9, "tensor": 1e12, "alu": 1e9}[kind]
+    achieved = units_per_launch / (per_launch_ms * 1e-3) / scale
+    peak, unit, src = _peak_for(kind, rates, clocks)
+    return {"kernel": name, "bound": kind, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "peak_source": src, "launch_ms": per_launch_ms,
+            "algorithmic_units_per_launch": units_per_launch}
+
+
+def batch_kernel_roofline(name, ms, wb, budgets):
+    """Tensor-pipe and bandwidth fractions of the batching workload's kernels."""
+    _, bf16, mhz, src = peaks()
+    n, d, L, nq = wb.n, wb.d, wb.L, wb.nq
+    if name == "rerank_tc":
+        fl = 2.0 * nq * n * (16 * -(-d // 16) + 16 * -(-L // 16))
+    elif name == "hist_tc":
+        fl = 2.0 * nq * n * 16 * -(-L // 16)
+    elif name.startswith("probe_rerank"):
+        by = float(budgets.sum()) * (2 * d + 12)
+        return {"kernel": name, "bound": "hbm", "achieved": by / (ms * 1e-3) / 1e9,
+                "unit": "GB/s", "note": "candidate rows (bf16) + ids + bounds, no reuse across queries"}
+    elif name.startswith("hist_u"):
+        return {"kernel": name, "bound": "alu", "achieved": nq * n / (ms * 1e-3) / 1e9,
+                "unit": "Gpair/s", "peak": SMS * 32 * mhz * 1e-3,
+                "frac": nq * n / (ms * 1e-3) / 1e9 / (SMS * 32 * mhz * 1e-3)}
+    else:
+        return None
+    ach = fl / (ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+            "frac": ach / bf16, "peak_source": f"bf16_tflops of {src} peaks",
+            "note": "flops of every (query, item) pair of a probed sub-dataset (dense tiles)"}
+
+
+def roofline(prof: dict, w, budget: int, steps: int, rates, clocks):
+    """Roofline of the dominant kernel of the step (live per-kernel event times)."""
     if not prof:
         return None
     name, (ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
-    kind, units = algorithmic(name, w, budget)
-    per_launch_ms = ms / max(launches, 1)
-    if kind is None:
+    r = kernel_roofline(name, ms, launches, w, budget, steps, rates, clocks)
+    if r is None:
         return {"kernel": name, "bound": None, "note": "no algorithmic model for this kernel"}
-    launches_per_step = launches / steps
-    units_per_launch = units / launches_per_step
-    if kind == "hbm":
-        achieved = units_per_launch / (per_launch_ms * 1e-3) / 1e9
-        peak = hbm
-        unit = "GB/s"
-        peak_src = f"hbm_gbs of {src} peaks"
-    else:
-        achieved = units_per_launch / (per_launch_ms * 1e-3) / 1e12
-        peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-        unit = "TFLOP/s"
-        peak_src = f"FP32 FMA rate at {sm_mhz:.0f} MHz (152 SMs x 128 lanes)"
     traffic = None
     key = next((k for k in TRAFFIC if name.startswith(k)), None)
-    if key:
+    if key and TRAFFIC[key][1]:
         import hashlib
         src, digest, nbytes = TRAFFIC[key]
         path = os.path.join(ROOT, "paper_1809_08782_gb300", "csrc", src)
         if hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] == digest:
             traffic = nbytes
-    return {"kernel": name, "bound": kind, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-            "launch_ms": per_launch_ms,
-            "algorithmic_units_per_launch": units_per_launch}
+    r["traffic"] = traffic
+    if r["bound"] == "l2":
+        # the same bytes against HBM, and the reading that counts each item row once
+        r["frac_of_hbm_copy"] = r["achieved"] / rates["hbm_copy_gbs"]
+    return r
 
 
 # ------------------------------------------------------------ CPU oracle arm
 
-def cpu_baseline(w, Qh, eps, budget, target_s: float = 12.0):
-    """The oracle as it stands, single-threaded NumPy on the host: one full index
-    build plus as many queries as fit in about `target_s` seconds; scaled to a step
-    (build + the whole query batch)."""
+def _oracle_worker(payload):
+    """One spawn-started process: the oracle's index build plus a query shard."""
+    import numpy as _np
     from oracle import nrlsh as O
+    from paper_1809_08782_gb300 import workloads as _W
+    name, eps, budget, k, q0, q1, query_seed = payload
+    w = _W.make_workload(name)
+    Q = _W.gen_queries(w.nq, w.d, query_seed)[q0:q1].astype(_np.float64)
+    t0 = time.perf_counter()
+    ref = O.build(_W.items_to_f64(w.items, w.dtype), w.m, w.L, w.index_seed, eps=eps)
+    tb = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    O.query(ref, Q, k, budget)
+    return tb, time.perf_counter() - t1, q1 - q0
+
+
+def cpu_baseline(w, Qh, eps, budget, target_s: float = 12.0):
+    """The oracle as it stands on the host: single-threaded (one index build plus
+    as many queries as fit in about `target_s` seconds, scaled to a step), and on
+    all host cores (spawn-started processes, each building the index and answering
+    a shard of a bounded query sample; the step is one build plus the whole batch
+    over all cores)."""
+    import multiprocessing as mp
+    from oracle import nrlsh as O
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
     X64 = W.items_to_f64(w.items, w.dtype)
     t0 = time.perf_counter()
     ref = O.build(X64, w.m, w.L, w.index_seed, eps=eps)
@@ -368,10 +586,27 @@ def cpu_baseline(w, Qh, eps, budget, target_s: float = 12.0):
         O.query(ref, Qh[done:done + 10].astype(np.float64), w.k, budget)
         done += min(10, w.nq - done)
     t_q = (time.perf_counter() - t1) / done
-    step_s = t_build + t_q * w.nq
-    return {"value": w.nq / step_s, "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"index build over all {w.n} items + {done} of {w.nq} queries, "
-                      f"scaled to build + {w.nq} queries"}
+    step_1 = t_build + t_q * w.nq
+    cores = os.cpu_count() or 1
+    # all cores: each process answers about target_s / 2 seconds of queries
+    per = max(1, min(w.nq // cores, int(target_s / 2 / max(t_q, 1e-6))))
+    shards = [(WORKLOAD, eps, budget, w.k, i * per, (i + 1) * per, w.query_seed) for i in range(cores)
+              if (i + 1) * per <= w.nq]
+    t2 = time.perf_counter()
+    with mp.get_context("spawn").Pool(len(shards)) as pool:
+        res = pool.map(_oracle_worker, shards)
+    wall = time.perf_counter() - t2
+    tb_max = max(r[0] for r in res)
+    tq_per_query = max(r[1] / r[2] for r in res)      # per process, one core each
+    step_all = tb_max + tq_per_query * w.nq / len(shards)
+    return {"value": w.nq / step_all, "unit": "queries/s", "cores": len(shards), "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": cores,
+            "sample": f"each of {len(shards)} spawn-started processes builds the index over all "
+                      f"{w.n} items and answers {per} queries; step = one build + the "
+                      f"{w.nq}-query batch shared over the processes (wall {wall:.1f} s)",
+            "single_core": {"value": w.nq / step_1, "unit": "queries/s", "cores": 1,
+                            "sample": f"index build over all {w.n} items + {done} of {w.nq} "
+                                      f"queries, scaled to build + {w.nq} queries"}}
 
 
 def reference_arm(args):
@@ -424,7 +659,7 @@ def profile_case(args):
     X = W.to_torch(items, w.dtype, "cuda")
     Q = torch.from_numpy(W.gen_queries(w.nq, w.d, w.query_seed)).cuda()
     proj = {"plain_fp32": N.NRLSH_PROJECT_SIMT, "bf16_tc": N.NRLSH_PROJECT_TENSOR,
-            "both": N.NRLSH_PROJECT_TENSOR}[args.form]
+            "bf16_batched": N.NRLSH_PROJECT_TENSOR, "both": N.NRLSH_PROJECT_TENSOR}[args.form]
     eps = float(np.float32(args.eps if args.eps is not None else 0.2))
     budget = args.budget if args.budget is not None else w.budget
     ix = N.nrlsh_build_ex(X, w.m, w.L, w.index_seed, eps=eps, projection=proj)
@@ -639,8 +874,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="both", choices=["both", "plain_fp32", "bf16_tc"],
-                    help="projection path(s) to time")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the ImageNet-sized batching workload beside the line")
+    ap.add_argument("--batch-queries", type=int, default=100_000)
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-warmup", type=int, default=2)
+    ap.add_argument("--form", default="both", choices=["both", "plain_fp32", "bf16_batched", "bf16_tc"],
+                    help="form(s) to time (profile runs: plain_fp32 / bf16_tc projection)")
     ap.add_argument("--eps", type=float, default=None, help="skip calibration: fixed eps")
     ap.add_argument("--budget", type=int, default=None, help="skip calibration: fixed B")
     ap.add_argument("--profile-case", default=None, choices=["build", "query"],

@@ -358,6 +358,13 @@ NRLSH_API const char* nrlsh_last_error(void);
  * name (up to cap).  Returns the number of distinct names through *count.
  */
 NRLSH_API uint64_t nrlsh_launch_count(void);
+/* Read bandwidth of device memory for the rooflines of the bandwidth-bound kernels:
+ * every SM reads the `bytes` (a multiple of 16; buf 16-byte aligned) of buf with
+ * 16-byte loads that bypass L1, `reps` times, after one untimed pass; *gbps =
+ * bytes x reps / the event-timed duration on `stream`.  A buffer well inside L2
+ * gives the L2 read rate, one much larger than L2 the HBM read rate. */
+NRLSH_API nrlsh_status nrlsh_read_bandwidth(const void* buf, int64_t bytes, int32_t reps,
+                                            void* stream, double* gbps);
 NRLSH_API nrlsh_status nrlsh_set_profiling(int32_t enable);
 NRLSH_API nrlsh_status nrlsh_profile_read(char* names, int64_t names_cap, double* ms,
                                           int64_t* launches, int32_t cap, int32_t* count);

@@ -1443,6 +1443,74 @@ NRLSH_API const char* nrlsh_last_error(void) { return g_last_error.c_str(); }
 
 NRLSH_API uint64_t nrlsh_launch_count(void) { return g_launches.load(); }
 
+}  // extern "C"
+
+namespace {
+
+// Every thread reads 16-byte words of the buffer, grid-strided, `reps` times, from
+// L2 (ld.global.cg); the folded words are written only if they match an
+// impossible value, which keeps the loads.
+__global__ void __launch_bounds__(256) read_probe_kernel(const uint4* __restrict__ buf, int64_t words,
+                                                         int reps, uint32_t* __restrict__ sink) {
+    NRLSH_PDL_ENTRY();
+    uint32_t acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += 4 * stride) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = i + u * stride;
+                v[u] = k < words ? __ldcg(buf + k) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+        }
+        acc = acc * 2654435761u + (uint32_t)r;
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;
+}
+
+}  // namespace
+
+extern "C" {
+
+NRLSH_API nrlsh_status nrlsh_read_bandwidth(const void* buf, int64_t bytes, int32_t reps,
+                                            void* stream, double* gbps) {
+    if (!buf || !gbps) return arg_error("NULL argument");
+    if (bytes < 16 || bytes % 16 != 0) return arg_error("need bytes >= 16, a multiple of 16");
+    if (((uintptr_t)buf & 15) != 0) return arg_error("buf must be 16-byte aligned");
+    if (reps < 1) return arg_error("need reps >= 1");
+    if (!is_device_ptr(buf)) return arg_error("buf must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    NRLSH_CK(cudaGetLastError());
+    int dev = 0, sms = 0;
+    NRLSH_CK(cudaGetDevice(&dev));
+    NRLSH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    Scratch sc(st);
+    uint32_t* sink;
+    NRLSH_CKS(sc.get(&sink, 1));
+    const dim3 grid((unsigned)(sms * 8));
+    // one untimed pass brings an L2-sized buffer into L2
+    NRLSH_CK(launch("read_probe", read_probe_kernel, grid, dim3(256), 0, st, (const uint4*)buf,
+                    bytes / 16, 1, sink));
+    cudaEvent_t e0, e1;
+    NRLSH_CK(cudaEventCreate(&e0));
+    NRLSH_CK(cudaEventCreate(&e1));
+    NRLSH_CK(cudaEventRecord(e0, st));
+    const cudaError_t le = launch("read_probe", read_probe_kernel, grid, dim3(256), 0, st,
+                                  (const uint4*)buf, bytes / 16, (int)reps, sink);
+    NRLSH_CK(cudaEventRecord(e1, st));
+    NRLSH_CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    NRLSH_CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    NRLSH_CK(le);
+    *gbps = (double)bytes * reps / (ms * 1e-3) / 1e9;
+    return NRLSH_OK;
+}
+
 NRLSH_API nrlsh_status nrlsh_set_profiling(int32_t enable) {
     g_prof_on.store(enable != 0);
     return NRLSH_OK;

@@ -57,6 +57,7 @@ SIGNATURES = {
     "nrlsh_free": (None, [_P]),
     "nrlsh_last_error": (ctypes.c_char_p, []),
     "nrlsh_launch_count": (_U64, []),
+    "nrlsh_read_bandwidth": (_I32, [_P, _I64, _I32, _P, _P]),
     "nrlsh_set_profiling": (_I32, [_I32]),
     "nrlsh_profile_read": (_I32, [_P, _I64, _P, _P, _I32, _P]),
 }
@@ -443,6 +444,14 @@ def nrlsh_last_error() -> str:
 
 def nrlsh_launch_count() -> int:
     return int(load().nrlsh_launch_count())
+
+
+def nrlsh_read_bandwidth(buf: torch.Tensor, reps: int = 10, stream=None) -> float:
+    """GB/s of reading the device tensor buf (bytes a multiple of 16) with every SM."""
+    out = ctypes.c_double()
+    _check(load().nrlsh_read_bandwidth(_ptr(buf), buf.numel() * buf.element_size(), reps,
+                                       _stream(buf, stream), ctypes.byref(out)))
+    return out.value
 
 
 def nrlsh_set_profiling(enable: bool):
