@@ -954,12 +954,12 @@ nrlsh_status run_tc_chunk(const nrlsh_index* ix, const float* Q, int64_t qc, con
                                  w.qcodes, ix->code_bytes, w.qamb_list, w.qamb, (unsigned)w.qamb_cap,
                                  ix->At32, st));
     NRLSH_CK(launch_prep_queries(Q, qc, ix->d, Kq, w.qcodes, ix->code_bytes, ix->L, w.Qb, w.Qs,
-                                 w.err, st));
+                                 w.err, w.nlist + 2, st));
     if (hist_tc) {
         NRLSH_CK(launch_pairs_tc(false, w.Qb, w.Qs, qc, ix->tc_xb, ix->tc_xs, ix->n, ix->d, ix->dp,
                                  ix->m, ix->L, ix->seg, nullptr, nullptr, H, nullptr, nullptr,
                                  nullptr, nullptr, nullptr, 0.0f, nullptr, nullptr, nullptr, 0,
-                                 w.err, st, test_spin_first()));
+                                 w.err, w.nlist + 2, st, test_spin_first()));
     } else {
         if (!ix->tiles_exclusive)
             NRLSH_CK(cudaMemsetAsync(H, 0, sizeof(uint32_t) * qc * ix->ncls, st));
@@ -976,7 +976,7 @@ nrlsh_status run_tc_chunk(const nrlsh_index* ix, const float* Q, int64_t qc, con
     NRLSH_CK(launch_pairs_tc(true, w.Qb, w.Qs, qc, ix->tc_xb, ix->tc_xs, ix->n, ix->d, ix->dp,
                              ix->m, ix->L, ix->seg, w.list, w.nlist, nullptr, w.lam, w.off, w.tb,
                              ix->xnorm, w.qnorm, c_tc, w.cand, w.lo, w.hi, w.cap, w.err,
-                             st, test_spin_first()));
+                             w.nlist + 1, st, test_spin_first()));
     // the last kernel skips its work when the call's error word is set and
     // copies that word into the index's
     if (cand_out)

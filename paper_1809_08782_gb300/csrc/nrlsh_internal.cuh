@@ -336,10 +336,11 @@ int tc_query_k_chunks(int d);
 // c_tc: |score_tc - score_fp64| <= c_tc ||q|| ||x|| for the bf16 tensor-core scores.
 float tc_score_bound(int d, bool fp32_items);
 // Qb (nq x 64 tc_query_k_chunks(d) bf16) and Qs (nq x 64 bf16 +-1 signs of the codes).
-// Also clears the call's error word *err (the tensor-path kernels' timeouts).
+// Also clears the call's error word *err (the tensor-path kernels' timeouts) and
+// the histogram kernel's work counter *hist_ctr.
 cudaError_t launch_prep_queries(const float* Q, int64_t nq, int d, int Kq, const void* qcodes,
                                 int code_bytes, int L, __nv_bfloat16* Qb, __nv_bfloat16* Qs,
-                                int* err, cudaStream_t st);
+                                int* err, uint32_t* hist_ctr, cudaStream_t st);
 // *report = *err when *report is still 0 and *err is not.
 cudaError_t launch_report_err(const int* err, int* report, cudaStream_t st);
 // Xs (n x 64 bf16): the +-1 signs of the item codes, storage order.
@@ -356,8 +357,8 @@ cudaError_t launch_pairs_tc(bool rerank, const __nv_bfloat16* Qb, const __nv_bfl
                             const uint32_t* list, const uint32_t* nlist, uint32_t* H,
                             const uint8_t* lam, const uint32_t* off, const TcBoundary* tb,
                             const float* xnorm, const float* qnorm, float c_tc, uint32_t* cand,
-                            float* lo, float* hi, int64_t cap, int* err, cudaStream_t st,
-                            uint32_t spin_first = 1u << 22);
+                            float* lo, float* hi, int64_t cap, int* err, uint32_t* work_ctr,
+                            cudaStream_t st, uint32_t spin_first = 1u << 22);
 // Bucket walk of every query (budgets per query or one budget, clamped to [1, cap]),
 // then per sub-dataset the probed counts as list offsets off (nq x (m + 1)), the
 // boundary cut (tb), bnd[q].full = min(B, n) (r = 0) for the top-k pass, and
@@ -369,7 +370,8 @@ cudaError_t launch_tc_walk(const uint32_t* H, const uint32_t* order, int m, int 
                            int code_bytes, uint8_t* lam, uint32_t* off, TcBoundary* tb,
                            Boundary* bnd, uint8_t* work_flag, int nqt, const int* err,
                            cudaStream_t st);
-// Indices of the nonzero flags, ascending (list), and their number (*count).
+// Indices of the nonzero flags, ascending (list), their number (count[0]), and
+// count[1] = 0 (the work counter of the kernel that consumes the list).
 cudaError_t launch_work_list(const uint8_t* flag, int nflag, uint32_t* list, uint32_t* count,
                              cudaStream_t st);
 

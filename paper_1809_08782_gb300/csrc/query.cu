@@ -339,7 +339,10 @@ __global__ void __launch_bounds__(1024)
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *count = carry_s;
+    if (threadIdx.x == 0) {
+        *count = carry_s;
+        count[1] = 0;      // the consumer's work counter starts at zero
+    }
 }
 
 // ------------------------------------------------------------------ select

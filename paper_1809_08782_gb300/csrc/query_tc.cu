@@ -52,6 +52,7 @@ constexpr int kPThreads = 32 * (2 + kEpiWarps);
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;       // 2 buffers x (128 score + 128 sign columns)
 constexpr int kMaxStages = 8;
+constexpr int kWorkRing = 4;              // work items in flight between the roles
 
 struct PairsArgs {
     const uint32_t* list;       // work items (j * nqt + query tile); null: all m * nqt
@@ -72,6 +73,7 @@ struct PairsArgs {
     float* hi;
     int64_t cap;
     int* err;
+    uint32_t* work_ctr;         // work items handed out so far (zeroed before the launch)
     uint32_t spin_first;        // polls of the MMA thread's first wait for a stage
 };
 
@@ -113,7 +115,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
     uint64_t* a_full = acc_empty + 2;
     uint64_t* a_empty = a_full + 1;
     uint64_t* drain = a_empty + 1;
-    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    uint64_t* wq_full = drain + 1;              // kWorkRing: a work item is published
+    uint64_t* wq_empty = wq_full + kWorkRing;   // kWorkRing: the MMA thread and the
+                                                // epilogue leader have read it
+    volatile int* wq_item = (volatile int*)(wq_empty + kWorkRing);
+    volatile int* epi_item = wq_item + kWorkRing;
+    uint32_t* tmem_slot = (uint32_t*)(wq_item + kWorkRing + 4);
     volatile int* abort_s = (volatile int*)(tmem_slot + 1);
     uint32_t* extra = (uint32_t*)(tmem_slot + 4);
     // HIST: counters [l][half][row]; RERANK: staged xnorm [warp][64], counts
@@ -140,6 +147,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
         mbar_init(drain, 1);
+        for (int r = 0; r < kWorkRing; ++r) {
+            mbar_init(&wq_full[r], 1);
+            mbar_init(&wq_empty[r], 2);
+        }
         *abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -168,9 +179,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
         fence_after();
     }
 
-    // Work items are taken from the end of the (sub-dataset major, ascending) order:
-    // the highest-norm sub-datasets, whose tiles hold the most candidates, go first,
-    // so the static round-robin spreads them over all CTAs.
+    // Work items are handed out dynamically: the producer thread claims the next
+    // index from the global counter and publishes it in the ring; the MMA thread
+    // and the epilogue take the same sequence.  Indices run from the end of the
+    // (sub-dataset major, ascending) order, so the highest-norm sub-datasets,
+    // whose tiles hold the most candidates, start first.
     auto decode = [&](int i, int& j, int& qt, int64_t& p0, int& ntile) {
         const int ir = nwork - 1 - i;
         const uint32_t w = a.list ? a.list[ir] : (uint32_t)ir;
@@ -189,10 +202,24 @@ __global__ void __launch_bounds__(kPThreads, 1)
             uint32_t issued_par[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) issued[s] = 0, issued_par[s] = 0;
             int a_issued = 0;
-            for (int i = blockIdx.x; i < nwork && !*abort_s; i += gridDim.x) {
+            for (int k = 0;; ++k) {
+                const int rs = k % kWorkRing;
+                int item = -1;
+                if (!*abort_s) {
+                    if (k >= kWorkRing && !mbar_wait(&wq_empty[rs], ((k / kWorkRing) - 1) & 1)) {
+                        atomicCAS(a.err, 0, 16);
+                        *abort_s = 1;
+                    } else {
+                        const uint32_t c = atomicAdd(a.work_ctr, 1u);
+                        if (c < (uint32_t)nwork) item = (int)c;
+                    }
+                }
+                wq_item[rs] = item;
+                mbar_arrive(&wq_full[rs]);
+                if (item < 0) break;
                 int j, qt, ntile;
                 int64_t p0;
-                decode(i, j, qt, p0, ntile);
+                decode(item, j, qt, p0, ntile);
                 if (ntile == 0) continue;
                 if (!mbar_wait(a_empty, (a_round & 1) ^ 1)) {
                     atomicCAS(a.err, 0, 11);
@@ -244,10 +271,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
             int stage = 0, buf = 0;
             uint32_t phase = 0, acc_phase = 0, a_round = 0;
             bool ok = true, first = true;
-            for (int i = blockIdx.x; ok && i < nwork && !*abort_s; i += gridDim.x) {
+            for (int k = 0; ok; ++k) {
+                const int rs = k % kWorkRing;
+                if (*abort_s || !mbar_wait(&wq_full[rs], (k / kWorkRing) & 1)) {
+                    ok = false;
+                    break;
+                }
+                const int item = wq_item[rs];
+                mbar_arrive(&wq_empty[rs]);
+                if (item < 0) break;
                 int j, qt, ntile;
                 int64_t p0;
-                decode(i, j, qt, p0, ntile);
+                decode(item, j, qt, p0, ntile);
                 if (ntile == 0) continue;
                 if (!mbar_wait(a_full, a_round & 1)) {
                     ok = false;
@@ -321,10 +356,29 @@ __global__ void __launch_bounds__(kPThreads, 1)
         int buf = 0;
         uint32_t acc_phase = 0;
         bool aborted = false;
-        for (int i = blockIdx.x; i < nwork; i += gridDim.x) {
+        for (int k = 0;; ++k) {
+            // one leader takes the next item (a bounded wait) and the 256 epilogue
+            // threads meet once, so all of them follow the same sequence of items
+            if (et == 0) {
+                const int rs = k % kWorkRing;
+                int item = -1;
+                if (!*abort_s) {
+                    if (mbar_wait(&wq_full[rs], (k / kWorkRing) & 1)) {
+                        item = wq_item[rs];
+                    } else {
+                        atomicCAS(a.err, 0, 17);
+                        *abort_s = 1;
+                    }
+                }
+                *epi_item = item;
+                mbar_arrive(&wq_empty[rs]);
+            }
+            epi_sync();
+            const int item = *epi_item;     // read before the item's closing barriers
+            if (item < 0) break;
             int j, qt, ntile;
             int64_t p0;
-            decode(i, j, qt, p0, ntile);
+            decode(item, j, qt, p0, ntile);
             const int64_t q = (int64_t)qt * kPM + row;
             const bool qv = q < a.nq;
             const int64_t p1 = a.seg[j + 1];
@@ -559,9 +613,12 @@ template <typename C>
 __global__ void prep_queries_kernel(const float* __restrict__ Q, int64_t nq, int d, int Kq,
                                     const C* __restrict__ qcodes, int L,
                                     __nv_bfloat16* __restrict__ Qb, __nv_bfloat16* __restrict__ Qs,
-                                    int* __restrict__ err) {
+                                    int* __restrict__ err, uint32_t* __restrict__ hist_ctr) {
     NRLSH_PDL_ENTRY();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;   // the call's error word starts clear
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *err = 0;          // the call's error word starts clear
+        *hist_ctr = 0;     // the histogram kernel's work counter
+    }
     const int64_t total = nq * Kq;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -619,7 +676,8 @@ size_t pairs_smem_bytes(bool rerank, int nkc, int L, int stages) {
     const int na = rerank ? nkc + 1 : 1;
     const size_t extra = rerank ? (size_t)(kEpiWarps * 64 + 2 * kPM + kEpiWarps * 32 * 33) * 4
                                 : (size_t)(L + 1) * 2 * kPM * 4;
-    return 1024 + (size_t)(na + stages) * kChunk + (2 * (size_t)stages + 7) * 8 + 16 + extra;
+    return 1024 + (size_t)(na + stages) * kChunk + (2 * (size_t)stages + 7 + 2 * kWorkRing) * 8 +
+           (kWorkRing + 4) * 4 + 16 + extra;
 }
 
 int pairs_stages(bool rerank, int nkc, int L) {
@@ -668,13 +726,13 @@ float tc_score_bound(int d, bool fp32_items) {
 
 cudaError_t launch_prep_queries(const float* Q, int64_t nq, int d, int Kq, const void* qcodes,
                                 int code_bytes, int L, __nv_bfloat16* Qb, __nv_bfloat16* Qs,
-                                int* err, cudaStream_t st) {
+                                int* err, uint32_t* hist_ctr, cudaStream_t st) {
     const dim3 grid(grid_for(nq * Kq));
     if (code_bytes == 4)
         return launch("prep_queries", prep_queries_kernel<uint32_t>, grid, dim3(256), 0, st, Q, nq, d,
-                      Kq, (const uint32_t*)qcodes, L, Qb, Qs, err);
+                      Kq, (const uint32_t*)qcodes, L, Qb, Qs, err, hist_ctr);
     return launch("prep_queries", prep_queries_kernel<uint64_t>, grid, dim3(256), 0, st, Q, nq, d, Kq,
-                  (const uint64_t*)qcodes, L, Qb, Qs, err);
+                  (const uint64_t*)qcodes, L, Qb, Qs, err, hist_ctr);
 }
 
 __global__ void report_err_kernel(const int* __restrict__ err, int* __restrict__ report) {
@@ -707,8 +765,8 @@ cudaError_t launch_pairs_tc(bool rerank, const __nv_bfloat16* Qb, const __nv_bfl
                             const uint32_t* list, const uint32_t* nlist, uint32_t* H,
                             const uint8_t* lam, const uint32_t* off, const TcBoundary* tb,
                             const float* xnorm, const float* qnorm, float c_tc, uint32_t* cand,
-                            float* lo, float* hi, int64_t cap, int* err, cudaStream_t st,
-                            uint32_t spin_first) {
+                            float* lo, float* hi, int64_t cap, int* err, uint32_t* work_ctr,
+                            cudaStream_t st, uint32_t spin_first) {
     if (nq <= 0) return cudaSuccess;
     const int nkc = tc_query_k_chunks(d);
     const int Kq = 64 * nkc;
@@ -748,9 +806,11 @@ cudaError_t launch_pairs_tc(bool rerank, const __nv_bfloat16* Qb, const __nv_bfl
     a.hi = hi;
     a.cap = cap;
     a.err = err;
+    a.work_ctr = work_ctr;
     a.spin_first = spin_first;
     const size_t smem = pairs_smem_bytes(rerank, nkc, L, a.stages);
-    // one CTA per SM; with a work list of unknown length (on the device) every SM
+    // one CTA per SM (items are handed out dynamically; a work list's length is on
+    // the device)
     const int grid = list ? sm_count() : (int)std::min<int64_t>(a.nwork_all, sm_count());
     if (rerank) {
         auto kern = pairs_tc_kernel<true>;
