@@ -13,12 +13,13 @@ to exact MIPS).
 
 Two forms are timed on that step (the metric's comparison):
   plain_fp32    FP32 CUDA-core projection, FP32 gather re-rank (persistent kernel)
-  bf16_batched  bf16 tcgen05 projection, probing and re-rank on tensor cores
-                (nrlsh_query_batched, NRLSH_QUERY_TENSOR)
+  bf16_batched  bf16 tcgen05 projection, then the batched query on bf16 operands
+                (nrlsh_query_batched, NRLSH_QUERY_BF16: the autotuner picks tensor
+                cores or the FP32 re-rank over a bf16 copy of the rows)
 and, beside the line, the batching workload the batched form is built for: the
 ImageNet-sized preset (n = 2,340,373 x 150 bf16, m = 64, L = 64) with 100,000
 queries of per-query budgets U[0.1%, 5%] of n and k in {1, 10, 100}, built once,
-both forms through nrlsh_query_batched (the tensor form replayed as a CUDA graph).
+both forms through nrlsh_query_batched (the bf16 form replayed as a CUDA graph).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -223,7 +224,7 @@ def gpu_arm(args):
 
     ks_d = torch.full((w.nq,), w.k, dtype=torch.int32, device=dev)
     bs_d = torch.full((w.nq,), budget, dtype=torch.int64, device=dev)
-    tc_flags = N.NRLSH_QUERY_TENSOR | N.NRLSH_QUERY_NO_TUNE
+    tc_flags = N.NRLSH_QUERY_BF16
 
     def step_plain(Xs, Qs, ids=None, scores=None):
         ix = N.nrlsh_build_ex(Xs, w.m, w.L, w.index_seed, eps=eps, projection=N.NRLSH_PROJECT_SIMT)
@@ -401,7 +402,7 @@ def batching_form(args, N, torch, dev, stream, world):
            "step": "one batch over the resident index",
            "l2": "inputs and index larger than L2"}
     forms = {"plain_fp32": N.NRLSH_QUERY_FP32,
-             "bf16_batched": N.NRLSH_QUERY_TENSOR | N.NRLSH_QUERY_GRAPH}
+             "bf16_batched": N.NRLSH_QUERY_BF16 | N.NRLSH_QUERY_GRAPH}
     results = {}
     with torch.cuda.stream(side):
         for name, fl in forms.items():
@@ -453,9 +454,11 @@ def algorithmic(name: str, w, budget: int):
     n, d, L, nq, m = w.n, w.d, w.L, w.nq, w.m
     cb = 4 if L <= 32 else 8
     if name.startswith("probe_rerank") or name.startswith("rerank_fp32"):
-        # per query: the candidate rows and ids, their bounds, the histogram row and
-        # the selection's sweep of the probed position range (at most n codes)
-        return "l2", float(nq * (budget * (4 * d + 4 + 8) + m * (L + 1) * 4 + n * cb))
+        # per query: the candidate rows (bf16 for the bf16 variants) and ids, their
+        # bounds, the histogram row and the selection's sweep of the probed
+        # position range (at most n codes)
+        rb = 2 if "bf16" in name else 4
+        return "l2", float(nq * (budget * (rb * d + 4 + 8) + m * (L + 1) * 4 + n * cb))
     if name.startswith("hist_u"):
         return "alu", float(nq * n)
     if name == "hist_tc":

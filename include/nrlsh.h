@@ -210,19 +210,27 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* index, const float* que
  *                 call with these pointers and sizes, and replay it on later identical
  *                 calls (needs a non-NULL stream; the graph and its workspace live
  *                 until nrlsh_free).
- * The first call for a given (nq, k_max, budget_max) shape times the candidate
- * configurations on a prefix of the batch (the autotuner) and keeps the fastest:
- * the FP32 path (popcount histograms with 32, 64 or 128 queries per block, the
- * persistent re-rank at 1, 2 or 4 CTAs per SM) and the tensor-core path of
- * nrlsh_query_ex's NRLSH_QUERY_TENSOR (histograms on tensor cores or by popcount);
- * NRLSH_QUERY_TENSOR / NRLSH_QUERY_FP32 restrict it to one path.  Make that call
- * before any stream capture of your own.  ks and budgets may be device or host
- * pointers like the other arrays.
+ * The first call for a given shape (device, the index's n, d, m, L, dtype and eps,
+ * and the call's nq, k_max, budget_max and path flags) times the candidate
+ * configurations on a prefix of the batch (the autotuner) and keeps the fastest
+ * for every later call of that shape, on any index of the process:
+ *   - the FP32 re-rank: popcount histograms with 32, 64 or 128 queries per block,
+ *     the persistent re-rank at 1, 2 or 4 CTAs per SM, gathering the stored rows
+ *     or (fp32 items) a bf16 copy of them: the scores' intervals then also cover
+ *     that copy's rounding, and the exact top-k still rescores from the stored rows;
+ *   - the tensor-core path of nrlsh_query_ex's NRLSH_QUERY_TENSOR (histograms on
+ *     tensor cores or by popcount).
+ * NRLSH_QUERY_TENSOR, NRLSH_QUERY_FP32 and NRLSH_QUERY_BF16 (at most one) restrict
+ * it.  Every path returns the same ids and scores.  Make that first call before
+ * any stream capture of your own.  ks and budgets may be device or host pointers
+ * like the other arrays.
  */
 #define NRLSH_QUERY_GRAPH 0x2u
 #define NRLSH_QUERY_NO_TUNE 0x4u   /* skip the autotuner: last tuned (or default) tiles */
-#define NRLSH_QUERY_FP32 0x10u     /* the FP32 CUDA-core path only (NRLSH_QUERY_TENSOR: the
-                                      tensor-core path only; neither: the autotuner picks) */
+#define NRLSH_QUERY_FP32 0x10u     /* the FP32 re-rank over the stored rows only */
+#define NRLSH_QUERY_BF16 0x20u     /* bf16 operands only: tensor cores, or the FP32 re-rank
+                                      over bf16 rows (NRLSH_QUERY_TENSOR: tensor cores only;
+                                      none of the three: the autotuner picks among all) */
 NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* index, const float* queries,
                                            int64_t nq, const int32_t* ks, const int64_t* budgets,
                                            int32_t k_max, int64_t budget_max, uint32_t flags,
@@ -236,7 +244,8 @@ NRLSH_API nrlsh_status nrlsh_batched_scratch_bytes(const nrlsh_index* index, int
                                                    uint32_t flags, int64_t* bytes);
 /* The autotuned configuration last used for this index: histogram queries per
  * block and persistent CTAs per SM (0, 0 before any batched call), and in
- * *tensor bit 0 = histograms on tensor cores, bit 1 = re-rank on tensor cores.
+ * *tensor bit 0 = histograms on tensor cores, bit 1 = re-rank on tensor cores,
+ * bit 2 = the FP32 re-rank gathers a bf16 copy of fp32 rows.
  * Any output may be NULL. */
 NRLSH_API nrlsh_status nrlsh_get_tuning(const nrlsh_index* index, int32_t* hist_queries_per_block,
                                         int32_t* ctas_per_sm, int32_t* tensor);

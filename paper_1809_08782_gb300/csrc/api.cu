@@ -19,6 +19,11 @@ struct nrlsh_batch_cfg {
     int ctas_per_sm = 2;    // persistent probe/re-rank CTAs per SM (FP32 re-rank)
     int hist_tc = 0;        // 1: histograms on tensor cores (sign products)
     int rerank_tc = 0;      // 1: candidates and score intervals on tensor cores
+    int rows_bf16 = 0;      // 1: the FP32 re-rank gathers a bf16 copy of fp32 rows
+    bool operator==(const nrlsh_batch_cfg& o) const {
+        return hist_qb == o.hist_qb && ctas_per_sm == o.ctas_per_sm && hist_tc == o.hist_tc &&
+               rerank_tc == o.rerank_tc && rows_bf16 == o.rows_bf16;
+    }
 };
 
 // A captured batched-query launch sequence with its fixed workspace.
@@ -27,7 +32,7 @@ struct nrlsh_graph_entry {
                const void*, void*> key;
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> workspace;
-    int rerank_tc = 0, hist_tc = 0, hist_qb = 0, ctas_per_sm = 0;   // the captured configuration
+    nrlsh_batch_cfg cfg{0, 0, 0, 0};   // the captured configuration
 };
 
 struct nrlsh_index {
@@ -79,9 +84,8 @@ struct nrlsh_index {
     mutable __nv_bfloat16* tc_xb = nullptr;
     mutable cudaEvent_t tc_ready = nullptr;
     mutable std::vector<void*> tc_owned;
-    // batched queries: autotuned configurations per (nq, k_max, cap) and graph cache
+    // batched queries: the configuration last used and the graph cache
     mutable std::mutex batch_mu;
-    mutable std::map<std::tuple<int64_t, int, int64_t, int>, nrlsh_batch_cfg> tuned;
     mutable nrlsh_batch_cfg last_cfg{0, 0, 0, 0};
     mutable std::vector<nrlsh_graph_entry> graphs;
 };
@@ -1646,6 +1650,7 @@ nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, cons
     }
     BatchWs w;
     batch_ws_assign(w, p, ix, nq, batch_ctas(cfg, cap));
+    const __nv_bfloat16* xr16 = cfg.rows_bf16 && ix->dtype == NRLSH_F32 ? ix->tc_xb : nullptr;
     NRLSH_CK(launch_hash_queries(Q, nq, ix->d, ix->L, ix->Lp, ix->A_pad, ix->anorm, w.qnorm,
                                  w.qcodes, ix->code_bytes, w.qamb_list, w.qamb,
                                  (unsigned)w.qamb_cap, ix->At32, st));
@@ -1662,21 +1667,74 @@ nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, cons
             ix->code_bytes,
             ix->Xp, ix->dtype, ix->dp, ix->d, Q + q0 * ix->d, ix->xnorm, w.qnorm + q0, ix->perm,
             ks + q0, k_max, w.slabs, cap, w.ctas, w.work, qc, ids + q0 * k_max,
-            scores + q0 * k_max, st));
+            scores + q0 * k_max, st, xr16));
     }
     return NRLSH_OK;
 }
 
-// Which paths a batched call may use: 0 either (autotuned), 1 tensor cores only,
-// 2 FP32 CUDA cores only.
+nrlsh_status check_batch_flags(uint32_t flags) {
+    const uint32_t path = NRLSH_QUERY_TENSOR | NRLSH_QUERY_FP32 | NRLSH_QUERY_BF16;
+    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE | path)) return arg_error("unknown flags");
+    const uint32_t p = flags & path;
+    if (p & (p - 1))
+        return arg_error("NRLSH_QUERY_TENSOR, NRLSH_QUERY_FP32 and NRLSH_QUERY_BF16 exclude each other");
+    return NRLSH_OK;
+}
+
+// Which paths a batched call may use: 0 any (autotuned), 1 tensor cores only,
+// 2 the FP32 re-rank over the stored rows only, 3 bf16 operands only (tensor
+// cores, or the FP32 re-rank over bf16 rows).
 int batch_mode(uint32_t flags) {
-    return (flags & NRLSH_QUERY_TENSOR) ? 1 : (flags & NRLSH_QUERY_FP32) ? 2 : 0;
+    return (flags & NRLSH_QUERY_TENSOR) ? 1
+           : (flags & NRLSH_QUERY_FP32) ? 2
+           : (flags & NRLSH_QUERY_BF16) ? 3
+                                        : 0;
+}
+
+// bf16 copies of the rows exist (or can be made) for this index.
+bool bf16_rows_ok(const nrlsh_index* ix) {
+    return ix->dtype == NRLSH_BF16 || tc_path_supported(ix);
+}
+
+// Whether a configuration belongs to the paths `mode` allows.
+bool cfg_allowed(const nrlsh_index* ix, int mode, const nrlsh_batch_cfg& c) {
+    switch (mode) {
+        case 1: return c.rerank_tc != 0;
+        case 2: return !c.rerank_tc && !c.rows_bf16;
+        case 3: return c.rerank_tc || c.rows_bf16 || ix->dtype == NRLSH_BF16;
+        default: return true;
+    }
+}
+
+// A path's configuration when nothing was tuned for it.
+nrlsh_batch_cfg default_cfg(const nrlsh_index* ix, int mode) {
+    nrlsh_batch_cfg c;
+    if (mode == 1) c.rerank_tc = c.hist_tc = 1;
+    if (mode == 3 && ix->dtype == NRLSH_F32) c.rows_bf16 = 1;
+    return c;
+}
+
+// The autotuner's results, shared by every index of the process: a configuration
+// depends on the device, the index's shape and the batch's sizes, not on the
+// values, so a rebuilt index of the same shape reuses it.
+using TuneKey = std::tuple<int, int64_t, int, int, int, int, int, uint32_t, int64_t, int, int64_t, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, nrlsh_batch_cfg> g_tuned;
+
+TuneKey tune_key(const nrlsh_index* ix, int64_t nq, int k_max, int64_t cap, int mode) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    uint32_t eb;
+    std::memcpy(&eb, &ix->eps, 4);
+    return TuneKey(dev, ix->n, ix->d, ix->m, ix->L, (int)ix->dtype, ix->code_bytes, eb, nq, k_max,
+                   cap, mode);
 }
 
 // Time the candidate configurations on a prefix of the batch; keep the fastest.
-// FP32 path: the popcount histogram's query tile (32, 64, 128) and the persistent
-// re-rank's CTAs per SM (1, 2, 4).  Tensor-core path: histograms on tensor cores
-// or by popcount (best tile), candidates and scores on tensor cores.
+// FP32 re-rank: the popcount histogram's query tile (32, 64, 128) and the
+// persistent re-rank's CTAs per SM (1, 2, 4), over the stored rows or (fp32
+// items) their bf16 copy.  Tensor-core path: histograms on tensor cores or by
+// popcount (best tile), candidates and scores on tensor cores.
 nrlsh_status autotune(const nrlsh_index* ix, const float* Q, int64_t nq, const int32_t* ks,
                       const int64_t* budgets, int k_max, int64_t cap, int mode, int64_t* ids,
                       float* scores, cudaStream_t st, nrlsh_batch_cfg* best) {
@@ -1712,6 +1770,8 @@ nrlsh_status autotune(const nrlsh_index* ix, const float* Q, int64_t nq, const i
     };
     nrlsh_batch_cfg c;
     int best_qb = 64;
+    // the re-rank's row copy the tile sweep runs with
+    const int rb = mode == 3 && ix->dtype == NRLSH_F32 ? 1 : 0;
     {
         // the popcount histogram's tile (FP32 re-rank at 2 CTAs per SM)
         float qb_ms = 1e30f;
@@ -1719,6 +1779,7 @@ nrlsh_status autotune(const nrlsh_index* ix, const float* Q, int64_t nq, const i
             c = nrlsh_batch_cfg{};
             c.hist_qb = qb;
             c.ctas_per_sm = 2;
+            c.rows_bf16 = rb;
             float ms;
             NRLSH_CKS(time_cfg(c, &ms));
             if (ms < qb_ms) {
@@ -1736,10 +1797,20 @@ nrlsh_status autotune(const nrlsh_index* ix, const float* Q, int64_t nq, const i
             c = nrlsh_batch_cfg{};
             c.hist_qb = best_qb;
             c.ctas_per_sm = cps;
+            c.rows_bf16 = rb;
             NRLSH_CKS(consider(c));
         }
     }
-    if (mode != 2 && tc_path_supported(ix)) {
+    if (mode == 0 && ix->dtype == NRLSH_F32 && bf16_rows_ok(ix)) {
+        for (int cps : {2, 4}) {
+            c = nrlsh_batch_cfg{};
+            c.hist_qb = best_qb;
+            c.ctas_per_sm = cps;
+            c.rows_bf16 = 1;
+            NRLSH_CKS(consider(c));
+        }
+    }
+    if ((mode == 0 || mode == 1 || mode == 3) && tc_path_supported(ix)) {
         for (int htc : {1, 0}) {
             c = nrlsh_batch_cfg{};
             c.hist_qb = best_qb;
@@ -1763,14 +1834,15 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     NRLSH_CKS(check_query_args(ix, queries, nq));
     if (k_max < 1 || k_max > NRLSH_MAX_K) return arg_error("need 1 <= k_max <= 1024");
     if (budget_max < 1) return arg_error("need budget_max >= 1");
-    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE | NRLSH_QUERY_TENSOR | NRLSH_QUERY_FP32))
-        return arg_error("unknown flags");
-    if ((flags & NRLSH_QUERY_TENSOR) && (flags & NRLSH_QUERY_FP32))
-        return arg_error("NRLSH_QUERY_TENSOR and NRLSH_QUERY_FP32 exclude each other");
+    NRLSH_CKS(check_batch_flags(flags));
     if (nq > 0 && (!ids || !scores || !ks || !budgets)) return arg_error("NULL array");
     const int mode = batch_mode(flags);
     if (mode == 1 && !tc_path_supported(ix)) {
         set_error("the tensor-core query path needs an sm_100-family GPU and rows that fit its tiles");
+        return NRLSH_ERR_UNSUPPORTED;
+    }
+    if (mode == 3 && !bf16_rows_ok(ix)) {
+        set_error("the bf16 query paths need an sm_100-family GPU and rows that fit its tiles");
         return NRLSH_ERR_UNSUPPORTED;
     }
     if (nq == 0) return NRLSH_OK;
@@ -1785,7 +1857,7 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) NRLSH_CK(cudaStreamIsCapturing(st, &cs));
     const bool capturing = cs != cudaStreamCaptureStatusNone;
-    // the tensor path's index operands exist before any tuning or capture
+    // the bf16 paths' index operands exist before any tuning or capture
     if (mode != 2 && tc_path_supported(ix)) NRLSH_CKS(ensure_tc_items(ix, st, capturing));
     Scratch sc(st);
     const void *Qd, *ksd, *bd;
@@ -1798,24 +1870,27 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     NRLSH_CKS(stage_out(sc, ids, (size_t)nq * k_max, oi, &idsd));
     NRLSH_CKS(stage_out(sc, scores, (size_t)nq * k_max, os, &scd));
 
-    nrlsh_batch_cfg cfg;
-    if (mode == 1) {
-        cfg.rerank_tc = 1;
-        cfg.hist_tc = 1;
-    }
+    nrlsh_batch_cfg cfg = default_cfg(ix, mode);
     {
         std::lock_guard<std::mutex> g(ix->batch_mu);
-        const auto key = std::make_tuple(nq, (int)k_max, cap, mode);
-        auto it = ix->tuned.find(key);
-        if (it != ix->tuned.end()) {
-            cfg = it->second;
-        } else if (flags & NRLSH_QUERY_NO_TUNE) {
+        const TuneKey key = tune_key(ix, nq, k_max, cap, mode);
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> gt(g_tune_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                cfg = it->second;
+                found = true;
+            }
+        }
+        if (!found && (flags & NRLSH_QUERY_NO_TUNE)) {
             const nrlsh_batch_cfg& l = ix->last_cfg;
-            if (l.hist_qb && (mode == 0 || (mode == 1) == (l.rerank_tc != 0))) cfg = l;
-        } else if (!capturing) {
+            if (l.hist_qb && cfg_allowed(ix, mode, l)) cfg = l;
+        } else if (!found && !capturing) {
             NRLSH_CKS(autotune(ix, (const float*)Qd, nq, (const int32_t*)ksd, (const int64_t*)bd,
                                k_max, cap, mode, idsd, scd, st, &cfg));
-            ix->tuned[key] = cfg;
+            std::lock_guard<std::mutex> gt(g_tune_mu);
+            g_tuned[key] = cfg;
         }
         ix->last_cfg = cfg;
     }
@@ -1836,17 +1911,13 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     const auto key = std::make_tuple((const void*)queries, nq, (const void*)ks, (const void*)budgets,
                                      (int)k_max, cap, (const void*)ids, (const void*)scores, stream);
     for (auto& e : ix->graphs)
-        if (e.key == key && e.rerank_tc == cfg.rerank_tc && e.hist_tc == cfg.hist_tc &&
-            e.hist_qb == cfg.hist_qb && e.ctas_per_sm == cfg.ctas_per_sm) {
+        if (e.key == key && e.cfg == cfg) {
             NRLSH_CK(cudaGraphLaunch(e.exec, st));
             return NRLSH_OK;
         }
     nrlsh_graph_entry e;
     e.key = key;
-    e.rerank_tc = cfg.rerank_tc;
-    e.hist_tc = cfg.hist_tc;
-    e.hist_qb = cfg.hist_qb;
-    e.ctas_per_sm = cfg.ctas_per_sm;
+    e.cfg = cfg;
     for (size_t b : cfg_ws_sizes(ix, cfg, nq, cap)) {
         void* q = nullptr;
         cudaError_t err = cudaMalloc(&q, std::max<size_t>(b, 16));
@@ -1882,27 +1953,25 @@ extern "C" NRLSH_API nrlsh_status nrlsh_batched_scratch_bytes(const nrlsh_index*
                                                               uint32_t flags, int64_t* bytes) {
     if (!ix || !bytes) return arg_error("NULL argument");
     if (nq < 0 || k_max < 1 || budget_max < 1) return arg_error("bad sizes");
-    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE | NRLSH_QUERY_TENSOR | NRLSH_QUERY_FP32))
-        return arg_error("unknown flags");
+    NRLSH_CKS(check_batch_flags(flags));
     const int mode = batch_mode(flags);
     const int64_t cap = std::min<int64_t>(budget_max, ix->n);
     const int64_t qn = std::max<int64_t>(nq, 1);
-    // the configuration nrlsh_query_batched would use for these sizes and flags: a
-    // tuned one for (nq, k_max, cap) when it exists (with no path restriction, the
-    // largest of them), else the last one used when it is allowed, else the
-    // path's default
+    // the configuration nrlsh_query_batched would use for these sizes and flags: the
+    // tuned one when it exists, else the last one used when the flags allow it,
+    // else the path's default
     std::vector<nrlsh_batch_cfg> cfgs;
     {
         std::lock_guard<std::mutex> g(ix->batch_mu);
-        for (const auto& kv : ix->tuned)
-            if (std::get<0>(kv.first) == nq && std::get<1>(kv.first) == (int)k_max &&
-                std::get<2>(kv.first) == cap && (mode == 0 || std::get<3>(kv.first) == mode))
-                cfgs.push_back(kv.second);
+        {
+            std::lock_guard<std::mutex> gt(g_tune_mu);
+            auto it = g_tuned.find(tune_key(ix, nq, k_max, cap, mode));
+            if (it != g_tuned.end()) cfgs.push_back(it->second);
+        }
         if (cfgs.empty()) {
             const nrlsh_batch_cfg& l = ix->last_cfg;
-            nrlsh_batch_cfg c;
-            if (mode == 1) c.rerank_tc = c.hist_tc = 1;
-            if (l.hist_qb && (mode == 0 || (mode == 1) == (l.rerank_tc != 0))) c = l;
+            nrlsh_batch_cfg c = default_cfg(ix, mode);
+            if (l.hist_qb && cfg_allowed(ix, mode, l)) c = l;
             cfgs.push_back(c);
         }
     }
@@ -1923,7 +1992,9 @@ extern "C" NRLSH_API nrlsh_status nrlsh_get_tuning(const nrlsh_index* ix, int32_
     std::lock_guard<std::mutex> g(ix->batch_mu);
     if (hist_qb) *hist_qb = ix->last_cfg.hist_qb;
     if (ctas_per_sm) *ctas_per_sm = ix->last_cfg.ctas_per_sm;
-    if (tensor) *tensor = (ix->last_cfg.hist_tc ? 1 : 0) | (ix->last_cfg.rerank_tc ? 2 : 0);
+    if (tensor)
+        *tensor = (ix->last_cfg.hist_tc ? 1 : 0) | (ix->last_cfg.rerank_tc ? 2 : 0) |
+                  (ix->last_cfg.rows_bf16 ? 4 : 0);
     return NRLSH_OK;
 }
 

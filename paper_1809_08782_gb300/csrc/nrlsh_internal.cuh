@@ -285,7 +285,8 @@ cudaError_t launch_probe_rerank(const uint32_t* H, const uint32_t* order, int m,
                                 float* out_scores, int out_ld, cudaStream_t st);
 // Persistent form: `ctas` CTAs pull queries from *work (zeroed by the caller).
 // budgets/ks may be null: then every query uses budget / k_max.  ctas <= 0: as many
-// CTAs as fit on the device at once.  slabs: ctas x 6 cap words.
+// CTAs as fit on the device at once.  slabs: ctas x 6 cap words.  Xr16 (fp32 items
+// only, may be null): a bf16 copy of the stored rows for the gathered re-rank.
 cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* order, int m, int L,
                                            int64_t n, const int64_t* seg, int64_t budget,
                                            const int64_t* budgets, const void* codes,
@@ -295,7 +296,9 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
                                            const uint32_t* perm, const int32_t* ks, int k_max,
                                            uint32_t* slabs, int64_t cap, int ctas, unsigned* work,
                                            int64_t nq, int64_t* out_ids, float* out_scores,
-                                           cudaStream_t st);
+                                           cudaStream_t st, const __nv_bfloat16* Xr16 = nullptr);
+// Interval factor of the gathered re-rank over a bf16 copy of fp32 rows.
+float rerank_bf16_rows_bound(int d);
 // Multi-table single probe (Algorithm 2): L bits as `tables` tables of L / tables
 // bits; block per query selects C(q), re-ranks and takes the exact top-k of its
 // first min(|C(q)|, cap) items.  probed (may be null) receives |C(q)|; with

@@ -692,34 +692,46 @@ __device__ void select_digit(const uint32_t* hist, int rem, int* dg_out, int* re
 constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
 constexpr int kDot2Max = 512;        // contenders scored by the compensated FP32 tier
 
+// Compensated dot products of two rows with the query at once (their loads in
+// flight together); row 1 may be null (then only row 0 is summed).
 template <typename T> struct RowDot2;
 template <> struct RowDot2<float> {
-    __device__ static void dot(const float* xr, const float* qs, int dp, int lane, float& sh,
-                               float& sl) {
-        const float4* x4 = (const float4*)xr;
+    __device__ static void dot(const float* xr0, const float* xr1, const float* qs, int dp,
+                               int lane, float (&sh)[2], float (&sl)[2]) {
+        const float4* a4 = (const float4*)xr0;
+        const float4* b4 = (const float4*)(xr1 ? xr1 : xr0);
         const float4* q4 = (const float4*)qs;
-#pragma unroll 4
+#pragma unroll 2
         for (int c = lane; c < dp / 4; c += 32) {
-            const float4 x = x4[c], y = q4[c];
-            dot2_step(x.x, y.x, sh, sl);
-            dot2_step(x.y, y.y, sh, sl);
-            dot2_step(x.z, y.z, sh, sl);
-            dot2_step(x.w, y.w, sh, sl);
+            const float4 x = a4[c], z = b4[c], y = q4[c];
+            dot2_step(x.x, y.x, sh[0], sl[0]);
+            dot2_step(z.x, y.x, sh[1], sl[1]);
+            dot2_step(x.y, y.y, sh[0], sl[0]);
+            dot2_step(z.y, y.y, sh[1], sl[1]);
+            dot2_step(x.z, y.z, sh[0], sl[0]);
+            dot2_step(z.z, y.z, sh[1], sl[1]);
+            dot2_step(x.w, y.w, sh[0], sl[0]);
+            dot2_step(z.w, y.w, sh[1], sl[1]);
         }
     }
 };
 template <> struct RowDot2<__nv_bfloat16> {
-    __device__ static void dot(const __nv_bfloat16* xr, const float* qs, int dp, int lane,
-                               float& sh, float& sl) {
-#pragma unroll 2
+    __device__ static void dot(const __nv_bfloat16* xr0, const __nv_bfloat16* xr1, const float* qs,
+                               int dp, int lane, float (&sh)[2], float (&sl)[2]) {
+        const uint4* a = (const uint4*)xr0;
+        const uint4* b = (const uint4*)(xr1 ? xr1 : xr0);
         for (int c = lane; c < dp / 8; c += 32) {
-            const uint4 raw = ((const uint4*)xr)[c];
-            const __nv_bfloat162* h = (const __nv_bfloat162*)&raw;
+            const uint4 ra = a[c], rb = b[c];
+            const __nv_bfloat162* ha = (const __nv_bfloat162*)&ra;
+            const __nv_bfloat162* hb = (const __nv_bfloat162*)&rb;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float2 x = __bfloat1622float2(h[i]);
-                dot2_step(x.x, qs[c * 8 + 2 * i], sh, sl);
-                dot2_step(x.y, qs[c * 8 + 2 * i + 1], sh, sl);
+                const float2 x = __bfloat1622float2(ha[i]), z = __bfloat1622float2(hb[i]);
+                const float y0 = qs[c * 8 + 2 * i], y1 = qs[c * 8 + 2 * i + 1];
+                dot2_step(x.x, y0, sh[0], sl[0]);
+                dot2_step(z.x, y0, sh[1], sl[1]);
+                dot2_step(x.y, y1, sh[0], sl[0]);
+                dot2_step(z.y, y1, sh[1], sl[1]);
             }
         }
     }
@@ -786,7 +798,22 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __shared__ double rank_lo[kDot2Max], rank_hi[kDot2Max];
     __shared__ uint16_t flagged[kDot2Max], flagged2[kDot2Max];
     __shared__ uint32_t nflag_s, nflag2_s;
+    __shared__ uint32_t idc_s[kDot2Max];      // original ids of the contenders (compensated tier)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // lists of up to kStageMax entries: both bounds read once into shared memory,
+    // so the selection passes and the contender scan do not wait on L2 again
+    constexpr int kStageMax = kRescoreSmem / 8;
+    const bool staged = count <= kStageMax;
+    if (staged) {
+        for (int64_t i = threadIdx.x; i < count; i += 256) {
+            rows_s[i] = loq[i];
+            rows_s[kStageMax + i] = hiq[i];
+        }
+        __syncthreads();
+    }
+    const float* lov = staged ? rows_s : loq;
+    const float* hiv = staged ? rows_s + kStageMax : hiq;
 
     float tau = -FLT_MAX;
     if (count > kq) {
@@ -801,7 +828,7 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
             const uint32_t prefix = prefix_s, mask = mask_s;
             const int rem = rem_s;
             for (int64_t i = threadIdx.x; i < count; i += 256) {
-                const uint32_t key = float_order(loq[i]);
+                const uint32_t key = float_order(lov[i]);
                 if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 0xFFu], 1u);
             }
             __syncthreads();
@@ -818,7 +845,7 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     if (threadIdx.x == 0) nc_s = 0;
     __syncthreads();
     for (int64_t i = threadIdx.x; i < count; i += 256) {
-        if (hiq[i] >= tau) contq[atomicAdd(&nc_s, 1u)] = (uint32_t)i;
+        if (hiv[i] >= tau) contq[atomicAdd(&nc_s, 1u)] = (uint32_t)i;
     }
     __syncthreads();
     const uint32_t nc = nc_s;
@@ -833,26 +860,38 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
         const int mlane = sizeof(T) == 4 ? 4 * ((dp / 4 + 31) / 32) : 8 * ((dp / 8 + 31) / 32);
         const double c2 = 4.0 * 0x1p-48 * (2.0 * mlane * (mlane + 1) + 10.0 * (dp + 32)) +
                           (double)(d + 2) * 0x1p-53;
-        for (uint32_t c = warp; c < nc; c += 8) {
-            const uint32_t pos = candq[contq[c]];
-            float sh = 0.0f, sl = 0.0f;
-            RowDot2<T>::dot(Xp + (int64_t)pos * dp, qs, dp, lane, sh, sl);
-            for (int o = 16; o; o >>= 1) {
-                const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
-                const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
-                const float s2 = __fadd_rn(sh, oh);
-                const float bb = __fsub_rn(s2, sh);
-                const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(oh, bb));
-                sh = s2;
-                sl = __fadd_rn(__fadd_rn(sl, ol), t);
+        // two contenders per warp at a time (c and c + 8 of each 16)
+        for (uint32_t c0 = warp; c0 < nc; c0 += 16) {
+            const uint32_t c1 = c0 + 8;
+            const bool two = c1 < nc;
+            const uint32_t pos0 = candq[contq[c0]];
+            const uint32_t pos1 = two ? candq[contq[c1]] : pos0;
+            float sh[2] = {0.0f, 0.0f}, sl[2] = {0.0f, 0.0f};
+            RowDot2<T>::dot(Xp + (int64_t)pos0 * dp, two ? Xp + (int64_t)pos1 * dp : nullptr, qs, dp,
+                            lane, sh, sl);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                for (int o = 16; o; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, sh[h], o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, sl[h], o);
+                    const float s2 = __fadd_rn(sh[h], oh);
+                    const float bb = __fsub_rn(s2, sh[h]);
+                    const float t = __fadd_rn(__fsub_rn(sh[h], __fsub_rn(s2, bb)), __fsub_rn(oh, bb));
+                    sh[h] = s2;
+                    sl[h] = __fadd_rn(__fadd_rn(sl[h], ol), t);
+                }
             }
-            if (lane == 0) {
-                const double v = __dadd_rn((double)sh, (double)sl);
+            if (lane < 2 && (lane == 0 || two)) {
+                const uint32_t c = lane == 0 ? c0 : c1;
+                const uint32_t pos = lane == 0 ? pos0 : pos1;
+                const float vh = lane == 0 ? sh[0] : sh[1], vl = lane == 0 ? sl[0] : sl[1];
+                const double v = __dadd_rn((double)vh, (double)vl);
                 const double e = c2 * (double)qn * (double)xnorm[pos] * (1.0 + 0x1p-20) +
                                  0x1p-52 * fabs(v) + 0x1p-120;
                 rank_lo[c] = __dsub_rd(v, e);
                 rank_hi[c] = __dadd_ru(v, e);
                 contsq[c] = v;
+                idc_s[c] = perm[pos];
             }
         }
         __syncthreads();
@@ -950,9 +989,10 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
         // unique (ids are), so rank < k places the item directly
         unsigned long long* key_s = (unsigned long long*)rows_s;
         int64_t* id_s = (int64_t*)(key_s + nc);
+        const bool have_ids = nc <= (uint32_t)kDot2Max;   // fetched by the compensated tier
         for (uint32_t c = threadIdx.x; c < nc; c += 256) {
             key_s[c] = double_key(contsq[c]);
-            id_s[c] = perm[candq[contq[c]]];
+            id_s[c] = have_ids ? (int64_t)idc_s[c] : (int64_t)perm[candq[contq[c]]];
         }
         __syncthreads();
         for (uint32_t c = threadIdx.x; c < nc; c += 256) {
@@ -1096,13 +1136,17 @@ __global__ void __launch_bounds__(256, 4)
 // nq, each reusing its own scratch slab (cand, lo, hi, cont: cap words each;
 // cont_s: cap doubles).  Per-query budgets and k; rows of the outputs are k_max
 // wide, padded with (-1, -inf).
-template <typename T, typename C>
+//
+// R is the row type of the gathered re-rank: T itself, or (fp32 items) a bf16
+// copy Xr of the rows, whose scores' intervals also cover the copy's rounding
+// (kappa); the exact top-k tiers always rescore from the stored rows Xp.
+template <typename T, typename C, typename R>
 __global__ void __launch_bounds__(256, 4)
     probe_rerank_persistent_kernel(const uint32_t* __restrict__ H, const uint32_t* __restrict__ order,
                                    int m, int L, int64_t n, const int64_t* __restrict__ seg,
                                    int64_t budget, const int64_t* __restrict__ budgets,
                                    const C* __restrict__ codes, const C* __restrict__ qcodes,
-                                   const T* __restrict__ Xp, int dp, int d,
+                                   const T* __restrict__ Xp, const R* __restrict__ Xr, int dp, int d,
                                    const float* __restrict__ Q, const float* __restrict__ xnorm,
                                    const float* __restrict__ qnorm, float kappa,
                                    const uint32_t* __restrict__ perm, const int32_t* __restrict__ ks,
@@ -1133,7 +1177,7 @@ __global__ void __launch_bounds__(256, 4)
         dev_select(codes, qcodes[q], seg, m, L, lam_s, b, cand, (uint32_t*)phase_s);
         __syncthreads();
         const int64_t count = (int64_t)b.full + b.r;
-        dev_rerank(Xp, dp, qs, cand, 0, count, xnorm, qnorm[q], kappa, lo, hi);
+        dev_rerank(Xr, dp, qs, cand, 0, count, xnorm, qnorm[q], kappa, lo, hi);
         __syncthreads();
         dev_topk(lo, hi, cand, count, ks ? min(max(ks[q], 1), k_max) : k_max, k_max, Xp, dp, d,
                  qs, qnorm[q],
@@ -1523,12 +1567,13 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
                                            const uint32_t* perm, const int32_t* ks, int k_max,
                                            uint32_t* slabs, int64_t cap, int ctas, unsigned* work,
                                            int64_t nq, int64_t* out_ids, float* out_scores,
-                                           cudaStream_t st) {
+                                           cudaStream_t st, const __nv_bfloat16* Xr16) {
     const size_t smem = sizeof(float) * (size_t)dp + (sizeof(uint32_t) + 1) * (size_t)m;
-    const float kappa = (float)(d + 2) * 0x1p-22f;
-#define NRLSH_PP(T_, C_, NAME)                                                                  \
+    const float kappa32 = (float)(d + 2) * 0x1p-22f;
+    const float kappa = Xr16 && dt == NRLSH_F32 ? rerank_bf16_rows_bound(d) : kappa32;
+#define NRLSH_PP(T_, C_, R_, XR_, NAME)                                                         \
     {                                                                                           \
-        auto kern = probe_rerank_persistent_kernel<T_, C_>;                                     \
+        auto kern = probe_rerank_persistent_kernel<T_, C_, R_>;                                 \
         cudaError_t e = ensure_dyn_smem((const void*)kern, smem);                               \
         if (e != cudaSuccess) return e;                                                         \
         if (ctas <= 0) {                                                                        \
@@ -1536,18 +1581,35 @@ cudaError_t launch_probe_rerank_persistent(const uint32_t* H, const uint32_t* or
             if (e != cudaSuccess) return e;                                                     \
         }                                                                                       \
         return launch(NAME, kern, dim3((unsigned)ctas), dim3(256), smem, st, H, order, m, L, n,  \
-                      seg, budget, budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp, dp, \
-                      d, Q,                                                                     \
-                      xnorm, qnorm, kappa, perm, ks, k_max, slabs, cap, work, nq, out_ids,      \
-                      out_scores);                                                              \
+                      seg, budget, budgets, (const C_*)codes, (const C_*)qcodes, (const T_*)Xp,  \
+                      (const R_*)(XR_), dp, d, Q, xnorm, qnorm, kappa, perm, ks, k_max, slabs,   \
+                      cap, work, nq, out_ids, out_scores);                                      \
     }
     if (dt == NRLSH_BF16) {
-        if (code_bytes == 4) NRLSH_PP(__nv_bfloat16, uint32_t, "probe_rerank_persistent_bf16")
-        NRLSH_PP(__nv_bfloat16, uint64_t, "probe_rerank_persistent_bf16")
+        if (code_bytes == 4)
+            NRLSH_PP(__nv_bfloat16, uint32_t, __nv_bfloat16, Xp, "probe_rerank_persistent_bf16")
+        NRLSH_PP(__nv_bfloat16, uint64_t, __nv_bfloat16, Xp, "probe_rerank_persistent_bf16")
     }
-    if (code_bytes == 4) NRLSH_PP(float, uint32_t, "probe_rerank_persistent")
-    NRLSH_PP(float, uint64_t, "probe_rerank_persistent")
+    if (Xr16) {
+        if (code_bytes == 4)
+            NRLSH_PP(float, uint32_t, __nv_bfloat16, Xr16, "probe_rerank_persistent_bf16rows")
+        NRLSH_PP(float, uint64_t, __nv_bfloat16, Xr16, "probe_rerank_persistent_bf16rows")
+    }
+    if (code_bytes == 4) NRLSH_PP(float, uint32_t, float, Xp, "probe_rerank_persistent")
+    NRLSH_PP(float, uint64_t, float, Xp, "probe_rerank_persistent")
 #undef NRLSH_PP
+}
+
+float rerank_bf16_rows_bound(int d) {
+    // x~ = bf16(x) = x (1 + delta), |delta| <= 2^-8 (an 8-bit significand, round to
+    // nearest): |q.x~ - q.x| <= 2^-8 sum|q x|; the FP32 sum of the q_k x~_k within
+    // (d + 2) 2^-22 sum|q x~| (4x the first-order bound), and the canonical FP64
+    // in-order sum's own (d + 2) 2^-53, all relative to sum|q x| <= ||q|| ||x||
+    const double c = (0x1p-8 + (d + 2.0) * 0x1p-22 * (1.0 + 0x1p-8) + (d + 2.0) * 0x1p-53) *
+                     (1.0 + 0x1p-20);
+    float f = (float)c;
+    if ((double)f < c) f = nextafterf(f, 1.0f);
+    return f;
 }
 
 cudaError_t launch_multitable(const void* codes, const void* qcodes, int code_bytes, int64_t n,
@@ -1621,12 +1683,13 @@ cudaError_t launch_rerank_work(const void* Xp, nrlsh_dtype dt, int dp, int d, co
 
 int probe_rerank_ctas(nrlsh_dtype dt, int code_bytes, int dp, int m, int64_t nq) {
     const size_t smem = sizeof(float) * (size_t)dp + (sizeof(uint32_t) + 1) * (size_t)m;
+    using BF = __nv_bfloat16;
     const void* kern =
         dt == NRLSH_BF16
-            ? (code_bytes == 4 ? (const void*)probe_rerank_persistent_kernel<__nv_bfloat16, uint32_t>
-                               : (const void*)probe_rerank_persistent_kernel<__nv_bfloat16, uint64_t>)
-            : (code_bytes == 4 ? (const void*)probe_rerank_persistent_kernel<float, uint32_t>
-                               : (const void*)probe_rerank_persistent_kernel<float, uint64_t>);
+            ? (code_bytes == 4 ? (const void*)probe_rerank_persistent_kernel<BF, uint32_t, BF>
+                               : (const void*)probe_rerank_persistent_kernel<BF, uint64_t, BF>)
+            : (code_bytes == 4 ? (const void*)probe_rerank_persistent_kernel<float, uint32_t, float>
+                               : (const void*)probe_rerank_persistent_kernel<float, uint64_t, float>);
     int ctas = 1;
     if (ensure_dyn_smem(kern, smem) != cudaSuccess || resident_ctas(kern, smem, nq, &ctas) != cudaSuccess)
         return (int)std::max<int64_t>(1, std::min<int64_t>(nq, 152));

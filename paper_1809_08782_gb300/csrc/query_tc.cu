@@ -709,13 +709,14 @@ bool tc_query_supported(int d, int L) {
 }
 
 float tc_score_bound(int d, bool fp32_items) {
-    // operand rounding: q~ = q (1 + d1), x~ = x (1 + d2), |d1| <= 2^-9 (round to
-    // nearest bf16), |d2| <= 2^-9 for fp32 items, 0 for bf16 items; accumulation of
+    // operand rounding: q~ = q (1 + d1), x~ = x (1 + d2), |d1| <= 2^-8 (round to
+    // nearest bf16: an 8-bit significand), |d2| <= 2^-8 for fp32 items, 0 for bf16
+    // items; accumulation of
     // K products within 16x the first-order FP32 bound, (K + 8) 2^-20; and the
     // canonical FP64 in-order sum's own (d + 2) 2^-53 -- all relative to
     // sum |q_k x_k| <= ||q|| ||x||.
     const double K = 16.0 * (double)ceil_div(d, 16);
-    const double rq = 0x1p-9, rx = fp32_items ? 0x1p-9 : 0.0;
+    const double rq = 0x1p-8, rx = fp32_items ? 0x1p-8 : 0.0;
     const double grow = (1.0 + rq) * (1.0 + rx);
     const double kappa = (K + 8.0) * 0x1p-20;
     const double c = ((grow - 1.0) + kappa * grow + (d + 2.0) * 0x1p-53) * (1.0 + 0x1p-20);

@@ -25,6 +25,7 @@ NRLSH_QUERY_GRAPH = 0x2
 NRLSH_QUERY_NO_TUNE = 0x4
 NRLSH_QUERY_TENSOR = 0x8
 NRLSH_QUERY_FP32 = 0x10
+NRLSH_QUERY_BF16 = 0x20
 
 _STATUS = {0: "NRLSH_OK", -1: "NRLSH_ERR_ARG", -2: "NRLSH_ERR_OOM", -3: "NRLSH_ERR_CUDA",
            -4: "NRLSH_ERR_TIMEOUT", -5: "NRLSH_ERR_UNSUPPORTED"}
@@ -311,12 +312,14 @@ def nrlsh_batched_scratch_bytes(index: Index, nq: int, k_max: int, budget_max: i
 
 def nrlsh_get_tuning(index: Index):
     """The autotuned batched configuration: popcount histogram tile, persistent
-    CTAs per SM, and whether the histograms / the re-rank run on tensor cores."""
+    CTAs per SM, whether the histograms / the re-rank run on tensor cores, and
+    whether the FP32 re-rank gathers a bf16 copy of the rows."""
     qb, cps, tc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().nrlsh_get_tuning(index.handle, ctypes.byref(qb), ctypes.byref(cps),
                                    ctypes.byref(tc)))
     return {"hist_queries_per_block": qb.value, "ctas_per_sm": cps.value,
-            "hist_tensor": bool(tc.value & 1), "rerank_tensor": bool(tc.value & 2)}
+            "hist_tensor": bool(tc.value & 1), "rerank_tensor": bool(tc.value & 2),
+            "rows_bf16": bool(tc.value & 4)}
 
 
 def nrlsh_hash_queries(index: Index, queries: torch.Tensor, stream=None) -> torch.Tensor:

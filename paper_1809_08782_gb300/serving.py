@@ -63,10 +63,12 @@ class Server:
     memory_budget  bytes of device scratch all in-flight batches may use
     max_batch      requests per batch at most
     path           "auto": the configuration the index's autotuner chose last;
-                   "tensor": the tensor-core path; "fp32": the FP32 CUDA-core path
+                   "tensor": the tensor-core path; "fp32": the FP32 re-rank over the
+                   stored rows; "bf16": bf16 operands (tensor cores or bf16 rows)
     """
 
-    _PATH_FLAGS = {"auto": 0, "tensor": N.NRLSH_QUERY_TENSOR, "fp32": N.NRLSH_QUERY_FP32}
+    _PATH_FLAGS = {"auto": 0, "tensor": N.NRLSH_QUERY_TENSOR, "fp32": N.NRLSH_QUERY_FP32,
+                   "bf16": N.NRLSH_QUERY_BF16}
 
     def __init__(self, index: "N.Index", slots: int = 3, memory_budget: int = 1 << 30,
                  max_batch: int = 4096, path: str = "auto"):

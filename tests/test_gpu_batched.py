@@ -41,8 +41,9 @@ def check_batched(ids, sc, ref, Q, ks, budgets, k_max):
         assert np.all(ids[i, k:] == -1) and np.all(np.isneginf(sc[i, k:]))
 
 
+@pytest.mark.parametrize("path", ["auto", "bf16"])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_batched_uneven_budgets_and_k(N, dtype):
+def test_batched_uneven_budgets_and_k(N, dtype, path):
     n, d, m, L = 20_000, 48, 16, 64
     items = rand_items(n, d, 3, dtype)
     lib, ref = build_pair(items, dtype, m, L, seed=7, eps=0.2)
@@ -50,12 +51,16 @@ def test_batched_uneven_budgets_and_k(N, dtype):
     Q = W.gen_queries(300, d, 11)
     budgets, ks = W.per_query_budgets_and_k(300, n, 0.001, 0.05, seed=12)
     k_max = int(ks.max())
+    flags = {"auto": 0, "bf16": N.NRLSH_QUERY_BF16}[path]
     ids, sc = N.nrlsh_query_batched(lib, torch.from_numpy(Q).cuda(), torch.from_numpy(ks).cuda(),
-                                    torch.from_numpy(budgets).cuda(), k_max, int(budgets.max()))
+                                    torch.from_numpy(budgets).cuda(), k_max, int(budgets.max()),
+                                    flags=flags)
     torch.cuda.synchronize()
     check_batched(ids, sc, ref, Q, ks, budgets, k_max)
     tun = N.nrlsh_get_tuning(lib)
     assert tun["hist_queries_per_block"] in (32, 64, 128) and tun["ctas_per_sm"] in (1, 2, 4)
+    if path == "bf16" and dtype == "f32":
+        assert tun["rerank_tensor"] or tun["rows_bf16"]
 
 
 def test_batched_graph_replay_and_clamping(N):

@@ -80,6 +80,8 @@ def test_large_k_batched(N, tied):
     ks = rng.choice([1, 100, 600, 1024], 40).astype(np.int32)
     budgets = rng.integers(1_024, 20_001, 40).astype(np.int64)
     check_batched(N, lib, ref, Q, ks, budgets, N.NRLSH_QUERY_FP32)
+    check_batched(N, lib, ref, Q, ks, budgets, N.NRLSH_QUERY_BF16 | N.NRLSH_QUERY_NO_TUNE)
+    assert N.nrlsh_get_tuning(lib)["rows_bf16"]
     check_batched(N, lib, ref, Q, ks, budgets, N.NRLSH_QUERY_TENSOR)
 
 
@@ -106,6 +108,8 @@ def test_large_budgets_batched(N, big):
     budgets = rng.choice([1, 500, 10_000, 60_000, 100_000, 200_000], 48).astype(np.int64)
     ks = rng.choice([1, 10, 100], 48).astype(np.int32)
     check_batched(N, lib, ref, Q, ks, budgets, N.NRLSH_QUERY_FP32)
+    check_batched(N, lib, ref, Q, ks, budgets, N.NRLSH_QUERY_BF16 | N.NRLSH_QUERY_NO_TUNE)
+    assert N.nrlsh_get_tuning(lib)["rows_bf16"]
     check_batched(N, lib, ref, Q, ks, budgets, N.NRLSH_QUERY_TENSOR)
 
 

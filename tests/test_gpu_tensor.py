@@ -200,3 +200,45 @@ def test_tc_batched_graph_replay_and_autotuned_choice(N):
     torch.cuda.synchronize()
     assert torch.equal(ids_f, ids) and torch.equal(sc_f, sc)
     assert not N.nrlsh_get_tuning(lib)["rerank_tensor"]
+
+
+def test_score_intervals_cover_worst_case_bf16_rounding(N):
+    """Round to nearest bf16 (an 8-bit significand) moves a value by up to 2^-8 of
+    itself.  Item 0's coordinates and the query's on them sit just below the
+    midpoint 1 + 2^-8 (both round down); item 1's and the query's on them just
+    above it (both round up), so the bf16 products err by about -2^-7 and +2^-7 in
+    opposite directions while item 0's exact score is the larger by 2^-13.  An
+    interval taken with 2^-9 per rounding puts item 0's entirely below item 1's
+    and drops the true top-1 before the exact rescoring; both bf16 paths (tensor
+    cores, and the FP32 re-rank over a bf16 copy of the rows) must return the
+    oracle's top-2."""
+    n, d = 1000, 129
+    a = np.float32(1 + 2**-8 - 2**-20)
+    b = np.float32(1 + 2**-8 + 2**-20)
+    X = np.random.default_rng(5).standard_normal((n, d)).astype(np.float32) * np.float32(1e-3)
+    X[0] = 0
+    X[0, :64] = a
+    X[0, 128] = np.float32(3 * 2**-13)
+    X[1] = 0
+    X[1, 64:128] = b
+    q = np.zeros((1, d), np.float32)
+    q[0, :64] = a
+    q[0, 64:128] = b
+    q[0, 128] = 1
+    lib, ref = build_pair(X, "f32", 4, 32, 9, 0.1)
+    rids, rsc = O.query(ref, q.astype(np.float64), 2, n)
+    assert rids[0].tolist() == [0, 1]
+    Qd = torch.from_numpy(q).cuda()
+    ks = torch.full((1,), 2, dtype=torch.int32, device="cuda")
+    bs = torch.full((1,), n, dtype=torch.int64, device="cuda")
+    runs = {"tensor": N.nrlsh_query_ex(lib, Qd, 2, n, flags=N.NRLSH_QUERY_TENSOR),
+            "fp32": N.nrlsh_query_ex(lib, Qd, 2, n)}
+    runs["bf16_rows"] = N.nrlsh_query_batched(lib, Qd, ks, bs, 2, n,
+                                              flags=N.NRLSH_QUERY_BF16 | N.NRLSH_QUERY_NO_TUNE)
+    assert N.nrlsh_get_tuning(lib)["rows_bf16"]
+    runs["tensor_batched"] = N.nrlsh_query_batched(lib, Qd, ks, bs, 2, n,
+                                                   flags=N.NRLSH_QUERY_TENSOR | N.NRLSH_QUERY_NO_TUNE)
+    torch.cuda.synchronize()
+    for name, (ids, sc) in runs.items():
+        assert ids.cpu().numpy().tolist() == rids.tolist(), name
+        assert np.array_equal(sc.cpu().numpy(), rsc), name
