@@ -19,11 +19,6 @@ namespace nrlsh {
 
 namespace {
 
-__device__ __forceinline__ float warp_sum(float v) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -691,6 +686,7 @@ __device__ void select_digit(const uint32_t* hist, int rem, int* dg_out, int* re
 
 constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
 constexpr int kDot2Max = 512;        // contenders scored by the compensated FP32 tier
+constexpr int kStageMax = kRescoreSmem / 8;   // bound lists staged in shared memory
 
 // Compensated dot products of two rows with the query at once (their loads in
 // flight together); row 1 may be null (then only row 0 is summed).
@@ -799,11 +795,11 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __shared__ uint16_t flagged[kDot2Max], flagged2[kDot2Max];
     __shared__ uint32_t nflag_s, nflag2_s;
     __shared__ uint32_t idc_s[kDot2Max];      // original ids of the contenders (compensated tier)
+    __shared__ uint32_t cpos_s[kDot2Max];     // their storage positions
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     // lists of up to kStageMax entries: both bounds read once into shared memory,
     // so the selection passes and the contender scan do not wait on L2 again
-    constexpr int kStageMax = kRescoreSmem / 8;
     const bool staged = count <= kStageMax;
     if (staged) {
         for (int64_t i = threadIdx.x; i < count; i += 256) {
@@ -845,7 +841,11 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     if (threadIdx.x == 0) nc_s = 0;
     __syncthreads();
     for (int64_t i = threadIdx.x; i < count; i += 256) {
-        if (hiv[i] >= tau) contq[atomicAdd(&nc_s, 1u)] = (uint32_t)i;
+        if (hiv[i] >= tau) {
+            const uint32_t slot = atomicAdd(&nc_s, 1u);
+            contq[slot] = (uint32_t)i;
+            if (slot < (uint32_t)kDot2Max) cpos_s[slot] = candq[i];
+        }
     }
     __syncthreads();
     const uint32_t nc = nc_s;
@@ -864,8 +864,12 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
         for (uint32_t c0 = warp; c0 < nc; c0 += 16) {
             const uint32_t c1 = c0 + 8;
             const bool two = c1 < nc;
-            const uint32_t pos0 = candq[contq[c0]];
-            const uint32_t pos1 = two ? candq[contq[c1]] : pos0;
+            const uint32_t pos0 = cpos_s[c0];
+            const uint32_t pos1 = two ? cpos_s[c1] : pos0;
+            // the lane's row norm and id, loaded while the rows are
+            const uint32_t posl = lane == 0 ? pos0 : pos1;
+            const float xnl = lane < 2 ? xnorm[posl] : 0.0f;
+            const uint32_t idl = lane < 2 ? perm[posl] : 0u;
             float sh[2] = {0.0f, 0.0f}, sl[2] = {0.0f, 0.0f};
             RowDot2<T>::dot(Xp + (int64_t)pos0 * dp, two ? Xp + (int64_t)pos1 * dp : nullptr, qs, dp,
                             lane, sh, sl);
@@ -883,15 +887,14 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
             }
             if (lane < 2 && (lane == 0 || two)) {
                 const uint32_t c = lane == 0 ? c0 : c1;
-                const uint32_t pos = lane == 0 ? pos0 : pos1;
                 const float vh = lane == 0 ? sh[0] : sh[1], vl = lane == 0 ? sl[0] : sl[1];
                 const double v = __dadd_rn((double)vh, (double)vl);
-                const double e = c2 * (double)qn * (double)xnorm[pos] * (1.0 + 0x1p-20) +
+                const double e = c2 * (double)qn * (double)xnl * (1.0 + 0x1p-20) +
                                  0x1p-52 * fabs(v) + 0x1p-120;
                 rank_lo[c] = __dsub_rd(v, e);
                 rank_hi[c] = __dadd_ru(v, e);
                 contsq[c] = v;
-                idc_s[c] = perm[pos];
+                idc_s[c] = idl;
             }
         }
         __syncthreads();
