@@ -33,8 +33,9 @@
  * Memory and streams.  Unless stated otherwise pointers may be device pointers
  * (any CUDA allocation of the current device, e.g. from PyTorch) or host
  * pointers.  Host inputs are copied into device memory before the call returns
- * (a build waits for that copy only and leaves its work queued); a call with a
- * host output synchronises its stream before returning.  With device pointers
+ * (a build, nrlsh_query_ex and nrlsh_query_batched wait for those copies only,
+ * queued ahead of the wait for the build, and leave their work queued); a call
+ * with a host output synchronises its stream before returning.  With device pointers
  * only, calls are asynchronous on `stream` (NULL = the legacy default stream);
  * a query call on another stream than the index's build makes its stream wait
  * for the end of the build (an event recorded by the build).  The caller
@@ -120,7 +121,13 @@ typedef struct nrlsh_build_options {
     int32_t projection;          /* nrlsh_projection */
     int32_t partition;           /* nrlsh_partition (0 = percentile) */
     void* stream;                /* cudaStream_t; NULL = legacy default stream */
+    uint32_t flags;              /* NRLSH_BUILD_* (0 = none) */
 } nrlsh_build_options;
+
+/* Build flag: host items are read by the build's stream in order, and the call
+ * returns without waiting for their copy.  The caller keeps the buffer unchanged
+ * until the stream has passed the build (an event recorded after the call). */
+#define NRLSH_BUILD_ASYNC_INPUT 0x1u
 
 typedef struct nrlsh_info {
     int64_t n;
@@ -156,9 +163,10 @@ NRLSH_API nrlsh_status nrlsh_build(const float* items, int64_t n, int32_t d, int
 NRLSH_API nrlsh_status nrlsh_build_ex(const void* items, int64_t n, int32_t d, int32_t m,
                                       int32_t L, uint64_t seed, nrlsh_dtype dtype, float eps,
                                       void* stream, nrlsh_index** out);
-/* As nrlsh_build_ex, with the projection path chosen by opts->projection and the
- * partition by opts->partition.  NRLSH_PROJECT_TENSOR on a device without tcgen05
- * returns NRLSH_ERR_UNSUPPORTED; an unknown partition returns NRLSH_ERR_ARG.
+/* As nrlsh_build_ex, with the projection path chosen by opts->projection, the
+ * partition by opts->partition and opts->flags (NRLSH_BUILD_ASYNC_INPUT).
+ * NRLSH_PROJECT_TENSOR on a device without tcgen05 returns NRLSH_ERR_UNSUPPORTED;
+ * an unknown partition or flag returns NRLSH_ERR_ARG.
  * Storage order is (sub-dataset, id) under either partition. */
 NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d, int32_t m,
                                         int32_t L, uint64_t seed, const nrlsh_build_options* opts,
@@ -173,7 +181,10 @@ NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d,
  *   scores        nq x k fp32: the matching inner products; -inf past the end
  *   flags         NRLSH_WHOLE_BUCKETS: the boundary bucket is probed whole;
  *                 NRLSH_QUERY_TENSOR: the probing and the re-rank run on tensor
- *                 cores (below); results are the same
+ *                 cores (below); results are the same;
+ *                 NRLSH_QUERY_ASYNC_INPUT: host queries are read by `stream` in
+ *                 order and the call does not wait for their copy (the caller
+ *                 keeps the buffer unchanged until the stream has passed the call)
  * nrlsh_query runs on the legacy default stream with no flags.
  *
  * The tensor-core path handles every (query, item) pair of a probed sub-dataset
@@ -187,6 +198,7 @@ NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d,
  * call's stream; make it before any stream capture.
  */
 #define NRLSH_QUERY_TENSOR 0x8u
+#define NRLSH_QUERY_ASYNC_INPUT 0x40u   /* also taken by nrlsh_query_batched (ks, budgets too) */
 NRLSH_API nrlsh_status nrlsh_query(const nrlsh_index* index, const float* queries, int64_t nq,
                                    int32_t k, int64_t probe_budget, int64_t* ids,
                                    float* scores);

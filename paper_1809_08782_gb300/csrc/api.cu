@@ -381,7 +381,7 @@ nrlsh_status stage_in(Scratch& sc, const void* src, size_t bytes, const void** d
 
 nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int32_t L,
                         uint64_t seed, nrlsh_dtype dtype, float eps, void* stream, int projection,
-                        int partition, nrlsh_index** out) {
+                        int partition, nrlsh_index** out, uint32_t build_flags = 0) {
     if (!out) return arg_error("out is NULL");
     *out = nullptr;
     if (!items) return arg_error("items is NULL");
@@ -661,7 +661,7 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
     B_CU(cudaEventRecord(ix->built, st));
     // the caller may reuse a host item buffer once its copy is done; the build
     // itself stays queued
-    if (host_items) B_CU(cudaEventSynchronize(t_staged));
+    if (host_items && !(build_flags & NRLSH_BUILD_ASYNC_INPUT)) B_CU(cudaEventSynchronize(t_staged));
 #undef B_CK
 #undef B_CU
     *out = ix;
@@ -1126,6 +1126,31 @@ nrlsh_status finish_out(cudaStream_t st, std::initializer_list<OutStage*> outs, 
     return NRLSH_OK;
 }
 
+// The copies of a call's host inputs, queued before the call waits for the build
+// (so they do not queue behind it): with device outputs the call returns once they
+// have landed, without waiting for its kernels.
+struct InputCopies {
+    cudaEvent_t ev = nullptr;
+    ~InputCopies() {
+        if (ev) cudaEventDestroy(ev);
+    }
+    nrlsh_status mark(cudaStream_t st, bool any_host, uint32_t flags) {
+        if (!any_host || (flags & NRLSH_QUERY_ASYNC_INPUT)) return NRLSH_OK;
+        NRLSH_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        NRLSH_CK(cudaEventRecord(ev, st));
+        return NRLSH_OK;
+    }
+};
+
+nrlsh_status finish_out(cudaStream_t st, std::initializer_list<OutStage*> outs,
+                        const InputCopies& in) {
+    bool host_out = false;
+    for (OutStage* o : outs) host_out = host_out || o->host;
+    if (host_out) return finish_out(st, outs, true);
+    if (in.ev) NRLSH_CK(cudaEventSynchronize(in.ev));
+    return NRLSH_OK;
+}
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -1149,8 +1174,9 @@ NRLSH_API nrlsh_status nrlsh_build_opts(const void* items, int64_t n, int32_t d,
                                         int32_t L, uint64_t seed, const nrlsh_build_options* opts,
                                         nrlsh_index** out) {
     if (!opts) return arg_error("opts is NULL");
+    if (opts->flags & ~NRLSH_BUILD_ASYNC_INPUT) return arg_error("unknown build flags");
     return build_impl(items, n, d, m, L, seed, (nrlsh_dtype)opts->dtype, opts->eps, opts->stream,
-                      opts->projection, opts->partition, out);
+                      opts->projection, opts->partition, out, opts->flags);
 }
 
 NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* queries, int64_t nq,
@@ -1159,7 +1185,8 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* querie
     NRLSH_CKS(check_query_args(ix, queries, nq));
     if (k < 1 || k > NRLSH_MAX_K) return arg_error("need 1 <= k <= 1024");
     if (probe_budget < 1) return arg_error("need probe_budget >= 1");
-    if (flags & ~(NRLSH_WHOLE_BUCKETS | NRLSH_QUERY_TENSOR)) return arg_error("unknown flags");
+    if (flags & ~(NRLSH_WHOLE_BUCKETS | NRLSH_QUERY_TENSOR | NRLSH_QUERY_ASYNC_INPUT))
+        return arg_error("unknown flags");
     if (nq > 0 && (!ids || !scores)) return arg_error("ids/scores is NULL");
     const bool tensor = (flags & NRLSH_QUERY_TENSOR) != 0;
     if (tensor && !tc_path_supported(ix)) {
@@ -1169,11 +1196,13 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* querie
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
-    NRLSH_CK(wait_for_build(ix, st));
-    if (tensor) NRLSH_CKS(tensor_query_prologue(ix, st));
     Scratch sc(st);
     const void* Qd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
+    InputCopies in;
+    NRLSH_CKS(in.mark(st, Qd != queries, flags));
+    NRLSH_CK(wait_for_build(ix, st));
+    if (tensor) NRLSH_CKS(tensor_query_prologue(ix, st));
     OutStage oi, os;
     QueryOut o;
     NRLSH_CKS(stage_out(sc, ids, (size_t)nq * k, oi, &o.ids));
@@ -1183,7 +1212,7 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* ix, const float* querie
         NRLSH_CKS(run_queries_tc(ix, (const float*)Qd, nq, k, probe_budget, flags, Stage::TopK, o, st));
     else
         NRLSH_CKS(run_queries(ix, (const float*)Qd, nq, k, probe_budget, flags, Stage::TopK, o, st));
-    return finish_out(st, {&oi, &os}, oi.host || os.host || Qd != queries);
+    return finish_out(st, {&oi, &os}, in);
 }
 
 NRLSH_API nrlsh_status nrlsh_query(const nrlsh_index* ix, const float* queries, int64_t nq,
@@ -1674,7 +1703,8 @@ nrlsh_status run_batched(const nrlsh_index* ix, const float* Q, int64_t nq, cons
 
 nrlsh_status check_batch_flags(uint32_t flags) {
     const uint32_t path = NRLSH_QUERY_TENSOR | NRLSH_QUERY_FP32 | NRLSH_QUERY_BF16;
-    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE | path)) return arg_error("unknown flags");
+    if (flags & ~(NRLSH_QUERY_GRAPH | NRLSH_QUERY_NO_TUNE | NRLSH_QUERY_ASYNC_INPUT | path))
+        return arg_error("unknown flags");
     const uint32_t p = flags & path;
     if (p & (p - 1))
         return arg_error("NRLSH_QUERY_TENSOR, NRLSH_QUERY_FP32 and NRLSH_QUERY_BF16 exclude each other");
@@ -1848,7 +1878,6 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     if (nq == 0) return NRLSH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     NRLSH_CK(cudaGetLastError());
-    NRLSH_CK(wait_for_build(ix, st));
     const int64_t cap = std::min<int64_t>(budget_max, ix->n);
     const bool graph = (flags & NRLSH_QUERY_GRAPH) && st != nullptr;
     if (graph && !(is_device_ptr(queries) && is_device_ptr(ks) && is_device_ptr(budgets) &&
@@ -1857,13 +1886,16 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) NRLSH_CK(cudaStreamIsCapturing(st, &cs));
     const bool capturing = cs != cudaStreamCaptureStatusNone;
-    // the bf16 paths' index operands exist before any tuning or capture
-    if (mode != 2 && tc_path_supported(ix)) NRLSH_CKS(ensure_tc_items(ix, st, capturing));
     Scratch sc(st);
     const void *Qd, *ksd, *bd;
     NRLSH_CKS(stage_in(sc, queries, sizeof(float) * nq * ix->d, &Qd));
     NRLSH_CKS(stage_in(sc, ks, sizeof(int32_t) * nq, &ksd));
     NRLSH_CKS(stage_in(sc, budgets, sizeof(int64_t) * nq, &bd));
+    InputCopies in;
+    NRLSH_CKS(in.mark(st, Qd != queries || ksd != ks || bd != budgets, flags));
+    NRLSH_CK(wait_for_build(ix, st));
+    // the bf16 paths' index operands exist before any tuning or capture
+    if (mode != 2 && tc_path_supported(ix)) NRLSH_CKS(ensure_tc_items(ix, st, capturing));
     OutStage oi, os;
     int64_t* idsd;
     float* scd;
@@ -1903,8 +1935,7 @@ extern "C" NRLSH_API nrlsh_status nrlsh_query_batched(const nrlsh_index* ix, con
         }
         NRLSH_CKS(run_batched(ix, (const float*)Qd, nq, (const int32_t*)ksd, (const int64_t*)bd,
                               k_max, cap, cfg, p, idsd, scd, st));
-        return finish_out(st, {&oi, &os}, oi.host || os.host || Qd != queries || ksd != ks ||
-                                              bd != budgets);
+        return finish_out(st, {&oi, &os}, in);
     }
     // graph mode: replay a captured sequence for identical calls
     std::lock_guard<std::mutex> g(ix->batch_mu);

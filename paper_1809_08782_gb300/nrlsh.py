@@ -26,6 +26,7 @@ NRLSH_QUERY_NO_TUNE = 0x4
 NRLSH_QUERY_TENSOR = 0x8
 NRLSH_QUERY_FP32 = 0x10
 NRLSH_QUERY_BF16 = 0x20
+NRLSH_QUERY_ASYNC_INPUT = 0x40
 
 _STATUS = {0: "NRLSH_OK", -1: "NRLSH_ERR_ARG", -2: "NRLSH_ERR_OOM", -3: "NRLSH_ERR_CUDA",
            -4: "NRLSH_ERR_TIMEOUT", -5: "NRLSH_ERR_UNSUPPORTED"}
@@ -74,7 +75,7 @@ class NrlshInfo(ctypes.Structure):
 
 class NrlshBuildOptions(ctypes.Structure):
     _fields_ = [("dtype", _I32), ("eps", _F32), ("projection", _I32), ("partition", _I32),
-                ("stream", _P)]
+                ("stream", _P), ("flags", ctypes.c_uint32)]
 
 
 NRLSH_PROJECT_AUTO = 0
@@ -82,6 +83,7 @@ NRLSH_PROJECT_SIMT = 1
 NRLSH_PROJECT_TENSOR = 2
 NRLSH_PARTITION_PERCENTILE = 0
 NRLSH_PARTITION_UNIFORM = 1
+NRLSH_BUILD_ASYNC_INPUT = 0x1
 
 
 class NrlshError(RuntimeError):
@@ -164,27 +166,35 @@ def _items_dtype(items: torch.Tensor) -> int:
 
 def nrlsh_build_ex(items: torch.Tensor, m: int, L: int, seed: int, eps: float = 0.1,
                    stream=None, projection: Optional[int] = None,
-                   partition: Optional[int] = None) -> Index:
+                   partition: Optional[int] = None, build_flags: int = 0) -> Index:
     """Index building (Algorithm 1).  items: (n, d) float32 or bfloat16, row-major.
-    projection selects the projection path and partition the split into
-    sub-datasets (nrlsh_build_opts) when either is given."""
+    projection selects the projection path, partition the split into sub-datasets
+    and build_flags the NRLSH_BUILD_* flags (nrlsh_build_opts) when any is given."""
     lib = load()
     if items.dim() != 2:
         raise ValueError("items must be 2-D (n, d)")
     items = items.contiguous()
     n, d = items.shape
     out = ctypes.c_void_p()
-    if projection is None and partition is None:
+    if projection is None and partition is None and not build_flags:
         _check(lib.nrlsh_build_ex(_ptr(items), n, d, m, L, seed, _items_dtype(items), eps,
                                   _stream(items, stream), ctypes.byref(out)))
     else:
         st = _stream(items, stream)
         opts = NrlshBuildOptions(_items_dtype(items), eps,
                                  NRLSH_PROJECT_AUTO if projection is None else projection,
-                                 NRLSH_PARTITION_PERCENTILE if partition is None else partition, st)
+                                 NRLSH_PARTITION_PERCENTILE if partition is None else partition, st,
+                                 build_flags)
         _check(lib.nrlsh_build_opts(_ptr(items), n, d, m, L, seed, ctypes.byref(opts),
                                     ctypes.byref(out)))
-    return Index(out, n, d, m, L, items.device)
+    return Index(out, n, d, m, L, _index_device(items))
+
+
+def _index_device(items: torch.Tensor) -> torch.device:
+    """The GPU an index lives on: the items' device, or for host items the current one."""
+    if items.is_cuda:
+        return items.device
+    return torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else items.device
 
 
 def nrlsh_build(items: torch.Tensor, m: int, L: int, seed: int) -> Index:
@@ -196,13 +206,20 @@ def nrlsh_build(items: torch.Tensor, m: int, L: int, seed: int) -> Index:
     n, d = items.shape
     out = ctypes.c_void_p()
     _check(lib.nrlsh_build(_ptr(items), n, d, m, L, seed, ctypes.byref(out)))
-    return Index(out, n, d, m, L, items.device)
+    return Index(out, n, d, m, L, _index_device(items))
 
 
 def _queries(index: Index, queries: torch.Tensor) -> torch.Tensor:
     if queries.dtype != torch.float32 or queries.dim() != 2 or queries.shape[1] != index.d:
         raise ValueError(f"queries must be float32 of shape (nq, {index.d})")
     return queries.contiguous()
+
+
+def _out_devices(index: "Index", queries: torch.Tensor) -> tuple:
+    """Where the outputs of a query call may live: host memory or the index's GPU
+    (the C ABI takes either for every argument)."""
+    dev = index.device if index.device.type == "cuda" else queries.device
+    return tuple({torch.device("cpu"), dev, queries.device})
 
 
 def _check_out(t: torch.Tensor, name: str, dtype: torch.dtype, shape: tuple, device):
@@ -217,8 +234,9 @@ def _check_out(t: torch.Tensor, name: str, dtype: torch.dtype, shape: tuple, dev
         raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
-    if t.device != device:
-        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    devices = device if isinstance(device, tuple) else (device,)
+    if t.device not in devices:
+        raise ValueError(f"{name} must be on one of {[str(x) for x in devices]}, got {t.device}")
 
 
 def nrlsh_query_ex(index: Index, queries: torch.Tensor, k: int, probe_budget: int,
@@ -231,11 +249,11 @@ def nrlsh_query_ex(index: Index, queries: torch.Tensor, k: int, probe_budget: in
     if ids is None:
         ids = torch.empty((nq, k), dtype=torch.int64, device=queries.device)
     else:
-        _check_out(ids, "ids", torch.int64, (nq, k), queries.device)
+        _check_out(ids, "ids", torch.int64, (nq, k), _out_devices(index, queries))
     if scores is None:
         scores = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
     else:
-        _check_out(scores, "scores", torch.float32, (nq, k), queries.device)
+        _check_out(scores, "scores", torch.float32, (nq, k), _out_devices(index, queries))
     lib = load()
     _check(lib.nrlsh_query_ex(index.handle, _ptr(queries), nq, k, probe_budget, flags,
                               _ptr(ids), _ptr(scores), _stream(queries, stream)))
@@ -289,11 +307,11 @@ def nrlsh_query_batched(index: Index, queries: torch.Tensor, ks: torch.Tensor,
     if ids is None:
         ids = torch.empty((nq, k_max), dtype=torch.int64, device=queries.device)
     else:
-        _check_out(ids, "ids", torch.int64, (nq, k_max), queries.device)
+        _check_out(ids, "ids", torch.int64, (nq, k_max), _out_devices(index, queries))
     if scores is None:
         scores = torch.empty((nq, k_max), dtype=torch.float32, device=queries.device)
     else:
-        _check_out(scores, "scores", torch.float32, (nq, k_max), queries.device)
+        _check_out(scores, "scores", torch.float32, (nq, k_max), _out_devices(index, queries))
     lib = load()
     _check(lib.nrlsh_query_batched(index.handle, _ptr(queries), nq, _ptr(ks), _ptr(budgets),
                                    k_max, budget_max, flags, _ptr(ids), _ptr(scores),

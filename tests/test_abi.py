@@ -90,11 +90,14 @@ def test_build_opts_rejects_unknown_partition_and_projection(lib):
     import paper_1809_08782_gb300.nrlsh as N
     buf = np.zeros(64, dtype=np.float32)
     for proj, part in ((0, 7), (0, -1), (9, 0)):
-        opts = N.NrlshBuildOptions(0, 0.1, proj, part, None)
+        opts = N.NrlshBuildOptions(0, 0.1, proj, part, None, 0)
         out = ctypes.c_void_p()
         st = lib.nrlsh_build_opts(buf.ctypes.data, 16, 4, 2, 8, 1, ctypes.byref(opts),
                                   ctypes.byref(out))
         assert st == -1 and out.value is None
+    opts = N.NrlshBuildOptions(0, 0.1, 0, 0, None, 0x2)     # an unknown build flag
+    assert lib.nrlsh_build_opts(buf.ctypes.data, 16, 4, 2, 8, 1, ctypes.byref(opts),
+                                ctypes.byref(out)) == -1
     assert lib.nrlsh_build_opts(buf.ctypes.data, 16, 4, 2, 8, 1, None, ctypes.byref(out)) == -1
 
 

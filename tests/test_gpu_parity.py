@@ -155,6 +155,49 @@ def test_host_buffers_and_streams():
     assert torch.equal(ids_s.cpu(), ids_h)
 
 
+def test_async_host_input_build_and_device_outputs_of_host_queries():
+    """NRLSH_BUILD_ASYNC_INPUT: the build returns with the pinned items' copy still
+    queued on its stream; host queries with device outputs return once the queries
+    have landed (with NRLSH_QUERY_ASYNC_INPUT, at once).  All give what the
+    synchronous calls give, on two streams."""
+    import paper_1809_08782_gb300.nrlsh as N
+    items = rand_items(3000, 40, 33)
+    Q = rand_q(16, 40, 34)
+    eps = f32(0.2)
+    ref = N.nrlsh_build_ex(torch.from_numpy(items).cuda(), 8, 32, 7, eps=eps)
+    ids_r, sc_r = N.nrlsh_query_ex(ref, torch.from_numpy(Q).cuda(), 10, 500)
+    torch.cuda.synchronize()
+    Xh = torch.from_numpy(items).pin_memory()
+    Qh = torch.from_numpy(Q).pin_memory()
+    sb, sq = torch.cuda.Stream(), torch.cuda.Stream()
+    ix = N.nrlsh_build_ex(Xh, 8, 32, 7, eps=eps, stream=sb, build_flags=N.NRLSH_BUILD_ASYNC_INPUT)
+    ids = torch.empty((16, 10), dtype=torch.int64, device="cuda")
+    sc = torch.empty((16, 10), dtype=torch.float32, device="cuda")
+    N.nrlsh_query_ex(ix, Qh, 10, 500, ids=ids, scores=sc, stream=sq)
+    sq.synchronize()
+    assert torch.equal(N.nrlsh_get_codes(ix), N.nrlsh_get_codes(ref))
+    assert torch.equal(ids, ids_r) and torch.equal(sc, sc_r)
+    ks = torch.full((16,), 10, dtype=torch.int32)
+    bs = torch.full((16,), 500, dtype=torch.int64)
+    ids_b = torch.empty((16, 10), dtype=torch.int64, device="cuda")
+    sc_b = torch.empty((16, 10), dtype=torch.float32, device="cuda")
+    N.nrlsh_query_batched(ix, Qh, ks, bs, 10, 500, ids=ids_b, scores=sc_b, stream=sq)
+    sq.synchronize()
+    assert torch.equal(ids_b, ids_r) and torch.equal(sc_b, sc_r)
+    # NRLSH_QUERY_ASYNC_INPUT: the queries' copy is left queued on the stream
+    ids_a = torch.empty_like(ids)
+    sc_a = torch.empty_like(sc)
+    N.nrlsh_query_ex(ix, Qh, 10, 500, flags=N.NRLSH_QUERY_ASYNC_INPUT, ids=ids_a, scores=sc_a,
+                     stream=sq)
+    ids_c = torch.empty_like(ids_b)
+    sc_c = torch.empty_like(sc_b)
+    N.nrlsh_query_batched(ix, Qh, ks, bs, 10, 500, flags=N.NRLSH_QUERY_ASYNC_INPUT, ids=ids_c,
+                          scores=sc_c, stream=sq)
+    sq.synchronize()
+    assert torch.equal(ids_a, ids_r) and torch.equal(sc_a, sc_r)
+    assert torch.equal(ids_c, ids_r) and torch.equal(sc_c, sc_r)
+
+
 def test_empty_query_batch_and_launch_count():
     import paper_1809_08782_gb300.nrlsh as N
     items = rand_items(100, 8, 1)
