@@ -822,6 +822,7 @@ struct TcWs {
     uint32_t* cont = nullptr;
     double* cont_s = nullptr;
     int* err = nullptr;           // the call's error word (copied into the index's at the end)
+    float* qce = nullptr;         // per-query score interval factors
     int64_t qc = 0;
     int64_t cap = 0;
 };
@@ -836,7 +837,7 @@ std::vector<size_t> tc_ws_sizes(const nrlsh_index* ix, int64_t qc, int64_t cap) 
     return {q * 4, 16, ambiguity_capacity(qc, ix->L) * 8, q * ix->code_bytes, q * Kq * 2, q * 128,
             q * ix->ncls * 4, q * ix->m, q * (ix->m + 1) * 4, q * sizeof(TcBoundary),
             q * sizeof(Boundary), nw, nw * 4, 16, q * c * 4, q * c * 4, q * c * 4, q * c * 4,
-            q * c * 8, 16};
+            q * c * 8, 16, q * 4};
 }
 
 size_t tc_ws_bytes(const nrlsh_index* ix, int64_t qc, int64_t cap) {
@@ -868,6 +869,7 @@ void tc_ws_assign(TcWs& w, const std::vector<void*>& p, const nrlsh_index* ix, i
     w.cont = (uint32_t*)p[17];
     w.cont_s = (double*)p[18];
     w.err = (int*)p[19];
+    w.qce = (float*)p[20];
     w.qc = qc;
     w.cap = cap;
 }
@@ -962,7 +964,7 @@ nrlsh_status run_tc_chunk(const nrlsh_index* ix, const float* Q, int64_t qc, con
     if (hist_tc) {
         NRLSH_CK(launch_pairs_tc(false, w.Qb, w.Qs, qc, ix->tc_xb, ix->tc_xs, ix->n, ix->d, ix->dp,
                                  ix->m, ix->L, ix->seg, nullptr, nullptr, H, nullptr, nullptr,
-                                 nullptr, nullptr, nullptr, 0.0f, nullptr, nullptr, nullptr, 0,
+                                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
                                  w.err, w.nlist + 2, st, test_spin_first()));
     } else {
         if (!ix->tiles_exclusive)
@@ -976,10 +978,10 @@ nrlsh_status run_tc_chunk(const nrlsh_index* ix, const float* Q, int64_t qc, con
                             flags, ix->codes, w.qcodes, ix->code_bytes, w.lam, w.off, w.tb, w.bnd,
                             w.flag, nqt, w.err, st));
     NRLSH_CK(launch_work_list(w.flag, ix->m * nqt, w.list, w.nlist, st));
-    const float c_tc = tc_score_bound(ix->d, ix->dtype == NRLSH_F32);
+    NRLSH_CK(launch_query_bounds(Q, qc, ix->d, w.qnorm, ix->dtype == NRLSH_F32, w.qce, st));
     NRLSH_CK(launch_pairs_tc(true, w.Qb, w.Qs, qc, ix->tc_xb, ix->tc_xs, ix->n, ix->d, ix->dp,
                              ix->m, ix->L, ix->seg, w.list, w.nlist, nullptr, w.lam, w.off, w.tb,
-                             ix->xnorm, w.qnorm, c_tc, w.cand, w.lo, w.hi, w.cap, w.err,
+                             ix->xnorm, w.qce, w.cand, w.lo, w.hi, w.cap, w.err,
                              w.nlist + 1, st, test_spin_first()));
     // the last kernel skips its work when the call's error word is set and
     // copies that word into the index's

@@ -336,8 +336,10 @@ struct TcBoundary {
 bool tc_query_supported(int d, int L);
 // 64-element K chunks of a row of d values.
 int tc_query_k_chunks(int d);
-// c_tc: |score_tc - score_fp64| <= c_tc ||q|| ||x|| for the bf16 tensor-core scores.
-float tc_score_bound(int d, bool fp32_items);
+// qce[q] = a_q with |score_tc - score_fp64| <= a_q ||x|| for the bf16 tensor-core
+// scores of query q (qnorm: the queries' norm bounds).
+cudaError_t launch_query_bounds(const float* Q, int64_t nq, int d, const float* qnorm,
+                                bool fp32_items, float* qce, cudaStream_t st);
 // Qb (nq x 64 tc_query_k_chunks(d) bf16) and Qs (nq x 64 bf16 +-1 signs of the codes).
 // Also clears the call's error word *err (the tensor-path kernels' timeouts) and
 // the histogram kernel's work counter *hist_ctr.
@@ -359,7 +361,7 @@ cudaError_t launch_pairs_tc(bool rerank, const __nv_bfloat16* Qb, const __nv_bfl
                             int64_t n, int d, int dp, int m, int L, const int64_t* seg,
                             const uint32_t* list, const uint32_t* nlist, uint32_t* H,
                             const uint8_t* lam, const uint32_t* off, const TcBoundary* tb,
-                            const float* xnorm, const float* qnorm, float c_tc, uint32_t* cand,
+                            const float* xnorm, const float* qce, uint32_t* cand,
                             float* lo, float* hi, int64_t cap, int* err, uint32_t* work_ctr,
                             cudaStream_t st, uint32_t spin_first = 1u << 22);
 // Bucket walk of every query (budgets per query or one budget, clamped to [1, cap]),

@@ -686,7 +686,6 @@ __device__ void select_digit(const uint32_t* hist, int rem, int* dg_out, int* re
 
 constexpr int kRescoreSmem = 16384;  // bytes of staged contender rows
 constexpr int kDot2Max = 512;        // contenders scored by the compensated FP32 tier
-constexpr int kStageMax = kRescoreSmem / 8;   // bound lists staged in shared memory
 
 // Compensated dot products of two rows with the query at once (their loads in
 // flight together); row 1 may be null (then only row 0 is summed).
@@ -798,19 +797,6 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __shared__ uint32_t cpos_s[kDot2Max];     // their storage positions
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // lists of up to kStageMax entries: both bounds read once into shared memory,
-    // so the selection passes and the contender scan do not wait on L2 again
-    const bool staged = count <= kStageMax;
-    if (staged) {
-        for (int64_t i = threadIdx.x; i < count; i += 256) {
-            rows_s[i] = loq[i];
-            rows_s[kStageMax + i] = hiq[i];
-        }
-        __syncthreads();
-    }
-    const float* lov = staged ? rows_s : loq;
-    const float* hiv = staged ? rows_s + kStageMax : hiq;
-
     float tau = -FLT_MAX;
     if (count > kq) {
         if (threadIdx.x == 0) {
@@ -824,7 +810,7 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
             const uint32_t prefix = prefix_s, mask = mask_s;
             const int rem = rem_s;
             for (int64_t i = threadIdx.x; i < count; i += 256) {
-                const uint32_t key = float_order(lov[i]);
+                const uint32_t key = float_order(loq[i]);
                 if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 0xFFu], 1u);
             }
             __syncthreads();
@@ -841,7 +827,7 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     if (threadIdx.x == 0) nc_s = 0;
     __syncthreads();
     for (int64_t i = threadIdx.x; i < count; i += 256) {
-        if (hiv[i] >= tau) {
+        if (hiq[i] >= tau) {
             const uint32_t slot = atomicAdd(&nc_s, 1u);
             contq[slot] = (uint32_t)i;
             if (slot < (uint32_t)kDot2Max) cpos_s[slot] = candq[i];
@@ -852,8 +838,8 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     const int rb = max(1, min(256, kRescoreSmem / (int)(sizeof(float) * dp)));
     if (nc <= (uint32_t)kDot2Max) {
         // Compensated FP32 tier (Ogita, Rump, Oishi, "Accurate sum and dot product",
-        // 2005): a warp per contender, TwoProduct by fma and TwoSum per lane, the
-        // same transformations across lanes.  With m terms per lane (mlane) and 5
+        // 2005): a warp per two contenders, TwoProduct by fma and TwoSum per lane,
+        // the same transformations across lanes.  With m terms per lane (mlane) and 5
         // tree levels, |hi + lo - q^T x| <= u^2 (2m(m+1) + 10(dp+32)) sum|q x|,
         // u = 2^-24; the bound below takes 4x that, plus the FP64 rounding of the
         // canonical in-order sum ((d+2) 2^-53 sum|q x|) and of hi + lo.

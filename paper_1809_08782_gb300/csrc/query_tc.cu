@@ -10,7 +10,8 @@
 //                 l is exact: the same number as L - popcount(c_q xor c_x).
 //   scores        q~ . x~ with q~ = q rounded to bf16 and x~ the bf16 items
 //                 (fp32 items: rounded to bf16), FP32 accumulation; the interval
-//                 [s - e, s + e], e = c_tc ||q|| ||x||, holds the FP64 score.
+//                 [s - e, s + e], e = a_q ||x|| (a_q from the query's own bf16
+//                 rounding error, query_bound_kernel), holds the FP64 score.
 //
 // Two epilogues share the kernel:
 //   HIST     H[q][j][l] += 1 for every pair (private shared-memory counters per
@@ -66,8 +67,7 @@ struct PairsArgs {
     const uint32_t* off;        // nq x (m + 1) list offsets
     const TcBoundary* tb;       // nq
     const float* xnorm;         // n, storage order
-    const float* qnorm;         // nq
-    float c_tc;
+    const float* qce;           // nq: a_q of the score interval
     uint32_t* cand;             // nq x cap
     float* lo;
     float* hi;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 base_j = (int32_t)a.off[q * (a.m + 1) + j];
                 cnt_j = (int32_t)(a.off[q * (a.m + 1) + j + 1] - (uint32_t)base_j);
                 slot = half == 0 ? base_j : base_j + cnt_j - 1;
-                ce = __fmul_ru(a.c_tc, a.qnorm[q]);
+                ce = a.qce[q];
             }
             bool overflow = false;
             const uint32_t hist_k = smem_u32(hist) + 4u * (uint32_t)(half * kPM + row) +
@@ -708,21 +708,51 @@ bool tc_query_supported(int d, int L) {
     return pairs_smem_bytes(true, nkc, L, 2) <= 225 * 1024;
 }
 
-float tc_score_bound(int d, bool fp32_items) {
-    // operand rounding: q~ = q (1 + d1), x~ = x (1 + d2), |d1| <= 2^-8 (round to
-    // nearest bf16: an 8-bit significand), |d2| <= 2^-8 for fp32 items, 0 for bf16
-    // items; accumulation of
-    // K products within 16x the first-order FP32 bound, (K + 8) 2^-20; and the
-    // canonical FP64 in-order sum's own (d + 2) 2^-53 -- all relative to
-    // sum |q_k x_k| <= ||q|| ||x||.
-    const double K = 16.0 * (double)ceil_div(d, 16);
-    const double rq = 0x1p-8, rx = fp32_items ? 0x1p-8 : 0.0;
-    const double grow = (1.0 + rq) * (1.0 + rx);
-    const double kappa = (K + 8.0) * 0x1p-20;
-    const double c = ((grow - 1.0) + kappa * grow + (d + 2.0) * 0x1p-53) * (1.0 + 0x1p-20);
-    float f = (float)c;
-    if ((double)f < c) f = nextafterf(f, 1.0f);
-    return f;
+// a_q of every query (a warp per query): with q~ = bf16(q), dq = q - q~ (exact in
+// fp32 by Sterbenz's lemma) and x~ the bf16 items (x~ = x for bf16 items, else
+// |x - x~| <= 2^-8 |x| elementwise: an 8-bit significand rounded to nearest),
+//   |q.x - q~.x~| <= ||dq|| ||x|| + ||q~|| ||x - x~||,
+//   the FP32 accumulation of the K (16-padded) products within (K + 8) 2^-20
+//   ||q~|| ||x~|| (16x the first-order bound), and the canonical FP64 in-order
+//   sum within (d + 2) 2^-53 ||q|| ||x||,
+// with ||q~|| <= ||q|| + ||dq|| and ||x~|| <= (1 + rx) ||x||.  So e = a_q ||x||,
+//   a_q = D + rx (Q + D) + (K + 8) 2^-20 (Q + D)(1 + rx) + (d + 2) 2^-53 Q,
+// Q >= ||q|| the query norm bound, D >= ||dq|| (FP64 sum of the exact squares,
+// enlarged by its own rounding), every step rounded up, times (1 + 2^-20).
+__global__ void query_bound_kernel(const float* __restrict__ Q, int64_t nq, int d,
+                                   const float* __restrict__ qnorm, int fp32_items,
+                                   float* __restrict__ qce) {
+    NRLSH_PDL_ENTRY();
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    double ss = 0.0;
+    for (int k = lane; k < d; k += 32) {
+        const float v = Q[q * d + k];
+        const float r = v - __bfloat162float(__float2bfloat16_rn(v));
+        ss = fma((double)r, (double)r, ss);
+    }
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) {
+        const double D = __dsqrt_ru(__dmul_ru(ss, 1.0 + (d + 40) * 0x1p-52));
+        const double Qn = (double)qnorm[q];
+        const double rx = fp32_items ? 0x1p-8 : 0.0;
+        const double K = 16.0 * (double)ceil_div(d, 16);
+        const double QD = __dadd_ru(Qn, D);
+        double t = __dmul_ru(__dmul_ru((K + 8.0) * 0x1p-20, QD), 1.0 + rx);
+        t = __dadd_ru(t, __dmul_ru(rx, QD));
+        t = __dadd_ru(t, D);
+        t = __dadd_ru(t, __dmul_ru((d + 2.0) * 0x1p-53, Qn));
+        qce[q] = __double2float_ru(__dmul_ru(t, 1.0 + 0x1p-20));
+    }
+}
+
+cudaError_t launch_query_bounds(const float* Q, int64_t nq, int d, const float* qnorm,
+                                bool fp32_items, float* qce, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)ceil_div(nq * 32, (int64_t)256);
+    return launch("query_bounds", query_bound_kernel, dim3(grid), dim3(256), 0, st, Q, nq, d, qnorm,
+                  fp32_items ? 1 : 0, qce);
 }
 
 cudaError_t launch_prep_queries(const float* Q, int64_t nq, int d, int Kq, const void* qcodes,
@@ -765,7 +795,7 @@ cudaError_t launch_pairs_tc(bool rerank, const __nv_bfloat16* Qb, const __nv_bfl
                             int64_t n, int d, int dp, int m, int L, const int64_t* seg,
                             const uint32_t* list, const uint32_t* nlist, uint32_t* H,
                             const uint8_t* lam, const uint32_t* off, const TcBoundary* tb,
-                            const float* xnorm, const float* qnorm, float c_tc, uint32_t* cand,
+                            const float* xnorm, const float* qce, uint32_t* cand,
                             float* lo, float* hi, int64_t cap, int* err, uint32_t* work_ctr,
                             cudaStream_t st, uint32_t spin_first) {
     if (nq <= 0) return cudaSuccess;
@@ -800,8 +830,7 @@ cudaError_t launch_pairs_tc(bool rerank, const __nv_bfloat16* Qb, const __nv_bfl
     a.off = off;
     a.tb = tb;
     a.xnorm = xnorm;
-    a.qnorm = qnorm;
-    a.c_tc = c_tc;
+    a.qce = qce;
     a.cand = cand;
     a.lo = lo;
     a.hi = hi;

@@ -108,3 +108,60 @@ def test_compensated_tier_is_much_tighter_than_fp32():
     e32 = np.abs(plain.astype(np.float64) - S)
     e2 = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - S)
     assert np.median(e2[e32 > 0] / e32[e32 > 0]) < 1e-4
+
+
+def _bf16(v):
+    """Round float32 to bfloat16 (nearest, ties to even), back as float32."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=F)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def _tc_factor(q, d, fp32_items):
+    """a_q of the tensor-core score interval e = a_q ||x|| (query_bound_kernel):
+    D = ||q - bf16(q)||, Q = ||q||, rx = 2^-8 for fp32 items entered as bf16."""
+    D = math.sqrt(math.fsum(float(r) ** 2 for r in (q - _bf16(q)).astype(np.float64)))
+    Q = math.sqrt(math.fsum(float(v) ** 2 for v in q.astype(np.float64)))
+    rx = 2.0 ** -8 if fp32_items else 0.0
+    K = 16 * -(-d // 16)
+    return (D + rx * (Q + D) + (K + 8) * 2.0 ** -20 * (Q + D) * (1 + rx) + (d + 2) * 2.0 ** -53 * Q) * (1 + 2.0 ** -20)
+
+
+def test_tensor_core_score_interval_bound():
+    """bf16 operands (query always, items when stored as fp32) and FP32 accumulation,
+    emulated in two orders (sequential, and 16-wide partial sums as the K = 16 MMA
+    steps add them): the FP64 score lies within a_q ||x||.  Random, cancelling and
+    worst-case rounding inputs (every coordinate just below or above a bf16
+    rounding midpoint, so the two roundings err by up to 2^-8 each, aligned)."""
+    rng = np.random.default_rng(11)
+    for d in (7, 64, 129, 300):
+        q = rng.standard_normal((60, d)).astype(F)
+        x = rng.standard_normal((60, d)).astype(F)
+        # worst case: q and x just below the midpoint 1 + 2^-8 (both round down)
+        q[:10] = F(1 + 2 ** -8 - 2 ** -20)
+        x[:10] = F(1 + 2 ** -8 - 2 ** -20)
+        # cancellation: x orthogonal to q in float64
+        x[10:20] -= (np.sum(x[10:20] * q[10:20], 1) / np.sum(q[10:20] ** 2, 1))[:, None] * q[10:20]
+        for fp32_items in (True, False):
+            xs = x if fp32_items else _bf16(x)
+            qt, xt = _bf16(q), _bf16(xs)
+            S = exact(q, xs)
+            prods = (qt.astype(np.float64) * xt.astype(np.float64)).astype(F)   # exact in fp32
+            seq = np.zeros(q.shape[0], F)
+            for k in range(d):
+                seq = (seq + prods[:, k]).astype(F)
+            chunk = np.zeros(q.shape[0], F)
+            for k0 in range(0, d, 16):
+                part = np.zeros(q.shape[0], F)
+                for k in range(k0, min(d, k0 + 16)):
+                    part = (part + prods[:, k]).astype(F)
+                chunk = (chunk + part).astype(F)
+            xn = np.sqrt(np.sum(xs.astype(np.float64) ** 2, 1))
+            for s in (seq, chunk):
+                err = np.abs(s.astype(np.float64) - S)
+                bound = np.array([_tc_factor(q[i], d, fp32_items) for i in range(q.shape[0])]) * xn
+                assert np.all(err <= bound), (d, fp32_items, float(np.max(err / bound)))
+            if fp32_items:
+                # 2^-9 per rounding (half the unit roundoff) does not hold here
+                Qn = np.sqrt(np.sum(q.astype(np.float64) ** 2, 1))
+                half = ((1 + 2.0 ** -9) ** 2 - 1) * Qn * xn
+                assert np.any(np.abs(seq.astype(np.float64) - S) > half)
