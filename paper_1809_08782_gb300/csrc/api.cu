@@ -885,10 +885,21 @@ nrlsh_status tc_ws_scratch(Scratch& sc, TcWs& w, const nrlsh_index* ix, int64_t 
     return NRLSH_OK;
 }
 
-// Queries per chunk of the tensor-core path: the chunk's workspace within 8 GiB.
+// Queries per chunk of the tensor-core path: the chunk's workspace within an eighth
+// of the device's memory, at most 32 GiB (a fixed function of the device, so that
+// the workspace a call sizes and the chunks it runs always agree).  Fewer, larger
+// chunks leave less of each kernel's last wave idle.
 int64_t tc_chunk(const nrlsh_index* ix, int64_t nq, int64_t cap) {
+    static const int64_t budget = [] {
+        size_t fr = 0, total = 0;
+        if (cudaMemGetInfo(&fr, &total) != cudaSuccess) {
+            cudaGetLastError();
+            total = (size_t)64 << 30;
+        }
+        return std::max<int64_t>((int64_t)1 << 30, std::min<int64_t>((int64_t)32 << 30, (int64_t)(total / 8)));
+    }();
     const int64_t per = (int64_t)tc_ws_bytes(ix, 128, cap) / 128 + 1;
-    int64_t c = std::max<int64_t>(128, ((int64_t)8 << 30) / per);
+    int64_t c = std::max<int64_t>(128, budget / per);
     return std::min<int64_t>(c, std::max<int64_t>(nq, 1));
 }
 
