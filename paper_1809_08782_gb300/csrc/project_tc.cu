@@ -29,8 +29,13 @@ namespace {
 
 constexpr int kTcM = 128;            // items per tile (MMA M)
 constexpr int kTcKC = 64;            // K elements per stage: 128 bytes of bf16
-constexpr int kTcStagesOne = 4;  // stages of one 16 KB tile
-constexpr int kTcStagesTwo = 3;  // stages of two 16 KB tiles (split fp32 items)
+constexpr int kTcMaxStages = 8;
+constexpr int kAmbWarp = 64;         // undecided (item, bit) entries buffered per epilogue warp
+
+__device__ __forceinline__ void set_code_bit(uint32_t* w, int bit) { atomicOr(w, 1u << bit); }
+__device__ __forceinline__ void set_code_bit(uint64_t* w, int bit) {
+    atomicOr((unsigned long long*)w, 1ull << bit);
+}  // ring stages (each one or, for split fp32 items, two 16 KB tiles)
 constexpr int kTcThreads = 192;
 constexpr uint32_t kTmemCols = 128;  // two accumulators of up to 64 fp32 columns
 constexpr uint32_t kXStageBytes = kTcM * kTcKC * 2;
@@ -59,11 +64,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                       const void* __restrict__ X_exact, int fp32_items, int ldx,
                       const double* __restrict__ tau64, C* __restrict__ codes,
                       unsigned long long* __restrict__ amb_list, unsigned* amb_count,
-                      unsigned amb_cap, int* err, uint32_t spin_first) {
+                      unsigned amb_cap, int* err, uint32_t spin_first, int kTcStages) {
     NRLSH_PDL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int kTcStages = split == 2 ? kTcStagesTwo : kTcStagesOne;
     const TcSmem L_{nkc, N, split, kTcStages};
     const uint32_t stage_bytes = (uint32_t)split * kXStageBytes;
     uint64_t* bars = L_.bars(base);
@@ -78,6 +82,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float* s_c1 = (float*)(tmem_slot + 4);       // 64: (kappa_tc + round_x) ||a_b||
     float* s_c2 = s_c1 + 64;                     // 64: 2^-20 |a_{d,b}|
     float* s_ad = s_c2 + 64;                     // 64: a_{d,b}
+    unsigned long long* amb_s = (unsigned long long*)(s_ad + 64);   // 4 x kAmbWarp entries
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = ceil_div(n, kTcM);
@@ -117,8 +122,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int c = 0; c < nkc; ++c) tma_load_2d(L_.a_tile(base, c), &map_a, a_bar, c * kTcKC, 0);
             int stage = 0;
             uint32_t phase = 0;
-            int issued[kTcStagesOne] = {0, 0, 0, 0};
-            uint32_t issued_par[kTcStagesOne] = {0, 0, 0, 0};
+            int issued[kTcMaxStages] = {0, 0, 0, 0, 0, 0, 0, 0};
+            uint32_t issued_par[kTcMaxStages] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int64_t t = blockIdx.x; t < ntiles && !*abort_s; t += gridDim.x) {
                 for (int c = 0; c < nkc; ++c) {
                     if (!mbar_wait(&empty[stage], phase ^ 1)) {
@@ -205,25 +210,79 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int sub = warp & 3;
         int buf = 0;
         uint32_t acc_phase = 0;
+        // the row's norm bound and tau of the next tile are loaded while this
+        // tile's accumulator is awaited
+        auto row_of = [&](int64_t t) { return t * kTcM + 32 * sub + lane; };
+        // the canonical FP64 form of one (row, bit), for entries the list has no room for
+        auto canonical = [&](int64_t r, int bit) {
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k) {
+                const double xk = fp32_items ? (double)((const float*)X_exact)[r * ldx + k]
+                                             : (double)__bfloat162float(
+                                                   ((const __nv_bfloat16*)X_exact)[r * ldx + k]);
+                acc = fma(xk, (double)A_pad[(int64_t)k * Lp + bit], acc);
+            }
+            acc = __dadd_rn(acc, __dmul_rn((double)s_ad[bit], tau64[r]));
+            return acc >= 0.0;
+        };
+        unsigned long long* wbuf = amb_s + (warp - 2) * kAmbWarp;
+        unsigned wn = 0;   // entries in this warp's buffer (uniform in the warp)
+        auto flush = [&]() {
+            __syncwarp();
+            if (wn == 0) return;
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(amb_count, wn);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (unsigned i = lane; i < wn; i += 32) {
+                const unsigned long long e = wbuf[i];
+                if (base + i < amb_cap) {
+                    amb_list[base + i] = e;
+                } else {
+                    const int64_t r = (int64_t)(e >> 6);
+                    const int bit = (int)(e & 63);
+                    if (canonical(r, bit)) set_code_bit(codes + r, bit);
+                }
+            }
+            wn = 0;
+            __syncwarp();
+        };
+        float xn_next = 0.0f, t32_next = 0.0f;
+        if ((int64_t)blockIdx.x < ntiles && row_of(blockIdx.x) < n) {
+            xn_next = xnorm[row_of(blockIdx.x)];
+            t32_next = tau32[row_of(blockIdx.x)];
+        }
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const float xn = xn_next, t32 = t32_next;
+            const int64_t tn = t + gridDim.x;
+            if (tn < ntiles && row_of(tn) < n) {
+                xn_next = xnorm[row_of(tn)];
+                t32_next = tau32[row_of(tn)];
+            }
             if (*abort_s || !mbar_wait(&acc_full[buf], acc_phase)) {
                 atomicExch(err, 3);
                 *abort_s = 1;
                 break;
             }
             fence_after();
-            const int64_t row = t * kTcM + 32 * sub + lane;
+            const int64_t row = row_of(t);
             const bool valid = row < n;
-            const float xn = valid ? xnorm[row] : 0.0f;
-            const float t32 = valid ? tau32[row] : 0.0f;
             unsigned long long word = 0, undecided = 0;
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem_base + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 64 + c0), r);
+            // all of the row's columns in flight at once (up to 64), then one wait
+            uint32_t r2[2][32];
+            const uint32_t taddr = tmem_base + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 64);
+            tmem_ld32_nowait(taddr, r2[0]);
+            if (N > 32) tmem_ld32_nowait(taddr + 32, r2[1]);
+            tmem_wait_ld();
+            // the accumulator is in registers: the MMA may overwrite it now
+            fence_before();
+            mbar_arrive(&acc_empty[buf]);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int bit = c0 + i;
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int bit = 32 * h + i;
                     if (!valid || bit >= L) continue;
+                    const uint32_t* r = r2[h];
                     const float v = fmaf(s_ad[bit], t32, __uint_as_float(r[i]));
                     // accumulation bound (kappa_tc) plus, for fp32 items, the bf16
                     // rounding of x (round_x); Cauchy-Schwarz for sum |a_k x_k|
@@ -235,45 +294,48 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                 }
             }
-            // one list reservation per warp
+            // undecided pairs go to this warp's buffer in shared memory, flushed to
+            // the global list (one reservation per flush) when it would overflow;
+            // a flush only touches rows of earlier tiles, already stored
             const unsigned cnt = (unsigned)__popcll(undecided);
             unsigned incl = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += v;
             }
-            unsigned wbase = 0;
-            if (lane == 31 && incl) wbase = atomicAdd(amb_count, incl);
-            wbase = __shfl_sync(0xffffffffu, wbase, 31);
-            unsigned slot = wbase + incl - cnt;
-            while (undecided) {
-                const int bit = __ffsll((long long)undecided) - 1;
-                undecided &= undecided - 1;
-                if (slot < amb_cap) {
-                    amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
-                } else {
-                    // list full: the canonical FP64 evaluation, here
-                    double acc = 0.0;
-                    for (int k = 0; k < d; ++k) {
-                        const double xk =
-                            fp32_items ? (double)((const float*)X_exact)[row * ldx + k]
-                                       : (double)__bfloat162float(
-                                             ((const __nv_bfloat16*)X_exact)[row * ldx + k]);
-                        acc = fma(xk, (double)A_pad[(int64_t)k * Lp + bit], acc);
-                    }
-                    acc = __dadd_rn(acc, __dmul_rn((double)s_ad[bit], tau64[row]));
-                    if (acc >= 0.0) word |= 1ull << bit;
+            const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
+            if (tot > 0 && wn + tot > (unsigned)kAmbWarp) flush();
+            if (tot <= (unsigned)kAmbWarp) {
+                unsigned pos = wn + incl - cnt;
+                while (undecided) {
+                    const int bit = __ffsll((long long)undecided) - 1;
+                    undecided &= undecided - 1;
+                    wbuf[pos++] = ((unsigned long long)row << 6) | (unsigned)bit;
                 }
-                ++slot;
+                wn += tot;
+            } else {
+                // more than a buffer in one tile: straight to the global list
+                unsigned wbase = 0;
+                if (lane == 31) wbase = atomicAdd(amb_count, tot);
+                wbase = __shfl_sync(0xffffffffu, wbase, 31);
+                unsigned slot = wbase + incl - cnt;
+                while (undecided) {
+                    const int bit = __ffsll((long long)undecided) - 1;
+                    undecided &= undecided - 1;
+                    if (slot < amb_cap)
+                        amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
+                    else if (canonical(row, bit))
+                        word |= 1ull << bit;
+                    ++slot;
+                }
             }
-            fence_before();
-            mbar_arrive(&acc_empty[buf]);
             if (valid) codes[row] = (C)word;
             if (++buf == 2) {
                 buf = 0;
                 acc_phase ^= 1;
             }
         }
+        flush();
     }
     fence_before();
     __syncthreads();
@@ -313,10 +375,27 @@ bool make_map_bf16(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t out
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t project_tc_smem_bytes(int d, int N, int split) {
+size_t project_tc_smem_bytes(int d, int N, int split, int stages) {
     const int nkc = (int)ceil_div(d, kTcKC);
-    const int stages = split == 2 ? kTcStagesTwo : kTcStagesOne;
-    return 1024 + (size_t)nkc * N * 128 + (size_t)stages * split * kXStageBytes + 256 + 3 * 64 * 4;
+    return 1024 + (size_t)nkc * N * 128 + (size_t)stages * split * kXStageBytes + 256 + 3 * 64 * 4 +
+           4 * kAmbWarp * 8;
+}
+
+// With more tiles than SMs, the deepest ring (at most kTcMaxStages) that keeps two
+// CTAs on an SM (two epilogues per SM); else, or if none does, the deepest that fits
+// one.  0 if not even two stages fit.
+int project_tc_stages(int d, int N, int split, bool two_per_sm, int* per_sm) {
+    for (int s = kTcMaxStages; two_per_sm && s >= 2; --s)
+        if (2 * project_tc_smem_bytes(d, N, split, s) <= 227 * 1024) {
+            *per_sm = 2;
+            return s;
+        }
+    for (int s = kTcMaxStages; s >= 2; --s)
+        if (project_tc_smem_bytes(d, N, split, s) <= 220 * 1024) {
+            *per_sm = 1;
+            return s;
+        }
+    return 0;
 }
 
 bool project_tc_supported(int d, int L) {
@@ -327,7 +406,8 @@ bool project_tc_supported(int d, int L) {
     cudaGetLastError();
     if (major != 10) return false;
     const int N = L <= 16 ? 16 : L <= 32 ? 32 : L <= 48 ? 48 : 64;
-    return project_tc_smem_bytes(d, N, 2) <= 220 * 1024 && tensor_map_encoder() != nullptr;
+    int per_sm = 0;
+    return project_tc_stages(d, N, 2, false, &per_sm) > 0 && tensor_map_encoder() != nullptr;
 }
 
 cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2, const void* X_exact,
@@ -345,12 +425,14 @@ cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2,
         !make_map_bf16(&map_x2, Xb2 ? Xb2 : Xb, (uint64_t)d, (uint64_t)n, (uint64_t)dp, kTcM) ||
         !make_map_bf16(&map_a, At, (uint64_t)d, (uint64_t)N, (uint64_t)dp, (uint32_t)N))
         return cudaErrorNotSupported;
-    const size_t smem = project_tc_smem_bytes(d, N, split);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = ceil_div(n, kTcM);
-    const int per_sm = smem * 2 <= 227 * 1024 ? 2 : 1;
+    int per_sm = 1;
+    const int stages = project_tc_stages(d, N, split, ntiles > sms, &per_sm);
+    if (stages == 0) return cudaErrorNotSupported;
+    const size_t smem = project_tc_smem_bytes(d, N, split, stages);
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
     // accumulation bound: 16x the first-order FP32 bound (the adder's rounding mode
     // inside the tensor core is not assumed).  fp32 items enter as x = hi + lo + r
@@ -366,7 +448,7 @@ cudaError_t launch_project_tc(const __nv_bfloat16* Xb, const __nv_bfloat16* Xb2,
         return launch("project_tc", kern, dim3(grid), dim3(kTcThreads), smem, st, map_x, map_x2, \
                       map_a, split, n, nkc, L, N, Lp, d, A_pad, anorm, tau32, xnorm, kappa_tc, \
                       round_x, X_exact, fp32_items ? 1 : 0, dp, tau64, (C_*)codes, amb_list,  \
-                      amb_count, amb_cap, err, spin_first);                                  \
+                      amb_count, amb_cap, err, spin_first, stages);                          \
     }
     if (code_bytes == 4) NRLSH_TC(uint32_t)
     NRLSH_TC(uint64_t)
