@@ -66,8 +66,10 @@ def bucket_stats(idx: "N.Index") -> Dict:
     (the bucket-balance figures of Sections 3.1 and 3.2)."""
     codes = N.nrlsh_get_codes(idx).numpy().view(np.uint64)
     sub, _, _ = N.nrlsh_get_partition(idx)
-    key = (sub.numpy().astype(np.uint64) << np.uint64(58)) ^ codes
-    _, counts = np.unique(key, return_counts=True)
+    # (sub-dataset, code) pairs as rows: a code may use all 64 bits, so the pair
+    # does not fit one 64-bit key
+    pairs = np.stack([sub.numpy().astype(np.uint64), codes], axis=1)
+    _, counts = np.unique(pairs, axis=0, return_counts=True)
     return {"buckets": int(counts.size), "largest_bucket": int(counts.max())}
 
 

@@ -103,6 +103,30 @@ def test_batched_graph_replay_and_clamping(N):
     assert torch.equal(ids_h, ids.cpu()) and torch.equal(sc_h, sc.cpu())
 
 
+def test_tuning_is_shared_by_indexes_of_the_same_shape(N):
+    """The autotuner's choice is kept per device and index shape for the process: a
+    rebuilt index of the same shape answers its first batched call without tuning
+    again (far fewer launches) and with the same configuration and results."""
+    n, d = 9_000, 48
+    items = rand_items(n, d, 13)
+    Q = torch.from_numpy(W.gen_queries(300, d, 14)).cuda()
+    ks = torch.full((300,), 10, dtype=torch.int32, device="cuda")
+    bs = torch.full((300,), 450, dtype=torch.int64, device="cuda")
+    runs = []
+    for _ in range(2):
+        lib, _ = build_pair(items, "f32", 8, 32, seed=6, eps=0.2)
+        torch.cuda.synchronize()
+        c0 = N.nrlsh_launch_count()
+        ids, sc = N.nrlsh_query_batched(lib, Q, ks, bs, 10, 450)
+        torch.cuda.synchronize()
+        runs.append((N.nrlsh_launch_count() - c0, N.nrlsh_get_tuning(lib), ids.cpu(), sc.cpu()))
+        lib.free()
+    (l0, t0, i0, s0), (l1, t1, i1, s1) = runs
+    assert l1 < l0, (l0, l1)
+    assert t0 == t1
+    assert torch.equal(i0, i1) and torch.equal(s0, s1)
+
+
 def test_batched_matches_single_query_path(N):
     n, d = 8_000, 64
     items = rand_items(n, d, 9)

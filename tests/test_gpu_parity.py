@@ -359,3 +359,18 @@ def test_queries_opposite_to_every_item():
                                     torch.from_numpy(budgets).cuda(), 10, int(budgets.max()))
     rids, rsc = O.query(ref, Q.astype(np.float64), ks, budgets)
     assert np.array_equal(ids.cpu().numpy(), rids) and np.array_equal(sc.cpu().numpy(), rsc)
+
+
+@pytest.mark.parametrize("L", [16, 64])
+def test_bucket_stats_count_sub_dataset_code_pairs(L):
+    """curves.bucket_stats (the bucket-balance figures of Sections 3.1-3.2) equals a
+    count of the distinct (sub-dataset, code) pairs of the oracle's index, for
+    codes of all 64 bits too."""
+    from paper_1809_08782_gb300 import curves
+    items = rand_items(6000, 24, 41)
+    lib, ref = build_pair(items, "f32", 16, L, seed=4, eps=0.2)
+    got = curves.bucket_stats(lib)
+    pairs = {}
+    for j, c in zip(ref.sub.tolist(), ref.codes.tolist()):
+        pairs[(j, c)] = pairs.get((j, c), 0) + 1
+    assert got == {"buckets": len(pairs), "largest_bucket": max(pairs.values())}

@@ -31,13 +31,14 @@ def alone(N, idx, q, k, b):
     return ids.cpu().numpy()[0], sc.cpu().numpy()[0]
 
 
-def test_results_equal_alone_and_in_the_mix(setup):
+@pytest.mark.parametrize("path", ["auto", "tensor", "bf16"])
+def test_results_equal_alone_and_in_the_mix(setup, path):
     from paper_1809_08782_gb300.serving import Request, Server, latency_summary
     N, idx, Q, ks, budgets = setup
     reqs = [Request(i, Q[i], int(ks[i]), int(budgets[i])) for i in range(len(Q))]
     rng = np.random.default_rng(3)
     arrivals = np.cumsum(rng.exponential(1.0 / 50_000.0, len(reqs)))   # Poisson, 50k q/s
-    srv = Server(idx, slots=3, memory_budget=256 << 20, max_batch=64)
+    srv = Server(idx, slots=3, memory_budget=256 << 20, max_batch=64, path=path)
     done = srv.serve(reqs, arrivals)
     assert all(r.ids is not None for r in done)
     assert srv.batches < len(reqs)            # requests were batched together
