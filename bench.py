@@ -84,7 +84,7 @@ def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
 
 
 def peaks():
-    """(HBM GB/s, bf16 TFLOP/s burst, SM max MHz, source) from the driver's file."""
+    """(HBM GB/s, bf16 TFLOP/s burst, SM max MHz, source) from MEASURED_PEAKS.json."""
     try:
         with open(PEAKS_FILE) as f:
             p = json.load(f)

@@ -79,7 +79,7 @@ typedef enum nrlsh_status {
     NRLSH_ERR_OOM = -2,          /* a device or host allocation failed */
     NRLSH_ERR_CUDA = -3,         /* a CUDA call failed */
     NRLSH_ERR_TIMEOUT = -4,      /* a bounded device wait ran out */
-    NRLSH_ERR_UNSUPPORTED = -5   /* valid request this build does not support */
+    NRLSH_ERR_UNSUPPORTED = -5   /* valid request this library or device does not support */
 } nrlsh_status;
 
 typedef enum nrlsh_dtype {
