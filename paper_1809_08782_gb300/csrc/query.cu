@@ -649,6 +649,17 @@ __device__ __forceinline__ unsigned long long double_key(double v) {
     return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// The same for an interval end point, with -0 and +0 mapped alike (so that
+// comparing keys is comparing the values), and its inverse.
+__device__ __forceinline__ unsigned long long interval_key(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    if ((u << 1) == 0ull) u = 0ull;
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
+
 // (s, id) beats (s', id') when s > s', or s == s' and id < id'.
 __device__ __forceinline__ bool better(double s, int64_t id, double s2, int64_t id2) {
     return s > s2 || (s == s2 && id < id2);
@@ -790,7 +801,9 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
     __shared__ double best_s[8];
     __shared__ int64_t bid_s[8];
     __shared__ int bc_s[8];
-    __shared__ double rank_lo[kDot2Max], rank_hi[kDot2Max];
+    // the contenders' score intervals as order-preserving integer keys (compared on
+    // the integer pipes: GB300's FP64 rate is a small fraction of its FP32 rate)
+    __shared__ unsigned long long rank_lo[kDot2Max], rank_hi[kDot2Max];
     __shared__ uint16_t flagged[kDot2Max], flagged2[kDot2Max];
     __shared__ uint32_t nflag_s, nflag2_s;
     __shared__ uint32_t idc_s[kDot2Max];      // original ids of the contenders (compensated tier)
@@ -877,8 +890,8 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
                 const double v = __dadd_rn((double)vh, (double)vl);
                 const double e = c2 * (double)qn * (double)xnl * (1.0 + 0x1p-20) +
                                  0x1p-52 * fabs(v) + 0x1p-120;
-                rank_lo[c] = __dsub_rd(v, e);
-                rank_hi[c] = __dadd_ru(v, e);
+                rank_lo[c] = interval_key(__dsub_rd(v, e));
+                rank_hi[c] = interval_key(__dadd_ru(v, e));
                 contsq[c] = v;
                 idc_s[c] = idl;
             }
@@ -889,8 +902,8 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
         if (threadIdx.x == 0) nflag_s = 0;
         __syncthreads();
         for (uint32_t c = threadIdx.x; c < nc; c += 256) {
-            const double lo_c = rank_lo[c], hi_c = rank_hi[c];
-            bool flag = __double2float_rn(lo_c) != __double2float_rn(hi_c);
+            const unsigned long long lo_c = rank_lo[c], hi_c = rank_hi[c];
+            bool flag = __double2float_rn(key_value(lo_c)) != __double2float_rn(key_value(hi_c));
             for (uint32_t c1 = 0; c1 < nc && !flag; ++c1)
                 flag = c1 != c && rank_lo[c1] <= hi_c && lo_c <= rank_hi[c1];
             if (flag) flagged[atomicAdd(&nflag_s, 1u)] = (uint16_t)c;
@@ -916,8 +929,8 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
                 }
                 if (lane == 0) {
                     const double e = __dmul_ru(cw, sa);
-                    rank_lo[c] = fmax(rank_lo[c], __dsub_rd(sd, e));
-                    rank_hi[c] = fmin(rank_hi[c], __dadd_ru(sd, e));
+                    rank_lo[c] = max(rank_lo[c], interval_key(__dsub_rd(sd, e)));
+                    rank_hi[c] = min(rank_hi[c], interval_key(__dadd_ru(sd, e)));
                     contsq[c] = sd;
                 }
             }
@@ -929,8 +942,8 @@ __device__ void dev_topk(const float* __restrict__ loq, const float* __restrict_
             __syncthreads();
             for (uint32_t f = threadIdx.x; f < nf; f += 256) {
                 const uint32_t c = flagged[f];
-                const double lo_c = rank_lo[c], hi_c = rank_hi[c];
-                bool flag = __double2float_rn(lo_c) != __double2float_rn(hi_c);
+                const unsigned long long lo_c = rank_lo[c], hi_c = rank_hi[c];
+                bool flag = __double2float_rn(key_value(lo_c)) != __double2float_rn(key_value(hi_c));
                 for (uint32_t c1 = 0; c1 < nc && !flag; ++c1)
                     flag = c1 != c && rank_lo[c1] <= hi_c && lo_c <= rank_hi[c1];
                 if (flag) flagged2[atomicAdd(&nflag2_s, 1u)] = (uint16_t)c;
