@@ -221,7 +221,11 @@ NRLSH_API nrlsh_status nrlsh_query_ex(const nrlsh_index* index, const float* que
  *   flags         NRLSH_QUERY_GRAPH: capture the launches in a CUDA graph on the first
  *                 call with these pointers and sizes, and replay it on later identical
  *                 calls (needs a non-NULL stream; the graph and its workspace live
- *                 until nrlsh_free).
+ *                 until nrlsh_free); NRLSH_QUERY_ASYNC_INPUT: host queries, ks and
+ *                 budgets are read by `stream` in order and the call does not wait
+ *                 for their copies; the path flags below.
+ * The tensor-core path runs the queries in chunks whose workspace is at most an
+ * eighth of the device's memory (at most 32 GiB).
  * The first call for a given shape (device, the index's n, d, m, L, dtype and eps,
  * and the call's nq, k_max, budget_max and path flags) times the candidate
  * configurations on a prefix of the batch (the autotuner) and keeps the fastest
