@@ -58,7 +58,7 @@ SMS = 152
 # reported only while the kernel's source file is byte-identical to the captured one.
 # (profiles/probe_rerank_persistent_netflix.md: ncu replays with flushed caches, so these
 # are first-touch bytes of one launch.)
-TRAFFIC = {"probe_rerank_persistent": ("query.cu", "bb468b32ca5d7f28", 5948672)}
+TRAFFIC = {"probe_rerank_persistent": ("query.cu", "63560376fe2e762d", 5950464)}
 
 
 def env_rank():
