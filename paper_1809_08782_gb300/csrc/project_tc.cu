@@ -3,15 +3,17 @@
 // bfloat16 items (n x d, row stride dp) and A the bfloat16-valued projections,
 // accumulated in FP32 in tensor memory, then + a_d tau and the sign.
 //
-// Persistent warp-specialised CTAs (192 threads):
+// Persistent warp-specialised CTAs (320 threads, two per SM when there are more
+// tiles than SMs):
 //   warp 0   one thread issues TMA loads: all of A^T once (K-major, 128-byte
 //            swizzle), then a ring of stages, each a 128-item x 64-K tile of X~
 //            (fp32 items: two tiles, the bf16 high and low parts of x);
 //   warp 1   allocates 128 TMEM columns (two accumulators of up to 64 columns)
 //            and one thread issues tcgen05.mma (M = 128, N = 16..64, K = 16);
-//   warps 2-5 read the accumulator rows (warp w reads TMEM lanes 32 (w % 4)..),
-//            add the tail term, decide each bit against a proven bound and
-//            write the code word; undecided (item, bit) pairs go to a list that
+//   warps 2-9 read the accumulator rows (warp w reads TMEM lanes 32 (w % 4)..;
+//            warps 2-5 columns 0-31, warps 6-9 columns 32-63), add the tail
+//            term, decide each bit against a proven bound and write their half
+//            of the code word; undecided (item, bit) pairs go to a list that
 //            the FP32 and FP64 tiers resolve.
 // Every mbarrier wait is bounded; on a timeout the kernel records an error in
 // *err, stops issuing work, waits (bounded) for its own copies, frees TMEM and
@@ -36,7 +38,8 @@ __device__ __forceinline__ void set_code_bit(uint32_t* w, int bit) { atomicOr(w,
 __device__ __forceinline__ void set_code_bit(uint64_t* w, int bit) {
     atomicOr((unsigned long long*)w, 1ull << bit);
 }  // ring stages (each one or, for split fp32 items, two 16 KB tiles)
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 320;
+constexpr int kEpiWarps = 8;         // two per TMEM lane quadrant, one per 32-column half
 constexpr uint32_t kTmemCols = 128;  // two accumulators of up to 64 fp32 columns
 constexpr uint32_t kXStageBytes = kTcM * kTcKC * 2;
 
@@ -53,7 +56,7 @@ struct TcSmem {
 };
 
 template <typename C>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     project_tc_kernel(const __grid_constant__ CUtensorMap map_x,
                       const __grid_constant__ CUtensorMap map_x2,
                       const __grid_constant__ CUtensorMap map_a, int split, int64_t n, int nkc, int L,
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float* s_c1 = (float*)(tmem_slot + 4);       // 64: (kappa_tc + round_x) ||a_b||
     float* s_c2 = s_c1 + 64;                     // 64: 2^-20 |a_{d,b}|
     float* s_ad = s_c2 + 64;                     // 64: a_{d,b}
-    unsigned long long* amb_s = (unsigned long long*)(s_ad + 64);   // 4 x kAmbWarp entries
+    unsigned long long* amb_s = (unsigned long long*)(s_ad + 64);   // kEpiWarps x kAmbWarp entries
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = ceil_div(n, kTcM);
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 128);
+            mbar_init(&acc_empty[b], 32 * kEpiWarps);
         }
         mbar_init(a_bar, 1);
         mbar_init(drain, 1);
@@ -206,8 +209,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_wait(drain, 0);
         }
     } else {
-        // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) + lane
+        // ---- epilogue: warps 2..9, TMEM lanes 32 (warp % 4) + lane; warps 2..5 take
+        // bits 0..31 of their rows, warps 6..9 bits 32..63
         const int sub = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const bool has_bits = 32 * half < L;   // warp-uniform
         int buf = 0;
         uint32_t acc_phase = 0;
         // the row's norm bound and tau of the next tile are loaded while this
@@ -226,6 +232,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             return acc >= 0.0;
         };
         unsigned long long* wbuf = amb_s + (warp - 2) * kAmbWarp;
+        uint32_t* codes32 = (uint32_t*)codes;
         unsigned wn = 0;   // entries in this warp's buffer (uniform in the warp)
         auto flush = [&]() {
             __syncwarp();
@@ -266,38 +273,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             fence_after();
             const int64_t row = row_of(t);
             const bool valid = row < n;
-            unsigned long long word = 0, undecided = 0;
-            // all of the row's columns in flight at once (up to 64), then one wait
-            uint32_t r2[2][32];
-            const uint32_t taddr = tmem_base + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * 64);
-            tmem_ld32_nowait(taddr, r2[0]);
-            if (N > 32) tmem_ld32_nowait(taddr + 32, r2[1]);
-            tmem_wait_ld();
+            uint32_t word = 0, undecided = 0;   // bits 32 half + i of the row's code
+            uint32_t r[32];
+            if (has_bits) {
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * sub) << 16) +
+                                       (uint32_t)(buf * 64 + 32 * half);
+                tmem_ld32_nowait(taddr, r);
+                tmem_wait_ld();
+            }
             // the accumulator is in registers: the MMA may overwrite it now
             fence_before();
             mbar_arrive(&acc_empty[buf]);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            if (has_bits) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const int bit = 32 * h + i;
+                    const int bit = 32 * half + i;
                     if (!valid || bit >= L) continue;
-                    const uint32_t* r = r2[h];
                     const float v = fmaf(s_ad[bit], t32, __uint_as_float(r[i]));
                     // accumulation bound (kappa_tc) plus, for fp32 items, the bf16
                     // rounding of x (round_x); Cauchy-Schwarz for sum |a_k x_k|
                     const float bound = fmaf(s_c1[bit], xn, s_c2[bit] * t32);
                     if (fabsf(v) * (1.0f - 0x1p-21f) > bound) {
-                        if (v > 0.0f) word |= 1ull << bit;
+                        if (v > 0.0f) word |= 1u << i;
                     } else {
-                        undecided |= 1ull << bit;
+                        undecided |= 1u << i;
                     }
                 }
             }
             // undecided pairs go to this warp's buffer in shared memory, flushed to
             // the global list (one reservation per flush) when it would overflow;
             // a flush only touches rows of earlier tiles, already stored
-            const unsigned cnt = (unsigned)__popcll(undecided);
+            const unsigned cnt = (unsigned)__popc(undecided);
             unsigned incl = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -308,9 +314,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (tot <= (unsigned)kAmbWarp) {
                 unsigned pos = wn + incl - cnt;
                 while (undecided) {
-                    const int bit = __ffsll((long long)undecided) - 1;
+                    const int i = __ffs(undecided) - 1;
                     undecided &= undecided - 1;
-                    wbuf[pos++] = ((unsigned long long)row << 6) | (unsigned)bit;
+                    wbuf[pos++] = ((unsigned long long)row << 6) | (unsigned)(32 * half + i);
                 }
                 wn += tot;
             } else {
@@ -320,16 +326,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 wbase = __shfl_sync(0xffffffffu, wbase, 31);
                 unsigned slot = wbase + incl - cnt;
                 while (undecided) {
-                    const int bit = __ffsll((long long)undecided) - 1;
+                    const int i = __ffs(undecided) - 1;
                     undecided &= undecided - 1;
+                    const int bit = 32 * half + i;
                     if (slot < amb_cap)
                         amb_list[slot] = ((unsigned long long)row << 6) | (unsigned)bit;
                     else if (canonical(row, bit))
-                        word |= 1ull << bit;
+                        word |= 1u << i;
                     ++slot;
                 }
             }
-            if (valid) codes[row] = (C)word;
+            // each half stores its own 32 bits of the code (one word for L <= 32)
+            if (valid && has_bits) {
+                if (sizeof(C) == 4)
+                    codes32[row] = word;
+                else
+                    codes32[2 * row + half] = word;
+            }
             if (++buf == 2) {
                 buf = 0;
                 acc_phase ^= 1;
@@ -378,7 +391,7 @@ bool make_map_bf16(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t out
 size_t project_tc_smem_bytes(int d, int N, int split, int stages) {
     const int nkc = (int)ceil_div(d, kTcKC);
     return 1024 + (size_t)nkc * N * 128 + (size_t)stages * split * kXStageBytes + 256 + 3 * 64 * 4 +
-           4 * kAmbWarp * 8;
+           kEpiWarps * kAmbWarp * 8;
 }
 
 // With more tiles than SMs, the deepest ring (at most kTcMaxStages) that keeps two
