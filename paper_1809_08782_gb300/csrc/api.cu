@@ -643,14 +643,23 @@ nrlsh_status build_impl(const void* items, int64_t n, int32_t d, int32_t m, int3
                                    ix->anorm, ix->tau32, ix->tau64, ix->xnorm, dtype == NRLSH_F32,
                                    ix->codes, ix->code_bytes, amb_list, ix->ambiguous,
                                    (unsigned)amb_cap, ix->dev_err, st, test_spin_first()));
-            // bits the tensor-core bound left open: FP32 on CUDA cores, then FP64
-            B_CU(launch_resolve_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->anorm,
-                                     ix->xnorm, ix->tau32, ix->tau64, amb_list, ix->ambiguous,
-                                     (unsigned)amb_cap, ix->codes, ix->code_bytes, amb_list2,
-                                     amb_count2, (unsigned)amb_cap2, st));
-            B_CU(launch_resolve_fp64(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad, ix->tau64,
-                                     amb_list2, amb_count2, (unsigned)amb_cap2, ix->codes,
-                                     ix->code_bytes, st));
+            // bits the tensor-core bound left open: compensated FP32, FP64 and canonical
+            // tiers in one launch (with the fp32 A^T copy), else FP32 then FP64 lists
+            if (ix->At32) {
+                B_CU(launch_resolve_tiers(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->At32,
+                                          ix->A_pad, ix->anorm, ix->xnorm, ix->tau64, amb_list,
+                                          ix->ambiguous, (unsigned)amb_cap, ix->codes,
+                                          ix->code_bytes, st));
+            } else {
+                B_CU(launch_resolve_fp32(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad,
+                                         ix->anorm, ix->xnorm, ix->tau32, ix->tau64, amb_list,
+                                         ix->ambiguous, (unsigned)amb_cap, ix->codes,
+                                         ix->code_bytes, amb_list2, amb_count2,
+                                         (unsigned)amb_cap2, st));
+                B_CU(launch_resolve_fp64(ix->Xp, dtype, n, d, ix->dp, L, ix->Lp, ix->A_pad,
+                                         ix->tau64, amb_list2, amb_count2, (unsigned)amb_cap2,
+                                         ix->codes, ix->code_bytes, st));
+            }
         }
         // Eq. 12 and the sorted (U_j, l) structure (the cosines, and for the
         // queries the offsets, come from side stream 1)

@@ -218,6 +218,14 @@ cudaError_t launch_resolve_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
                                 unsigned cap, void* codes, int code_bytes,
                                 unsigned long long* list2, unsigned* count2, unsigned cap2,
                                 cudaStream_t st);
+// The tensor-core pass's open bits in one launch (compensated FP32, FP64, canonical
+// tiers, a warp per listed pair); needs the fp32 A^T copy (At32, warp_proj_stride
+// layout): cudaErrorNotSupported without it.
+cudaError_t launch_resolve_tiers(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                 int Lp, const float* At32, const float* A_pad, const float* anorm,
+                                 const float* xnorm, const double* tau64,
+                                 const unsigned long long* list, const unsigned* count,
+                                 unsigned cap, void* codes, int code_bytes, cudaStream_t st);
 cudaError_t launch_resolve_fp64(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
                                 int Lp, const float* A_pad, const double* tau64,
                                 const unsigned long long* list, const unsigned* count,

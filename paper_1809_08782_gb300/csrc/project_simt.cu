@@ -452,6 +452,33 @@ cudaError_t project_rows(const void* X, int64_t n, int d, int ldx, int L, int Lp
 
 constexpr size_t kWarpProjMaxSmem = 227 * 1024;
 
+// The bits the tensor-core pass left open, settled in one launch: a warp per
+// listed (row, bit) runs the compensated FP32 tier, then (rarely) the FP64 tier and
+// the canonical form (settle_bit_warp), with column b of A read contiguously from
+// the fp32 A^T copy (row stride dpa).
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    resolve_tiers_kernel(const T* __restrict__ X, int d, int ldx, int Lp, int dpa,
+                         const float* __restrict__ At32, const float* __restrict__ A_pad,
+                         const float* __restrict__ anorm, const float* __restrict__ xnorm,
+                         const double* __restrict__ tau64, const unsigned long long* __restrict__ list,
+                         const unsigned* __restrict__ count, unsigned cap, C* __restrict__ codes) {
+    NRLSH_PDL_ENTRY();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned cnt = min(*count, cap);
+    for (int64_t e = warp; e < cnt; e += nwarps) {
+        const unsigned long long entry = list[e];
+        const int64_t row = (int64_t)(entry >> 6);
+        const int bit = (int)(entry & 63);
+        const bool set = settle_bit_warp(X + row * ldx, d, At32 + (int64_t)bit * dpa,
+                                         A_pad[(int64_t)d * Lp + bit], tau64[row], true, xnorm[row],
+                                         anorm[bit], A_pad, Lp, bit);
+        if (lane == 0 && set) or_bit(codes + row, bit);
+    }
+}
+
 }  // namespace
 
 // Row stride (columns) of A^T for the warp-per-row projection, or 0 when it does
@@ -726,6 +753,28 @@ cudaError_t launch_resolve_fp32(const void* X, nrlsh_dtype dt, int64_t n, int d,
     if (code_bytes == 4) NRLSH_R32(float, uint32_t)
     NRLSH_R32(float, uint64_t)
 #undef NRLSH_R32
+}
+
+cudaError_t launch_resolve_tiers(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
+                                 int Lp, const float* At32, const float* A_pad, const float* anorm,
+                                 const float* xnorm, const double* tau64,
+                                 const unsigned long long* list, const unsigned* count,
+                                 unsigned cap, void* codes, int code_bytes, cudaStream_t st) {
+    const int dpa = warp_proj_stride(d, Lp);
+    if (dpa == 0 || At32 == nullptr) return cudaErrorNotSupported;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(n * L / 32, 32), 8),
+                                                      16 * 152);
+#define NRLSH_RT(T_, C_)                                                                     \
+    return launch("resolve_tiers", resolve_tiers_kernel<T_, C_>, dim3(grid), dim3(256), 0, st, \
+                  (const T_*)X, d, ldx, Lp, dpa, At32, A_pad, anorm, xnorm, tau64, list, count, \
+                  cap, (C_*)codes);
+    if (dt == NRLSH_BF16) {
+        if (code_bytes == 4) NRLSH_RT(__nv_bfloat16, uint32_t)
+        NRLSH_RT(__nv_bfloat16, uint64_t)
+    }
+    if (code_bytes == 4) NRLSH_RT(float, uint32_t)
+    NRLSH_RT(float, uint64_t)
+#undef NRLSH_RT
 }
 
 cudaError_t launch_resolve_fp64(const void* X, nrlsh_dtype dt, int64_t n, int d, int ldx, int L,
